@@ -1,0 +1,292 @@
+"""Pins of the oracle's filament model and solver (paper Sec. 2.4-2.9, 3, App. B).
+
+* moments: straight untwisted filament -> 0; a helix (constant relative
+  rotation) -> closed form derived from the quaternion algebra; a small planar
+  bend -> the planar formula K_B t_n x t_{n+1} / dL of Sec. 2.8.1,
+* telescoping invariants of the discrete balances (net constraint force and
+  net elastic torque vanish; internal loads exert no net moment when the
+  constraint holds),
+* residual at rest is exactly zero and the state stays at rest,
+* a sedimenting sphere and a sphere pair follow the Stokes / RPY velocities,
+* J0 of App. B.2 equals the finite-difference Jacobian of the drag-only f_0
+  at a straight, untwisted state (where its approximations are exact),
+* Algorithm 2's limited-memory iterates equal the textbook dense bad-Broyden
+  update, and a linear problem with J0 = J converges in one iteration,
+* a converged timestep equals a finite-difference Newton solve,
+* quaternions stay unit across steps (multiplicative update, Sec. 2.9.3).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+from oracle import filament as fo
+
+
+def _params(**kw):
+    base = dict(a=1.0, eta=1.0, dL=2.2, KB=2.0, KT=1.3, dt=0.05, tol=1e-12, max_iter=60)
+    base.update(kw)
+    return fo.Params(**base)
+
+
+def _rand_quat(rng):
+    q = rng.standard_normal(4)
+    return q / np.linalg.norm(q)
+
+
+def test_straight_untwisted_has_no_moment():
+    rng = np.random.default_rng(0)
+    p = _params()
+    q = np.tile(_rand_quat(rng), (5, 1))
+    M = fo.internal_moments(q[:-1], q[1:], p)
+    np.testing.assert_allclose(M, 0.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("theta", [1e-3, 0.4, 1.7])
+def test_helix_closed_form(theta):
+    """q_{n+1} = r q_n with r a rotation by theta about v: the moment is
+    R(q_{n+1/2}) D ((4/dL) sin(theta/4) R(q_n)^T v - (g0, kmu, knu)), with
+    q_{n+1/2} the rotation by theta/2 about v applied after q_n."""
+    rng = np.random.default_rng(int(theta * 1000))
+    p = _params(KB=1.7, KT=0.9, gamma0=0.2, kappa_mu=-0.3, kappa_nu=0.15)
+    v = rng.standard_normal(3)
+    v /= np.linalg.norm(v)
+    r = np.concatenate([[math.cos(theta / 2)], math.sin(theta / 2) * v])
+    qn = _rand_quat(rng)
+    qn1 = fo.qmul(r, qn)
+    M = fo.internal_moments(qn[None], qn1[None], p)[0]
+    Rn = Rotation.from_quat(np.roll(qn, -1)).as_matrix()        # scipy is scalar-last
+    Rh = Rotation.from_rotvec(theta / 2 * v).as_matrix() @ Rn
+    D = np.diag([p.KT, p.KB, p.KB])
+    expect = Rh @ D @ ((4 / p.dL) * math.sin(theta / 4) * Rn.T @ v
+                       - np.array([p.gamma0, p.kappa_mu, p.kappa_nu]))
+    np.testing.assert_allclose(M, expect, rtol=1e-12, atol=1e-13)
+
+
+def test_small_planar_bend_matches_planar_formula():
+    """Bending in the plane normal to nu by a small angle: the 3D moment tends
+    to K_B t_n x t_{n+1} / dL (eq. discrete2Dmoments) with O(theta^3) error."""
+    p = _params(KB=1.0, KT=5.0)
+    for th in (1e-2, 1e-3):
+        q0 = fo.quat_from_frame([1.0, 0, 0], [0, 1.0, 0])[0]
+        r = np.array([math.cos(th / 2), 0, 0, math.sin(th / 2)])     # about e_z = nu
+        q1 = fo.qmul(r, q0)
+        M = fo.internal_moments(q0[None], q1[None], p)[0]
+        t0 = fo.frames(q0)[0]
+        t1 = fo.frames(q1)[0]
+        planar = p.KB * np.cross(t0, t1) / p.dL
+        assert np.linalg.norm(M - planar) <= th ** 3 * p.KB / p.dL
+
+
+def _random_filament_state(rng, lay, p, twist=0.3):
+    base = rng.standard_normal((lay.M, 3))
+    from paper_1903_12609_gb300.inputs import random_frames
+    t, mu = random_frames(rng, lay.M)
+    xi = twist * rng.standard_normal((lay.S, 3))
+    return fo.initial_state(lay, p, base, t, mu, xi)
+
+
+def test_telescoping_and_net_moment():
+    rng = np.random.default_rng(3)
+    lay = fo.Layout([7, 4])
+    p = _params()
+    st = _random_filament_state(rng, lay, p)
+    u = 0.2 * rng.standard_normal((lay.S, 3))
+    lam = rng.standard_normal((lay.n_lam, 3))
+    X = lay.join_X(np.array([st.Y[0], st.Y[7]]), u, lam)
+    q, t, Y, _, lam2 = fo.unpack(lay, p, X, st.q)
+    F, T = fo.forces_torques(lay, p, q, t, lam2, None)
+    for i in range(lay.M):
+        s, e = lay.off_seg[i], lay.off_seg[i + 1]
+        np.testing.assert_allclose(F[s:e].sum(axis=0), 0.0, atol=1e-13)
+        net = T[s:e].sum(axis=0) + np.cross(Y[s:e], F[s:e]).sum(axis=0)
+        np.testing.assert_allclose(net, 0.0, atol=1e-12)
+    # elastic torques alone also telescope
+    F0, T0 = fo.forces_torques(lay, p, q, t, np.zeros_like(lam2), None)
+    np.testing.assert_allclose(F0, 0.0, atol=0)
+    for i in range(lay.M):
+        s, e = lay.off_seg[i], lay.off_seg[i + 1]
+        np.testing.assert_allclose(T0[s:e].sum(axis=0), 0.0, atol=1e-13)
+
+
+def test_rest_state_is_a_solution():
+    rng = np.random.default_rng(4)
+    lay = fo.Layout([6])
+    p = _params()
+    from paper_1903_12609_gb300.inputs import random_frames
+    t, mu = random_frames(rng, 1)
+    st = fo.initial_state(lay, p, np.array([[1.0, 2.0, 3.0]]), t, mu)
+    st.Yprev = st.Y.copy()
+    st.u = np.zeros((lay.S, 3))
+    X0 = fo.initial_guess(lay, st)
+    f = fo.residual(lay, p, st, None, X0)
+    np.testing.assert_allclose(f, 0.0, atol=1e-14)
+    st2, iters = fo.step(lay, p, st, None)
+    assert iters == 0
+    np.testing.assert_allclose(st2.Y, st.Y, atol=1e-14)
+    np.testing.assert_allclose(st2.q, st.q, atol=1e-15)
+
+
+def test_single_sphere_sediments_at_stokes_velocity():
+    lay = fo.Layout([1])
+    p = _params(dt=0.3)
+    st = fo.State(Y=np.array([[0.0, 0.0, 5.0]]), q=np.array([[1.0, 0, 0, 0]]))
+    ext = fo.External(Fext=np.array([[0.0, 0.0, -2.0]]))
+    V = -2.0 / (6 * math.pi)
+    for j in range(4):
+        st, iters = fo.step(lay, p, st, ext)
+        # f is linear with J0 = I: one iteration on the first step; afterwards the
+        # linear extrapolation of Y_1 is already exact for uniform motion
+        assert iters == (1 if j == 0 else 0)
+        np.testing.assert_allclose(st.Y[0], [0, 0, 5.0 + (j + 1) * p.dt * V], atol=1e-13)
+        np.testing.assert_allclose(st.q[0], [1, 0, 0, 0], atol=1e-15)
+
+
+def test_sphere_pair_sediments_at_rpy_velocity():
+    lay = fo.Layout([1, 1])
+    d = 5.0
+    p = _params(dt=0.2)
+    st = fo.State(Y=np.array([[0.0, 0, 0], [d, 0, 0]]), q=np.tile([1.0, 0, 0, 0], (2, 1)))
+    ext = fo.External(Fext=np.array([[0, 0, -1.0], [0, 0, -1.0]]))
+    V = -(1 / (6 * math.pi) + (1 + 2 / (3 * d * d)) / (8 * math.pi * d))
+    for j in range(3):
+        st, _ = fo.step(lay, p, st, ext)
+        np.testing.assert_allclose(st.Y[:, 2], (j + 1) * p.dt * V, atol=1e-11)
+        np.testing.assert_allclose(st.Y[:, 0], [0, d], atol=1e-11)
+
+
+def _fd_jacobian(fun, X, h=1e-6):
+    f0 = fun(X)
+    J = np.zeros((f0.size, X.size))
+    for k in range(X.size):
+        e = np.zeros_like(X)
+        e[k] = h
+        J[:, k] = (fun(X + e) - fun(X - e)) / (2 * h)
+    return J
+
+
+@pytest.mark.parametrize("bdf2", [False, True])
+def test_J0_equals_fd_jacobian_of_drag_model_when_straight(bdf2):
+    rng = np.random.default_rng(5)
+    lay = fo.Layout([5])
+    p = _params(KB=1.5, KT=0.7)
+    from paper_1903_12609_gb300.inputs import random_frames
+    t, mu = random_frames(rng, 1)
+    st = fo.initial_state(lay, p, np.zeros((1, 3)), t, mu)
+    if bdf2:
+        st.Yprev = st.Y + 0.01
+        st.u = 0.01 * rng.standard_normal((lay.S, 3))
+    lam = rng.standard_normal((lay.n_lam, 3))
+    X = lay.join_X(st.Y[:1], np.zeros((lay.S, 3)), lam)
+    J0 = fo.jacobian0(lay, p, st, X)[0]
+
+    def f0(Xv):
+        return fo.residual(lay, p, st, None, Xv, mob=fo.drag_mobility)
+
+    Jfd = _fd_jacobian(f0, X)
+    np.testing.assert_allclose(J0, Jfd, rtol=0, atol=1e-8 * np.abs(Jfd).max())
+
+
+def test_J0_is_close_to_fd_jacobian_when_bent():
+    """Away from the straight state J0 is an approximation (Taylor-truncated
+    dexpinv, frame-vector moments); it stays a few per cent from the exact
+    drag-model Jacobian for a gently bent, twisted filament."""
+    rng = np.random.default_rng(6)
+    lay = fo.Layout([6])
+    p = _params(KB=1.5, KT=0.7)
+    st = _random_filament_state(rng, lay, p, twist=0.05)
+    lam = 0.3 * rng.standard_normal((lay.n_lam, 3))
+    u = 0.05 * rng.standard_normal((lay.S, 3))
+    X = lay.join_X(st.Y[:1], u, lam)
+    J0 = fo.jacobian0(lay, p, st, X)[0]
+    Jfd = _fd_jacobian(lambda Xv: fo.residual(lay, p, st, None, Xv, mob=fo.drag_mobility), X)
+    rel = np.linalg.norm(J0 - Jfd) / np.linalg.norm(Jfd)
+    assert rel < 0.05
+
+
+def _dense_bad_broyden(fun, J0inv, X0, iters):
+    X = X0.copy()
+    f = fun(X)
+    H = J0inv.copy()
+    out = []
+    for _ in range(iters):
+        dX = -H @ f
+        Xn = X + dX
+        fn = fun(Xn)
+        df = fn - f
+        H = H + np.outer(dX - H @ df, df) / (df @ df)
+        X, f = Xn, fn
+        out.append(X.copy())
+    return out
+
+
+def test_limited_memory_broyden_equals_dense_update():
+    rng = np.random.default_rng(7)
+    n = 12
+    A = np.eye(n) * 3 + 0.3 * rng.standard_normal((n, n))
+    b = rng.standard_normal(n)
+
+    def fun(X):
+        return A @ X + 0.2 * np.sin(X) + 0.05 * X ** 3 - b
+
+    J0inv = np.linalg.inv(A)
+    X0 = np.zeros(n)
+    br = fo.Broyden(fun, lambda v: J0inv @ v, X0, 1e-14)
+    dense = _dense_bad_broyden(fun, J0inv, X0, 8)
+    for k in range(8):
+        X, _ = br.iterate()
+        np.testing.assert_allclose(X, dense[k], rtol=1e-12, atol=1e-13)
+
+
+def test_linear_problem_with_exact_J0_converges_in_one_iteration():
+    rng = np.random.default_rng(8)
+    n = 9
+    A = np.eye(n) + 0.4 * rng.standard_normal((n, n))
+    b = rng.standard_normal(n)
+    Ainv = np.linalg.inv(A)
+    br = fo.Broyden(lambda X: A @ X - b, lambda v: Ainv @ v, np.zeros(n), 1e-12)
+    br.iterate()
+    assert br.converged()
+    np.testing.assert_allclose(br.X, np.linalg.solve(A, b), rtol=1e-12)
+
+
+def test_converged_step_equals_newton_solution():
+    rng = np.random.default_rng(9)
+    lay = fo.Layout([4])
+    p = _params(KB=3.0, KT=3.0, dt=0.1, tol=1e-13)
+    _, t, mu, xi = (np.zeros((1, 3)), np.array([[0.6, 0, 0.8]]), np.array([[0, 1.0, 0]]),
+                    0.05 * rng.standard_normal((4, 3)))
+    st = fo.initial_state(lay, p, np.zeros((1, 3)), t, mu, xi)
+    ext = fo.External(Fext=np.tile([0, 0, -0.5], (4, 1)))
+    br = fo.begin_step(lay, p, st, ext)
+    while not br.converged():
+        br.iterate()
+
+    def fun(X):
+        return fo.residual(lay, p, st, ext, X)
+
+    X = fo.initial_guess(lay, st)
+    for _ in range(20):
+        f = fun(X)
+        if np.abs(f).max() < 1e-14:
+            break
+        X = X - np.linalg.solve(_fd_jacobian(fun, X, 1e-7), f)
+    np.testing.assert_allclose(br.X, X, rtol=0, atol=1e-10)
+
+
+def test_quaternions_stay_unit_over_steps():
+    rng = np.random.default_rng(10)
+    lay = fo.Layout([6, 5])
+    p = _params(KB=2.0, KT=2.0, dt=0.2, tol=1e-10)
+    st = _random_filament_state(rng, lay, p, twist=0.1)
+    ext = fo.External(Fext=np.tile([0, 0, -1.0], (lay.S, 1)), follower=np.array([0.0, 0.3]))
+    for _ in range(4):
+        st, _ = fo.step(lay, p, st, ext)
+        np.testing.assert_allclose(np.linalg.norm(st.q, axis=1), 1.0, atol=2e-15)
+        # the constraint holds at every committed state
+        t = fo.frames(st.q)[0]
+        for i in range(lay.M):
+            s, e = lay.off_seg[i], lay.off_seg[i + 1]
+            g = st.Y[s + 1:e] - st.Y[s:e - 1] - 0.5 * p.dL * (t[s:e - 1] + t[s + 1:e])
+            np.testing.assert_allclose(g, 0.0, atol=1e-13)
