@@ -1,0 +1,361 @@
+"""Benchmark: RPY pair interactions per second during BDF2 timesteps of a
+32 000-segment filament suspension on one GB300 (per GPU; weak scaling over
+independent replicas when launched on several GPUs).
+
+One step = one whole timestep of the method: initial guess, J0 assembly and
+banded LU, the Broyden loop (each iteration: unpack, forces, RPY mobility over
+all S^2 pairs, residual, J0 solve, rank-one update) and the commit. The value
+is the number of RPY pair interactions evaluated in the timed steps divided by
+their device time (S^2 per residual evaluation; begin + one per iteration).
+
+Workload (synthetic, seeded; shapes of the paper's 3D filament clouds):
+1000 filaments x 32 segments, a = 1, dL = 2.2a, eta = 1, isotropic straight
+initial filaments in a cube at 2% volume fraction (overlaps redrawn); the first
+500 filaments sediment under gravity (B = L^3 W / K_B = 1000), the other 500
+carry a compressive tip follower force f L^2 / K_B = 100 and no weight;
+dt = T/200 with T = eta L / W; Broyden tolerance 1e-4 (||f||_inf <= tol a).
+Precision: FP32-compensated pair sums, FP64 everything else ("mixed").
+
+Output: one JSON line (see the keys below). --impl reference times the FP64
+CPU oracle on bounded samples of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("RPY pair interactions/s (% FMA peak); timesteps/s at 32k segments, "
+          "plain vs chosen form")
+UNIT = "pair interactions/s"
+FLOPS_PER_PAIR = 81          # algorithmic flops of one far-field pair (FMA = 2)
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+FP32_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.55
+
+
+def workload(n_fil=1000, n_seg=32, seed=0):
+    from paper_1903_12609_gb300.inputs import cloud_frames, workload_params
+    wl = workload_params(n_fil, n_seg, B=1000.0, dt_over_T=1.0 / 200.0, tol=1e-4, max_iter=60)
+    base, t, mu, side = cloud_frames(n_fil, n_seg, dL=wl.dL, volume_fraction=0.02, seed=seed)
+    S = n_fil * n_seg
+    passive = np.arange(n_fil) < n_fil // 2
+    Fext = np.zeros((S, 3))
+    Fext[np.repeat(passive, n_seg), 2] = -wl.W * wl.dL
+    L = wl.extra["L"]
+    follower = np.where(passive, 0.0, 100.0 * wl.KB / L ** 2)
+    return wl, base, t, mu, Fext, follower
+
+
+def clocks_start():
+    try:
+        f = open(os.path.join(ROOT, ".bench_clocks.csv"), "w")
+        p = subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def clocks_stop(handle, gpu_index):
+    p, f = handle
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    path = os.path.join(ROOT, ".bench_clocks.csv")
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    os.remove(path)
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(Y, FT, seconds=10.0):
+    """The FP64 oracle on the host cores: a bounded sample of target rows of one
+    mobility apply of the same workload, scaled to pairs/s."""
+    from oracle import rpy
+    cores = os.cpu_count() or 1
+    S = Y.shape[0]
+    rows = np.arange(64, dtype=np.int32)
+    t0 = time.perf_counter()
+    rpy.apply_rows(Y, FT, rows, nthreads=cores)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    n = int(min(S, max(64, 64 * seconds / dt)))
+    rows = np.linspace(0, S - 1, n).astype(np.int32)
+    t0 = time.perf_counter()
+    rpy.apply_rows(Y, FT, rows, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n * S / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d target rows x %d sources of one mobility apply (%.1f s)" % (n, S, dt)}
+
+
+def traffic_from_profile(kernel_src):
+    """dram bytes per launch from the committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "rpy_pair32_suspension32k_counters.json")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+        if rec.get("source_sha256") == h:
+            return rec.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from oracle import build as obuild
+    obuild.build()
+    from oracle import rpy
+    wl, base, t, mu, Fext, follower = workload()
+    S = 1000 * 32
+    Y = np.concatenate([base[i] + np.arange(32)[:, None] * wl.dL * t[i] for i in range(1000)])
+    FT = np.random.default_rng(1).standard_normal((S, 6))
+    cores = os.cpu_count() or 1
+    rows = np.linspace(0, S - 1, 2048).astype(np.int32)
+    for _ in range(args.warmup):
+        rpy.apply_rows(Y, FT, rows[:64], nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rpy.apply_rows(Y, FT, rows, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = args.steps * rows.size * S / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "FP64 CPU oracle: %d target rows x 32000 sources of the "
+                                   "RPY mobility apply per step (suspension 1000x32)" % rows.size,
+                       "segments": S},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d rows x %d sources per step" % (rows.size, S)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--plain-steps", type=int, default=2,
+                    help="timed steps of the plain FP64 form for comparison (0 = skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1903_12609_gb300 import fil
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n_fil, n_seg = 1000, 32
+    S = n_fil * n_seg
+    wl, base, t, mu, Fext, follower = workload(n_fil, n_seg, seed=rank)
+    stream = torch.cuda.Stream()
+    prec = fil.FIL_MIXED if args.precision == "mixed" else fil.FIL_FP64
+    params = dict(a=wl.a, eta=wl.eta, dL=wl.dL, KB=wl.KB, KT=wl.KT, dt=wl.dt, tol=wl.tol,
+                  max_iter=wl.max_iter)
+    m = fil.Filaments(wl.seg_per_fil, precision=prec, stream=stream.cuda_stream, **params)
+    m.init_straight(base, t, mu, None)
+    m.set_external(Fext, None, follower)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        m.step()
+
+    # ---- timed region: K steps, L2 flushed between steps ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    a0, i0, k0 = m.counters()
+    m.profile(True)
+    m.profile_read()
+    barrier()
+    clk = clocks_start()
+    t_wall = time.perf_counter()
+    iters = []
+    with torch.cuda.stream(stream):
+        for j in range(args.steps):
+            flush.fill_(float(j))
+            ev[j][0].record(stream)
+            iters.append(m.step())
+            ev[j][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = clocks_stop(clk, local)
+    n_pair_launch, pair_ms = m.profile_read()
+    m.profile(False)
+    a1, i1, k1 = m.counters()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    dev_ms = float(sum(step_ms))
+    applies = a1 - a0
+    pairs = applies * float(S) * S
+    local_val = pairs / (dev_ms * 1e-3)
+
+    # whole-job aggregate: units of all ranks over the slowest rank's time
+    tot_pairs, max_ms = pairs, dev_ms
+    if dist is not None:
+        tt = torch.tensor([pairs, dev_ms], dtype=torch.float64, device="cuda")
+        p_all = tt.clone()
+        dist.all_reduce(p_all[:1], op=dist.ReduceOp.SUM)
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.MAX)
+        tot_pairs, max_ms = float(p_all[0]), float(tt[1])
+    value = tot_pairs / (max_ms * 1e-3)
+
+    # ---- dominant kernel: the RPY pair kernel, timed live by the library ----
+    pair_avg_ms = pair_ms / max(n_pair_launch, 1)
+    achieved = FLOPS_PER_PAIR * float(S) * S / (pair_avg_ms * 1e-3) / 1e12
+    kernel_src = os.path.join(ROOT, "paper_1903_12609_gb300", "csrc", "rpy.cu")
+    traffic = traffic_from_profile(kernel_src) if prec == fil.FIL_MIXED else None
+
+    # ---- end to end through the C ABI with host buffers ----
+    Yh = np.zeros((S, 3)); qh = np.zeros((S, 4)); Yph = np.zeros((S, 3)); uh = np.zeros((S, 3))
+    lh = np.zeros((S - n_fil, 3))
+    m.get_state(Yh, qh, Yph, uh, lh)
+    e2e_pairs = 0.0
+    a2, _, _ = m.counters()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        m.set_state(Yh, qh, Yph, uh, lh)
+        m.step()
+        m.get_state(Yh, qh, Yph, uh, lh)
+    e1.record(stream)
+    barrier()
+    a3, _, _ = m.counters()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_pairs = (a3 - a2) * float(S) * S
+    state_bytes = 8 * (Yh.size + qh.size + Yph.size + uh.size + lh.size)
+    m.close()
+
+    # ---- plain FP64 form on the same workload (timesteps/s for comparison) ----
+    plain = None
+    if args.plain_steps > 0 and prec == fil.FIL_MIXED:
+        mp = fil.Filaments(wl.seg_per_fil, precision=fil.FIL_FP64, stream=stream.cuda_stream,
+                           **params)
+        mp.set_state(Yh, qh, Yph, uh, lh)
+        mp.set_external(Fext, None, follower)
+        barrier()
+        pa0, _, _ = mp.counters()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.plain_steps):
+            mp.step()
+        p1.record(stream)
+        barrier()
+        pa1, _, _ = mp.counters()
+        pms = p0.elapsed_time(p1)
+        plain = {"timesteps_per_s": args.plain_steps / (pms * 1e-3),
+                 "pairs_per_s": (pa1 - pa0) * float(S) * S / (pms * 1e-3),
+                 "steps": args.plain_steps, "precision": "fp64"}
+        mp.close()
+
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+
+    import __graft_entry__ as _g  # noqa: F401
+    cpu = cpu_baseline(Yh, np.random.default_rng(2).standard_normal((S, 6)),
+                       args.cpu_seconds) if world == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == fil.FIL_MIXED else "f64", "data": "synthetic",
+        "config": {
+            "workload": "suspension 1000 filaments x 32 segments (32000), 2% volume fraction, "
+                        "half sedimenting (B=1000) half tip-follower (fL^2/KB=100), BDF2 "
+                        "dt=T/200, Broyden tol 1e-4",
+            "segments": S, "precision": args.precision, "parallelism": "replicas" if world > 1
+            else "single",
+            "l2": "flushed between timed steps (256 MiB write)"},
+        "timesteps_per_s": args.steps / (max_ms * 1e-3),
+        "broyden_iters_per_step": float(np.mean(iters)),
+        "mobility_applies": int(applies),
+        "roofline": {"kernel": "rpy_pair32" if prec == fil.FIL_MIXED else "rpy_pair64",
+                     "bound": "alu", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS if prec == fil.FIL_MIXED else None,
+                     "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS if prec == fil.FIL_MIXED else None,
+                     "traffic": traffic, "flops_per_pair": FLOPS_PER_PAIR,
+                     "avg_launch_ms": pair_avg_ms, "launches": int(n_pair_launch),
+                     "share_of_step": pair_ms / dev_ms if dev_ms > 0 else None,
+                     "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+        "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                "steps": args.e2e_steps},
+        "gpu_launches": int(k1 - k0),
+        "clocks": clocks,
+        "wall_s": t_wall,
+    }
+    if plain is not None:
+        line["plain_fp64"] = plain
+        line["mixed_over_plain_timesteps"] = line["timesteps_per_s"] / plain["timesteps_per_s"]
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

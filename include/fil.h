@@ -1,0 +1,189 @@
+/*
+ * fil.h -- C ABI of the GB300 filament-suspension hot path.
+ *
+ * Method: Schoeller, Townsend, Westwood & Keaveny, "Methods for suspensions
+ * of passive and active filaments". Each filament is N rigid spheres
+ * ("segments") of radius a, spacing dL, with a unit quaternion per segment
+ * (Sec. 2.9). One timestep solves f(X) = 0 (eqn RA-3d-system) for
+ * X = (Y_1, u_1..u_N, Lambda_{3/2}..Lambda_{N-1/2}) per filament by the
+ * limited-memory bad Broyden method (Algorithm 2) with the block-diagonal
+ * approximate Jacobian J0 of App. B.2; every residual evaluation applies the
+ * Rotne-Prager-Yamakawa mobility (Sec. 2.7.1) to all segment pairs.
+ *
+ * Conventions (all entry points):
+ *  - Every entry point returns a fil_status; nothing aborts, exits or throws
+ *    across the ABI. fil_last_error(ctx) holds a message for the last failure.
+ *  - Pointers to arrays may be HOST or DEVICE memory (detected per call with
+ *    cudaPointerGetAttributes); host buffers are staged through the context's
+ *    device workspace with copies on the context stream. The caller owns
+ *    every buffer it passes; the library never frees or retains them.
+ *  - The library allocates device memory only in fil_create (and frees it in
+ *    fil_destroy). Work is issued on the stream given at creation. Calls that
+ *    return host scalars (finf, converged, iters) or read host arrays
+ *    synchronise that stream before returning.
+ *  - Segments of all filaments are concatenated filament-major: segment n
+ *    (0-based) of filament i is row off[i] + n, off[i] = sum_{k<i} N_k.
+ *    S = sum N_i. Per-segment arrays are row-major: Y, u are S x 3, q is
+ *    S x 4 scalar-first (q0, q1, q2, q3), FT and VW are S x 6 (F then T,
+ *    V then Omega). Lambda is sum(N_i - 1) x 3, filament-major, row n of a
+ *    filament holding Lambda_{n+3/2}.
+ *  - X and f are 6S long, per filament [Y_1 (3), u_1..u_N (3N),
+ *    Lambda_{3/2}..Lambda_{N-1/2} (3(N-1))] and [f^1 (3), f^2_1..N (3N),
+ *    f^3_2..N (3(N-1))] (eqn RA-3d-system).
+ *  - Units are the caller's; a, eta, dL, KB, KT must be > 0.
+ */
+#ifndef FIL_H
+#define FIL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fil_ctx fil_ctx;
+
+typedef enum {
+    FIL_OK = 0,
+    FIL_EINVAL = 1,   /* bad argument or size                                 */
+    FIL_ENOMEM = 2,   /* device allocation failed in fil_create               */
+    FIL_ECUDA = 3,    /* a CUDA call failed (message in fil_last_error)       */
+    FIL_ENOCONV = 4,  /* Broyden reached max_iter without ||f||_inf <= tol*a  */
+    FIL_ENAN = 5,     /* the residual became NaN or Inf                       */
+    FIL_ESTALL = 6,   /* ||f(X_{k+1}) - f(X_k)||_2 = 0: no secant update      */
+    FIL_ESTATE = 7    /* call out of order (e.g. a Broyden step before begin) */
+} fil_status;
+
+typedef enum {
+    FIL_FP64 = 0,     /* every step in FP64, including the RPY pair sums       */
+    FIL_MIXED = 1     /* RPY pair sums in FP32 with per-target compensated
+                         accumulation; everything else FP64                    */
+} fil_precision;
+
+typedef struct {
+    int32_t n_fil;                /* number of filaments M >= 1                    */
+    const int32_t *seg_per_fil;   /* HOST array of M segment counts N_i >= 1; copied */
+    double a;                     /* segment radius                                */
+    double eta;                   /* viscosity                                     */
+    double dL;                    /* segment spacing Delta L                       */
+    double KB, KT;                /* bending and twist moduli (Sec. 2.2)           */
+    double gamma0, kappa_mu, kappa_nu; /* preferred twist and curvatures (Sec. 2.2) */
+    double dt;                    /* timestep                                      */
+    double tol;                   /* Broyden stops when ||f||_inf <= tol * a       */
+    int32_t max_iter;             /* Broyden iteration cap and history depth >= 1  */
+    int32_t precision;            /* fil_precision                                 */
+    void *stream;                 /* cudaStream_t, or NULL for the legacy stream   */
+} fil_params;
+
+/* Create a context: validates p, copies the layout, allocates every device
+ * buffer the other calls use (state, workspace, Broyden history of depth
+ * max_iter, J0 band factors, RPY partial sums). The state starts with all
+ * segments at the origin and identity quaternions; call fil_set_state or
+ * fil_init_straight before stepping. *out is NULL on failure. */
+fil_status fil_create(const fil_params *p, fil_ctx **out);
+
+/* Release the context and its device memory (synchronises its stream). */
+void fil_destroy(fil_ctx *c);
+
+/* Message of the last failed call on this context ("" if none). */
+const char *fil_last_error(const fil_ctx *c);
+
+/* Sizes of the context: S segments, 6S unknowns, sum(N_i - 1) multipliers. */
+fil_status fil_sizes(const fil_ctx *c, int64_t *n_seg, int64_t *n_unknowns, int64_t *n_lambda);
+
+/* Set the time-integration state (Sec. 2.9.3): positions Y^j (S x 3) and
+ * quaternions q^j (S x 4) are required; Yprev = Y^{j-1} (S x 3) and u^j
+ * (S x 3, the Lie-algebra elements of the previous step) are optional and
+ * must be given together: with them the next step is BDF2, without them the
+ * next step is backward Euler (first step). Lambda (sum(N_i-1) x 3) is
+ * optional (zero if NULL) and seeds the next step's initial guess. */
+fil_status fil_set_state(fil_ctx *c, const double *Y, const double *q, const double *Yprev,
+                         const double *u, const double *Lambda);
+
+/* Read the state back; any pointer may be NULL to skip that array. Yprev and
+ * u are zero before the first committed step. */
+fil_status fil_get_state(fil_ctx *c, double *Y, double *q, double *Yprev, double *u,
+                         double *Lambda);
+
+/* Initialise straight filaments (App. A.1 and A.5): filament i starts at
+ * base[i] (M x 3) with unit tangent t[i] and unit normal mu[i] (M x 3,
+ * orthonormal); the quaternion of every segment is the one whose rotation
+ * maps (e_x, e_y) to (t, mu) (App. A.1 steps 1-5); if xi (S x 3) is not NULL
+ * each quaternion is then perturbed to exp(xi_n) q_n. Positions follow the
+ * robot-arm construction Y_n = Y_1 + (dL/2) sum_{m=2}^n (t_{m-1} + t_m)
+ * (eqn positionSubstitution-3d). History is cleared (next step is backward
+ * Euler), Lambda is zero. */
+fil_status fil_init_straight(fil_ctx *c, const double *base, const double *t, const double *mu,
+                             const double *xi);
+
+/* External loads (Sec. 2.5): a constant force Fext (S x 3) and torque Text
+ * (S x 3) per segment, and a follower force -follower[i] * t_N on the last
+ * segment of filament i (M entries). NULL clears the corresponding load. */
+fil_status fil_set_external(fil_ctx *c, const double *Fext, const double *Text,
+                            const double *follower);
+
+/* Mobility apply (Sec. 2.7.1, eq. mobility-problem): VW = M(Y) FT over all
+ * S^2 ordered segment pairs of the context, with the self term for n = m,
+ * the far form for r >= 2a and the equal-radius overlapping form for r < 2a
+ * (r = 0 between distinct segments takes the self values). Y is S x 3, FT and
+ * VW are S x 6. Precision follows the context (FP64, or FP32 pair sums with
+ * compensated per-target accumulation). */
+fil_status fil_mobility_apply(fil_ctx *c, const double *Y, const double *FT, double *VW);
+
+/* Residual f(X) of eqn RA-3d-system at X (6S), using the context's state
+ * and external loads: unpack (q = exp(u) q^j, robot-arm positions), forces
+ * and torques (Sec. 2.5, eq. quaternionM), mobility, then the BDF2 rows
+ * (backward Euler before the first committed step). Writes f (6S) and, if
+ * finf is not NULL, ||f||_inf. */
+fil_status fil_residual(fil_ctx *c, const double *X, double *f, double *finf);
+
+/* Start a timestep (set-up of Algorithm 2): initial guess X_0 (Y_1
+ * extrapolated linearly, u = u^j, Lambda = Lambda^j; first step Y_1^j, 0,
+ * Lambda^j), J0 of App. B.2 at X_0 assembled and LU-factored per filament,
+ * f(X_0). Writes ||f(X_0)||_inf to *finf if not NULL. */
+fil_status fil_broyden_begin(fil_ctx *c, double *finf);
+
+/* One pass of Algorithm 2's loop: dX_k = -H_k f(X_k), X_{k+1} = X_k + dX_k,
+ * f(X_{k+1}), and the rank-one pair (c_{k+1}, d_{k+1}). *converged is set to 1
+ * when ||f(X_{k+1})||_inf <= tol * a (the pair is then not formed). Returns
+ * FIL_ESTATE before fil_broyden_begin, FIL_ENOCONV once max_iter iterations
+ * were taken without convergence, FIL_ENAN / FIL_ESTALL as documented. */
+fil_status fil_broyden_step(fil_ctx *c, int32_t *converged, double *finf);
+
+/* Copy the current iterate X_k and f(X_k) (each 6S, either may be NULL). */
+fil_status fil_get_iterate(fil_ctx *c, double *X, double *f);
+
+/* Apply the factored J0^{-1} of the current step to b (6S) -> x (6S). */
+fil_status fil_j0_solve(fil_ctx *c, const double *b, double *x);
+
+/* Finish the timestep at the current iterate: q^{j+1} = exp(u) q^j,
+ * Y^{j+1} from the robot arm, Y^{j-1} <- Y^j, u^j <- u, Lambda^j <- Lambda. */
+fil_status fil_broyden_commit(fil_ctx *c);
+
+/* One whole timestep: begin, Broyden steps until convergence, commit.
+ * *iters (if not NULL) receives the number of Broyden iterations. On
+ * FIL_ENOCONV / FIL_ENAN / FIL_ESTALL the state is left at the previous step
+ * (the caller may retry with a smaller dt via fil_set_dt). */
+fil_status fil_step(fil_ctx *c, int32_t *iters);
+
+/* Change the timestep (takes effect at the next fil_broyden_begin). */
+fil_status fil_set_dt(fil_ctx *c, double dt);
+
+/* Counters since creation: RPY applies, Broyden iterations and kernels this
+ * library launched (any pointer may be NULL). */
+fil_status fil_counters(const fil_ctx *c, int64_t *mobility_applies, int64_t *broyden_iters,
+                        int64_t *kernel_launches);
+
+/* Kernel timing: while enabled, every RPY pair-kernel launch is bracketed by
+ * two CUDA events recorded on the context stream (at most 4096 launches are
+ * kept). fil_profile_read synchronises the stream, returns the number of
+ * timed launches and their summed device time in milliseconds, and clears the
+ * record. Enabling is cheap; the events add no synchronisation. */
+fil_status fil_profile(fil_ctx *c, int32_t enable);
+fil_status fil_profile_read(fil_ctx *c, int64_t *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIL_H */

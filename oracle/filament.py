@@ -460,6 +460,112 @@ def jacobian0(lay: Layout, p: Params, state: State, X):
     return blocks
 
 
+def filament_mobility(p: Params, Yf, model):
+    """6N x 6N matrix mapping (F_m, T_m) to (V_n, Omega_n) within one filament
+    (index 6n + c). model 'drag': the diagonal self mobility of App. B
+    (1/(6 pi eta a), 1/(8 pi eta a^3)); model 'rpy': the RPY blocks of every
+    pair of segments of this filament (Sec. 2.7.1, same branches as rpy.c)."""
+    n = Yf.shape[0]
+    Mf = np.zeros((6 * n, 6 * n))
+    if model == "drag":
+        for k in range(n):
+            Mf[6 * k:6 * k + 3, 6 * k:6 * k + 3] = np.eye(3) / (6.0 * PI * p.eta * p.a)
+            Mf[6 * k + 3:6 * k + 6, 6 * k + 3:6 * k + 6] = np.eye(3) / (8.0 * PI * p.eta * p.a ** 3)
+        return Mf
+    for i in range(n):
+        for j in range(n):
+            tt, tr, rt, rr = rpy.pair_blocks(Yf[i] - Yf[j], i == j, p.a, p.eta)
+            Mf[6 * i:6 * i + 3, 6 * j:6 * j + 3] = tt
+            Mf[6 * i:6 * i + 3, 6 * j + 3:6 * j + 6] = tr
+            Mf[6 * i + 3:6 * i + 6, 6 * j:6 * j + 3] = rt
+            Mf[6 * i + 3:6 * i + 6, 6 * j + 3:6 * j + 6] = rr
+    return Mf
+
+
+def jacobian0_general(lay: Layout, p: Params, state: State, X, model="rpy"):
+    """J0 = d f_0 / dX with f_0 the residual whose mobility is a per-filament
+    matrix M_f held fixed at X (no dM/dY term), internal loads only, and the
+    derivative approximations of App. B.2 (d t/d u = [x t], frame-vector
+    moments, three-term dexpinv):
+
+      position rows n:  I (Y_1) + arm terms - b dt (M_f G)_{V_n}
+      rotation rows n:  I (u_n) - b dt [A_n (M_f G)_{Omega_n}
+                         + delta_{u_n}(-[x Om_n]/2 + ([x (u_n x Om_n)] + [u_n x][x Om_n])/12)]
+
+    with G = d(F, T)/dX the App. B.2 load derivatives, A_n = I - [u_n x]/2 +
+    [u_n x]^2/12, Om_n the internal-load angular velocity at X and b the scheme
+    weight. With model='drag' (M_f = self mobility) this is exactly the J0 of
+    App. B.2; model='rpy' keeps every segment-segment RPY block of the filament
+    (the coupling along a filament that the drag model drops)."""
+    _, _, be, _ = scheme(state)
+    bdt = be * p.dt
+    q, t, Y, u, lam = unpack(lay, p, X, state.q)
+    _, mu, nu = frames(q)
+    Fi, Ti = forces_torques(lay, p, q, t, lam, None)
+    I3 = np.eye(3)
+    blocks = []
+    for i, n in enumerate(lay.N):
+        s = lay.off_seg[i]
+        nX = 6 * n
+        L = np.zeros((n + 1, 3))
+        L[1:n] = lam[lay.off_lam[i]:lay.off_lam[i + 1]]
+
+        def ucol(k):          # u_k, k = 0..N-1
+            return 3 + 3 * k
+
+        def lcol(j):          # Lambda joint j (between k = j and j+1), j = 0..N-2
+            return 3 + 3 * n + 3 * j
+
+        G = np.zeros((6 * n, nX))             # rows 6m + c: (F_m, T_m)
+        Da = [None] * n
+        Db = [None] * n
+        for j in range(n - 1):
+            Da[j], Db[j] = _dM_du(p, t[s + j], t[s + j + 1], mu[s + j], mu[s + j + 1],
+                                  nu[s + j], nu[s + j + 1])
+        for m in range(n):
+            # F_m = Lam[m] - Lam[m-1]  (Lam[k] here = L[k+1])
+            if m <= n - 2:
+                G[6 * m:6 * m + 3, lcol(m):lcol(m) + 3] += I3
+                G[6 * m + 3:6 * m + 6, lcol(m):lcol(m) + 3] += 0.5 * p.dL * _cross_left(t[s + m])
+            if m >= 1:
+                G[6 * m:6 * m + 3, lcol(m - 1):lcol(m - 1) + 3] -= I3
+                G[6 * m + 3:6 * m + 6, lcol(m - 1):lcol(m - 1) + 3] += \
+                    0.5 * p.dL * _cross_left(t[s + m])
+            dT = 0.5 * p.dL * _cross_right(L[m + 1] + L[m]) @ _cross_right(t[s + m])
+            if m <= n - 2:
+                dT = dT + Da[m]
+                G[6 * m + 3:6 * m + 6, ucol(m + 1):ucol(m + 1) + 3] += Db[m]
+            if m >= 1:
+                dT = dT - Db[m - 1]
+                G[6 * m + 3:6 * m + 6, ucol(m - 1):ucol(m - 1) + 3] += -Da[m - 1]
+            G[6 * m + 3:6 * m + 6, ucol(m):ucol(m) + 3] += dT
+        Mf = filament_mobility(p, Y[s:s + n], model)
+        MG = Mf @ G
+        FT = np.zeros(6 * n)
+        for m in range(n):
+            FT[6 * m:6 * m + 3] = Fi[s + m]
+            FT[6 * m + 3:6 * m + 6] = Ti[s + m]
+        Om = (Mf @ FT).reshape(n, 6)[:, 3:]
+        J = np.zeros((nX, nX))
+        for k in range(n):
+            prow = 0 if k == 0 else 3 + 3 * n + 3 * (k - 1)
+            rrow = 3 + 3 * k
+            J[prow:prow + 3, 0:3] = I3
+            J[prow:prow + 3, :] -= bdt * MG[6 * k:6 * k + 3, :]
+            for kk in range(1, k + 1):        # arm: (dL/2) sum_{k'=1}^{k} (t_{k'-1} + t_{k'})
+                for c in (kk - 1, kk):
+                    J[prow:prow + 3, ucol(c):ucol(c) + 3] += 0.5 * p.dL * _cross_right(t[s + c])
+            uk = u[s + k]
+            ux = _cross_left(uk)
+            A = I3 - 0.5 * ux + ux @ ux / 12.0
+            J[rrow:rrow + 3, :] -= bdt * A @ MG[6 * k + 3:6 * k + 6, :]
+            xO = _cross_right(Om[k])
+            J[rrow:rrow + 3, ucol(k):ucol(k) + 3] += I3 - bdt * (
+                -0.5 * xO + (_cross_right(np.cross(uk, Om[k])) + ux @ xO) / 12.0)
+        blocks.append(J)
+    return blocks
+
+
 class J0Solver:
     """J0^{-1} v by a dense LU of each filament block (scipy/LAPACK)."""
 
@@ -539,10 +645,18 @@ def initial_guess(lay: Layout, state: State):
     return lay.join_X(Y1, u, lam)
 
 
-def begin_step(lay: Layout, p: Params, state: State, ext: External | None, nthreads=1):
-    """Initial guess, J0 at it (LU-factored) and f(X_0): the set-up of Algorithm 2."""
+def begin_step(lay: Layout, p: Params, state: State, ext: External | None, nthreads=1,
+               j0_model="drag"):
+    """Initial guess, J0 at it (LU-factored) and f(X_0): the set-up of Algorithm 2.
+
+    j0_model 'drag' is App. B.2 as printed; 'rpy' keeps each filament's own
+    RPY blocks in f_0 (see jacobian0_general)."""
     X0 = initial_guess(lay, state)
-    solver = J0Solver(lay, jacobian0(lay, p, state, X0))
+    if j0_model == "drag":
+        blocks = jacobian0(lay, p, state, X0)
+    else:
+        blocks = jacobian0_general(lay, p, state, X0, model=j0_model)
+    solver = J0Solver(lay, blocks)
 
     def fun(X):
         return residual(lay, p, state, ext, X, nthreads)
@@ -556,9 +670,10 @@ def commit_step(lay: Layout, p: Params, state: State, X):
     return State(Y=Y, q=q, Yprev=state.Y.copy(), u=u, lam=lam, steps=state.steps + 1)
 
 
-def step(lay: Layout, p: Params, state: State, ext: External | None, nthreads=1):
+def step(lay: Layout, p: Params, state: State, ext: External | None, nthreads=1,
+         j0_model="drag"):
     """One timestep; returns (new_state, iterations)."""
-    br = begin_step(lay, p, state, ext, nthreads)
+    br = begin_step(lay, p, state, ext, nthreads, j0_model)
     while not br.converged():
         if br.k >= p.max_iter:
             raise RuntimeError("Broyden did not converge in %d iterations" % p.max_iter)

@@ -1,0 +1,560 @@
+// C ABI of the filament library (declared in include/fil.h).
+//
+// All device memory of a context is one arena allocated in fil_create; the
+// other entry points only enqueue kernels and copies on the context stream.
+// The timestep loop is host-driven: the single host decision per Broyden
+// iteration is the convergence test ||f||_inf <= tol * a, read back together
+// with the stall / singular flags in one small copy.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fil_internal.cuh"
+
+using namespace fil;
+
+namespace {
+
+struct StatusBlock {
+    unsigned long long finf_bits;
+    int flags[4];   // [0] stall (|df| = 0), [1] J0 singular
+};
+
+fil_status set_err(fil_ctx *c, fil_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+fil_status cuda_err(fil_ctx *c, cudaError_t e, const char *what) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    return set_err(c, FIL_ECUDA, buf);
+}
+
+#define CK(expr)                                                 \
+    do {                                                         \
+        cudaError_t e_ = (expr);                                 \
+        if (e_ != cudaSuccess) return cuda_err(c, e_, #expr);    \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device view of an input array: the pointer itself, or a copy in `stage`.
+cudaError_t input_view(fil_ctx *c, const double *p, int64_t n, double *stage, const double **out) {
+    if (is_device_ptr(p)) {
+        *out = p;
+        return cudaSuccess;
+    }
+    *out = stage;
+    return cudaMemcpyAsync(stage, p, (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
+                           c->stream);
+}
+
+// Copy a device result to the caller's buffer (host or device) and wait.
+cudaError_t output_copy(fil_ctx *c, double *dst, const double *src, int64_t n) {
+    if (dst == src) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(dst, src, (size_t)n * sizeof(double), cudaMemcpyDefault,
+                                    c->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(c->stream);
+}
+
+struct Arena {
+    char *base = nullptr;
+    size_t used = 0;
+    template <typename T>
+    T *take(size_t count) {
+        size_t off = (used + 255) & ~(size_t)255;
+        used = off + count * sizeof(T);
+        return base ? reinterpret_cast<T *>(base + off) : nullptr;
+    }
+};
+
+void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
+    const int64_t S = c->lay.S, nX = c->lay.nX, M = c->lay.M;
+    const int64_t nlam = c->lay.nlam;
+    const int64_t nband = 6 * S - 3 * M;
+    c->lay.N = ar.take<int>(M);
+    c->lay.off = ar.take<int>(M + 1);
+    c->lay.fil_of = ar.take<int>(S);
+    c->Y = ar.take<double>(3 * S);
+    c->Yprev = ar.take<double>(3 * S);
+    c->q = ar.take<double>(4 * S);
+    c->uprev = ar.take<double>(3 * S);
+    c->lam = ar.take<double>(3 * (nlam > 0 ? nlam : 1));
+    c->Fext = ar.take<double>(3 * S);
+    c->Text = ar.take<double>(3 * S);
+    c->follower = ar.take<double>(M);
+    c->qc = ar.take<double>(4 * S);
+    c->Yc = ar.take<double>(3 * S);
+    c->FT = ar.take<double>(6 * S);
+    c->Tint = ar.take<double>(3 * S);
+    c->VW = ar.take<double>(6 * S);
+    c->Mh = nullptr;
+    if (c->prec == FIL_MIXED) {
+        c->src32 = ar.take<float4>(3 * c->Spad);
+        c->src64 = nullptr;
+    } else {
+        c->src64 = ar.take<double>(9 * c->Spad);
+        c->src32 = nullptr;
+    }
+    c->partials = ar.take<char>(partial_bytes);
+    c->Xk = ar.take<double>(nX);
+    c->fk = ar.take<double>(nX);
+    c->Xn = ar.take<double>(nX);
+    c->fn = ar.take<double>(nX);
+    c->w = ar.take<double>(nX);
+    c->g = ar.take<double>(nX);
+    c->C = ar.take<double>((size_t)c->max_iter * nX);
+    c->D = ar.take<double>((size_t)c->max_iter * nX);
+    c->scal = ar.take<double>(c->max_iter + 8);
+    c->red_part = ar.take<double>((size_t)(c->max_iter + 2) * red_blocks);
+    StatusBlock *sb = ar.take<StatusBlock>(1);
+    c->d_finf = sb ? &sb->finf_bits : nullptr;
+    c->d_flags = sb ? sb->flags : nullptr;
+    c->band = ar.take<double>((size_t)nband * kBandW);
+    c->piv = ar.take<int>(nband);
+    c->stage_a = ar.take<double>(nX);
+    c->stage_b = ar.take<double>(nX);
+    c->stage_c = ar.take<double>(nX);
+}
+
+fil_status read_status(fil_ctx *c, StatusBlock *hs) {
+    CK(cudaMemcpyAsync(c->h_pinned, c->d_finf, sizeof(StatusBlock), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::memcpy(hs, c->h_pinned, sizeof(StatusBlock));
+    return FIL_OK;
+}
+
+double finf_of(const StatusBlock &s) {
+    double v;
+    std::memcpy(&v, &s.finf_bits, sizeof(double));
+    return v;
+}
+
+// f(X): unpack + forces (with_forces = 2 also keeps the internal torque for
+// J0), RPY mobility, residual rows, ||f||_inf into the status block.
+cudaError_t eval_residual(fil_ctx *c, const double *X, double *f, int with_forces) {
+    cudaError_t e = unpack_forces(c, X, with_forces);
+    if (e != cudaSuccess) return e;
+    e = rpy_apply(c, c->Yc, c->FT, c->VW);
+    if (e != cudaSuccess) return e;
+    return residual_rows(c, X, f);
+}
+
+}  // namespace
+
+extern "C" {
+
+fil_status fil_create(const fil_params *p, fil_ctx **out) {
+    if (!out) return FIL_EINVAL;
+    *out = nullptr;
+    if (!p || p->n_fil < 1 || !p->seg_per_fil) return FIL_EINVAL;
+    if (!(p->a > 0) || !(p->eta > 0) || !(p->dL > 0) || !(p->dt > 0) || !(p->tol > 0) ||
+        !(p->KB >= 0) || !(p->KT >= 0) || p->max_iter < 1 ||
+        (p->precision != FIL_FP64 && p->precision != FIL_MIXED) ||
+        !std::isfinite(p->gamma0) || !std::isfinite(p->kappa_mu) || !std::isfinite(p->kappa_nu))
+        return FIL_EINVAL;
+    int64_t S = 0;
+    int maxN = 0;
+    for (int i = 0; i < p->n_fil; ++i) {
+        if (p->seg_per_fil[i] < 1) return FIL_EINVAL;
+        S += p->seg_per_fil[i];
+        if (p->seg_per_fil[i] > maxN) maxN = p->seg_per_fil[i];
+    }
+    if (S > (int64_t)1 << 30) return FIL_EINVAL;
+    // the band solve keeps a filament's right-hand side in shared memory
+    if (maxN > kMaxSegPerFil) return FIL_EINVAL;
+
+    fil_ctx *c = new (std::nothrow) fil_ctx();
+    if (!c) return FIL_ENOMEM;
+    c->lay.M = p->n_fil;
+    c->lay.S = S;
+    c->lay.nX = 6 * S;
+    c->lay.nlam = S - p->n_fil;
+    c->lay.maxN = maxN;
+    c->N_host.assign(p->seg_per_fil, p->seg_per_fil + p->n_fil);
+    c->off_host.resize(p->n_fil + 1);
+    c->off_host[0] = 0;
+    for (int i = 0; i < p->n_fil; ++i) c->off_host[i + 1] = c->off_host[i] + c->N_host[i];
+    c->a = p->a; c->eta = p->eta; c->dL = p->dL; c->KB = p->KB; c->KT = p->KT;
+    c->g0 = p->gamma0; c->kmu = p->kappa_mu; c->knu = p->kappa_nu;
+    c->dt = p->dt; c->tol = p->tol; c->max_iter = p->max_iter; c->prec = p->precision;
+    c->stream = (cudaStream_t)p->stream;
+    c->have_prev = 0; c->steps = 0; c->k = 0; c->in_step = 0;
+    c->has_Fext = c->has_Text = c->has_follower = 0;
+    c->n_applies = c->n_iters = 0;
+    c->iters_step = 0; c->conv = 0;
+    c->arena = nullptr; c->h_pinned = nullptr;
+    c->n_launches = 0; c->prof_on = 0; c->prof_n = 0; c->prof_ev = nullptr;
+
+    auto bail = [&](fil_status s, const char *what, cudaError_t e) {
+        if (c->arena) cudaFree(c->arena);
+        if (c->h_pinned) cudaFreeHost(c->h_pinned);
+        std::fprintf(stderr, "fil_create: %s: %s\n", what, cudaGetErrorString(e));
+        delete c;
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return bail(FIL_ECUDA, "cudaGetDevice", e);
+    e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) return bail(FIL_ECUDA, "cudaDeviceGetAttribute", e);
+    e = rpy_setup(c);
+    if (e != cudaSuccess) return bail(FIL_ECUDA, "rpy_setup", e);
+    c->red_blocks = 2 * c->num_sms;
+    const size_t pbytes = rpy_partial_bytes(c);
+
+    Arena sizing;
+    carve(c, sizing, c->red_blocks, pbytes);
+    c->arena_bytes = sizing.used;
+    e = cudaMalloc(&c->arena, c->arena_bytes);
+    if (e != cudaSuccess) return bail(FIL_ENOMEM, "cudaMalloc", e);
+    Arena ar;
+    ar.base = (char *)c->arena;
+    carve(c, ar, c->red_blocks, pbytes);
+    e = cudaMallocHost(&c->h_pinned, 256);
+    if (e != cudaSuccess) return bail(FIL_ENOMEM, "cudaMallocHost", e);
+
+    // layout tables and a neutral initial state
+    std::vector<int> fil_of(S);
+    for (int i = 0; i < p->n_fil; ++i)
+        for (int n = c->off_host[i]; n < c->off_host[i + 1]; ++n) fil_of[n] = i;
+    std::vector<double> q0(4 * S, 0.0);
+    for (int64_t n = 0; n < S; ++n) q0[4 * n] = 1.0;
+    e = cudaMemsetAsync(c->arena, 0, c->arena_bytes, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->lay.N, c->N_host.data(), sizeof(int) * p->n_fil,
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->lay.off, c->off_host.data(), sizeof(int) * (p->n_fil + 1),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->lay.fil_of, fil_of.data(), sizeof(int) * S,
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->q, q0.data(), sizeof(double) * 4 * S, cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail(FIL_ECUDA, "initial upload", e);
+    *out = c;
+    return FIL_OK;
+}
+
+void fil_destroy(fil_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (c->arena) cudaFree(c->arena);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->prof_ev) {
+        for (int i = 0; i < 2 * kProfMax; ++i) cudaEventDestroy(c->prof_ev[i]);
+        delete[] c->prof_ev;
+    }
+    delete c;
+}
+
+const char *fil_last_error(const fil_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+fil_status fil_sizes(const fil_ctx *c, int64_t *n_seg, int64_t *n_unknowns, int64_t *n_lambda) {
+    if (!c) return FIL_EINVAL;
+    if (n_seg) *n_seg = c->lay.S;
+    if (n_unknowns) *n_unknowns = c->lay.nX;
+    if (n_lambda) *n_lambda = c->lay.nlam;
+    return FIL_OK;
+}
+
+fil_status fil_set_state(fil_ctx *c, const double *Y, const double *q, const double *Yprev,
+                         const double *u, const double *Lambda) {
+    if (!c) return FIL_EINVAL;
+    if (!Y || !q) return set_err(c, FIL_EINVAL, "fil_set_state: Y and q are required");
+    if ((Yprev == nullptr) != (u == nullptr))
+        return set_err(c, FIL_EINVAL, "fil_set_state: Yprev and u go together");
+    CK(cudaSetDevice(c->device));
+    const int64_t S = c->lay.S;
+    CK(cudaMemcpyAsync(c->Y, Y, sizeof(double) * 3 * S, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(c->q, q, sizeof(double) * 4 * S, cudaMemcpyDefault, c->stream));
+    if (Yprev) {
+        CK(cudaMemcpyAsync(c->Yprev, Yprev, sizeof(double) * 3 * S, cudaMemcpyDefault, c->stream));
+        CK(cudaMemcpyAsync(c->uprev, u, sizeof(double) * 3 * S, cudaMemcpyDefault, c->stream));
+    } else {
+        CK(cudaMemsetAsync(c->Yprev, 0, sizeof(double) * 3 * S, c->stream));
+        CK(cudaMemsetAsync(c->uprev, 0, sizeof(double) * 3 * S, c->stream));
+    }
+    if (c->lay.nlam > 0) {
+        if (Lambda)
+            CK(cudaMemcpyAsync(c->lam, Lambda, sizeof(double) * 3 * c->lay.nlam,
+                               cudaMemcpyDefault, c->stream));
+        else
+            CK(cudaMemsetAsync(c->lam, 0, sizeof(double) * 3 * c->lay.nlam, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_prev = Yprev ? 1 : 0;
+    c->in_step = 0;
+    return FIL_OK;
+}
+
+fil_status fil_get_state(fil_ctx *c, double *Y, double *q, double *Yprev, double *u,
+                         double *Lambda) {
+    if (!c) return FIL_EINVAL;
+    CK(cudaSetDevice(c->device));
+    const int64_t S = c->lay.S;
+    if (Y) CK(cudaMemcpyAsync(Y, c->Y, sizeof(double) * 3 * S, cudaMemcpyDefault, c->stream));
+    if (q) CK(cudaMemcpyAsync(q, c->q, sizeof(double) * 4 * S, cudaMemcpyDefault, c->stream));
+    if (Yprev)
+        CK(cudaMemcpyAsync(Yprev, c->Yprev, sizeof(double) * 3 * S, cudaMemcpyDefault, c->stream));
+    if (u) CK(cudaMemcpyAsync(u, c->uprev, sizeof(double) * 3 * S, cudaMemcpyDefault, c->stream));
+    if (Lambda && c->lay.nlam > 0)
+        CK(cudaMemcpyAsync(Lambda, c->lam, sizeof(double) * 3 * c->lay.nlam, cudaMemcpyDefault,
+                           c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FIL_OK;
+}
+
+fil_status fil_init_straight(fil_ctx *c, const double *base, const double *t, const double *mu,
+                             const double *xi) {
+    if (!c) return FIL_EINVAL;
+    if (!base || !t || !mu) return set_err(c, FIL_EINVAL, "fil_init_straight: base, t, mu required");
+    CK(cudaSetDevice(c->device));
+    const int64_t M = c->lay.M, S = c->lay.S;
+    // 3M + 3M doubles in stage_a and 3M in stage_c (each stage holds 6S >= 6M)
+    double *sb = c->stage_a, *st = c->stage_a + 3 * M, *sm = c->stage_c;
+    CK(cudaMemcpyAsync(sb, base, sizeof(double) * 3 * M, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(st, t, sizeof(double) * 3 * M, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(sm, mu, sizeof(double) * 3 * M, cudaMemcpyDefault, c->stream));
+    const double *sxi = nullptr;
+    if (xi) {
+        CK(cudaMemcpyAsync(c->stage_b, xi, sizeof(double) * 3 * S, cudaMemcpyDefault, c->stream));
+        sxi = c->stage_b;
+    }
+    CK(init_straight(c, sb, st, sm, sxi));
+    CK(cudaMemsetAsync(c->Yprev, 0, sizeof(double) * 3 * S, c->stream));
+    CK(cudaMemsetAsync(c->uprev, 0, sizeof(double) * 3 * S, c->stream));
+    if (c->lay.nlam > 0) CK(cudaMemsetAsync(c->lam, 0, sizeof(double) * 3 * c->lay.nlam, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_prev = 0;
+    c->in_step = 0;
+    return FIL_OK;
+}
+
+fil_status fil_set_external(fil_ctx *c, const double *Fext, const double *Text,
+                            const double *follower) {
+    if (!c) return FIL_EINVAL;
+    CK(cudaSetDevice(c->device));
+    const int64_t S = c->lay.S, M = c->lay.M;
+    if (Fext) CK(cudaMemcpyAsync(c->Fext, Fext, sizeof(double) * 3 * S, cudaMemcpyDefault, c->stream));
+    if (Text) CK(cudaMemcpyAsync(c->Text, Text, sizeof(double) * 3 * S, cudaMemcpyDefault, c->stream));
+    if (follower)
+        CK(cudaMemcpyAsync(c->follower, follower, sizeof(double) * M, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->has_Fext = Fext ? 1 : 0;
+    c->has_Text = Text ? 1 : 0;
+    c->has_follower = follower ? 1 : 0;
+    return FIL_OK;
+}
+
+fil_status fil_mobility_apply(fil_ctx *c, const double *Y, const double *FT, double *VW) {
+    if (!c) return FIL_EINVAL;
+    if (!Y || !FT || !VW) return set_err(c, FIL_EINVAL, "fil_mobility_apply: null pointer");
+    CK(cudaSetDevice(c->device));
+    const int64_t S = c->lay.S;
+    const double *dY, *dFT;
+    CK(input_view(c, Y, 3 * S, c->stage_a, &dY));
+    CK(input_view(c, FT, 6 * S, c->stage_b, &dFT));
+    const bool dev_out = is_device_ptr(VW);
+    double *dVW = dev_out ? VW : c->stage_c;
+    CK(rpy_apply(c, dY, dFT, dVW));
+    if (!dev_out) CK(output_copy(c, VW, dVW, 6 * S));
+    return FIL_OK;
+}
+
+fil_status fil_residual(fil_ctx *c, const double *X, double *f, double *finf) {
+    if (!c) return FIL_EINVAL;
+    if (!X || !f) return set_err(c, FIL_EINVAL, "fil_residual: null pointer");
+    CK(cudaSetDevice(c->device));
+    const int64_t nX = c->lay.nX;
+    const double *dX;
+    CK(input_view(c, X, nX, c->stage_a, &dX));
+    const bool dev_out = is_device_ptr(f);
+    double *df = dev_out ? f : c->stage_b;
+    CK(eval_residual(c, dX, df, 1));
+    if (!dev_out) CK(output_copy(c, f, df, nX));
+    if (finf) {
+        StatusBlock sb;
+        fil_status s = read_status(c, &sb);
+        if (s != FIL_OK) return s;
+        *finf = finf_of(sb);
+    }
+    return FIL_OK;
+}
+
+fil_status fil_broyden_begin(fil_ctx *c, double *finf) {
+    if (!c) return FIL_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), c->stream));
+    CK(extrapolate_guess(c, c->Xk));
+    CK(eval_residual(c, c->Xk, c->fk, 2));
+    CK(j0_build_factor(c, c->Xk));
+    StatusBlock sb;
+    fil_status s = read_status(c, &sb);
+    if (s != FIL_OK) return s;
+    const double f0 = finf_of(sb);
+    if (finf) *finf = f0;
+    c->k = 0;
+    c->iters_step = 0;
+    c->in_step = 0;
+    if (sb.flags[1]) return set_err(c, FIL_ENAN, "fil_broyden_begin: J0 is singular");
+    if (!std::isfinite(f0)) return set_err(c, FIL_ENAN, "fil_broyden_begin: f(X_0) not finite");
+    c->conv = (f0 <= c->tol * c->a) ? 1 : 0;
+    if (!c->conv) CK(j0_solve(c, c->fk, c->w));
+    c->in_step = 1;
+    return FIL_OK;
+}
+
+fil_status fil_broyden_step(fil_ctx *c, int32_t *converged, double *finf) {
+    if (!c) return FIL_EINVAL;
+    if (!c->in_step) return set_err(c, FIL_ESTATE, "fil_broyden_step: no step in progress");
+    CK(cudaSetDevice(c->device));
+    if (c->conv) {
+        if (converged) *converged = 1;
+        return FIL_OK;
+    }
+    if (c->iters_step >= c->max_iter)
+        return set_err(c, FIL_ENOCONV, "Broyden: max_iter reached without convergence");
+    CK(broyden_axpy_step(c));
+    CK(eval_residual(c, c->Xn, c->fn, 1));
+    StatusBlock sb;
+    fil_status s = read_status(c, &sb);
+    if (s != FIL_OK) return s;
+    if (sb.flags[0]) return set_err(c, FIL_ESTALL, "Broyden: ||df|| = 0 (stalled)");
+    const double fv = finf_of(sb);
+    if (finf) *finf = fv;
+    if (!std::isfinite(fv)) return set_err(c, FIL_ENAN, "Broyden: residual not finite");
+    c->iters_step += 1;
+    c->n_iters += 1;
+    if (fv <= c->tol * c->a) {
+        std::swap(c->Xk, c->Xn);
+        std::swap(c->fk, c->fn);
+        c->conv = 1;
+        if (converged) *converged = 1;
+        return FIL_OK;
+    }
+    CK(broyden_dots(c));
+    CK(j0_solve(c, c->fn, c->g));
+    CK(broyden_update(c));
+    std::swap(c->Xk, c->Xn);
+    std::swap(c->fk, c->fn);
+    c->k += 1;
+    if (converged) *converged = 0;
+    return FIL_OK;
+}
+
+fil_status fil_get_iterate(fil_ctx *c, double *X, double *f) {
+    if (!c) return FIL_EINVAL;
+    if (!c->in_step) return set_err(c, FIL_ESTATE, "fil_get_iterate: no step in progress");
+    CK(cudaSetDevice(c->device));
+    if (X) CK(cudaMemcpyAsync(X, c->Xk, sizeof(double) * c->lay.nX, cudaMemcpyDefault, c->stream));
+    if (f) CK(cudaMemcpyAsync(f, c->fk, sizeof(double) * c->lay.nX, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FIL_OK;
+}
+
+fil_status fil_j0_solve(fil_ctx *c, const double *b, double *x) {
+    if (!c) return FIL_EINVAL;
+    if (!b || !x) return set_err(c, FIL_EINVAL, "fil_j0_solve: null pointer");
+    if (!c->in_step) return set_err(c, FIL_ESTATE, "fil_j0_solve: J0 exists only inside a step");
+    CK(cudaSetDevice(c->device));
+    const int64_t nX = c->lay.nX;
+    const double *db;
+    CK(input_view(c, b, nX, c->stage_a, &db));
+    const bool dev_out = is_device_ptr(x);
+    double *dx = dev_out ? x : c->stage_b;
+    CK(j0_solve(c, db, dx));
+    if (!dev_out) CK(output_copy(c, x, dx, nX));
+    return FIL_OK;
+}
+
+fil_status fil_broyden_commit(fil_ctx *c) {
+    if (!c) return FIL_EINVAL;
+    if (!c->in_step) return set_err(c, FIL_ESTATE, "fil_broyden_commit: no step in progress");
+    CK(cudaSetDevice(c->device));
+    CK(commit_state(c, c->Xk));
+    c->have_prev = 1;
+    c->steps += 1;
+    c->in_step = 0;
+    return FIL_OK;
+}
+
+fil_status fil_step(fil_ctx *c, int32_t *iters) {
+    if (!c) return FIL_EINVAL;
+    fil_status s = fil_broyden_begin(c, nullptr);
+    if (s != FIL_OK) return s;
+    int32_t conv = c->conv;
+    while (!conv) {
+        s = fil_broyden_step(c, &conv, nullptr);
+        if (s != FIL_OK) {
+            c->in_step = 0;
+            return s;
+        }
+    }
+    if (iters) *iters = c->iters_step;
+    return fil_broyden_commit(c);
+}
+
+fil_status fil_set_dt(fil_ctx *c, double dt) {
+    if (!c) return FIL_EINVAL;
+    if (!(dt > 0)) return set_err(c, FIL_EINVAL, "fil_set_dt: dt must be > 0");
+    c->dt = dt;
+    return FIL_OK;
+}
+
+fil_status fil_counters(const fil_ctx *c, int64_t *mobility_applies, int64_t *broyden_iters,
+                        int64_t *kernel_launches) {
+    if (!c) return FIL_EINVAL;
+    if (mobility_applies) *mobility_applies = c->n_applies;
+    if (broyden_iters) *broyden_iters = c->n_iters;
+    if (kernel_launches) *kernel_launches = c->n_launches;
+    return FIL_OK;
+}
+
+fil_status fil_profile(fil_ctx *c, int32_t enable) {
+    if (!c) return FIL_EINVAL;
+    CK(cudaSetDevice(c->device));
+    if (enable && !c->prof_ev) {
+        c->prof_ev = new (std::nothrow) cudaEvent_t[2 * kProfMax];
+        if (!c->prof_ev) return set_err(c, FIL_ENOMEM, "fil_profile: host allocation");
+        for (int i = 0; i < 2 * kProfMax; ++i) CK(cudaEventCreate(&c->prof_ev[i]));
+    }
+    c->prof_on = enable ? 1 : 0;
+    return FIL_OK;
+}
+
+fil_status fil_profile_read(fil_ctx *c, int64_t *launches, double *total_ms) {
+    if (!c) return FIL_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    double sum = 0.0;
+    for (int i = 0; i < c->prof_n; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]));
+        sum += ms;
+    }
+    if (launches) *launches = c->prof_n;
+    if (total_ms) *total_ms = sum;
+    c->prof_n = 0;
+    return FIL_OK;
+}
+
+}  // extern "C"

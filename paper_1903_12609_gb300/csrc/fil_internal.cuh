@@ -1,0 +1,132 @@
+// Internal declarations of the GB300 filament library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fil.h"
+
+namespace fil {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kProfMax = 4096;   // timed pair-kernel launches kept per read
+
+// ----------------------------------------------------------------------------
+// RPY pair-kernel geometry (shared by the launcher and the kernels).
+// ----------------------------------------------------------------------------
+constexpr int kRpyThreads = 128;               // threads per CTA
+constexpr int kRpyTargetsPerThread = 2;        // register-blocked targets
+constexpr int kRpyTile = kRpyThreads * kRpyTargetsPerThread;   // targets per tile
+constexpr int kRpyChunk = 64;                  // sources per shared-memory chunk
+constexpr int kRpyComp = 32;                   // sources per compensated partial (FP32)
+
+// ----------------------------------------------------------------------------
+// J0 band geometry: after eliminating Y_1 and differencing the constraint rows
+// the per-filament system is block-pentadiagonal in 3x3 blocks, i.e. a banded
+// matrix with 8 sub- and 8 super-diagonals (16 after partial pivoting).
+// ----------------------------------------------------------------------------
+constexpr int kBandKL = 8;
+constexpr int kBandKU = 8;
+constexpr int kBandW = 2 * kBandKL + kBandKU + 1;   // row window: c - i in [-8, 16]
+constexpr size_t kSolveSmemMax = 200 * 1024;        // shared memory of one band-solve CTA
+constexpr int kMaxSegPerFil = (int)(kSolveSmemMax / (6 * sizeof(double)));
+
+struct Layout {
+    int M = 0;           // filaments
+    int64_t S = 0;       // segments
+    int64_t nX = 0;      // 6S
+    int64_t nlam = 0;    // S - M
+    int maxN = 0;
+    int *N = nullptr;        // [M]
+    int *off = nullptr;      // [M+1] segment offsets
+    int *fil_of = nullptr;   // [S] filament of a segment
+};
+
+}  // namespace fil
+
+struct fil_ctx {
+    // parameters
+    fil::Layout lay;
+    std::vector<int> N_host, off_host;
+    double a, eta, dL, KB, KT, g0, kmu, knu, dt, tol;
+    int max_iter, prec;
+    cudaStream_t stream;
+    int device, num_sms;
+    std::string err;
+
+    // time-integration state
+    double *Y, *Yprev, *q, *uprev, *lam;
+    int have_prev;
+    int64_t steps;
+
+    // external loads
+    double *Fext, *Text, *follower;
+    int has_Fext, has_Text, has_follower;
+
+    // residual-evaluation buffers
+    double *qc, *Yc, *FT, *Tint, *VW, *Mh;
+
+    // RPY workspace
+    float4 *src32;        // 3 float4 per (padded) segment, mixed path
+    double *src64;        // 12 doubles per (padded) segment, FP64 path
+    int64_t Spad;
+    void *partials;       // stream-K partial sums
+    int rpy_grid32, rpy_grid64;
+    int64_t rpy_tiles;
+
+    // Broyden state
+    double *Xk, *fk, *Xn, *fn, *w, *g, *C, *D;
+    double *scal;          // device scalars: [alpha_0..alpha_{max-1}, ndf2, dff, ...]
+    double *red_part;      // reduction partials
+    int red_blocks;
+    unsigned long long *d_finf;   // atomic max of |f| bits
+    int *d_flags;          // [0] stall flag, [1] singular J0 flag
+    double *h_pinned;      // small pinned host buffer
+    int k;                 // stored (c, d) pairs of the current step
+    int in_step;           // a step was begun and not committed
+    int iters_step;        // Broyden iterations of the current step
+    int conv;              // current iterate satisfies ||f||_inf <= tol * a
+
+    // J0 band factors
+    double *band;
+    int *piv;
+
+    // staging for host pointers (6S doubles each)
+    double *stage_a, *stage_b, *stage_c;
+
+    int64_t n_applies, n_iters;
+
+    void *arena;           // the single device allocation
+    size_t arena_bytes;
+
+    int64_t n_launches;    // kernels launched by this library
+    int prof_on;           // time RPY pair-kernel launches with CUDA events
+    int prof_n;
+    cudaEvent_t *prof_ev;  // 2 * kProfMax events, created on first use
+};
+
+namespace fil {
+
+// Launchers (all enqueue on c->stream and return a cudaError_t).
+cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW);
+cudaError_t rpy_setup(fil_ctx *c);          // grid sizes, called once at create
+size_t rpy_partial_bytes(const fil_ctx *c);
+
+cudaError_t unpack_forces(fil_ctx *c, const double *X, int with_forces);
+cudaError_t residual_rows(fil_ctx *c, const double *X, double *f);
+cudaError_t init_straight(fil_ctx *c, const double *base, const double *t, const double *mu,
+                          const double *xi);
+cudaError_t extrapolate_guess(fil_ctx *c, double *X0);
+cudaError_t commit_state(fil_ctx *c, const double *X);
+
+cudaError_t j0_build_factor(fil_ctx *c, const double *X);
+cudaError_t j0_solve(fil_ctx *c, const double *b, double *x);
+
+cudaError_t broyden_axpy_step(fil_ctx *c);                 // Xn = Xk - w
+cudaError_t broyden_dots(fil_ctx *c);                      // alpha_i, ndf2, dff
+cudaError_t broyden_update(fil_ctx *c);                    // history pair, new w
+
+}  // namespace fil

@@ -1,0 +1,292 @@
+// Per-filament kernels of the residual f(X) (paper Sec. 2.5, 2.9.3):
+//   unpack  : q_n = exp(u_n) q_n^j, t_n = R(q_n) e_x, robot-arm positions
+//             Y_n = Y_1 + (dL/2) sum_{m=2}^n (t_{m-1} + t_m)  (positionSubstitution-3d)
+//   forces  : F_n = Lam_{n+1/2} - Lam_{n-1/2} + external,
+//             T_n = M_{n+1/2} - M_{n-1/2} + (dL/2) t_n x (Lam_{n+1/2} + Lam_{n-1/2}) + external
+//             (constraint-force, constraint-torque, elastic-torque, quaternionM)
+//   residual: position rows Y_n - a1 Y^j_n - a0 Y^{j-1}_n - b dt V_n and rotation rows
+//             u_n - g u^j_n - b dt dexpinv_{u_n}(Omega_n) (RA-3d-system).
+// One warp per filament for the scans along the filament (the robot-arm prefix
+// sum uses warp shuffles, 32 segments per pass with a carry); one thread per
+// segment for the element-wise residual rows.
+#include <cuda_runtime.h>
+
+#include "fil_internal.cuh"
+#include "quat.cuh"
+
+namespace fil {
+namespace {
+
+__device__ __forceinline__ V3 shfl_up3(V3 v, int d) {
+    return {__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d),
+            __shfl_up_sync(0xffffffffu, v.z, d)};
+}
+__device__ __forceinline__ V3 shfl3(V3 v, int src) {
+    return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+            __shfl_sync(0xffffffffu, v.z, src)};
+}
+
+struct ForceParams {
+    double dL, KB, KT, g0, kmu, knu;
+};
+
+// Warp-wide robot-arm positions for one filament: given t_n per lane (one pass
+// of up to 32 segments), carry = Y of the segment before the pass and the
+// tangent before the pass. Returns Y_n for the lane; updates the carries.
+__device__ __forceinline__ V3 robot_arm_pass(V3 t, bool active, int n, double dL, V3 &carry_Y,
+                                             V3 &carry_t, int lane) {
+    V3 tprev = shfl_up3(t, 1);
+    if (lane == 0) tprev = carry_t;
+    V3 inc = (active && n > 0) ? (0.5 * dL) * (tprev + t) : v3(0, 0, 0);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        V3 o = shfl_up3(inc, d);
+        if (lane >= d) inc = inc + o;
+    }
+    V3 Yn = carry_Y + inc;
+    carry_Y = shfl3(Yn, 31);
+    carry_t = shfl3(t, 31);
+    return Yn;
+}
+
+// unpack (+ forces): one warp per filament.
+__global__ void unpack_forces_kernel(Layout lay, const double *__restrict__ X,
+                                     const double *__restrict__ qj, ForceParams fp,
+                                     const double *__restrict__ Fext,
+                                     const double *__restrict__ Text,
+                                     const double *__restrict__ follower, int with_forces,
+                                     double *__restrict__ qc, double *__restrict__ Yc,
+                                     double *__restrict__ FT, double *__restrict__ Tint) {
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= lay.M) return;
+    const int s0 = lay.off[warp];
+    const int N = lay.off[warp + 1] - s0;
+    const double *Xf = X + 6 * (int64_t)s0;
+
+    V3 carry_Y = ld3(Xf);
+    V3 carry_t = v3(0, 0, 0);
+    for (int base = 0; base < N; base += 32) {
+        const int n = base + lane;
+        const bool active = n < N;
+        Q4 q = {1, 0, 0, 0};
+        V3 t = v3(0, 0, 0);
+        if (active) {
+            q = qmul(qexp(ld3(Xf + 3 + 3 * n)), ld4(qj + 4 * (int64_t)(s0 + n)));
+            t = frame_t(q);
+        }
+        V3 Yn = robot_arm_pass(t, active, n, fp.dL, carry_Y, carry_t, lane);
+        if (active) {
+            st4(qc + 4 * (int64_t)(s0 + n), q);
+            st3(Yc + 3 * (int64_t)(s0 + n), Yn);
+        }
+    }
+    if (!with_forces) return;
+    __syncwarp();
+
+    const double *Lam = Xf + 3 + 3 * N;   // Lambda_{j+3/2}, j = 0..N-2
+    const double follow = follower ? follower[warp] : 0.0;
+    for (int n = lane; n < N; n += 32) {
+        const int64_t g = s0 + n;
+        const Q4 q = ld4(qc + 4 * g);
+        const V3 t = frame_t(q);
+        const V3 Lr = (n <= N - 2) ? ld3(Lam + 3 * n) : v3(0, 0, 0);
+        const V3 Ll = (n >= 1) ? ld3(Lam + 3 * (n - 1)) : v3(0, 0, 0);
+        V3 Mr = v3(0, 0, 0), Ml = v3(0, 0, 0);
+        if (n <= N - 2)
+            Mr = internal_moment(q, ld4(qc + 4 * (g + 1)), fp.dL, fp.KB, fp.KT, fp.g0, fp.kmu,
+                                 fp.knu);
+        if (n >= 1)
+            Ml = internal_moment(ld4(qc + 4 * (g - 1)), q, fp.dL, fp.KB, fp.KT, fp.g0, fp.kmu,
+                                 fp.knu);
+        V3 F = Lr - Ll;
+        V3 Ti = (Mr - Ml) + (0.5 * fp.dL) * cross(t, Lr + Ll);
+        if (Fext) F = F + ld3(Fext + 3 * g);
+        if (n == N - 1) F = F - follow * t;
+        V3 T = Ti;
+        if (Text) T = T + ld3(Text + 3 * g);
+        st3(FT + 6 * g, F);
+        st3(FT + 6 * g + 3, T);
+        if (Tint) st3(Tint + 3 * g, Ti);
+    }
+}
+
+struct Scheme {
+    double a1, a0, bdt, g;   // f = Y - a1 Y^j - a0 Y^{j-1} - bdt V ; u - g u^j - bdt dexpinv
+};
+
+// One thread per segment: both 3-rows of the residual, plus ||f||_inf (as the
+// maximum of the IEEE bit patterns of |f|; a NaN compares above every number).
+__global__ void residual_rows_kernel(Layout lay, const double *__restrict__ X,
+                                     const double *__restrict__ Yc,
+                                     const double *__restrict__ VW,
+                                     const double *__restrict__ Yj,
+                                     const double *__restrict__ Yjm1,
+                                     const double *__restrict__ uj, Scheme sc,
+                                     double *__restrict__ f,
+                                     unsigned long long *__restrict__ finf_bits) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double m = 0.0;
+    if (g < lay.S) {
+        const int i = lay.fil_of[g];
+        const int s0 = lay.off[i];
+        const int N = lay.off[i + 1] - s0;
+        const int n = (int)(g - s0);
+        const double *Xf = X + 6 * (int64_t)s0;
+        double *ff = f + 6 * (int64_t)s0;
+        const V3 u = ld3(Xf + 3 + 3 * n);
+        const V3 V = ld3(VW + 6 * g), W = ld3(VW + 6 * g + 3);
+        V3 pos = ld3(Yc + 3 * g) - sc.a1 * ld3(Yj + 3 * g) - sc.bdt * V;
+        if (sc.a0 != 0.0) pos = pos - sc.a0 * ld3(Yjm1 + 3 * g);
+        V3 rot = u - sc.bdt * dexpinv(u, W);
+        if (sc.g != 0.0) rot = rot - sc.g * ld3(uj + 3 * g);
+        st3(ff + 3 + 3 * n, rot);
+        st3(n == 0 ? ff : ff + 3 + 3 * N + 3 * (n - 1), pos);
+        m = fmax(fmax(fmax(fabs(pos.x), fabs(pos.y)), fmax(fabs(pos.z), fabs(rot.x))),
+                 fmax(fabs(rot.y), fabs(rot.z)));
+        if (isnan(pos.x + pos.y + pos.z + rot.x + rot.y + rot.z)) m = __longlong_as_double(
+            0x7ff8000000000000ll);
+    }
+    unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        unsigned long long o = __shfl_down_sync(0xffffffffu, bits, d);
+        bits = o > bits ? o : bits;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(finf_bits, bits);
+}
+
+// Straight filaments from (base, t, mu) with the App. A.1 construction and an
+// optional perturbation q <- exp(xi) q; one warp per filament.
+__global__ void init_straight_kernel(Layout lay, const double *__restrict__ base,
+                                     const double *__restrict__ tt,
+                                     const double *__restrict__ mu,
+                                     const double *__restrict__ xi, double dL,
+                                     double *__restrict__ Y, double *__restrict__ q) {
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= lay.M) return;
+    const int s0 = lay.off[warp];
+    const int N = lay.off[warp + 1] - s0;
+    const V3 t = ld3(tt + 3 * warp), m = ld3(mu + 3 * warp);
+    // p1 = (e_x . t, e_x x t)^{1/2} = (t1, 0, -t3, t2)^{1/2}
+    const Q4 p1 = qsqrt(Q4{t.x, 0.0, -t.z, t.y});
+    // n' = R(p1) e_y, p2 = (n'.mu, n' x mu)^{1/2}, q = p2 p1
+    const V3 np = frame_mu(p1);
+    const V3 c = cross(np, m);
+    const Q4 p2 = qsqrt(Q4{dot(np, m), c.x, c.y, c.z});
+    const Q4 qf = qmul(p2, p1);
+    V3 carry_Y = ld3(base + 3 * warp);
+    V3 carry_t = v3(0, 0, 0);
+    for (int b = 0; b < N; b += 32) {
+        const int n = b + lane;
+        const bool active = n < N;
+        Q4 qn = qf;
+        if (active && xi) qn = qmul(qexp(ld3(xi + 3 * (int64_t)(s0 + n))), qf);
+        const V3 tn = active ? frame_t(qn) : v3(0, 0, 0);
+        const V3 Yn = robot_arm_pass(tn, active, n, dL, carry_Y, carry_t, lane);
+        if (active) {
+            st4(q + 4 * (int64_t)(s0 + n), qn);
+            st3(Y + 3 * (int64_t)(s0 + n), Yn);
+        }
+    }
+}
+
+// X_0 of a step: Y_1 = 2 Y_1^j - Y_1^{j-1} (Y_1^j on the first step),
+// u = u^j (0 on the first step), Lambda = Lambda^j. One thread per segment.
+__global__ void extrapolate_kernel(Layout lay, const double *__restrict__ Y,
+                                   const double *__restrict__ Yprev,
+                                   const double *__restrict__ uprev,
+                                   const double *__restrict__ lam, int have_prev,
+                                   double *__restrict__ X0) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= lay.S) return;
+    const int i = lay.fil_of[g];
+    const int s0 = lay.off[i];
+    const int N = lay.off[i + 1] - s0;
+    const int n = (int)(g - s0);
+    double *Xf = X0 + 6 * (int64_t)s0;
+    if (n == 0) {
+        V3 y1 = ld3(Y + 3 * g);
+        if (have_prev) y1 = 2.0 * y1 - ld3(Yprev + 3 * g);
+        st3(Xf, y1);
+    }
+    st3(Xf + 3 + 3 * n, have_prev ? ld3(uprev + 3 * g) : v3(0, 0, 0));
+    if (n <= N - 2) st3(Xf + 3 + 3 * N + 3 * n, ld3(lam + 3 * (int64_t)(s0 - i + n)));
+}
+
+// History shift after convergence (qc, Yc hold the unpack of X).
+__global__ void commit_kernel(Layout lay, const double *__restrict__ X,
+                              const double *__restrict__ qc, const double *__restrict__ Yc,
+                              double *__restrict__ Y, double *__restrict__ Yprev,
+                              double *__restrict__ q, double *__restrict__ uprev,
+                              double *__restrict__ lam) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= lay.S) return;
+    const int i = lay.fil_of[g];
+    const int s0 = lay.off[i];
+    const int N = lay.off[i + 1] - s0;
+    const int n = (int)(g - s0);
+    const double *Xf = X + 6 * (int64_t)s0;
+    st3(Yprev + 3 * g, ld3(Y + 3 * g));
+    st3(Y + 3 * g, ld3(Yc + 3 * g));
+    st4(q + 4 * g, ld4(qc + 4 * g));
+    st3(uprev + 3 * g, ld3(Xf + 3 + 3 * n));
+    if (n <= N - 2) st3(lam + 3 * (int64_t)(s0 - i + n), ld3(Xf + 3 + 3 * N + 3 * n));
+}
+
+unsigned warp_grid(int M, int threads) { return (unsigned)(((int64_t)M * 32 + threads - 1) / threads); }
+unsigned seg_grid(int64_t S, int threads) { return (unsigned)((S + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t unpack_forces(fil_ctx *c, const double *X, int with_forces) {
+    ForceParams fp{c->dL, c->KB, c->KT, c->g0, c->kmu, c->knu};
+    unpack_forces_kernel<<<warp_grid(c->lay.M, 128), 128, 0, c->stream>>>(
+        c->lay, X, c->q, fp, c->has_Fext ? c->Fext : nullptr, c->has_Text ? c->Text : nullptr,
+        c->has_follower ? c->follower : nullptr, with_forces, c->qc, c->Yc, c->FT,
+        with_forces == 2 ? c->Tint : nullptr);
+    c->n_launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t residual_rows(fil_ctx *c, const double *X, double *f) {
+    Scheme sc;
+    if (c->have_prev) {
+        sc = {4.0 / 3.0, -1.0 / 3.0, 2.0 / 3.0 * c->dt, 1.0 / 3.0};
+    } else {
+        sc = {1.0, 0.0, c->dt, 0.0};
+    }
+    cudaError_t e = cudaMemsetAsync(c->d_finf, 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+    residual_rows_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(
+        c->lay, X, c->Yc, c->VW, c->Y, c->Yprev, c->uprev, sc, f, c->d_finf);
+    c->n_launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t init_straight(fil_ctx *c, const double *base, const double *t, const double *mu,
+                          const double *xi) {
+    init_straight_kernel<<<warp_grid(c->lay.M, 128), 128, 0, c->stream>>>(c->lay, base, t, mu, xi,
+                                                                          c->dL, c->Y, c->q);
+    c->n_launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t extrapolate_guess(fil_ctx *c, double *X0) {
+    extrapolate_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(
+        c->lay, c->Y, c->Yprev, c->uprev, c->lam, c->have_prev, X0);
+    c->n_launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t commit_state(fil_ctx *c, const double *X) {
+    cudaError_t e = unpack_forces(c, X, 0);
+    if (e != cudaSuccess) return e;
+    commit_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(c->lay, X, c->qc, c->Yc, c->Y,
+                                                                    c->Yprev, c->q, c->uprev, c->lam);
+    c->n_launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace fil

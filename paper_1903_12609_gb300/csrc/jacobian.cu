@@ -1,0 +1,366 @@
+// Approximate Jacobian J0 of App. B.2 and its solve, one filament per warp.
+//
+// Per filament, J0 = [[I, 0, J13], [0, J22, J23], [I, J32, J33]] acting on
+// (Y_1, u_0..u_{N-1}, Lam_0..Lam_{N-2}) (0-based segments; Lam_j joins segments
+// j and j+1). Its blocks are those of App. B.2 (J13, J33 as in App. B.1):
+//   J13 = -c_t I on Lam_0;  J33: c_t (Lam_{s-1} - Lam_s) in the row of segment s;
+//   J32: (dL/2) w [x t_n] with w = 1 at the ends of the cumulative sum, 2 inside;
+//   J22, J23 from the Taylor-truncated dexpinv and the frame-vector moments;
+//   c_t = b dt/(6 pi eta a), c_r = b dt/(8 pi eta a^3), b = 2/3 (BDF2) or 1.
+//
+// The paper factors each 6N x 6N block densely (O(N^3)). Here the same linear
+// system is solved exactly in O(N): row 1 gives Y_1 = b1 + c_t Lam_0; subtracting
+// consecutive constraint rows (row_{s+1} - row_s, and row_1 - row of Y_1) removes
+// Y_1 and turns the cumulative J32 into two neighbour terms. With the unknowns
+// interleaved as (u_0, Lam_0, u_1, Lam_1, ..., Lam_{N-2}, u_{N-1}) the remaining
+// (6N-3) x (6N-3) matrix is block-pentadiagonal in 3x3 blocks, i.e. banded with
+// 8 sub- and 8 super-diagonals, and is factored by Gaussian elimination with
+// partial pivoting inside the band (U gains up to 8 more super-diagonals).
+//
+// Band storage: row-major windows, A(i, c) at band[i * kBandW + (c - i + kBandKL)]
+// for c - i in [-8, 16]; filament f starts at row 6 off[f] - 3 f.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "fil_internal.cuh"
+#include "quat.cuh"
+
+namespace fil {
+namespace {
+
+struct M33 {
+    double m[9];
+};
+
+__device__ __forceinline__ M33 mzero() {
+    M33 r;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) r.m[i] = 0.0;
+    return r;
+}
+__device__ __forceinline__ M33 meye() {
+    M33 r = mzero();
+    r.m[0] = r.m[4] = r.m[8] = 1.0;
+    return r;
+}
+// [v x]: [v x] w = v x w
+__device__ __forceinline__ M33 skew(V3 v) {
+    M33 r;
+    r.m[0] = 0.0;   r.m[1] = -v.z; r.m[2] = v.y;
+    r.m[3] = v.z;   r.m[4] = 0.0;  r.m[5] = -v.x;
+    r.m[6] = -v.y;  r.m[7] = v.x;  r.m[8] = 0.0;
+    return r;
+}
+// [x v] = -[v x]: [x v] w = w x v
+__device__ __forceinline__ M33 rskew(V3 v) { return skew(v3(-v.x, -v.y, -v.z)); }
+__device__ __forceinline__ M33 mmul(const M33 &a, const M33 &b) {
+    M33 r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            r.m[3 * i + j] = a.m[3 * i] * b.m[j] + a.m[3 * i + 1] * b.m[3 + j] +
+                             a.m[3 * i + 2] * b.m[6 + j];
+    return r;
+}
+__device__ __forceinline__ M33 madd(const M33 &a, const M33 &b, double s = 1.0) {
+    M33 r;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) r.m[i] = a.m[i] + s * b.m[i];
+    return r;
+}
+__device__ __forceinline__ M33 mscale(const M33 &a, double s) {
+    M33 r;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) r.m[i] = s * a.m[i];
+    return r;
+}
+__device__ __forceinline__ M33 outer(V3 a, V3 b) {
+    M33 r;
+    r.m[0] = a.x * b.x; r.m[1] = a.x * b.y; r.m[2] = a.x * b.z;
+    r.m[3] = a.y * b.x; r.m[4] = a.y * b.y; r.m[5] = a.y * b.z;
+    r.m[6] = a.z * b.x; r.m[7] = a.z * b.y; r.m[8] = a.z * b.z;
+    return r;
+}
+
+struct J0Params {
+    double dL, KB, KT, g0, kmu, knu, ct, cr;
+};
+
+// Derivatives of the frame-vector moment of joint (a, b) with respect to u_a
+// (Da) and u_b (Db), App. B.2.
+__device__ void moment_derivs(const J0Params &p, Q4 qa, Q4 qb, M33 &Da, M33 &Db) {
+    const V3 ta = frame_t(qa), tb = frame_t(qb);
+    const V3 ma = frame_mu(qa), mb = frame_mu(qb);
+    const V3 na = frame_nu(qa), nb = frame_nu(qb);
+    const double beta = (dot(mb, na) - dot(ma, nb)) / (2.0 * p.dL) - p.g0;
+    const V3 w = cross(na, mb) - cross(ma, nb);
+    const M33 tw = mscale(outer(ta + tb, w), 1.0 / (2.0 * p.dL));
+    // Da = KB([x tb][x ta]/dL - kmu/2 [x ma] - knu/2 [x na]) + KT/2 (beta [x ta] + tw)
+    M33 bend = mscale(mmul(rskew(tb), rskew(ta)), 1.0 / p.dL);
+    bend = madd(bend, rskew(ma), -0.5 * p.kmu);
+    bend = madd(bend, rskew(na), -0.5 * p.knu);
+    Da = madd(mscale(bend, p.KB), madd(mscale(rskew(ta), beta), tw), 0.5 * p.KT);
+    // Db = KB([ta x][x tb]/dL - kmu/2 [x mb] - knu/2 [x nb]) + KT/2 (beta [x tb] - tw)
+    bend = mscale(mmul(skew(ta), rskew(tb)), 1.0 / p.dL);
+    bend = madd(bend, rskew(mb), -0.5 * p.kmu);
+    bend = madd(bend, rskew(nb), -0.5 * p.knu);
+    Db = madd(mscale(bend, p.KB), madd(mscale(rskew(tb), beta), tw, -1.0), 0.5 * p.KT);
+}
+
+__device__ __forceinline__ void put_block(double *band, int64_t row_block, int64_t col_block,
+                                          const M33 &B) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int64_t i = 3 * row_block + r;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            const int64_t col = 3 * col_block + cc;
+            band[i * kBandW + (col - i + kBandKL)] = B.m[3 * r + cc];
+        }
+    }
+}
+
+// Assemble the band of each filament (one warp per filament).
+__global__ void j0_build_kernel(Layout lay, const double *__restrict__ X,
+                                const double *__restrict__ qc, const double *__restrict__ Tint,
+                                J0Params p, double *__restrict__ band_all) {
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= lay.M) return;
+    const int s0 = lay.off[warp];
+    const int N = lay.off[warp + 1] - s0;
+    const int64_t nrow = 6 * (int64_t)N - 3;
+    double *band = band_all + (6 * (int64_t)s0 - 3 * (int64_t)warp) * kBandW;
+    for (int64_t i = lane; i < nrow * kBandW; i += 32) band[i] = 0.0;
+    __syncwarp();
+    const double *Xf = X + 6 * (int64_t)s0;
+    const double *Lam = Xf + 3 + 3 * N;
+    const M33 I3 = meye();
+    for (int s = lane; s < N; s += 32) {
+        const int64_t g = s0 + s;
+        const Q4 qs = ld4(qc + 4 * g);
+        const V3 ts = frame_t(qs);
+        const V3 u = ld3(Xf + 3 + 3 * s);
+        const V3 T = ld3(Tint + 3 * g);
+        const V3 Lsum = ((s <= N - 2) ? ld3(Lam + 3 * s) : v3(0, 0, 0)) +
+                        ((s >= 1) ? ld3(Lam + 3 * (s - 1)) : v3(0, 0, 0));
+        M33 Da_r, Db_r, Da_l, Db_l;   // joint s (right) and joint s-1 (left)
+        if (s <= N - 2) moment_derivs(p, qs, ld4(qc + 4 * (g + 1)), Da_r, Db_r);
+        if (s >= 1) moment_derivs(p, ld4(qc + 4 * (g - 1)), qs, Da_l, Db_l);
+        const M33 ux = skew(u);
+        const M33 ux2 = mmul(ux, ux);
+        // A_s = I - [u x]/2 + [u x]^2/12
+        const M33 A = madd(madd(I3, ux, -0.5), ux2, 1.0 / 12.0);
+        // dT_s/du_s
+        M33 dT = mscale(mmul(rskew(Lsum), rskew(ts)), 0.5 * p.dL);
+        if (s <= N - 2) dT = madd(dT, Da_r);
+        if (s >= 1) dT = madd(dT, Db_l, -1.0);
+        // J22_ss = I - c_r { dT - ([x T] + [u x] dT)/2 + ([x (u x T)] + [u x][x T] + [u x]^2 dT)/12 }
+        const M33 xT = rskew(T);
+        M33 inner = madd(dT, madd(xT, mmul(ux, dT)), -0.5);
+        M33 third = madd(madd(rskew(cross(u, T)), mmul(ux, xT)), mmul(ux2, dT));
+        inner = madd(inner, third, 1.0 / 12.0);
+        const int64_t rb = 2 * s;   // block row of the rotation rows of segment s
+        put_block(band, rb, 2 * s, madd(I3, inner, -p.cr));
+        if (s <= N - 2) put_block(band, rb, 2 * s + 2, mscale(mmul(A, Db_r), -p.cr));
+        if (s >= 1) put_block(band, rb, 2 * s - 2, mscale(mmul(A, Da_l), p.cr));
+        // J23: -c_r A (dL/2) [t_s x] on Lam_{s-1} and Lam_s
+        const M33 G = mscale(mmul(A, skew(ts)), -p.cr * 0.5 * p.dL);
+        if (s >= 1) put_block(band, rb, 2 * s - 1, G);
+        if (s <= N - 2) put_block(band, rb, 2 * s + 1, G);
+        // differenced constraint rows of joint j = s:
+        // (dL/2)([x t_s] u_s + [x t_{s+1}] u_{s+1}) + c_t(-Lam_{s-1} + 2 Lam_s - Lam_{s+1})
+        if (s <= N - 2) {
+            const int64_t cb = 2 * s + 1;
+            const V3 tn = frame_t(ld4(qc + 4 * (g + 1)));
+            put_block(band, cb, 2 * s, mscale(rskew(ts), 0.5 * p.dL));
+            put_block(band, cb, 2 * s + 2, mscale(rskew(tn), 0.5 * p.dL));
+            put_block(band, cb, 2 * s + 1, mscale(I3, 2.0 * p.ct));
+            if (s >= 1) put_block(band, cb, 2 * s - 1, mscale(I3, -p.ct));
+            if (s + 1 <= N - 2) put_block(band, cb, 2 * s + 3, mscale(I3, -p.ct));
+        }
+    }
+}
+
+// In-place banded LU with partial pivoting (one warp per filament).
+__global__ void band_lu_kernel(Layout lay, double *__restrict__ band_all, int *__restrict__ piv_all,
+                               int *__restrict__ flags) {
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= lay.M) return;
+    const int s0 = lay.off[warp];
+    const int N = lay.off[warp + 1] - s0;
+    const int n = 6 * N - 3;
+    const int64_t row0 = 6 * (int64_t)s0 - 3 * (int64_t)warp;
+    double *A = band_all + row0 * kBandW;
+    int *piv = piv_all + row0;
+#define BAND(i, c) A[(int64_t)(i) * kBandW + ((c) - (i) + kBandKL)]
+    for (int j = 0; j < n; ++j) {
+        const int last = min(n - 1, j + kBandKL);
+        // pivot: first row of maximal |A(i, j)|, i in [j, last]
+        double v = -1.0;
+        int idx = j;
+        if (j + lane <= last && lane <= kBandKL) {
+            v = fabs(BAND(j + lane, j));
+            idx = j + lane;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, v, d);
+            const int oi = __shfl_down_sync(0xffffffffu, idx, d);
+            if (ov > v || (ov == v && oi < idx)) {
+                v = ov;
+                idx = oi;
+            }
+        }
+        const int p = __shfl_sync(0xffffffffu, idx, 0);
+        const double pv = __shfl_sync(0xffffffffu, v, 0);
+        if (lane == 0) piv[j] = p;
+        const int cmax = min(n - 1, j + kBandKL + kBandKU);
+        if (p != j) {
+            const int c = j + lane;
+            if (c <= cmax) {
+                const double t = BAND(j, c);
+                BAND(j, c) = BAND(p, c);
+                BAND(p, c) = t;
+            }
+        }
+        __syncwarp();
+        if (pv == 0.0) {
+            if (lane == 0) atomicOr(flags + 1, 1);
+            continue;
+        }
+        const double inv = 1.0 / BAND(j, j);
+        double l = 0.0;
+        if (lane >= 1 && j + lane <= last) {
+            l = BAND(j + lane, j) * inv;
+            BAND(j + lane, j) = l;
+        }
+        __syncwarp();
+        // rank-1 update of rows j+1..last, columns j+1..cmax
+        const int nr = last - j, nc = cmax - j;
+        for (int e = lane; e < nr * nc; e += 32) {
+            const int i = j + 1 + e / nc;
+            const int c = j + 1 + e % nc;
+            BAND(i, c) -= BAND(i, j) * BAND(j, c);
+        }
+        __syncwarp();
+    }
+#undef BAND
+}
+
+// x = J0^{-1} b for every filament (b and x in the X / f layout; may alias).
+__global__ void band_solve_kernel(Layout lay, const double *__restrict__ band_all,
+                                  const int *__restrict__ piv_all, double ct,
+                                  const double *b, double *x, int zmax) {
+    extern __shared__ double zs[];
+    const int wib = threadIdx.x >> 5;
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= lay.M) return;
+    double *z = zs + (int64_t)wib * zmax;
+    const int s0 = lay.off[warp];
+    const int N = lay.off[warp + 1] - s0;
+    const int n = 6 * N - 3;
+    const int64_t row0 = 6 * (int64_t)s0 - 3 * (int64_t)warp;
+    const double *A = band_all + row0 * kBandW;
+    const int *piv = piv_all + row0;
+    const double *bf = b + 6 * (int64_t)s0;
+    double *xf = x + 6 * (int64_t)s0;
+#define BAND(i, c) A[(int64_t)(i) * kBandW + ((c) - (i) + kBandKL)]
+    // gather the right-hand side in band order
+    for (int e = lane; e < 3 * N; e += 32) {
+        const int s = e / 3, r = e % 3;
+        z[6 * s + r] = bf[3 + 3 * s + r];   // rotation rows of segment s
+        if (s <= N - 2) {
+            const double b3n = bf[3 + 3 * N + 3 * s + r];                      // f3 of segment s+1
+            const double b3p = (s == 0) ? bf[r] : bf[3 + 3 * N + 3 * (s - 1) + r];
+            z[6 * s + 3 + r] = b3n - b3p;
+        }
+    }
+    const double b1x = bf[0], b1y = bf[1], b1z = bf[2];
+    __syncwarp();
+    // forward: L with row interchanges applied in elimination order
+    for (int j = 0; j < n; ++j) {
+        const int p = piv[j];
+        if (p != j && lane == 0) {
+            const double t = z[j];
+            z[j] = z[p];
+            z[p] = t;
+        }
+        __syncwarp();
+        const double zj = z[j];
+        const int i = j + 1 + lane;
+        if (lane < kBandKL && i < n) z[i] -= BAND(i, j) * zj;
+        __syncwarp();
+    }
+    // backward: U has kl + ku super-diagonals
+    for (int j = n - 1; j >= 0; --j) {
+        const int c = j + 1 + lane;
+        double t = (lane < kBandKL + kBandKU && c < n) ? BAND(j, c) * z[c] : 0.0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) t += __shfl_down_sync(0xffffffffu, t, d);
+        if (lane == 0) z[j] = (z[j] - t) / BAND(j, j);
+        __syncwarp();
+    }
+    // scatter back: u_s, Lam_j, and Y_1 = b1 + c_t Lam_0
+    for (int e = lane; e < 3 * N; e += 32) {
+        const int s = e / 3, r = e % 3;
+        xf[3 + 3 * s + r] = z[6 * s + r];
+        if (s <= N - 2) xf[3 + 3 * N + 3 * s + r] = z[6 * s + 3 + r];
+    }
+    if (lane == 0) {
+        const double l0 = (N >= 2) ? z[3] : 0.0, l1 = (N >= 2) ? z[4] : 0.0,
+                     l2 = (N >= 2) ? z[5] : 0.0;
+        xf[0] = b1x + ct * l0;
+        xf[1] = b1y + ct * l1;
+        xf[2] = b1z + ct * l2;
+    }
+#undef BAND
+}
+
+constexpr int kJ0Threads = 128;
+
+J0Params make_params(const fil_ctx *c) {
+    const double beta = c->have_prev ? 2.0 / 3.0 : 1.0;
+    return J0Params{c->dL, c->KB, c->KT, c->g0, c->kmu, c->knu,
+                    beta * c->dt / (6.0 * kPi * c->eta * c->a),
+                    beta * c->dt / (8.0 * kPi * c->eta * c->a * c->a * c->a)};
+}
+
+}  // namespace
+
+cudaError_t j0_build_factor(fil_ctx *c, const double *X) {
+    const unsigned grid = (unsigned)(((int64_t)c->lay.M * 32 + kJ0Threads - 1) / kJ0Threads);
+    const J0Params p = make_params(c);
+    j0_build_kernel<<<grid, kJ0Threads, 0, c->stream>>>(c->lay, X, c->qc, c->Tint, p, c->band);
+    band_lu_kernel<<<grid, kJ0Threads, 0, c->stream>>>(c->lay, c->band, c->piv, c->d_flags);
+    c->n_launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t j0_solve(fil_ctx *c, const double *b, double *x) {
+    // one warp per filament; up to 4 warps per CTA, fewer for long filaments so
+    // that each warp's right-hand side fits in shared memory
+    const int zmax = 6 * c->lay.maxN;
+    const size_t per_warp = (size_t)zmax * sizeof(double);
+    int warps = (int)std::min<size_t>(4, kSolveSmemMax / per_warp);
+    if (warps < 1) return cudaErrorInvalidValue;
+    const size_t smem = warps * per_warp;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(band_solve_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int threads = 32 * warps;
+    const unsigned grid = (unsigned)(((int64_t)c->lay.M * 32 + threads - 1) / threads);
+    band_solve_kernel<<<grid, threads, smem, c->stream>>>(c->lay, c->band, c->piv,
+                                                          make_params(c).ct, b, x, zmax);
+    c->n_launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace fil

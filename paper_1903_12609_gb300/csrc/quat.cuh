@@ -1,0 +1,114 @@
+// FP64 quaternion / Lie-group helpers for device code (paper Sec. 2.9, App. A).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace fil {
+
+struct Q4 {
+    double w, x, y, z;   // (q0, q1, q2, q3), scalar first
+};
+
+struct V3 {
+    double x, y, z;
+};
+
+__device__ __forceinline__ V3 v3(double x, double y, double z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ double norm(V3 a) { return sqrt(dot(a, a)); }
+
+__device__ __forceinline__ V3 ld3(const double *p) { return {p[0], p[1], p[2]}; }
+__device__ __forceinline__ void st3(double *p, V3 v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; }
+__device__ __forceinline__ Q4 ld4(const double *p) { return {p[0], p[1], p[2], p[3]}; }
+__device__ __forceinline__ void st4(double *p, Q4 q) { p[0] = q.w; p[1] = q.x; p[2] = q.y; p[3] = q.z; }
+
+// Product (p0 q0 - p.q, p0 q + q0 p + p x q), Sec. 2.9.1.
+__device__ __forceinline__ Q4 qmul(Q4 p, Q4 q) {
+    return {p.w * q.w - (p.x * q.x + p.y * q.y + p.z * q.z),
+            p.w * q.x + q.w * p.x + (p.y * q.z - p.z * q.y),
+            p.w * q.y + q.w * p.y + (p.z * q.x - p.x * q.z),
+            p.w * q.z + q.w * p.z + (p.x * q.y - p.y * q.x)};
+}
+__device__ __forceinline__ Q4 qconj(Q4 q) { return {q.w, -q.x, -q.y, -q.z}; }
+
+// Square root of a unit quaternion, App. A.1 (special case p0 = -1).
+__device__ __forceinline__ Q4 qsqrt(Q4 p) {
+    if (p.w == -1.0) return {0.0, 0.0, 0.0, 1.0};
+    double s = sqrt(2.0 * (p.w + 1.0));
+    return {sqrt((p.w + 1.0) * 0.5), p.x / s, p.y / s, p.z / s};
+}
+
+// exp(u) = (cos(|u|/2), sin(|u|/2) u/|u|), Sec. 2.9.3. For tiny |u| the
+// factor sin(x/2)/x uses its Taylor series 1/2 - x^2/48 + x^4/3840.
+__device__ __forceinline__ Q4 qexp(V3 u) {
+    double th = norm(u);
+    double s, c;
+    sincos(0.5 * th, &s, &c);
+    double f;
+    if (th < 1e-4) {
+        double t2 = th * th;
+        f = 0.5 - t2 / 48.0 + t2 * t2 / 3840.0;
+    } else {
+        f = s / th;
+    }
+    return {c, f * u.x, f * u.y, f * u.z};
+}
+
+// Columns of R(q) (eq. quaternion_rotation_matrix): tangent, mu, nu.
+__device__ __forceinline__ V3 frame_t(Q4 q) {
+    return {1.0 - 2.0 * (q.y * q.y + q.z * q.z), 2.0 * (q.x * q.y + q.z * q.w),
+            2.0 * (q.x * q.z - q.y * q.w)};
+}
+__device__ __forceinline__ V3 frame_mu(Q4 q) {
+    return {2.0 * (q.x * q.y - q.z * q.w), 1.0 - 2.0 * (q.x * q.x + q.z * q.z),
+            2.0 * (q.z * q.y + q.x * q.w)};
+}
+__device__ __forceinline__ V3 frame_nu(Q4 q) {
+    return {2.0 * (q.x * q.z + q.y * q.w), 2.0 * (q.z * q.y - q.x * q.w),
+            1.0 - 2.0 * (q.y * q.y + q.x * q.x)};
+}
+// R(q) v
+__device__ __forceinline__ V3 rotate(Q4 q, V3 v) {
+    V3 t = frame_t(q), m = frame_mu(q), n = frame_nu(q);
+    return {t.x * v.x + m.x * v.y + n.x * v.z, t.y * v.x + m.y * v.y + n.y * v.z,
+            t.z * v.x + m.z * v.y + n.z * v.z};
+}
+
+// dexpinv_u(W) = W - (u x W)/2 - c(|u|) u x (u x W), eq. dexpinv_definition,
+// c(x) = (x cot(x/2) - 2)/(2x^2); below x = 1e-2 the Taylor series of x cot(x/2)
+// gives c = -1/12 - x^2/720 - x^4/30240.
+__device__ __forceinline__ V3 dexpinv(V3 u, V3 W) {
+    double th = norm(u);
+    double c;
+    if (th < 1e-2) {
+        double t2 = th * th;
+        c = -1.0 / 12.0 - t2 / 720.0 - t2 * t2 / 30240.0;
+    } else {
+        c = (th / tan(0.5 * th) - 2.0) / (2.0 * th * th);
+    }
+    V3 uw = cross(u, W);
+    V3 uuw = cross(u, uw);
+    return {W.x - 0.5 * uw.x - c * uuw.x, W.y - 0.5 * uw.y - c * uuw.y,
+            W.z - 0.5 * uw.z - c * uuw.z};
+}
+
+// Internal moment between neighbouring segments, eq. quaternionM:
+// q_h = (q_b q_a^*)^{1/2} q_a,
+// M = R(q_h) D (2 [q_h^* (q_b - q_a)/dL]_R3 - (gamma0, kappa_mu, kappa_nu)),
+// D = diag(KT, KB, KB).
+__device__ __forceinline__ V3 internal_moment(Q4 qa, Q4 qb, double dL, double KB, double KT,
+                                              double g0, double kmu, double knu) {
+    Q4 qh = qmul(qsqrt(qmul(qb, qconj(qa))), qa);
+    Q4 dq = {(qb.w - qa.w) / dL, (qb.x - qa.x) / dL, (qb.y - qa.y) / dL, (qb.z - qa.z) / dL};
+    Q4 s = qmul(qconj(qh), dq);
+    V3 strain = {KT * (2.0 * s.x - g0), KB * (2.0 * s.y - kmu), KB * (2.0 * s.z - knu)};
+    return rotate(qh, strain);
+}
+
+}  // namespace fil

@@ -1,0 +1,518 @@
+// Rotne-Prager-Yamakawa mobility apply on sm_103a (paper Sec. 2.7.1).
+//
+//   V_n     = sum_m Mtt_nm F_m + Mtr_nm T_m
+//   Omega_n = sum_m Mrt_nm F_m + Mrr_nm T_m      over all S^2 ordered pairs.
+//
+// With d = Y_n - Y_m, r = |d| and every block scaled by 8 pi eta, a pair adds
+//   V     += A F + B (d.F) d + G (T x d)
+//   Omega += C T + D (d.T) d + G (F x d)
+// far form (r >= 2a):  A = 1/r + (2a^2/3)/r^3, B = 1/r^3 - 2a^2/r^5,
+//                      C = -1/(2 r^3), D = 3/(2 r^5), G = 1/r^3;
+// overlapping spheres (r < 2a, equal-radius form of Wajnryb et al., which the
+// paper cites for this case):
+//                      A = (4/(3a)) (1 - 9r/(32a)),  B = 1/(8 a^2 r),
+//                      C = (1 - 27r/(32a) + 5r^3/(64a^3)) / a^3,
+//                      D = (9/(32 a r) - 3r/(64 a^3)) / a^3,
+//                      G = (1 - 3r/(8a)) / (2 a^3);
+// at r = 0 (the self pair, or coincident distinct segments) the d-terms vanish
+// and A, C give the self mobilities 1/(6 pi eta a), 1/(8 pi eta a^3).
+//
+// Kernel design (GB300, one GPU):
+//  * No tensor cores: the pair sum is not a dense contraction. The bound is the
+//    FP32 (or FP64) FMA pipe; a pair costs ~55 FP32 instructions + 1 MUFU.
+//  * Each thread owns kRpyTargetsPerThread targets in registers; a CTA owns a
+//    tile of kRpyTile targets and streams sources through double-buffered
+//    shared memory in chunks of kRpyChunk; all lanes read the same source
+//    (broadcast), so shared-memory traffic is 3 LDS.128 per source per thread.
+//  * Stream-K persistent grid: the (tile, chunk) work units are split evenly
+//    over G = #SMs x resident-CTAs; a CTA writes one partial per tile it
+//    touches into slot (cta + tile) and a deterministic reduce kernel sums
+//    them in CTA order. No atomics: results are bitwise reproducible.
+//  * Mixed precision: positions enter as FP32 hi/lo pairs so that d keeps
+//    ~2 ulp relative accuracy for close pairs; each target sums kRpyComp pair
+//    terms in FP32 and folds them into a (hi, lo) compensated accumulator
+//    (TwoSum); the reduce adds the partials in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "fil_internal.cuh"
+
+namespace fil {
+namespace {
+
+constexpr float kFarPad = 1.0e5f;   // position of padding sources (they carry no load)
+
+struct RpyConst32 {
+    float near2;       // (2a)^2
+    float k23a2;       // 2a^2/3
+    float k2a2;        // 2a^2
+    float ov_A0, ov_A1;          // A = ov_A0 - ov_A1 r
+    float ov_B;                  // B = ov_B / r
+    float ov_C0, ov_C1, ov_C3;   // C = ov_C0 - ov_C1 r + ov_C3 r^3
+    float ov_D0, ov_D1;          // D = ov_D0 / r - ov_D1 r
+    float ov_G0, ov_G1;          // G = ov_G0 - ov_G1 r
+};
+
+struct RpyConst64 {
+    double near2, k23a2, k2a2;
+    double ov_A0, ov_A1, ov_B, ov_C0, ov_C1, ov_C3, ov_D0, ov_D1, ov_G0, ov_G1;
+};
+
+template <typename T, typename K>
+__host__ K make_const(double a) {
+    K k;
+    k.near2 = (T)(4.0 * a * a);
+    k.k23a2 = (T)(2.0 * a * a / 3.0);
+    k.k2a2 = (T)(2.0 * a * a);
+    k.ov_A0 = (T)(4.0 / (3.0 * a));
+    k.ov_A1 = (T)(4.0 / (3.0 * a) * 9.0 / (32.0 * a));
+    k.ov_B = (T)(1.0 / (8.0 * a * a));
+    double ia3 = 1.0 / (a * a * a);
+    k.ov_C0 = (T)ia3;
+    k.ov_C1 = (T)(ia3 * 27.0 / (32.0 * a));
+    k.ov_C3 = (T)(ia3 * 5.0 / (64.0 * a * a * a));
+    k.ov_D0 = (T)(ia3 * 9.0 / (32.0 * a));
+    k.ov_D1 = (T)(ia3 * 3.0 / (64.0 * a * a * a));
+    k.ov_G0 = (T)(0.5 * ia3);
+    k.ov_G1 = (T)(0.5 * ia3 * 3.0 / (8.0 * a));
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// Pack: FP64 (Y, FT) -> padded FP32 source records, 3 float4 per segment:
+//   [0] = (hi_x, hi_y, hi_z, F_x), [1] = (lo_x, lo_y, lo_z, F_y),
+//   [2] = (T_x, T_y, T_z, F_z), with hi = fl32(Y), lo = fl32(Y - hi).
+// Padding records sit far away with zero load, so they add exactly zero.
+// ---------------------------------------------------------------------------
+__global__ void pack32_kernel(const double *__restrict__ Y, const double *__restrict__ FT,
+                              int64_t S, int64_t Spad, float4 *__restrict__ src) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Spad) return;
+    float4 r0, r1, r2;
+    if (i < S) {
+        double y0 = Y[3 * i], y1 = Y[3 * i + 1], y2 = Y[3 * i + 2];
+        float h0 = __double2float_rn(y0), h1 = __double2float_rn(y1), h2 = __double2float_rn(y2);
+        float l0 = __double2float_rn(y0 - (double)h0);
+        float l1 = __double2float_rn(y1 - (double)h1);
+        float l2 = __double2float_rn(y2 - (double)h2);
+        const double *f = FT + 6 * i;
+        r0 = make_float4(h0, h1, h2, __double2float_rn(f[0]));
+        r1 = make_float4(l0, l1, l2, __double2float_rn(f[1]));
+        r2 = make_float4(__double2float_rn(f[3]), __double2float_rn(f[4]),
+                         __double2float_rn(f[5]), __double2float_rn(f[2]));
+    } else {
+        r0 = make_float4(kFarPad, kFarPad, kFarPad, 0.f);
+        r1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        r2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    src[3 * i] = r0;
+    src[3 * i + 1] = r1;
+    src[3 * i + 2] = r2;
+}
+
+// FP64 records: 9 doubles per segment (Y, F, T); padding far away, no load.
+__global__ void pack64_kernel(const double *__restrict__ Y, const double *__restrict__ FT,
+                              int64_t S, int64_t Spad, double *__restrict__ src) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Spad) return;
+    double *o = src + 9 * i;
+    if (i < S) {
+        o[0] = Y[3 * i];
+        o[1] = Y[3 * i + 1];
+        o[2] = Y[3 * i + 2];
+        for (int k = 0; k < 6; ++k) o[3 + k] = FT[6 * i + k];
+    } else {
+        o[0] = o[1] = o[2] = (double)kFarPad;
+        for (int k = 0; k < 6; ++k) o[3 + k] = 0.0;
+    }
+}
+
+// Error-free transformation s + e = a + b (Knuth's TwoSum), with the adds
+// kept out of FMA contraction and reassociation.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// One pair in FP32: target (hi, lo) position vs. source record (s0, s1, s2).
+__device__ __forceinline__ void pair32(float thx, float thy, float thz, float tlx, float tly,
+                                       float tlz, const float4 s0, const float4 s1,
+                                       const float4 s2, const RpyConst32 &k, float *acc) {
+    const float dx = __fsub_rn(thx, s0.x) + __fsub_rn(tlx, s1.x);
+    const float dy = __fsub_rn(thy, s0.y) + __fsub_rn(tly, s1.y);
+    const float dz = __fsub_rn(thz, s0.z) + __fsub_rn(tlz, s1.z);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float A, B, C, D, G;
+    if (__builtin_expect(r2 < k.near2, 0)) {
+        const float r = sqrtf(r2);
+        const float rinv = r > 0.f ? 1.0f / r : 0.f;
+        A = fmaf(-k.ov_A1, r, k.ov_A0);
+        B = k.ov_B * rinv;
+        C = fmaf(k.ov_C3 * r2, r, fmaf(-k.ov_C1, r, k.ov_C0));
+        D = fmaf(k.ov_D0, rinv, -k.ov_D1 * r);
+        G = fmaf(-k.ov_G1, r, k.ov_G0);
+    } else {
+        const float rinv = rsqrtf(r2);
+        const float rinv2 = rinv * rinv;
+        const float rinv3 = rinv * rinv2;
+        const float rinv5 = rinv3 * rinv2;
+        A = fmaf(k.k23a2, rinv3, rinv);
+        B = fmaf(-k.k2a2, rinv5, rinv3);
+        C = -0.5f * rinv3;
+        D = 1.5f * rinv5;
+        G = rinv3;
+    }
+    const float Fx = s0.w, Fy = s1.w, Fz = s2.w;
+    const float Tx = s2.x, Ty = s2.y, Tz = s2.z;
+    const float bF = B * fmaf(dx, Fx, fmaf(dy, Fy, dz * Fz));
+    const float dT = D * fmaf(dx, Tx, fmaf(dy, Ty, dz * Tz));
+    const float ex = G * dx, ey = G * dy, ez = G * dz;
+    acc[0] = fmaf(A, Fx, fmaf(bF, dx, fmaf(Ty, ez, fmaf(-Tz, ey, acc[0]))));
+    acc[1] = fmaf(A, Fy, fmaf(bF, dy, fmaf(Tz, ex, fmaf(-Tx, ez, acc[1]))));
+    acc[2] = fmaf(A, Fz, fmaf(bF, dz, fmaf(Tx, ey, fmaf(-Ty, ex, acc[2]))));
+    acc[3] = fmaf(C, Tx, fmaf(dT, dx, fmaf(Fy, ez, fmaf(-Fz, ey, acc[3]))));
+    acc[4] = fmaf(C, Ty, fmaf(dT, dy, fmaf(Fz, ex, fmaf(-Fx, ez, acc[4]))));
+    acc[5] = fmaf(C, Tz, fmaf(dT, dz, fmaf(Fx, ey, fmaf(-Fy, ex, acc[5]))));
+}
+
+// One pair in FP64 (record layout: Y, F, T).
+__device__ __forceinline__ void pair64(double tx, double ty, double tz, const double *s,
+                                       const RpyConst64 &k, double *acc) {
+    const double dx = tx - s[0], dy = ty - s[1], dz = tz - s[2];
+    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    double A, B, C, D, G;
+    if (__builtin_expect(r2 < k.near2, 0)) {
+        const double r = sqrt(r2);
+        const double rinv = r > 0.0 ? 1.0 / r : 0.0;
+        A = fma(-k.ov_A1, r, k.ov_A0);
+        B = k.ov_B * rinv;
+        C = fma(k.ov_C3 * r2, r, fma(-k.ov_C1, r, k.ov_C0));
+        D = fma(k.ov_D0, rinv, -k.ov_D1 * r);
+        G = fma(-k.ov_G1, r, k.ov_G0);
+    } else {
+        const double rinv = rsqrt(r2);
+        const double rinv2 = rinv * rinv;
+        const double rinv3 = rinv * rinv2;
+        const double rinv5 = rinv3 * rinv2;
+        A = fma(k.k23a2, rinv3, rinv);
+        B = fma(-k.k2a2, rinv5, rinv3);
+        C = -0.5 * rinv3;
+        D = 1.5 * rinv5;
+        G = rinv3;
+    }
+    const double Fx = s[3], Fy = s[4], Fz = s[5], Tx = s[6], Ty = s[7], Tz = s[8];
+    const double bF = B * fma(dx, Fx, fma(dy, Fy, dz * Fz));
+    const double dT = D * fma(dx, Tx, fma(dy, Ty, dz * Tz));
+    const double ex = G * dx, ey = G * dy, ez = G * dz;
+    acc[0] = fma(A, Fx, fma(bF, dx, fma(Ty, ez, fma(-Tz, ey, acc[0]))));
+    acc[1] = fma(A, Fy, fma(bF, dy, fma(Tz, ex, fma(-Tx, ez, acc[1]))));
+    acc[2] = fma(A, Fz, fma(bF, dz, fma(Tx, ey, fma(-Ty, ex, acc[2]))));
+    acc[3] = fma(C, Tx, fma(dT, dx, fma(Fy, ez, fma(-Fz, ey, acc[3]))));
+    acc[4] = fma(C, Ty, fma(dT, dy, fma(Fz, ex, fma(-Fx, ez, acc[4]))));
+    acc[5] = fma(C, Tz, fma(dT, dz, fma(Fx, ey, fma(-Fy, ex, acc[5]))));
+}
+
+// Unit range of CTA b in the stream-K split of W units over G CTAs.
+__device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
+    return (b * W) / G;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision pair kernel.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRpyThreads)
+rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, int G,
+                  RpyConst32 k, float *__restrict__ part) {
+    constexpr int kRec = 3 * kRpyChunk;           // float4 per chunk
+    __shared__ float4 sm[2][kRec];
+    const int tid = threadIdx.x;
+    const int64_t b = blockIdx.x;
+    int64_t u = unit_start(b, W, G);
+    const int64_t u_end = unit_start(b + 1, W, G);
+
+    while (u < u_end) {
+        const int64_t tile = u / n_chunks;
+        const int64_t c_begin = u - tile * n_chunks;
+        const int64_t c_end = min(n_chunks, c_begin + (u_end - u));
+
+        float th[kRpyTargetsPerThread][3], tl[kRpyTargetsPerThread][3];
+#pragma unroll
+        for (int t = 0; t < kRpyTargetsPerThread; ++t) {
+            const int64_t n = tile * kRpyTile + t * kRpyThreads + tid;
+            const float4 a0 = src[3 * n], a1 = src[3 * n + 1];
+            th[t][0] = a0.x; th[t][1] = a0.y; th[t][2] = a0.z;
+            tl[t][0] = a1.x; tl[t][1] = a1.y; tl[t][2] = a1.z;
+        }
+        float hi[kRpyTargetsPerThread][6], lo[kRpyTargetsPerThread][6];
+#pragma unroll
+        for (int t = 0; t < kRpyTargetsPerThread; ++t)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) hi[t][c] = lo[t][c] = 0.f;
+
+        // first chunk -> buffer 0
+        {
+            const float4 *g = src + 3 * (c_begin * kRpyChunk);
+            for (int i = tid; i < kRec; i += kRpyThreads) sm[0][i] = g[i];
+        }
+        __syncthreads();
+
+        for (int64_t ch = c_begin; ch < c_end; ++ch) {
+            const int buf = (int)((ch - c_begin) & 1);
+            // prefetch the next chunk into registers while computing this one
+            float4 pre0 = make_float4(0.f, 0.f, 0.f, 0.f), pre1 = pre0;
+            const bool has_next = (ch + 1 < c_end);
+            if (has_next) {
+                const float4 *g = src + 3 * ((ch + 1) * kRpyChunk);
+                pre0 = g[tid];
+                if (tid + kRpyThreads < kRec) pre1 = g[tid + kRpyThreads];
+            }
+            const float4 *s = sm[buf];
+#pragma unroll 1
+            for (int half = 0; half < kRpyChunk / kRpyComp; ++half) {
+                float acc[kRpyTargetsPerThread][6];
+#pragma unroll
+                for (int t = 0; t < kRpyTargetsPerThread; ++t)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) acc[t][c] = 0.f;
+#pragma unroll 4
+                for (int j = 0; j < kRpyComp; ++j) {
+                    const int rj = 3 * (half * kRpyComp + j);
+                    const float4 s0 = s[rj], s1 = s[rj + 1], s2 = s[rj + 2];
+#pragma unroll
+                    for (int t = 0; t < kRpyTargetsPerThread; ++t)
+                        pair32(th[t][0], th[t][1], th[t][2], tl[t][0], tl[t][1], tl[t][2], s0, s1,
+                               s2, k, acc[t]);
+                }
+#pragma unroll
+                for (int t = 0; t < kRpyTargetsPerThread; ++t)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        float sh, e;
+                        two_sum(hi[t][c], acc[t][c], sh, e);
+                        hi[t][c] = sh;
+                        lo[t][c] = __fadd_rn(lo[t][c], e);
+                    }
+            }
+            if (has_next) {
+                sm[buf ^ 1][tid] = pre0;
+                if (tid + kRpyThreads < kRec) sm[buf ^ 1][tid + kRpyThreads] = pre1;
+            }
+            __syncthreads();
+        }
+
+        // partial of this CTA for this tile -> slot (b + tile)
+        float *p = part + (size_t)(b + tile) * 12 * kRpyTile;
+#pragma unroll
+        for (int t = 0; t < kRpyTargetsPerThread; ++t) {
+            const int local = t * kRpyThreads + tid;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                p[c * kRpyTile + local] = hi[t][c];
+                p[(6 + c) * kRpyTile + local] = lo[t][c];
+            }
+        }
+        u = tile * n_chunks + c_end;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 pair kernel (same stream-K scaffolding).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRpyThreads)
+rpy_pair64_kernel(const double *__restrict__ src, int64_t n_chunks, int64_t W, int G,
+                  RpyConst64 k, double *__restrict__ part) {
+    constexpr int kRec = 9 * kRpyChunk;
+    __shared__ double sm[2][kRec];
+    const int tid = threadIdx.x;
+    const int64_t b = blockIdx.x;
+    int64_t u = unit_start(b, W, G);
+    const int64_t u_end = unit_start(b + 1, W, G);
+
+    while (u < u_end) {
+        const int64_t tile = u / n_chunks;
+        const int64_t c_begin = u - tile * n_chunks;
+        const int64_t c_end = min(n_chunks, c_begin + (u_end - u));
+
+        double ty[kRpyTargetsPerThread][3];
+#pragma unroll
+        for (int t = 0; t < kRpyTargetsPerThread; ++t) {
+            const int64_t n = tile * kRpyTile + t * kRpyThreads + tid;
+            ty[t][0] = src[9 * n];
+            ty[t][1] = src[9 * n + 1];
+            ty[t][2] = src[9 * n + 2];
+        }
+        double acc[kRpyTargetsPerThread][6];
+#pragma unroll
+        for (int t = 0; t < kRpyTargetsPerThread; ++t)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[t][c] = 0.0;
+
+        {
+            const double *g = src + 9 * (c_begin * kRpyChunk);
+            for (int i = tid; i < kRec; i += kRpyThreads) sm[0][i] = g[i];
+        }
+        __syncthreads();
+        for (int64_t ch = c_begin; ch < c_end; ++ch) {
+            const int buf = (int)((ch - c_begin) & 1);
+            double pre[(kRec + kRpyThreads - 1) / kRpyThreads];
+            const bool has_next = (ch + 1 < c_end);
+            if (has_next) {
+                const double *g = src + 9 * ((ch + 1) * kRpyChunk);
+#pragma unroll
+                for (int r = 0; r < (kRec + kRpyThreads - 1) / kRpyThreads; ++r) {
+                    const int i = tid + r * kRpyThreads;
+                    pre[r] = (i < kRec) ? g[i] : 0.0;
+                }
+            }
+            const double *s = sm[buf];
+#pragma unroll 2
+            for (int j = 0; j < kRpyChunk; ++j) {
+#pragma unroll
+                for (int t = 0; t < kRpyTargetsPerThread; ++t)
+                    pair64(ty[t][0], ty[t][1], ty[t][2], s + 9 * j, k, acc[t]);
+            }
+            if (has_next) {
+#pragma unroll
+                for (int r = 0; r < (kRec + kRpyThreads - 1) / kRpyThreads; ++r) {
+                    const int i = tid + r * kRpyThreads;
+                    if (i < kRec) sm[buf ^ 1][i] = pre[r];
+                }
+            }
+            __syncthreads();
+        }
+        double *p = part + (size_t)(b + tile) * 6 * kRpyTile;
+#pragma unroll
+        for (int t = 0; t < kRpyTargetsPerThread; ++t) {
+            const int local = t * kRpyThreads + tid;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) p[c * kRpyTile + local] = acc[t][c];
+        }
+        u = tile * n_chunks + c_end;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reduce the stream-K partials of each target (in CTA order) and scale by
+// 1/(8 pi eta). One thread per target.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cta_range_of_tile(int64_t tile, int64_t n_chunks, int64_t W,
+                                                  int64_t G, int64_t &b0, int64_t &b1) {
+    // CTA b owns units [floor(bW/G), floor((b+1)W/G)); the CTA that holds unit
+    // u is ceil((u+1)G/W) - 1.
+    const int64_t u0 = tile * n_chunks;
+    const int64_t u1 = (tile + 1) * n_chunks - 1;
+    b0 = ((u0 + 1) * G + W - 1) / W - 1;
+    b1 = ((u1 + 1) * G + W - 1) / W - 1;
+}
+
+__global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, int64_t n_chunks,
+                                    int64_t W, int G, double scale, double *__restrict__ VW) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= S) return;
+    const int64_t tile = n / kRpyTile;
+    const int local = (int)(n - tile * kRpyTile);
+    int64_t b0, b1;
+    cta_range_of_tile(tile, n_chunks, W, G, b0, b1);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t b = b0; b <= b1; ++b) {
+        const float *p = part + (size_t)(b + tile) * 12 * kRpyTile;
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            acc[c] += (double)p[c * kRpyTile + local] + (double)p[(6 + c) * kRpyTile + local];
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) VW[6 * n + c] = acc[c] * scale;
+}
+
+__global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, int64_t n_chunks,
+                                    int64_t W, int G, double scale, double *__restrict__ VW) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= S) return;
+    const int64_t tile = n / kRpyTile;
+    const int local = (int)(n - tile * kRpyTile);
+    int64_t b0, b1;
+    cta_range_of_tile(tile, n_chunks, W, G, b0, b1);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t b = b0; b <= b1; ++b) {
+        const double *p = part + (size_t)(b + tile) * 6 * kRpyTile;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] += p[c * kRpyTile + local];
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) VW[6 * n + c] = acc[c] * scale;
+}
+
+struct Geometry {
+    int64_t n_tiles, n_chunks, W;
+    int G;
+};
+
+Geometry geometry(const fil_ctx *c, int grid_max) {
+    Geometry g;
+    g.n_tiles = (c->lay.S + kRpyTile - 1) / kRpyTile;
+    g.n_chunks = (c->lay.S + kRpyChunk - 1) / kRpyChunk;
+    g.W = g.n_tiles * g.n_chunks;
+    g.G = (int)std::min<int64_t>(grid_max, g.W);
+    return g;
+}
+
+}  // namespace
+
+cudaError_t rpy_setup(fil_ctx *c) {
+    int occ32 = 0, occ64 = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, rpy_pair32_kernel,
+                                                                  kRpyThreads, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, rpy_pair64_kernel, kRpyThreads, 0);
+    if (e != cudaSuccess) return e;
+    c->rpy_grid32 = std::max(1, occ32) * c->num_sms;
+    c->rpy_grid64 = std::max(1, occ64) * c->num_sms;
+    c->rpy_tiles = (c->lay.S + kRpyTile - 1) / kRpyTile;
+    const int64_t n_chunks = (c->lay.S + kRpyChunk - 1) / kRpyChunk;
+    c->Spad = std::max(c->rpy_tiles * kRpyTile, n_chunks * kRpyChunk);
+    return cudaSuccess;
+}
+
+size_t rpy_partial_bytes(const fil_ctx *c) {
+    // slots b + tile for b < G and tile < n_tiles; 12 floats = 6 doubles per target
+    const int64_t G = std::max(c->rpy_grid32, c->rpy_grid64);
+    return (size_t)(G + c->rpy_tiles) * kRpyTile * 12 * sizeof(float);
+}
+
+cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW) {
+    const int64_t S = c->lay.S;
+    const double scale = 1.0 / (8.0 * kPi * c->eta);
+    const int pb = 256;
+    const unsigned pgrid = (unsigned)((c->Spad + pb - 1) / pb);
+    const unsigned rgrid = (unsigned)((S + pb - 1) / pb);
+    const bool timed = c->prof_on && c->prof_n < kProfMax;
+    if (c->prec == FIL_MIXED) {
+        Geometry g = geometry(c, c->rpy_grid32);
+        pack32_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, c->src32);
+        if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+        rpy_pair32_kernel<<<g.G, kRpyThreads, 0, c->stream>>>(
+            c->src32, g.n_chunks, g.W, g.G, make_const<float, RpyConst32>(c->a),
+            (float *)c->partials);
+        if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
+        rpy_reduce32_kernel<<<rgrid, pb, 0, c->stream>>>((const float *)c->partials, S,
+                                                         g.n_chunks, g.W, g.G, scale, VW);
+    } else {
+        Geometry g = geometry(c, c->rpy_grid64);
+        pack64_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, c->src64);
+        if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+        rpy_pair64_kernel<<<g.G, kRpyThreads, 0, c->stream>>>(
+            c->src64, g.n_chunks, g.W, g.G, make_const<double, RpyConst64>(c->a),
+            (double *)c->partials);
+        if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
+        rpy_reduce64_kernel<<<rgrid, pb, 0, c->stream>>>((const double *)c->partials, S,
+                                                         g.n_chunks, g.W, g.G, scale, VW);
+    }
+    if (timed) c->prof_n += 1;
+    c->n_applies += 1;
+    c->n_launches += 3;
+    return cudaGetLastError();
+}
+
+}  // namespace fil

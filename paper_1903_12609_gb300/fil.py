@@ -1,0 +1,241 @@
+"""Thin Python binding of the C ABI in include/fil.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: arrays are passed through as pointers. Arrays may be
+numpy arrays (host memory) or torch CUDA tensors (device memory); both must be
+C-contiguous float64 with the documented shapes. There is no fallback: if the
+shared library is missing or does not load, importing the binding raises.
+
+``Filaments`` is a small convenience wrapper that owns a context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfil.so")
+
+FIL_OK, FIL_EINVAL, FIL_ENOMEM, FIL_ECUDA, FIL_ENOCONV, FIL_ENAN, FIL_ESTALL, FIL_ESTATE = range(8)
+FIL_FP64, FIL_MIXED = 0, 1
+STATUS_NAMES = {0: "FIL_OK", 1: "FIL_EINVAL", 2: "FIL_ENOMEM", 3: "FIL_ECUDA", 4: "FIL_ENOCONV",
+                5: "FIL_ENAN", 6: "FIL_ESTALL", 7: "FIL_ESTATE"}
+
+EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set_state",
+            "fil_get_state", "fil_init_straight", "fil_set_external", "fil_mobility_apply",
+            "fil_residual", "fil_broyden_begin", "fil_broyden_step", "fil_get_iterate",
+            "fil_j0_solve", "fil_broyden_commit", "fil_step", "fil_set_dt", "fil_counters",
+            "fil_profile", "fil_profile_read"]
+
+
+class FilError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), message))
+        self.status = status
+
+
+class fil_params(ctypes.Structure):
+    _fields_ = [("n_fil", ctypes.c_int32), ("seg_per_fil", ctypes.POINTER(ctypes.c_int32)),
+                ("a", ctypes.c_double), ("eta", ctypes.c_double), ("dL", ctypes.c_double),
+                ("KB", ctypes.c_double), ("KT", ctypes.c_double), ("gamma0", ctypes.c_double),
+                ("kappa_mu", ctypes.c_double), ("kappa_nu", ctypes.c_double),
+                ("dt", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError("libfil.so not built at %s (run __graft_entry__.build())" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    I64 = ctypes.POINTER(ctypes.c_int64)
+    I32 = ctypes.POINTER(ctypes.c_int32)
+    sig = {
+        "fil_create": [ctypes.POINTER(fil_params), ctypes.POINTER(P)],
+        "fil_destroy": [P],
+        "fil_last_error": [P],
+        "fil_sizes": [P, I64, I64, I64],
+        "fil_set_state": [P, P, P, P, P, P],
+        "fil_get_state": [P, P, P, P, P, P],
+        "fil_init_straight": [P, P, P, P, P],
+        "fil_set_external": [P, P, P, P],
+        "fil_mobility_apply": [P, P, P, P],
+        "fil_residual": [P, P, P, D],
+        "fil_broyden_begin": [P, D],
+        "fil_broyden_step": [P, I32, D],
+        "fil_get_iterate": [P, P, P],
+        "fil_j0_solve": [P, P, P],
+        "fil_broyden_commit": [P],
+        "fil_step": [P, I32],
+        "fil_set_dt": [P, ctypes.c_double],
+        "fil_counters": [P, I64, I64, I64],
+        "fil_profile": [P, ctypes.c_int32],
+        "fil_profile_read": [P, I64, D],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = None if name == "fil_destroy" else (
+            ctypes.c_char_p if name == "fil_last_error" else ctypes.c_int)
+    return lib
+
+
+_lib = load_library()
+
+
+def _ptr(a):
+    """Device or host address of a float64 C-contiguous array (or None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):                       # torch tensor
+        if a.dtype.__repr__() != "torch.float64" or not a.is_contiguous():
+            raise TypeError("torch tensors must be contiguous float64")
+        return ctypes.c_void_p(a.data_ptr())
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise TypeError("numpy arrays must be C-contiguous float64")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(ctx, status):
+    if status != FIL_OK:
+        msg = _lib.fil_last_error(ctx) if ctx else b""
+        raise FilError(status, (msg or b"").decode())
+
+
+# ---- functions with the names of the C entry points ------------------------
+
+def fil_create(seg_per_fil, a=1.0, eta=1.0, dL=2.2, KB=1.0, KT=1.0, gamma0=0.0, kappa_mu=0.0,
+               kappa_nu=0.0, dt=0.01, tol=1e-8, max_iter=50, precision=FIL_FP64, stream=None):
+    segs = np.ascontiguousarray(seg_per_fil, dtype=np.int32)
+    p = fil_params(int(segs.size), segs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), a, eta, dL,
+                   KB, KT, gamma0, kappa_mu, kappa_nu, dt, tol, int(max_iter), int(precision),
+                   ctypes.c_void_p(stream) if stream else None)
+    ctx = ctypes.c_void_p()
+    _check(None, _lib.fil_create(ctypes.byref(p), ctypes.byref(ctx)))
+    return ctx
+
+
+def fil_destroy(ctx):
+    _lib.fil_destroy(ctx)
+
+
+def fil_last_error(ctx):
+    return (_lib.fil_last_error(ctx) or b"").decode()
+
+
+def fil_sizes(ctx):
+    s, x, l = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, _lib.fil_sizes(ctx, ctypes.byref(s), ctypes.byref(x), ctypes.byref(l)))
+    return s.value, x.value, l.value
+
+
+def fil_set_state(ctx, Y, q, Yprev=None, u=None, Lambda=None):
+    _check(ctx, _lib.fil_set_state(ctx, _ptr(Y), _ptr(q), _ptr(Yprev), _ptr(u), _ptr(Lambda)))
+
+
+def fil_get_state(ctx, Y=None, q=None, Yprev=None, u=None, Lambda=None):
+    _check(ctx, _lib.fil_get_state(ctx, _ptr(Y), _ptr(q), _ptr(Yprev), _ptr(u), _ptr(Lambda)))
+
+
+def fil_init_straight(ctx, base, t, mu, xi=None):
+    _check(ctx, _lib.fil_init_straight(ctx, _ptr(base), _ptr(t), _ptr(mu), _ptr(xi)))
+
+
+def fil_set_external(ctx, Fext=None, Text=None, follower=None):
+    _check(ctx, _lib.fil_set_external(ctx, _ptr(Fext), _ptr(Text), _ptr(follower)))
+
+
+def fil_mobility_apply(ctx, Y, FT, VW):
+    _check(ctx, _lib.fil_mobility_apply(ctx, _ptr(Y), _ptr(FT), _ptr(VW)))
+
+
+def fil_residual(ctx, X, f):
+    finf = ctypes.c_double()
+    _check(ctx, _lib.fil_residual(ctx, _ptr(X), _ptr(f), ctypes.byref(finf)))
+    return finf.value
+
+
+def fil_broyden_begin(ctx):
+    finf = ctypes.c_double()
+    _check(ctx, _lib.fil_broyden_begin(ctx, ctypes.byref(finf)))
+    return finf.value
+
+
+def fil_broyden_step(ctx):
+    conv, finf = ctypes.c_int32(), ctypes.c_double()
+    _check(ctx, _lib.fil_broyden_step(ctx, ctypes.byref(conv), ctypes.byref(finf)))
+    return bool(conv.value), finf.value
+
+
+def fil_get_iterate(ctx, X=None, f=None):
+    _check(ctx, _lib.fil_get_iterate(ctx, _ptr(X), _ptr(f)))
+
+
+def fil_j0_solve(ctx, b, x):
+    _check(ctx, _lib.fil_j0_solve(ctx, _ptr(b), _ptr(x)))
+
+
+def fil_broyden_commit(ctx):
+    _check(ctx, _lib.fil_broyden_commit(ctx))
+
+
+def fil_step(ctx):
+    it = ctypes.c_int32()
+    _check(ctx, _lib.fil_step(ctx, ctypes.byref(it)))
+    return it.value
+
+
+def fil_set_dt(ctx, dt):
+    _check(ctx, _lib.fil_set_dt(ctx, float(dt)))
+
+
+def fil_counters(ctx):
+    a, b, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, _lib.fil_counters(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(k)))
+    return a.value, b.value, k.value
+
+
+def fil_profile(ctx, enable):
+    _check(ctx, _lib.fil_profile(ctx, int(bool(enable))))
+
+
+def fil_profile_read(ctx):
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    _check(ctx, _lib.fil_profile_read(ctx, ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
+class Filaments:
+    """Owns one context; methods forward to the fil_* functions above."""
+
+    def __init__(self, seg_per_fil, **params):
+        self.ctx = fil_create(seg_per_fil, **params)
+        self.S, self.nX, self.nlam = fil_sizes(self.ctx)
+        self.M = len(seg_per_fil)
+
+    def close(self):
+        if self.ctx is not None:
+            fil_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __getattr__(self, name):
+        fn = globals().get("fil_" + name)
+        if fn is None:
+            raise AttributeError(name)
+        return lambda *a, **k: fn(self.ctx, *a, **k)

@@ -1,0 +1,198 @@
+"""GPU parity of the residual, J0 solve, Broyden iterates and timesteps
+(fil_residual, fil_j0_solve, fil_broyden_*, fil_step, fil_init_straight)
+against the oracle, plus the error statuses.
+
+FP64 path tolerances: residual entries within 1e-12 of the oracle relative to
+the largest position magnitude (the rows subtract O(|Y|) terms); J0 solves and
+Broyden iterates within 1e-10 relative (they go through a pivoted banded LU on
+the GPU and a dense LU in the oracle, whose rounding differs by cond(J0) eps).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import filament as fo  # noqa: E402
+from paper_1903_12609_gb300.inputs import (random_frames, single_filament,  # noqa: E402
+                                           workload_params)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fil():
+    assert torch.cuda.is_available()
+    from paper_1903_12609_gb300 import fil as _fil
+    return _fil
+
+
+def _system(segs, seed, history=False, KB=2.0, KT=1.5, dt=0.1, tol=1e-10, twist=0.05,
+            follower=True, **extra):
+    rng = np.random.default_rng(seed)
+    lay = fo.Layout(segs)
+    p = fo.Params(a=1.0, eta=1.0, dL=2.2, KB=KB, KT=KT, dt=dt, tol=tol, max_iter=60, **extra)
+    M = len(segs)
+    base = rng.uniform(0, 6.0 * M ** (1 / 3) * 3, size=(M, 3))
+    t, mu = random_frames(rng, M)
+    xi = twist * rng.standard_normal((lay.S, 3))
+    st = fo.initial_state(lay, p, base, t, mu, xi)
+    if history:
+        st.Yprev = st.Y + 0.01 * rng.standard_normal(st.Y.shape)
+        st.u = 0.02 * rng.standard_normal((lay.S, 3))
+    st.lam = 0.1 * rng.standard_normal((lay.n_lam, 3))
+    ext = fo.External(Fext=np.tile([0.0, 0.0, -2.2], (lay.S, 1)),
+                      Text=0.05 * rng.standard_normal((lay.S, 3)),
+                      follower=(rng.uniform(0, 1, M) if follower else None))
+    return lay, p, st, ext, (base, t, mu, xi)
+
+
+def _gpu(fil, lay, p, st, ext, prec=0):
+    m = fil.Filaments(lay.N, a=p.a, eta=p.eta, dL=p.dL, KB=p.KB, KT=p.KT, gamma0=p.gamma0,
+                      kappa_mu=p.kappa_mu, kappa_nu=p.kappa_nu, dt=p.dt, tol=p.tol,
+                      max_iter=p.max_iter, precision=prec)
+    m.set_state(st.Y, st.q, st.Yprev, st.u, st.lam if lay.n_lam else None)
+    m.set_external(ext.Fext, ext.Text, ext.follower)
+    return m
+
+
+SEGS = [[20], [1, 5, 33], [32] * 6, [40, 65, 2, 1]]
+
+
+@pytest.mark.parametrize("segs", SEGS)
+@pytest.mark.parametrize("history", [False, True])
+def test_residual_parity(fil, segs, history):
+    lay, p, st, ext, _ = _system(segs, 10 + len(segs), history=history, gamma0=0.1,
+                                 kappa_mu=-0.05, kappa_nu=0.2)
+    rng = np.random.default_rng(1)
+    Y1 = np.array([st.Y[lay.off_seg[i]] for i in range(lay.M)]) + 0.01
+    X = lay.join_X(Y1, 0.05 * rng.standard_normal((lay.S, 3)),
+                   rng.standard_normal((lay.n_lam, 3)))
+    ref = fo.residual(lay, p, st, ext, X, nthreads=4)
+    with _gpu(fil, lay, p, st, ext) as m:
+        f = np.zeros(6 * lay.S)
+        finf = m.residual(X, f)
+    scale = max(1.0, np.abs(st.Y).max())
+    np.testing.assert_allclose(f, ref, rtol=0, atol=1e-12 * scale)
+    assert abs(finf - np.abs(f).max()) == 0.0
+
+
+def test_residual_mixed_close_to_fp64(fil):
+    lay, p, st, ext, _ = _system([32] * 6, 3, history=True)
+    X = fo.initial_guess(lay, st)
+    ref = fo.residual(lay, p, st, ext, X)
+    with _gpu(fil, lay, p, st, ext, prec=1) as m:
+        f = np.zeros(6 * lay.S)
+        m.residual(X, f)
+    # velocity errors of a few 1e-7 relative, times (2/3) dt
+    np.testing.assert_allclose(f, ref, rtol=0, atol=1e-6 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("segs", SEGS)
+def test_init_straight_matches_oracle(fil, segs):
+    lay, p, st, ext, (base, t, mu, xi) = _system(segs, 20)
+    with _gpu(fil, lay, p, st, ext) as m:
+        m.init_straight(base, t, mu, xi)
+        Y = np.zeros((lay.S, 3))
+        q = np.zeros((lay.S, 4))
+        m.get_state(Y, q, None, None, None)
+    np.testing.assert_allclose(Y, st.Y, rtol=0, atol=1e-12 * max(1, np.abs(st.Y).max()))
+    np.testing.assert_allclose(q, st.q, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("segs", SEGS)
+@pytest.mark.parametrize("history", [False, True])
+def test_j0_solve_matches_dense_oracle(fil, segs, history):
+    lay, p, st, ext, _ = _system(segs, 30, history=history, twist=0.2)
+    with _gpu(fil, lay, p, st, ext) as m:
+        m.broyden_begin()
+        X0 = np.zeros(6 * lay.S)
+        m.get_iterate(X0, None)
+        np.testing.assert_allclose(X0, fo.initial_guess(lay, st), rtol=0, atol=1e-14 * 100)
+        b = np.random.default_rng(2).standard_normal(6 * lay.S)
+        x = np.zeros_like(b)
+        m.j0_solve(b, x)
+    ref = fo.J0Solver(lay, fo.jacobian0(lay, p, st, X0)).solve(b)
+    np.testing.assert_allclose(x, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("segs", [[20], [32] * 4, [1, 7, 33]])
+def test_broyden_iterates_match_oracle(fil, segs):
+    lay, p, st, ext, _ = _system(segs, 40, history=True, tol=1e-13)
+    br = fo.begin_step(lay, p, st, ext)
+    with _gpu(fil, lay, p, st, ext) as m:
+        f0 = m.broyden_begin()
+        assert abs(f0 - np.abs(br.f).max()) <= 1e-12 * max(1, np.abs(st.Y).max())
+        X = np.zeros(6 * lay.S)
+        f = np.zeros(6 * lay.S)
+        for k in range(6):
+            conv, finf = m.broyden_step()
+            br.iterate()
+            m.get_iterate(X, f)
+            sc = np.abs(br.X).max()
+            np.testing.assert_allclose(X, br.X, rtol=0, atol=1e-10 * sc)
+            np.testing.assert_allclose(f, br.f, rtol=0, atol=1e-10 * max(1, np.abs(br.f).max()))
+            if conv:
+                break
+
+
+def test_c0_trajectory_parity(fil):
+    """Single tilted filament, N = 20, B = 1000, dt = T/100, tol 1e-8: 25 steps."""
+    wl = workload_params(1, 20, B=1000.0, dt_over_T=0.01, tol=1e-8)
+    base, t, mu, xi = single_filament(20, seed=0)
+    lay = fo.Layout([20])
+    p = fo.Params(a=wl.a, eta=wl.eta, dL=wl.dL, KB=wl.KB, KT=wl.KT, dt=wl.dt, tol=wl.tol,
+                  max_iter=50)
+    st = fo.initial_state(lay, p, base, t, mu, xi)
+    ext = fo.External(Fext=np.tile([0.0, 0.0, -wl.W * wl.dL], (20, 1)))
+    with _gpu(fil, lay, p, st, ext) as m:
+        m.init_straight(base, t, mu, xi)
+        Y = np.zeros((20, 3))
+        q = np.zeros((20, 4))
+        for j in range(25):
+            st, it_ref = fo.step(lay, p, st, ext)
+            it = m.step()
+            m.get_state(Y, q, None, None, None)
+            assert abs(it - it_ref) <= 1
+            np.testing.assert_allclose(Y, st.Y, rtol=0, atol=1e-8)
+            np.testing.assert_allclose(np.linalg.norm(q, axis=1), 1.0, atol=1e-14)
+
+
+def test_mixed_step_converges_close_to_fp64(fil):
+    lay, p, st, ext, _ = _system([32] * 8, 50, tol=1e-6, dt=0.2)
+    ref = st
+    for _ in range(3):
+        ref, _ = fo.step(lay, p, ref, ext)
+    with _gpu(fil, lay, p, st, ext, prec=1) as m:
+        for _ in range(3):
+            m.step()
+        Y = np.zeros((lay.S, 3))
+        m.get_state(Y, None, None, None, None)
+    np.testing.assert_allclose(Y, ref.Y, rtol=0, atol=1e-4)
+
+
+def test_error_statuses(fil):
+    lay, p, st, ext, _ = _system([10, 10], 60)
+    with _gpu(fil, lay, p, st, ext) as m:
+        with pytest.raises(fil.FilError) as e:
+            m.broyden_step()
+        assert e.value.status == fil.FIL_ESTATE
+        with pytest.raises(fil.FilError) as e:
+            m.broyden_commit()
+        assert e.value.status == fil.FIL_ESTATE
+        bad = st.Y.copy()
+        bad[3, 1] = np.nan
+        m.set_state(bad, st.q)
+        with pytest.raises(fil.FilError) as e:
+            m.step()
+        assert e.value.status == fil.FIL_ENAN
+    # max_iter = 1 on a stiff step cannot converge to 1e-14
+    p1 = fo.Params(**{**p.__dict__, "max_iter": 1, "tol": 1e-14, "dt": 1.0})
+    with _gpu(fil, lay, p1, st, ext) as m:
+        Y0 = np.zeros((lay.S, 3))
+        m.get_state(Y0, None, None, None, None)
+        with pytest.raises(fil.FilError) as e:
+            m.step()
+        assert e.value.status == fil.FIL_ENOCONV
+        Y1 = np.zeros((lay.S, 3))
+        m.get_state(Y1, None, None, None, None)
+        np.testing.assert_array_equal(Y0, Y1)       # state untouched on failure

@@ -1,0 +1,127 @@
+"""GPU parity of the RPY mobility apply (fil_mobility_apply) against the oracle.
+
+FP64 path: normwise relative error <= 1e-12 per call.
+Mixed path (FP32 pair sums): every component within
+    |v_gpu - v_oracle| <= C_MIXED * 2^-24 * B
+where B is the oracle's sum over pairs of |parts of M_nm| (|F|, |T|) for that
+component. C_MIXED = 4 * 32 + 16: each group of 32 sources is accumulated by
+4 FP32 FMAs per component and pair (<= 128 roundings of the running sum), each
+pair term carries <= ~12 roundings (hi/lo difference, rsqrt, products) and the
+inputs are rounded to FP32 once; the compensated fold of the group sums and
+the FP64 reduce add O(u^2).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import rpy  # noqa: E402
+from paper_1903_12609_gb300.inputs import mobility_inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+C_MIXED = 4 * 32 + 16
+
+
+@pytest.fixture(scope="module")
+def fil():
+    assert torch.cuda.is_available()
+    from paper_1903_12609_gb300 import fil as _fil
+    return _fil
+
+
+def _gpu_apply(fil, segs, Y, FT, prec, host=False, a=1.0, eta=1.0):
+    with fil.Filaments(segs, a=a, eta=eta, precision=prec) as m:
+        if host:
+            VW = np.zeros((Y.shape[0], 6))
+            m.mobility_apply(np.ascontiguousarray(Y), np.ascontiguousarray(FT), VW)
+            return VW
+        Yd = torch.from_numpy(np.ascontiguousarray(Y)).cuda()
+        FTd = torch.from_numpy(np.ascontiguousarray(FT)).cuda()
+        VW = torch.empty((Y.shape[0], 6), dtype=torch.float64, device="cuda")
+        m.mobility_apply(Yd, FTd, VW)
+        torch.cuda.synchronize()
+        return VW.cpu().numpy()
+
+
+def _check_mixed(got, ref, ref_abs):
+    bound = C_MIXED * U32 * ref_abs
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), float((err / np.maximum(ref_abs, 1e-300)).max() / U32)
+    # typical error is a few ulps of B
+    assert np.median(err / np.maximum(ref_abs, 1e-300)) < 8 * U32
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_c1_workload_parity(fil, prec):
+    """100 random-walk filaments x 32 segments, 5% volume fraction, N(0,1) loads."""
+    Y, FT = mobility_inputs(100, 32, seed=0)
+    ref, ref_abs = rpy.apply(Y, FT, with_abs=True, nthreads=8)
+    got = _gpu_apply(fil, [32] * 100, Y, FT, prec)
+    if prec == fil.FIL_FP64:
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+    else:
+        _check_mixed(got, ref, ref_abs)
+
+
+@pytest.mark.parametrize("segs", [[1], [7], [255], [1, 256], [3, 254, 2], [100] * 5 + [13],
+                                  [64] * 17 + [5]])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ragged_sizes(fil, segs, prec):
+    S = sum(segs)
+    rng = np.random.default_rng(S)
+    Y = rng.uniform(0, max(4.0, S ** (1 / 3) * 3.0), size=(S, 3))
+    FT = rng.standard_normal((S, 6))
+    ref, ref_abs = rpy.apply(Y, FT, with_abs=True, nthreads=8)
+    got = _gpu_apply(fil, segs, Y, FT, prec)
+    if prec == fil.FIL_FP64:
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+    else:
+        _check_mixed(got, ref, ref_abs)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_overlaps_and_coincident_segments(fil, prec):
+    """Dense cluster: most pairs overlap (r < 2a); two pairs coincide exactly."""
+    rng = np.random.default_rng(11)
+    Y = rng.uniform(0, 3.0, size=(300, 3))
+    Y[5] = Y[4]
+    Y[77] = Y[200]
+    FT = rng.standard_normal((300, 6))
+    a, eta = 1.3, 0.8
+    ref, ref_abs = rpy.apply(Y, FT, a, eta, with_abs=True)
+    got = _gpu_apply(fil, [300], Y, FT, prec, a=a, eta=eta)
+    if prec == fil.FIL_FP64:
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+    else:
+        _check_mixed(got, ref, ref_abs)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_sampled_rows(fil, prec):
+    """32 000 segments (the full-suspension size): sampled targets vs the oracle."""
+    Y, FT = mobility_inputs(1000, 32, volume_fraction=0.02, seed=3)
+    got = _gpu_apply(fil, [32] * 1000, Y, FT, prec)
+    rows = np.concatenate([[0, 1, 255, 256, 31999], np.random.default_rng(4).integers(0, 32000, 59)])
+    ref, ref_abs = rpy.apply_rows(Y, FT, rows, with_abs=True, nthreads=8)
+    if prec == fil.FIL_FP64:
+        np.testing.assert_allclose(got[rows], ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    else:
+        _check_mixed(got[rows], ref, ref_abs)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_deterministic_and_host_pointers(fil, prec):
+    Y, FT = mobility_inputs(20, 32, seed=5)
+    a = _gpu_apply(fil, [32] * 20, Y, FT, prec)
+    b = _gpu_apply(fil, [32] * 20, Y, FT, prec)
+    c = _gpu_apply(fil, [32] * 20, Y, FT, prec, host=True)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a, c)
+
+
+def test_zero_load_gives_zero(fil):
+    Y, FT = mobility_inputs(4, 32, seed=6)
+    got = _gpu_apply(fil, [32] * 4, Y, np.zeros_like(FT), 1)
+    assert np.all(got == 0.0)

@@ -1,0 +1,55 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every entry point
+that include/fil.h declares, and rejects invalid parameters before touching
+the GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fil.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fil_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1903_12609_gb300 import build
+    build.build()
+    from paper_1903_12609_gb300 import fil
+    return fil
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib._lib, n), n
+    assert sorted(lib.EXPORTED) == names
+
+
+@pytest.mark.parametrize("bad", [dict(a=0.0), dict(eta=-1.0), dict(dL=0.0), dict(dt=0.0),
+                                 dict(tol=0.0), dict(max_iter=0), dict(precision=7),
+                                 dict(KB=float("nan"))])
+def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
+    with pytest.raises(lib.FilError) as e:
+        lib.fil_create([4, 4], **bad)
+    assert e.value.status == lib.FIL_EINVAL
+
+
+def test_invalid_layout_is_rejected(lib):
+    for segs in ([], [3, 0], [-1]):
+        with pytest.raises(lib.FilError) as e:
+            lib.fil_create(segs)
+        assert e.value.status == lib.FIL_EINVAL
+
+
+def test_oracle_library_builds():
+    from oracle import build
+    build.build()
+    assert os.path.exists(build.lib_path("liboracle_rpy.so"))
+    ctypes.CDLL(build.lib_path("liboracle_rpy.so"))

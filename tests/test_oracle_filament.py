@@ -290,3 +290,53 @@ def test_quaternions_stay_unit_over_steps():
             s, e = lay.off_seg[i], lay.off_seg[i + 1]
             g = st.Y[s + 1:e] - st.Y[s:e - 1] - 0.5 * p.dL * (t[s:e - 1] + t[s + 1:e])
             np.testing.assert_allclose(g, 0.0, atol=1e-13)
+
+
+@pytest.mark.parametrize("history", [False, True])
+def test_general_J0_with_drag_mobility_is_the_printed_J0(history):
+    """The J0 built from a per-filament mobility matrix reduces to App. B.2's
+    printed blocks when that matrix is the diagonal self mobility."""
+    rng = np.random.default_rng(11)
+    lay = fo.Layout([6, 1, 3])
+    p = _params(KB=1.5, KT=0.7, gamma0=0.1, kappa_mu=0.2, kappa_nu=-0.1)
+    st = _random_filament_state(rng, lay, p, twist=0.2)
+    if history:
+        st.Yprev = st.Y + 0.01
+        st.u = 0.01 * rng.standard_normal((lay.S, 3))
+    Y1 = np.array([st.Y[lay.off_seg[i]] for i in range(lay.M)])
+    X = lay.join_X(Y1, 0.1 * rng.standard_normal((lay.S, 3)), rng.standard_normal((lay.n_lam, 3)))
+    for a, b in zip(fo.jacobian0(lay, p, st, X), fo.jacobian0_general(lay, p, st, X, "drag")):
+        np.testing.assert_allclose(b, a, rtol=0, atol=1e-13 * np.abs(a).max())
+
+
+def test_filament_rpy_J0_equals_fd_jacobian_when_straight_and_unloaded():
+    """With the filament's own RPY blocks in f_0, J0 is the exact Jacobian of
+    that f_0 at a straight, untwisted, tension-free state (u = 0, Lambda = 0):
+    there the derivative approximations are exact and dM/dY multiplies zero
+    internal load."""
+    rng = np.random.default_rng(12)
+    lay = fo.Layout([5])
+    p = _params(KB=1.5, KT=0.7)
+    from paper_1903_12609_gb300.inputs import random_frames
+    t, mu = random_frames(rng, 1)
+    st = fo.initial_state(lay, p, np.zeros((1, 3)), t, mu)
+    X = lay.join_X(st.Y[:1], np.zeros((lay.S, 3)), np.zeros((lay.n_lam, 3)))
+    J0 = fo.jacobian0_general(lay, p, st, X, "rpy")[0]
+    Jfd = _fd_jacobian(lambda Xv: fo.residual(lay, p, st, None, Xv), X)
+    np.testing.assert_allclose(J0, Jfd, rtol=0, atol=1e-8 * np.abs(Jfd).max())
+
+
+def test_filament_rpy_J0_cuts_broyden_iterations():
+    """Several straight sedimenting filaments: the filament-RPY J0 converges in
+    fewer Broyden iterations than the drag-only J0 and to the same solution."""
+    from paper_1903_12609_gb300.inputs import cloud_frames, workload_params
+    wl = workload_params(6, 16, B=1000.0, dt_over_T=0.005, tol=1e-10)
+    base, t, mu, _ = cloud_frames(6, 16, volume_fraction=0.02, seed=3)
+    lay = fo.Layout([16] * 6)
+    p = fo.Params(a=1, eta=1, dL=2.2, KB=wl.KB, KT=wl.KT, dt=wl.dt, tol=wl.tol, max_iter=200)
+    st = fo.initial_state(lay, p, base, t, mu)
+    ext = fo.External(Fext=np.tile([0, 0, -2.2], (lay.S, 1)))
+    s_drag, it_drag = fo.step(lay, p, st, ext, j0_model="drag")
+    s_rpy, it_rpy = fo.step(lay, p, st, ext, j0_model="rpy")
+    assert it_rpy < it_drag
+    np.testing.assert_allclose(s_rpy.Y, s_drag.Y, rtol=0, atol=1e-8)
