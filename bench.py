@@ -180,6 +180,8 @@ def main():
                     help="timed steps of the plain FP64 form for comparison (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--j0", default="filament_rpy", choices=["filament_rpy", "drag"],
+                    help="approximate Jacobian: filament RPY blocks (default) or App. B.2 drag")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -211,8 +213,9 @@ def main():
     wl, base, t, mu, Fext, follower = workload(n_fil, n_seg, seed=rank)
     stream = torch.cuda.Stream()
     prec = fil.FIL_MIXED if args.precision == "mixed" else fil.FIL_FP64
+    j0 = fil.FIL_J0_FILAMENT_RPY if args.j0 == "filament_rpy" else fil.FIL_J0_DRAG
     params = dict(a=wl.a, eta=wl.eta, dL=wl.dL, KB=wl.KB, KT=wl.KT, dt=wl.dt, tol=wl.tol,
-                  max_iter=wl.max_iter)
+                  max_iter=wl.max_iter, j0_model=j0)
     m = fil.Filaments(wl.seg_per_fil, precision=prec, stream=stream.cuda_stream, **params)
     m.init_straight(base, t, mu, None)
     m.set_external(Fext, None, follower)
@@ -327,8 +330,8 @@ def main():
             "workload": "suspension 1000 filaments x 32 segments (32000), 2% volume fraction, "
                         "half sedimenting (B=1000) half tip-follower (fL^2/KB=100), BDF2 "
                         "dt=T/200, Broyden tol 1e-4",
-            "segments": S, "precision": args.precision, "parallelism": "replicas" if world > 1
-            else "single",
+            "segments": S, "precision": args.precision, "j0": args.j0,
+            "parallelism": "replicas" if world > 1 else "single",
             "l2": "flushed between timed steps (256 MiB write)"},
         "timesteps_per_s": args.steps / (max_ms * 1e-3),
         "broyden_iters_per_step": float(np.mean(iters)),

@@ -60,6 +60,17 @@ typedef enum {
                          accumulation; everything else FP64                    */
 } fil_precision;
 
+typedef enum {
+    FIL_J0_DRAG = 0,          /* J0 of App. B.2 as printed: diagonal (self) mobility
+                                 in f_0; banded O(N) factorisation per filament     */
+    FIL_J0_FILAMENT_RPY = 1   /* f_0 keeps every RPY block between segments of the
+                                 same filament (inter-filament coupling and dM/dY
+                                 dropped); dense LU per filament. Reduces to
+                                 FIL_J0_DRAG when those blocks are cut to the self
+                                 term; far fewer Broyden iterations in dense
+                                 suspensions                                         */
+} fil_j0_model;
+
 typedef struct {
     int32_t n_fil;                /* number of filaments M >= 1                    */
     const int32_t *seg_per_fil;   /* HOST array of M segment counts N_i >= 1; copied */
@@ -72,8 +83,11 @@ typedef struct {
     double tol;                   /* Broyden stops when ||f||_inf <= tol * a       */
     int32_t max_iter;             /* Broyden iteration cap and history depth >= 1  */
     int32_t precision;            /* fil_precision                                 */
+    int32_t j0_model;             /* fil_j0_model                                  */
     void *stream;                 /* cudaStream_t, or NULL for the legacy stream   */
 } fil_params;
+/* Limits: S = sum N_i <= 2^30 and N_i <= 4266 (a filament's right-hand side is
+ * kept in shared memory by the J0 solves). */
 
 /* Create a context: validates p, copies the layout, allocates every device
  * buffer the other calls use (state, workspace, Broyden history of depth

@@ -124,8 +124,16 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     StatusBlock *sb = ar.take<StatusBlock>(1);
     c->d_finf = sb ? &sb->finf_bits : nullptr;
     c->d_flags = sb ? sb->flags : nullptr;
-    c->band = ar.take<double>((size_t)nband * kBandW);
-    c->piv = ar.take<int>(nband);
+    if (c->j0_model == FIL_J0_DRAG) {
+        c->band = ar.take<double>((size_t)nband * kBandW);
+        c->jdense = nullptr;
+        c->jofs = nullptr;
+    } else {
+        c->band = nullptr;
+        c->jdense = ar.take<double>((size_t)c->jdense_len);
+        c->jofs = ar.take<int64_t>(M + 1);
+    }
+    c->piv = ar.take<int>(6 * S);
     c->stage_a = ar.take<double>(nX);
     c->stage_b = ar.take<double>(nX);
     c->stage_c = ar.take<double>(nX);
@@ -155,6 +163,10 @@ cudaError_t eval_residual(fil_ctx *c, const double *X, double *f, int with_force
     return residual_rows(c, X, f);
 }
 
+cudaError_t j0_apply(fil_ctx *c, const double *b, double *x) {
+    return c->j0_model == FIL_J0_DRAG ? j0_solve(c, b, x) : j0_dense_solve(c, b, x);
+}
+
 }  // namespace
 
 extern "C" {
@@ -166,6 +178,7 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
     if (!(p->a > 0) || !(p->eta > 0) || !(p->dL > 0) || !(p->dt > 0) || !(p->tol > 0) ||
         !(p->KB >= 0) || !(p->KT >= 0) || p->max_iter < 1 ||
         (p->precision != FIL_FP64 && p->precision != FIL_MIXED) ||
+        (p->j0_model != FIL_J0_DRAG && p->j0_model != FIL_J0_FILAMENT_RPY) ||
         !std::isfinite(p->gamma0) || !std::isfinite(p->kappa_mu) || !std::isfinite(p->kappa_nu))
         return FIL_EINVAL;
     int64_t S = 0;
@@ -193,6 +206,11 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
     c->a = p->a; c->eta = p->eta; c->dL = p->dL; c->KB = p->KB; c->KT = p->KT;
     c->g0 = p->gamma0; c->kmu = p->kappa_mu; c->knu = p->kappa_nu;
     c->dt = p->dt; c->tol = p->tol; c->max_iter = p->max_iter; c->prec = p->precision;
+    c->j0_model = p->j0_model;
+    std::vector<int64_t> jofs(p->n_fil + 1, 0);
+    for (int i = 0; i < p->n_fil; ++i)
+        jofs[i + 1] = jofs[i] + (int64_t)36 * c->N_host[i] * c->N_host[i];
+    c->jdense_len = jofs[p->n_fil];
     c->stream = (cudaStream_t)p->stream;
     c->have_prev = 0; c->steps = 0; c->k = 0; c->in_step = 0;
     c->has_Fext = c->has_Text = c->has_follower = 0;
@@ -247,6 +265,9 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->q, q0.data(), sizeof(double) * 4 * S, cudaMemcpyHostToDevice,
                             c->stream);
+    if (e == cudaSuccess && c->jofs)
+        e = cudaMemcpyAsync(c->jofs, jofs.data(), sizeof(int64_t) * (p->n_fil + 1),
+                            cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bail(FIL_ECUDA, "initial upload", e);
     *out = c;
@@ -406,7 +427,10 @@ fil_status fil_broyden_begin(fil_ctx *c, double *finf) {
     CK(cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), c->stream));
     CK(extrapolate_guess(c, c->Xk));
     CK(eval_residual(c, c->Xk, c->fk, 2));
-    CK(j0_build_factor(c, c->Xk));
+    if (c->j0_model == FIL_J0_DRAG)
+        CK(j0_build_factor(c, c->Xk));
+    else
+        CK(j0_dense_build_factor(c, c->Xk));
     StatusBlock sb;
     fil_status s = read_status(c, &sb);
     if (s != FIL_OK) return s;
@@ -418,7 +442,7 @@ fil_status fil_broyden_begin(fil_ctx *c, double *finf) {
     if (sb.flags[1]) return set_err(c, FIL_ENAN, "fil_broyden_begin: J0 is singular");
     if (!std::isfinite(f0)) return set_err(c, FIL_ENAN, "fil_broyden_begin: f(X_0) not finite");
     c->conv = (f0 <= c->tol * c->a) ? 1 : 0;
-    if (!c->conv) CK(j0_solve(c, c->fk, c->w));
+    if (!c->conv) CK(j0_apply(c, c->fk, c->w));
     c->in_step = 1;
     return FIL_OK;
 }
@@ -452,7 +476,7 @@ fil_status fil_broyden_step(fil_ctx *c, int32_t *converged, double *finf) {
         return FIL_OK;
     }
     CK(broyden_dots(c));
-    CK(j0_solve(c, c->fn, c->g));
+    CK(j0_apply(c, c->fn, c->g));
     CK(broyden_update(c));
     std::swap(c->Xk, c->Xn);
     std::swap(c->fk, c->fn);
@@ -481,7 +505,7 @@ fil_status fil_j0_solve(fil_ctx *c, const double *b, double *x) {
     CK(input_view(c, b, nX, c->stage_a, &db));
     const bool dev_out = is_device_ptr(x);
     double *dx = dev_out ? x : c->stage_b;
-    CK(j0_solve(c, db, dx));
+    CK(j0_apply(c, db, dx));
     if (!dev_out) CK(output_copy(c, x, dx, nX));
     return FIL_OK;
 }

@@ -90,9 +90,14 @@ struct fil_ctx {
     int iters_step;        // Broyden iterations of the current step
     int conv;              // current iterate satisfies ||f||_inf <= tol * a
 
-    // J0 band factors
+    // J0 factors: banded (drag mobility, App. B.2) or dense per filament
+    // (filament RPY mobility); piv holds 6S pivots (band rows use 6S - 3M)
+    int j0_model;
     double *band;
     int *piv;
+    double *jdense;
+    int64_t *jofs;         // [M+1] offsets of the dense blocks
+    int64_t jdense_len;
 
     // staging for host pointers (6S doubles each)
     double *stage_a, *stage_b, *stage_c;
@@ -124,6 +129,8 @@ cudaError_t commit_state(fil_ctx *c, const double *X);
 
 cudaError_t j0_build_factor(fil_ctx *c, const double *X);
 cudaError_t j0_solve(fil_ctx *c, const double *b, double *x);
+cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X);
+cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x);
 
 cudaError_t broyden_axpy_step(fil_ctx *c);                 // Xn = Xk - w
 cudaError_t broyden_dots(fil_ctx *c);                      // alpha_i, ndf2, dff

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfil.so")
 
 FIL_OK, FIL_EINVAL, FIL_ENOMEM, FIL_ECUDA, FIL_ENOCONV, FIL_ENAN, FIL_ESTALL, FIL_ESTATE = range(8)
 FIL_FP64, FIL_MIXED = 0, 1
+FIL_J0_DRAG, FIL_J0_FILAMENT_RPY = 0, 1
 STATUS_NAMES = {0: "FIL_OK", 1: "FIL_EINVAL", 2: "FIL_ENOMEM", 3: "FIL_ECUDA", 4: "FIL_ENOCONV",
                 5: "FIL_ENAN", 6: "FIL_ESTALL", 7: "FIL_ESTATE"}
 
@@ -43,7 +44,7 @@ class fil_params(ctypes.Structure):
                 ("kappa_mu", ctypes.c_double), ("kappa_nu", ctypes.c_double),
                 ("dt", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("j0_model", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 def load_library(path=LIB_PATH):
@@ -109,11 +110,12 @@ def _check(ctx, status):
 # ---- functions with the names of the C entry points ------------------------
 
 def fil_create(seg_per_fil, a=1.0, eta=1.0, dL=2.2, KB=1.0, KT=1.0, gamma0=0.0, kappa_mu=0.0,
-               kappa_nu=0.0, dt=0.01, tol=1e-8, max_iter=50, precision=FIL_FP64, stream=None):
+               kappa_nu=0.0, dt=0.01, tol=1e-8, max_iter=50, precision=FIL_FP64,
+               j0_model=FIL_J0_DRAG, stream=None):
     segs = np.ascontiguousarray(seg_per_fil, dtype=np.int32)
     p = fil_params(int(segs.size), segs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), a, eta, dL,
                    KB, KT, gamma0, kappa_mu, kappa_nu, dt, tol, int(max_iter), int(precision),
-                   ctypes.c_void_p(stream) if stream else None)
+                   int(j0_model), ctypes.c_void_p(stream) if stream else None)
     ctx = ctypes.c_void_p()
     _check(None, _lib.fil_create(ctypes.byref(p), ctypes.byref(ctx)))
     return ctx

@@ -46,10 +46,10 @@ def _system(segs, seed, history=False, KB=2.0, KT=1.5, dt=0.1, tol=1e-10, twist=
     return lay, p, st, ext, (base, t, mu, xi)
 
 
-def _gpu(fil, lay, p, st, ext, prec=0):
+def _gpu(fil, lay, p, st, ext, prec=0, j0=0):
     m = fil.Filaments(lay.N, a=p.a, eta=p.eta, dL=p.dL, KB=p.KB, KT=p.KT, gamma0=p.gamma0,
                       kappa_mu=p.kappa_mu, kappa_nu=p.kappa_nu, dt=p.dt, tol=p.tol,
-                      max_iter=p.max_iter, precision=prec)
+                      max_iter=p.max_iter, precision=prec, j0_model=j0)
     m.set_state(st.Y, st.q, st.Yprev, st.u, st.lam if lay.n_lam else None)
     m.set_external(ext.Fext, ext.Text, ext.follower)
     return m
@@ -99,11 +99,15 @@ def test_init_straight_matches_oracle(fil, segs):
     np.testing.assert_allclose(q, st.q, rtol=0, atol=1e-14)
 
 
+J0_MODELS = [(0, "drag"), (1, "rpy")]
+
+
 @pytest.mark.parametrize("segs", SEGS)
 @pytest.mark.parametrize("history", [False, True])
-def test_j0_solve_matches_dense_oracle(fil, segs, history):
+@pytest.mark.parametrize("model", J0_MODELS)
+def test_j0_solve_matches_dense_oracle(fil, segs, history, model):
     lay, p, st, ext, _ = _system(segs, 30, history=history, twist=0.2)
-    with _gpu(fil, lay, p, st, ext) as m:
+    with _gpu(fil, lay, p, st, ext, j0=model[0]) as m:
         m.broyden_begin()
         X0 = np.zeros(6 * lay.S)
         m.get_iterate(X0, None)
@@ -111,15 +115,18 @@ def test_j0_solve_matches_dense_oracle(fil, segs, history):
         b = np.random.default_rng(2).standard_normal(6 * lay.S)
         x = np.zeros_like(b)
         m.j0_solve(b, x)
-    ref = fo.J0Solver(lay, fo.jacobian0(lay, p, st, X0)).solve(b)
+    blocks = (fo.jacobian0(lay, p, st, X0) if model[1] == "drag"
+              else fo.jacobian0_general(lay, p, st, X0, model[1]))
+    ref = fo.J0Solver(lay, blocks).solve(b)
     np.testing.assert_allclose(x, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
 
 
 @pytest.mark.parametrize("segs", [[20], [32] * 4, [1, 7, 33]])
-def test_broyden_iterates_match_oracle(fil, segs):
+@pytest.mark.parametrize("model", J0_MODELS)
+def test_broyden_iterates_match_oracle(fil, segs, model):
     lay, p, st, ext, _ = _system(segs, 40, history=True, tol=1e-13)
-    br = fo.begin_step(lay, p, st, ext)
-    with _gpu(fil, lay, p, st, ext) as m:
+    br = fo.begin_step(lay, p, st, ext, j0_model=model[1])
+    with _gpu(fil, lay, p, st, ext, j0=model[0]) as m:
         f0 = m.broyden_begin()
         assert abs(f0 - np.abs(br.f).max()) <= 1e-12 * max(1, np.abs(st.Y).max())
         X = np.zeros(6 * lay.S)
@@ -196,3 +203,16 @@ def test_error_statuses(fil):
         Y1 = np.zeros((lay.S, 3))
         m.get_state(Y1, None, None, None, None)
         np.testing.assert_array_equal(Y0, Y1)       # state untouched on failure
+
+
+def test_filament_rpy_j0_step_matches_oracle(fil):
+    """Timesteps with the filament-RPY J0 agree with the oracle driven the same way."""
+    lay, p, st, ext, _ = _system([32] * 5, 70, tol=1e-10, dt=0.3)
+    with _gpu(fil, lay, p, st, ext, j0=1) as m:
+        Y = np.zeros((lay.S, 3))
+        for _ in range(3):
+            st, it_ref = fo.step(lay, p, st, ext, j0_model="rpy")
+            it = m.step()
+            assert abs(it - it_ref) <= 1
+            m.get_state(Y, None, None, None, None)
+            np.testing.assert_allclose(Y, st.Y, rtol=0, atol=1e-8)
