@@ -169,6 +169,33 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_mobility(args, fil, torch):
+    """RPY applies alone on the positions of the 32k suspension with N(0,1)
+    loads: a lean launch sequence for kernel profiling (one JSON line)."""
+    wl, base, t, mu, Fext, follower = workload()
+    S = 1000 * 32
+    Y = np.concatenate([base[i] + np.arange(32)[:, None] * wl.dL * t[i] for i in range(1000)])
+    FT = np.random.default_rng(1).standard_normal((S, 6))
+    prec = fil.FIL_MIXED if args.precision == "mixed" else fil.FIL_FP64
+    m = fil.Filaments(wl.seg_per_fil, precision=prec)
+    Yd = torch.from_numpy(Y).cuda()
+    FTd = torch.from_numpy(FT).cuda()
+    VW = torch.empty((S, 6), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        m.mobility_apply(Yd, FTd, VW)
+    m.profile(True)
+    m.profile_read()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        m.mobility_apply(Yd, FTd, VW)
+    n, ms = m.profile_read()
+    m.close()
+    avg = ms / max(n, 1)
+    print(json.dumps({"workload": "mobility apply, 32000 segments", "precision": args.precision,
+                      "pair_kernel_ms": avg, "pairs_per_s": S * S / (avg * 1e-3),
+                      "tflops": FLOPS_PER_PAIR * S * S / (avg * 1e-3) / 1e12}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,6 +209,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--j0", default="filament_rpy", choices=["filament_rpy", "drag"],
                     help="approximate Jacobian: filament RPY blocks (default) or App. B.2 drag")
+    ap.add_argument("--workload", default="suspension", choices=["suspension", "mobility"],
+                    help="'mobility': only RPY applies on the 32k configuration (for profiling)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -198,6 +227,9 @@ def main():
     from paper_1903_12609_gb300 import fil
 
     torch.cuda.set_device(local)
+    if args.workload == "mobility":
+        run_mobility(args, fil, torch)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

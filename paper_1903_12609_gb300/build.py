@@ -32,7 +32,11 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, extra_flags=()):
+def build(force=False, verbose=False, extra_flags=(), libdir=None):
+    """Compile (if stale) and link; returns the path of libfil.so. libdir and
+    extra_flags let tile-shape sweeps build variants beside the default."""
+    LIBDIR = libdir or globals()["LIBDIR"]
+    LIB = os.path.join(LIBDIR, "libfil.so")
     os.makedirs(LIBDIR, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "fil.h"))

@@ -136,6 +136,14 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// 1/sqrt(x) for normal x > 0: one MUFU operation (PTX rsqrt.approx.ftz.f32,
+// max relative error 2^-22.9). Used only for r^2 >= (2a)^2, never on denormals.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // One pair in FP32: target (hi, lo) position vs. source record (s0, s1, s2).
 __device__ __forceinline__ void pair32(float thx, float thy, float thz, float tlx, float tly,
                                        float tlz, const float4 s0, const float4 s1,
@@ -154,7 +162,7 @@ __device__ __forceinline__ void pair32(float thx, float thy, float thz, float tl
         D = fmaf(k.ov_D0, rinv, -k.ov_D1 * r);
         G = fmaf(-k.ov_G1, r, k.ov_G0);
     } else {
-        const float rinv = rsqrtf(r2);
+        const float rinv = rsqrt_approx(r2);
         const float rinv2 = rinv * rinv;
         const float rinv3 = rinv * rinv2;
         const float rinv5 = rinv3 * rinv2;
@@ -220,13 +228,18 @@ __device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision pair kernel.
+// Mixed-precision pair kernel. Each thread owns kRpyTargetsPerThread targets;
+// their pair terms are summed in registers over kRpyComp sources and then
+// folded (TwoSum) into (hi, lo) accumulators kept in shared memory, which
+// keeps the register file for the pair arithmetic.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kRpyThreads)
+__global__ void __launch_bounds__(kRpyThreads, FIL_RPY_MINB)
 rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, int G,
                   RpyConst32 k, float *__restrict__ part) {
     constexpr int kRec = 3 * kRpyChunk;           // float4 per chunk
+    constexpr int kT = kRpyTargetsPerThread;
     __shared__ float4 sm[2][kRec];
+    __shared__ float comp[kT * 12][kRpyThreads];  // [t * 12 + c] hi (c < 6), lo (c >= 6)
     const int tid = threadIdx.x;
     const int64_t b = blockIdx.x;
     int64_t u = unit_start(b, W, G);
@@ -237,19 +250,16 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
         const int64_t c_begin = u - tile * n_chunks;
         const int64_t c_end = min(n_chunks, c_begin + (u_end - u));
 
-        float th[kRpyTargetsPerThread][3], tl[kRpyTargetsPerThread][3];
+        float th[kT][3], tl[kT][3];
 #pragma unroll
-        for (int t = 0; t < kRpyTargetsPerThread; ++t) {
+        for (int t = 0; t < kT; ++t) {
             const int64_t n = tile * kRpyTile + t * kRpyThreads + tid;
             const float4 a0 = src[3 * n], a1 = src[3 * n + 1];
             th[t][0] = a0.x; th[t][1] = a0.y; th[t][2] = a0.z;
             tl[t][0] = a1.x; tl[t][1] = a1.y; tl[t][2] = a1.z;
         }
-        float hi[kRpyTargetsPerThread][6], lo[kRpyTargetsPerThread][6];
 #pragma unroll
-        for (int t = 0; t < kRpyTargetsPerThread; ++t)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) hi[t][c] = lo[t][c] = 0.f;
+        for (int r = 0; r < kT * 12; ++r) comp[r][tid] = 0.f;
 
         // first chunk -> buffer 0
         {
@@ -270,29 +280,29 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
             }
             const float4 *s = sm[buf];
 #pragma unroll 1
-            for (int half = 0; half < kRpyChunk / kRpyComp; ++half) {
-                float acc[kRpyTargetsPerThread][6];
+            for (int grp = 0; grp < kRpyChunk / kRpyComp; ++grp) {
+                float acc[kT][6];
 #pragma unroll
-                for (int t = 0; t < kRpyTargetsPerThread; ++t)
+                for (int t = 0; t < kT; ++t)
 #pragma unroll
                     for (int c = 0; c < 6; ++c) acc[t][c] = 0.f;
-#pragma unroll 4
+#pragma unroll kRpyUnroll
                 for (int j = 0; j < kRpyComp; ++j) {
-                    const int rj = 3 * (half * kRpyComp + j);
+                    const int rj = 3 * (grp * kRpyComp + j);
                     const float4 s0 = s[rj], s1 = s[rj + 1], s2 = s[rj + 2];
 #pragma unroll
-                    for (int t = 0; t < kRpyTargetsPerThread; ++t)
+                    for (int t = 0; t < kT; ++t)
                         pair32(th[t][0], th[t][1], th[t][2], tl[t][0], tl[t][1], tl[t][2], s0, s1,
                                s2, k, acc[t]);
                 }
 #pragma unroll
-                for (int t = 0; t < kRpyTargetsPerThread; ++t)
+                for (int t = 0; t < kT; ++t)
 #pragma unroll
                     for (int c = 0; c < 6; ++c) {
                         float sh, e;
-                        two_sum(hi[t][c], acc[t][c], sh, e);
-                        hi[t][c] = sh;
-                        lo[t][c] = __fadd_rn(lo[t][c], e);
+                        two_sum(comp[t * 12 + c][tid], acc[t][c], sh, e);
+                        comp[t * 12 + c][tid] = sh;
+                        comp[t * 12 + 6 + c][tid] = __fadd_rn(comp[t * 12 + 6 + c][tid], e);
                     }
             }
             if (has_next) {
@@ -305,13 +315,10 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
         // partial of this CTA for this tile -> slot (b + tile)
         float *p = part + (size_t)(b + tile) * 12 * kRpyTile;
 #pragma unroll
-        for (int t = 0; t < kRpyTargetsPerThread; ++t) {
+        for (int t = 0; t < kT; ++t) {
             const int local = t * kRpyThreads + tid;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                p[c * kRpyTile + local] = hi[t][c];
-                p[(6 + c) * kRpyTile + local] = lo[t][c];
-            }
+            for (int c = 0; c < 12; ++c) p[c * kRpyTile + local] = comp[t * 12 + c][tid];
         }
         u = tile * n_chunks + c_end;
     }

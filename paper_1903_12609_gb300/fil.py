@@ -16,7 +16,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libfil.so")
+# FIL_LIBRARY may point at another build of the same library (e.g. a tile-shape variant)
+LIB_PATH = os.environ.get("FIL_LIBRARY") or os.path.join(_HERE, "_lib", "libfil.so")
 
 FIL_OK, FIL_EINVAL, FIL_ENOMEM, FIL_ECUDA, FIL_ENOCONV, FIL_ENAN, FIL_ESTALL, FIL_ESTATE = range(8)
 FIL_FP64, FIL_MIXED = 0, 1
