@@ -209,6 +209,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--j0", default="filament_rpy", choices=["filament_rpy", "drag"],
                     help="approximate Jacobian: filament RPY blocks (default) or App. B.2 drag")
+    ap.add_argument("--n-fil", type=int, default=1000,
+                    help="filaments of 32 segments (1000 = the 32k suspension; smaller for profiling)")
     ap.add_argument("--workload", default="suspension", choices=["suspension", "mobility"],
                     help="'mobility': only RPY applies on the 32k configuration (for profiling)")
     args = ap.parse_args()
@@ -240,7 +242,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    n_fil, n_seg = 1000, 32
+    n_fil, n_seg = args.n_fil, 32
     S = n_fil * n_seg
     wl, base, t, mu, Fext, follower = workload(n_fil, n_seg, seed=rank)
     stream = torch.cuda.Stream()
@@ -359,9 +361,9 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if prec == fil.FIL_MIXED else "f64", "data": "synthetic",
         "config": {
-            "workload": "suspension 1000 filaments x 32 segments (32000), 2% volume fraction, "
+            "workload": "suspension %d filaments x 32 segments (%d), 2%% volume fraction, "
                         "half sedimenting (B=1000) half tip-follower (fL^2/KB=100), BDF2 "
-                        "dt=T/200, Broyden tol 1e-4",
+                        "dt=T/200, Broyden tol 1e-4" % (n_fil, S),
             "segments": S, "precision": args.precision, "j0": args.j0,
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "flushed between timed steps (256 MiB write)"},

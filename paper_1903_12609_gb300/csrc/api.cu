@@ -127,11 +127,17 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     if (c->j0_model == FIL_J0_DRAG) {
         c->band = ar.take<double>((size_t)nband * kBandW);
         c->jdense = nullptr;
+        c->jinv = nullptr;
         c->jofs = nullptr;
+        c->j0_rhs = c->j0_x = c->j0_res = nullptr;
     } else {
         c->band = nullptr;
         c->jdense = ar.take<double>((size_t)c->jdense_len);
+        c->jinv = ar.take<float>((size_t)c->jdense_len);
         c->jofs = ar.take<int64_t>(M + 1);
+        c->j0_rhs = ar.take<double>(nX);
+        c->j0_x = ar.take<double>(nX);
+        c->j0_res = ar.take<double>(nX);
     }
     c->piv = ar.take<int>(6 * S);
     c->stage_a = ar.take<double>(nX);
@@ -189,8 +195,10 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
         if (p->seg_per_fil[i] > maxN) maxN = p->seg_per_fil[i];
     }
     if (S > (int64_t)1 << 30) return FIL_EINVAL;
-    // the band solve keeps a filament's right-hand side in shared memory
+    // the band solve keeps a filament's right-hand side in shared memory; the
+    // filament-RPY J0 inverts each filament block in shared memory
     if (maxN > kMaxSegPerFil) return FIL_EINVAL;
+    if (p->j0_model == FIL_J0_FILAMENT_RPY && maxN > kMaxDenseSeg) return FIL_EINVAL;
 
     fil_ctx *c = new (std::nothrow) fil_ctx();
     if (!c) return FIL_ENOMEM;

@@ -45,6 +45,10 @@ constexpr int kBandKU = 8;
 constexpr int kBandW = 2 * kBandKL + kBandKU + 1;   // row window: c - i in [-8, 16]
 constexpr size_t kSolveSmemMax = 200 * 1024;        // shared memory of one band-solve CTA
 constexpr int kMaxSegPerFil = (int)(kSolveSmemMax / (6 * sizeof(double)));
+// The filament-RPY J0 keeps a filament's block in shared memory for its
+// FP32 inverse: (6N)^2 floats <= 200 KB, i.e. N <= 38; refinement steps per solve.
+constexpr int kMaxDenseSeg = 38;
+constexpr int kJ0Refine = 2;
 
 struct Layout {
     int M = 0;           // filaments
@@ -108,6 +112,8 @@ struct fil_ctx {
     double *band;
     int *piv;
     double *jdense;
+    float *jinv;           // FP32 inverse of each dense block (same offsets)
+    double *j0_rhs, *j0_x, *j0_res;   // refinement scratch (6S each)
     int64_t *jofs;         // [M+1] offsets of the dense blocks
     int64_t jdense_len;
 
@@ -143,6 +149,7 @@ cudaError_t j0_build_factor(fil_ctx *c, const double *X);
 cudaError_t j0_solve(fil_ctx *c, const double *b, double *x);
 cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X);
 cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x);
+size_t j0_dense_smem_needed(int maxN);
 
 cudaError_t broyden_axpy_step(fil_ctx *c);                 // Xn = Xk - w
 cudaError_t broyden_dots(fil_ctx *c);                      // alpha_i, ndf2, dff

@@ -17,9 +17,13 @@
 // coupling along a filament, which the drag model drops and which makes
 // Broyden need O(number of filaments) iterations in dense suspensions.
 //
-// Storage: row-major (6N)^2 FP64 block per filament at jofs[i]; factored in
-// place by Gaussian elimination with partial pivoting (one CTA per filament),
-// solved by one warp per filament.
+// Storage: row-major (6N)^2 FP64 block per filament at jofs[i] (kept for the
+// refinement residuals) and its inverse in FP32 at the same offsets, computed
+// by Gauss-Jordan elimination with partial pivoting in shared memory (one CTA
+// per filament; FP32 runs at 64x the FP64 rate on this part). A solve applies
+// the FP32 inverse and then kJ0Refine steps of iterative refinement with FP64
+// residuals b - J0 x, which brings x to FP64 accuracy (each step multiplies
+// the error by ~cond(J0) * 2^-24).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,7 +36,8 @@ namespace fil {
 namespace {
 
 constexpr int kAsmThreads = 256;
-constexpr int kLuThreads = 256;
+constexpr int kInvThreads = 512;
+constexpr int kMaxInvN = 6 * kMaxDenseSeg;   // rows of the largest inverted block
 
 struct DenseParams {
     J0Params jp;
@@ -123,6 +128,17 @@ j0_dense_assemble_kernel(Layout lay, const int64_t *__restrict__ jofs, const dou
         st3(g.Ti + 3 * n, ld3(Tint + 3 * gg));
     }
     for (int64_t e = threadIdx.x; e < (int64_t)n6 * n6; e += blockDim.x) J[e] = 0.0;
+    // per-pair RPY coefficients and per-joint moment derivatives, computed once
+    PairCoef *pc = reinterpret_cast<PairCoef *>(sm + 25 * N);      // N*N entries
+    M33 *DaJ = reinterpret_cast<M33 *>(sm + 25 * N + 5 * N * N);    // N-1 joints
+    M33 *DbJ = DaJ + (N > 1 ? N - 1 : 0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int n = e / N, m = e - (e / N) * N;
+        pc[e] = pair_coef(ld3(g.Y + 3 * n) - ld3(g.Y + 3 * m), dp.a);
+    }
+    for (int jn = threadIdx.x; jn < N - 1; jn += blockDim.x)
+        moment_derivs(dp.jp, ld4(g.Q + 4 * jn), ld4(g.Q + 4 * (jn + 1)), DaJ[jn], DbJ[jn]);
     __syncthreads();
     // angular velocity of the internal loads, filament block only
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
@@ -130,8 +146,7 @@ j0_dense_assemble_kernel(Layout lay, const int64_t *__restrict__ jofs, const dou
         const V3 Yn = ld3(g.Y + 3 * n);
         for (int m = 0; m < N; ++m) {
             const V3 d = Yn - ld3(g.Y + 3 * m);
-            const PairCoef k = pair_coef(d, dp.a);
-            apply_pair(k, d, ld3(g.Fi + 3 * m), ld3(g.Ti + 3 * m), V, W);
+            apply_pair(pc[n * N + m], d, ld3(g.Fi + 3 * m), ld3(g.Ti + 3 * m), V, W);
         }
         st3(g.Om + 3 * n, dp.inv8pieta * W);
     }
@@ -150,26 +165,22 @@ j0_dense_assemble_kernel(Layout lay, const int64_t *__restrict__ jofs, const dou
             // d T_m / d u_k, m = k-1, k, k+1 (App. B.2)
             const int k = x;
             colX = 3 + 3 * k;
-            const Q4 qk = ld4(g.Q + 4 * k);
-            M33 Da_k, Db_k, Da_km, Db_km;
-            if (k <= N - 2) moment_derivs(dp.jp, qk, ld4(g.Q + 4 * (k + 1)), Da_k, Db_k);
-            if (k >= 1) moment_derivs(dp.jp, ld4(g.Q + 4 * (k - 1)), qk, Da_km, Db_km);
             for (int mm = -1; mm <= 1; ++mm) {
                 const int m = k + mm;
                 if (m < 0 || m > N - 1) continue;
                 M33 Gt;
                 if (mm == -1) {
-                    Gt = Db_km;
+                    Gt = DbJ[k - 1];
                 } else if (mm == 0) {
                     Gt = mscale(mmul(rskew(ld3(g.Ls + 3 * k)), rskew(ld3(g.t + 3 * k))),
                                 0.5 * dp.jp.dL);
-                    if (k <= N - 2) Gt = madd(Gt, Da_k);
-                    if (k >= 1) Gt = madd(Gt, Db_km, -1.0);
+                    if (k <= N - 2) Gt = madd(Gt, DaJ[k]);
+                    if (k >= 1) Gt = madd(Gt, DbJ[k - 1], -1.0);
                 } else {
-                    Gt = mscale(Da_k, -1.0);
+                    Gt = mscale(DaJ[k], -1.0);
                 }
                 const V3 d = Yn - ld3(g.Y + 3 * m);
-                const PairCoef kc = pair_coef(d, dp.a);
+                const PairCoef kc = pc[n * N + m];
                 for (int c = 0; c < 3; ++c) apply_pair(kc, d, v3(0, 0, 0), col(Gt, c), MV[c], MW[c]);
             }
         } else {
@@ -181,7 +192,7 @@ j0_dense_assemble_kernel(Layout lay, const int64_t *__restrict__ jofs, const dou
                 const M33 Gt = mscale(skew(ld3(g.t + 3 * m)), 0.5 * dp.jp.dL);
                 const double sF = mm == 0 ? 1.0 : -1.0;
                 const V3 d = Yn - ld3(g.Y + 3 * m);
-                const PairCoef kc = pair_coef(d, dp.a);
+                const PairCoef kc = pc[n * N + m];
                 for (int c = 0; c < 3; ++c) {
                     V3 e = v3(c == 0 ? sF : 0.0, c == 1 ? sF : 0.0, c == 2 ? sF : 0.0);
                     apply_pair(kc, d, e, col(Gt, c), MV[c], MW[c]);
@@ -238,132 +249,198 @@ j0_dense_assemble_kernel(Layout lay, const int64_t *__restrict__ jofs, const dou
     }
 }
 
-// In-place LU with partial pivoting of each filament's block (LAPACK getf2
-// order: the whole pivot row is swapped, then the trailing rank-1 update).
-__global__ void __launch_bounds__(kLuThreads)
-dense_lu_kernel(Layout lay, const int64_t *__restrict__ jofs, double *__restrict__ J_all,
-                int *__restrict__ piv_all, int *__restrict__ flags) {
-    __shared__ double red_v[kLuThreads / 32];
-    __shared__ int red_i[kLuThreads / 32];
-    __shared__ int s_piv;
-    extern __shared__ double prow[];   // pivot row (n doubles)
+// Inverse of each filament's J0 in FP32 by Gauss-Jordan elimination with
+// partial pivoting, in place in shared memory (one CTA per filament):
+// for each k, swap the pivot row into place, scale it by 1/pivot (the pivot
+// entry becomes 1/pivot), then eliminate column k from every other row. The
+// column-k entries of the other rows are saved and zeroed first, so that the
+// elimination is one FMA per element: a_ic <- a_ic - a_ik * p_c, which also
+// leaves -a_ik / pivot in column k. Row swaps are undone as column swaps at
+// the end. Threads own column chunks c = lane + 32 jj (jj < NCH, the pivot row
+// of those columns in registers) and rows i = warp + nwarps * r.
+template <int NCH>
+__global__ void __launch_bounds__(kInvThreads)
+gauss_jordan_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
+                            const double *__restrict__ J_all, float *__restrict__ inv_all,
+                            int *__restrict__ flags) {
+    extern __shared__ float Asm[];                  // n rows of stride ld = n + 1
+    __shared__ float colk[kMaxInvN];
+    __shared__ int perm[kMaxInvN];
+    __shared__ float red_v[kInvThreads / 32];
+    __shared__ int red_i[kInvThreads / 32];
+    __shared__ int s_p;
     const int f = blockIdx.x;
     const int s0 = lay.off[f];
     const int n = 6 * (lay.off[f + 1] - s0);
-    double *A = J_all + jofs[f];
-    int *piv = piv_all + 6 * (int64_t)s0;
+    const double *J = J_all + jofs[f];
+    float *out = inv_all + jofs[f];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int j = 0; j < n; ++j) {
-        double v = -1.0;
-        int idx = j;
-        for (int i = j + tid; i < n; i += blockDim.x) {
-            const double a = fabs(A[(int64_t)i * n + j]);
-            if (a > v) {
-                v = a;
-                idx = i;
-            }
+    const int nw = (int)(blockDim.x >> 5);
+    const int ld = n + 1;   // odd stride: column accesses hit distinct banks
+    for (int i = wid; i < n; i += nw)
+        for (int c = lane; c < n; c += 32) Asm[i * ld + c] = (float)J[(int64_t)i * n + c];
+    bool valid[NCH];
+#pragma unroll
+    for (int jj = 0; jj < NCH; ++jj) valid[jj] = (lane + 32 * jj) < n;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        // pivot: first row of maximal |a_ik|, i >= k
+        float v = -1.f;
+        int idx = k;
+        for (int i = k + tid; i < n; i += blockDim.x) {
+            const float a = fabsf(Asm[i * ld + k]);
+            if (a > v) { v = a; idx = i; }
         }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, v, d);
+            const float ov = __shfl_down_sync(0xffffffffu, v, d);
             const int oi = __shfl_down_sync(0xffffffffu, idx, d);
-            if (ov > v || (ov == v && oi < idx)) {
-                v = ov;
-                idx = oi;
+            if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+        }
+        if (lane == 0) { red_v[wid] = v; red_i[wid] = idx; }
+        __syncthreads();
+        if (wid == 0) {
+            float bv = lane < nw ? red_v[lane] : -1.f;
+            int bi = lane < nw ? red_i[lane] : 0x7fffffff;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                const float ov = __shfl_down_sync(0xffffffffu, bv, d);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, d);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            if (lane == 0) {
+                s_p = bi;
+                perm[k] = bi;
+                if (!(bv > 0.f)) atomicOr(flags + 1, 1);
             }
         }
-        if (lane == 0) {
-            red_v[wid] = v;
-            red_i[wid] = idx;
-        }
         __syncthreads();
-        if (tid == 0) {
-            double bv = red_v[0];
-            int bi = red_i[0];
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-                if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bi)) {
-                    bv = red_v[w];
-                    bi = red_i[w];
-                }
-            s_piv = bi;
-            piv[j] = bi;
-            if (!(bv > 0.0)) atomicOr(flags + 1, 1);
-        }
-        __syncthreads();
-        const int p = s_piv;
-        if (p != j) {
+        const int p = s_p;
+        if (p != k)
             for (int c = tid; c < n; c += blockDim.x) {
-                const double tmp = A[(int64_t)j * n + c];
-                A[(int64_t)j * n + c] = A[(int64_t)p * n + c];
-                A[(int64_t)p * n + c] = tmp;
+                const float t = Asm[k * ld + c];
+                Asm[k * ld + c] = Asm[p * ld + c];
+                Asm[p * ld + c] = t;
             }
-            __syncthreads();
-        }
-        const double piv_inv = 1.0 / A[(int64_t)j * n + j];
-        for (int c = j + 1 + tid; c < n; c += blockDim.x) prow[c] = A[(int64_t)j * n + c];
-        for (int i = j + 1 + tid; i < n; i += blockDim.x) A[(int64_t)i * n + j] *= piv_inv;
         __syncthreads();
-        const int w = n - j - 1;
-        for (int64_t e = tid; e < (int64_t)w * w; e += blockDim.x) {
-            const int i = j + 1 + (int)(e / w);
-            const int c = j + 1 + (int)(e % w);
-            A[(int64_t)i * n + c] -= A[(int64_t)i * n + j] * prow[c];
+        const float pinv = 1.f / Asm[k * ld + k];
+        // save and zero column k of the other rows; scale the pivot row
+        for (int i = tid; i < n; i += blockDim.x) {
+            if (i != k) {
+                colk[i] = Asm[i * ld + k];
+                Asm[i * ld + k] = 0.f;
+            } else {
+                colk[i] = 0.f;
+            }
         }
         __syncthreads();
+        for (int c = tid; c < n; c += blockDim.x)
+            Asm[k * ld + c] = (c == k) ? pinv : Asm[k * ld + c] * pinv;
+        __syncthreads();
+        float pr[NCH];
+#pragma unroll
+        for (int jj = 0; jj < NCH; ++jj) pr[jj] = valid[jj] ? Asm[k * ld + lane + 32 * jj] : 0.f;
+        for (int i = wid; i < n; i += nw) {
+            if (i == k) continue;
+            const float mf = -colk[i];
+            float *row = Asm + i * ld + lane;
+#pragma unroll
+            for (int jj = 0; jj < NCH; ++jj)
+                if (valid[jj]) row[32 * jj] = fmaf(mf, pr[jj], row[32 * jj]);
+        }
+        __syncthreads();
+    }
+    // undo the row interchanges as column interchanges, last first
+    for (int k = n - 1; k >= 0; --k) {
+        const int p = perm[k];
+        if (p != k)
+            for (int i = tid; i < n; i += blockDim.x) {
+                const float t = Asm[i * ld + k];
+                Asm[i * ld + k] = Asm[i * ld + p];
+                Asm[i * ld + p] = t;
+            }
+        __syncthreads();
+    }
+    for (int i = wid; i < n; i += nw)
+        for (int c = lane; c < n; c += 32) out[(int64_t)i * n + c] = Asm[i * ld + c];
+}
+
+// Refined solve, as grid-wide GEMV phases over every row of every filament
+// (one warp per row, lanes stride the columns with coalesced loads):
+//   x = Inv b;  then kJ0Refine times:  r = b - J0 x (FP64);  x += Inv r.
+__global__ void inv_apply_kernel(Layout lay, const int64_t *__restrict__ jofs,
+                                 const float *__restrict__ inv_all, const float *__restrict__ r,
+                                 double *__restrict__ x, int accumulate) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= lay.nX) return;
+    const int f = lay.fil_of[row / 6];
+    const int64_t r0 = 6 * (int64_t)lay.off[f];
+    const int n = (int)(6 * (int64_t)lay.off[f + 1] - r0);
+    const int i = (int)(row - r0);
+    const float *A = inv_all + jofs[f] + (int64_t)i * n;
+    const float *rf = r + r0;
+    float t = 0.f;
+    for (int c = lane; c < n; c += 32) t = fmaf(A[c], rf[c], t);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) t += __shfl_down_sync(0xffffffffu, t, d);
+    if (lane == 0) x[row] = accumulate ? x[row] + (double)t : (double)t;
+}
+
+__global__ void to_float_kernel(int64_t n, const double *__restrict__ b, double *__restrict__ bb,
+                                float *__restrict__ r) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double v = b[i];
+        bb[i] = v;
+        r[i] = (float)v;
     }
 }
 
-// x = J0^{-1} b, one warp per filament: row interchanges, unit-lower forward,
-// upper backward substitution; rows are read with coalesced loads.
-__global__ void dense_solve_kernel(Layout lay, const int64_t *__restrict__ jofs,
-                                   const double *__restrict__ J_all, const int *__restrict__ piv_all,
-                                   const double *b, double *x, int zmax) {
-    extern __shared__ double zs[];
-    const int wib = threadIdx.x >> 5;
-    const int f = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+__global__ void residual_gemv_kernel(Layout lay, const int64_t *__restrict__ jofs,
+                                     const double *__restrict__ J_all, const double *__restrict__ b,
+                                     const double *__restrict__ x, float *__restrict__ r) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (f >= lay.M) return;
-    double *z = zs + (int64_t)wib * zmax;
-    const int s0 = lay.off[f];
-    const int n = 6 * (lay.off[f + 1] - s0);
-    const double *A = J_all + jofs[f];
-    const int *piv = piv_all + 6 * (int64_t)s0;
-    const double *bf = b + 6 * (int64_t)s0;
-    double *xf = x + 6 * (int64_t)s0;
-    for (int i = lane; i < n; i += 32) z[i] = bf[i];
-    __syncwarp();
-    if (lane == 0)
-        for (int j = 0; j < n; ++j) {
-            const int p = piv[j];
-            if (p != j) {
-                const double t = z[j];
-                z[j] = z[p];
-                z[p] = t;
-            }
-        }
-    __syncwarp();
-    for (int i = 1; i < n; ++i) {
-        const double *row = A + (int64_t)i * n;
-        double t = 0.0;
-        for (int c = lane; c < i; c += 32) t += row[c] * z[c];
+    if (row >= lay.nX) return;
+    const int f = lay.fil_of[row / 6];
+    const int64_t r0 = 6 * (int64_t)lay.off[f];
+    const int n = (int)(6 * (int64_t)lay.off[f + 1] - r0);
+    const int i = (int)(row - r0);
+    const double *A = J_all + jofs[f] + (int64_t)i * n;
+    const double *xf = x + r0;
+    double t = 0.0;
+    for (int c = lane; c < n; c += 32) t = fma(A[c], xf[c], t);
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) t += __shfl_down_sync(0xffffffffu, t, d);
-        if (lane == 0) z[i] -= t;
-        __syncwarp();
-    }
-    for (int i = n - 1; i >= 0; --i) {
-        const double *row = A + (int64_t)i * n;
-        double t = 0.0;
-        for (int c = i + 1 + lane; c < n; c += 32) t += row[c] * z[c];
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) t += __shfl_down_sync(0xffffffffu, t, d);
-        if (lane == 0) z[i] = (z[i] - t) / row[i];
-        __syncwarp();
-    }
-    for (int i = lane; i < n; i += 32) xf[i] = z[i];
+    for (int d = 16; d > 0; d >>= 1) t += __shfl_down_sync(0xffffffffu, t, d);
+    if (lane == 0) r[row] = (float)(b[row] - t);
 }
 
 }  // namespace
+
+template <int NCH>
+cudaError_t launch_gj(fil_ctx *c, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(gauss_jordan_inverse_kernel<NCH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gauss_jordan_inverse_kernel<NCH><<<c->lay.M, kInvThreads, smem, c->stream>>>(
+        c->lay, c->jofs, c->jdense, c->jinv, c->d_flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_jordan(fil_ctx *c, int nch, size_t smem) {
+    switch (nch) {
+        case 1: return launch_gj<1>(c, smem);
+        case 2: return launch_gj<2>(c, smem);
+        case 3: return launch_gj<3>(c, smem);
+        case 4: return launch_gj<4>(c, smem);
+        case 5: return launch_gj<5>(c, smem);
+        case 6: return launch_gj<6>(c, smem);
+        case 7: return launch_gj<7>(c, smem);
+        case 8: return launch_gj<8>(c, smem);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
     const double beta = c->have_prev ? 2.0 / 3.0 : 1.0;
@@ -373,46 +450,47 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
     dp.inv8pieta = 1.0 / (8.0 * kPi * c->eta);
     dp.near2 = 4.0 * c->a * c->a;
     dp.a = c->a;
-    const size_t smem_asm = (size_t)25 * c->lay.maxN * sizeof(double);
-    if (smem_asm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(j0_dense_assemble_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_asm);
-        if (e != cudaSuccess) return e;
-    }
+    const int N = c->lay.maxN;
+    const size_t smem_asm = (size_t)(25 * N + 5 * N * N) * sizeof(double) +
+                            (size_t)2 * (N > 1 ? N - 1 : 0) * sizeof(M33);
+    cudaError_t e = cudaFuncSetAttribute(j0_dense_assemble_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_asm);
+    if (e != cudaSuccess) return e;
     j0_dense_assemble_kernel<<<c->lay.M, kAsmThreads, smem_asm, c->stream>>>(
         c->lay, c->jofs, X, c->qc, c->Yc, c->Tint, dp, c->jdense);
-    const size_t smem_lu = (size_t)6 * c->lay.maxN * sizeof(double);
-    if (smem_lu > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(dense_lu_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_lu);
-        if (e != cudaSuccess) return e;
-    }
-    dense_lu_kernel<<<c->lay.M, kLuThreads, smem_lu, c->stream>>>(c->lay, c->jofs, c->jdense,
-                                                                   c->piv, c->d_flags);
+    const size_t smem_inv = (size_t)6 * N * (6 * N + 1) * sizeof(float);
+    const int nch = (6 * N + 31) / 32;
+    e = launch_gauss_jordan(c, nch, smem_inv);
+    if (e != cudaSuccess) return e;
     c->n_launches += 2;
     return cudaGetLastError();
 }
 
 cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x) {
-    const int zmax = 6 * c->lay.maxN;
-    const size_t per_warp = (size_t)zmax * sizeof(double);
-    int warps = (int)std::min<size_t>(4, kSolveSmemMax / per_warp);
-    if (warps < 1) return cudaErrorInvalidValue;
-    const size_t smem = warps * per_warp;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(dense_solve_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
+    // b and x may alias: b is copied into the refinement scratch first
+    const int64_t nX = c->lay.nX;
+    const unsigned grid = (unsigned)((nX * 32 + 255) / 256);
+    double *bb = c->j0_rhs, *xx = c->j0_x;
+    float *rr = reinterpret_cast<float *>(c->j0_res);
+    to_float_kernel<<<(unsigned)((nX + 255) / 256), 256, 0, c->stream>>>(nX, b, bb, rr);
+    inv_apply_kernel<<<grid, 256, 0, c->stream>>>(c->lay, c->jofs, c->jinv, rr, xx, 0);
+    for (int it = 0; it < kJ0Refine; ++it) {
+        residual_gemv_kernel<<<grid, 256, 0, c->stream>>>(c->lay, c->jofs, c->jdense, bb, xx, rr);
+        inv_apply_kernel<<<grid, 256, 0, c->stream>>>(c->lay, c->jofs, c->jinv, rr, xx, 1);
     }
-    const int threads = 32 * warps;
-    const unsigned grid = (unsigned)(((int64_t)c->lay.M * 32 + threads - 1) / threads);
-    dense_solve_kernel<<<grid, threads, smem, c->stream>>>(c->lay, c->jofs, c->jdense, c->piv, b,
-                                                           x, zmax);
-    c->n_launches += 1;
+    cudaError_t e = cudaMemcpyAsync(x, xx, sizeof(double) * nX, cudaMemcpyDeviceToDevice,
+                                    c->stream);
+    c->n_launches += 2 + 2 * kJ0Refine;
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+size_t j0_dense_smem_needed(int maxN) {
+    const size_t a = (size_t)(25 * maxN + 5 * maxN * maxN) * sizeof(double) +
+                     (size_t)2 * maxN * sizeof(M33);
+    const size_t b = (size_t)6 * maxN * (6 * maxN + 1) * sizeof(float);
+    return a > b ? a : b;
 }
 
 }  // namespace fil
