@@ -23,7 +23,7 @@ constexpr int kProfMax = 4096;   // timed pair-kernel launches kept per read
 #define FIL_RPY_TPT 2
 #endif
 #ifndef FIL_RPY_UNROLL
-#define FIL_RPY_UNROLL 4
+#define FIL_RPY_UNROLL 8
 #endif
 #ifndef FIL_RPY_MINB
 #define FIL_RPY_MINB 1

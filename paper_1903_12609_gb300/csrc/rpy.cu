@@ -32,6 +32,9 @@
 //    ~2 ulp relative accuracy for close pairs; each target sums kRpyComp pair
 //    terms in FP32 and folds them into a (hi, lo) compensated accumulator
 //    (TwoSum); the reduce adds the partials in FP64.
+//  * The inner loop is branch-free (far form with r^2 clamped at contact);
+//    overlapping pairs are rare, so a group of kRpyComp sources in which a warp
+//    met one is recomputed with the exact far/overlap branches.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -185,6 +188,41 @@ __device__ __forceinline__ void pair32(float thx, float thy, float thz, float tl
     acc[5] = fmaf(C, Tz, fmaf(dT, dz, fmaf(Fx, ey, fmaf(-Fy, ex, acc[5]))));
 }
 
+// The far-form pair term for every pair, branch-free: r^2 is clamped at contact
+// ((2a)^2) so the coefficients stay finite for overlapping and coincident
+// pairs, and the smallest r^2 seen is tracked. A group of sources in which a
+// warp saw r^2 < (2a)^2 is recomputed with pair32 (exact branches).
+__device__ __forceinline__ void pair32_far(float thx, float thy, float thz, float tlx, float tly,
+                                           float tlz, const float4 s0, const float4 s1,
+                                           const float4 s2, const RpyConst32 &k, float *acc,
+                                           float &rmin2) {
+    const float dx = __fsub_rn(thx, s0.x) + __fsub_rn(tlx, s1.x);
+    const float dy = __fsub_rn(thy, s0.y) + __fsub_rn(tly, s1.y);
+    const float dz = __fsub_rn(thz, s0.z) + __fsub_rn(tlz, s1.z);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    rmin2 = fminf(rmin2, r2);
+    const float rinv = rsqrt_approx(fmaxf(r2, k.near2));
+    const float rinv2 = rinv * rinv;
+    const float rinv3 = rinv * rinv2;
+    const float rinv5 = rinv3 * rinv2;
+    const float A = fmaf(k.k23a2, rinv3, rinv);
+    const float B = fmaf(-k.k2a2, rinv5, rinv3);
+    const float C = -0.5f * rinv3;
+    const float D = 1.5f * rinv5;
+    const float G = rinv3;
+    const float Fx = s0.w, Fy = s1.w, Fz = s2.w;
+    const float Tx = s2.x, Ty = s2.y, Tz = s2.z;
+    const float bF = B * fmaf(dx, Fx, fmaf(dy, Fy, dz * Fz));
+    const float dT = D * fmaf(dx, Tx, fmaf(dy, Ty, dz * Tz));
+    const float ex = G * dx, ey = G * dy, ez = G * dz;
+    acc[0] = fmaf(A, Fx, fmaf(bF, dx, fmaf(Ty, ez, fmaf(-Tz, ey, acc[0]))));
+    acc[1] = fmaf(A, Fy, fmaf(bF, dy, fmaf(Tz, ex, fmaf(-Tx, ez, acc[1]))));
+    acc[2] = fmaf(A, Fz, fmaf(bF, dz, fmaf(Tx, ey, fmaf(-Ty, ex, acc[2]))));
+    acc[3] = fmaf(C, Tx, fmaf(dT, dx, fmaf(Fy, ez, fmaf(-Fz, ey, acc[3]))));
+    acc[4] = fmaf(C, Ty, fmaf(dT, dy, fmaf(Fz, ex, fmaf(-Fx, ez, acc[4]))));
+    acc[5] = fmaf(C, Tz, fmaf(dT, dz, fmaf(Fx, ey, fmaf(-Fy, ex, acc[5]))));
+}
+
 // One pair in FP64 (record layout: Y, F, T).
 __device__ __forceinline__ void pair64(double tx, double ty, double tz, const double *s,
                                        const RpyConst64 &k, double *acc) {
@@ -229,9 +267,10 @@ __device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
 
 // ---------------------------------------------------------------------------
 // Mixed-precision pair kernel. Each thread owns kRpyTargetsPerThread targets;
-// their pair terms are summed in registers over kRpyComp sources and then
-// folded (TwoSum) into (hi, lo) accumulators kept in shared memory, which
-// keeps the register file for the pair arithmetic.
+// their pair terms are summed in registers over groups of kRpyComp sources
+// with the branch-free far form, a group in which the warp met an overlapping
+// pair is recomputed exactly, and the group sums are folded (TwoSum) into
+// (hi, lo) accumulators.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRpyThreads, FIL_RPY_MINB)
 rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, int G,
@@ -239,7 +278,6 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
     constexpr int kRec = 3 * kRpyChunk;           // float4 per chunk
     constexpr int kT = kRpyTargetsPerThread;
     __shared__ float4 sm[2][kRec];
-    __shared__ float comp[kT * 12][kRpyThreads];  // [t * 12 + c] hi (c < 6), lo (c >= 6)
     const int tid = threadIdx.x;
     const int64_t b = blockIdx.x;
     int64_t u = unit_start(b, W, G);
@@ -258,8 +296,11 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
             th[t][0] = a0.x; th[t][1] = a0.y; th[t][2] = a0.z;
             tl[t][0] = a1.x; tl[t][1] = a1.y; tl[t][2] = a1.z;
         }
+        float hi[kT][6], lo[kT][6];
 #pragma unroll
-        for (int r = 0; r < kT * 12; ++r) comp[r][tid] = 0.f;
+        for (int t = 0; t < kT; ++t)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) hi[t][c] = lo[t][c] = 0.f;
 
         // first chunk -> buffer 0
         {
@@ -286,23 +327,40 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
                 for (int t = 0; t < kT; ++t)
 #pragma unroll
                     for (int c = 0; c < 6; ++c) acc[t][c] = 0.f;
+                float rmin2 = k.near2;
 #pragma unroll kRpyUnroll
                 for (int j = 0; j < kRpyComp; ++j) {
                     const int rj = 3 * (grp * kRpyComp + j);
                     const float4 s0 = s[rj], s1 = s[rj + 1], s2 = s[rj + 2];
 #pragma unroll
                     for (int t = 0; t < kT; ++t)
-                        pair32(th[t][0], th[t][1], th[t][2], tl[t][0], tl[t][1], tl[t][2], s0, s1,
-                               s2, k, acc[t]);
+                        pair32_far(th[t][0], th[t][1], th[t][2], tl[t][0], tl[t][1], tl[t][2], s0,
+                                   s1, s2, k, acc[t], rmin2);
+                }
+                if (__any_sync(0xffffffffu, rmin2 < k.near2)) {
+                    // an overlapping (or self) pair: redo this group with the exact branches
+#pragma unroll
+                    for (int t = 0; t < kT; ++t)
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) acc[t][c] = 0.f;
+#pragma unroll 1
+                    for (int j = 0; j < kRpyComp; ++j) {
+                        const int rj = 3 * (grp * kRpyComp + j);
+                        const float4 s0 = s[rj], s1 = s[rj + 1], s2 = s[rj + 2];
+#pragma unroll
+                        for (int t = 0; t < kT; ++t)
+                            pair32(th[t][0], th[t][1], th[t][2], tl[t][0], tl[t][1], tl[t][2], s0,
+                                   s1, s2, k, acc[t]);
+                    }
                 }
 #pragma unroll
                 for (int t = 0; t < kT; ++t)
 #pragma unroll
                     for (int c = 0; c < 6; ++c) {
                         float sh, e;
-                        two_sum(comp[t * 12 + c][tid], acc[t][c], sh, e);
-                        comp[t * 12 + c][tid] = sh;
-                        comp[t * 12 + 6 + c][tid] = __fadd_rn(comp[t * 12 + 6 + c][tid], e);
+                        two_sum(hi[t][c], acc[t][c], sh, e);
+                        hi[t][c] = sh;
+                        lo[t][c] = __fadd_rn(lo[t][c], e);
                     }
             }
             if (has_next) {
@@ -318,7 +376,10 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
         for (int t = 0; t < kT; ++t) {
             const int local = t * kRpyThreads + tid;
 #pragma unroll
-            for (int c = 0; c < 12; ++c) p[c * kRpyTile + local] = comp[t * 12 + c][tid];
+            for (int c = 0; c < 6; ++c) {
+                p[c * kRpyTile + local] = hi[t][c];
+                p[(6 + c) * kRpyTile + local] = lo[t][c];
+            }
         }
         u = tile * n_chunks + c_end;
     }
