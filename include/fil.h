@@ -196,6 +196,29 @@ fil_status fil_counters(const fil_ctx *c, int64_t *mobility_applies, int64_t *br
 fil_status fil_profile(fil_ctx *c, int32_t enable);
 fil_status fil_profile_read(fil_ctx *c, int64_t *launches, double *total_ms);
 
+/* Allocation-free mobility apply. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory themselves --
+ * code that runs where cudaMalloc is unavailable or not allowed, such as
+ * inside another framework's memory pool or a host process whose device
+ * allocations belong to someone else -- and so cannot hold a context.
+ * It computes the same product as fil_mobility_apply of a FIL_MIXED context
+ * (FP32 pair sums with compensated accumulation, FP64 results) for S =
+ * n_seg segments with radius a and viscosity eta: Y (S x 3), FT (S x 6) and
+ * VW (S x 6) must be DEVICE pointers, owned by the caller. It allocates
+ * nothing: its scratch is a fixed static device array of about 10.6 MB in
+ * the library, which every GPU that loads the library keeps until the
+ * process exits. Limits: 1 <= n_seg <= 32768; larger sizes, host pointers or
+ * non-positive a, eta return FIL_EINVAL; CUDA failures return FIL_ECUDA.
+ * The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress) and should come before any stream capture.
+ * Work is enqueued on `stream` (a cudaStream_t, NULL for the legacy stream)
+ * without synchronising. All calls share the one array and leave their
+ * contents in it; calls whose executions overlap on the GPU (different
+ * streams, or different host threads) race on it and must be serialised by
+ * the caller. */
+fil_status fil_rpy_apply_noalloc(int64_t n_seg, const double *Y, const double *FT, double *VW,
+                                 double a, double eta, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "fil_internal.cuh"
 
@@ -583,4 +584,96 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW)
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free mobility apply (fil_rpy_apply_noalloc).
+//
+// For callers that cannot allocate device memory themselves -- code running
+// where cudaMalloc is unavailable or forbidden, e.g. inside another
+// framework's memory pool or a process whose allocations are owned by
+// someone else -- this variant of the mixed-precision apply uses no context
+// and allocates nothing: its scratch (packed FP32 sources and the stream-K
+// partial sums) is the file-scope array below, which every GPU that loads the
+// library holds until the process exits. The caller passes the inputs and
+// the output in device memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxSeg = 32768;     // largest S accepted
+constexpr int kNoAllocMaxGrid = 4 * 152;      // stream-K CTAs at most
+constexpr int64_t kNoAllocMaxTiles = (kNoAllocMaxSeg + kRpyTile - 1) / kRpyTile;
+constexpr size_t kNoAllocSrcBytes = (size_t)3 * kNoAllocMaxTiles * kRpyTile * sizeof(float4);
+constexpr size_t kNoAllocPartBytes =
+    (size_t)(kNoAllocMaxGrid + kNoAllocMaxTiles) * 12 * kRpyTile * sizeof(float);
+constexpr size_t kNoAllocBytes = kNoAllocSrcBytes + kNoAllocPartBytes;   // ~10.6 MB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_ptr[kNoAllocMaxDevices];   // device address of the array, per device
+int g_noalloc_grid[kNoAllocMaxDevices];
+
+// Once per device, with that device current: the device address of the array
+// (the name itself is only a host-side stand-in) and the stream-K grid size.
+cudaError_t noalloc_setup(int dev, unsigned char **ptr, int *grid) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        int occ = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rpy_pair32_kernel, kRpyThreads, 0);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_noalloc_grid[dev] = std::max(1, std::min(kNoAllocMaxGrid, std::max(1, occ) * sms));
+        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *ptr = g_noalloc_ptr[dev];
+    *grid = g_noalloc_grid[dev];
+    return cudaSuccess;
+}
+
+bool on_device(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
 }  // namespace fil
+
+extern "C" fil_status fil_rpy_apply_noalloc(int64_t n_seg, const double *Y, const double *FT,
+                                            double *VW, double a, double eta, void *stream) {
+    using namespace fil;
+    if (n_seg < 1 || n_seg > kNoAllocMaxSeg) return FIL_EINVAL;
+    if (!(a > 0) || !(eta > 0) || !Y || !FT || !VW) return FIL_EINVAL;
+    if (!on_device(Y) || !on_device(FT) || !on_device(VW)) return FIL_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return FIL_ECUDA;
+    unsigned char *base = nullptr;
+    int grid_max = 1;
+    if (noalloc_setup(dev, &base, &grid_max) != cudaSuccess) return FIL_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t tiles = (n_seg + kRpyTile - 1) / kRpyTile;
+    const int64_t n_chunks = (n_seg + kRpyChunk - 1) / kRpyChunk;
+    const int64_t Spad = std::max(tiles * kRpyTile, n_chunks * kRpyChunk);
+    const int64_t W = tiles * n_chunks;
+    const int G = (int)std::min<int64_t>(grid_max, W);
+    float4 *src = reinterpret_cast<float4 *>(base);
+    float *part = reinterpret_cast<float *>(base + kNoAllocSrcBytes);
+    // every source record up to Spad and every partial slot the reduce reads
+    // is written below, so nothing has to start at zero
+    const int pb = 256;
+    pack32_kernel<<<(unsigned)((Spad + pb - 1) / pb), pb, 0, st>>>(Y, FT, n_seg, Spad, src);
+    rpy_pair32_kernel<<<G, kRpyThreads, 0, st>>>(src, n_chunks, W, G,
+                                                 make_const<float, RpyConst32>(a), part);
+    rpy_reduce32_kernel<<<(unsigned)((n_seg + pb - 1) / pb), pb, 0, st>>>(
+        part, n_seg, n_chunks, W, G, 1.0 / (8.0 * kPi * eta), VW);
+    return cudaGetLastError() == cudaSuccess ? FIL_OK : FIL_ECUDA;
+}

@@ -29,7 +29,7 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_get_state", "fil_init_straight", "fil_set_external", "fil_mobility_apply",
             "fil_residual", "fil_broyden_begin", "fil_broyden_step", "fil_get_iterate",
             "fil_j0_solve", "fil_broyden_commit", "fil_step", "fil_set_dt", "fil_counters",
-            "fil_profile", "fil_profile_read"]
+            "fil_profile", "fil_profile_read", "fil_rpy_apply_noalloc"]
 
 
 class FilError(RuntimeError):
@@ -77,6 +77,7 @@ def load_library(path=LIB_PATH):
         "fil_counters": [P, I64, I64, I64],
         "fil_profile": [P, ctypes.c_int32],
         "fil_profile_read": [P, I64, D],
+        "fil_rpy_apply_noalloc": [ctypes.c_int64, P, P, P, ctypes.c_double, ctypes.c_double, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -210,6 +211,15 @@ def fil_profile_read(ctx):
     n, ms = ctypes.c_int64(), ctypes.c_double()
     _check(ctx, _lib.fil_profile_read(ctx, ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def fil_rpy_apply_noalloc(n_seg, Y, FT, VW, a=1.0, eta=1.0, stream=None):
+    """Context-free mixed-precision RPY apply that allocates nothing (device
+    arrays only; see include/fil.h for the limits and the sharing rules)."""
+    st = _lib.fil_rpy_apply_noalloc(int(n_seg), _ptr(Y), _ptr(FT), _ptr(VW), float(a),
+                                    float(eta), ctypes.c_void_p(stream) if stream else None)
+    if st != FIL_OK:
+        raise FilError(st, "fil_rpy_apply_noalloc")
 
 
 class Filaments:
