@@ -121,15 +121,17 @@ def cpu_baseline(Y, FT, seconds=10.0):
             "sample": "%d target rows x %d sources of one mobility apply (%.1f s)" % (n, S, dt)}
 
 
-def traffic_from_profile(kernel_src):
-    """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current source of the kernel (else None)."""
+def traffic_from_profile():
+    """DRAM bytes per launch of the pair kernel from the committed ncu record,
+    if it was taken on the current kernel sources (else None)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "rpy_pair32_suspension32k_counters.json")
+    path = os.path.join(ROOT, "profiles", "rpy_pair32_32k_counters.json")
     try:
         rec = json.load(open(path))
-        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-        if rec.get("source_sha256") == h:
+        m = hashlib.sha256()
+        for src in rec["sources"]:
+            m.update(open(os.path.join(ROOT, src), "rb").read())
+        if rec.get("source_sha256") == m.hexdigest():
             return rec.get("dram_bytes_per_launch")
     except Exception:
         pass
@@ -167,6 +169,18 @@ def run_reference(args, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def aggregate_ranks(units, ms, dist, device):
+    """(sum of units over ranks, max of device time over ranks); one rank: as is."""
+    if dist is None:
+        return units, ms
+    import torch
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u[0]), float(t[0])
 
 
 def run_mobility(args, fil, torch):
@@ -287,20 +301,13 @@ def main():
     local_val = pairs / (dev_ms * 1e-3)
 
     # whole-job aggregate: units of all ranks over the slowest rank's time
-    tot_pairs, max_ms = pairs, dev_ms
-    if dist is not None:
-        tt = torch.tensor([pairs, dev_ms], dtype=torch.float64, device="cuda")
-        p_all = tt.clone()
-        dist.all_reduce(p_all[:1], op=dist.ReduceOp.SUM)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.MAX)
-        tot_pairs, max_ms = float(p_all[0]), float(tt[1])
+    tot_pairs, max_ms = aggregate_ranks(pairs, dev_ms, dist, "cuda")
     value = tot_pairs / (max_ms * 1e-3)
 
     # ---- dominant kernel: the RPY pair kernel, timed live by the library ----
     pair_avg_ms = pair_ms / max(n_pair_launch, 1)
     achieved = FLOPS_PER_PAIR * float(S) * S / (pair_avg_ms * 1e-3) / 1e12
-    kernel_src = os.path.join(ROOT, "paper_1903_12609_gb300", "csrc", "rpy.cu")
-    traffic = traffic_from_profile(kernel_src) if prec == fil.FIL_MIXED else None
+    traffic = traffic_from_profile() if prec == fil.FIL_MIXED else None
 
     # ---- end to end through the C ABI with host buffers ----
     Yh = np.zeros((S, 3)); qh = np.zeros((S, 4)); Yph = np.zeros((S, 3)); uh = np.zeros((S, 3))
