@@ -151,10 +151,13 @@ fil_status fil_mobility_apply(fil_ctx *c, const double *Y, const double *FT, dou
  * finf is not NULL, ||f||_inf. */
 fil_status fil_residual(fil_ctx *c, const double *X, double *f, double *finf);
 
-/* Start a timestep (set-up of Algorithm 2): initial guess X_0 (Y_1
- * extrapolated linearly, u = u^j, Lambda = Lambda^j; first step Y_1^j, 0,
- * Lambda^j), J0 of App. B.2 at X_0 assembled and LU-factored per filament,
- * f(X_0). Writes ||f(X_0)||_inf to *finf if not NULL. */
+/* Start a timestep (set-up of Algorithm 2): initial guess X_0 (each unknown
+ * extrapolated linearly from the two previous steps, 2 x^j - x^{j-1}, where
+ * both exist: Y_1 whenever Y^{j-1} is known, u and Lambda once two steps were
+ * committed since the last fil_set_state / fil_init_straight; otherwise the
+ * last value, with u = 0 on the first step), J0 at X_0 (App. B.2, or the
+ * filament-RPY variant) assembled and factored per filament, f(X_0). Writes
+ * ||f(X_0)||_inf to *finf if not NULL. */
 fil_status fil_broyden_begin(fil_ctx *c, double *finf);
 
 /* One pass of Algorithm 2's loop: dX_k = -H_k f(X_k), X_{k+1} = X_k + dX_k,

@@ -18,8 +18,10 @@ Layouts
 Readings where the paper is silent (each also listed in the design notes):
 * First step (no Y^{j-1}): backward Euler, f^1 = Y - Y^j - dt V,
   f^2 = u - dt dexpinv_u(Omega); BDF2 from the second step on.
-* Initial guess of a step: Y_1 = 2 Y_1^j - Y_1^{j-1} (Y_1^j on the first
-  step), u = u^j (0 on the first step), Lambda = Lambda^j.
+* Initial guess of a step: every unknown linearly extrapolated from the two
+  previous steps, x_0 = 2 x^j - x^{j-1}, when both exist (Y_1 from the BDF2
+  history; u and Lambda from the last two committed steps); with one previous
+  step u = u^j and Lambda = Lambda^j; on the first step Y_1^j, u = 0, Lambda^j.
 * Convergence: ||f||_inf <= tol * a (Sec. 3.3 states the tolerance for the
   infinity norm relative to a). Norms in Algorithm 2 are the 2-norm over the
   whole system.
@@ -213,20 +215,24 @@ class External:
 
 @dataclass
 class State:
-    """BDF2 history: Y^j, Y^{j-1} (None before the first step), q^j, u^j, Lambda^j."""
+    """BDF2 history: Y^j, Y^{j-1} (None before the first step), q^j, u^j, Lambda^j,
+    and for the initial guess u^{j-1}, Lambda^{j-1} (None until two steps exist)."""
     Y: np.ndarray
     q: np.ndarray
     Yprev: np.ndarray | None = None
     u: np.ndarray | None = None
     lam: np.ndarray | None = None
     steps: int = 0
+    u_prev: np.ndarray | None = None
+    lam_prev: np.ndarray | None = None
     extra: dict = field(default_factory=dict)
 
     def copy(self):
-        return State(Y=self.Y.copy(), q=self.q.copy(),
-                     Yprev=None if self.Yprev is None else self.Yprev.copy(),
-                     u=None if self.u is None else self.u.copy(),
-                     lam=None if self.lam is None else self.lam.copy(), steps=self.steps)
+        def cp(a):
+            return None if a is None else a.copy()
+        return State(Y=self.Y.copy(), q=self.q.copy(), Yprev=cp(self.Yprev), u=cp(self.u),
+                     lam=cp(self.lam), steps=self.steps, u_prev=cp(self.u_prev),
+                     lam_prev=cp(self.lam_prev))
 
 
 # --------------------------------------------------------------------------
@@ -635,13 +641,19 @@ class Broyden:
 # --------------------------------------------------------------------------
 
 def initial_guess(lay: Layout, state: State):
-    """X_0 of a step: Y_1 extrapolated linearly, u = u^j, Lambda = Lambda^j."""
+    """X_0 of a step: each unknown extrapolated linearly from the two previous
+    steps where both exist (x_0 = 2 x^j - x^{j-1}), else the last value."""
     Y1 = np.array([state.Y[lay.off_seg[i]] for i in range(lay.M)])
     if state.Yprev is not None:
         Y1 = 2.0 * Y1 - np.array([state.Yprev[lay.off_seg[i]] for i in range(lay.M)])
-    u = state.u.copy() if (state.u is not None and state.Yprev is not None) \
-        else np.zeros((lay.S, 3))
-    lam = state.lam.copy() if state.lam is not None else np.zeros((lay.n_lam, 3))
+    if state.u is not None and state.Yprev is not None:
+        u = 2.0 * state.u - state.u_prev if state.u_prev is not None else state.u.copy()
+    else:
+        u = np.zeros((lay.S, 3))
+    if state.lam is not None:
+        lam = 2.0 * state.lam - state.lam_prev if state.lam_prev is not None else state.lam.copy()
+    else:
+        lam = np.zeros((lay.n_lam, 3))
     return lay.join_X(Y1, u, lam)
 
 
@@ -665,9 +677,13 @@ def begin_step(lay: Layout, p: Params, state: State, ext: External | None, nthre
 
 
 def commit_step(lay: Layout, p: Params, state: State, X):
-    """q^{j+1} = exp(u*) q^j, Y^{j+1} from the robot arm, and the history shift."""
+    """q^{j+1} = exp(u*) q^j, Y^{j+1} from the robot arm, and the history shift.
+    u^{j-1}, Lambda^{j-1} are kept only when they came from a committed step."""
     q, t, Y, u, lam = unpack(lay, p, X, state.q)
-    return State(Y=Y, q=q, Yprev=state.Y.copy(), u=u, lam=lam, steps=state.steps + 1)
+    stepped = state.steps >= 1
+    return State(Y=Y, q=q, Yprev=state.Y.copy(), u=u, lam=lam, steps=state.steps + 1,
+                 u_prev=state.u.copy() if (stepped and state.u is not None) else None,
+                 lam_prev=state.lam.copy() if (stepped and state.lam is not None) else None)
 
 
 def step(lay: Layout, p: Params, state: State, ext: External | None, nthreads=1,

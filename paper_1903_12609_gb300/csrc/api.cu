@@ -94,6 +94,8 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->q = ar.take<double>(4 * S);
     c->uprev = ar.take<double>(3 * S);
     c->lam = ar.take<double>(3 * (nlam > 0 ? nlam : 1));
+    c->uprev2 = ar.take<double>(3 * S);
+    c->lamprev = ar.take<double>(3 * (nlam > 0 ? nlam : 1));
     c->Fext = ar.take<double>(3 * S);
     c->Text = ar.take<double>(3 * S);
     c->follower = ar.take<double>(M);
@@ -220,7 +222,7 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
         jofs[i + 1] = jofs[i] + (int64_t)36 * c->N_host[i] * c->N_host[i];
     c->jdense_len = jofs[p->n_fil];
     c->stream = (cudaStream_t)p->stream;
-    c->have_prev = 0; c->steps = 0; c->k = 0; c->in_step = 0;
+    c->have_prev = 0; c->hist = 0; c->steps = 0; c->k = 0; c->in_step = 0;
     c->has_Fext = c->has_Text = c->has_follower = 0;
     c->n_applies = c->n_iters = 0;
     c->iters_step = 0; c->conv = 0;
@@ -331,6 +333,7 @@ fil_status fil_set_state(fil_ctx *c, const double *Y, const double *q, const dou
     }
     CK(cudaStreamSynchronize(c->stream));
     c->have_prev = Yprev ? 1 : 0;
+    c->hist = 0;
     c->in_step = 0;
     return FIL_OK;
 }
@@ -374,6 +377,7 @@ fil_status fil_init_straight(fil_ctx *c, const double *base, const double *t, co
     if (c->lay.nlam > 0) CK(cudaMemsetAsync(c->lam, 0, sizeof(double) * 3 * c->lay.nlam, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->have_prev = 0;
+    c->hist = 0;
     c->in_step = 0;
     return FIL_OK;
 }
@@ -524,6 +528,7 @@ fil_status fil_broyden_commit(fil_ctx *c) {
     CK(cudaSetDevice(c->device));
     CK(commit_state(c, c->Xk));
     c->have_prev = 1;
+    c->hist += 1;
     c->steps += 1;
     c->in_step = 0;
     return FIL_OK;

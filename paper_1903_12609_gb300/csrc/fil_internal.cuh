@@ -8,32 +8,12 @@
 #include <vector>
 
 #include "../../include/fil.h"
+#include "rpy_config.cuh"
 
 namespace fil {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kProfMax = 4096;   // timed pair-kernel launches kept per read
-
-// ----------------------------------------------------------------------------
-// RPY pair-kernel geometry (shared by the launcher and the kernels).
-// ----------------------------------------------------------------------------
-// Tile shape of the FP32 pair kernel; the defaults are the tuned values and the
-// macros only exist so that tile-shape sweeps can rebuild the library.
-#ifndef FIL_RPY_TPT
-#define FIL_RPY_TPT 2
-#endif
-#ifndef FIL_RPY_UNROLL
-#define FIL_RPY_UNROLL 8
-#endif
-#ifndef FIL_RPY_MINB
-#define FIL_RPY_MINB 1
-#endif
-constexpr int kRpyThreads = 128;               // threads per CTA
-constexpr int kRpyUnroll = FIL_RPY_UNROLL;     // unroll of the per-source loop
-constexpr int kRpyTargetsPerThread = FIL_RPY_TPT;   // register-blocked targets
-constexpr int kRpyTile = kRpyThreads * kRpyTargetsPerThread;   // targets per tile
-constexpr int kRpyChunk = 64;                  // sources per shared-memory chunk
-constexpr int kRpyComp = 32;                   // sources per compensated partial (FP32)
 
 // ----------------------------------------------------------------------------
 // J0 band geometry: after eliminating Y_1 and differencing the constraint rows
@@ -73,9 +53,11 @@ struct fil_ctx {
     int device, num_sms;
     std::string err;
 
-    // time-integration state
-    double *Y, *Yprev, *q, *uprev, *lam;
+    // time-integration state (uprev2, lamprev: u and Lambda one step further
+    // back, used by the initial guess once hist >= 2)
+    double *Y, *Yprev, *q, *uprev, *lam, *uprev2, *lamprev;
     int have_prev;
+    int hist;              // steps committed since the last set_state / init
     int64_t steps;
 
     // external loads

@@ -192,12 +192,16 @@ __global__ void init_straight_kernel(Layout lay, const double *__restrict__ base
     }
 }
 
-// X_0 of a step: Y_1 = 2 Y_1^j - Y_1^{j-1} (Y_1^j on the first step),
-// u = u^j (0 on the first step), Lambda = Lambda^j. One thread per segment.
+// X_0 of a step: each unknown extrapolated linearly from the two previous
+// steps (x_0 = 2 x^j - x^{j-1}) where both exist -- Y_1 from the BDF2 history,
+// u and Lambda once two steps were committed (lin) -- else the last value
+// (u = 0 and Y_1 = Y_1^j on the first step). One thread per segment.
 __global__ void extrapolate_kernel(Layout lay, const double *__restrict__ Y,
                                    const double *__restrict__ Yprev,
                                    const double *__restrict__ uprev,
-                                   const double *__restrict__ lam, int have_prev,
+                                   const double *__restrict__ lam,
+                                   const double *__restrict__ uprev2,
+                                   const double *__restrict__ lamprev, int have_prev, int lin,
                                    double *__restrict__ X0) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= lay.S) return;
@@ -211,8 +215,18 @@ __global__ void extrapolate_kernel(Layout lay, const double *__restrict__ Y,
         if (have_prev) y1 = 2.0 * y1 - ld3(Yprev + 3 * g);
         st3(Xf, y1);
     }
-    st3(Xf + 3 + 3 * n, have_prev ? ld3(uprev + 3 * g) : v3(0, 0, 0));
-    if (n <= N - 2) st3(Xf + 3 + 3 * N + 3 * n, ld3(lam + 3 * (int64_t)(s0 - i + n)));
+    V3 u0 = v3(0, 0, 0);
+    if (have_prev) {
+        u0 = ld3(uprev + 3 * g);
+        if (lin) u0 = 2.0 * u0 - ld3(uprev2 + 3 * g);
+    }
+    st3(Xf + 3 + 3 * n, u0);
+    if (n <= N - 2) {
+        const int64_t li = 3 * (int64_t)(s0 - i + n);
+        V3 l0 = ld3(lam + li);
+        if (lin) l0 = 2.0 * l0 - ld3(lamprev + li);
+        st3(Xf + 3 + 3 * N + 3 * n, l0);
+    }
 }
 
 // History shift after convergence (qc, Yc hold the unpack of X).
@@ -220,7 +234,8 @@ __global__ void commit_kernel(Layout lay, const double *__restrict__ X,
                               const double *__restrict__ qc, const double *__restrict__ Yc,
                               double *__restrict__ Y, double *__restrict__ Yprev,
                               double *__restrict__ q, double *__restrict__ uprev,
-                              double *__restrict__ lam) {
+                              double *__restrict__ lam, double *__restrict__ uprev2,
+                              double *__restrict__ lamprev) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= lay.S) return;
     const int i = lay.fil_of[g];
@@ -231,8 +246,13 @@ __global__ void commit_kernel(Layout lay, const double *__restrict__ X,
     st3(Yprev + 3 * g, ld3(Y + 3 * g));
     st3(Y + 3 * g, ld3(Yc + 3 * g));
     st4(q + 4 * g, ld4(qc + 4 * g));
+    st3(uprev2 + 3 * g, ld3(uprev + 3 * g));
     st3(uprev + 3 * g, ld3(Xf + 3 + 3 * n));
-    if (n <= N - 2) st3(lam + 3 * (int64_t)(s0 - i + n), ld3(Xf + 3 + 3 * N + 3 * n));
+    if (n <= N - 2) {
+        const int64_t li = 3 * (int64_t)(s0 - i + n);
+        st3(lamprev + li, ld3(lam + li));
+        st3(lam + li, ld3(Xf + 3 + 3 * N + 3 * n));
+    }
 }
 
 unsigned warp_grid(int M, int threads) { return (unsigned)(((int64_t)M * 32 + threads - 1) / threads); }
@@ -275,7 +295,8 @@ cudaError_t init_straight(fil_ctx *c, const double *base, const double *t, const
 
 cudaError_t extrapolate_guess(fil_ctx *c, double *X0) {
     extrapolate_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(
-        c->lay, c->Y, c->Yprev, c->uprev, c->lam, c->have_prev, X0);
+        c->lay, c->Y, c->Yprev, c->uprev, c->lam, c->uprev2, c->lamprev, c->have_prev,
+        c->hist >= 2 ? 1 : 0, X0);
     c->n_launches += 1;
     return cudaGetLastError();
 }
@@ -283,8 +304,8 @@ cudaError_t extrapolate_guess(fil_ctx *c, double *X0) {
 cudaError_t commit_state(fil_ctx *c, const double *X) {
     cudaError_t e = unpack_forces(c, X, 0);
     if (e != cudaSuccess) return e;
-    commit_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(c->lay, X, c->qc, c->Yc, c->Y,
-                                                                    c->Yprev, c->q, c->uprev, c->lam);
+    commit_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(
+        c->lay, X, c->qc, c->Yc, c->Y, c->Yprev, c->q, c->uprev, c->lam, c->uprev2, c->lamprev);
     c->n_launches += 1;
     return cudaGetLastError();
 }
