@@ -250,14 +250,17 @@ j0_dense_assemble_kernel(Layout lay, const int64_t *__restrict__ jofs, const dou
 }
 
 // Inverse of each filament's J0 in FP32 by Gauss-Jordan elimination with
-// partial pivoting, in place in shared memory (one CTA per filament):
-// for each k, swap the pivot row into place, scale it by 1/pivot (the pivot
-// entry becomes 1/pivot), then eliminate column k from every other row. The
-// column-k entries of the other rows are saved and zeroed first, so that the
-// elimination is one FMA per element: a_ic <- a_ic - a_ik * p_c, which also
-// leaves -a_ik / pivot in column k. Row swaps are undone as column swaps at
-// the end. Threads own column chunks c = lane + 32 jj (jj < NCH, the pivot row
-// of those columns in registers) and rows i = warp + nwarps * r.
+// partial pivoting, in place in shared memory (one CTA per filament). Step k:
+//   (1) save column k (colk) and zero it in the matrix;
+//   (2) one warp finds the pivot row p (first maximal |a_ik|, i >= k);
+//   (3) form the scaled pivot row pr = row p / pivot with entry k = 1/pivot,
+//       and keep row k (krow) if it is displaced (p != k);
+//   (4) row k <- pr; every other row i <- row - a_ik pr, where row p starts
+//       from krow and uses the old a_kk (the swap), which also leaves
+//       -a_ik / pivot in column k.
+// Four barriers per step. Row swaps are undone as column swaps at the end.
+// Threads own column chunks c = lane + 32 jj (jj < NCH, pr in registers) and
+// rows i = warp + nwarps * r.
 template <int NCH>
 __global__ void __launch_bounds__(kInvThreads)
 gauss_jordan_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
@@ -265,9 +268,10 @@ gauss_jordan_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
                             int *__restrict__ flags) {
     extern __shared__ float Asm[];                  // n rows of stride ld = n + 1
     __shared__ float colk[kMaxInvN];
+    __shared__ float pr_s[kMaxInvN];
+    __shared__ float krow[kMaxInvN];
     __shared__ int perm[kMaxInvN];
-    __shared__ float red_v[kInvThreads / 32];
-    __shared__ int red_i[kInvThreads / 32];
+    __shared__ int pos[kMaxInvN];
     __shared__ int s_p;
     const int f = blockIdx.x;
     const int s0 = lay.off[f];
@@ -284,85 +288,191 @@ gauss_jordan_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
     for (int jj = 0; jj < NCH; ++jj) valid[jj] = (lane + 32 * jj) < n;
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-        // pivot: first row of maximal |a_ik|, i >= k
-        float v = -1.f;
-        int idx = k;
-        for (int i = k + tid; i < n; i += blockDim.x) {
-            const float a = fabsf(Asm[i * ld + k]);
-            if (a > v) { v = a; idx = i; }
+        for (int i = tid; i < n; i += blockDim.x) {
+            colk[i] = Asm[i * ld + k];
+            Asm[i * ld + k] = 0.f;
         }
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            const float ov = __shfl_down_sync(0xffffffffu, v, d);
-            const int oi = __shfl_down_sync(0xffffffffu, idx, d);
-            if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
-        }
-        if (lane == 0) { red_v[wid] = v; red_i[wid] = idx; }
         __syncthreads();
         if (wid == 0) {
-            float bv = lane < nw ? red_v[lane] : -1.f;
-            int bi = lane < nw ? red_i[lane] : 0x7fffffff;
+            float v = -1.f;
+            int idx = 0x7fffffff;
+            for (int i = k + lane; i < n; i += 32) {
+                const float x = fabsf(colk[i]);
+                if (x > v) { v = x; idx = i; }
+            }
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) {
-                const float ov = __shfl_down_sync(0xffffffffu, bv, d);
-                const int oi = __shfl_down_sync(0xffffffffu, bi, d);
-                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+                const float ov = __shfl_down_sync(0xffffffffu, v, d);
+                const int oi = __shfl_down_sync(0xffffffffu, idx, d);
+                if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
             }
             if (lane == 0) {
-                s_p = bi;
-                perm[k] = bi;
-                if (!(bv > 0.f)) atomicOr(flags + 1, 1);
+                s_p = idx;
+                perm[k] = idx;
+                if (!(v > 0.f)) atomicOr(flags + 1, 1);
             }
         }
         __syncthreads();
         const int p = s_p;
-        if (p != k)
-            for (int c = tid; c < n; c += blockDim.x) {
-                const float t = Asm[k * ld + c];
-                Asm[k * ld + c] = Asm[p * ld + c];
-                Asm[p * ld + c] = t;
-            }
-        __syncthreads();
-        const float pinv = 1.f / Asm[k * ld + k];
-        // save and zero column k of the other rows; scale the pivot row
-        for (int i = tid; i < n; i += blockDim.x) {
-            if (i != k) {
-                colk[i] = Asm[i * ld + k];
-                Asm[i * ld + k] = 0.f;
-            } else {
-                colk[i] = 0.f;
-            }
+        const float pinv = 1.f / colk[p];
+        for (int c = tid; c < n; c += blockDim.x) {
+            pr_s[c] = (c == k) ? pinv : Asm[p * ld + c] * pinv;
+            krow[c] = Asm[k * ld + c];
         }
-        __syncthreads();
-        for (int c = tid; c < n; c += blockDim.x)
-            Asm[k * ld + c] = (c == k) ? pinv : Asm[k * ld + c] * pinv;
         __syncthreads();
         float pr[NCH];
 #pragma unroll
-        for (int jj = 0; jj < NCH; ++jj) pr[jj] = valid[jj] ? Asm[k * ld + lane + 32 * jj] : 0.f;
+        for (int jj = 0; jj < NCH; ++jj) pr[jj] = valid[jj] ? pr_s[lane + 32 * jj] : 0.f;
         for (int i = wid; i < n; i += nw) {
-            if (i == k) continue;
-            const float mf = -colk[i];
             float *row = Asm + i * ld + lane;
+            if (i == k) {
 #pragma unroll
-            for (int jj = 0; jj < NCH; ++jj)
-                if (valid[jj]) row[32 * jj] = fmaf(mf, pr[jj], row[32 * jj]);
+                for (int jj = 0; jj < NCH; ++jj)
+                    if (valid[jj]) row[32 * jj] = pr[jj];
+            } else if (i == p) {
+                const float mf = -colk[k];
+#pragma unroll
+                for (int jj = 0; jj < NCH; ++jj)
+                    if (valid[jj]) row[32 * jj] = fmaf(mf, pr[jj], krow[lane + 32 * jj]);
+            } else {
+                const float mf = -colk[i];
+#pragma unroll
+                for (int jj = 0; jj < NCH; ++jj)
+                    if (valid[jj]) row[32 * jj] = fmaf(mf, pr[jj], row[32 * jj]);
+            }
         }
         __syncthreads();
     }
-    // undo the row interchanges as column interchanges, last first
-    for (int k = n - 1; k >= 0; --k) {
-        const int p = perm[k];
-        if (p != k)
-            for (int i = tid; i < n; i += blockDim.x) {
-                const float t = Asm[i * ld + k];
-                Asm[i * ld + k] = Asm[i * ld + p];
-                Asm[i * ld + p] = t;
-            }
-        __syncthreads();
+    // row interchanges undone as column interchanges, last first: column c of
+    // the result is column idx[c] of the current matrix; pos is its inverse
+    if (tid == 0) {
+        for (int c = 0; c < n; ++c) krow[c] = __int_as_float(c);
+        for (int k = n - 1; k >= 0; --k) {
+            const float t = krow[k];
+            krow[k] = krow[perm[k]];
+            krow[perm[k]] = t;
+        }
+        for (int c = 0; c < n; ++c) pos[__float_as_int(krow[c])] = c;
     }
+    __syncthreads();
     for (int i = wid; i < n; i += nw)
-        for (int c = lane; c < n; c += 32) out[(int64_t)i * n + c] = Asm[i * ld + c];
+        for (int c = lane; c < n; c += 32) out[(int64_t)i * n + pos[c]] = Asm[i * ld + c];
+}
+
+// Register-resident Gauss-Jordan inverse for blocks of n <= 192 (N <= 32),
+// with implicit pivoting. Thread (w, l) of 16 warps holds rows i = w + 16 r
+// (r < 12) and columns c = l + 32 j (j < 6) in registers. Step k pivots column
+// k on the unused row p of largest |a_pk| (recorded, never swapped) and applies
+//   a_i <- s_i a_i + t_i pr,   pr = row p / a_pk with entry k = 1/a_pk,
+// with (s, t) = (0, 1) for row p and (1, -a_ik) otherwise, after column k has
+// been zeroed -- the in-place Gauss-Jordan update, uniform over all rows. The
+// step loop is unrolled over the six 32-column chunks so that column k has a
+// static register index. The result is A^{-1} with rows and columns permuted:
+// A^{-1}[k][m] = S[p_k][q(m)], p_k the pivot row of column k and q its inverse.
+constexpr int kGjWarps = 16, kGjRows = 12, kGjCols = 6, kGjMaxN = 32 * kGjCols;  // 192
+
+__global__ void __launch_bounds__(32 * kGjWarps, 1)
+gauss_jordan_inverse_reg_kernel(Layout lay, const int64_t *__restrict__ jofs,
+                                const double *__restrict__ J_all, float *__restrict__ inv_all,
+                                int *__restrict__ flags) {
+    __shared__ float colk[kGjMaxN];
+    __shared__ float prow[kGjMaxN];
+    __shared__ int used[kGjMaxN];
+    __shared__ int pivrow[kGjMaxN];
+    __shared__ int qinv[kGjMaxN];
+    __shared__ int s_p;
+    const int f = blockIdx.x;
+    const int s0 = lay.off[f];
+    const int n = 6 * (lay.off[f + 1] - s0);
+    const double *J = J_all + jofs[f];
+    float *out = inv_all + jofs[f];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    float a[kGjRows][kGjCols];
+#pragma unroll
+    for (int r = 0; r < kGjRows; ++r)
+#pragma unroll
+        for (int j = 0; j < kGjCols; ++j) {
+            const int i = wid + kGjWarps * r, c = lane + 32 * j;
+            a[r][j] = (i < n && c < n) ? (float)J[(int64_t)i * n + c] : 0.f;
+        }
+    for (int i = tid; i < kGjMaxN; i += blockDim.x) used[i] = (i < n) ? 0 : 1;
+    __syncthreads();
+#pragma unroll
+    for (int kj = 0; kj < kGjCols; ++kj) {
+        for (int kl = 0; kl < 32; ++kl) {
+            const int k = 32 * kj + kl;
+            if (k >= n) break;
+            // (1) column k -> colk (held by lane kl), then zero it
+            if (lane == kl) {
+#pragma unroll
+                for (int r = 0; r < kGjRows; ++r) {
+                    colk[wid + kGjWarps * r] = a[r][kj];
+                    a[r][kj] = 0.f;
+                }
+            }
+            __syncthreads();
+            // (2) pivot: unused row of largest |a_ik| (first such), by warp 0
+            if (wid == 0) {
+                float v = -1.f;
+                int idx = 0x7fffffff;
+                for (int i = lane; i < n; i += 32) {
+                    const float x = used[i] ? -1.f : fabsf(colk[i]);
+                    if (x > v) { v = x; idx = i; }
+                }
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) {
+                    const float ov = __shfl_down_sync(0xffffffffu, v, d);
+                    const int oi = __shfl_down_sync(0xffffffffu, idx, d);
+                    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+                }
+                if (lane == 0) {
+                    s_p = idx;
+                    pivrow[k] = idx;
+                    used[idx] = 1;
+                    if (!(v > 0.f)) atomicOr(flags + 1, 1);
+                }
+            }
+            __syncthreads();
+            const int p = s_p;
+            // (3) row p -> prow (its owner warp; static registers, predicated stores)
+            if (wid == p % kGjWarps) {
+                const int pr = p / kGjWarps;
+#pragma unroll
+                for (int r = 0; r < kGjRows; ++r)
+                    if (r == pr)
+#pragma unroll
+                        for (int j = 0; j < kGjCols; ++j) prow[lane + 32 * j] = a[r][j];
+            }
+            __syncthreads();
+            // (4) a_i <- s_i a_i + t_i pr for every row
+            const float pinv = 1.f / colk[p];
+            float pr_r[kGjCols];
+#pragma unroll
+            for (int j = 0; j < kGjCols; ++j) {
+                const int c = lane + 32 * j;
+                pr_r[j] = (c == k) ? pinv : prow[c] * pinv;
+            }
+#pragma unroll
+            for (int r = 0; r < kGjRows; ++r) {
+                const int i = wid + kGjWarps * r;
+                const float sc = (i == p) ? 0.f : 1.f;
+                const float t = (i == p) ? 1.f : -colk[i];
+#pragma unroll
+                for (int j = 0; j < kGjCols; ++j) a[r][j] = fmaf(t, pr_r[j], sc * a[r][j]);
+            }
+            __syncthreads();
+        }
+    }
+    // A^{-1}[k][m] = S[p_k][q(m)]: element S[i][c] goes to out[q(i)][p_c]
+    for (int k = tid; k < n; k += blockDim.x) qinv[pivrow[k]] = k;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kGjRows; ++r)
+#pragma unroll
+        for (int j = 0; j < kGjCols; ++j) {
+            const int i = wid + kGjWarps * r, c = lane + 32 * j;
+            if (i < n && c < n) out[(int64_t)qinv[i] * n + pivrow[c]] = a[r][j];
+        }
 }
 
 // Refined solve, as grid-wide GEMV phases over every row of every filament
@@ -459,9 +569,17 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
     if (e != cudaSuccess) return e;
     j0_dense_assemble_kernel<<<c->lay.M, kAsmThreads, smem_asm, c->stream>>>(
         c->lay, c->jofs, X, c->qc, c->Yc, c->Tint, dp, c->jdense);
-    const size_t smem_inv = (size_t)6 * N * (6 * N + 1) * sizeof(float);
-    const int nch = (6 * N + 31) / 32;
-    e = launch_gauss_jordan(c, nch, smem_inv);
+#ifndef FIL_GJ_SHARED_ONLY
+    if (6 * N <= kGjMaxN) {
+        gauss_jordan_inverse_reg_kernel<<<c->lay.M, 32 * kGjWarps, 0, c->stream>>>(
+            c->lay, c->jofs, c->jdense, c->jinv, c->d_flags);
+        e = cudaGetLastError();
+    } else
+#endif
+    {
+        const size_t smem_inv = (size_t)6 * N * (6 * N + 1) * sizeof(float);
+        e = launch_gauss_jordan(c, (6 * N + 31) / 32, smem_inv);
+    }
     if (e != cudaSuccess) return e;
     c->n_launches += 2;
     return cudaGetLastError();

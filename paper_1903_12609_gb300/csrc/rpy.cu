@@ -140,8 +140,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// 1/sqrt(x) for normal x > 0: one MUFU operation (PTX rsqrt.approx.ftz.f32,
-// max relative error 2^-22.9). Used only for r^2 >= (2a)^2, never on denormals.
+// 1/sqrt(x): one MUFU operation (PTX rsqrt.approx.ftz.f32, max relative error
+// 2^-22.9 for normal x). Its results are kept only for r^2 >= (2a)^2.
 __device__ __forceinline__ float rsqrt_approx(float x) {
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -189,10 +189,11 @@ __device__ __forceinline__ void pair32(float thx, float thy, float thz, float tl
     acc[5] = fmaf(C, Tz, fmaf(dT, dz, fmaf(Fx, ey, fmaf(-Fy, ex, acc[5]))));
 }
 
-// The far-form pair term for every pair, branch-free: r^2 is clamped at contact
-// ((2a)^2) so the coefficients stay finite for overlapping and coincident
-// pairs, and the smallest r^2 seen is tracked. A group of sources in which a
-// warp saw r^2 < (2a)^2 is recomputed with pair32 (exact branches).
+// The far-form pair term for every pair, branch-free, tracking the smallest
+// r^2 seen. A group of sources in which a warp saw r^2 < (2a)^2 is recomputed
+// from zero with pair32 (exact branches), so whatever this form produced for
+// overlapping or coincident pairs there (possibly Inf/NaN at r = 0) is
+// discarded; for every other group r^2 >= (2a)^2 and the terms are finite.
 __device__ __forceinline__ void pair32_far(float thx, float thy, float thz, float tlx, float tly,
                                            float tlz, const float4 s0, const float4 s1,
                                            const float4 s2, const RpyConst32 &k, float *acc,
@@ -202,7 +203,7 @@ __device__ __forceinline__ void pair32_far(float thx, float thy, float thz, floa
     const float dz = __fsub_rn(thz, s0.z) + __fsub_rn(tlz, s1.z);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     rmin2 = fminf(rmin2, r2);
-    const float rinv = rsqrt_approx(fmaxf(r2, k.near2));
+    const float rinv = rsqrt_approx(r2);
     const float rinv2 = rinv * rinv;
     const float rinv3 = rinv * rinv2;
     const float rinv5 = rinv3 * rinv2;
@@ -313,12 +314,14 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
         for (int64_t ch = c_begin; ch < c_end; ++ch) {
             const int buf = (int)((ch - c_begin) & 1);
             // prefetch the next chunk into registers while computing this one
-            float4 pre0 = make_float4(0.f, 0.f, 0.f, 0.f), pre1 = pre0;
+            constexpr int kPre = (kRec + kRpyThreads - 1) / kRpyThreads;
+            float4 pre[kPre];
             const bool has_next = (ch + 1 < c_end);
             if (has_next) {
                 const float4 *g = src + 3 * ((ch + 1) * kRpyChunk);
-                pre0 = g[tid];
-                if (tid + kRpyThreads < kRec) pre1 = g[tid + kRpyThreads];
+#pragma unroll
+                for (int r = 0; r < kPre; ++r)
+                    if (tid + r * kRpyThreads < kRec) pre[r] = g[tid + r * kRpyThreads];
             }
             const float4 *s = sm[buf];
 #pragma unroll 1
@@ -365,8 +368,9 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
                     }
             }
             if (has_next) {
-                sm[buf ^ 1][tid] = pre0;
-                if (tid + kRpyThreads < kRec) sm[buf ^ 1][tid + kRpyThreads] = pre1;
+#pragma unroll
+                for (int r = 0; r < kPre; ++r)
+                    if (tid + r * kRpyThreads < kRec) sm[buf ^ 1][tid + r * kRpyThreads] = pre[r];
             }
             __syncthreads();
         }

@@ -21,7 +21,7 @@ constexpr int kRpyThreads = 128;               // threads per CTA
 constexpr int kRpyUnroll = FIL_RPY_UNROLL;     // unroll of the per-source loop
 constexpr int kRpyTargetsPerThread = FIL_RPY_TPT;   // register-blocked targets
 constexpr int kRpyTile = kRpyThreads * kRpyTargetsPerThread;   // targets per tile
-constexpr int kRpyChunk = 64;                  // sources per shared-memory chunk
+constexpr int kRpyChunk = 128;                 // sources per shared-memory chunk
 constexpr int kRpyComp = 32;                   // sources per compensated partial (FP32)
 
 }  // namespace fil
