@@ -128,15 +128,17 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->d_flags = sb ? sb->flags : nullptr;
     if (c->j0_model == FIL_J0_DRAG) {
         c->band = ar.take<double>((size_t)nband * kBandW);
-        c->jdense = nullptr;
         c->jinv = nullptr;
         c->jofs = nullptr;
+        c->aux = nullptr;
+        c->auxofs = nullptr;
         c->j0_rhs = c->j0_x = c->j0_res = nullptr;
     } else {
         c->band = nullptr;
-        c->jdense = ar.take<double>((size_t)c->jdense_len);
         c->jinv = ar.take<float>((size_t)c->jdense_len);
         c->jofs = ar.take<int64_t>(M + 1);
+        c->aux = ar.take<double>((size_t)c->aux_len);
+        c->auxofs = ar.take<int64_t>(M + 1);
         c->j0_rhs = ar.take<double>(nX);
         c->j0_x = ar.take<double>(nX);
         c->j0_res = ar.take<double>(nX);
@@ -217,10 +219,14 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
     c->g0 = p->gamma0; c->kmu = p->kappa_mu; c->knu = p->kappa_nu;
     c->dt = p->dt; c->tol = p->tol; c->max_iter = p->max_iter; c->prec = p->precision;
     c->j0_model = p->j0_model;
-    std::vector<int64_t> jofs(p->n_fil + 1, 0);
-    for (int i = 0; i < p->n_fil; ++i)
-        jofs[i + 1] = jofs[i] + (int64_t)36 * c->N_host[i] * c->N_host[i];
+    std::vector<int64_t> jofs(p->n_fil + 1, 0), auxofs(p->n_fil + 1, 0);
+    for (int i = 0; i < p->n_fil; ++i) {
+        const int64_t Ni = c->N_host[i];
+        jofs[i + 1] = jofs[i] + 36 * Ni * Ni;
+        auxofs[i + 1] = auxofs[i] + 60 * Ni + 5 * Ni * Ni;   // layout in jacobian_dense.cu
+    }
     c->jdense_len = jofs[p->n_fil];
+    c->aux_len = auxofs[p->n_fil];
     c->stream = (cudaStream_t)p->stream;
     c->have_prev = 0; c->hist = 0; c->steps = 0; c->k = 0; c->in_step = 0;
     c->has_Fext = c->has_Text = c->has_follower = 0;
@@ -277,6 +283,9 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
                             c->stream);
     if (e == cudaSuccess && c->jofs)
         e = cudaMemcpyAsync(c->jofs, jofs.data(), sizeof(int64_t) * (p->n_fil + 1),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && c->auxofs)
+        e = cudaMemcpyAsync(c->auxofs, auxofs.data(), sizeof(int64_t) * (p->n_fil + 1),
                             cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bail(FIL_ECUDA, "initial upload", e);

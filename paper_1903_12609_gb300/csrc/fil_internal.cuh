@@ -93,11 +93,14 @@ struct fil_ctx {
     int j0_model;
     double *band;
     int *piv;
-    double *jdense;
-    float *jinv;           // FP32 inverse of each dense block (same offsets)
-    double *j0_rhs, *j0_x, *j0_res;   // refinement scratch (6S each)
-    int64_t *jofs;         // [M+1] offsets of the dense blocks
+    float *jinv;           // per filament: FP32 J0, then its inverse in place
+    int64_t *jofs;         // [M+1] offsets of the (6N)^2 blocks
     int64_t jdense_len;
+    double *aux;           // per-filament FP64 data of J0 (matrix-free residual)
+    int64_t *auxofs;       // [M+1]
+    int64_t aux_len;
+    double j0_dp_bdt;      // scheme weight * dt of the current J0
+    double *j0_rhs, *j0_x, *j0_res;   // refinement scratch (6S each)
 
     // staging for host pointers (6S doubles each)
     double *stage_a, *stage_b, *stage_c;
@@ -131,7 +134,6 @@ cudaError_t j0_build_factor(fil_ctx *c, const double *X);
 cudaError_t j0_solve(fil_ctx *c, const double *b, double *x);
 cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X);
 cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x);
-size_t j0_dense_smem_needed(int maxN);
 
 cudaError_t broyden_axpy_step(fil_ctx *c);                 // Xn = Xk - w
 cudaError_t broyden_dots(fil_ctx *c);                      // alpha_i, ndf2, dff

@@ -17,13 +17,19 @@
 // coupling along a filament, which the drag model drops and which makes
 // Broyden need O(number of filaments) iterations in dense suspensions.
 //
-// Storage: row-major (6N)^2 FP64 block per filament at jofs[i] (kept for the
-// refinement residuals) and its inverse in FP32 at the same offsets, computed
-// by Gauss-Jordan elimination with partial pivoting in shared memory (one CTA
-// per filament; FP32 runs at 64x the FP64 rate on this part). A solve applies
-// the FP32 inverse and then kJ0Refine steps of iterative refinement with FP64
-// residuals b - J0 x, which brings x to FP64 accuracy (each step multiplies
-// the error by ~cond(J0) * 2^-24).
+// Per step and filament:
+//   1. j0_precompute_kernel (FP64): frames, Lambda sums, dexpinv matrices A_n,
+//      the u-diagonal dexpinv terms Du_n, the load derivatives dT_m/du_m, the
+//      joint moment derivatives Da, Db, the angular velocity of the internal
+//      loads and every pair's RPY coefficients -> a per-filament aux block.
+//   2. j0_assemble32_kernel (FP32): the (6N)^2 matrix J0 from the aux block,
+//      written into the inverse buffer and inverted there in FP32 by
+//      Gauss-Jordan elimination (FP32 runs at 64x the FP64 rate on this part).
+// A solve applies the FP32 inverse and then kJ0Refine steps of iterative
+// refinement x += Inv (b - J0 x), with b - J0 x evaluated matrix-free in FP64
+// from the aux block (j0_residual_mf_kernel) -- the same operator as the
+// dense definition -- so x reaches FP64 accuracy (each step multiplies the
+// error by ~cond(J0) * 2^-24).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -84,160 +90,228 @@ __device__ __forceinline__ void apply_pair(const PairCoef &k, V3 d, V3 v, V3 w, 
     W = W + k.G * cross(v, d) + k.C * w + (k.D * dot(d, w)) * d;
 }
 
-__device__ __forceinline__ V3 col(const M33 &m, int c) { return {m.m[c], m.m[3 + c], m.m[6 + c]}; }
-
-// Per-segment data staged in shared memory for one filament.
-struct SegSmem {
-    double *Y, *t, *u, *Ls, *Fi, *Ti, *Om;   // 3N each
-    double *Q;                                // 4N
+// Aux block of one filament with N segments, 60 N + 5 N^2 doubles, offsets in units of N:
+//   t 3N | Ls 3N | u 3N | Om 3N | Y 3N | A 9N | Du 9N | dTmm 9N | Da 9N | Db 9N | pc 5N^2
+// (everything at the X where J0 was built: the solves of later iterates must
+// apply the same operator)
+// (Da, Db: joint m between segments m and m+1; pc[n N + m] = A,B,C,D,G of the
+// pair (n, m) in units of 1/(8 pi eta)).
+struct AuxView {
+    double *t, *Ls, *u, *Om, *Y, *A, *Du, *dT, *Da, *Db, *pc;
 };
+__device__ __forceinline__ AuxView aux_view(double *base, int N) {
+    AuxView v;
+    v.t = base; v.Ls = base + 3 * N; v.u = base + 6 * N; v.Om = base + 9 * N;
+    v.Y = base + 12 * N; v.A = base + 15 * N; v.Du = base + 24 * N; v.dT = base + 33 * N;
+    v.Da = base + 42 * N; v.Db = base + 51 * N; v.pc = base + 60 * N;
+    return v;
+}
+__device__ __forceinline__ void st33(double *p, const M33 &m) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) p[i] = m.m[i];
+}
+__device__ __forceinline__ M33 ld33(const double *p) {
+    M33 m;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) m.m[i] = p[i];
+    return m;
+}
+__device__ __forceinline__ V3 mv(const M33 &m, V3 v) {
+    return {m.m[0] * v.x + m.m[1] * v.y + m.m[2] * v.z, m.m[3] * v.x + m.m[4] * v.y + m.m[5] * v.z,
+            m.m[6] * v.x + m.m[7] * v.y + m.m[8] * v.z};
+}
 
 __global__ void __launch_bounds__(kAsmThreads)
-j0_dense_assemble_kernel(Layout lay, const int64_t *__restrict__ jofs, const double *__restrict__ X,
-                         const double *__restrict__ qc, const double *__restrict__ Yc,
-                         const double *__restrict__ Tint, DenseParams dp,
-                         double *__restrict__ J_all) {
-    extern __shared__ double sm[];
+j0_precompute_kernel(Layout lay, const int64_t *__restrict__ auxofs, const double *__restrict__ X,
+                     const double *__restrict__ qc, const double *__restrict__ Yc,
+                     const double *__restrict__ Tint, DenseParams dp, double *__restrict__ aux_all) {
+    extern __shared__ double sm[];     // F_int 3N | Yrel 3N
     const int f = blockIdx.x;
     const int s0 = lay.off[f];
     const int N = lay.off[f + 1] - s0;
-    const int n6 = 6 * N;
-    double *J = J_all + jofs[f];
-    SegSmem g;
-    g.Y = sm;
-    g.t = sm + 3 * N;
-    g.u = sm + 6 * N;
-    g.Ls = sm + 9 * N;
-    g.Fi = sm + 12 * N;
-    g.Ti = sm + 15 * N;
-    g.Om = sm + 18 * N;
-    g.Q = sm + 21 * N;
+    AuxView g = aux_view(aux_all + auxofs[f], N);
+    double *Fi = sm, *Yf = sm + 3 * N;
     const double *Xf = X + 6 * (int64_t)s0;
     const double *Lam = Xf + 3 + 3 * N;
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
         const int64_t gg = s0 + n;
-        const Q4 q = ld4(qc + 4 * gg);
-        st4(g.Q + 4 * n, q);
-        st3(g.Y + 3 * n, ld3(Yc + 3 * gg));
-        st3(g.t + 3 * n, frame_t(q));
-        st3(g.u + 3 * n, ld3(Xf + 3 + 3 * n));
+        st3(g.t + 3 * n, frame_t(ld4(qc + 4 * gg)));
+        const V3 u = ld3(Xf + 3 + 3 * n);
+        st3(g.u + 3 * n, u);
         const V3 Lr = (n <= N - 2) ? ld3(Lam + 3 * n) : v3(0, 0, 0);
         const V3 Ll = (n >= 1) ? ld3(Lam + 3 * (n - 1)) : v3(0, 0, 0);
         st3(g.Ls + 3 * n, Lr + Ll);
-        st3(g.Fi + 3 * n, Lr - Ll);
-        st3(g.Ti + 3 * n, ld3(Tint + 3 * gg));
+        st3(Fi + 3 * n, Lr - Ll);
+        st3(Yf + 3 * n, ld3(Yc + 3 * gg));
+        st3(g.Y + 3 * n, ld3(Yc + 3 * gg));
+        const M33 ux = skew(u);
+        st33(g.A + 9 * n, madd(madd(meye(), ux, -0.5), mmul(ux, ux), 1.0 / 12.0));
+        if (n <= N - 2) {
+            M33 Da, Db;
+            moment_derivs(dp.jp, ld4(qc + 4 * gg), ld4(qc + 4 * (gg + 1)), Da, Db);
+            st33(g.Da + 9 * n, Da);
+            st33(g.Db + 9 * n, Db);
+        }
     }
-    for (int64_t e = threadIdx.x; e < (int64_t)n6 * n6; e += blockDim.x) J[e] = 0.0;
-    // per-pair RPY coefficients and per-joint moment derivatives, computed once
-    PairCoef *pc = reinterpret_cast<PairCoef *>(sm + 25 * N);      // N*N entries
-    M33 *DaJ = reinterpret_cast<M33 *>(sm + 25 * N + 5 * N * N);    // N-1 joints
-    M33 *DbJ = DaJ + (N > 1 ? N - 1 : 0);
     __syncthreads();
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
         const int n = e / N, m = e - (e / N) * N;
-        pc[e] = pair_coef(ld3(g.Y + 3 * n) - ld3(g.Y + 3 * m), dp.a);
+        const PairCoef k = pair_coef(ld3(Yf + 3 * n) - ld3(Yf + 3 * m), dp.a);
+        double *pc = g.pc + 5 * (int64_t)e;
+        pc[0] = k.A; pc[1] = k.B; pc[2] = k.C; pc[3] = k.D; pc[4] = k.G;
     }
-    for (int jn = threadIdx.x; jn < N - 1; jn += blockDim.x)
-        moment_derivs(dp.jp, ld4(g.Q + 4 * jn), ld4(g.Q + 4 * (jn + 1)), DaJ[jn], DbJ[jn]);
     __syncthreads();
-    // angular velocity of the internal loads, filament block only
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        // dT_n/du_n = (dL/2)[x Ls][x t] + Da(n) - Db(n-1)
+        M33 dT = mscale(mmul(rskew(ld3(g.Ls + 3 * n)), rskew(ld3(g.t + 3 * n))), 0.5 * dp.jp.dL);
+        if (n <= N - 2) dT = madd(dT, ld33(g.Da + 9 * n));
+        if (n >= 1) dT = madd(dT, ld33(g.Db + 9 * (n - 1)), -1.0);
+        st33(g.dT + 9 * n, dT);
+        // angular velocity of the internal loads within the filament
         V3 V = v3(0, 0, 0), W = v3(0, 0, 0);
-        const V3 Yn = ld3(g.Y + 3 * n);
+        const V3 Yn = ld3(Yf + 3 * n);
         for (int m = 0; m < N; ++m) {
-            const V3 d = Yn - ld3(g.Y + 3 * m);
-            apply_pair(pc[n * N + m], d, ld3(g.Fi + 3 * m), ld3(g.Ti + 3 * m), V, W);
+            const double *pc = g.pc + 5 * ((int64_t)n * N + m);
+            const PairCoef k{pc[0], pc[1], pc[2], pc[3], pc[4]};
+            apply_pair(k, Yn - ld3(Yf + 3 * m), ld3(Fi + 3 * m), ld3(Tint + 3 * (int64_t)(s0 + m)),
+                       V, W);
         }
-        st3(g.Om + 3 * n, dp.inv8pieta * W);
+        const V3 Om = dp.inv8pieta * W;
+        st3(g.Om + 3 * n, Om);
+        const V3 u = ld3(g.u + 3 * n);
+        const M33 ux = skew(u), xO = rskew(Om);
+        st33(g.Du + 9 * n, madd(mscale(xO, -0.5), madd(rskew(cross(u, Om)), mmul(ux, xO)), 1.0 / 12.0));
     }
-    __syncthreads();
+}
 
-    // tasks: (row segment n, column block x), x = 0..N-1 -> u_x, x = N..2N-2 -> Lam_{x-N}
+// FP32 helpers for the assembly.
+struct F3 {
+    float x, y, z;
+};
+__device__ __forceinline__ F3 f3v(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ float fdot(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ F3 fcross(F3 a, F3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ F3 fmad3(float s, F3 a, F3 b) {
+    return {fmaf(s, a.x, b.x), fmaf(s, a.y, b.y), fmaf(s, a.z, b.z)};
+}
+// (V, W) += M_nm (v, w) with FP32 coefficients (units of 1/(8 pi eta))
+__device__ __forceinline__ void apply_pair32(const float *c, F3 d, F3 v, F3 w, F3 &V, F3 &W) {
+    const float A = c[0], B = c[1], C = c[2], D = c[3], G = c[4];
+    V = fmad3(A, v, V);
+    V = fmad3(B * fdot(d, v), d, V);
+    V = fmad3(G, fcross(w, d), V);
+    W = fmad3(G, fcross(v, d), W);
+    W = fmad3(C, w, W);
+    W = fmad3(D * fdot(d, w), d, W);
+}
+__device__ __forceinline__ F3 mcol(const double *m9, int c) {
+    return {(float)m9[c], (float)m9[3 + c], (float)m9[6 + c]};
+}
+
+// J0 in FP32 from the aux block, written into the inverse buffer (row-major).
+__global__ void __launch_bounds__(kAsmThreads)
+j0_assemble32_kernel(Layout lay, const int64_t *__restrict__ jofs,
+                     const int64_t *__restrict__ auxofs, DenseParams dp, const double *__restrict__ aux_all, float *__restrict__ J_all) {
+    extern __shared__ float smf[];     // pc 5N^2 | Yrel 3N | t 3N
+    const int f = blockIdx.x;
+    const int s0 = lay.off[f];
+    const int N = lay.off[f + 1] - s0;
+    const int n6 = 6 * N;
+    const AuxView g = aux_view(const_cast<double *>(aux_all) + auxofs[f], N);
+    float *pcs = smf, *Ys = smf + 5 * N * N, *ts = Ys + 3 * N;
+    float *J = J_all + jofs[f];
+    const double *Y0 = g.Y;
+    for (int e = threadIdx.x; e < 5 * N * N; e += blockDim.x) pcs[e] = (float)g.pc[e];
+    for (int e = threadIdx.x; e < 3 * N; e += blockDim.x) {
+        Ys[e] = (float)(Y0[e] - Y0[e % 3]);     // positions relative to segment 0
+        ts[e] = (float)g.t[e];
+    }
+    for (int64_t e = threadIdx.x; e < (int64_t)n6 * n6; e += blockDim.x) J[e] = 0.f;
+    __syncthreads();
+    const float s = (float)(-dp.bdt * dp.inv8pieta);
+    const float hdL = (float)(0.5 * dp.jp.dL);
     const int ncol = 2 * N - 1;
     for (int task = threadIdx.x; task < N * ncol; task += blockDim.x) {
         const int n = task / ncol;
         const int x = task - n * ncol;
-        const V3 Yn = ld3(g.Y + 3 * n);
-        V3 MV[3] = {v3(0, 0, 0), v3(0, 0, 0), v3(0, 0, 0)};
-        V3 MW[3] = {v3(0, 0, 0), v3(0, 0, 0), v3(0, 0, 0)};
+        const F3 Yn = f3v(Ys[3 * n], Ys[3 * n + 1], Ys[3 * n + 2]);
+        F3 MV[3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        F3 MW[3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         int colX;
         if (x < N) {
-            // d T_m / d u_k, m = k-1, k, k+1 (App. B.2)
             const int k = x;
             colX = 3 + 3 * k;
             for (int mm = -1; mm <= 1; ++mm) {
                 const int m = k + mm;
                 if (m < 0 || m > N - 1) continue;
-                M33 Gt;
-                if (mm == -1) {
-                    Gt = DbJ[k - 1];
-                } else if (mm == 0) {
-                    Gt = mscale(mmul(rskew(ld3(g.Ls + 3 * k)), rskew(ld3(g.t + 3 * k))),
-                                0.5 * dp.jp.dL);
-                    if (k <= N - 2) Gt = madd(Gt, DaJ[k]);
-                    if (k >= 1) Gt = madd(Gt, DbJ[k - 1], -1.0);
-                } else {
-                    Gt = mscale(DaJ[k], -1.0);
+                // d T_m / d u_k: Db(k-1) for m = k-1, dT_k for m = k, -Da(k) for m = k+1
+                const double *Gt = (mm == -1) ? g.Db + 9 * (k - 1) : (mm == 0) ? g.dT + 9 * k : g.Da + 9 * k;
+                const float sg = (mm == 1) ? -1.f : 1.f;
+                const F3 d = f3v(Yn.x - Ys[3 * m], Yn.y - Ys[3 * m + 1], Yn.z - Ys[3 * m + 2]);
+                const float *c5 = pcs + 5 * (n * N + m);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    F3 w = mcol(Gt, c);
+                    w = {sg * w.x, sg * w.y, sg * w.z};
+                    apply_pair32(c5, d, f3v(0, 0, 0), w, MV[c], MW[c]);
                 }
-                const V3 d = Yn - ld3(g.Y + 3 * m);
-                const PairCoef kc = pc[n * N + m];
-                for (int c = 0; c < 3; ++c) apply_pair(kc, d, v3(0, 0, 0), col(Gt, c), MV[c], MW[c]);
             }
         } else {
-            // d(F_m, T_m)/d Lam_j for m = j (F += I) and m = j+1 (F -= I); T: (dL/2)[t_m x]
+            // d(F_m, T_m)/d Lam_j: F += I (m = j), F -= I (m = j+1); T: (dL/2)[t_m x]
             const int j = x - N;
             colX = 3 + 3 * N + 3 * j;
             for (int mm = 0; mm <= 1; ++mm) {
                 const int m = j + mm;
-                const M33 Gt = mscale(skew(ld3(g.t + 3 * m)), 0.5 * dp.jp.dL);
-                const double sF = mm == 0 ? 1.0 : -1.0;
-                const V3 d = Yn - ld3(g.Y + 3 * m);
-                const PairCoef kc = pc[n * N + m];
+                const F3 tm = f3v(ts[3 * m], ts[3 * m + 1], ts[3 * m + 2]);
+                const float sF = mm == 0 ? 1.f : -1.f;
+                const F3 d = f3v(Yn.x - Ys[3 * m], Yn.y - Ys[3 * m + 1], Yn.z - Ys[3 * m + 2]);
+                const float *c5 = pcs + 5 * (n * N + m);
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    V3 e = v3(c == 0 ? sF : 0.0, c == 1 ? sF : 0.0, c == 2 ? sF : 0.0);
-                    apply_pair(kc, d, e, col(Gt, c), MV[c], MW[c]);
+                    const F3 e = f3v(c == 0 ? sF : 0.f, c == 1 ? sF : 0.f, c == 2 ? sF : 0.f);
+                    // column c of (dL/2)[t_m x] is (dL/2) t_m x e_c
+                    const F3 ec = f3v(c == 0 ? 1.f : 0.f, c == 1 ? 1.f : 0.f, c == 2 ? 1.f : 0.f);
+                    F3 w = fcross(tm, ec);
+                    w = {hdL * w.x, hdL * w.y, hdL * w.z};
+                    apply_pair32(c5, d, e, w, MV[c], MW[c]);
                 }
             }
         }
-        // rows of segment n
         const int prow = (n == 0) ? 0 : 3 + 3 * N + 3 * (n - 1);
         const int rrow = 3 + 3 * n;
-        const V3 un = ld3(g.u + 3 * n);
-        const M33 ux = skew(un);
-        const M33 A = madd(madd(meye(), ux, -0.5), mmul(ux, ux), 1.0 / 12.0);
-        const double s = -dp.bdt * dp.inv8pieta;
+        const double *An = g.A + 9 * n;
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const V3 w = v3(A.m[0] * MW[c].x + A.m[1] * MW[c].y + A.m[2] * MW[c].z,
-                            A.m[3] * MW[c].x + A.m[4] * MW[c].y + A.m[5] * MW[c].z,
-                            A.m[6] * MW[c].x + A.m[7] * MW[c].y + A.m[8] * MW[c].z);
-            double *Jp = J + (int64_t)prow * n6 + colX + c;
+            float *Jp = J + (int64_t)prow * n6 + colX + c;
             Jp[0] = s * MV[c].x;
             Jp[n6] = s * MV[c].y;
             Jp[2 * n6] = s * MV[c].z;
-            double *Jr = J + (int64_t)rrow * n6 + colX + c;
-            Jr[0] = s * w.x;
-            Jr[n6] = s * w.y;
-            Jr[2 * n6] = s * w.z;
+            float *Jr = J + (int64_t)rrow * n6 + colX + c;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                Jr[r * n6] = s * ((float)An[3 * r] * MW[c].x + (float)An[3 * r + 1] * MW[c].y +
+                                  (float)An[3 * r + 2] * MW[c].z);
         }
         if (x < N) {
             const int k = x;
-            // robot-arm term of position row n >= 1 on u_k: (dL/2) w [x t_k]
             if (n >= 1 && k <= n) {
-                const double wgt = (k == 0 || k == n) ? 1.0 : 2.0;
-                const M33 arm = mscale(rskew(ld3(g.t + 3 * k)), 0.5 * dp.jp.dL * wgt);
+                // robot-arm term (dL/2) w [x t_k], w = 1 at k = 0 and k = n, else 2
+                const float wgt = (k == 0 || k == n) ? hdL : 2.f * hdL;
+                const F3 tk = f3v(ts[3 * k], ts[3 * k + 1], ts[3 * k + 2]);
+                // [x t] = -[t x]: rows (0, tz, -ty), (-tz, 0, tx), (ty, -tx, 0)
+                const float arm[9] = {0.f, tk.z, -tk.y, -tk.z, 0.f, tk.x, tk.y, -tk.x, 0.f};
                 for (int r = 0; r < 3; ++r)
                     for (int c = 0; c < 3; ++c)
-                        J[(int64_t)(prow + r) * n6 + colX + c] += arm.m[3 * r + c];
+                        J[(int64_t)(prow + r) * n6 + colX + c] += wgt * arm[3 * r + c];
             }
             if (k == n) {
-                const V3 Om = ld3(g.Om + 3 * n);
-                const M33 xO = rskew(Om);
-                M33 dd = madd(mscale(xO, -0.5),
-                              madd(rskew(cross(un, Om)), mmul(ux, xO)), 1.0 / 12.0);
-                dd = madd(meye(), dd, -dp.bdt);
+                const double *Du = g.Du + 9 * n;
                 for (int r = 0; r < 3; ++r)
                     for (int c = 0; c < 3; ++c)
-                        J[(int64_t)(rrow + r) * n6 + colX + c] += dd.m[3 * r + c];
+                        J[(int64_t)(rrow + r) * n6 + colX + c] +=
+                            (r == c ? 1.f : 0.f) - (float)(dp.bdt * Du[3 * r + c]);
             }
         }
     }
@@ -245,7 +319,113 @@ j0_dense_assemble_kernel(Layout lay, const int64_t *__restrict__ jofs, const dou
     for (int e = threadIdx.x; e < 3 * N; e += blockDim.x) {
         const int n = e / 3, r = e % 3;
         const int prow = (n == 0) ? 0 : 3 + 3 * N + 3 * (n - 1);
-        J[(int64_t)(prow + r) * n6 + r] = 1.0;
+        J[(int64_t)(prow + r) * n6 + r] = 1.f;
+    }
+}
+
+// r = b - J0 x for every filament, matrix-free in FP64 from the aux block:
+//   (F, T) = G x, (V, W) = M_f (F, T) (filament's RPY blocks), then
+//   position rows  x_Y1 + arm_n(x_u) - b dt V_n,
+//   rotation rows  x_u_n - b dt (A_n W_n + Du_n x_u_n);
+// the result is stored in FP32 (it feeds the FP32 inverse). One CTA per filament.
+__global__ void __launch_bounds__(kAsmThreads)
+j0_residual_mf_kernel(Layout lay, const int64_t *__restrict__ auxofs, DenseParams dp, const double *__restrict__ aux_all,
+                      const double *__restrict__ b, const double *__restrict__ x,
+                      float *__restrict__ r) {
+    extern __shared__ double smr[];    // FT 6N | VW 6N | Y 3N
+    const int f = blockIdx.x;
+    const int s0 = lay.off[f];
+    const int N = lay.off[f + 1] - s0;
+    const AuxView g = aux_view(const_cast<double *>(aux_all) + auxofs[f], N);
+    double *FT = smr, *VW = smr + 6 * N, *Ys = smr + 12 * N;
+    const double *xf = x + 6 * (int64_t)s0;
+    const double *bf = b + 6 * (int64_t)s0;
+    float *rf = r + 6 * (int64_t)s0;
+    const double *xu = xf + 3, *xL = xf + 3 + 3 * N;
+    for (int m = threadIdx.x; m < N; m += blockDim.x) {
+        const V3 Lr = (m <= N - 2) ? ld3(xL + 3 * m) : v3(0, 0, 0);
+        const V3 Ll = (m >= 1) ? ld3(xL + 3 * (m - 1)) : v3(0, 0, 0);
+        V3 T = (0.5 * dp.jp.dL) * cross(ld3(g.t + 3 * m), Lr + Ll);
+        T = T + mv(ld33(g.dT + 9 * m), ld3(xu + 3 * m));
+        if (m <= N - 2) T = T + mv(ld33(g.Db + 9 * m), ld3(xu + 3 * (m + 1)));
+        if (m >= 1) T = T - mv(ld33(g.Da + 9 * (m - 1)), ld3(xu + 3 * (m - 1)));
+        st3(FT + 6 * m, Lr - Ll);
+        st3(FT + 6 * m + 3, T);
+        st3(Ys + 3 * m, ld3(g.Y + 3 * m));
+    }
+    __syncthreads();
+    // pair sums: 8 lanes per target, reduced with shuffles in fixed order
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < N; base += (int)blockDim.x / 8) {
+        const int n = base + (int)threadIdx.x / 8;
+        const int sub = threadIdx.x & 7;
+        V3 V = v3(0, 0, 0), W = v3(0, 0, 0);
+        if (n < N) {
+            const V3 Yn = ld3(Ys + 3 * n);
+            for (int m = sub; m < N; m += 8) {
+                const double *pc = g.pc + 5 * ((int64_t)n * N + m);
+                const PairCoef k{pc[0], pc[1], pc[2], pc[3], pc[4]};
+                apply_pair(k, Yn - ld3(Ys + 3 * m), ld3(FT + 6 * m), ld3(FT + 6 * m + 3), V, W);
+            }
+        }
+#pragma unroll
+        for (int d = 4; d > 0; d >>= 1) {
+            V.x += __shfl_xor_sync(0xffffffffu, V.x, d);
+            V.y += __shfl_xor_sync(0xffffffffu, V.y, d);
+            V.z += __shfl_xor_sync(0xffffffffu, V.z, d);
+            W.x += __shfl_xor_sync(0xffffffffu, W.x, d);
+            W.y += __shfl_xor_sync(0xffffffffu, W.y, d);
+            W.z += __shfl_xor_sync(0xffffffffu, W.z, d);
+        }
+        if (n < N && sub == 0) {
+            st3(VW + 6 * n, dp.inv8pieta * V);
+            st3(VW + 6 * n + 3, dp.inv8pieta * W);
+        }
+    }
+    __syncthreads();
+    // rotation rows
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const V3 un = ld3(xu + 3 * n);
+        const V3 rot = un - dp.bdt * (mv(ld33(g.A + 9 * n), ld3(VW + 6 * n + 3)) +
+                                      mv(ld33(g.Du + 9 * n), un));
+        const V3 bb = ld3(bf + 3 + 3 * n);
+        rf[3 + 3 * n] = (float)(bb.x - rot.x);
+        rf[3 + 3 * n + 1] = (float)(bb.y - rot.y);
+        rf[3 + 3 * n + 2] = (float)(bb.z - rot.z);
+    }
+    // position rows: arm_n = (dL/2) sum_{k=1}^{n} (x_{k-1} x t_{k-1} + x_k x t_k), by warp 0
+    if (threadIdx.x < 32) {
+        V3 carry = v3(0, 0, 0), cprev = v3(0, 0, 0);
+        const V3 xY = ld3(xf);
+        for (int base = 0; base < N; base += 32) {
+            const int n = base + lane;
+            const bool act = n < N;
+            const V3 cn = act ? cross(ld3(xu + 3 * n), ld3(g.t + 3 * n)) : v3(0, 0, 0);
+            V3 cp = v3(__shfl_up_sync(0xffffffffu, cn.x, 1), __shfl_up_sync(0xffffffffu, cn.y, 1),
+                       __shfl_up_sync(0xffffffffu, cn.z, 1));
+            if (lane == 0) cp = cprev;
+            V3 inc = (act && n > 0) ? (0.5 * dp.jp.dL) * (cp + cn) : v3(0, 0, 0);
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const V3 o = v3(__shfl_up_sync(0xffffffffu, inc.x, d),
+                                __shfl_up_sync(0xffffffffu, inc.y, d),
+                                __shfl_up_sync(0xffffffffu, inc.z, d));
+                if (lane >= d) inc = inc + o;
+            }
+            const V3 arm = carry + inc;
+            if (act) {
+                const V3 pos = xY + arm - dp.bdt * ld3(VW + 6 * n);
+                const int prow = (n == 0) ? 0 : 3 + 3 * N + 3 * (n - 1);
+                const V3 bb = ld3(bf + prow);
+                rf[prow] = (float)(bb.x - pos.x);
+                rf[prow + 1] = (float)(bb.y - pos.y);
+                rf[prow + 2] = (float)(bb.z - pos.z);
+            }
+            carry = v3(__shfl_sync(0xffffffffu, arm.x, 31), __shfl_sync(0xffffffffu, arm.y, 31),
+                       __shfl_sync(0xffffffffu, arm.z, 31));
+            cprev = v3(__shfl_sync(0xffffffffu, cn.x, 31), __shfl_sync(0xffffffffu, cn.y, 31),
+                       __shfl_sync(0xffffffffu, cn.z, 31));
+        }
     }
 }
 
@@ -264,7 +444,7 @@ j0_dense_assemble_kernel(Layout lay, const int64_t *__restrict__ jofs, const dou
 template <int NCH>
 __global__ void __launch_bounds__(kInvThreads)
 gauss_jordan_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
-                            const double *__restrict__ J_all, float *__restrict__ inv_all,
+                            const float *J_all, float *inv_all,
                             int *__restrict__ flags) {
     extern __shared__ float Asm[];                  // n rows of stride ld = n + 1
     __shared__ float colk[kMaxInvN];
@@ -276,13 +456,13 @@ gauss_jordan_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
     const int f = blockIdx.x;
     const int s0 = lay.off[f];
     const int n = 6 * (lay.off[f + 1] - s0);
-    const double *J = J_all + jofs[f];
+    const float *J = J_all + jofs[f];   // J0 in FP32, inverted in place
     float *out = inv_all + jofs[f];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nw = (int)(blockDim.x >> 5);
     const int ld = n + 1;   // odd stride: column accesses hit distinct banks
     for (int i = wid; i < n; i += nw)
-        for (int c = lane; c < n; c += 32) Asm[i * ld + c] = (float)J[(int64_t)i * n + c];
+        for (int c = lane; c < n; c += 32) Asm[i * ld + c] = J[(int64_t)i * n + c];
     bool valid[NCH];
 #pragma unroll
     for (int jj = 0; jj < NCH; ++jj) valid[jj] = (lane + 32 * jj) < n;
@@ -373,7 +553,7 @@ constexpr int kGjWarps = 16, kGjRows = 12, kGjCols = 6, kGjMaxN = 32 * kGjCols; 
 
 __global__ void __launch_bounds__(32 * kGjWarps, 1)
 gauss_jordan_inverse_reg_kernel(Layout lay, const int64_t *__restrict__ jofs,
-                                const double *__restrict__ J_all, float *__restrict__ inv_all,
+                                const float *J_all, float *inv_all,
                                 int *__restrict__ flags) {
     __shared__ float colk[kGjMaxN];
     __shared__ float prow[kGjMaxN];
@@ -384,7 +564,7 @@ gauss_jordan_inverse_reg_kernel(Layout lay, const int64_t *__restrict__ jofs,
     const int f = blockIdx.x;
     const int s0 = lay.off[f];
     const int n = 6 * (lay.off[f + 1] - s0);
-    const double *J = J_all + jofs[f];
+    const float *J = J_all + jofs[f];   // J0 in FP32, inverted in place
     float *out = inv_all + jofs[f];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     float a[kGjRows][kGjCols];
@@ -393,7 +573,7 @@ gauss_jordan_inverse_reg_kernel(Layout lay, const int64_t *__restrict__ jofs,
 #pragma unroll
         for (int j = 0; j < kGjCols; ++j) {
             const int i = wid + kGjWarps * r, c = lane + 32 * j;
-            a[r][j] = (i < n && c < n) ? (float)J[(int64_t)i * n + c] : 0.f;
+            a[r][j] = (i < n && c < n) ? J[(int64_t)i * n + c] : 0.f;
         }
     for (int i = tid; i < kGjMaxN; i += blockDim.x) used[i] = (i < n) ? 0 : 1;
     __syncthreads();
@@ -475,9 +655,10 @@ gauss_jordan_inverse_reg_kernel(Layout lay, const int64_t *__restrict__ jofs,
         }
 }
 
-// Refined solve, as grid-wide GEMV phases over every row of every filament
-// (one warp per row, lanes stride the columns with coalesced loads):
-//   x = Inv b;  then kJ0Refine times:  r = b - J0 x (FP64);  x += Inv r.
+// Application of the FP32 inverses as one grid-wide GEMV over every row of
+// every filament (one warp per row, lanes stride the columns with coalesced
+// loads). A refined solve is
+//   x = Inv b;  then kJ0Refine times:  r = b - J0 x (j0_residual_mf_kernel);  x += Inv r.
 __global__ void inv_apply_kernel(Layout lay, const int64_t *__restrict__ jofs,
                                  const float *__restrict__ inv_all, const float *__restrict__ r,
                                  double *__restrict__ x, int accumulate) {
@@ -507,25 +688,6 @@ __global__ void to_float_kernel(int64_t n, const double *__restrict__ b, double 
     }
 }
 
-__global__ void residual_gemv_kernel(Layout lay, const int64_t *__restrict__ jofs,
-                                     const double *__restrict__ J_all, const double *__restrict__ b,
-                                     const double *__restrict__ x, float *__restrict__ r) {
-    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (row >= lay.nX) return;
-    const int f = lay.fil_of[row / 6];
-    const int64_t r0 = 6 * (int64_t)lay.off[f];
-    const int n = (int)(6 * (int64_t)lay.off[f + 1] - r0);
-    const int i = (int)(row - r0);
-    const double *A = J_all + jofs[f] + (int64_t)i * n;
-    const double *xf = x + r0;
-    double t = 0.0;
-    for (int c = lane; c < n; c += 32) t = fma(A[c], xf[c], t);
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) t += __shfl_down_sync(0xffffffffu, t, d);
-    if (lane == 0) r[row] = (float)(b[row] - t);
-}
-
 }  // namespace
 
 template <int NCH>
@@ -534,7 +696,7 @@ cudaError_t launch_gj(fil_ctx *c, size_t smem) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     gauss_jordan_inverse_kernel<NCH><<<c->lay.M, kInvThreads, smem, c->stream>>>(
-        c->lay, c->jofs, c->jdense, c->jinv, c->d_flags);
+        c->lay, c->jofs, c->jinv, c->jinv, c->d_flags);
     return cudaGetLastError();
 }
 
@@ -560,19 +722,21 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
     dp.inv8pieta = 1.0 / (8.0 * kPi * c->eta);
     dp.near2 = 4.0 * c->a * c->a;
     dp.a = c->a;
+    c->j0_dp_bdt = dp.bdt;
     const int N = c->lay.maxN;
-    const size_t smem_asm = (size_t)(25 * N + 5 * N * N) * sizeof(double) +
-                            (size_t)2 * (N > 1 ? N - 1 : 0) * sizeof(M33);
-    cudaError_t e = cudaFuncSetAttribute(j0_dense_assemble_kernel,
+    j0_precompute_kernel<<<c->lay.M, kAsmThreads, (size_t)6 * N * sizeof(double), c->stream>>>(
+        c->lay, c->auxofs, X, c->qc, c->Yc, c->Tint, dp, c->aux);
+    const size_t smem_asm = (size_t)(5 * N * N + 6 * N) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(j0_assemble32_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_asm);
     if (e != cudaSuccess) return e;
-    j0_dense_assemble_kernel<<<c->lay.M, kAsmThreads, smem_asm, c->stream>>>(
-        c->lay, c->jofs, X, c->qc, c->Yc, c->Tint, dp, c->jdense);
+    j0_assemble32_kernel<<<c->lay.M, kAsmThreads, smem_asm, c->stream>>>(
+        c->lay, c->jofs, c->auxofs, dp, c->aux, c->jinv);
 #ifndef FIL_GJ_SHARED_ONLY
     if (6 * N <= kGjMaxN) {
         gauss_jordan_inverse_reg_kernel<<<c->lay.M, 32 * kGjWarps, 0, c->stream>>>(
-            c->lay, c->jofs, c->jdense, c->jinv, c->d_flags);
+            c->lay, c->jofs, c->jinv, c->jinv, c->d_flags);
         e = cudaGetLastError();
     } else
 #endif
@@ -581,7 +745,7 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
         e = launch_gauss_jordan(c, (6 * N + 31) / 32, smem_inv);
     }
     if (e != cudaSuccess) return e;
-    c->n_launches += 2;
+    c->n_launches += 3;
     return cudaGetLastError();
 }
 
@@ -591,10 +755,18 @@ cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x) {
     const unsigned grid = (unsigned)((nX * 32 + 255) / 256);
     double *bb = c->j0_rhs, *xx = c->j0_x;
     float *rr = reinterpret_cast<float *>(c->j0_res);
+    DenseParams dp;
+    dp.jp = J0Params{c->dL, c->KB, c->KT, c->g0, c->kmu, c->knu, 0.0, 0.0};
+    dp.bdt = c->j0_dp_bdt;
+    dp.inv8pieta = 1.0 / (8.0 * kPi * c->eta);
+    dp.near2 = 4.0 * c->a * c->a;
+    dp.a = c->a;
+    const size_t smem_res = (size_t)15 * c->lay.maxN * sizeof(double);
     to_float_kernel<<<(unsigned)((nX + 255) / 256), 256, 0, c->stream>>>(nX, b, bb, rr);
     inv_apply_kernel<<<grid, 256, 0, c->stream>>>(c->lay, c->jofs, c->jinv, rr, xx, 0);
     for (int it = 0; it < kJ0Refine; ++it) {
-        residual_gemv_kernel<<<grid, 256, 0, c->stream>>>(c->lay, c->jofs, c->jdense, bb, xx, rr);
+        j0_residual_mf_kernel<<<c->lay.M, kAsmThreads, smem_res, c->stream>>>(
+            c->lay, c->auxofs, dp, c->aux, bb, xx, rr);
         inv_apply_kernel<<<grid, 256, 0, c->stream>>>(c->lay, c->jofs, c->jinv, rr, xx, 1);
     }
     cudaError_t e = cudaMemcpyAsync(x, xx, sizeof(double) * nX, cudaMemcpyDeviceToDevice,
@@ -602,13 +774,6 @@ cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x) {
     c->n_launches += 2 + 2 * kJ0Refine;
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
-}
-
-size_t j0_dense_smem_needed(int maxN) {
-    const size_t a = (size_t)(25 * maxN + 5 * maxN * maxN) * sizeof(double) +
-                     (size_t)2 * maxN * sizeof(M33);
-    const size_t b = (size_t)6 * maxN * (6 * maxN + 1) * sizeof(float);
-    return a > b ? a : b;
 }
 
 }  // namespace fil
