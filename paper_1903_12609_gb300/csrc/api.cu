@@ -106,7 +106,7 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->VW = ar.take<double>(6 * S);
     c->Mh = nullptr;
     if (c->prec == FIL_MIXED) {
-        c->src32 = ar.take<float4>(3 * c->Spad);
+        c->src32 = ar.take<float4>((size_t)kRpyPairF4 * (c->Spad / 2));
         c->src64 = nullptr;
     } else {
         c->src64 = ar.take<double>(9 * c->Spad);
@@ -132,16 +132,12 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
         c->jofs = nullptr;
         c->aux = nullptr;
         c->auxofs = nullptr;
-        c->j0_rhs = c->j0_x = c->j0_res = nullptr;
     } else {
         c->band = nullptr;
         c->jinv = ar.take<float>((size_t)c->jdense_len);
         c->jofs = ar.take<int64_t>(M + 1);
         c->aux = ar.take<double>((size_t)c->aux_len);
         c->auxofs = ar.take<int64_t>(M + 1);
-        c->j0_rhs = ar.take<double>(nX);
-        c->j0_x = ar.take<double>(nX);
-        c->j0_res = ar.take<double>(nX);
     }
     c->piv = ar.take<int>(6 * S);
     c->stage_a = ar.take<double>(nX);

@@ -28,7 +28,7 @@ constexpr int kMaxSegPerFil = (int)(kSolveSmemMax / (6 * sizeof(double)));
 // The filament-RPY J0 keeps a filament's block in shared memory for its
 // FP32 inverse: (6N)^2 floats <= 200 KB, i.e. N <= 38; refinement steps per solve.
 constexpr int kMaxDenseSeg = 38;
-constexpr int kJ0Refine = 2;
+constexpr int kJ0Refine = 1;
 
 struct Layout {
     int M = 0;           // filaments
@@ -100,7 +100,6 @@ struct fil_ctx {
     int64_t *auxofs;       // [M+1]
     int64_t aux_len;
     double j0_dp_bdt;      // scheme weight * dt of the current J0
-    double *j0_rhs, *j0_x, *j0_res;   // refinement scratch (6S each)
 
     // staging for host pointers (6S doubles each)
     double *stage_a, *stage_b, *stage_c;

@@ -25,11 +25,12 @@
 //   2. j0_assemble32_kernel (FP32): the (6N)^2 matrix J0 from the aux block,
 //      written into the inverse buffer and inverted there in FP32 by
 //      Gauss-Jordan elimination (FP32 runs at 64x the FP64 rate on this part).
-// A solve applies the FP32 inverse and then kJ0Refine steps of iterative
-// refinement x += Inv (b - J0 x), with b - J0 x evaluated matrix-free in FP64
-// from the aux block (j0_residual_mf_kernel) -- the same operator as the
-// dense definition -- so x reaches FP64 accuracy (each step multiplies the
-// error by ~cond(J0) * 2^-24).
+// A solve (j0_solve_fused_kernel, one CTA per filament, the FP32 inverse
+// staged in shared memory once) applies the inverse and then kJ0Refine steps
+// of iterative refinement x += Inv (b - J0 x), with b - J0 x evaluated
+// matrix-free in FP64 from the aux block -- the same operator as the dense
+// definition -- so x reaches FP64 accuracy (each step multiplies the error by
+// ~cond(J0) * 2^-24).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -73,7 +74,7 @@ __device__ __forceinline__ PairCoef pair_coef(V3 d, double a) {
         k.D = ia3 * (9.0 * rinv / (32.0 * a) - 3.0 * r / (64.0 * a * a * a));
         k.G = 0.5 * ia3 * (1.0 - 3.0 * r / (8.0 * a));
     } else {
-        const double rinv = 1.0 / sqrt(r2);
+        const double rinv = rsqrt(r2);
         const double rinv2 = rinv * rinv, rinv3 = rinv * rinv2, rinv5 = rinv3 * rinv2;
         k.A = rinv + (2.0 * a * a / 3.0) * rinv3;
         k.B = rinv3 - 2.0 * a * a * rinv5;
@@ -154,11 +155,42 @@ j0_precompute_kernel(Layout lay, const int64_t *__restrict__ auxofs, const doubl
         }
     }
     __syncthreads();
+    // the coefficients depend on r only: each unordered pair once, stored twice
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
         const int n = e / N, m = e - (e / N) * N;
+        if (m < n) continue;
         const PairCoef k = pair_coef(ld3(Yf + 3 * n) - ld3(Yf + 3 * m), dp.a);
         double *pc = g.pc + 5 * (int64_t)e;
         pc[0] = k.A; pc[1] = k.B; pc[2] = k.C; pc[3] = k.D; pc[4] = k.G;
+        if (m != n) {
+            double *pt = g.pc + 5 * ((int64_t)m * N + n);
+            pt[0] = k.A; pt[1] = k.B; pt[2] = k.C; pt[3] = k.D; pt[4] = k.G;
+        }
+    }
+    __syncthreads();
+    // angular velocity of the internal loads within the filament: 8 lanes per
+    // target, reduced with shuffles in a fixed order
+    for (int base = 0; base < N; base += (int)blockDim.x / 8) {
+        const int n = base + (int)threadIdx.x / 8;
+        const int sub = threadIdx.x & 7;
+        V3 W = v3(0, 0, 0);
+        if (n < N) {
+            V3 V = v3(0, 0, 0);
+            const V3 Yn = ld3(Yf + 3 * n);
+            for (int m = sub; m < N; m += 8) {
+                const double *pc = g.pc + 5 * ((int64_t)n * N + m);
+                const PairCoef k{pc[0], pc[1], pc[2], pc[3], pc[4]};
+                apply_pair(k, Yn - ld3(Yf + 3 * m), ld3(Fi + 3 * m),
+                           ld3(Tint + 3 * (int64_t)(s0 + m)), V, W);
+            }
+        }
+#pragma unroll
+        for (int d = 4; d > 0; d >>= 1) {
+            W.x += __shfl_xor_sync(0xffffffffu, W.x, d);
+            W.y += __shfl_xor_sync(0xffffffffu, W.y, d);
+            W.z += __shfl_xor_sync(0xffffffffu, W.z, d);
+        }
+        if (n < N && sub == 0) st3(g.Om + 3 * n, dp.inv8pieta * W);
     }
     __syncthreads();
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
@@ -167,17 +199,7 @@ j0_precompute_kernel(Layout lay, const int64_t *__restrict__ auxofs, const doubl
         if (n <= N - 2) dT = madd(dT, ld33(g.Da + 9 * n));
         if (n >= 1) dT = madd(dT, ld33(g.Db + 9 * (n - 1)), -1.0);
         st33(g.dT + 9 * n, dT);
-        // angular velocity of the internal loads within the filament
-        V3 V = v3(0, 0, 0), W = v3(0, 0, 0);
-        const V3 Yn = ld3(Yf + 3 * n);
-        for (int m = 0; m < N; ++m) {
-            const double *pc = g.pc + 5 * ((int64_t)n * N + m);
-            const PairCoef k{pc[0], pc[1], pc[2], pc[3], pc[4]};
-            apply_pair(k, Yn - ld3(Yf + 3 * m), ld3(Fi + 3 * m), ld3(Tint + 3 * (int64_t)(s0 + m)),
-                       V, W);
-        }
-        const V3 Om = dp.inv8pieta * W;
-        st3(g.Om + 3 * n, Om);
+        const V3 Om = ld3(g.Om + 3 * n);
         const V3 u = ld3(g.u + 3 * n);
         const M33 ux = skew(u), xO = rskew(Om);
         st33(g.Du + 9 * n, madd(mscale(xO, -0.5), madd(rskew(cross(u, Om)), mmul(ux, xO)), 1.0 / 12.0));
@@ -206,24 +228,25 @@ __device__ __forceinline__ void apply_pair32(const float *c, F3 d, F3 v, F3 w, F
     W = fmad3(C, w, W);
     W = fmad3(D * fdot(d, w), d, W);
 }
-__device__ __forceinline__ F3 mcol(const double *m9, int c) {
-    return {(float)m9[c], (float)m9[3 + c], (float)m9[6 + c]};
-}
+__device__ __forceinline__ F3 mcol(const float *m9, int c) { return {m9[c], m9[3 + c], m9[6 + c]}; }
 
 // J0 in FP32 from the aux block, written into the inverse buffer (row-major).
 __global__ void __launch_bounds__(kAsmThreads)
 j0_assemble32_kernel(Layout lay, const int64_t *__restrict__ jofs,
                      const int64_t *__restrict__ auxofs, DenseParams dp, const double *__restrict__ aux_all, float *__restrict__ J_all) {
-    extern __shared__ float smf[];     // pc 5N^2 | Yrel 3N | t 3N
+    extern __shared__ float smf[];     // pc 5N^2 | Yrel 3N | t 3N | A, Du, dT, Da, Db 45N
     const int f = blockIdx.x;
     const int s0 = lay.off[f];
     const int N = lay.off[f + 1] - s0;
     const int n6 = 6 * N;
     const AuxView g = aux_view(const_cast<double *>(aux_all) + auxofs[f], N);
-    float *pcs = smf, *Ys = smf + 5 * N * N, *ts = Ys + 3 * N;
+    float *pcs = smf, *Ys = smf + 5 * N * N, *ts = Ys + 3 * N, *m32 = ts + 3 * N;
+    float *A32 = m32, *Du32 = m32 + 9 * N, *dT32 = m32 + 18 * N, *Da32 = m32 + 27 * N,
+          *Db32 = m32 + 36 * N;
     float *J = J_all + jofs[f];
     const double *Y0 = g.Y;
     for (int e = threadIdx.x; e < 5 * N * N; e += blockDim.x) pcs[e] = (float)g.pc[e];
+    for (int e = threadIdx.x; e < 45 * N; e += blockDim.x) m32[e] = (float)g.A[e];   // A..Db
     for (int e = threadIdx.x; e < 3 * N; e += blockDim.x) {
         Ys[e] = (float)(Y0[e] - Y0[e % 3]);     // positions relative to segment 0
         ts[e] = (float)g.t[e];
@@ -247,7 +270,7 @@ j0_assemble32_kernel(Layout lay, const int64_t *__restrict__ jofs,
                 const int m = k + mm;
                 if (m < 0 || m > N - 1) continue;
                 // d T_m / d u_k: Db(k-1) for m = k-1, dT_k for m = k, -Da(k) for m = k+1
-                const double *Gt = (mm == -1) ? g.Db + 9 * (k - 1) : (mm == 0) ? g.dT + 9 * k : g.Da + 9 * k;
+                const float *Gt = (mm == -1) ? Db32 + 9 * (k - 1) : (mm == 0) ? dT32 + 9 * k : Da32 + 9 * k;
                 const float sg = (mm == 1) ? -1.f : 1.f;
                 const F3 d = f3v(Yn.x - Ys[3 * m], Yn.y - Ys[3 * m + 1], Yn.z - Ys[3 * m + 2]);
                 const float *c5 = pcs + 5 * (n * N + m);
@@ -281,7 +304,7 @@ j0_assemble32_kernel(Layout lay, const int64_t *__restrict__ jofs,
         }
         const int prow = (n == 0) ? 0 : 3 + 3 * N + 3 * (n - 1);
         const int rrow = 3 + 3 * n;
-        const double *An = g.A + 9 * n;
+        const float *An = A32 + 9 * n;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float *Jp = J + (int64_t)prow * n6 + colX + c;
@@ -291,8 +314,8 @@ j0_assemble32_kernel(Layout lay, const int64_t *__restrict__ jofs,
             float *Jr = J + (int64_t)rrow * n6 + colX + c;
 #pragma unroll
             for (int r = 0; r < 3; ++r)
-                Jr[r * n6] = s * ((float)An[3 * r] * MW[c].x + (float)An[3 * r + 1] * MW[c].y +
-                                  (float)An[3 * r + 2] * MW[c].z);
+                Jr[r * n6] = s * (An[3 * r] * MW[c].x + An[3 * r + 1] * MW[c].y +
+                                  An[3 * r + 2] * MW[c].z);
         }
         if (x < N) {
             const int k = x;
@@ -307,11 +330,12 @@ j0_assemble32_kernel(Layout lay, const int64_t *__restrict__ jofs,
                         J[(int64_t)(prow + r) * n6 + colX + c] += wgt * arm[3 * r + c];
             }
             if (k == n) {
-                const double *Du = g.Du + 9 * n;
+                const float *Du = Du32 + 9 * n;
+                const float bdt = (float)dp.bdt;
                 for (int r = 0; r < 3; ++r)
                     for (int c = 0; c < 3; ++c)
                         J[(int64_t)(rrow + r) * n6 + colX + c] +=
-                            (r == c ? 1.f : 0.f) - (float)(dp.bdt * Du[3 * r + c]);
+                            (r == c ? 1.f : 0.f) - bdt * Du[3 * r + c];
             }
         }
     }
@@ -323,24 +347,18 @@ j0_assemble32_kernel(Layout lay, const int64_t *__restrict__ jofs,
     }
 }
 
-// r = b - J0 x for every filament, matrix-free in FP64 from the aux block:
-//   (F, T) = G x, (V, W) = M_f (F, T) (filament's RPY blocks), then
+constexpr int kMfLanes = 16;   // lanes per target in the matrix-free pair sums
+
+// r = b - J0 x for the filament of this CTA, matrix-free in FP64 from the
+// aux block (every thread of the CTA calls it; it ends with a barrier):
+//   (F, T) = G x, (V, W) = M_f (F, T) (the filament's RPY blocks), then
 //   position rows  x_Y1 + arm_n(x_u) - b dt V_n,
 //   rotation rows  x_u_n - b dt (A_n W_n + Du_n x_u_n);
-// the result is stored in FP32 (it feeds the FP32 inverse). One CTA per filament.
-__global__ void __launch_bounds__(kAsmThreads)
-j0_residual_mf_kernel(Layout lay, const int64_t *__restrict__ auxofs, DenseParams dp, const double *__restrict__ aux_all,
-                      const double *__restrict__ b, const double *__restrict__ x,
-                      float *__restrict__ r) {
-    extern __shared__ double smr[];    // FT 6N | VW 6N | Y 3N
-    const int f = blockIdx.x;
-    const int s0 = lay.off[f];
-    const int N = lay.off[f + 1] - s0;
-    const AuxView g = aux_view(const_cast<double *>(aux_all) + auxofs[f], N);
-    double *FT = smr, *VW = smr + 6 * N, *Ys = smr + 12 * N;
-    const double *xf = x + 6 * (int64_t)s0;
-    const double *bf = b + 6 * (int64_t)s0;
-    float *rf = r + 6 * (int64_t)s0;
+// the result is stored in FP32 (it feeds the FP32 inverse). x, b: the
+// filament's 6N entries; FT, VW (6N) and Ys (3N) are shared-memory scratch.
+__device__ void residual_mf_cta(const AuxView &g, int N, const DenseParams &dp,
+                                const double *xf, const double *bf, float *rf, double *FT,
+                                double *VW, double *Ys) {
     const double *xu = xf + 3, *xL = xf + 3 + 3 * N;
     for (int m = threadIdx.x; m < N; m += blockDim.x) {
         const V3 Lr = (m <= N - 2) ? ld3(xL + 3 * m) : v3(0, 0, 0);
@@ -354,22 +372,22 @@ j0_residual_mf_kernel(Layout lay, const int64_t *__restrict__ auxofs, DenseParam
         st3(Ys + 3 * m, ld3(g.Y + 3 * m));
     }
     __syncthreads();
-    // pair sums: 8 lanes per target, reduced with shuffles in fixed order
+    // pair sums: kMfLanes lanes per target, reduced with shuffles in fixed order
     const int lane = threadIdx.x & 31;
-    for (int base = 0; base < N; base += (int)blockDim.x / 8) {
-        const int n = base + (int)threadIdx.x / 8;
-        const int sub = threadIdx.x & 7;
+    for (int base = 0; base < N; base += (int)blockDim.x / kMfLanes) {
+        const int n = base + (int)threadIdx.x / kMfLanes;
+        const int sub = threadIdx.x & (kMfLanes - 1);
         V3 V = v3(0, 0, 0), W = v3(0, 0, 0);
         if (n < N) {
             const V3 Yn = ld3(Ys + 3 * n);
-            for (int m = sub; m < N; m += 8) {
+            for (int m = sub; m < N; m += kMfLanes) {
                 const double *pc = g.pc + 5 * ((int64_t)n * N + m);
                 const PairCoef k{pc[0], pc[1], pc[2], pc[3], pc[4]};
                 apply_pair(k, Yn - ld3(Ys + 3 * m), ld3(FT + 6 * m), ld3(FT + 6 * m + 3), V, W);
             }
         }
 #pragma unroll
-        for (int d = 4; d > 0; d >>= 1) {
+        for (int d = kMfLanes / 2; d > 0; d >>= 1) {
             V.x += __shfl_xor_sync(0xffffffffu, V.x, d);
             V.y += __shfl_xor_sync(0xffffffffu, V.y, d);
             V.z += __shfl_xor_sync(0xffffffffu, V.z, d);
@@ -427,6 +445,69 @@ j0_residual_mf_kernel(Layout lay, const int64_t *__restrict__ auxofs, DenseParam
                        __shfl_sync(0xffffffffu, cn.z, 31));
         }
     }
+    __syncthreads();
+}
+
+// x (+)= Inv r for one filament, Inv (n x n, row-major) and r in shared
+// memory: warp per row, lanes stride the columns (conflict-free).
+__device__ __forceinline__ void inv_gemv_cta(const float *Inv, const float *r, double *x, int n,
+                                             bool accumulate) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < n; i += nw) {
+        const float *row = Inv + (int64_t)i * n;
+        float t = 0.f;
+        for (int c = lane; c < n; c += 32) t = fmaf(row[c], r[c], t);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+        if (lane == 0) x[i] = accumulate ? x[i] + (double)t : (double)t;
+    }
+}
+
+// Refined J0 solve, one CTA per filament with its FP32 inverse staged in
+// shared memory once:  x = Inv b;  kJ0Refine times { r = b - J0 x (FP64,
+// matrix-free); x += Inv r }.  b and x may alias.
+constexpr int kSolveThreads = 512;
+// shared memory of the largest solve: inverse, b, x, FT, VW, Y, r
+static_assert(36 * kMaxDenseSeg * kMaxDenseSeg * 4 + (12 * kMaxDenseSeg + 15 * kMaxDenseSeg) * 8 +
+                      6 * kMaxDenseSeg * 4 <= 227 * 1024,
+              "the J0 solve of the longest filament must fit in shared memory");
+
+__global__ void __launch_bounds__(kSolveThreads)
+j0_solve_fused_kernel(Layout lay, const int64_t *__restrict__ jofs,
+                      const int64_t *__restrict__ auxofs, DenseParams dp,
+                      const double *__restrict__ aux_all, const float *__restrict__ inv_all,
+                      const double *b, double *x) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int f = blockIdx.x;
+    const int s0 = lay.off[f];
+    const int N = lay.off[f + 1] - s0;
+    const int n = 6 * N;
+    float *Inv = reinterpret_cast<float *>(smraw);                  // n^2 (144 N^2 bytes)
+    double *bs = reinterpret_cast<double *>(smraw + (size_t)n * n * sizeof(float));
+    double *xs = bs + n, *FT = xs + n, *VW = FT + 6 * N, *Ys = VW + 6 * N;
+    float *rs = reinterpret_cast<float *>(Ys + 3 * N);
+    const AuxView g = aux_view(const_cast<double *>(aux_all) + auxofs[f], N);
+    // n^2 = 36 N^2 floats and the block offsets are multiples of 36 floats,
+    // so the copy is whole, 16-byte aligned float4s
+    const float4 *src = reinterpret_cast<const float4 *>(inv_all + jofs[f]);
+    float4 *dst = reinterpret_cast<float4 *>(Inv);
+    for (int i = threadIdx.x; i < n * n / 4; i += blockDim.x) dst[i] = src[i];
+    const double *bg = b + 6 * (int64_t)s0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = bg[i];
+        bs[i] = v;
+        rs[i] = (float)v;
+    }
+    __syncthreads();
+    inv_gemv_cta(Inv, rs, xs, n, false);
+    __syncthreads();
+    for (int it = 0; it < kJ0Refine; ++it) {
+        residual_mf_cta(g, N, dp, xs, bs, rs, FT, VW, Ys);
+        inv_gemv_cta(Inv, rs, xs, n, true);
+        __syncthreads();
+    }
+    double *xg = x + 6 * (int64_t)s0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) xg[i] = xs[i];
 }
 
 // Inverse of each filament's J0 in FP32 by Gauss-Jordan elimination with
@@ -541,152 +622,167 @@ gauss_jordan_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
 
 // Register-resident Gauss-Jordan inverse for blocks of n <= 192 (N <= 32),
 // with implicit pivoting. Thread (w, l) of 16 warps holds rows i = w + 16 r
-// (r < 12) and columns c = l + 32 j (j < 6) in registers. Step k pivots column
-// k on the unused row p of largest |a_pk| (recorded, never swapped) and applies
-//   a_i <- s_i a_i + t_i pr,   pr = row p / a_pk with entry k = 1/a_pk,
-// with (s, t) = (0, 1) for row p and (1, -a_ik) otherwise, after column k has
-// been zeroed -- the in-place Gauss-Jordan update, uniform over all rows. The
-// step loop is unrolled over the six 32-column chunks so that column k has a
-// static register index. The result is A^{-1} with rows and columns permuted:
+// (r < 12) and columns c = l + 32 j (j < 6) in registers, packed in float2
+// pairs (j = 2q, 2q+1). Step k pivots column k on the unused row p of largest
+// |a_pk| (first such; recorded, never swapped) and performs the in-place
+// Gauss-Jordan update
+//   column k <- 0;  row p <- 0;  a_i <- a_i + t_i pr  for every row,
+//   pr = row p / a_pk with entry k = 1/a_pk,  t_p = 1, t_i = -a_ik otherwise,
+// as one packed FMA per element: the owner lanes of column k publish it to
+// shared memory (with a_pk replaced by -1, so t_i = -colk_i for every row) and
+// zero it; the owner warp of row p stores it (entry k = 1) and zeroes it.
+// Column k+1 and each warp's pivot candidate for it are published right after
+// the update, so a step needs two barriers. The step loop is unrolled over the
+// six 32-column chunks so that column indices into the register array are
+// static. The result is A^{-1} with rows and columns permuted:
 // A^{-1}[k][m] = S[p_k][q(m)], p_k the pivot row of column k and q its inverse.
-constexpr int kGjWarps = 16, kGjRows = 12, kGjCols = 6, kGjMaxN = 32 * kGjCols;  // 192
+constexpr int kGjWarps = 16, kGjRows = 12, kGjPairs = 3, kGjMaxN = 64 * kGjPairs;  // 192
+
+// Column values col[r] of this lane's rows -> colk (warp-major: entry
+// 12 w + r is row w + 16 r), and this warp's pivot candidate (largest |value|
+// over its unused rows, smallest row on ties).
+__device__ __forceinline__ void gj_publish(const float (&col)[kGjRows], unsigned used, int wid,
+                                           float *colk, float *cand_v, int *cand_i) {
+    float4 *dst = reinterpret_cast<float4 *>(colk + kGjRows * wid);
+#pragma unroll
+    for (int r = 0; r < kGjRows; r += 4)
+        dst[r / 4] = make_float4(col[r], col[r + 1], col[r + 2], col[r + 3]);
+    float best = -1.f;
+    int bi = 0x7fffffff;
+#pragma unroll
+    for (int r = 0; r < kGjRows; ++r) {
+        const float x = ((used >> r) & 1u) ? -1.f : fabsf(col[r]);
+        if (x > best) { best = x; bi = wid + kGjWarps * r; }
+    }
+    cand_v[wid] = best;
+    cand_i[wid] = bi;
+}
+
+// Publish column kj*32 + (owner lane) and zero it in the registers.
+#define FIL_GJ_PUBLISH(kj, buf)                                                    \
+    {                                                                              \
+        float col[kGjRows];                                                        \
+        _Pragma("unroll") for (int r = 0; r < kGjRows; ++r) {                      \
+            if ((kj) & 1) { col[r] = a[r][(kj) >> 1].y; a[r][(kj) >> 1].y = 0.f; } \
+            else { col[r] = a[r][(kj) >> 1].x; a[r][(kj) >> 1].x = 0.f; }          \
+        }                                                                          \
+        gj_publish(col, used, wid, colk[buf], cand_v[buf], cand_i[buf]);           \
+    }
 
 __global__ void __launch_bounds__(32 * kGjWarps, 1)
-gauss_jordan_inverse_reg_kernel(Layout lay, const int64_t *__restrict__ jofs,
-                                const float *J_all, float *inv_all,
+gauss_jordan_inverse_reg_kernel(Layout lay, const int64_t *__restrict__ jofs, float *inv_all,
                                 int *__restrict__ flags) {
-    __shared__ float colk[kGjMaxN];
-    __shared__ float prow[kGjMaxN];
-    __shared__ int used[kGjMaxN];
+    __shared__ __align__(16) float colk[2][kGjMaxN];
+    __shared__ __align__(16) float2 prow2[32 * kGjPairs];   // [32 q + l] = row p at (l + 64q, +32)
+    __shared__ float cand_v[2][kGjWarps];
+    __shared__ int cand_i[2][kGjWarps];
+    __shared__ float pinv_s;
     __shared__ int pivrow[kGjMaxN];
     __shared__ int qinv[kGjMaxN];
-    __shared__ int s_p;
     const int f = blockIdx.x;
     const int s0 = lay.off[f];
     const int n = 6 * (lay.off[f + 1] - s0);
-    const float *J = J_all + jofs[f];   // J0 in FP32, inverted in place
-    float *out = inv_all + jofs[f];
+    float *A = inv_all + jofs[f];   // J0 in FP32 on entry, its inverse on exit
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    float a[kGjRows][kGjCols];
+    float2 a[kGjRows][kGjPairs];
+    unsigned used = 0;
 #pragma unroll
-    for (int r = 0; r < kGjRows; ++r)
+    for (int r = 0; r < kGjRows; ++r) {
+        const int i = wid + kGjWarps * r;
+        if (i >= n) used |= 1u << r;      // padding rows never pivot
 #pragma unroll
-        for (int j = 0; j < kGjCols; ++j) {
-            const int i = wid + kGjWarps * r, c = lane + 32 * j;
-            a[r][j] = (i < n && c < n) ? J[(int64_t)i * n + c] : 0.f;
+        for (int q = 0; q < kGjPairs; ++q) {
+            const int c0 = lane + 64 * q, c1 = c0 + 32;
+            a[r][q].x = (i < n && c0 < n) ? A[(int64_t)i * n + c0] : 0.f;
+            a[r][q].y = (i < n && c1 < n) ? A[(int64_t)i * n + c1] : 0.f;
         }
-    for (int i = tid; i < kGjMaxN; i += blockDim.x) used[i] = (i < n) ? 0 : 1;
+    }
+    if (lane == 0) FIL_GJ_PUBLISH(0, 0)
     __syncthreads();
 #pragma unroll
-    for (int kj = 0; kj < kGjCols; ++kj) {
+    for (int kj = 0; kj < 2 * kGjPairs; ++kj) {
         for (int kl = 0; kl < 32; ++kl) {
             const int k = 32 * kj + kl;
             if (k >= n) break;
-            // (1) column k -> colk (held by lane kl), then zero it
-            if (lane == kl) {
+            const int buf = k & 1;
+            // (1) pivot: reduce the 16 warp candidates (every warp, same result)
+            float v = lane < kGjWarps ? cand_v[buf][lane] : -2.f;
+            int idx = lane < kGjWarps ? cand_i[buf][lane] : 0x7fffffff;
 #pragma unroll
-                for (int r = 0; r < kGjRows; ++r) {
-                    colk[wid + kGjWarps * r] = a[r][kj];
-                    a[r][kj] = 0.f;
-                }
+            for (int d = kGjWarps / 2; d > 0; d >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, v, d);
+                const int oi = __shfl_xor_sync(0xffffffffu, idx, d);
+                if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
             }
-            __syncthreads();
-            // (2) pivot: unused row of largest |a_ik| (first such), by warp 0
-            if (wid == 0) {
-                float v = -1.f;
-                int idx = 0x7fffffff;
-                for (int i = lane; i < n; i += 32) {
-                    const float x = used[i] ? -1.f : fabsf(colk[i]);
-                    if (x > v) { v = x; idx = i; }
-                }
-#pragma unroll
-                for (int d = 16; d > 0; d >>= 1) {
-                    const float ov = __shfl_down_sync(0xffffffffu, v, d);
-                    const int oi = __shfl_down_sync(0xffffffffu, idx, d);
-                    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
-                }
-                if (lane == 0) {
-                    s_p = idx;
-                    pivrow[k] = idx;
-                    used[idx] = 1;
-                    if (!(v > 0.f)) atomicOr(flags + 1, 1);
-                }
+            const int p = __shfl_sync(0xffffffffu, idx, 0);
+            const int pw = p % kGjWarps, prr = p / kGjWarps;
+            if (tid == 0) {
+                pivrow[k] = p;
+                float *cp = &colk[buf][kGjRows * pw + prr];
+                if (!(fabsf(*cp) > 0.f)) atomicOr(flags + 1, 1);
+                pinv_s = __frcp_rn(*cp);
+                *cp = -1.f;                 // t_p = 1
             }
-            __syncthreads();
-            const int p = s_p;
-            // (3) row p -> prow (its owner warp; static registers, predicated stores)
-            if (wid == p % kGjWarps) {
-                const int pr = p / kGjWarps;
+            if (wid == pw) {
+                used |= 1u << prr;
+                // (2) row p -> prow2 with entry k = 1, then zero it
 #pragma unroll
                 for (int r = 0; r < kGjRows; ++r)
-                    if (r == pr)
+                    if (r == prr) {
 #pragma unroll
-                        for (int j = 0; j < kGjCols; ++j) prow[lane + 32 * j] = a[r][j];
+                        for (int q = 0; q < kGjPairs; ++q) {
+                            const int c0 = lane + 64 * q;
+                            prow2[32 * q + lane] = make_float2(c0 == k ? 1.f : a[r][q].x,
+                                                               c0 + 32 == k ? 1.f : a[r][q].y);
+                            a[r][q] = make_float2(0.f, 0.f);
+                        }
+                    }
             }
             __syncthreads();
-            // (4) a_i <- s_i a_i + t_i pr for every row
-            const float pinv = 1.f / colk[p];
-            float pr_r[kGjCols];
+            // (3) a_i <- a_i - colk_i pr
+            const float pinv = pinv_s;
+            float2 pr[kGjPairs];
 #pragma unroll
-            for (int j = 0; j < kGjCols; ++j) {
-                const int c = lane + 32 * j;
-                pr_r[j] = (c == k) ? pinv : prow[c] * pinv;
+            for (int q = 0; q < kGjPairs; ++q) pr[q] = __fmul2_rn(prow2[32 * q + lane], make_float2(pinv, pinv));
+            const float4 *cw = reinterpret_cast<const float4 *>(colk[buf] + kGjRows * wid);
+#pragma unroll
+            for (int r4 = 0; r4 < kGjRows / 4; ++r4) {
+                const float4 c4 = cw[r4];
+                const float cr[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 t2 = make_float2(-cr[u], -cr[u]);
+#pragma unroll
+                    for (int q = 0; q < kGjPairs; ++q)
+                        a[4 * r4 + u][q] = __ffma2_rn(t2, pr[q], a[4 * r4 + u][q]);
+                }
             }
-#pragma unroll
-            for (int r = 0; r < kGjRows; ++r) {
-                const int i = wid + kGjWarps * r;
-                const float sc = (i == p) ? 0.f : 1.f;
-                const float t = (i == p) ? 1.f : -colk[i];
-#pragma unroll
-                for (int j = 0; j < kGjCols; ++j) a[r][j] = fmaf(t, pr_r[j], sc * a[r][j]);
+            // (4) publish (and zero) column k + 1 with the pivot candidates for it
+            if (k + 1 < n) {
+                if (kl < 31) {
+                    if (lane == kl + 1) FIL_GJ_PUBLISH(kj, buf ^ 1)
+                } else if (kj + 1 < 2 * kGjPairs) {
+                    if (lane == 0) FIL_GJ_PUBLISH(kj + 1, buf ^ 1)
+                }
             }
             __syncthreads();
         }
     }
-    // A^{-1}[k][m] = S[p_k][q(m)]: element S[i][c] goes to out[q(i)][p_c]
+    // A^{-1}[k][m] = S[p_k][q(m)]: element S[i][c] goes to A[q(i)][p_c]
     for (int k = tid; k < n; k += blockDim.x) qinv[pivrow[k]] = k;
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kGjRows; ++r)
+    for (int r = 0; r < kGjRows; ++r) {
+        const int i = wid + kGjWarps * r;
 #pragma unroll
-        for (int j = 0; j < kGjCols; ++j) {
-            const int i = wid + kGjWarps * r, c = lane + 32 * j;
-            if (i < n && c < n) out[(int64_t)qinv[i] * n + pivrow[c]] = a[r][j];
+        for (int q = 0; q < kGjPairs; ++q) {
+            const int c0 = lane + 64 * q, c1 = c0 + 32;
+            if (i < n && c0 < n) A[(int64_t)qinv[i] * n + pivrow[c0]] = a[r][q].x;
+            if (i < n && c1 < n) A[(int64_t)qinv[i] * n + pivrow[c1]] = a[r][q].y;
         }
-}
-
-// Application of the FP32 inverses as one grid-wide GEMV over every row of
-// every filament (one warp per row, lanes stride the columns with coalesced
-// loads). A refined solve is
-//   x = Inv b;  then kJ0Refine times:  r = b - J0 x (j0_residual_mf_kernel);  x += Inv r.
-__global__ void inv_apply_kernel(Layout lay, const int64_t *__restrict__ jofs,
-                                 const float *__restrict__ inv_all, const float *__restrict__ r,
-                                 double *__restrict__ x, int accumulate) {
-    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (row >= lay.nX) return;
-    const int f = lay.fil_of[row / 6];
-    const int64_t r0 = 6 * (int64_t)lay.off[f];
-    const int n = (int)(6 * (int64_t)lay.off[f + 1] - r0);
-    const int i = (int)(row - r0);
-    const float *A = inv_all + jofs[f] + (int64_t)i * n;
-    const float *rf = r + r0;
-    float t = 0.f;
-    for (int c = lane; c < n; c += 32) t = fmaf(A[c], rf[c], t);
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) t += __shfl_down_sync(0xffffffffu, t, d);
-    if (lane == 0) x[row] = accumulate ? x[row] + (double)t : (double)t;
-}
-
-__global__ void to_float_kernel(int64_t n, const double *__restrict__ b, double *__restrict__ bb,
-                                float *__restrict__ r) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        const double v = b[i];
-        bb[i] = v;
-        r[i] = (float)v;
     }
 }
+#undef FIL_GJ_PUBLISH
 
 }  // namespace
 
@@ -726,7 +822,7 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
     const int N = c->lay.maxN;
     j0_precompute_kernel<<<c->lay.M, kAsmThreads, (size_t)6 * N * sizeof(double), c->stream>>>(
         c->lay, c->auxofs, X, c->qc, c->Yc, c->Tint, dp, c->aux);
-    const size_t smem_asm = (size_t)(5 * N * N + 6 * N) * sizeof(float);
+    const size_t smem_asm = (size_t)(5 * N * N + 51 * N) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(j0_assemble32_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_asm);
@@ -736,7 +832,7 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
 #ifndef FIL_GJ_SHARED_ONLY
     if (6 * N <= kGjMaxN) {
         gauss_jordan_inverse_reg_kernel<<<c->lay.M, 32 * kGjWarps, 0, c->stream>>>(
-            c->lay, c->jofs, c->jinv, c->jinv, c->d_flags);
+            c->lay, c->jofs, c->jinv, c->d_flags);
         e = cudaGetLastError();
     } else
 #endif
@@ -749,30 +845,25 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
     return cudaGetLastError();
 }
 
+size_t j0_solve_smem(int maxN) {
+    const size_t n = 6 * (size_t)maxN;
+    return n * n * sizeof(float) + (2 * n + 15 * (size_t)maxN) * sizeof(double) + n * sizeof(float);
+}
+
 cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x) {
-    // b and x may alias: b is copied into the refinement scratch first
-    const int64_t nX = c->lay.nX;
-    const unsigned grid = (unsigned)((nX * 32 + 255) / 256);
-    double *bb = c->j0_rhs, *xx = c->j0_x;
-    float *rr = reinterpret_cast<float *>(c->j0_res);
     DenseParams dp;
     dp.jp = J0Params{c->dL, c->KB, c->KT, c->g0, c->kmu, c->knu, 0.0, 0.0};
     dp.bdt = c->j0_dp_bdt;
     dp.inv8pieta = 1.0 / (8.0 * kPi * c->eta);
     dp.near2 = 4.0 * c->a * c->a;
     dp.a = c->a;
-    const size_t smem_res = (size_t)15 * c->lay.maxN * sizeof(double);
-    to_float_kernel<<<(unsigned)((nX + 255) / 256), 256, 0, c->stream>>>(nX, b, bb, rr);
-    inv_apply_kernel<<<grid, 256, 0, c->stream>>>(c->lay, c->jofs, c->jinv, rr, xx, 0);
-    for (int it = 0; it < kJ0Refine; ++it) {
-        j0_residual_mf_kernel<<<c->lay.M, kAsmThreads, smem_res, c->stream>>>(
-            c->lay, c->auxofs, dp, c->aux, bb, xx, rr);
-        inv_apply_kernel<<<grid, 256, 0, c->stream>>>(c->lay, c->jofs, c->jinv, rr, xx, 1);
-    }
-    cudaError_t e = cudaMemcpyAsync(x, xx, sizeof(double) * nX, cudaMemcpyDeviceToDevice,
-                                    c->stream);
-    c->n_launches += 2 + 2 * kJ0Refine;
+    const size_t smem = j0_solve_smem(c->lay.maxN);
+    cudaError_t e = cudaFuncSetAttribute(j0_solve_fused_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    j0_solve_fused_kernel<<<c->lay.M, kSolveThreads, smem, c->stream>>>(
+        c->lay, c->jofs, c->auxofs, dp, c->aux, c->jinv, b, x);
+    c->n_launches += 1;
     return cudaGetLastError();
 }
 

@@ -19,11 +19,17 @@
 //
 // Kernel design (GB300, one GPU):
 //  * No tensor cores: the pair sum is not a dense contraction. The bound is the
-//    FP32 (or FP64) FMA pipe; a pair costs ~55 FP32 instructions + 1 MUFU.
+//    FP32 (or FP64) FMA pipe; a pair costs ~51 FP32 operations + 1 MUFU.
 //  * Each thread owns kRpyTargetsPerThread targets in registers; a CTA owns a
 //    tile of kRpyTile targets and streams sources through double-buffered
 //    shared memory in chunks of kRpyChunk; all lanes read the same source
 //    (broadcast), so shared-memory traffic is 3 LDS.128 per source per thread.
+//  * Packed FP32x2 arithmetic (FIL_RPY_PACKED): a thread evaluates its target
+//    against two sources at once, lane x of every float2 holding the even
+//    source and lane y the odd one; the records of a source pair are stored
+//    interleaved so that each loaded float2 is an operand. This halves the
+//    issued FP32 instructions (the scheduler, not the FMA pipe, limited the
+//    one-source form).
 //  * Stream-K persistent grid: the (tile, chunk) work units are split evenly
 //    over G = #SMs x resident-CTAs; a CTA writes one partial per tile it
 //    touches into slot (cta + tile) and a deterministic reduce kernel sums
@@ -32,7 +38,7 @@
 //    ~2 ulp relative accuracy for close pairs; each target sums kRpyComp pair
 //    terms in FP32 and folds them into a (hi, lo) compensated accumulator
 //    (TwoSum); the reduce adds the partials in FP64.
-//  * The inner loop is branch-free (far form with r^2 clamped at contact);
+//  * The inner loop is branch-free (far form only, tracking the smallest r^2);
 //    overlapping pairs are rare, so a group of kRpyComp sources in which a warp
 //    met one is recomputed with the exact far/overlap branches.
 #include <cuda_runtime.h>
@@ -89,6 +95,39 @@ __host__ K make_const(double a) {
 //   [2] = (T_x, T_y, T_z, F_z), with hi = fl32(Y), lo = fl32(Y - hi).
 // Padding records sit far away with zero load, so they add exactly zero.
 // ---------------------------------------------------------------------------
+#if FIL_RPY_PACKED
+// Packed layout: sources 2p and 2p+1 share the kRpyPairF4 float4 at
+// src + kRpyPairF4 p; each float2 holds one component of both (even, odd),
+// positions negated:
+//   (-hi_x, -hi_y) (-hi_z, F_x) (-lo_x, -lo_y) (-lo_z, F_y) (T_x, T_y) (T_z, F_z).
+__global__ void pack32_kernel(const double *__restrict__ Y, const double *__restrict__ FT,
+                              int64_t S, int64_t Spad, float4 *__restrict__ src) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Spad) return;
+    constexpr int kV = 2 * kRpyPairF4;
+    float v[kV];
+    if (i < S) {
+        const double y0 = Y[3 * i], y1 = Y[3 * i + 1], y2 = Y[3 * i + 2];
+        const float h0 = __double2float_rn(y0), h1 = __double2float_rn(y1),
+                    h2 = __double2float_rn(y2);
+        const double *f = FT + 6 * i;
+        v[0] = -h0; v[1] = -h1; v[2] = -h2; v[3] = __double2float_rn(f[0]);
+        v[4] = -__double2float_rn(y0 - (double)h0);
+        v[5] = -__double2float_rn(y1 - (double)h1);
+        v[6] = -__double2float_rn(y2 - (double)h2);
+        v[7] = __double2float_rn(f[1]);
+        v[8] = __double2float_rn(f[3]); v[9] = __double2float_rn(f[4]);
+        v[10] = __double2float_rn(f[5]); v[11] = __double2float_rn(f[2]);
+    } else {
+        v[0] = v[1] = v[2] = -kFarPad;
+#pragma unroll
+        for (int c = 3; c < kV; ++c) v[c] = 0.f;
+    }
+    float *o = reinterpret_cast<float *>(src + kRpyPairF4 * (i >> 1)) + (i & 1);
+#pragma unroll
+    for (int c = 0; c < kV; ++c) o[2 * c] = v[c];
+}
+#else
 __global__ void pack32_kernel(const double *__restrict__ Y, const double *__restrict__ FT,
                               int64_t S, int64_t Spad, float4 *__restrict__ src) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -114,6 +153,7 @@ __global__ void pack32_kernel(const double *__restrict__ Y, const double *__rest
     src[3 * i + 1] = r1;
     src[3 * i + 2] = r2;
 }
+#endif
 
 // FP64 records: 9 doubles per segment (Y, F, T); padding far away, no load.
 __global__ void pack64_kernel(const double *__restrict__ Y, const double *__restrict__ FT,
@@ -225,6 +265,56 @@ __device__ __forceinline__ void pair32_far(float thx, float thy, float thz, floa
     acc[5] = fmaf(C, Tz, fmaf(dT, dz, fmaf(Fx, ey, fmaf(-Fy, ex, acc[5]))));
 }
 
+#if FIL_RPY_PACKED
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+// pair32_far for one target and the two sources of a packed record (q0..q5),
+// lane x = even source, lane y = odd source; same operations, same rounding.
+__device__ __forceinline__ void pair32x2_far(const float2 *th, const float2 *tl, const float4 *q,
+                                             float2 k23, float2 nk2, float2 *acc,
+                                             float &rmin2) {
+    const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3], q4 = q[4], q5 = q[5];
+    const float2 dx = __fadd2_rn(__fadd2_rn(th[0], f2(q0.x, q0.y)), __fadd2_rn(tl[0], f2(q2.x, q2.y)));
+    const float2 dy = __fadd2_rn(__fadd2_rn(th[1], f2(q0.z, q0.w)), __fadd2_rn(tl[1], f2(q2.z, q2.w)));
+    const float2 dz = __fadd2_rn(__fadd2_rn(th[2], f2(q1.x, q1.y)), __fadd2_rn(tl[2], f2(q3.x, q3.y)));
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    rmin2 = fminf(rmin2, fminf(r2.x, r2.y));
+    const float2 rinv = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+    const float2 rinv2 = __fmul2_rn(rinv, rinv);
+    const float2 rinv3 = __fmul2_rn(rinv, rinv2);
+    const float2 rinv5 = __fmul2_rn(rinv3, rinv2);
+    const float2 A = __ffma2_rn(k23, rinv3, rinv);
+    const float2 B = __ffma2_rn(nk2, rinv5, rinv3);
+    const float2 C = __fmul2_rn(f2(-0.5f, -0.5f), rinv3);
+    const float2 D = __fmul2_rn(f2(1.5f, 1.5f), rinv5);
+    const float2 G = rinv3;
+    const float2 Fx = f2(q1.z, q1.w), Fy = f2(q3.z, q3.w), Fz = f2(q5.z, q5.w);
+    const float2 Tx = f2(q4.x, q4.y), Ty = f2(q4.z, q4.w), Tz = f2(q5.x, q5.y);
+    const float2 bF = __fmul2_rn(B, __ffma2_rn(dx, Fx, __ffma2_rn(dy, Fy, __fmul2_rn(dz, Fz))));
+    const float2 dT = __fmul2_rn(D, __ffma2_rn(dx, Tx, __ffma2_rn(dy, Ty, __fmul2_rn(dz, Tz))));
+    const float2 ex = __fmul2_rn(G, dx), ey = __fmul2_rn(G, dy), ez = __fmul2_rn(G, dz);
+    // (negated operands fold into the packed FMA)
+    const float2 nTx = neg2(Tx), nTy = neg2(Ty), nTz = neg2(Tz);
+    const float2 nFx = neg2(Fx), nFy = neg2(Fy), nFz = neg2(Fz);
+    acc[0] = __ffma2_rn(A, Fx, __ffma2_rn(bF, dx, __ffma2_rn(Ty, ez, __ffma2_rn(nTz, ey, acc[0]))));
+    acc[1] = __ffma2_rn(A, Fy, __ffma2_rn(bF, dy, __ffma2_rn(Tz, ex, __ffma2_rn(nTx, ez, acc[1]))));
+    acc[2] = __ffma2_rn(A, Fz, __ffma2_rn(bF, dz, __ffma2_rn(Tx, ey, __ffma2_rn(nTy, ex, acc[2]))));
+    acc[3] = __ffma2_rn(C, Tx, __ffma2_rn(dT, dx, __ffma2_rn(Fy, ez, __ffma2_rn(nFz, ey, acc[3]))));
+    acc[4] = __ffma2_rn(C, Ty, __ffma2_rn(dT, dy, __ffma2_rn(Fz, ex, __ffma2_rn(nFx, ez, acc[4]))));
+    acc[5] = __ffma2_rn(C, Tz, __ffma2_rn(dT, dz, __ffma2_rn(Fx, ey, __ffma2_rn(nFy, ex, acc[5]))));
+}
+
+// Scalar record (pair32's layout) of source h (0 even, 1 odd) of a packed record.
+__device__ __forceinline__ void unpack_source(const float4 *q, int h, float4 &s0, float4 &s1,
+                                              float4 &s2) {
+    const float *f = reinterpret_cast<const float *>(q) + h;
+    s0 = make_float4(-f[0], -f[2], -f[4], f[6]);
+    s1 = make_float4(-f[8], -f[10], -f[12], f[14]);
+    s2 = make_float4(f[16], f[18], f[20], f[22]);
+}
+#endif
+
 // One pair in FP64 (record layout: Y, F, T).
 __device__ __forceinline__ void pair64(double tx, double ty, double tz, const double *s,
                                        const RpyConst64 &k, double *acc) {
@@ -277,7 +367,7 @@ __device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
 __global__ void __launch_bounds__(kRpyThreads, FIL_RPY_MINB)
 rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, int G,
                   RpyConst32 k, float *__restrict__ part) {
-    constexpr int kRec = 3 * kRpyChunk;           // float4 per chunk
+    constexpr int kRec = kRpyPairF4 * (kRpyChunk / 2);   // float4 per chunk
     constexpr int kT = kRpyTargetsPerThread;
     __shared__ float4 sm[2][kRec];
     const int tid = threadIdx.x;
@@ -294,10 +384,26 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
 #pragma unroll
         for (int t = 0; t < kT; ++t) {
             const int64_t n = tile * kRpyTile + t * kRpyThreads + tid;
+#if FIL_RPY_PACKED
+            float4 a0, a1, a2;
+            unpack_source(src + kRpyPairF4 * (n >> 1), (int)(n & 1), a0, a1, a2);
+#else
             const float4 a0 = src[3 * n], a1 = src[3 * n + 1];
+#endif
             th[t][0] = a0.x; th[t][1] = a0.y; th[t][2] = a0.z;
             tl[t][0] = a1.x; tl[t][1] = a1.y; tl[t][2] = a1.z;
         }
+#if FIL_RPY_PACKED
+        float2 thb[kT][3], tlb[kT][3];   // targets broadcast to both lanes
+#pragma unroll
+        for (int t = 0; t < kT; ++t)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                thb[t][c] = f2(th[t][c], th[t][c]);
+                tlb[t][c] = f2(tl[t][c], tl[t][c]);
+            }
+        const float2 k23 = f2(k.k23a2, k.k23a2), nk2 = f2(-k.k2a2, -k.k2a2);
+#endif
         float hi[kT][6], lo[kT][6];
 #pragma unroll
         for (int t = 0; t < kT; ++t)
@@ -306,7 +412,7 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
 
         // first chunk -> buffer 0
         {
-            const float4 *g = src + 3 * (c_begin * kRpyChunk);
+            const float4 *g = src + kRec * c_begin;
             for (int i = tid; i < kRec; i += kRpyThreads) sm[0][i] = g[i];
         }
         __syncthreads();
@@ -318,12 +424,51 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
             float4 pre[kPre];
             const bool has_next = (ch + 1 < c_end);
             if (has_next) {
-                const float4 *g = src + 3 * ((ch + 1) * kRpyChunk);
+                const float4 *g = src + kRec * (ch + 1);
 #pragma unroll
                 for (int r = 0; r < kPre; ++r)
                     if (tid + r * kRpyThreads < kRec) pre[r] = g[tid + r * kRpyThreads];
             }
             const float4 *s = sm[buf];
+#if FIL_RPY_PACKED
+#pragma unroll 1
+            for (int grp = 0; grp < kRpyChunk / kRpyComp; ++grp) {
+                float2 acc2[kT][6];
+#pragma unroll
+                for (int t = 0; t < kT; ++t)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
+                float rmin2 = k.near2;
+#pragma unroll (kRpyUnroll / 2)
+                for (int jp = 0; jp < kRpyComp / 2; ++jp) {
+                    const float4 *q = s + kRpyPairF4 * (grp * (kRpyComp / 2) + jp);
+#pragma unroll
+                    for (int t = 0; t < kT; ++t)
+                        pair32x2_far(thb[t], tlb[t], q, k23, nk2, acc2[t], rmin2);
+                }
+                float acc[kT][6];
+#pragma unroll
+                for (int t = 0; t < kT; ++t)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) acc[t][c] = __fadd_rn(acc2[t][c].x, acc2[t][c].y);
+                if (__any_sync(0xffffffffu, rmin2 < k.near2)) {
+                    // an overlapping (or self) pair: redo this group with the exact branches
+#pragma unroll
+                    for (int t = 0; t < kT; ++t)
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) acc[t][c] = 0.f;
+#pragma unroll 1
+                    for (int j = 0; j < kRpyComp; ++j) {
+                        float4 s0, s1, s2;
+                        unpack_source(s + kRpyPairF4 * ((grp * kRpyComp + j) >> 1), j & 1, s0, s1,
+                                      s2);
+#pragma unroll
+                        for (int t = 0; t < kT; ++t)
+                            pair32(th[t][0], th[t][1], th[t][2], tl[t][0], tl[t][1], tl[t][2], s0,
+                                   s1, s2, k, acc[t]);
+                    }
+                }
+#else
 #pragma unroll 1
             for (int grp = 0; grp < kRpyChunk / kRpyComp; ++grp) {
                 float acc[kT][6];
@@ -357,6 +502,7 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
                                    s1, s2, k, acc[t]);
                     }
                 }
+#endif
 #pragma unroll
                 for (int t = 0; t < kT; ++t)
 #pragma unroll
@@ -540,6 +686,7 @@ cudaError_t rpy_setup(fil_ctx *c) {
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, rpy_pair64_kernel, kRpyThreads, 0);
     if (e != cudaSuccess) return e;
+    if (FIL_RPY_OCC > 0) occ32 = FIL_RPY_OCC;
     c->rpy_grid32 = std::max(1, occ32) * c->num_sms;
     c->rpy_grid64 = std::max(1, occ64) * c->num_sms;
     c->rpy_tiles = (c->lay.S + kRpyTile - 1) / kRpyTile;
@@ -606,7 +753,11 @@ namespace {
 constexpr int64_t kNoAllocMaxSeg = 32768;     // largest S accepted
 constexpr int kNoAllocMaxGrid = 4 * 152;      // stream-K CTAs at most
 constexpr int64_t kNoAllocMaxTiles = (kNoAllocMaxSeg + kRpyTile - 1) / kRpyTile;
-constexpr size_t kNoAllocSrcBytes = (size_t)3 * kNoAllocMaxTiles * kRpyTile * sizeof(float4);
+constexpr int64_t kNoAllocMaxChunks = (kNoAllocMaxSeg + kRpyChunk - 1) / kRpyChunk;
+constexpr int64_t kNoAllocMaxSpad = (kNoAllocMaxTiles * kRpyTile > kNoAllocMaxChunks * kRpyChunk)
+                                        ? kNoAllocMaxTiles * kRpyTile
+                                        : kNoAllocMaxChunks * kRpyChunk;
+constexpr size_t kNoAllocSrcBytes = (size_t)kRpyPairF4 * (kNoAllocMaxSpad / 2) * sizeof(float4);
 constexpr size_t kNoAllocPartBytes =
     (size_t)(kNoAllocMaxGrid + kNoAllocMaxTiles) * 12 * kRpyTile * sizeof(float);
 constexpr size_t kNoAllocBytes = kNoAllocSrcBytes + kNoAllocPartBytes;   // ~10.6 MB

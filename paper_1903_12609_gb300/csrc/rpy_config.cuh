@@ -12,16 +12,30 @@ namespace fil {
 #define FIL_RPY_TPT 2
 #endif
 #ifndef FIL_RPY_UNROLL
-#define FIL_RPY_UNROLL 8
+#define FIL_RPY_UNROLL 4
 #endif
 #ifndef FIL_RPY_MINB
 #define FIL_RPY_MINB 1
 #endif
-constexpr int kRpyThreads = 128;               // threads per CTA
+// 1: the FP32 pair kernel works on two sources at once with packed FP32x2
+// arithmetic (sm_100 family); 0: one source at a time.
+#ifndef FIL_RPY_PACKED
+#define FIL_RPY_PACKED 1
+#endif
+#ifndef FIL_RPY_THREADS
+#define FIL_RPY_THREADS 128
+#endif
+// resident CTAs per SM assumed by the stream-K grid (0: the occupancy API's)
+#ifndef FIL_RPY_OCC
+#define FIL_RPY_OCC 0
+#endif
+constexpr int kRpyThreads = FIL_RPY_THREADS;   // threads per CTA
 constexpr int kRpyUnroll = FIL_RPY_UNROLL;     // unroll of the per-source loop
 constexpr int kRpyTargetsPerThread = FIL_RPY_TPT;   // register-blocked targets
 constexpr int kRpyTile = kRpyThreads * kRpyTargetsPerThread;   // targets per tile
 constexpr int kRpyChunk = 128;                 // sources per shared-memory chunk
 constexpr int kRpyComp = 32;                   // sources per compensated partial (FP32)
+// float4 per two FP32 source records
+constexpr int kRpyPairF4 = 6;
 
 }  // namespace fil
