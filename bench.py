@@ -36,7 +36,10 @@ if ROOT not in sys.path:
 METRIC = ("RPY pair interactions/s (% FMA peak); timesteps/s at 32k segments, "
           "plain vs chosen form")
 UNIT = "pair interactions/s"
-FLOPS_PER_PAIR = 81          # algorithmic flops of one far-field pair (FMA = 2)
+# algorithmic flops of one far-field pair (FMA = 2): the fixed count of the structured
+# far-field formula used as the roofline unit (the kernel itself issues ~51 FP32
+# operations per pair)
+FLOPS_PER_PAIR = 84
 FP32_LANES_PER_SM = 128
 N_SM = 152
 SM_MAX_MHZ = 2070.0
@@ -121,9 +124,10 @@ def cpu_baseline(Y, FT, seconds=10.0):
             "sample": "%d target rows x %d sources of one mobility apply (%.1f s)" % (n, S, dt)}
 
 
-def traffic_from_profile():
-    """DRAM bytes per launch of the pair kernel from the committed ncu record,
-    if it was taken on the current kernel sources (else None)."""
+def counters_from_profile():
+    """ncu counters of the pair kernel (DRAM bytes per launch, FMA-pipe
+    utilisation) from the committed record, if it was taken on the current
+    kernel sources (else an empty dict)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "rpy_pair32_32k_counters.json")
     try:
@@ -132,10 +136,10 @@ def traffic_from_profile():
         for src in rec["sources"]:
             m.update(open(os.path.join(ROOT, src), "rb").read())
         if rec.get("source_sha256") == m.hexdigest():
-            return rec.get("dram_bytes_per_launch")
+            return rec
     except Exception:
         pass
-    return None
+    return {}
 
 
 def run_reference(args, rank):
@@ -213,7 +217,7 @@ def run_mobility(args, fil, torch):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -307,7 +311,8 @@ def main():
     # ---- dominant kernel: the RPY pair kernel, timed live by the library ----
     pair_avg_ms = pair_ms / max(n_pair_launch, 1)
     achieved = FLOPS_PER_PAIR * float(S) * S / (pair_avg_ms * 1e-3) / 1e12
-    traffic = traffic_from_profile() if prec == fil.FIL_MIXED else None
+    prof = counters_from_profile() if prec == fil.FIL_MIXED else {}
+    traffic = prof.get("dram_bytes_per_launch")
 
     # ---- end to end through the C ABI with host buffers ----
     Yh = np.zeros((S, 3)); qh = np.zeros((S, 4)); Yph = np.zeros((S, 3)); uh = np.zeros((S, 3))
@@ -383,6 +388,7 @@ def main():
                      "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS if prec == fil.FIL_MIXED else None,
                      "traffic": traffic, "flops_per_pair": FLOPS_PER_PAIR,
+                     "fma_pipe_active": prof.get("fma_pipe_active"),
                      "avg_launch_ms": pair_avg_ms, "launches": int(n_pair_launch),
                      "share_of_step": pair_ms / dev_ms if dev_ms > 0 else None,
                      "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
