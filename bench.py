@@ -47,16 +47,8 @@ FP32_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80
 
 
 def workload(n_fil=1000, n_seg=32, seed=0):
-    from paper_1903_12609_gb300.inputs import cloud_frames, workload_params
-    wl = workload_params(n_fil, n_seg, B=1000.0, dt_over_T=1.0 / 200.0, tol=1e-4, max_iter=60)
-    base, t, mu, side = cloud_frames(n_fil, n_seg, dL=wl.dL, volume_fraction=0.02, seed=seed)
-    S = n_fil * n_seg
-    passive = np.arange(n_fil) < n_fil // 2
-    Fext = np.zeros((S, 3))
-    Fext[np.repeat(passive, n_seg), 2] = -wl.W * wl.dL
-    L = wl.extra["L"]
-    follower = np.where(passive, 0.0, 100.0 * wl.KB / L ** 2)
-    return wl, base, t, mu, Fext, follower
+    from paper_1903_12609_gb300.inputs import suspension
+    return suspension(n_fil, n_seg, seed=seed)
 
 
 def clocks_start():
@@ -229,6 +221,9 @@ def main():
                     help="approximate Jacobian: filament RPY blocks (default) or App. B.2 drag")
     ap.add_argument("--n-fil", type=int, default=1000,
                     help="filaments of 32 segments (1000 = the 32k suspension; smaller for profiling)")
+    ap.add_argument("--warm", default="prediction_first",
+                    choices=["prediction_first", "best_of_two", "off"],
+                    help="learned warm start of each step (the committed network) and its mode")
     ap.add_argument("--workload", default="suspension", choices=["suspension", "mobility"],
                     help="'mobility': only RPY applies on the 32k configuration (for profiling)")
     args = ap.parse_args()
@@ -272,9 +267,22 @@ def main():
     m.init_straight(base, t, mu, None)
     m.set_external(Fext, None, follower)
 
+    # learned warm start (chosen form): the committed network, trained on other seeds
+    net, warm_mode = None, None
+    if args.warm != "off" and prec == fil.FIL_MIXED:
+        from paper_1903_12609_gb300 import warmstart
+        if os.path.exists(warmstart.DEFAULT_WEIGHTS):
+            net = warmstart.load(max_batch=max(64, n_fil), stream=stream.cuda_stream)
+            warm_mode = (fil.FIL_WARM_PREDICTION_FIRST if args.warm == "prediction_first"
+                         else fil.FIL_WARM_BEST_OF_TWO)
+            fil.fil_warm_attach(m.ctx, net, warm_mode)
+
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         m.step()
+    st0 = [np.zeros((S, 3)), np.zeros((S, 4)), np.zeros((S, 3)), np.zeros((S, 3)),
+           np.zeros((S - n_fil, 3))]
+    m.get_state(*st0)
 
     # ---- timed region: K steps, L2 flushed between steps ----
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -334,7 +342,28 @@ def main():
     e2e_ms = e0.elapsed_time(e1)
     e2e_pairs = (a3 - a2) * float(S) * S
     state_bytes = 8 * (Yh.size + qh.size + Yph.size + uh.size + lh.size)
+
+    # ---- learned warm start vs extrapolation, both from the state before the timed steps ----
+    warm = None
+    if net is not None:
+        warm = {"mode": args.warm, "weights": os.path.relpath(warmstart.DEFAULT_WEIGHTS, ROOT)}
+        K = min(args.steps, 20)
+        for name, use in (("extrapolation", False), ("learned", True)):
+            m.set_state(*st0)
+            fil.fil_warm_attach(m.ctx, net if use else None, warm_mode)
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            barrier()
+            c0.record(stream)
+            its = [m.step() for _ in range(K)]
+            c1.record(stream)
+            barrier()
+            warm[name] = {"timesteps_per_s": K / (c0.elapsed_time(c1) * 1e-3),
+                          "broyden_iters_per_step": float(np.mean(its)), "steps": K}
+        fil.fil_warm_attach(m.ctx, None)
     m.close()
+    if net is not None:
+        fil.fil_mlp_destroy(net)
 
     # ---- plain FP64 form on the same workload (timesteps/s for comparison) ----
     plain = None
@@ -377,9 +406,12 @@ def main():
                         "half sedimenting (B=1000) half tip-follower (fL^2/KB=100), BDF2 "
                         "dt=T/200, Broyden tol 1e-4" % (n_fil, S),
             "segments": S, "precision": args.precision, "j0": args.j0,
+            "initial_guess": ("learned warm start (%s)" % args.warm) if net is not None
+                             else "extrapolation",
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "flushed between timed steps (256 MiB write)"},
         "timesteps_per_s": args.steps / (max_ms * 1e-3),
+        "warm_start": warm,
         "broyden_iters_per_step": float(np.mean(iters)),
         "mobility_applies": int(applies),
         "roofline": {"kernel": "rpy_pair32" if prec == fil.FIL_MIXED else "rpy_pair64",

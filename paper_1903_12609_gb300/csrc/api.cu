@@ -143,6 +143,10 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->stage_a = ar.take<double>(nX);
     c->stage_b = ar.take<double>(nX);
     c->stage_c = ar.take<double>(nX);
+    c->warm_feat = ar.take<float>((size_t)M * FIL_MLP_IN);
+    c->warm_out = ar.take<float>((size_t)M * FIL_MLP_OUT);
+    c->warm_xex = ar.take<double>(nX);
+    c->warm_corr = ar.take<double>(nX);
 }
 
 fil_status read_status(fil_ctx *c, StatusBlock *hs) {
@@ -339,6 +343,7 @@ fil_status fil_set_state(fil_ctx *c, const double *Y, const double *q, const dou
     CK(cudaStreamSynchronize(c->stream));
     c->have_prev = Yprev ? 1 : 0;
     c->hist = 0;
+    c->warm_corr_ok = 0;
     c->in_step = 0;
     return FIL_OK;
 }
@@ -383,6 +388,7 @@ fil_status fil_init_straight(fil_ctx *c, const double *base, const double *t, co
     CK(cudaStreamSynchronize(c->stream));
     c->have_prev = 0;
     c->hist = 0;
+    c->warm_corr_ok = 0;
     c->in_step = 0;
     return FIL_OK;
 }
@@ -438,20 +444,72 @@ fil_status fil_residual(fil_ctx *c, const double *X, double *f, double *finf) {
     return FIL_OK;
 }
 
-fil_status fil_broyden_begin(fil_ctx *c, double *finf) {
+// X_0 of a step: the extrapolation, or -- with a warm-start network attached
+// and use_net set -- the network's prediction: FIL_WARM_BEST_OF_TWO keeps
+// whichever of the two has the smaller ||f||_inf, FIL_WARM_PREDICTION_FIRST
+// the prediction whenever f is finite there. On return Xk, fk hold X_0,
+// f(X_0), and qc, Yc, FT, Tint the unpack of X_0.
+fil_status initial_iterate(fil_ctx *c, bool use_net, double *f0) {
+    CK(extrapolate_guess(c, c->Xk));
+    CK(cudaMemcpyAsync(c->warm_xex, c->Xk, sizeof(double) * c->lay.nX, cudaMemcpyDeviceToDevice,
+                       c->stream));
+    c->warm_from_pred = 0;
+    StatusBlock sb;
+    fil_status s;
+    if (use_net && c->warm_net && c->warm_mode == FIL_WARM_PREDICTION_FIRST) {
+        CK(warm_predict(c, c->Xk, c->Xn));
+        CK(eval_residual(c, c->Xn, c->fn, 2));
+        s = read_status(c, &sb);
+        if (s != FIL_OK) return s;
+        const double fp = finf_of(sb);
+        if (std::isfinite(fp)) {
+            std::swap(c->Xk, c->Xn);
+            std::swap(c->fk, c->fn);
+            *f0 = fp;
+            c->warm_from_pred = 1;
+            c->warm_pred += 1;
+            return FIL_OK;
+        }
+        c->warm_extrap += 1;
+        use_net = false;
+    }
+    CK(eval_residual(c, c->Xk, c->fk, 2));
+    s = read_status(c, &sb);
+    if (s != FIL_OK) return s;
+    *f0 = finf_of(sb);
+    if (!use_net || !c->warm_net) return FIL_OK;
+    CK(warm_predict(c, c->Xk, c->Xn));
+    CK(eval_residual(c, c->Xn, c->fn, 2));
+    s = read_status(c, &sb);
+    if (s != FIL_OK) return s;
+    const double fp = finf_of(sb);
+    if (std::isfinite(fp) && fp < *f0) {
+        std::swap(c->Xk, c->Xn);
+        std::swap(c->fk, c->fn);
+        *f0 = fp;
+        c->warm_from_pred = 1;
+        c->warm_pred += 1;
+    } else {
+        CK(unpack_forces(c, c->Xk, 2));      // back to the unpack of the extrapolation
+        c->warm_extrap += 1;
+    }
+    return FIL_OK;
+}
+
+fil_status begin_step(fil_ctx *c, double *finf, bool use_net) {
     if (!c) return FIL_EINVAL;
     CK(cudaSetDevice(c->device));
     CK(cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), c->stream));
-    CK(extrapolate_guess(c, c->Xk));
-    CK(eval_residual(c, c->Xk, c->fk, 2));
+    double f0 = 0.0;
+    fil_status s = initial_iterate(c, use_net, &f0);
+    if (s != FIL_OK) return s;
     if (c->j0_model == FIL_J0_DRAG)
         CK(j0_build_factor(c, c->Xk));
     else
         CK(j0_dense_build_factor(c, c->Xk));
     StatusBlock sb;
-    fil_status s = read_status(c, &sb);
+    s = read_status(c, &sb);
     if (s != FIL_OK) return s;
-    const double f0 = finf_of(sb);
     if (finf) *finf = f0;
     c->k = 0;
     c->iters_step = 0;
@@ -463,6 +521,8 @@ fil_status fil_broyden_begin(fil_ctx *c, double *finf) {
     c->in_step = 1;
     return FIL_OK;
 }
+
+fil_status fil_broyden_begin(fil_ctx *c, double *finf) { return begin_step(c, finf, true); }
 
 fil_status fil_broyden_step(fil_ctx *c, int32_t *converged, double *finf) {
     if (!c) return FIL_EINVAL;
@@ -532,6 +592,8 @@ fil_status fil_broyden_commit(fil_ctx *c) {
     if (!c->in_step) return set_err(c, FIL_ESTATE, "fil_broyden_commit: no step in progress");
     CK(cudaSetDevice(c->device));
     CK(commit_state(c, c->Xk));
+    CK(warm_record_correction(c));
+    c->warm_corr_ok = 1;
     c->have_prev = 1;
     c->hist += 1;
     c->steps += 1;
@@ -541,24 +603,70 @@ fil_status fil_broyden_commit(fil_ctx *c) {
 
 fil_status fil_step(fil_ctx *c, int32_t *iters) {
     if (!c) return FIL_EINVAL;
-    fil_status s = fil_broyden_begin(c, nullptr);
-    if (s != FIL_OK) return s;
-    int32_t conv = c->conv;
-    while (!conv) {
-        s = fil_broyden_step(c, &conv, nullptr);
-        if (s != FIL_OK) {
-            c->in_step = 0;
-            return s;
+    int32_t total = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        // a start from the network's prediction that fails restarts from the extrapolation
+        fil_status s = begin_step(c, nullptr, attempt == 0);
+        if (s != FIL_OK) return s;
+        int32_t conv = c->conv;
+        while (!conv && s == FIL_OK) s = fil_broyden_step(c, &conv, nullptr);
+        total += c->iters_step;
+        if (s == FIL_OK) {
+            if (iters) *iters = total;
+            return fil_broyden_commit(c);
         }
+        c->in_step = 0;
+        if (!c->warm_from_pred) return s;
+        c->warm_restart += 1;
     }
-    if (iters) *iters = c->iters_step;
-    return fil_broyden_commit(c);
+    return FIL_ECUDA;   // not reached: the second attempt never starts from the prediction
 }
 
 fil_status fil_set_dt(fil_ctx *c, double dt) {
     if (!c) return FIL_EINVAL;
     if (!(dt > 0)) return set_err(c, FIL_EINVAL, "fil_set_dt: dt must be > 0");
     c->dt = dt;
+    return FIL_OK;
+}
+
+fil_status fil_warm_features(fil_ctx *c, float *feat) {
+    if (!c) return FIL_EINVAL;
+    if (!feat || !is_device_ptr(feat)) return set_err(c, FIL_EINVAL, "fil_warm_features: device array");
+    if (c->in_step) return set_err(c, FIL_ESTATE, "fil_warm_features: a step is in progress");
+    CK(cudaSetDevice(c->device));
+    CK(warm_features(c, nullptr, feat));
+    CK(cudaStreamSynchronize(c->stream));
+    return FIL_OK;
+}
+
+fil_status fil_warm_targets(fil_ctx *c, float *targ) {
+    if (!c) return FIL_EINVAL;
+    if (!targ || !is_device_ptr(targ)) return set_err(c, FIL_EINVAL, "fil_warm_targets: device array");
+    if (c->in_step || c->hist < 1)
+        return set_err(c, FIL_ESTATE, "fil_warm_targets: needs a step committed since the last set_state");
+    CK(cudaSetDevice(c->device));
+    CK(warm_targets(c, targ));
+    CK(cudaStreamSynchronize(c->stream));
+    return FIL_OK;
+}
+
+fil_status fil_warm_attach(fil_ctx *c, fil_mlp *net, int32_t mode) {
+    if (!c) return FIL_EINVAL;
+    if (net && mlp_max_batch(net) < c->lay.M)
+        return set_err(c, FIL_EINVAL, "fil_warm_attach: the network's max_batch is below n_fil");
+    if (mode != FIL_WARM_BEST_OF_TWO && mode != FIL_WARM_PREDICTION_FIRST)
+        return set_err(c, FIL_EINVAL, "fil_warm_attach: unknown mode");
+    c->warm_net = net;
+    c->warm_mode = mode;
+    return FIL_OK;
+}
+
+fil_status fil_warm_stats(const fil_ctx *c, int64_t *from_prediction, int64_t *from_extrapolation,
+                          int64_t *restarts) {
+    if (!c) return FIL_EINVAL;
+    if (from_prediction) *from_prediction = c->warm_pred;
+    if (from_extrapolation) *from_extrapolation = c->warm_extrap;
+    if (restarts) *restarts = c->warm_restart;
     return FIL_OK;
 }
 

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/fil.h"
+#include "../../include/fil_mlp.h"
 #include "rpy_config.cuh"
 
 namespace fil {
@@ -106,6 +107,17 @@ struct fil_ctx {
 
     int64_t n_applies, n_iters;
 
+    // learned warm start (include/fil_mlp.h)
+    fil_mlp *warm_net;     // attached network or null
+    float *warm_feat;      // [M x FIL_MLP_IN] network inputs
+    float *warm_out;       // [M x FIL_MLP_OUT] network outputs
+    double *warm_xex;      // [6S] the extrapolated X_0 of the current / last step
+    double *warm_corr;     // [6S] X* - X_ex of the last committed step
+    int warm_corr_ok;      // warm_corr belongs to the current history
+    int warm_mode;         // fil_warm_mode
+    int warm_from_pred;    // the current step started from the prediction
+    int64_t warm_pred, warm_extrap, warm_restart;   // starts from each candidate, restarts
+
     void *arena;           // the single device allocation
     size_t arena_bytes;
 
@@ -136,6 +148,14 @@ cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x);
 
 cudaError_t broyden_axpy_step(fil_ctx *c);                 // Xn = Xk - w
 cudaError_t broyden_dots(fil_ctx *c);                      // alpha_i, ndf2, dff
-cudaError_t broyden_update(fil_ctx *c);                    // history pair, new w
+cudaError_t broyden_update(fil_ctx *c);
+cudaError_t warm_features(fil_ctx *c, const double *Xex, float *feat);
+cudaError_t warm_targets(fil_ctx *c, float *targ);
+cudaError_t warm_record_correction(fil_ctx *c);
+cudaError_t warm_predict(fil_ctx *c, const double *Xex, double *Xpred);
+// network forward pass on `st` (mlp.cu); launches are added to *launches
+cudaError_t mlp_forward_async(fil_mlp *m, const float *x, float *y, int64_t batch,
+                              cudaStream_t st, int64_t *launches);
+int64_t mlp_max_batch(const fil_mlp *m);                    // history pair, new w
 
 }  // namespace fil

@@ -29,7 +29,14 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_get_state", "fil_init_straight", "fil_set_external", "fil_mobility_apply",
             "fil_residual", "fil_broyden_begin", "fil_broyden_step", "fil_get_iterate",
             "fil_j0_solve", "fil_broyden_commit", "fil_step", "fil_set_dt", "fil_counters",
-            "fil_profile", "fil_profile_read", "fil_rpy_apply_noalloc"]
+            "fil_profile", "fil_profile_read", "fil_rpy_apply_noalloc",
+            "fil_mlp_create", "fil_mlp_destroy", "fil_mlp_set_params", "fil_mlp_get_params",
+            "fil_mlp_set_norm", "fil_mlp_forward", "fil_mlp_gradients", "fil_mlp_train_step",
+            "fil_tc_gemm_bf16", "fil_warm_features", "fil_warm_targets", "fil_warm_attach",
+            "fil_warm_stats"]
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_SEG = 800, 256, 192, 32
+MLP_NPARAM = 256 * 800 + 256 + 2 * (256 * 256 + 256) + 192 * 256 + 192
+FIL_WARM_BEST_OF_TWO, FIL_WARM_PREDICTION_FIRST = 0, 1
 
 
 class FilError(RuntimeError):
@@ -78,11 +85,26 @@ def load_library(path=LIB_PATH):
         "fil_profile": [P, ctypes.c_int32],
         "fil_profile_read": [P, I64, D],
         "fil_rpy_apply_noalloc": [ctypes.c_int64, P, P, P, ctypes.c_double, ctypes.c_double, P],
+        "fil_mlp_create": [ctypes.c_int64, P, ctypes.POINTER(P)],
+        "fil_mlp_destroy": [P],
+        "fil_mlp_set_params": [P, P],
+        "fil_mlp_get_params": [P, P],
+        "fil_mlp_set_norm": [P, P, P, P, P],
+        "fil_mlp_forward": [P, P, P, ctypes.c_int64],
+        "fil_mlp_gradients": [P, P, P, ctypes.c_int64, P, ctypes.POINTER(ctypes.c_float)],
+        "fil_mlp_train_step": [P, P, P, ctypes.c_int64, ctypes.c_float,
+                               ctypes.POINTER(ctypes.c_float)],
+        "fil_tc_gemm_bf16": [P, ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int64,
+                             ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P],
+        "fil_warm_features": [P, P],
+        "fil_warm_targets": [P, P],
+        "fil_warm_attach": [P, P, ctypes.c_int32],
+        "fil_warm_stats": [P, I64, I64, I64],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = None if name == "fil_destroy" else (
+        fn.restype = None if name in ("fil_destroy", "fil_mlp_destroy") else (
             ctypes.c_char_p if name == "fil_last_error" else ctypes.c_int)
     return lib
 
@@ -90,16 +112,16 @@ def load_library(path=LIB_PATH):
 _lib = load_library()
 
 
-def _ptr(a):
-    """Device or host address of a float64 C-contiguous array (or None)."""
+def _ptr(a, dtype="float64"):
+    """Device or host address of a C-contiguous array of `dtype` (or None)."""
     if a is None:
         return None
     if hasattr(a, "data_ptr"):                       # torch tensor
-        if a.dtype.__repr__() != "torch.float64" or not a.is_contiguous():
-            raise TypeError("torch tensors must be contiguous float64")
+        if str(a.dtype) != "torch." + dtype or not a.is_contiguous():
+            raise TypeError("torch tensors must be contiguous " + dtype)
         return ctypes.c_void_p(a.data_ptr())
-    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
-        raise TypeError("numpy arrays must be C-contiguous float64")
+    if not (isinstance(a, np.ndarray) and a.dtype == np.dtype(dtype) and a.flags["C_CONTIGUOUS"]):
+        raise TypeError("numpy arrays must be C-contiguous " + dtype)
     return ctypes.c_void_p(a.ctypes.data)
 
 
@@ -222,6 +244,79 @@ def fil_rpy_apply_noalloc(n_seg, Y, FT, VW, a=1.0, eta=1.0, stream=None):
         raise FilError(st, "fil_rpy_apply_noalloc")
 
 
+# ---- warm-start network (include/fil_mlp.h); FP32 arrays ---------------------
+
+def _f32(a):
+    return _ptr(a, "float32")
+
+
+def fil_mlp_create(max_batch, stream=None):
+    m = ctypes.c_void_p()
+    _check(None, _lib.fil_mlp_create(int(max_batch), ctypes.c_void_p(stream) if stream else None,
+                                     ctypes.byref(m)))
+    return m
+
+
+def fil_mlp_destroy(m):
+    _lib.fil_mlp_destroy(m)
+
+
+def fil_mlp_set_params(m, params):
+    _check(None, _lib.fil_mlp_set_params(m, _f32(params)))
+
+
+def fil_mlp_get_params(m, params):
+    _check(None, _lib.fil_mlp_get_params(m, _f32(params)))
+
+
+def fil_mlp_set_norm(m, in_mean, in_std, out_mean, out_std):
+    _check(None, _lib.fil_mlp_set_norm(m, _f32(in_mean), _f32(in_std), _f32(out_mean),
+                                       _f32(out_std)))
+
+
+def fil_mlp_forward(m, x, y, batch):
+    _check(None, _lib.fil_mlp_forward(m, _f32(x), _f32(y), int(batch)))
+
+
+def fil_mlp_gradients(m, x, target, batch, grad):
+    loss = ctypes.c_float()
+    _check(None, _lib.fil_mlp_gradients(m, _f32(x), _f32(target), int(batch), _f32(grad),
+                                        ctypes.byref(loss)))
+    return loss.value
+
+
+def fil_mlp_train_step(m, x, target, batch, lr):
+    loss = ctypes.c_float()
+    _check(None, _lib.fil_mlp_train_step(m, _f32(x), _f32(target), int(batch), float(lr),
+                                         ctypes.byref(loss)))
+    return loss.value
+
+
+def fil_tc_gemm_bf16(A, lda, B, ldb, C, ldc, M, N, K, stream=None):
+    """A, B: uint16 (BF16 bit patterns) device tensors viewed as int16; C float32."""
+    _check(None, _lib.fil_tc_gemm_bf16(_ptr(A, "int16"), int(lda), _ptr(B, "int16"), int(ldb),
+                                       _f32(C), int(ldc), int(M), int(N), int(K),
+                                       ctypes.c_void_p(stream) if stream else None))
+
+
+def fil_warm_features(ctx, feat):
+    _check(ctx, _lib.fil_warm_features(ctx, _f32(feat)))
+
+
+def fil_warm_targets(ctx, targ):
+    _check(ctx, _lib.fil_warm_targets(ctx, _f32(targ)))
+
+
+def fil_warm_attach(ctx, net, mode=FIL_WARM_BEST_OF_TWO):
+    _check(ctx, _lib.fil_warm_attach(ctx, net, int(mode)))
+
+
+def fil_warm_stats(ctx):
+    a, b, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, _lib.fil_warm_stats(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(r)))
+    return a.value, b.value, r.value
+
+
 class Filaments:
     """Owns one context; methods forward to the fil_* functions above."""
 
@@ -248,6 +343,8 @@ class Filaments:
         self.close()
 
     def __getattr__(self, name):
+        if name.startswith("__"):
+            raise AttributeError(name)
         fn = globals().get("fil_" + name)
         if fn is None:
             raise AttributeError(name)

@@ -164,3 +164,22 @@ def workload_params(n_fil: int, n_seg: int, B: float = 1000.0, dt_over_T: float 
     return Workload(n_fil=n_fil, seg_per_fil=[n_seg] * n_fil, a=a, eta=eta, dL=dL, KB=KB,
                     KT=KT_over_KB * KB, W=W, dt=dt_over_T * T, tol=tol, max_iter=max_iter,
                     extra={"L": L, "T": T, "B": B})
+
+
+def suspension(n_fil: int = 1000, n_seg: int = 32, seed: int = 0, volume_fraction: float = 0.02):
+    """The suspension workload: n_fil straight filaments of n_seg segments in a
+    cube at the given volume fraction (cloud_frames), half sedimenting passive
+    filaments (gravity -W dL per segment, B = 1000) and half active filaments
+    driven by a compressive tip follower force f with f L^2 / K_B = 100 (no
+    weight); BDF2 with dt = T/200, Broyden tolerance 1e-4.
+    Returns (Workload, base, t, mu, Fext [S x 3], follower [n_fil])."""
+    wl = workload_params(n_fil, n_seg, B=1000.0, dt_over_T=1.0 / 200.0, tol=1e-4, max_iter=60)
+    base, t, mu, _ = cloud_frames(n_fil, n_seg, dL=wl.dL, volume_fraction=volume_fraction,
+                                  seed=seed)
+    S = n_fil * n_seg
+    passive = np.arange(n_fil) < n_fil // 2
+    Fext = np.zeros((S, 3))
+    Fext[np.repeat(passive, n_seg), 2] = -wl.W * wl.dL
+    L = wl.extra["L"]
+    follower = np.where(passive, 0.0, 100.0 * wl.KB / L ** 2)
+    return wl, base, t, mu, Fext, follower
