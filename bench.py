@@ -206,6 +206,71 @@ def run_mobility(args, fil, torch):
                       "tflops": FLOPS_PER_PAIR * S * S / (avg * 1e-3) / 1e12}), flush=True)
 
 
+def run_ensemble(args, fil, torch):
+    """Batched ensemble: 256 independent suspensions in one context (one launch
+    per kernel, per-system Broyden); JSON line with aggregate and per-system
+    rates."""
+    from paper_1903_12609_gb300.inputs import ensemble
+    rank = int(os.environ.get("RANK", "0"))
+    wl, fps, segs, base, t, mu, Fext, follower = ensemble(args.n_sys, seed=rank)
+    n_sys = len(fps)
+    off = np.concatenate([[0], np.cumsum(fps)])
+    seg_arr = np.array(segs)
+    S_sys = np.array([seg_arr[off[k]:off[k + 1]].sum() for k in range(n_sys)], dtype=np.float64)
+    pairs_per_apply = float(np.sum(S_sys ** 2))
+    stream = torch.cuda.Stream()
+    j0 = fil.FIL_J0_FILAMENT_RPY if max(segs) <= 38 else fil.FIL_J0_DRAG
+    m = fil.Filaments(segs, fil_per_sys=fps, a=wl.a, eta=wl.eta, dL=wl.dL, KB=wl.KB, KT=wl.KT,
+                      dt=wl.dt, tol=wl.tol, max_iter=args.ens_max_iter, precision=fil.FIL_MIXED,
+                      j0_model=j0, stream=stream.cuda_stream)
+    m.init_straight(base, t, mu, None)
+    m.set_external(Fext, None, follower)
+    for _ in range(args.warmup):
+        m.step()
+    a0, i0, k0 = m.counters()
+    m.profile(True)
+    m.profile_read()
+    torch.cuda.synchronize()
+    clk = clocks_start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    iters, sys_iters = [], []
+    e0.record(stream)
+    for _ in range(args.steps):
+        iters.append(m.step())
+        sys_iters.append(m.sys_stats()[0].copy())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clocks_stop(clk, 0)
+    n_pair, pair_ms = m.profile_read()
+    a1, _, k1 = m.counters()
+    m.close()
+    ms = e0.elapsed_time(e1)
+    si = np.array(sys_iters)
+    pair_avg = pair_ms / max(n_pair, 1)
+    achieved = FLOPS_PER_PAIR * pairs_per_apply / (pair_avg * 1e-3) / 1e12
+    print(json.dumps({
+        "metric": METRIC, "value": (a1 - a0) * pairs_per_apply / (ms * 1e-3), "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "ensemble of %d independent suspensions, filaments U[1,64] x "
+                               "segments U[16,48] (%d filaments, %d segments), physics of the "
+                               "32k suspension" % (n_sys, len(segs), int(S_sys.sum())),
+                   "j0": "filament_rpy" if j0 == fil.FIL_J0_FILAMENT_RPY else "drag",
+                   "pairs_per_apply": pairs_per_apply, "parallelism": "single"},
+        "timesteps_per_s_per_system": args.steps / (ms * 1e-3),
+        "system_timesteps_per_s": n_sys * args.steps / (ms * 1e-3),
+        "broyden_iters_per_step": {"max_over_systems": float(np.mean(iters)),
+                                   "mean_over_systems": float(si.mean()),
+                                   "p90_over_systems": float(np.percentile(si, 90))},
+        "roofline": {"kernel": "rpy_pair32", "bound": "alu", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "avg_launch_ms": pair_avg,
+                     "launches": int(n_pair), "share_of_step": pair_ms / ms},
+        "gpu_launches": int(k1 - k0), "clocks": clocks}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -224,7 +289,10 @@ def main():
     ap.add_argument("--warm", default="prediction_first",
                     choices=["prediction_first", "best_of_two", "off"],
                     help="learned warm start of each step (the committed network) and its mode")
-    ap.add_argument("--workload", default="suspension", choices=["suspension", "mobility"],
+    ap.add_argument("--n-sys", type=int, default=256, help="systems of the ensemble workload")
+    ap.add_argument("--ens-max-iter", type=int, default=100)
+    ap.add_argument("--workload", default="suspension",
+                    choices=["suspension", "mobility", "ensemble"],
                     help="'mobility': only RPY applies on the 32k configuration (for profiling)")
     args = ap.parse_args()
 
@@ -244,6 +312,9 @@ def main():
     torch.cuda.set_device(local)
     if args.workload == "mobility":
         run_mobility(args, fil, torch)
+        return
+    if args.workload == "ensemble":
+        run_ensemble(args, fil, torch)
         return
     dist = None
     if world > 1:

@@ -96,6 +96,21 @@ typedef struct {
  * fil_init_straight before stepping. *out is NULL on failure. */
 fil_status fil_create(const fil_params *p, fil_ctx **out);
 
+/* Ensemble of n_sys independent systems in one context (batched suspensions):
+ * the filaments of p are taken in consecutive groups of fil_per_sys[s] >= 1
+ * (HOST array; sum = p->n_fil). The mobility couples segments of the same
+ * system only (Sec. 2.7.1 per system) and every system has its own Broyden
+ * scalars, norms and convergence test (Algorithm 2 per system): a system that
+ * meets the tolerance keeps its iterate while the others continue. All systems
+ * share one launch per kernel (the RPY apply stays one persistent launch over
+ * all systems' work units). fil_create is the case n_sys = 1. */
+fil_status fil_create_ensemble(const fil_params *p, int32_t n_sys, const int32_t *fil_per_sys,
+                               fil_ctx **out);
+
+/* Per system (host arrays of n_sys, nullable): Broyden iterations of the
+ * current / last step and the last ||f||_inf that was read. */
+fil_status fil_sys_stats(const fil_ctx *c, int32_t *iters, double *finf);
+
 /* Release the context and its device memory (synchronises its stream). */
 void fil_destroy(fil_ctx *c);
 

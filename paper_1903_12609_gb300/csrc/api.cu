@@ -9,6 +9,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <limits>
 #include <cstring>
 #include <new>
 #include <string>
@@ -19,10 +20,13 @@ using namespace fil;
 
 namespace {
 
+// Device status: int flags[4] ([0] stall |df| = 0, [1] J0 singular), then
+// the bits of ||f||_inf of every system (atomic max). Read back as:
 struct StatusBlock {
-    unsigned long long finf_bits;
-    int flags[4];   // [0] stall (|df| = 0), [1] J0 singular
+    int flags[4];
+    double fmax;    // max over the systems still iterating (all systems outside a step)
 };
+constexpr int kRedChunk = 2048;   // X entries per Broyden reduction block
 
 fil_status set_err(fil_ctx *c, fil_status s, const std::string &msg) {
     if (c) c->err = msg;
@@ -89,6 +93,12 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->lay.N = ar.take<int>(M);
     c->lay.off = ar.take<int>(M + 1);
     c->lay.fil_of = ar.take<int>(S);
+    c->lay.sys_of = ar.take<int>(S);
+    c->sys_xoff = ar.take<int64_t>(c->n_sys + 1);
+    c->tile_unit_off_d = ar.take<int64_t>(c->rpy_tiles + 1);
+    c->tile_src_d = ar.take<int64_t>(c->rpy_tiles);
+    c->pos_of_seg_d = ar.take<int64_t>(S);
+    c->pad_map_d = ar.take<int>(c->Spad);
     c->Y = ar.take<double>(3 * S);
     c->Yprev = ar.take<double>(3 * S);
     c->q = ar.take<double>(4 * S);
@@ -121,11 +131,15 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->g = ar.take<double>(nX);
     c->C = ar.take<double>((size_t)c->max_iter * nX);
     c->D = ar.take<double>((size_t)c->max_iter * nX);
-    c->scal = ar.take<double>(c->max_iter + 8);
+    c->scal = ar.take<double>((size_t)c->n_sys * c->sstride);
     c->red_part = ar.take<double>((size_t)(c->max_iter + 2) * red_blocks);
-    StatusBlock *sb = ar.take<StatusBlock>(1);
-    c->d_finf = sb ? &sb->finf_bits : nullptr;
-    c->d_flags = sb ? sb->flags : nullptr;
+    c->blk_sys = ar.take<int>(red_blocks);
+    c->blk_beg = ar.take<int64_t>(red_blocks + 1);
+    c->sys_blk_off = ar.take<int>(c->n_sys + 1);
+    c->d_active = ar.take<int>(c->n_sys);
+    char *sb = ar.take<char>(16 + 8 * (size_t)c->n_sys);
+    c->d_flags = sb ? reinterpret_cast<int *>(sb) : nullptr;
+    c->d_finf = sb ? reinterpret_cast<unsigned long long *>(sb + 16) : nullptr;
     if (c->j0_model == FIL_J0_DRAG) {
         c->band = ar.take<double>((size_t)nband * kBandW);
         c->jinv = nullptr;
@@ -149,19 +163,29 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->warm_corr = ar.take<double>(nX);
 }
 
-fil_status read_status(fil_ctx *c, StatusBlock *hs) {
-    CK(cudaMemcpyAsync(c->h_pinned, c->d_finf, sizeof(StatusBlock), cudaMemcpyDeviceToHost,
-                       c->stream));
+// Flags and the per-system norms (into c->finf_h); fmax over the systems still
+// iterating when `active_only`, else over all.
+fil_status read_status(fil_ctx *c, StatusBlock *hs, bool active_only = false) {
+    const size_t bytes = 16 + 8 * (size_t)c->n_sys;
+    CK(cudaMemcpyAsync(c->h_pinned, c->d_flags, bytes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    std::memcpy(hs, c->h_pinned, sizeof(StatusBlock));
+    const char *h = reinterpret_cast<const char *>(c->h_pinned);
+    std::memcpy(hs->flags, h, 16);
+    c->finf_h.resize(c->n_sys);
+    std::memcpy(c->finf_h.data(), h + 16, 8 * (size_t)c->n_sys);
+    double m = 0.0;
+    bool nan = false;
+    for (int s = 0; s < c->n_sys; ++s) {
+        if (active_only && !c->active_h[s]) continue;
+        const double v = c->finf_h[s];
+        if (!(v == v)) nan = true;
+        else if (v > m) m = v;
+    }
+    hs->fmax = nan ? std::numeric_limits<double>::quiet_NaN() : m;
     return FIL_OK;
 }
 
-double finf_of(const StatusBlock &s) {
-    double v;
-    std::memcpy(&v, &s.finf_bits, sizeof(double));
-    return v;
-}
+double finf_of(const StatusBlock &s) { return s.fmax; }
 
 // f(X): unpack + forces (with_forces = 2 also keeps the internal torque for
 // J0), RPY mobility, residual rows, ||f||_inf into the status block.
@@ -181,10 +205,20 @@ cudaError_t j0_apply(fil_ctx *c, const double *b, double *x) {
 
 extern "C" {
 
-fil_status fil_create(const fil_params *p, fil_ctx **out) {
+fil_status fil_create_ensemble(const fil_params *p, int32_t n_sys, const int32_t *fil_per_sys,
+                               fil_ctx **out) {
     if (!out) return FIL_EINVAL;
     *out = nullptr;
     if (!p || p->n_fil < 1 || !p->seg_per_fil) return FIL_EINVAL;
+    if (n_sys < 1 || !fil_per_sys) return FIL_EINVAL;
+    {
+        int64_t nf = 0;
+        for (int s = 0; s < n_sys; ++s) {
+            if (fil_per_sys[s] < 1) return FIL_EINVAL;
+            nf += fil_per_sys[s];
+        }
+        if (nf != p->n_fil) return FIL_EINVAL;
+    }
     if (!(p->a > 0) || !(p->eta > 0) || !(p->dL > 0) || !(p->dt > 0) || !(p->tol > 0) ||
         !(p->KB >= 0) || !(p->KT >= 0) || p->max_iter < 1 ||
         (p->precision != FIL_FP64 && p->precision != FIL_MIXED) ||
@@ -219,6 +253,37 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
     c->g0 = p->gamma0; c->kmu = p->kappa_mu; c->knu = p->kappa_nu;
     c->dt = p->dt; c->tol = p->tol; c->max_iter = p->max_iter; c->prec = p->precision;
     c->j0_model = p->j0_model;
+    c->n_sys = n_sys;
+    c->sys_seg_off_h.assign(n_sys + 1, 0);
+    std::vector<int> sys_of_seg(S);
+    {
+        int f = 0;
+        for (int s = 0; s < n_sys; ++s) {
+            const int f1 = f + fil_per_sys[s];
+            c->sys_seg_off_h[s + 1] = c->off_host[f1];
+            for (int64_t g = c->off_host[f]; g < c->off_host[f1]; ++g) sys_of_seg[g] = s;
+            f = f1;
+        }
+    }
+    c->sstride = c->max_iter + 8;
+    c->active_h.assign(n_sys, 0);
+    c->sys_iters_h.assign(n_sys, 0);
+    c->finf_h.assign(n_sys, 0.0);
+    // Broyden reduction blocks: consecutive slices of at most kRedChunk entries inside a system
+    std::vector<int> blk_sys;
+    std::vector<int64_t> blk_beg;
+    c->sys_blk_off_h.assign(n_sys + 1, 0);
+    for (int s = 0; s < n_sys; ++s) {
+        const int64_t x0 = 6 * c->sys_seg_off_h[s], x1 = 6 * c->sys_seg_off_h[s + 1];
+        for (int64_t x = x0; x < x1; x += kRedChunk) {
+            blk_sys.push_back(s);
+            blk_beg.push_back(x);
+        }
+        c->sys_blk_off_h[s + 1] = (int)blk_sys.size();
+    }
+    blk_beg.push_back(6 * S);
+    std::vector<int64_t> sys_xoff(n_sys + 1);
+    for (int s = 0; s <= n_sys; ++s) sys_xoff[s] = 6 * c->sys_seg_off_h[s];
     std::vector<int64_t> jofs(p->n_fil + 1, 0), auxofs(p->n_fil + 1, 0);
     for (int i = 0; i < p->n_fil; ++i) {
         const int64_t Ni = c->N_host[i];
@@ -248,7 +313,7 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
     if (e != cudaSuccess) return bail(FIL_ECUDA, "cudaDeviceGetAttribute", e);
     e = rpy_setup(c);
     if (e != cudaSuccess) return bail(FIL_ECUDA, "rpy_setup", e);
-    c->red_blocks = 2 * c->num_sms;
+    c->red_blocks = (int)blk_sys.size();
     const size_t pbytes = rpy_partial_bytes(c);
 
     Arena sizing;
@@ -259,7 +324,7 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
     Arena ar;
     ar.base = (char *)c->arena;
     carve(c, ar, c->red_blocks, pbytes);
-    e = cudaMallocHost(&c->h_pinned, 256);
+    e = cudaMallocHost(&c->h_pinned, std::max<size_t>(256, 16 + 8 * (size_t)n_sys));
     if (e != cudaSuccess) return bail(FIL_ENOMEM, "cudaMallocHost", e);
 
     // layout tables and a neutral initial state
@@ -279,6 +344,22 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
         e = cudaMemcpyAsync(c->lay.fil_of, fil_of.data(), sizeof(int) * S,
                             cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->lay.sys_of, sys_of_seg.data(), sizeof(int) * S,
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->sys_xoff, sys_xoff.data(), sizeof(int64_t) * (n_sys + 1),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->blk_sys, blk_sys.data(), sizeof(int) * blk_sys.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->blk_beg, blk_beg.data(), sizeof(int64_t) * blk_beg.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->sys_blk_off, c->sys_blk_off_h.data(), sizeof(int) * (n_sys + 1),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = rpy_upload_tables(c);
+    if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->q, q0.data(), sizeof(double) * 4 * S, cudaMemcpyHostToDevice,
                             c->stream);
     if (e == cudaSuccess && c->jofs)
@@ -291,6 +372,12 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
     if (e != cudaSuccess) return bail(FIL_ECUDA, "initial upload", e);
     *out = c;
     return FIL_OK;
+}
+
+fil_status fil_create(const fil_params *p, fil_ctx **out) {
+    if (!p) return FIL_EINVAL;
+    const int32_t all = p->n_fil;
+    return fil_create_ensemble(p, 1, &all, out);
 }
 
 void fil_destroy(fil_ctx *c) {
@@ -478,6 +565,7 @@ fil_status initial_iterate(fil_ctx *c, bool use_net, double *f0) {
     if (s != FIL_OK) return s;
     *f0 = finf_of(sb);
     if (!use_net || !c->warm_net) return FIL_OK;
+    const std::vector<double> f_ex = c->finf_h;
     CK(warm_predict(c, c->Xk, c->Xn));
     CK(eval_residual(c, c->Xn, c->fn, 2));
     s = read_status(c, &sb);
@@ -491,9 +579,28 @@ fil_status initial_iterate(fil_ctx *c, bool use_net, double *f0) {
         c->warm_pred += 1;
     } else {
         CK(unpack_forces(c, c->Xk, 2));      // back to the unpack of the extrapolation
+        c->finf_h = f_ex;
         c->warm_extrap += 1;
     }
     return FIL_OK;
+}
+
+// Systems whose ||f||_inf is within the tolerance stop iterating (host and
+// device flags); returns the number still active.
+int update_active(fil_ctx *c, bool count_iteration) {
+    int n = 0;
+    for (int sy = 0; sy < c->n_sys; ++sy) {
+        if (!c->active_h[sy]) continue;
+        if (count_iteration) c->sys_iters_h[sy] += 1;
+        if (c->finf_h[sy] <= c->tol * c->a) c->active_h[sy] = 0;
+        else ++n;
+    }
+    return n;
+}
+
+cudaError_t upload_active(fil_ctx *c) {
+    return cudaMemcpyAsync(c->d_active, c->active_h.data(), sizeof(int) * c->n_sys,
+                           cudaMemcpyHostToDevice, c->stream);
 }
 
 fil_status begin_step(fil_ctx *c, double *finf, bool use_net) {
@@ -503,6 +610,7 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net) {
     double f0 = 0.0;
     fil_status s = initial_iterate(c, use_net, &f0);
     if (s != FIL_OK) return s;
+    const std::vector<double> f0_sys = c->finf_h;
     if (c->j0_model == FIL_J0_DRAG)
         CK(j0_build_factor(c, c->Xk));
     else
@@ -510,14 +618,22 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net) {
     StatusBlock sb;
     s = read_status(c, &sb);
     if (s != FIL_OK) return s;
+    c->finf_h = f0_sys;
     if (finf) *finf = f0;
     c->k = 0;
     c->iters_step = 0;
     c->in_step = 0;
     if (sb.flags[1]) return set_err(c, FIL_ENAN, "fil_broyden_begin: J0 is singular");
     if (!std::isfinite(f0)) return set_err(c, FIL_ENAN, "fil_broyden_begin: f(X_0) not finite");
-    c->conv = (f0 <= c->tol * c->a) ? 1 : 0;
-    if (!c->conv) CK(j0_apply(c, c->fk, c->w));
+    c->active_h.assign(c->n_sys, 1);
+    c->sys_iters_h.assign(c->n_sys, 0);
+    const int n_active = update_active(c, false);
+    c->conv = n_active == 0 ? 1 : 0;
+    if (!c->conv) {
+        CK(upload_active(c));
+        CK(j0_apply(c, c->fk, c->w));
+        CK(broyden_mask_inactive(c, c->w));
+    }
     c->in_step = 1;
     return FIL_OK;
 }
@@ -545,13 +661,14 @@ fil_status fil_broyden_step(fil_ctx *c, int32_t *converged, double *finf) {
     if (!std::isfinite(fv)) return set_err(c, FIL_ENAN, "Broyden: residual not finite");
     c->iters_step += 1;
     c->n_iters += 1;
-    if (fv <= c->tol * c->a) {
+    if (update_active(c, true) == 0) {
         std::swap(c->Xk, c->Xn);
         std::swap(c->fk, c->fn);
         c->conv = 1;
         if (converged) *converged = 1;
         return FIL_OK;
     }
+    if (c->n_sys > 1) CK(upload_active(c));
     CK(broyden_dots(c));
     CK(j0_apply(c, c->fn, c->g));
     CK(broyden_update(c));
@@ -667,6 +784,15 @@ fil_status fil_warm_stats(const fil_ctx *c, int64_t *from_prediction, int64_t *f
     if (from_prediction) *from_prediction = c->warm_pred;
     if (from_extrapolation) *from_extrapolation = c->warm_extrap;
     if (restarts) *restarts = c->warm_restart;
+    return FIL_OK;
+}
+
+fil_status fil_sys_stats(const fil_ctx *c, int32_t *iters, double *finf) {
+    if (!c) return FIL_EINVAL;
+    for (int sy = 0; sy < c->n_sys; ++sy) {
+        if (iters) iters[sy] = c->sys_iters_h[sy];
+        if (finf) finf[sy] = c->finf_h[sy];
+    }
     return FIL_OK;
 }
 

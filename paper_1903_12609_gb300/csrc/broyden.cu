@@ -8,8 +8,12 @@
 // which is the algorithm's update with H_k f_{k+1} computed once and reused
 // for the next step (one J0 solve per iteration).
 //
-// Dot products are reduced deterministically: a fixed grid writes one partial
-// per block and output, and a single block adds the partials in block order.
+// Dot products and norms are taken per system (ensembles of independent
+// systems; one system otherwise) and reduced deterministically: every block
+// covers a slice of one system and writes one partial per output, and a warp
+// per (system, output) adds the system's partials in block order. Systems that
+// have converged (active = 0) keep their iterate: their step w is zero and
+// their history is not updated.
 #include <cuda_runtime.h>
 
 #include "fil_internal.cuh"
@@ -39,18 +43,20 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return s;
 }
 
-// Outputs o = 0..k-1: d_o . fn;  o = k: |fn - fk|^2;  o = k+1: (fn - fk) . fn.
+// Outputs o = 0..k-1: d_o . fn;  o = k: |fn - fk|^2;  o = k+1: (fn - fk) . fn,
+// over the X slice [blk_beg[b], blk_beg[b+1]) of block b.
 __global__ void dots_partial_kernel(int64_t n, const double *__restrict__ fn,
                                     const double *__restrict__ fk, const double *__restrict__ D,
-                                    int k, double *__restrict__ part) {
+                                    int k, const int64_t *__restrict__ blk_beg,
+                                    double *__restrict__ part) {
     __shared__ double sh[kRedThreads / 32];
     const int nout = k + 2;
+    const int64_t i0 = blk_beg[blockIdx.x], i1 = blk_beg[blockIdx.x + 1];
     for (int o0 = 0; o0 < nout; o0 += kDotGroup) {
         double acc[kDotGroup];
 #pragma unroll
         for (int j = 0; j < kDotGroup; ++j) acc[j] = 0.0;
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-             i += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             const double f = fn[i];
             const double df = f - fk[i];
 #pragma unroll
@@ -72,29 +78,39 @@ __global__ void dots_partial_kernel(int64_t n, const double *__restrict__ fn,
     }
 }
 
-__global__ void dots_final_kernel(int nout, int nblocks, const double *__restrict__ part,
+__global__ void dots_final_kernel(int n_sys, int nout, int nblocks, const int *__restrict__ sys_blk,
+                                  const double *__restrict__ part, int sstride,
                                   double *__restrict__ out) {
-    // one warp per output, lanes stride the partials, fixed-order tree
-    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // one warp per (system, output), lanes stride the system's partials, fixed-order tree
+    const int64_t job = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (o >= nout) return;
+    if (job >= (int64_t)n_sys * nout) return;
+    const int sy = (int)(job / nout), o = (int)(job - (int64_t)sy * nout);
     double s = 0.0;
-    for (int b = lane; b < nblocks; b += 32) s += part[(int64_t)o * nblocks + b];
+    for (int b = sys_blk[sy] + lane; b < sys_blk[sy + 1]; b += 32) s += part[(int64_t)o * nblocks + b];
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
-    if (lane == 0) out[o] = s;
+    if (lane == 0) out[(int64_t)sy * sstride + o] = s;
 }
 
-// g += sum_i c_i alpha_i; history pair k; w = g + c_k (df . fn)/|df|.
-__global__ void update_kernel(int64_t n, int k, const double *__restrict__ scal,
+// g += sum_i c_i alpha_i; history pair k; w = g + c_k (df . fn)/|df|, with the
+// scalars of entry i's system; w = 0 in systems that have converged.
+__global__ void update_kernel(int64_t n, int k, const double *__restrict__ scal_all, int sstride,
+                              const int *__restrict__ sys_of, const int *__restrict__ active,
                               const double *__restrict__ fn, const double *__restrict__ fk,
                               double *__restrict__ g, double *__restrict__ C,
                               double *__restrict__ D, double *__restrict__ w,
                               int *__restrict__ flags) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const double ndf2 = scal[k];
-    if (i == 0 && !(ndf2 > 0.0)) flags[0] = 1;
     if (i >= n) return;
+    const int sy = sys_of[i / 6];
+    if (!active[sy]) {
+        w[i] = 0.0;
+        return;
+    }
+    const double *scal = scal_all + (int64_t)sy * sstride;
+    const double ndf2 = scal[k];
+    if (!(ndf2 > 0.0)) flags[0] = 1;
     double gi = g[i];
     for (int l = 0; l < k; ++l) gi += C[(int64_t)l * n + i] * scal[l];
     const double ndf = sqrt(ndf2);
@@ -105,7 +121,22 @@ __global__ void update_kernel(int64_t n, int k, const double *__restrict__ scal,
     w[i] = gi + c * (scal[k + 1] / ndf);
 }
 
+__global__ void mask_inactive_kernel(int64_t n, const int *__restrict__ sys_of,
+                                     const int *__restrict__ active, double *__restrict__ v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !active[sys_of[i / 6]]) v[i] = 0.0;
+}
+
 }  // namespace
+
+cudaError_t broyden_mask_inactive(fil_ctx *c, double *v) {
+    if (c->n_sys == 1) return cudaSuccess;      // the one system is active inside a step
+    const int64_t n = c->lay.nX;
+    mask_inactive_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->lay.sys_of,
+                                                                             c->d_active, v);
+    c->n_launches += 1;
+    return cudaGetLastError();
+}
 
 cudaError_t broyden_axpy_step(fil_ctx *c) {
     const int64_t n = c->lay.nX;
@@ -117,10 +148,11 @@ cudaError_t broyden_axpy_step(fil_ctx *c) {
 cudaError_t broyden_dots(fil_ctx *c) {
     const int64_t n = c->lay.nX;
     dots_partial_kernel<<<c->red_blocks, kRedThreads, 0, c->stream>>>(n, c->fn, c->fk, c->D, c->k,
-                                                                       c->red_part);
+                                                                       c->blk_beg, c->red_part);
     const int nout = c->k + 2;
-    dots_final_kernel<<<(nout + 7) / 8, 256, 0, c->stream>>>(nout, c->red_blocks, c->red_part,
-                                                             c->scal);
+    const int64_t jobs = (int64_t)c->n_sys * nout;
+    dots_final_kernel<<<(unsigned)((jobs + 7) / 8), 256, 0, c->stream>>>(
+        c->n_sys, nout, c->red_blocks, c->sys_blk_off, c->red_part, c->sstride, c->scal);
     c->n_launches += 2;
     return cudaGetLastError();
 }
@@ -128,7 +160,8 @@ cudaError_t broyden_dots(fil_ctx *c) {
 cudaError_t broyden_update(fil_ctx *c) {
     const int64_t n = c->lay.nX;
     update_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
-        n, c->k, c->scal, c->fn, c->fk, c->g, c->C, c->D, c->w, c->d_flags);
+        n, c->k, c->scal, c->sstride, c->lay.sys_of, c->d_active, c->fn, c->fk, c->g, c->C, c->D,
+        c->w, c->d_flags);
     c->n_launches += 1;
     return cudaGetLastError();
 }

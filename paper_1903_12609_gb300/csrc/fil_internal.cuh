@@ -40,6 +40,7 @@ struct Layout {
     int *N = nullptr;        // [M]
     int *off = nullptr;      // [M+1] segment offsets
     int *fil_of = nullptr;   // [S] filament of a segment
+    int *sys_of = nullptr;   // [S] system of a segment (ensembles; one system: all 0)
 };
 
 }  // namespace fil
@@ -68,21 +69,40 @@ struct fil_ctx {
     // residual-evaluation buffers
     double *qc, *Yc, *FT, *Tint, *VW, *Mh;
 
-    // RPY workspace
+    // independent systems (ensembles): consecutive groups of filaments; the
+    // mobility couples segments of the same system only, and each system has
+    // its own Broyden scalars and convergence
+    int n_sys;
+    std::vector<int64_t> sys_seg_off_h;   // [n_sys + 1] segment offsets
+    int64_t *sys_xoff;                    // [n_sys + 1] offsets into X (6 x segments)
+
+    // RPY workspace; systems padded to whole target tiles (rpy.cu)
     float4 *src32;        // 3 float4 per (padded) segment, mixed path
     double *src64;        // 12 doubles per (padded) segment, FP64 path
     int64_t Spad;
     void *partials;       // stream-K partial sums
     int rpy_grid32, rpy_grid64;
-    int64_t rpy_tiles;
+    int64_t rpy_tiles, rpy_units;
+    std::vector<int64_t> sys_pad_off_h, tile_unit_off_h, tile_src_h, pos_of_seg_h;
+    std::vector<int> pad_map_h;
+    int64_t *tile_unit_off_d, *tile_src_d, *pos_of_seg_d;
+    int *pad_map_d;
 
     // Broyden state
     double *Xk, *fk, *Xn, *fn, *w, *g, *C, *D;
-    double *scal;          // device scalars: [alpha_0..alpha_{max-1}, ndf2, dff, ...]
-    double *red_part;      // reduction partials
-    int red_blocks;
-    unsigned long long *d_finf;   // atomic max of |f| bits
+    double *scal;          // per system (stride sstride): [alpha_0..alpha_{k-1}, ndf2, dff]
+    int sstride;
+    double *red_part;      // reduction partials, [(max_iter + 2) x red_blocks]
+    int red_blocks;        // reduction blocks, each inside one system
+    int *blk_sys;          // [red_blocks] system of a block
+    int64_t *blk_beg;      // [red_blocks + 1] X range of a block (contiguous per system)
+    int *sys_blk_off;      // [n_sys + 1] first block of each system
+    std::vector<int> sys_blk_off_h;
+    unsigned long long *d_finf;   // [n_sys] atomic max of |f| bits per system
     int *d_flags;          // [0] stall flag, [1] singular J0 flag
+    int *d_active;         // [n_sys] system still iterating in the current step
+    std::vector<int> active_h, sys_iters_h;   // host copies; iterations per system
+    std::vector<double> finf_h;               // ||f||_inf per system, last read
     double *h_pinned;      // small pinned host buffer
     int k;                 // stored (c, d) pairs of the current step
     int in_step;           // a step was begun and not committed
@@ -131,7 +151,8 @@ namespace fil {
 
 // Launchers (all enqueue on c->stream and return a cudaError_t).
 cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW);
-cudaError_t rpy_setup(fil_ctx *c);          // grid sizes, called once at create
+cudaError_t rpy_setup(fil_ctx *c);          // grid sizes and padded layout, once at create
+cudaError_t rpy_upload_tables(fil_ctx *c);  // the layout tables, after the arena exists
 size_t rpy_partial_bytes(const fil_ctx *c);
 
 cudaError_t unpack_forces(fil_ctx *c, const double *X, int with_forces);
@@ -149,6 +170,7 @@ cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x);
 cudaError_t broyden_axpy_step(fil_ctx *c);                 // Xn = Xk - w
 cudaError_t broyden_dots(fil_ctx *c);                      // alpha_i, ndf2, dff
 cudaError_t broyden_update(fil_ctx *c);
+cudaError_t broyden_mask_inactive(fil_ctx *c, double *v);   // v = 0 in converged systems
 cudaError_t warm_features(fil_ctx *c, const double *Xex, float *feat);
 cudaError_t warm_targets(fil_ctx *c, float *targ);
 cudaError_t warm_record_correction(fil_ctx *c);

@@ -115,8 +115,9 @@ struct Scheme {
     double a1, a0, bdt, g;   // f = Y - a1 Y^j - a0 Y^{j-1} - bdt V ; u - g u^j - bdt dexpinv
 };
 
-// One thread per segment: both 3-rows of the residual, plus ||f||_inf (as the
-// maximum of the IEEE bit patterns of |f|; a NaN compares above every number).
+// One thread per segment: both 3-rows of the residual, plus ||f||_inf of the
+// segment's system (as the maximum of the IEEE bit patterns of |f|; a NaN
+// compares above every number).
 __global__ void residual_rows_kernel(Layout lay, const double *__restrict__ X,
                                      const double *__restrict__ Yc,
                                      const double *__restrict__ VW,
@@ -148,12 +149,19 @@ __global__ void residual_rows_kernel(Layout lay, const double *__restrict__ X,
             0x7ff8000000000000ll);
     }
     unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+    const int sid = g < lay.S ? lay.sys_of[g] : -1;
+    const int sid0 = __shfl_sync(0xffffffffu, sid, 0);
+    if (__all_sync(0xffffffffu, sid == sid0 || sid < 0)) {
+        // the warp's segments belong to one system (the usual case)
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        unsigned long long o = __shfl_down_sync(0xffffffffu, bits, d);
-        bits = o > bits ? o : bits;
+        for (int d = 16; d > 0; d >>= 1) {
+            unsigned long long o = __shfl_down_sync(0xffffffffu, bits, d);
+            bits = o > bits ? o : bits;
+        }
+        if ((threadIdx.x & 31) == 0 && sid0 >= 0) atomicMax(finf_bits + sid0, bits);
+    } else if (sid >= 0) {
+        atomicMax(finf_bits + sid, bits);
     }
-    if ((threadIdx.x & 31) == 0) atomicMax(finf_bits, bits);
 }
 
 // Straight filaments from (base, t, mu) with the App. A.1 construction and an
@@ -277,7 +285,7 @@ cudaError_t residual_rows(fil_ctx *c, const double *X, double *f) {
     } else {
         sc = {1.0, 0.0, c->dt, 0.0};
     }
-    cudaError_t e = cudaMemsetAsync(c->d_finf, 0, sizeof(unsigned long long), c->stream);
+    cudaError_t e = cudaMemsetAsync(c->d_finf, 0, sizeof(unsigned long long) * c->n_sys, c->stream);
     if (e != cudaSuccess) return e;
     residual_rows_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(
         c->lay, X, c->Yc, c->VW, c->Y, c->Yprev, c->uprev, sc, f, c->d_finf);

@@ -90,6 +90,53 @@ __host__ K make_const(double a) {
 }
 
 // ---------------------------------------------------------------------------
+// Ensembles of independent systems: every system is padded to whole target
+// tiles (kRpyTile) in the source/target layout, so that a work unit (tile,
+// source chunk) never mixes systems and the apply stays one persistent launch.
+// System s owns padded positions [pad_off[s], pad_off[s+1]); its tiles come
+// in order, each with ceil(S_s / kRpyChunk) source chunks, and padding records
+// sit far away with zero load. With null tables there is one system whose
+// padded position equals the segment index (tile = u / n_chunks).
+// ---------------------------------------------------------------------------
+struct SysMap {
+    const int64_t *tile_unit_off;  // [n_tiles + 1] first unit of each tile
+    const int64_t *tile_src;       // [n_tiles] padded position of the tile's first source
+    const int64_t *pos_of_seg;     // [S] padded position of each segment
+    const int *pad_map;            // [Spad] segment at a padded position, or -1
+    int64_t n_tiles, n_chunks;     // n_chunks: the one-system case
+};
+
+__device__ __forceinline__ int64_t tile_unit_begin(const SysMap &m, int64_t tile) {
+    return m.tile_unit_off ? m.tile_unit_off[tile] : tile * m.n_chunks;
+}
+
+// Tile of work unit u, the tile's first unit and chunk count, and its first source.
+__device__ __forceinline__ void locate_unit(const SysMap &m, int64_t u, int64_t &tile,
+                                            int64_t &ubeg, int64_t &nch, int64_t &src0) {
+    if (!m.tile_unit_off) {
+        tile = u / m.n_chunks;
+        ubeg = tile * m.n_chunks;
+        nch = m.n_chunks;
+        src0 = 0;
+        return;
+    }
+    int64_t lo = 0, hi = m.n_tiles;      // tile_unit_off[lo] <= u < tile_unit_off[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (m.tile_unit_off[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    tile = lo;
+    ubeg = m.tile_unit_off[lo];
+    nch = m.tile_unit_off[lo + 1] - ubeg;
+    src0 = m.tile_src[lo];
+}
+
+__device__ __forceinline__ int64_t segment_at(const SysMap &m, int64_t P, int64_t S) {
+    return m.pad_map ? (int64_t)m.pad_map[P] : (P < S ? P : -1);
+}
+
+// ---------------------------------------------------------------------------
 // Pack: FP64 (Y, FT) -> padded FP32 source records, 3 float4 per segment:
 //   [0] = (hi_x, hi_y, hi_z, F_x), [1] = (lo_x, lo_y, lo_z, F_y),
 //   [2] = (T_x, T_y, T_z, F_z), with hi = fl32(Y), lo = fl32(Y - hi).
@@ -101,12 +148,13 @@ __host__ K make_const(double a) {
 // positions negated:
 //   (-hi_x, -hi_y) (-hi_z, F_x) (-lo_x, -lo_y) (-lo_z, F_y) (T_x, T_y) (T_z, F_z).
 __global__ void pack32_kernel(const double *__restrict__ Y, const double *__restrict__ FT,
-                              int64_t S, int64_t Spad, float4 *__restrict__ src) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Spad) return;
+                              int64_t S, int64_t Spad, SysMap sm, float4 *__restrict__ src) {
+    const int64_t P = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= Spad) return;
+    const int64_t i = segment_at(sm, P, S);
     constexpr int kV = 2 * kRpyPairF4;
     float v[kV];
-    if (i < S) {
+    if (i >= 0) {
         const double y0 = Y[3 * i], y1 = Y[3 * i + 1], y2 = Y[3 * i + 2];
         const float h0 = __double2float_rn(y0), h1 = __double2float_rn(y1),
                     h2 = __double2float_rn(y2);
@@ -123,17 +171,18 @@ __global__ void pack32_kernel(const double *__restrict__ Y, const double *__rest
 #pragma unroll
         for (int c = 3; c < kV; ++c) v[c] = 0.f;
     }
-    float *o = reinterpret_cast<float *>(src + kRpyPairF4 * (i >> 1)) + (i & 1);
+    float *o = reinterpret_cast<float *>(src + kRpyPairF4 * (P >> 1)) + (P & 1);
 #pragma unroll
     for (int c = 0; c < kV; ++c) o[2 * c] = v[c];
 }
 #else
 __global__ void pack32_kernel(const double *__restrict__ Y, const double *__restrict__ FT,
-                              int64_t S, int64_t Spad, float4 *__restrict__ src) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Spad) return;
+                              int64_t S, int64_t Spad, SysMap sm, float4 *__restrict__ src) {
+    const int64_t P = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= Spad) return;
+    const int64_t i = segment_at(sm, P, S);
     float4 r0, r1, r2;
-    if (i < S) {
+    if (i >= 0) {
         double y0 = Y[3 * i], y1 = Y[3 * i + 1], y2 = Y[3 * i + 2];
         float h0 = __double2float_rn(y0), h1 = __double2float_rn(y1), h2 = __double2float_rn(y2);
         float l0 = __double2float_rn(y0 - (double)h0);
@@ -149,19 +198,20 @@ __global__ void pack32_kernel(const double *__restrict__ Y, const double *__rest
         r1 = make_float4(0.f, 0.f, 0.f, 0.f);
         r2 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    src[3 * i] = r0;
-    src[3 * i + 1] = r1;
-    src[3 * i + 2] = r2;
+    src[3 * P] = r0;
+    src[3 * P + 1] = r1;
+    src[3 * P + 2] = r2;
 }
 #endif
 
 // FP64 records: 9 doubles per segment (Y, F, T); padding far away, no load.
 __global__ void pack64_kernel(const double *__restrict__ Y, const double *__restrict__ FT,
-                              int64_t S, int64_t Spad, double *__restrict__ src) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Spad) return;
-    double *o = src + 9 * i;
-    if (i < S) {
+                              int64_t S, int64_t Spad, SysMap sm, double *__restrict__ src) {
+    const int64_t P = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= Spad) return;
+    const int64_t i = segment_at(sm, P, S);
+    double *o = src + 9 * P;
+    if (i >= 0) {
         o[0] = Y[3 * i];
         o[1] = Y[3 * i + 1];
         o[2] = Y[3 * i + 2];
@@ -365,8 +415,8 @@ __device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
 // (hi, lo) accumulators.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRpyThreads, FIL_RPY_MINB)
-rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, int G,
-                  RpyConst32 k, float *__restrict__ part) {
+rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G, RpyConst32 k,
+                  float *__restrict__ part) {
     constexpr int kRec = kRpyPairF4 * (kRpyChunk / 2);   // float4 per chunk
     constexpr int kT = kRpyTargetsPerThread;
     __shared__ float4 sm[2][kRec];
@@ -376,9 +426,11 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
     const int64_t u_end = unit_start(b + 1, W, G);
 
     while (u < u_end) {
-        const int64_t tile = u / n_chunks;
-        const int64_t c_begin = u - tile * n_chunks;
+        int64_t tile, ubeg, n_chunks, src0;
+        locate_unit(smap, u, tile, ubeg, n_chunks, src0);
+        const int64_t c_begin = u - ubeg;
         const int64_t c_end = min(n_chunks, c_begin + (u_end - u));
+        const float4 *srcs = src + kRec * (src0 / kRpyChunk);   // this tile's system
 
         float th[kT][3], tl[kT][3];
 #pragma unroll
@@ -412,7 +464,7 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
 
         // first chunk -> buffer 0
         {
-            const float4 *g = src + kRec * c_begin;
+            const float4 *g = srcs + kRec * c_begin;
             for (int i = tid; i < kRec; i += kRpyThreads) sm[0][i] = g[i];
         }
         __syncthreads();
@@ -424,7 +476,7 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
             float4 pre[kPre];
             const bool has_next = (ch + 1 < c_end);
             if (has_next) {
-                const float4 *g = src + kRec * (ch + 1);
+                const float4 *g = srcs + kRec * (ch + 1);
 #pragma unroll
                 for (int r = 0; r < kPre; ++r)
                     if (tid + r * kRpyThreads < kRec) pre[r] = g[tid + r * kRpyThreads];
@@ -532,7 +584,7 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
                 p[(6 + c) * kRpyTile + local] = lo[t][c];
             }
         }
-        u = tile * n_chunks + c_end;
+        u = ubeg + c_end;
     }
 }
 
@@ -540,8 +592,8 @@ rpy_pair32_kernel(const float4 *__restrict__ src, int64_t n_chunks, int64_t W, i
 // FP64 pair kernel (same stream-K scaffolding).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRpyThreads)
-rpy_pair64_kernel(const double *__restrict__ src, int64_t n_chunks, int64_t W, int G,
-                  RpyConst64 k, double *__restrict__ part) {
+rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G, RpyConst64 k,
+                  double *__restrict__ part) {
     constexpr int kRec = 9 * kRpyChunk;
     __shared__ double sm[2][kRec];
     const int tid = threadIdx.x;
@@ -550,9 +602,11 @@ rpy_pair64_kernel(const double *__restrict__ src, int64_t n_chunks, int64_t W, i
     const int64_t u_end = unit_start(b + 1, W, G);
 
     while (u < u_end) {
-        const int64_t tile = u / n_chunks;
-        const int64_t c_begin = u - tile * n_chunks;
+        int64_t tile, ubeg, n_chunks, src0;
+        locate_unit(smap, u, tile, ubeg, n_chunks, src0);
+        const int64_t c_begin = u - ubeg;
         const int64_t c_end = min(n_chunks, c_begin + (u_end - u));
+        const double *srcs = src + 9 * src0;
 
         double ty[kRpyTargetsPerThread][3];
 #pragma unroll
@@ -569,7 +623,7 @@ rpy_pair64_kernel(const double *__restrict__ src, int64_t n_chunks, int64_t W, i
             for (int c = 0; c < 6; ++c) acc[t][c] = 0.0;
 
         {
-            const double *g = src + 9 * (c_begin * kRpyChunk);
+            const double *g = srcs + 9 * (c_begin * kRpyChunk);
             for (int i = tid; i < kRec; i += kRpyThreads) sm[0][i] = g[i];
         }
         __syncthreads();
@@ -578,7 +632,7 @@ rpy_pair64_kernel(const double *__restrict__ src, int64_t n_chunks, int64_t W, i
             double pre[(kRec + kRpyThreads - 1) / kRpyThreads];
             const bool has_next = (ch + 1 < c_end);
             if (has_next) {
-                const double *g = src + 9 * ((ch + 1) * kRpyChunk);
+                const double *g = srcs + 9 * ((ch + 1) * kRpyChunk);
 #pragma unroll
                 for (int r = 0; r < (kRec + kRpyThreads - 1) / kRpyThreads; ++r) {
                     const int i = tid + r * kRpyThreads;
@@ -608,7 +662,7 @@ rpy_pair64_kernel(const double *__restrict__ src, int64_t n_chunks, int64_t W, i
 #pragma unroll
             for (int c = 0; c < 6; ++c) p[c * kRpyTile + local] = acc[t][c];
         }
-        u = tile * n_chunks + c_end;
+        u = ubeg + c_end;
     }
 }
 
@@ -616,24 +670,25 @@ rpy_pair64_kernel(const double *__restrict__ src, int64_t n_chunks, int64_t W, i
 // Reduce the stream-K partials of each target (in CTA order) and scale by
 // 1/(8 pi eta). One thread per target.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cta_range_of_tile(int64_t tile, int64_t n_chunks, int64_t W,
+__device__ __forceinline__ void cta_range_of_tile(const SysMap &sm, int64_t tile, int64_t W,
                                                   int64_t G, int64_t &b0, int64_t &b1) {
     // CTA b owns units [floor(bW/G), floor((b+1)W/G)); the CTA that holds unit
     // u is ceil((u+1)G/W) - 1.
-    const int64_t u0 = tile * n_chunks;
-    const int64_t u1 = (tile + 1) * n_chunks - 1;
+    const int64_t u0 = tile_unit_begin(sm, tile);
+    const int64_t u1 = tile_unit_begin(sm, tile + 1) - 1;
     b0 = ((u0 + 1) * G + W - 1) / W - 1;
     b1 = ((u1 + 1) * G + W - 1) / W - 1;
 }
 
-__global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, int64_t n_chunks,
+__global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, SysMap sm,
                                     int64_t W, int G, double scale, double *__restrict__ VW) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= S) return;
-    const int64_t tile = n / kRpyTile;
-    const int local = (int)(n - tile * kRpyTile);
+    const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
+    const int64_t tile = P / kRpyTile;
+    const int local = (int)(P - tile * kRpyTile);
     int64_t b0, b1;
-    cta_range_of_tile(tile, n_chunks, W, G, b0, b1);
+    cta_range_of_tile(sm, tile, W, G, b0, b1);
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t b = b0; b <= b1; ++b) {
         const float *p = part + (size_t)(b + tile) * 12 * kRpyTile;
@@ -645,14 +700,15 @@ __global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, i
     for (int c = 0; c < 6; ++c) VW[6 * n + c] = acc[c] * scale;
 }
 
-__global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, int64_t n_chunks,
+__global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, SysMap sm,
                                     int64_t W, int G, double scale, double *__restrict__ VW) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= S) return;
-    const int64_t tile = n / kRpyTile;
-    const int local = (int)(n - tile * kRpyTile);
+    const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
+    const int64_t tile = P / kRpyTile;
+    const int local = (int)(P - tile * kRpyTile);
     int64_t b0, b1;
-    cta_range_of_tile(tile, n_chunks, W, G, b0, b1);
+    cta_range_of_tile(sm, tile, W, G, b0, b1);
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t b = b0; b <= b1; ++b) {
         const double *p = part + (size_t)(b + tile) * 6 * kRpyTile;
@@ -663,18 +719,15 @@ __global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, 
     for (int c = 0; c < 6; ++c) VW[6 * n + c] = acc[c] * scale;
 }
 
-struct Geometry {
-    int64_t n_tiles, n_chunks, W;
-    int G;
-};
-
-Geometry geometry(const fil_ctx *c, int grid_max) {
-    Geometry g;
-    g.n_tiles = (c->lay.S + kRpyTile - 1) / kRpyTile;
-    g.n_chunks = (c->lay.S + kRpyChunk - 1) / kRpyChunk;
-    g.W = g.n_tiles * g.n_chunks;
-    g.G = (int)std::min<int64_t>(grid_max, g.W);
-    return g;
+SysMap sys_map(const fil_ctx *c) {
+    SysMap m;
+    m.tile_unit_off = c->tile_unit_off_d;
+    m.tile_src = c->tile_src_d;
+    m.pos_of_seg = c->pos_of_seg_d;
+    m.pad_map = c->pad_map_d;
+    m.n_tiles = c->rpy_tiles;
+    m.n_chunks = 0;
+    return m;
 }
 
 }  // namespace
@@ -689,10 +742,51 @@ cudaError_t rpy_setup(fil_ctx *c) {
     if (FIL_RPY_OCC > 0) occ32 = FIL_RPY_OCC;
     c->rpy_grid32 = std::max(1, occ32) * c->num_sms;
     c->rpy_grid64 = std::max(1, occ64) * c->num_sms;
-    c->rpy_tiles = (c->lay.S + kRpyTile - 1) / kRpyTile;
-    const int64_t n_chunks = (c->lay.S + kRpyChunk - 1) / kRpyChunk;
-    c->Spad = std::max(c->rpy_tiles * kRpyTile, n_chunks * kRpyChunk);
+    // padded layout: system s gets ceil(S_s / tile) tiles of targets, each
+    // with ceil(S_s / chunk) source chunks
+    const int ns = c->n_sys;
+    c->sys_pad_off_h.assign(ns + 1, 0);
+    c->tile_unit_off_h.assign(1, 0);
+    c->tile_src_h.clear();
+    for (int s = 0; s < ns; ++s) {
+        const int64_t Ss = c->sys_seg_off_h[s + 1] - c->sys_seg_off_h[s];
+        const int64_t tiles = (Ss + kRpyTile - 1) / kRpyTile;
+        const int64_t chunks = (Ss + kRpyChunk - 1) / kRpyChunk;
+        c->sys_pad_off_h[s + 1] = c->sys_pad_off_h[s] + tiles * kRpyTile;
+        for (int64_t t = 0; t < tiles; ++t) {
+            c->tile_unit_off_h.push_back(c->tile_unit_off_h.back() + chunks);
+            c->tile_src_h.push_back(c->sys_pad_off_h[s]);
+        }
+    }
+    c->rpy_tiles = (int64_t)c->tile_src_h.size();
+    c->rpy_units = c->tile_unit_off_h.back();
+    c->Spad = c->sys_pad_off_h[ns];
+    c->pos_of_seg_h.resize(c->lay.S);
+    c->pad_map_h.assign(c->Spad, -1);
+    for (int s = 0; s < ns; ++s)
+        for (int64_t g = c->sys_seg_off_h[s]; g < c->sys_seg_off_h[s + 1]; ++g) {
+            const int64_t P = c->sys_pad_off_h[s] + (g - c->sys_seg_off_h[s]);
+            c->pos_of_seg_h[g] = P;
+            c->pad_map_h[P] = (int)g;
+        }
     return cudaSuccess;
+}
+
+cudaError_t rpy_upload_tables(fil_ctx *c) {
+    cudaError_t e = cudaMemcpyAsync(c->tile_unit_off_d, c->tile_unit_off_h.data(),
+                                    sizeof(int64_t) * c->tile_unit_off_h.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->tile_src_d, c->tile_src_h.data(), sizeof(int64_t) * c->tile_src_h.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->pos_of_seg_d, c->pos_of_seg_h.data(),
+                            sizeof(int64_t) * c->pos_of_seg_h.size(), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->pad_map_d, c->pad_map_h.data(), sizeof(int) * c->pad_map_h.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    return e;
 }
 
 size_t rpy_partial_bytes(const fil_ctx *c) {
@@ -708,26 +802,26 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW)
     const unsigned pgrid = (unsigned)((c->Spad + pb - 1) / pb);
     const unsigned rgrid = (unsigned)((S + pb - 1) / pb);
     const bool timed = c->prof_on && c->prof_n < kProfMax;
+    const SysMap sm = sys_map(c);
+    const int64_t W = c->rpy_units;
     if (c->prec == FIL_MIXED) {
-        Geometry g = geometry(c, c->rpy_grid32);
-        pack32_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, c->src32);
+        const int G = (int)std::min<int64_t>(c->rpy_grid32, W);
+        pack32_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, sm, c->src32);
         if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
-        rpy_pair32_kernel<<<g.G, kRpyThreads, 0, c->stream>>>(
-            c->src32, g.n_chunks, g.W, g.G, make_const<float, RpyConst32>(c->a),
-            (float *)c->partials);
+        rpy_pair32_kernel<<<G, kRpyThreads, 0, c->stream>>>(
+            c->src32, sm, W, G, make_const<float, RpyConst32>(c->a), (float *)c->partials);
         if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
-        rpy_reduce32_kernel<<<rgrid, pb, 0, c->stream>>>((const float *)c->partials, S,
-                                                         g.n_chunks, g.W, g.G, scale, VW);
+        rpy_reduce32_kernel<<<rgrid, pb, 0, c->stream>>>((const float *)c->partials, S, sm, W, G,
+                                                         scale, VW);
     } else {
-        Geometry g = geometry(c, c->rpy_grid64);
-        pack64_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, c->src64);
+        const int G = (int)std::min<int64_t>(c->rpy_grid64, W);
+        pack64_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, sm, c->src64);
         if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
-        rpy_pair64_kernel<<<g.G, kRpyThreads, 0, c->stream>>>(
-            c->src64, g.n_chunks, g.W, g.G, make_const<double, RpyConst64>(c->a),
-            (double *)c->partials);
+        rpy_pair64_kernel<<<G, kRpyThreads, 0, c->stream>>>(
+            c->src64, sm, W, G, make_const<double, RpyConst64>(c->a), (double *)c->partials);
         if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
-        rpy_reduce64_kernel<<<rgrid, pb, 0, c->stream>>>((const double *)c->partials, S,
-                                                         g.n_chunks, g.W, g.G, scale, VW);
+        rpy_reduce64_kernel<<<rgrid, pb, 0, c->stream>>>((const double *)c->partials, S, sm, W, G,
+                                                         scale, VW);
     }
     if (timed) c->prof_n += 1;
     c->n_applies += 1;
@@ -825,10 +919,13 @@ extern "C" fil_status fil_rpy_apply_noalloc(int64_t n_seg, const double *Y, cons
     // every source record up to Spad and every partial slot the reduce reads
     // is written below, so nothing has to start at zero
     const int pb = 256;
-    pack32_kernel<<<(unsigned)((Spad + pb - 1) / pb), pb, 0, st>>>(Y, FT, n_seg, Spad, src);
-    rpy_pair32_kernel<<<G, kRpyThreads, 0, st>>>(src, n_chunks, W, G,
-                                                 make_const<float, RpyConst32>(a), part);
+    SysMap sm{};                       // one system, no tables
+    sm.n_tiles = tiles;
+    sm.n_chunks = n_chunks;
+    pack32_kernel<<<(unsigned)((Spad + pb - 1) / pb), pb, 0, st>>>(Y, FT, n_seg, Spad, sm, src);
+    rpy_pair32_kernel<<<G, kRpyThreads, 0, st>>>(src, sm, W, G, make_const<float, RpyConst32>(a),
+                                                 part);
     rpy_reduce32_kernel<<<(unsigned)((n_seg + pb - 1) / pb), pb, 0, st>>>(
-        part, n_seg, n_chunks, W, G, 1.0 / (8.0 * kPi * eta), VW);
+        part, n_seg, sm, W, G, 1.0 / (8.0 * kPi * eta), VW);
     return cudaGetLastError() == cudaSuccess ? FIL_OK : FIL_ECUDA;
 }

@@ -33,7 +33,7 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_mlp_create", "fil_mlp_destroy", "fil_mlp_set_params", "fil_mlp_get_params",
             "fil_mlp_set_norm", "fil_mlp_forward", "fil_mlp_gradients", "fil_mlp_train_step",
             "fil_tc_gemm_bf16", "fil_warm_features", "fil_warm_targets", "fil_warm_attach",
-            "fil_warm_stats"]
+            "fil_warm_stats", "fil_create_ensemble", "fil_sys_stats"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_SEG = 800, 256, 192, 32
 MLP_NPARAM = 256 * 800 + 256 + 2 * (256 * 256 + 256) + 192 * 256 + 192
 FIL_WARM_BEST_OF_TWO, FIL_WARM_PREDICTION_FIRST = 0, 1
@@ -100,6 +100,9 @@ def load_library(path=LIB_PATH):
         "fil_warm_targets": [P, P],
         "fil_warm_attach": [P, P, ctypes.c_int32],
         "fil_warm_stats": [P, I64, I64, I64],
+        "fil_create_ensemble": [ctypes.POINTER(fil_params), ctypes.c_int32, I32,
+                                ctypes.POINTER(P)],
+        "fil_sys_stats": [P, I32, D],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -143,6 +146,29 @@ def fil_create(seg_per_fil, a=1.0, eta=1.0, dL=2.2, KB=1.0, KT=1.0, gamma0=0.0, 
     ctx = ctypes.c_void_p()
     _check(None, _lib.fil_create(ctypes.byref(p), ctypes.byref(ctx)))
     return ctx
+
+
+def fil_create_ensemble(seg_per_fil, fil_per_sys, a=1.0, eta=1.0, dL=2.2, KB=1.0, KT=1.0,
+                        gamma0=0.0, kappa_mu=0.0, kappa_nu=0.0, dt=0.01, tol=1e-8, max_iter=50,
+                        precision=FIL_FP64, j0_model=FIL_J0_DRAG, stream=None):
+    segs = np.ascontiguousarray(seg_per_fil, dtype=np.int32)
+    fps = np.ascontiguousarray(fil_per_sys, dtype=np.int32)
+    p = fil_params(int(segs.size), segs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), a, eta, dL,
+                   KB, KT, gamma0, kappa_mu, kappa_nu, dt, tol, int(max_iter), int(precision),
+                   int(j0_model), ctypes.c_void_p(stream) if stream else None)
+    ctx = ctypes.c_void_p()
+    _check(None, _lib.fil_create_ensemble(ctypes.byref(p), int(fps.size),
+                                          fps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          ctypes.byref(ctx)))
+    return ctx
+
+
+def fil_sys_stats(ctx, n_sys):
+    it = np.zeros(n_sys, dtype=np.int32)
+    fi = np.zeros(n_sys)
+    _check(ctx, _lib.fil_sys_stats(ctx, it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   fi.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return it, fi
 
 
 def fil_destroy(ctx):
@@ -320,10 +346,18 @@ def fil_warm_stats(ctx):
 class Filaments:
     """Owns one context; methods forward to the fil_* functions above."""
 
-    def __init__(self, seg_per_fil, **params):
-        self.ctx = fil_create(seg_per_fil, **params)
+    def __init__(self, seg_per_fil, fil_per_sys=None, **params):
+        if fil_per_sys is None:
+            self.ctx = fil_create(seg_per_fil, **params)
+            self.n_sys = 1
+        else:
+            self.ctx = fil_create_ensemble(seg_per_fil, fil_per_sys, **params)
+            self.n_sys = len(fil_per_sys)
         self.S, self.nX, self.nlam = fil_sizes(self.ctx)
         self.M = len(seg_per_fil)
+
+    def sys_stats(self):
+        return fil_sys_stats(self.ctx, self.n_sys)
 
     def close(self):
         if self.ctx is not None:

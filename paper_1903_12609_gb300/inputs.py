@@ -72,24 +72,26 @@ def random_frames(rng: np.random.Generator, n: int):
     return t, mu
 
 
-def cloud_frames(n_fil: int, n_seg: int, dL: float = 2.2, volume_fraction: float = 0.02,
-                 a: float = 1.0, seed: int = 0, max_tries: int = 1000):
+def cloud_frames(n_fil: int, n_seg, dL: float = 2.2, volume_fraction: float = 0.02,
+                 a: float = 1.0, seed: int = 0, max_tries: int = 1000, rng=None):
     """Isotropic cloud of straight filaments with no overlapping segments.
 
-    Returns (base, t, mu, side): base (M, 3) positions of the s = 0 ends, t and
-    mu (M, 3) tangent and normal of each filament, and the cube side. Segment
-    n of filament i sits at base[i] + n*dL*t[i] (n = 0..N-1); a filament whose
+    n_seg: segments per filament (an int, or a list of n_fil counts). Returns
+    (base, t, mu, side): base (M, 3) positions of the s = 0 ends, t and mu
+    (M, 3) tangent and normal of each filament, and the cube side. Segment n of
+    filament i sits at base[i] + n*dL*t[i] (n = 0..N_i-1); a filament whose
     segments come closer than 2a to an accepted filament is redrawn.
     """
-    rng = np.random.default_rng(seed)
-    side = box_side(n_fil * n_seg, volume_fraction, a)
+    rng = np.random.default_rng(seed) if rng is None else rng
+    segs = [int(n_seg)] * n_fil if np.isscalar(n_seg) else [int(n) for n in n_seg]
+    side = box_side(sum(segs), volume_fraction, a)
     cell = 2.0 * a
     grid: dict = {}
     base = np.empty((n_fil, 3))
     tt = np.empty((n_fil, 3))
     mm = np.empty((n_fil, 3))
-    offs = np.arange(n_seg)[:, None] * dL
     for i in range(n_fil):
+        offs = np.arange(segs[i])[:, None] * dL
         for _ in range(max_tries):
             b = rng.uniform(0.0, side, size=3)
             t, mu = random_frames(rng, 1)
@@ -183,3 +185,39 @@ def suspension(n_fil: int = 1000, n_seg: int = 32, seed: int = 0, volume_fractio
     L = wl.extra["L"]
     follower = np.where(passive, 0.0, 100.0 * wl.KB / L ** 2)
     return wl, base, t, mu, Fext, follower
+
+
+def ensemble(n_sys: int = 256, seed: int = 0, fil_range=(1, 64), seg_range=(16, 48),
+             volume_fraction: float = 0.02):
+    """Batch of independent suspensions with the physics of `suspension`:
+    system k has U[fil_range] filaments of U[seg_range] segments each
+    (inclusive, seeded), placed as an isotropic cloud at the given volume
+    fraction; in every system the first half of the filaments sediment and the
+    rest carry a tip follower force f_i = 100 K_B / L_i^2 (L_i = N_i dL). K_B,
+    K_T and dt are those of the 32-segment suspension (B = 1000 for N = 32,
+    dt = T/200), tolerance 1e-4.
+    Returns (Workload, fil_per_sys, seg_per_fil, base, t, mu, Fext, follower)."""
+    rng = np.random.default_rng(seed)
+    wl = workload_params(1, 32, B=1000.0, dt_over_T=1.0 / 200.0, tol=1e-4, max_iter=60)
+    fil_per_sys = rng.integers(fil_range[0], fil_range[1] + 1, size=n_sys)
+    segs_all, bases, ts, mus, Fs, fols = [], [], [], [], [], []
+    for k in range(n_sys):
+        m = int(fil_per_sys[k])
+        segs = [int(x) for x in rng.integers(seg_range[0], seg_range[1] + 1, size=m)]
+        base, t, mu, _ = cloud_frames(m, segs, dL=wl.dL, volume_fraction=volume_fraction,
+                                      rng=rng)
+        passive = np.arange(m) < m // 2
+        for i in range(m):
+            F = np.zeros((segs[i], 3))
+            if passive[i]:
+                F[:, 2] = -wl.W * wl.dL
+            Fs.append(F)
+            fols.append(0.0 if passive[i] else 100.0 * wl.KB / (segs[i] * wl.dL) ** 2)
+        segs_all += segs
+        bases.append(base)
+        ts.append(t)
+        mus.append(mu)
+    wl.n_fil = len(segs_all)
+    wl.seg_per_fil = segs_all
+    return (wl, [int(x) for x in fil_per_sys], segs_all, np.concatenate(bases), np.concatenate(ts),
+            np.concatenate(mus), np.concatenate(Fs), np.array(fols))

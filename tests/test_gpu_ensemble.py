@@ -1,0 +1,106 @@
+"""GPU parity of ensembles of independent systems (fil_create_ensemble): every
+system of the batch behaves exactly as the oracle run on that system alone --
+the mobility apply (no coupling across systems) and whole timesteps with
+per-system Broyden convergence (a system that converges first keeps its
+iterate while the others continue)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import filament as fo  # noqa: E402
+from oracle import rpy  # noqa: E402
+from paper_1903_12609_gb300.inputs import random_frames  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fil():
+    assert torch.cuda.is_available()
+    from paper_1903_12609_gb300 import fil as _fil
+    return _fil
+
+
+# systems: lists of segment counts (ragged, tiles and chunks cut mid-way)
+SYSTEMS = [[16], [20, 33, 7], [48] * 6, [1, 2, 3], [32] * 9, [17, 40]]
+
+
+def _positions(rng, segs, box):
+    Y = []
+    for n in segs:
+        base = rng.uniform(0, box, 3)
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        Y.append(base + 2.2 * np.arange(n)[:, None] * d)
+    return np.concatenate(Y)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mobility_is_block_diagonal_over_systems(fil, prec):
+    rng = np.random.default_rng(prec)
+    Ys, FTs = [], []
+    for segs in SYSTEMS:
+        Ys.append(_positions(rng, segs, 30.0))      # systems overlap in space
+        FTs.append(rng.standard_normal((sum(segs), 6)))
+    Y, FT = np.concatenate(Ys), np.concatenate(FTs)
+    segs_all = [n for segs in SYSTEMS for n in segs]
+    with fil.Filaments(segs_all, fil_per_sys=[len(s) for s in SYSTEMS], precision=prec,
+                       max_iter=10) as m:
+        VW = np.zeros_like(FT)
+        m.mobility_apply(Y, FT, VW)
+    off = 0
+    for Yi, FTi in zip(Ys, FTs):
+        ref, ref_abs = rpy.apply(Yi, FTi, with_abs=True)
+        got = VW[off:off + len(Yi)]
+        if prec == 0:
+            assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+        else:
+            assert np.all(np.abs(got - ref) <= 144 * 2.0 ** -24 * ref_abs + 1e-300)
+        off += len(Yi)
+
+
+def _system(segs, seed):
+    rng = np.random.default_rng(seed)
+    lay = fo.Layout(segs)
+    M = len(segs)
+    base = rng.uniform(0, 20.0 * M ** (1 / 3), size=(M, 3))
+    t, mu = random_frames(rng, M)
+    xi = 0.05 * rng.standard_normal((lay.S, 3))
+    return lay, base, t, mu, xi, rng
+
+
+@pytest.mark.parametrize("j0", [(0, "drag"), (1, "rpy")])
+def test_ensemble_steps_match_each_system_alone(fil, j0):
+    systems = [[16], [20, 33, 7], [30] * 5, [1, 2, 3]]
+    p = fo.Params(a=1.0, eta=1.0, dL=2.2, KB=2.0, KT=1.5, dt=0.2, tol=1e-10, max_iter=80)
+    states, exts, lays = [], [], []
+    for i, segs in enumerate(systems):
+        lay, base, t, mu, xi, rng = _system(segs, 10 + i)
+        st = fo.initial_state(lay, p, base, t, mu, xi)
+        ext = fo.External(Fext=np.tile([0.0, 0.0, -2.2], (lay.S, 1)),
+                          follower=rng.uniform(0, 2, lay.M))
+        states.append(st)
+        exts.append(ext)
+        lays.append(lay)
+    segs_all = [n for segs in systems for n in segs]
+    with fil.Filaments(segs_all, fil_per_sys=[len(s) for s in systems], a=p.a, eta=p.eta,
+                       dL=p.dL, KB=p.KB, KT=p.KT, dt=p.dt, tol=p.tol, max_iter=p.max_iter,
+                       j0_model=j0[0]) as m:
+        m.set_state(np.concatenate([s.Y for s in states]), np.concatenate([s.q for s in states]))
+        m.set_external(np.concatenate([e.Fext for e in exts]), None,
+                       np.concatenate([e.follower for e in exts]))
+        S = m.S
+        Y = np.zeros((S, 3))
+        for step in range(3):
+            it_all = m.step()
+            its, finf = m.sys_stats()
+            m.get_state(Y, None, None, None, None)
+            off = 0
+            for k, lay in enumerate(lays):
+                states[k], it_ref = fo.step(lay, p, states[k], exts[k], j0_model=j0[1])
+                assert abs(int(its[k]) - it_ref) <= 1, (step, k, its, it_ref)
+                np.testing.assert_allclose(Y[off:off + lay.S], states[k].Y, rtol=0, atol=1e-8)
+                assert finf[k] <= p.tol * p.a
+                off += lay.S
+            assert it_all == its.max()
