@@ -228,6 +228,7 @@ def run_ensemble(args, fil, torch):
     for _ in range(args.warmup):
         m.step()
     a0, i0, k0 = m.counters()
+    p0 = m.pair_count()
     m.profile(True)
     m.profile_read()
     torch.cuda.synchronize()
@@ -244,13 +245,15 @@ def run_ensemble(args, fil, torch):
     clocks = clocks_stop(clk, 0)
     n_pair, pair_ms = m.profile_read()
     a1, _, k1 = m.counters()
+    pairs = m.pair_count() - p0
     m.close()
     ms = e0.elapsed_time(e1)
     si = np.array(sys_iters)
+    # pairs actually evaluated (converged systems drop out of the applies)
+    achieved = FLOPS_PER_PAIR * pairs / (pair_ms * 1e-3) / 1e12
     pair_avg = pair_ms / max(n_pair, 1)
-    achieved = FLOPS_PER_PAIR * pairs_per_apply / (pair_avg * 1e-3) / 1e12
     print(json.dumps({
-        "metric": METRIC, "value": (a1 - a0) * pairs_per_apply / (ms * 1e-3), "unit": UNIT,
+        "metric": METRIC, "value": pairs / (ms * 1e-3), "unit": UNIT,
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",

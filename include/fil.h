@@ -111,6 +111,11 @@ fil_status fil_create_ensemble(const fil_params *p, int32_t n_sys, const int32_t
  * current / last step and the last ||f||_inf that was read. */
 fil_status fil_sys_stats(const fil_ctx *c, int32_t *iters, double *finf);
 
+/* RPY pair interactions evaluated by this context's mobility applies so far
+ * (sum over each apply of S_s^2 over the systems it evaluated; padding and
+ * converged systems excluded). */
+fil_status fil_pair_count(const fil_ctx *c, double *pairs);
+
 /* Release the context and its device memory (synchronises its stream). */
 void fil_destroy(fil_ctx *c);
 

@@ -97,6 +97,10 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->sys_xoff = ar.take<int64_t>(c->n_sys + 1);
     c->tile_unit_off_d = ar.take<int64_t>(c->rpy_tiles + 1);
     c->tile_src_d = ar.take<int64_t>(c->rpy_tiles);
+    c->act_unit_off_d = ar.take<int64_t>(c->rpy_tiles + 1);
+    c->act_src_d = ar.take<int64_t>(c->rpy_tiles);
+    c->act_tile_d = ar.take<int>(c->rpy_tiles);
+    c->act_slot_d = ar.take<int>(c->rpy_tiles);
     c->pos_of_seg_d = ar.take<int64_t>(S);
     c->pad_map_d = ar.take<int>(c->Spad);
     c->Y = ar.take<double>(3 * S);
@@ -189,12 +193,16 @@ double finf_of(const StatusBlock &s) { return s.fmax; }
 
 // f(X): unpack + forces (with_forces = 2 also keeps the internal torque for
 // J0), RPY mobility, residual rows, ||f||_inf into the status block.
-cudaError_t eval_residual(fil_ctx *c, const double *X, double *f, int with_forces) {
-    cudaError_t e = unpack_forces(c, X, with_forces);
+// fprev non-null: inside a Broyden iteration of an ensemble, only the
+// systems still iterating are evaluated; the others keep fprev's rows.
+cudaError_t eval_residual(fil_ctx *c, const double *X, double *f, int with_forces,
+                          const double *fprev = nullptr) {
+    const bool act = fprev != nullptr;
+    cudaError_t e = unpack_forces(c, X, with_forces, act);
     if (e != cudaSuccess) return e;
-    e = rpy_apply(c, c->Yc, c->FT, c->VW);
+    e = rpy_apply(c, c->Yc, c->FT, c->VW, act);
     if (e != cudaSuccess) return e;
-    return residual_rows(c, X, f);
+    return residual_rows(c, X, f, fprev);
 }
 
 cudaError_t j0_apply(fil_ctx *c, const double *b, double *x) {
@@ -588,6 +596,7 @@ fil_status initial_iterate(fil_ctx *c, bool use_net, double *f0) {
 // Systems whose ||f||_inf is within the tolerance stop iterating (host and
 // device flags); returns the number still active.
 int update_active(fil_ctx *c, bool count_iteration) {
+    c->active_prev_h = c->active_h;
     int n = 0;
     for (int sy = 0; sy < c->n_sys; ++sy) {
         if (!c->active_h[sy]) continue;
@@ -631,6 +640,7 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net) {
     c->conv = n_active == 0 ? 1 : 0;
     if (!c->conv) {
         CK(upload_active(c));
+        if (c->n_sys > 1) CK(rpy_set_active(c));
         CK(j0_apply(c, c->fk, c->w));
         CK(broyden_mask_inactive(c, c->w));
     }
@@ -651,7 +661,7 @@ fil_status fil_broyden_step(fil_ctx *c, int32_t *converged, double *finf) {
     if (c->iters_step >= c->max_iter)
         return set_err(c, FIL_ENOCONV, "Broyden: max_iter reached without convergence");
     CK(broyden_axpy_step(c));
-    CK(eval_residual(c, c->Xn, c->fn, 1));
+    CK(eval_residual(c, c->Xn, c->fn, 1, c->n_sys > 1 ? c->fk : nullptr));
     StatusBlock sb;
     fil_status s = read_status(c, &sb);
     if (s != FIL_OK) return s;
@@ -668,7 +678,10 @@ fil_status fil_broyden_step(fil_ctx *c, int32_t *converged, double *finf) {
         if (converged) *converged = 1;
         return FIL_OK;
     }
-    if (c->n_sys > 1) CK(upload_active(c));
+    if (c->n_sys > 1 && c->active_h != c->active_prev_h) {
+        CK(upload_active(c));
+        CK(rpy_set_active(c));
+    }
     CK(broyden_dots(c));
     CK(j0_apply(c, c->fn, c->g));
     CK(broyden_update(c));
@@ -784,6 +797,12 @@ fil_status fil_warm_stats(const fil_ctx *c, int64_t *from_prediction, int64_t *f
     if (from_prediction) *from_prediction = c->warm_pred;
     if (from_extrapolation) *from_extrapolation = c->warm_extrap;
     if (restarts) *restarts = c->warm_restart;
+    return FIL_OK;
+}
+
+fil_status fil_pair_count(const fil_ctx *c, double *pairs) {
+    if (!c || !pairs) return FIL_EINVAL;
+    *pairs = c->n_pairs;
     return FIL_OK;
 }
 

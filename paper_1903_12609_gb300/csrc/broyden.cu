@@ -22,7 +22,7 @@ namespace fil {
 namespace {
 
 constexpr int kRedThreads = 256;
-constexpr int kDotGroup = 4;   // outputs accumulated per pass over the vectors
+constexpr int kDotGroup = 8;   // outputs accumulated per pass over the vectors
 
 __global__ void axpy_neg_kernel(int64_t n, const double *__restrict__ x,
                                 const double *__restrict__ w, double *__restrict__ y) {
@@ -30,51 +30,81 @@ __global__ void axpy_neg_kernel(int64_t n, const double *__restrict__ x,
     if (i < n) y[i] = x[i] - w[i];
 }
 
-__device__ __forceinline__ double block_sum(double v, double *sh) {
+
+// Sums of G per-thread values over the block, written to part[o_j * nb + b]
+// (fixed order: warp shuffles, then the warps in order).
+template <int G>
+__device__ __forceinline__ void block_reduce_write(double (&acc)[G], double *sh, const int *o,
+                                                   int nb, double *part) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = 0; j < G; ++j) {
+        double v = acc[j];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+        if (lane == 0) sh[j * 32 + wid] = v;
+    }
     __syncthreads();
-    if (lane == 0) sh[wid] = v;
+    if ((int)threadIdx.x < G) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sh[threadIdx.x * 32 + w];
+        part[(int64_t)o[threadIdx.x] * nb + blockIdx.x] = s;
+    }
     __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
-    return s;
+}
+
+// d_{o0+j} . fn for j < G over [i0, i1)
+template <int G>
+__device__ __forceinline__ void dots_group(const double *__restrict__ D, int64_t n, int o0,
+                                           const double *__restrict__ fn, int64_t i0, int64_t i1,
+                                           double *sh, int nb, double *part) {
+    double acc[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) acc[j] = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const double f = fn[i];
+#pragma unroll
+        for (int j = 0; j < G; ++j) acc[j] = fma(D[(int64_t)(o0 + j) * n + i], f, acc[j]);
+    }
+    int o[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) o[j] = o0 + j;
+    block_reduce_write<G>(acc, sh, o, nb, part);
 }
 
 // Outputs o = 0..k-1: d_o . fn;  o = k: |fn - fk|^2;  o = k+1: (fn - fk) . fn,
-// over the X slice [blk_beg[b], blk_beg[b+1]) of block b.
+// over the X slice [blk_beg[b], blk_beg[b+1]) of block b. Outputs are taken
+// in compile-time groups so that every FP64 instruction is useful work.
 __global__ void dots_partial_kernel(int64_t n, const double *__restrict__ fn,
                                     const double *__restrict__ fk, const double *__restrict__ D,
                                     int k, const int64_t *__restrict__ blk_beg,
                                     double *__restrict__ part) {
-    __shared__ double sh[kRedThreads / 32];
-    const int nout = k + 2;
+    __shared__ double sh[kDotGroup * 32];
+    const int nb = gridDim.x;
     const int64_t i0 = blk_beg[blockIdx.x], i1 = blk_beg[blockIdx.x + 1];
-    for (int o0 = 0; o0 < nout; o0 += kDotGroup) {
-        double acc[kDotGroup];
-#pragma unroll
-        for (int j = 0; j < kDotGroup; ++j) acc[j] = 0.0;
+    {
+        double acc[2] = {0.0, 0.0};
         for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             const double f = fn[i];
             const double df = f - fk[i];
-#pragma unroll
-            for (int j = 0; j < kDotGroup; ++j) {
-                const int o = o0 + j;
-                if (o < k)
-                    acc[j] += D[(int64_t)o * n + i] * f;
-                else if (o == k)
-                    acc[j] += df * df;
-                else if (o == k + 1)
-                    acc[j] += df * f;
-            }
+            acc[0] = fma(df, df, acc[0]);
+            acc[1] = fma(df, f, acc[1]);
         }
-#pragma unroll
-        for (int j = 0; j < kDotGroup; ++j) {
-            const double s = block_sum(acc[j], sh);
-            if (threadIdx.x == 0 && o0 + j < nout) part[(int64_t)(o0 + j) * gridDim.x + blockIdx.x] = s;
-        }
+        const int o[2] = {k, k + 1};
+        block_reduce_write<2>(acc, sh, o, nb, part);
+    }
+    int o0 = 0;
+    for (; o0 + kDotGroup <= k; o0 += kDotGroup)
+        dots_group<kDotGroup>(D, n, o0, fn, i0, i1, sh, nb, part);
+    switch (k - o0) {
+        case 1: dots_group<1>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 2: dots_group<2>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 3: dots_group<3>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 4: dots_group<4>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 5: dots_group<5>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 6: dots_group<6>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 7: dots_group<7>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        default: break;
     }
 }
 

@@ -84,9 +84,16 @@ struct fil_ctx {
     int rpy_grid32, rpy_grid64;
     int64_t rpy_tiles, rpy_units;
     std::vector<int64_t> sys_pad_off_h, tile_unit_off_h, tile_src_h, pos_of_seg_h;
-    std::vector<int> pad_map_h;
+    std::vector<int> pad_map_h, tile_sys_h;
     int64_t *tile_unit_off_d, *tile_src_d, *pos_of_seg_d;
     int *pad_map_d;
+    // the tiles of the systems still iterating (ensembles): applies inside a
+    // Broyden iteration only evaluate those
+    int64_t act_tiles, act_units;
+    double pairs_all, pairs_act;   // sum of S_s^2 over all / the active systems
+    double n_pairs;                // pairs evaluated by all applies so far
+    int64_t *act_unit_off_d, *act_src_d;
+    int *act_tile_d, *act_slot_d;
 
     // Broyden state
     double *Xk, *fk, *Xn, *fn, *w, *g, *C, *D;
@@ -102,6 +109,7 @@ struct fil_ctx {
     int *d_flags;          // [0] stall flag, [1] singular J0 flag
     int *d_active;         // [n_sys] system still iterating in the current step
     std::vector<int> active_h, sys_iters_h;   // host copies; iterations per system
+    std::vector<int> active_prev_h;           // active_h before the last update
     std::vector<double> finf_h;               // ||f||_inf per system, last read
     double *h_pinned;      // small pinned host buffer
     int k;                 // stored (c, d) pairs of the current step
@@ -150,13 +158,16 @@ struct fil_ctx {
 namespace fil {
 
 // Launchers (all enqueue on c->stream and return a cudaError_t).
-cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW);
+cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
+                      bool active_only = false);
+cudaError_t rpy_set_active(fil_ctx *c);     // list the active systems' tiles
 cudaError_t rpy_setup(fil_ctx *c);          // grid sizes and padded layout, once at create
 cudaError_t rpy_upload_tables(fil_ctx *c);  // the layout tables, after the arena exists
 size_t rpy_partial_bytes(const fil_ctx *c);
 
-cudaError_t unpack_forces(fil_ctx *c, const double *X, int with_forces);
-cudaError_t residual_rows(fil_ctx *c, const double *X, double *f);
+cudaError_t unpack_forces(fil_ctx *c, const double *X, int with_forces, bool active_only = false);
+// fprev non-null: systems that have converged copy their rows from fprev
+cudaError_t residual_rows(fil_ctx *c, const double *X, double *f, const double *fprev = nullptr);
 cudaError_t init_straight(fil_ctx *c, const double *base, const double *t, const double *mu,
                           const double *xi);
 cudaError_t extrapolate_guess(fil_ctx *c, double *X0);

@@ -55,12 +55,14 @@ __global__ void unpack_forces_kernel(Layout lay, const double *__restrict__ X,
                                      const double *__restrict__ Fext,
                                      const double *__restrict__ Text,
                                      const double *__restrict__ follower, int with_forces,
-                                     double *__restrict__ qc, double *__restrict__ Yc,
-                                     double *__restrict__ FT, double *__restrict__ Tint) {
+                                     const int *__restrict__ active, double *__restrict__ qc,
+                                     double *__restrict__ Yc, double *__restrict__ FT,
+                                     double *__restrict__ Tint) {
     const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= lay.M) return;
     const int s0 = lay.off[warp];
+    if (active && !active[lay.sys_of[s0]]) return;   // a converged system keeps its unpack
     const int N = lay.off[warp + 1] - s0;
     const double *Xf = X + 6 * (int64_t)s0;
 
@@ -86,19 +88,25 @@ __global__ void unpack_forces_kernel(Layout lay, const double *__restrict__ X,
 
     const double *Lam = Xf + 3 + 3 * N;   // Lambda_{j+3/2}, j = 0..N-2
     const double follow = follower ? follower[warp] : 0.0;
-    for (int n = lane; n < N; n += 32) {
+    // each joint moment M_{n+1/2} once, by lane n; M_{n-1/2} from the lane below
+    V3 Mcarry = v3(0, 0, 0);               // M of the joint before this pass
+    for (int base = 0; base < N; base += 32) {
+        const int n = base + lane;
+        const bool act = n < N;
         const int64_t g = s0 + n;
-        const Q4 q = ld4(qc + 4 * g);
+        Q4 q = {1, 0, 0, 0};
+        if (act) q = ld4(qc + 4 * g);
+        V3 Mr = v3(0, 0, 0);
+        if (act && n <= N - 2)
+            Mr = internal_moment(q, ld4(qc + 4 * (g + 1)), fp.dL, fp.KB, fp.KT, fp.g0, fp.kmu,
+                                 fp.knu);
+        V3 Ml = shfl_up3(Mr, 1);
+        if (lane == 0) Ml = Mcarry;
+        Mcarry = shfl3(Mr, 31);
+        if (!act) continue;
         const V3 t = frame_t(q);
         const V3 Lr = (n <= N - 2) ? ld3(Lam + 3 * n) : v3(0, 0, 0);
         const V3 Ll = (n >= 1) ? ld3(Lam + 3 * (n - 1)) : v3(0, 0, 0);
-        V3 Mr = v3(0, 0, 0), Ml = v3(0, 0, 0);
-        if (n <= N - 2)
-            Mr = internal_moment(q, ld4(qc + 4 * (g + 1)), fp.dL, fp.KB, fp.KT, fp.g0, fp.kmu,
-                                 fp.knu);
-        if (n >= 1)
-            Ml = internal_moment(ld4(qc + 4 * (g - 1)), q, fp.dL, fp.KB, fp.KT, fp.g0, fp.kmu,
-                                 fp.knu);
         V3 F = Lr - Ll;
         V3 Ti = (Mr - Ml) + (0.5 * fp.dL) * cross(t, Lr + Ll);
         if (Fext) F = F + ld3(Fext + 3 * g);
@@ -124,11 +132,28 @@ __global__ void residual_rows_kernel(Layout lay, const double *__restrict__ X,
                                      const double *__restrict__ Yj,
                                      const double *__restrict__ Yjm1,
                                      const double *__restrict__ uj, Scheme sc,
-                                     double *__restrict__ f,
+                                     const int *__restrict__ active,
+                                     const double *__restrict__ fprev, double *__restrict__ f,
                                      unsigned long long *__restrict__ finf_bits) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double m = 0.0;
-    if (g < lay.S) {
+    bool eval = g < lay.S;
+    if (eval && active && !active[lay.sys_of[g]]) {
+        // a converged system keeps its residual (its iterate is frozen)
+        const int i = lay.fil_of[g];
+        const int s0 = lay.off[i];
+        const int N = lay.off[i + 1] - s0;
+        const int n = (int)(g - s0);
+        const int64_t r = 6 * (int64_t)s0;
+        const int64_t pr = r + (n == 0 ? 0 : 3 + 3 * N + 3 * (n - 1));
+        const int64_t rr = r + 3 + 3 * n;
+        for (int k = 0; k < 3; ++k) {
+            f[pr + k] = fprev[pr + k];
+            f[rr + k] = fprev[rr + k];
+        }
+        eval = false;
+    }
+    if (eval) {
         const int i = lay.fil_of[g];
         const int s0 = lay.off[i];
         const int N = lay.off[i + 1] - s0;
@@ -268,17 +293,17 @@ unsigned seg_grid(int64_t S, int threads) { return (unsigned)((S + threads - 1) 
 
 }  // namespace
 
-cudaError_t unpack_forces(fil_ctx *c, const double *X, int with_forces) {
+cudaError_t unpack_forces(fil_ctx *c, const double *X, int with_forces, bool active_only) {
     ForceParams fp{c->dL, c->KB, c->KT, c->g0, c->kmu, c->knu};
     unpack_forces_kernel<<<warp_grid(c->lay.M, 128), 128, 0, c->stream>>>(
         c->lay, X, c->q, fp, c->has_Fext ? c->Fext : nullptr, c->has_Text ? c->Text : nullptr,
-        c->has_follower ? c->follower : nullptr, with_forces, c->qc, c->Yc, c->FT,
-        with_forces == 2 ? c->Tint : nullptr);
+        c->has_follower ? c->follower : nullptr, with_forces, active_only ? c->d_active : nullptr,
+        c->qc, c->Yc, c->FT, with_forces == 2 ? c->Tint : nullptr);
     c->n_launches += 1;
     return cudaGetLastError();
 }
 
-cudaError_t residual_rows(fil_ctx *c, const double *X, double *f) {
+cudaError_t residual_rows(fil_ctx *c, const double *X, double *f, const double *fprev) {
     Scheme sc;
     if (c->have_prev) {
         sc = {4.0 / 3.0, -1.0 / 3.0, 2.0 / 3.0 * c->dt, 1.0 / 3.0};
@@ -288,7 +313,8 @@ cudaError_t residual_rows(fil_ctx *c, const double *X, double *f) {
     cudaError_t e = cudaMemsetAsync(c->d_finf, 0, sizeof(unsigned long long) * c->n_sys, c->stream);
     if (e != cudaSuccess) return e;
     residual_rows_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(
-        c->lay, X, c->Yc, c->VW, c->Y, c->Yprev, c->uprev, sc, f, c->d_finf);
+        c->lay, X, c->Yc, c->VW, c->Y, c->Yprev, c->uprev, sc, fprev ? c->d_active : nullptr,
+        fprev, f, c->d_finf);
     c->n_launches += 1;
     return cudaGetLastError();
 }

@@ -169,6 +169,11 @@ __global__ void band_lu_kernel(Layout lay, double *__restrict__ band_all, int *_
         }
         __syncwarp();
     }
+    // the solves multiply by the reciprocal pivots (FP64 division is slow here)
+    for (int j = lane; j < n; j += 32) {
+        const double d = BAND(j, j);
+        BAND(j, j) = d != 0.0 ? 1.0 / d : 0.0;
+    }
 #undef BAND
 }
 
@@ -217,13 +222,14 @@ __global__ void band_solve_kernel(Layout lay, const double *__restrict__ band_al
         if (lane < kBandKL && i < n) z[i] -= BAND(i, j) * zj;
         __syncwarp();
     }
-    // backward: U has kl + ku super-diagonals
+    // backward, column by column: z_j *= 1/U_jj (stored reciprocal), then the
+    // kl + ku rows above take their U_ij z_j; two FP64 instructions per column
     for (int j = n - 1; j >= 0; --j) {
-        const int c = j + 1 + lane;
-        double t = (lane < kBandKL + kBandKU && c < n) ? BAND(j, c) * z[c] : 0.0;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) t += __shfl_down_sync(0xffffffffu, t, d);
-        if (lane == 0) z[j] = (z[j] - t) / BAND(j, j);
+        const double zj = z[j] * BAND(j, j);
+        __syncwarp();                       // every lane has read z_j
+        const int i = j - 1 - lane;
+        if (lane < kBandKL + kBandKU && i >= 0) z[i] -= BAND(i, j) * zj;
+        if (lane == 0) z[j] = zj;
         __syncwarp();
     }
     // scatter back: u_s, Lam_j, and Y_1 = b1 + c_t Lam_0

@@ -37,25 +37,28 @@ __device__ __forceinline__ Q4 qmul(Q4 p, Q4 q) {
 }
 __device__ __forceinline__ Q4 qconj(Q4 q) { return {q.w, -q.x, -q.y, -q.z}; }
 
-// Square root of a unit quaternion, App. A.1 (special case p0 = -1).
+// Square root of a unit quaternion, App. A.1 (special case p0 = -1):
+// ((p0 + 1)/s, p/s) with s = sqrt(2 (p0 + 1)), using one reciprocal square
+// root (sqrt((p0 + 1)/2) = (p0 + 1)/s).
 __device__ __forceinline__ Q4 qsqrt(Q4 p) {
     if (p.w == -1.0) return {0.0, 0.0, 0.0, 1.0};
-    double s = sqrt(2.0 * (p.w + 1.0));
-    return {sqrt((p.w + 1.0) * 0.5), p.x / s, p.y / s, p.z / s};
+    const double r = rsqrt(2.0 * (p.w + 1.0));
+    return {(p.w + 1.0) * r, p.x * r, p.y * r, p.z * r};
 }
 
 // exp(u) = (cos(|u|/2), sin(|u|/2) u/|u|), Sec. 2.9.3. For tiny |u| the
 // factor sin(x/2)/x uses its Taylor series 1/2 - x^2/48 + x^4/3840.
 __device__ __forceinline__ Q4 qexp(V3 u) {
-    double th = norm(u);
+    const double t2 = dot(u, u);
+    const double ith = t2 > 0.0 ? rsqrt(t2) : 0.0;
+    const double th = t2 * ith;
     double s, c;
     sincos(0.5 * th, &s, &c);
     double f;
     if (th < 1e-4) {
-        double t2 = th * th;
-        f = 0.5 - t2 / 48.0 + t2 * t2 / 3840.0;
+        f = 0.5 - t2 * (1.0 / 48.0) + t2 * t2 * (1.0 / 3840.0);
     } else {
-        f = s / th;
+        f = s * ith;
     }
     return {c, f * u.x, f * u.y, f * u.z};
 }
@@ -105,7 +108,8 @@ __device__ __forceinline__ V3 dexpinv(V3 u, V3 W) {
 __device__ __forceinline__ V3 internal_moment(Q4 qa, Q4 qb, double dL, double KB, double KT,
                                               double g0, double kmu, double knu) {
     Q4 qh = qmul(qsqrt(qmul(qb, qconj(qa))), qa);
-    Q4 dq = {(qb.w - qa.w) / dL, (qb.x - qa.x) / dL, (qb.y - qa.y) / dL, (qb.z - qa.z) / dL};
+    const double idL = 1.0 / dL;
+    Q4 dq = {(qb.w - qa.w) * idL, (qb.x - qa.x) * idL, (qb.y - qa.y) * idL, (qb.z - qa.z) * idL};
     Q4 s = qmul(qconj(qh), dq);
     V3 strain = {KT * (2.0 * s.x - g0), KB * (2.0 * s.y - kmu), KB * (2.0 * s.z - knu)};
     return rotate(qh, strain);

@@ -99,11 +99,13 @@ __host__ K make_const(double a) {
 // padded position equals the segment index (tile = u / n_chunks).
 // ---------------------------------------------------------------------------
 struct SysMap {
-    const int64_t *tile_unit_off;  // [n_tiles + 1] first unit of each tile
+    const int64_t *tile_unit_off;  // [n_tiles + 1] first unit of each listed tile
     const int64_t *tile_src;       // [n_tiles] padded position of the tile's first source
+    const int *tile_id;            // [n_tiles] padded tile of each listed tile (null: same)
+    const int *slot_of;            // [all tiles] list index of a padded tile, -1 if not listed
     const int64_t *pos_of_seg;     // [S] padded position of each segment
     const int *pad_map;            // [Spad] segment at a padded position, or -1
-    int64_t n_tiles, n_chunks;     // n_chunks: the one-system case
+    int64_t n_tiles, n_chunks;     // listed tiles; n_chunks: the one-system case
 };
 
 __device__ __forceinline__ int64_t tile_unit_begin(const SysMap &m, int64_t tile) {
@@ -431,11 +433,12 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
         const int64_t c_begin = u - ubeg;
         const int64_t c_end = min(n_chunks, c_begin + (u_end - u));
         const float4 *srcs = src + kRec * (src0 / kRpyChunk);   // this tile's system
+        const int64_t ptile = smap.tile_id ? smap.tile_id[tile] : tile;   // padded tile
 
         float th[kT][3], tl[kT][3];
 #pragma unroll
         for (int t = 0; t < kT; ++t) {
-            const int64_t n = tile * kRpyTile + t * kRpyThreads + tid;
+            const int64_t n = ptile * kRpyTile + t * kRpyThreads + tid;
 #if FIL_RPY_PACKED
             float4 a0, a1, a2;
             unpack_source(src + kRpyPairF4 * (n >> 1), (int)(n & 1), a0, a1, a2);
@@ -607,11 +610,12 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
         const int64_t c_begin = u - ubeg;
         const int64_t c_end = min(n_chunks, c_begin + (u_end - u));
         const double *srcs = src + 9 * src0;
+        const int64_t ptile = smap.tile_id ? smap.tile_id[tile] : tile;
 
         double ty[kRpyTargetsPerThread][3];
 #pragma unroll
         for (int t = 0; t < kRpyTargetsPerThread; ++t) {
-            const int64_t n = tile * kRpyTile + t * kRpyThreads + tid;
+            const int64_t n = ptile * kRpyTile + t * kRpyThreads + tid;
             ty[t][0] = src[9 * n];
             ty[t][1] = src[9 * n + 1];
             ty[t][2] = src[9 * n + 2];
@@ -685,8 +689,12 @@ __global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, S
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= S) return;
     const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
-    const int64_t tile = P / kRpyTile;
+    int64_t tile = P / kRpyTile;
     const int local = (int)(P - tile * kRpyTile);
+    if (sm.slot_of) {
+        tile = sm.slot_of[tile];
+        if (tile < 0) return;         // a system left out of this apply
+    }
     int64_t b0, b1;
     cta_range_of_tile(sm, tile, W, G, b0, b1);
     double acc[6] = {0, 0, 0, 0, 0, 0};
@@ -705,8 +713,12 @@ __global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, 
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= S) return;
     const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
-    const int64_t tile = P / kRpyTile;
+    int64_t tile = P / kRpyTile;
     const int local = (int)(P - tile * kRpyTile);
+    if (sm.slot_of) {
+        tile = sm.slot_of[tile];
+        if (tile < 0) return;         // a system left out of this apply
+    }
     int64_t b0, b1;
     cta_range_of_tile(sm, tile, W, G, b0, b1);
     double acc[6] = {0, 0, 0, 0, 0, 0};
@@ -719,14 +731,24 @@ __global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, 
     for (int c = 0; c < 6; ++c) VW[6 * n + c] = acc[c] * scale;
 }
 
-SysMap sys_map(const fil_ctx *c) {
+SysMap sys_map(const fil_ctx *c, bool active_only) {
     SysMap m;
-    m.tile_unit_off = c->tile_unit_off_d;
-    m.tile_src = c->tile_src_d;
     m.pos_of_seg = c->pos_of_seg_d;
     m.pad_map = c->pad_map_d;
-    m.n_tiles = c->rpy_tiles;
     m.n_chunks = 0;
+    if (active_only) {
+        m.tile_unit_off = c->act_unit_off_d;
+        m.tile_src = c->act_src_d;
+        m.tile_id = c->act_tile_d;
+        m.slot_of = c->act_slot_d;
+        m.n_tiles = c->act_tiles;
+    } else {
+        m.tile_unit_off = c->tile_unit_off_d;
+        m.tile_src = c->tile_src_d;
+        m.tile_id = nullptr;
+        m.slot_of = nullptr;
+        m.n_tiles = c->rpy_tiles;
+    }
     return m;
 }
 
@@ -748,6 +770,7 @@ cudaError_t rpy_setup(fil_ctx *c) {
     c->sys_pad_off_h.assign(ns + 1, 0);
     c->tile_unit_off_h.assign(1, 0);
     c->tile_src_h.clear();
+    c->tile_sys_h.clear();
     for (int s = 0; s < ns; ++s) {
         const int64_t Ss = c->sys_seg_off_h[s + 1] - c->sys_seg_off_h[s];
         const int64_t tiles = (Ss + kRpyTile - 1) / kRpyTile;
@@ -756,9 +779,16 @@ cudaError_t rpy_setup(fil_ctx *c) {
         for (int64_t t = 0; t < tiles; ++t) {
             c->tile_unit_off_h.push_back(c->tile_unit_off_h.back() + chunks);
             c->tile_src_h.push_back(c->sys_pad_off_h[s]);
+            c->tile_sys_h.push_back(s);
         }
     }
     c->rpy_tiles = (int64_t)c->tile_src_h.size();
+    c->pairs_all = 0.0;
+    for (int s = 0; s < ns; ++s) {
+        const double Ss = (double)(c->sys_seg_off_h[s + 1] - c->sys_seg_off_h[s]);
+        c->pairs_all += Ss * Ss;
+    }
+    c->pairs_act = c->pairs_all;
     c->rpy_units = c->tile_unit_off_h.back();
     c->Spad = c->sys_pad_off_h[ns];
     c->pos_of_seg_h.resize(c->lay.S);
@@ -795,15 +825,52 @@ size_t rpy_partial_bytes(const fil_ctx *c) {
     return (size_t)(G + c->rpy_tiles) * kRpyTile * 12 * sizeof(float);
 }
 
-cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW) {
+// The tiles of the systems still iterating (c->active_h), listed for the
+// stream-K split of the next applies with active_only.
+cudaError_t rpy_set_active(fil_ctx *c) {
+    std::vector<int64_t> uoff(1, 0), src;
+    std::vector<int> tid, slot(c->rpy_tiles, -1);
+    for (int64_t t = 0; t < c->rpy_tiles; ++t) {
+        if (!c->active_h[c->tile_sys_h[t]]) continue;
+        slot[t] = (int)tid.size();
+        tid.push_back((int)t);
+        src.push_back(c->tile_src_h[t]);
+        uoff.push_back(uoff.back() + (c->tile_unit_off_h[t + 1] - c->tile_unit_off_h[t]));
+    }
+    c->act_tiles = (int64_t)tid.size();
+    c->act_units = uoff.back();
+    c->pairs_act = 0.0;
+    for (int s = 0; s < c->n_sys; ++s)
+        if (c->active_h[s]) {
+            const double Ss = (double)(c->sys_seg_off_h[s + 1] - c->sys_seg_off_h[s]);
+            c->pairs_act += Ss * Ss;
+        }
+    cudaError_t e = cudaMemcpyAsync(c->act_unit_off_d, uoff.data(), sizeof(int64_t) * uoff.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !tid.empty())
+        e = cudaMemcpyAsync(c->act_src_d, src.data(), sizeof(int64_t) * src.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !tid.empty())
+        e = cudaMemcpyAsync(c->act_tile_d, tid.data(), sizeof(int) * tid.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->act_slot_d, slot.data(), sizeof(int) * slot.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // host vectors go out of scope
+    return e;
+}
+
+cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
+                      bool active_only) {
     const int64_t S = c->lay.S;
     const double scale = 1.0 / (8.0 * kPi * c->eta);
     const int pb = 256;
     const unsigned pgrid = (unsigned)((c->Spad + pb - 1) / pb);
     const unsigned rgrid = (unsigned)((S + pb - 1) / pb);
     const bool timed = c->prof_on && c->prof_n < kProfMax;
-    const SysMap sm = sys_map(c);
-    const int64_t W = c->rpy_units;
+    const SysMap sm = sys_map(c, active_only);
+    const int64_t W = active_only ? c->act_units : c->rpy_units;
+    if (W == 0) return cudaSuccess;
     if (c->prec == FIL_MIXED) {
         const int G = (int)std::min<int64_t>(c->rpy_grid32, W);
         pack32_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, sm, c->src32);
@@ -825,6 +892,7 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW)
     }
     if (timed) c->prof_n += 1;
     c->n_applies += 1;
+    c->n_pairs += active_only ? c->pairs_act : c->pairs_all;
     c->n_launches += 3;
     return cudaGetLastError();
 }

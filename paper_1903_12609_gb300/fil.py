@@ -33,7 +33,7 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_mlp_create", "fil_mlp_destroy", "fil_mlp_set_params", "fil_mlp_get_params",
             "fil_mlp_set_norm", "fil_mlp_forward", "fil_mlp_gradients", "fil_mlp_train_step",
             "fil_tc_gemm_bf16", "fil_warm_features", "fil_warm_targets", "fil_warm_attach",
-            "fil_warm_stats", "fil_create_ensemble", "fil_sys_stats"]
+            "fil_warm_stats", "fil_create_ensemble", "fil_sys_stats", "fil_pair_count"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_SEG = 800, 256, 192, 32
 MLP_NPARAM = 256 * 800 + 256 + 2 * (256 * 256 + 256) + 192 * 256 + 192
 FIL_WARM_BEST_OF_TWO, FIL_WARM_PREDICTION_FIRST = 0, 1
@@ -103,6 +103,7 @@ def load_library(path=LIB_PATH):
         "fil_create_ensemble": [ctypes.POINTER(fil_params), ctypes.c_int32, I32,
                                 ctypes.POINTER(P)],
         "fil_sys_stats": [P, I32, D],
+        "fil_pair_count": [P, D],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -169,6 +170,12 @@ def fil_sys_stats(ctx, n_sys):
     _check(ctx, _lib.fil_sys_stats(ctx, it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                    fi.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return it, fi
+
+
+def fil_pair_count(ctx):
+    v = ctypes.c_double()
+    _check(ctx, _lib.fil_pair_count(ctx, ctypes.byref(v)))
+    return v.value
 
 
 def fil_destroy(ctx):
