@@ -225,12 +225,12 @@ def run_ensemble(args, fil, torch):
                       j0_model=j0, stream=stream.cuda_stream)
     m.init_straight(base, t, mu, None)
     m.set_external(Fext, None, follower)
+    m.set_graph(args.graph)
     for _ in range(args.warmup):
         m.step()
+    tuned = m.autotune(2) if args.tune else None
     a0, i0, k0 = m.counters()
     p0 = m.pair_count()
-    m.profile(True)
-    m.profile_read()
     torch.cuda.synchronize()
     clk = clocks_start()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -243,14 +243,23 @@ def run_ensemble(args, fil, torch):
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clocks_stop(clk, 0)
-    n_pair, pair_ms = m.profile_read()
     a1, _, k1 = m.counters()
     pairs = m.pair_count() - p0
-    m.close()
     ms = e0.elapsed_time(e1)
     si = np.array(sys_iters)
+    # the pair kernel on its own (CUDA events per launch, outside the graphs):
+    # two more steps with kernel launches and the library's timing on
+    m.set_graph(0)
+    m.profile(True)
+    m.profile_read()
+    q0 = m.pair_count()
+    for _ in range(2):
+        m.step()
+    n_pair, pair_ms = m.profile_read()
+    pairs_prof = m.pair_count() - q0
+    m.close()
     # pairs actually evaluated (converged systems drop out of the applies)
-    achieved = FLOPS_PER_PAIR * pairs / (pair_ms * 1e-3) / 1e12
+    achieved = FLOPS_PER_PAIR * pairs_prof / (pair_ms * 1e-3) / 1e12
     pair_avg = pair_ms / max(n_pair, 1)
     print(json.dumps({
         "metric": METRIC, "value": pairs / (ms * 1e-3), "unit": UNIT,
@@ -270,7 +279,10 @@ def run_ensemble(args, fil, torch):
         "roofline": {"kernel": "rpy_pair32", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "avg_launch_ms": pair_avg,
-                     "launches": int(n_pair), "share_of_step": pair_ms / ms},
+                     "launches": int(n_pair), "measured_over": "2 steps without graphs"},
+        "graph": bool(args.graph),
+        "autotuned": ({"tile": tuned[0], "ctas_per_sm": tuned[1], "ms_per_apply": tuned[2]}
+                      if tuned else None),
         "gpu_launches": int(k1 - k0), "clocks": clocks}), flush=True)
 
 
@@ -294,6 +306,9 @@ def main():
                     help="learned warm start of each step (the committed network) and its mode")
     ap.add_argument("--n-sys", type=int, default=256, help="systems of the ensemble workload")
     ap.add_argument("--ens-max-iter", type=int, default=100)
+    ap.add_argument("--tune", type=int, default=1, help="autotune the pair kernel (ensemble)")
+    ap.add_argument("--graph", type=int, default=1,
+                    help="run each Broyden iteration as one CUDA graph launch (ensemble)")
     ap.add_argument("--workload", default="suspension",
                     choices=["suspension", "mobility", "ensemble"],
                     help="'mobility': only RPY applies on the 32k configuration (for profiling)")

@@ -111,6 +111,24 @@ fil_status fil_create_ensemble(const fil_params *p, int32_t n_sys, const int32_t
  * current / last step and the last ||f||_inf that was read. */
 fil_status fil_sys_stats(const fil_ctx *c, int32_t *iters, double *finf);
 
+/* Autotuner of the RPY pair kernel: times `reps` mobility applies of the
+ * current state's loads for every candidate schedule -- tiles of 128 or 256
+ * targets (1 or 2 targets per thread) and 1..occupancy resident CTAs per SM
+ * for the stream-K split -- and keeps the fastest for all later applies.
+ * Reports the choice (nullable outputs) and its time per apply in ms. Results
+ * change only in rounding (the summation order of the pair terms). FIL_ESTATE
+ * inside a step. */
+fil_status fil_autotune(fil_ctx *c, int32_t reps, int32_t *tile, int32_t *ctas_per_sm,
+                        double *ms);
+
+/* Run each Broyden iteration of fil_broyden_step / fil_step as one CUDA graph
+ * launch (enable = 1) instead of separate kernel launches: the graph holds the
+ * update of X, the residual of the new iterate, the dot products, the J0 solve
+ * and the history update, captured once per buffer parity (again whenever an
+ * ensemble's set of iterating systems changes). Same results. Not with
+ * fil_profile on. FIL_ESTATE inside a step. */
+fil_status fil_set_graph(fil_ctx *c, int32_t enable);
+
 /* RPY pair interactions evaluated by this context's mobility applies so far
  * (sum over each apply of S_s^2 over the systems it evaluated; padding and
  * converged systems excluded). */

@@ -95,12 +95,14 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->lay.fil_of = ar.take<int>(S);
     c->lay.sys_of = ar.take<int>(S);
     c->sys_xoff = ar.take<int64_t>(c->n_sys + 1);
-    c->tile_unit_off_d = ar.take<int64_t>(c->rpy_tiles + 1);
-    c->tile_src_d = ar.take<int64_t>(c->rpy_tiles);
-    c->act_unit_off_d = ar.take<int64_t>(c->rpy_tiles + 1);
-    c->act_src_d = ar.take<int64_t>(c->rpy_tiles);
-    c->act_tile_d = ar.take<int>(c->rpy_tiles);
-    c->act_slot_d = ar.take<int>(c->rpy_tiles);
+    c->tile_unit_off_d = ar.take<int64_t>(c->rpy_tiles_max + 1);
+    c->tile_src_d = ar.take<int64_t>(c->rpy_tiles_max);
+    c->tile_id_d = ar.take<int>(c->rpy_tiles_max);
+    c->slot_d = ar.take<int>(c->Spad / kRpyThreads);
+    c->act_unit_off_d = ar.take<int64_t>(c->rpy_tiles_max + 1);
+    c->act_src_d = ar.take<int64_t>(c->rpy_tiles_max);
+    c->act_tile_d = ar.take<int>(c->rpy_tiles_max);
+    c->act_slot_d = ar.take<int>(c->Spad / kRpyThreads);
     c->pos_of_seg_d = ar.take<int64_t>(S);
     c->pad_map_d = ar.take<int>(c->Spad);
     c->Y = ar.take<double>(3 * S);
@@ -141,6 +143,7 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->blk_beg = ar.take<int64_t>(red_blocks + 1);
     c->sys_blk_off = ar.take<int>(c->n_sys + 1);
     c->d_active = ar.take<int>(c->n_sys);
+    c->d_k = ar.take<int>(1);
     char *sb = ar.take<char>(16 + 8 * (size_t)c->n_sys);
     c->d_flags = sb ? reinterpret_cast<int *>(sb) : nullptr;
     c->d_finf = sb ? reinterpret_cast<unsigned long long *>(sb + 16) : nullptr;
@@ -388,10 +391,14 @@ fil_status fil_create(const fil_params *p, fil_ctx **out) {
     return fil_create_ensemble(p, 1, &all, out);
 }
 
+void drop_graphs(fil_ctx *c);
+
 void fil_destroy(fil_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->arena) cudaFree(c->arena);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->prof_ev) {
@@ -612,6 +619,70 @@ cudaError_t upload_active(fil_ctx *c) {
                            cudaMemcpyHostToDevice, c->stream);
 }
 
+void drop_graphs(fil_ctx *c) {
+    for (int i = 0; i < 2; ++i) {
+        if (c->graph_exec[i]) cudaGraphExecDestroy(c->graph_exec[i]);
+        c->graph_exec[i] = nullptr;
+        c->graph_xk[i] = nullptr;
+    }
+}
+
+// One Broyden iteration as the device sees it in graph mode: the step, the
+// residual of the new iterate, and -- speculatively, before the host has
+// checked convergence -- the dot products, the J0 solve and the history update
+// (wasted once per step; for systems that have just converged, w is masked
+// afterwards).
+cudaError_t iteration_body(fil_ctx *c) {
+    cudaError_t e = broyden_axpy_step(c);
+    if (e == cudaSuccess) e = eval_residual(c, c->Xn, c->fn, 1, c->n_sys > 1 ? c->fk : nullptr);
+    if (e == cudaSuccess) e = broyden_dots(c);
+    if (e == cudaSuccess) e = j0_apply(c, c->fn, c->g);
+    if (e == cudaSuccess) e = broyden_update(c);
+    return e;
+}
+
+// The graph of iteration_body for the current buffers (captured if needed).
+cudaError_t graph_for_current(fil_ctx *c, int *slot) {
+    for (int i = 0; i < 2; ++i)
+        if (c->graph_exec[i] && c->graph_xk[i] == c->Xk) {
+            *slot = i;
+            return cudaSuccess;
+        }
+    const int i = c->graph_exec[0] ? 1 : 0;
+    const int64_t l0 = c->n_launches, a0 = c->n_applies;
+    const double p0 = c->n_pairs;
+    cudaGraph_t g = nullptr;
+    // captured on the context's private stream (the legacy stream cannot be
+    // captured); launched on the context's stream
+    const cudaStream_t own = c->stream;
+    c->stream = c->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        c->stream = own;
+        return e;
+    }
+    cudaError_t eb = iteration_body(c);
+    e = cudaStreamEndCapture(c->stream, &g);
+    c->stream = own;
+    if (eb != cudaSuccess) e = eb;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec[i], g, 0);
+    if (g) cudaGraphDestroy(g);
+    // the counters advanced during capture; each launch adds them instead
+    c->graph_launches[i] = c->n_launches - l0;
+    c->graph_applies[i] = c->n_applies - a0;
+    c->graph_pairs[i] = c->n_pairs - p0;
+    c->n_launches = l0;
+    c->n_applies = a0;
+    c->n_pairs = p0;
+    if (e != cudaSuccess) {
+        c->graph_exec[i] = nullptr;
+        return e;
+    }
+    c->graph_xk[i] = c->Xk;
+    *slot = i;
+    return cudaSuccess;
+}
+
 fil_status begin_step(fil_ctx *c, double *finf, bool use_net) {
     if (!c) return FIL_EINVAL;
     CK(cudaSetDevice(c->device));
@@ -630,6 +701,8 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net) {
     c->finf_h = f0_sys;
     if (finf) *finf = f0;
     c->k = 0;
+    CK(cudaMemsetAsync(c->d_k, 0, sizeof(int), c->stream));
+    drop_graphs(c);      // scheme weights, J0 and the active set may have changed
     c->iters_step = 0;
     c->in_step = 0;
     if (sb.flags[1]) return set_err(c, FIL_ENAN, "fil_broyden_begin: J0 is singular");
@@ -660,6 +733,41 @@ fil_status fil_broyden_step(fil_ctx *c, int32_t *converged, double *finf) {
     }
     if (c->iters_step >= c->max_iter)
         return set_err(c, FIL_ENOCONV, "Broyden: max_iter reached without convergence");
+    if (c->use_graph && !c->prof_on) {
+        int slot = 0;
+        CK(graph_for_current(c, &slot));
+        CK(cudaGraphLaunch(c->graph_exec[slot], c->stream));
+        c->n_launches += c->graph_launches[slot];
+        c->n_applies += c->graph_applies[slot];
+        c->n_pairs += c->graph_pairs[slot];
+        StatusBlock sb;
+        fil_status s = read_status(c, &sb);
+        if (s != FIL_OK) return s;
+        const double fv = finf_of(sb);
+        if (finf) *finf = fv;
+        if (!std::isfinite(fv)) return set_err(c, FIL_ENAN, "Broyden: residual not finite");
+        c->iters_step += 1;
+        c->n_iters += 1;
+        if (update_active(c, true) == 0) {
+            std::swap(c->Xk, c->Xn);
+            std::swap(c->fk, c->fn);
+            c->conv = 1;
+            if (converged) *converged = 1;
+            return FIL_OK;
+        }
+        if (sb.flags[0]) return set_err(c, FIL_ESTALL, "Broyden: ||df|| = 0 (stalled)");
+        if (c->n_sys > 1 && c->active_h != c->active_prev_h) {
+            CK(upload_active(c));
+            CK(broyden_mask_inactive(c, c->w));
+            CK(rpy_set_active(c));
+            drop_graphs(c);
+        }
+        std::swap(c->Xk, c->Xn);
+        std::swap(c->fk, c->fn);
+        c->k += 1;
+        if (converged) *converged = 0;
+        return FIL_OK;
+    }
     CK(broyden_axpy_step(c));
     CK(eval_residual(c, c->Xn, c->fn, 1, c->n_sys > 1 ? c->fk : nullptr));
     StatusBlock sb;
@@ -797,6 +905,32 @@ fil_status fil_warm_stats(const fil_ctx *c, int64_t *from_prediction, int64_t *f
     if (from_prediction) *from_prediction = c->warm_pred;
     if (from_extrapolation) *from_extrapolation = c->warm_extrap;
     if (restarts) *restarts = c->warm_restart;
+    return FIL_OK;
+}
+
+fil_status fil_autotune(fil_ctx *c, int32_t reps, int32_t *tile, int32_t *ctas_per_sm,
+                        double *ms) {
+    if (!c) return FIL_EINVAL;
+    if (reps < 1) return set_err(c, FIL_EINVAL, "fil_autotune: reps >= 1");
+    if (c->in_step) return set_err(c, FIL_ESTATE, "fil_autotune: a step is in progress");
+    CK(cudaSetDevice(c->device));
+    // the loads of the current state (the unpack of X = (Y_1, 0, Lambda))
+    CK(warm_features(c, nullptr, c->warm_feat));
+    CK(rpy_autotune(c, c->Yc, c->FT, c->VW, reps, ms));
+    drop_graphs(c);
+    if (tile) *tile = kRpyThreads * c->rpy_tpt;
+    if (ctas_per_sm) *ctas_per_sm = c->rpy_ctas;
+    return FIL_OK;
+}
+
+fil_status fil_set_graph(fil_ctx *c, int32_t enable) {
+    if (!c) return FIL_EINVAL;
+    if (c->in_step) return set_err(c, FIL_ESTATE, "fil_set_graph: a step is in progress");
+    CK(cudaSetDevice(c->device));
+    drop_graphs(c);
+    if (enable && !c->cap_stream)
+        CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    c->use_graph = enable ? 1 : 0;
     return FIL_OK;
 }
 

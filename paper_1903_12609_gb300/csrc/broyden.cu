@@ -77,9 +77,10 @@ __device__ __forceinline__ void dots_group(const double *__restrict__ D, int64_t
 // in compile-time groups so that every FP64 instruction is useful work.
 __global__ void dots_partial_kernel(int64_t n, const double *__restrict__ fn,
                                     const double *__restrict__ fk, const double *__restrict__ D,
-                                    int k, const int64_t *__restrict__ blk_beg,
+                                    const int *__restrict__ dk, const int64_t *__restrict__ blk_beg,
                                     double *__restrict__ part) {
     __shared__ double sh[kDotGroup * 32];
+    const int k = *dk;
     const int nb = gridDim.x;
     const int64_t i0 = blk_beg[blockIdx.x], i1 = blk_beg[blockIdx.x + 1];
     {
@@ -108,14 +109,15 @@ __global__ void dots_partial_kernel(int64_t n, const double *__restrict__ fn,
     }
 }
 
-__global__ void dots_final_kernel(int n_sys, int nout, int nblocks, const int *__restrict__ sys_blk,
-                                  const double *__restrict__ part, int sstride,
-                                  double *__restrict__ out) {
+__global__ void dots_final_kernel(int n_sys, int max_out, const int *__restrict__ dk, int nblocks,
+                                  const int *__restrict__ sys_blk, const double *__restrict__ part,
+                                  int sstride, double *__restrict__ out) {
     // one warp per (system, output), lanes stride the system's partials, fixed-order tree
     const int64_t job = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (job >= (int64_t)n_sys * nout) return;
-    const int sy = (int)(job / nout), o = (int)(job - (int64_t)sy * nout);
+    if (job >= (int64_t)n_sys * max_out) return;
+    const int sy = (int)(job / max_out), o = (int)(job - (int64_t)sy * max_out);
+    if (o >= *dk + 2) return;
     double s = 0.0;
     for (int b = sys_blk[sy] + lane; b < sys_blk[sy + 1]; b += 32) s += part[(int64_t)o * nblocks + b];
 #pragma unroll
@@ -125,7 +127,8 @@ __global__ void dots_final_kernel(int n_sys, int nout, int nblocks, const int *_
 
 // g += sum_i c_i alpha_i; history pair k; w = g + c_k (df . fn)/|df|, with the
 // scalars of entry i's system; w = 0 in systems that have converged.
-__global__ void update_kernel(int64_t n, int k, const double *__restrict__ scal_all, int sstride,
+__global__ void update_kernel(int64_t n, const int *__restrict__ dk,
+                              const double *__restrict__ scal_all, int sstride,
                               const int *__restrict__ sys_of, const int *__restrict__ active,
                               const double *__restrict__ fn, const double *__restrict__ fk,
                               double *__restrict__ g, double *__restrict__ C,
@@ -138,6 +141,7 @@ __global__ void update_kernel(int64_t n, int k, const double *__restrict__ scal_
         w[i] = 0.0;
         return;
     }
+    const int k = *dk;
     const double *scal = scal_all + (int64_t)sy * sstride;
     const double ndf2 = scal[k];
     if (!(ndf2 > 0.0)) flags[0] = 1;
@@ -150,6 +154,8 @@ __global__ void update_kernel(int64_t n, int k, const double *__restrict__ scal_
     D[(int64_t)k * n + i] = d;
     w[i] = gi + c * (scal[k + 1] / ndf);
 }
+
+__global__ void k_advance_kernel(int *dk) { *dk += 1; }
 
 __global__ void mask_inactive_kernel(int64_t n, const int *__restrict__ sys_of,
                                      const int *__restrict__ active, double *__restrict__ v) {
@@ -177,12 +183,12 @@ cudaError_t broyden_axpy_step(fil_ctx *c) {
 
 cudaError_t broyden_dots(fil_ctx *c) {
     const int64_t n = c->lay.nX;
-    dots_partial_kernel<<<c->red_blocks, kRedThreads, 0, c->stream>>>(n, c->fn, c->fk, c->D, c->k,
+    dots_partial_kernel<<<c->red_blocks, kRedThreads, 0, c->stream>>>(n, c->fn, c->fk, c->D, c->d_k,
                                                                        c->blk_beg, c->red_part);
-    const int nout = c->k + 2;
-    const int64_t jobs = (int64_t)c->n_sys * nout;
+    const int max_out = c->max_iter + 2;
+    const int64_t jobs = (int64_t)c->n_sys * max_out;
     dots_final_kernel<<<(unsigned)((jobs + 7) / 8), 256, 0, c->stream>>>(
-        c->n_sys, nout, c->red_blocks, c->sys_blk_off, c->red_part, c->sstride, c->scal);
+        c->n_sys, max_out, c->d_k, c->red_blocks, c->sys_blk_off, c->red_part, c->sstride, c->scal);
     c->n_launches += 2;
     return cudaGetLastError();
 }
@@ -190,9 +196,10 @@ cudaError_t broyden_dots(fil_ctx *c) {
 cudaError_t broyden_update(fil_ctx *c) {
     const int64_t n = c->lay.nX;
     update_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
-        n, c->k, c->scal, c->sstride, c->lay.sys_of, c->d_active, c->fn, c->fk, c->g, c->C, c->D,
+        n, c->d_k, c->scal, c->sstride, c->lay.sys_of, c->d_active, c->fn, c->fk, c->g, c->C, c->D,
         c->w, c->d_flags);
-    c->n_launches += 1;
+    k_advance_kernel<<<1, 1, 0, c->stream>>>(c->d_k);     // the next history slot
+    c->n_launches += 2;
     return cudaGetLastError();
 }
 

@@ -84,9 +84,13 @@ struct fil_ctx {
     int rpy_grid32, rpy_grid64;
     int64_t rpy_tiles, rpy_units;
     std::vector<int64_t> sys_pad_off_h, tile_unit_off_h, tile_src_h, pos_of_seg_h;
-    std::vector<int> pad_map_h, tile_sys_h;
+    std::vector<int> pad_map_h, tile_sys_h, tile_id_h;
     int64_t *tile_unit_off_d, *tile_src_d, *pos_of_seg_d;
-    int *pad_map_d;
+    int *pad_map_d, *tile_id_d, *slot_d;
+    int rpy_tpt;           // targets per thread of the pair kernels (tile = 128 x tpt)
+    int rpy_ctas;          // resident CTAs per SM of the stream-K grid
+    int rpy_ctas_max;
+    int64_t rpy_tiles_max; // listed tiles at the smallest tile size
     // the tiles of the systems still iterating (ensembles): applies inside a
     // Broyden iteration only evaluate those
     int64_t act_tiles, act_units;
@@ -113,6 +117,15 @@ struct fil_ctx {
     std::vector<double> finf_h;               // ||f||_inf per system, last read
     double *h_pinned;      // small pinned host buffer
     int k;                 // stored (c, d) pairs of the current step
+    int *d_k;              // the same count on the device (read by the Broyden kernels)
+    // CUDA graphs of one Broyden iteration (fil_set_graph): one per buffer
+    // parity, captured on first use in a step or after the active set changed
+    int use_graph;
+    cudaStream_t cap_stream;   // private stream the graphs are captured on
+    cudaGraphExec_t graph_exec[2];
+    const double *graph_xk[2];
+    int64_t graph_launches[2], graph_applies[2];
+    double graph_pairs[2];
     int in_step;           // a step was begun and not committed
     int iters_step;        // Broyden iterations of the current step
     int conv;              // current iterate satisfies ||f||_inf <= tol * a
@@ -161,6 +174,8 @@ namespace fil {
 cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
                       bool active_only = false);
 cudaError_t rpy_set_active(fil_ctx *c);     // list the active systems' tiles
+cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *VW, int reps,
+                         double *best_ms);
 cudaError_t rpy_setup(fil_ctx *c);          // grid sizes and padded layout, once at create
 cudaError_t rpy_upload_tables(fil_ctx *c);  // the layout tables, after the arena exists
 size_t rpy_partial_bytes(const fil_ctx *c);

@@ -416,11 +416,13 @@ __device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
 // pair is recomputed exactly, and the group sums are folded (TwoSum) into
 // (hi, lo) accumulators.
 // ---------------------------------------------------------------------------
+template <int TPT>
 __global__ void __launch_bounds__(kRpyThreads, FIL_RPY_MINB)
 rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G, RpyConst32 k,
                   float *__restrict__ part) {
     constexpr int kRec = kRpyPairF4 * (kRpyChunk / 2);   // float4 per chunk
-    constexpr int kT = kRpyTargetsPerThread;
+    constexpr int kT = TPT;                               // targets per thread
+    constexpr int kTile = kRpyThreads * TPT;              // targets per tile
     __shared__ float4 sm[2][kRec];
     const int tid = threadIdx.x;
     const int64_t b = blockIdx.x;
@@ -438,7 +440,7 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
         float th[kT][3], tl[kT][3];
 #pragma unroll
         for (int t = 0; t < kT; ++t) {
-            const int64_t n = ptile * kRpyTile + t * kRpyThreads + tid;
+            const int64_t n = ptile * kTile + t * kRpyThreads + tid;
 #if FIL_RPY_PACKED
             float4 a0, a1, a2;
             unpack_source(src + kRpyPairF4 * (n >> 1), (int)(n & 1), a0, a1, a2);
@@ -577,14 +579,14 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
         }
 
         // partial of this CTA for this tile -> slot (b + tile)
-        float *p = part + (size_t)(b + tile) * 12 * kRpyTile;
+        float *p = part + (size_t)(b + tile) * 12 * kTile;
 #pragma unroll
         for (int t = 0; t < kT; ++t) {
             const int local = t * kRpyThreads + tid;
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                p[c * kRpyTile + local] = hi[t][c];
-                p[(6 + c) * kRpyTile + local] = lo[t][c];
+                p[c * kTile + local] = hi[t][c];
+                p[(6 + c) * kTile + local] = lo[t][c];
             }
         }
         u = ubeg + c_end;
@@ -594,10 +596,12 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
 // ---------------------------------------------------------------------------
 // FP64 pair kernel (same stream-K scaffolding).
 // ---------------------------------------------------------------------------
+template <int TPT>
 __global__ void __launch_bounds__(kRpyThreads)
 rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G, RpyConst64 k,
                   double *__restrict__ part) {
     constexpr int kRec = 9 * kRpyChunk;
+    constexpr int kTile = kRpyThreads * TPT;
     __shared__ double sm[2][kRec];
     const int tid = threadIdx.x;
     const int64_t b = blockIdx.x;
@@ -612,17 +616,17 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
         const double *srcs = src + 9 * src0;
         const int64_t ptile = smap.tile_id ? smap.tile_id[tile] : tile;
 
-        double ty[kRpyTargetsPerThread][3];
+        double ty[TPT][3];
 #pragma unroll
-        for (int t = 0; t < kRpyTargetsPerThread; ++t) {
-            const int64_t n = ptile * kRpyTile + t * kRpyThreads + tid;
+        for (int t = 0; t < TPT; ++t) {
+            const int64_t n = ptile * kTile + t * kRpyThreads + tid;
             ty[t][0] = src[9 * n];
             ty[t][1] = src[9 * n + 1];
             ty[t][2] = src[9 * n + 2];
         }
-        double acc[kRpyTargetsPerThread][6];
+        double acc[TPT][6];
 #pragma unroll
-        for (int t = 0; t < kRpyTargetsPerThread; ++t)
+        for (int t = 0; t < TPT; ++t)
 #pragma unroll
             for (int c = 0; c < 6; ++c) acc[t][c] = 0.0;
 
@@ -647,7 +651,7 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
 #pragma unroll 2
             for (int j = 0; j < kRpyChunk; ++j) {
 #pragma unroll
-                for (int t = 0; t < kRpyTargetsPerThread; ++t)
+                for (int t = 0; t < TPT; ++t)
                     pair64(ty[t][0], ty[t][1], ty[t][2], s + 9 * j, k, acc[t]);
             }
             if (has_next) {
@@ -659,12 +663,12 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
             }
             __syncthreads();
         }
-        double *p = part + (size_t)(b + tile) * 6 * kRpyTile;
+        double *p = part + (size_t)(b + tile) * 6 * kTile;
 #pragma unroll
-        for (int t = 0; t < kRpyTargetsPerThread; ++t) {
+        for (int t = 0; t < TPT; ++t) {
             const int local = t * kRpyThreads + tid;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) p[c * kRpyTile + local] = acc[t][c];
+            for (int c = 0; c < 6; ++c) p[c * kTile + local] = acc[t][c];
         }
         u = ubeg + c_end;
     }
@@ -685,12 +689,13 @@ __device__ __forceinline__ void cta_range_of_tile(const SysMap &sm, int64_t tile
 }
 
 __global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, SysMap sm,
-                                    int64_t W, int G, double scale, double *__restrict__ VW) {
+                                    int64_t W, int G, int T, double scale,
+                                    double *__restrict__ VW) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= S) return;
     const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
-    int64_t tile = P / kRpyTile;
-    const int local = (int)(P - tile * kRpyTile);
+    int64_t tile = P / T;
+    const int local = (int)(P - tile * T);
     if (sm.slot_of) {
         tile = sm.slot_of[tile];
         if (tile < 0) return;         // a system left out of this apply
@@ -699,22 +704,23 @@ __global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, S
     cta_range_of_tile(sm, tile, W, G, b0, b1);
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t b = b0; b <= b1; ++b) {
-        const float *p = part + (size_t)(b + tile) * 12 * kRpyTile;
+        const float *p = part + (size_t)(b + tile) * 12 * T;
 #pragma unroll
         for (int c = 0; c < 6; ++c)
-            acc[c] += (double)p[c * kRpyTile + local] + (double)p[(6 + c) * kRpyTile + local];
+            acc[c] += (double)p[c * T + local] + (double)p[(6 + c) * T + local];
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c) VW[6 * n + c] = acc[c] * scale;
 }
 
 __global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, SysMap sm,
-                                    int64_t W, int G, double scale, double *__restrict__ VW) {
+                                    int64_t W, int G, int T, double scale,
+                                    double *__restrict__ VW) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= S) return;
     const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
-    int64_t tile = P / kRpyTile;
-    const int local = (int)(P - tile * kRpyTile);
+    int64_t tile = P / T;
+    const int local = (int)(P - tile * T);
     if (sm.slot_of) {
         tile = sm.slot_of[tile];
         if (tile < 0) return;         // a system left out of this apply
@@ -723,9 +729,9 @@ __global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, 
     cta_range_of_tile(sm, tile, W, G, b0, b1);
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t b = b0; b <= b1; ++b) {
-        const double *p = part + (size_t)(b + tile) * 6 * kRpyTile;
+        const double *p = part + (size_t)(b + tile) * 6 * T;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) acc[c] += p[c * kRpyTile + local];
+        for (int c = 0; c < 6; ++c) acc[c] += p[c * T + local];
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c) VW[6 * n + c] = acc[c] * scale;
@@ -745,51 +751,79 @@ SysMap sys_map(const fil_ctx *c, bool active_only) {
     } else {
         m.tile_unit_off = c->tile_unit_off_d;
         m.tile_src = c->tile_src_d;
-        m.tile_id = nullptr;
-        m.slot_of = nullptr;
+        m.tile_id = c->tile_id_d;
+        m.slot_of = c->slot_d;
         m.n_tiles = c->rpy_tiles;
     }
     return m;
 }
 
-}  // namespace
+constexpr int kRpyPad = 256;   // systems start at multiples of this in the padded layout
 
-cudaError_t rpy_setup(fil_ctx *c) {
-    int occ32 = 0, occ64 = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, rpy_pair32_kernel,
-                                                                  kRpyThreads, 0);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, rpy_pair64_kernel, kRpyThreads, 0);
-    if (e != cudaSuccess) return e;
-    if (FIL_RPY_OCC > 0) occ32 = FIL_RPY_OCC;
-    c->rpy_grid32 = std::max(1, occ32) * c->num_sms;
-    c->rpy_grid64 = std::max(1, occ64) * c->num_sms;
-    // padded layout: system s gets ceil(S_s / tile) tiles of targets, each
-    // with ceil(S_s / chunk) source chunks
-    const int ns = c->n_sys;
-    c->sys_pad_off_h.assign(ns + 1, 0);
+int64_t count_tiles(const fil_ctx *c, int T) {
+    int64_t n = 0;
+    for (int s = 0; s < c->n_sys; ++s)
+        n += (c->sys_seg_off_h[s + 1] - c->sys_seg_off_h[s] + T - 1) / T;
+    return n;
+}
+
+// Tiles of T targets of every system (only tiles that hold real targets),
+// each with ceil(S_s / chunk) source chunks.
+void build_tiles(fil_ctx *c) {
+    const int T = kRpyThreads * c->rpy_tpt;
     c->tile_unit_off_h.assign(1, 0);
     c->tile_src_h.clear();
     c->tile_sys_h.clear();
-    for (int s = 0; s < ns; ++s) {
+    c->tile_id_h.clear();
+    for (int s = 0; s < c->n_sys; ++s) {
         const int64_t Ss = c->sys_seg_off_h[s + 1] - c->sys_seg_off_h[s];
-        const int64_t tiles = (Ss + kRpyTile - 1) / kRpyTile;
+        const int64_t tiles = (Ss + T - 1) / T;
         const int64_t chunks = (Ss + kRpyChunk - 1) / kRpyChunk;
-        c->sys_pad_off_h[s + 1] = c->sys_pad_off_h[s] + tiles * kRpyTile;
         for (int64_t t = 0; t < tiles; ++t) {
             c->tile_unit_off_h.push_back(c->tile_unit_off_h.back() + chunks);
             c->tile_src_h.push_back(c->sys_pad_off_h[s]);
             c->tile_sys_h.push_back(s);
+            c->tile_id_h.push_back((int)(c->sys_pad_off_h[s] / T + t));
         }
     }
     c->rpy_tiles = (int64_t)c->tile_src_h.size();
+    c->rpy_units = c->tile_unit_off_h.back();
+}
+
+template <typename K>
+int occupancy(K kernel) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kRpyThreads, 0) != cudaSuccess)
+        return 1;
+    return std::max(1, occ);
+}
+
+void set_grids(fil_ctx *c) {
+    c->rpy_grid32 = c->rpy_ctas * c->num_sms;
+    c->rpy_grid64 = c->rpy_ctas * c->num_sms;
+}
+
+}  // namespace
+
+cudaError_t rpy_setup(fil_ctx *c) {
+    c->rpy_tpt = kRpyTargetsPerThread;
+    int occ = c->prec == FIL_MIXED ? occupancy(rpy_pair32_kernel<kRpyTargetsPerThread>)
+                                   : occupancy(rpy_pair64_kernel<kRpyTargetsPerThread>);
+    if (FIL_RPY_OCC > 0) occ = FIL_RPY_OCC;
+    c->rpy_ctas = occ;
+    c->rpy_ctas_max = std::max({occ, occupancy(rpy_pair32_kernel<1>), occupancy(rpy_pair32_kernel<2>),
+                                occupancy(rpy_pair64_kernel<1>), occupancy(rpy_pair64_kernel<2>)});
+    set_grids(c);
+    // padded layout: system s occupies [pad_off[s], pad_off[s+1]), a multiple of kRpyPad
+    const int ns = c->n_sys;
+    c->sys_pad_off_h.assign(ns + 1, 0);
     c->pairs_all = 0.0;
     for (int s = 0; s < ns; ++s) {
-        const double Ss = (double)(c->sys_seg_off_h[s + 1] - c->sys_seg_off_h[s]);
-        c->pairs_all += Ss * Ss;
+        const int64_t Ss = c->sys_seg_off_h[s + 1] - c->sys_seg_off_h[s];
+        c->sys_pad_off_h[s + 1] = c->sys_pad_off_h[s] + (Ss + kRpyPad - 1) / kRpyPad * kRpyPad;
+        c->pairs_all += (double)Ss * (double)Ss;
     }
     c->pairs_act = c->pairs_all;
-    c->rpy_units = c->tile_unit_off_h.back();
     c->Spad = c->sys_pad_off_h[ns];
     c->pos_of_seg_h.resize(c->lay.S);
     c->pad_map_h.assign(c->Spad, -1);
@@ -799,16 +833,33 @@ cudaError_t rpy_setup(fil_ctx *c) {
             c->pos_of_seg_h[g] = P;
             c->pad_map_h[P] = (int)g;
         }
+    c->rpy_tiles_max = std::max(count_tiles(c, kRpyThreads), count_tiles(c, 2 * kRpyThreads));
+    build_tiles(c);
     return cudaSuccess;
 }
 
-cudaError_t rpy_upload_tables(fil_ctx *c) {
+// Tile tables of the current tile size (after the arena exists, and after a retune).
+cudaError_t upload_tiles(fil_ctx *c) {
+    std::vector<int> slot(c->Spad / kRpyThreads, -1);
+    for (int64_t t = 0; t < c->rpy_tiles; ++t) slot[c->tile_id_h[t]] = (int)t;
     cudaError_t e = cudaMemcpyAsync(c->tile_unit_off_d, c->tile_unit_off_h.data(),
                                     sizeof(int64_t) * c->tile_unit_off_h.size(),
                                     cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->tile_src_d, c->tile_src_h.data(), sizeof(int64_t) * c->tile_src_h.size(),
                             cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->tile_id_d, c->tile_id_h.data(), sizeof(int) * c->tile_id_h.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->slot_d, slot.data(), sizeof(int) * slot.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // slot goes out of scope
+    return e;
+}
+
+cudaError_t rpy_upload_tables(fil_ctx *c) {
+    cudaError_t e = upload_tiles(c);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->pos_of_seg_d, c->pos_of_seg_h.data(),
                             sizeof(int64_t) * c->pos_of_seg_h.size(), cudaMemcpyHostToDevice,
@@ -820,20 +871,27 @@ cudaError_t rpy_upload_tables(fil_ctx *c) {
 }
 
 size_t rpy_partial_bytes(const fil_ctx *c) {
-    // slots b + tile for b < G and tile < n_tiles; 12 floats = 6 doubles per target
-    const int64_t G = std::max(c->rpy_grid32, c->rpy_grid64);
-    return (size_t)(G + c->rpy_tiles) * kRpyTile * 12 * sizeof(float);
+    // slots b + tile for b < G and listed tiles; 12 floats = 6 doubles per target;
+    // the largest over the tile sizes and grids the autotuner may choose
+    const int64_t G = (int64_t)c->rpy_ctas_max * c->num_sms;
+    size_t most = 0;
+    for (int tpt = 1; tpt <= 2; ++tpt) {
+        const int T = kRpyThreads * tpt;
+        const size_t b = (size_t)(G + count_tiles(c, T)) * T * 12 * sizeof(float);
+        most = std::max(most, b);
+    }
+    return most;
 }
 
 // The tiles of the systems still iterating (c->active_h), listed for the
 // stream-K split of the next applies with active_only.
 cudaError_t rpy_set_active(fil_ctx *c) {
     std::vector<int64_t> uoff(1, 0), src;
-    std::vector<int> tid, slot(c->rpy_tiles, -1);
+    std::vector<int> tid, slot(c->Spad / kRpyThreads, -1);
     for (int64_t t = 0; t < c->rpy_tiles; ++t) {
         if (!c->active_h[c->tile_sys_h[t]]) continue;
-        slot[t] = (int)tid.size();
-        tid.push_back((int)t);
+        slot[c->tile_id_h[t]] = (int)tid.size();
+        tid.push_back(c->tile_id_h[t]);
         src.push_back(c->tile_src_h[t]);
         uoff.push_back(uoff.back() + (c->tile_unit_off_h[t + 1] - c->tile_unit_off_h[t]));
     }
@@ -871,24 +929,35 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
     const SysMap sm = sys_map(c, active_only);
     const int64_t W = active_only ? c->act_units : c->rpy_units;
     if (W == 0) return cudaSuccess;
+    const int T = kRpyThreads * c->rpy_tpt;
     if (c->prec == FIL_MIXED) {
         const int G = (int)std::min<int64_t>(c->rpy_grid32, W);
         pack32_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, sm, c->src32);
         if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
-        rpy_pair32_kernel<<<G, kRpyThreads, 0, c->stream>>>(
-            c->src32, sm, W, G, make_const<float, RpyConst32>(c->a), (float *)c->partials);
+        const RpyConst32 k = make_const<float, RpyConst32>(c->a);
+        if (c->rpy_tpt == 1)
+            rpy_pair32_kernel<1><<<G, kRpyThreads, 0, c->stream>>>(c->src32, sm, W, G, k,
+                                                                   (float *)c->partials);
+        else
+            rpy_pair32_kernel<2><<<G, kRpyThreads, 0, c->stream>>>(c->src32, sm, W, G, k,
+                                                                   (float *)c->partials);
         if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
         rpy_reduce32_kernel<<<rgrid, pb, 0, c->stream>>>((const float *)c->partials, S, sm, W, G,
-                                                         scale, VW);
+                                                         T, scale, VW);
     } else {
         const int G = (int)std::min<int64_t>(c->rpy_grid64, W);
         pack64_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, sm, c->src64);
         if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
-        rpy_pair64_kernel<<<G, kRpyThreads, 0, c->stream>>>(
-            c->src64, sm, W, G, make_const<double, RpyConst64>(c->a), (double *)c->partials);
+        const RpyConst64 k = make_const<double, RpyConst64>(c->a);
+        if (c->rpy_tpt == 1)
+            rpy_pair64_kernel<1><<<G, kRpyThreads, 0, c->stream>>>(c->src64, sm, W, G, k,
+                                                                   (double *)c->partials);
+        else
+            rpy_pair64_kernel<2><<<G, kRpyThreads, 0, c->stream>>>(c->src64, sm, W, G, k,
+                                                                   (double *)c->partials);
         if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
         rpy_reduce64_kernel<<<rgrid, pb, 0, c->stream>>>((const double *)c->partials, S, sm, W, G,
-                                                         scale, VW);
+                                                         T, scale, VW);
     }
     if (timed) c->prof_n += 1;
     c->n_applies += 1;
@@ -897,6 +966,59 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
     return cudaGetLastError();
 }
 
+
+// Autotuner of the pair kernel: times every (targets per thread, resident CTAs
+// per SM) candidate on `reps` applies of (Y, FT) and keeps the fastest.
+cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *VW, int reps,
+                         double *best_ms) {
+    const int64_t a0 = c->n_applies, l0 = c->n_launches;
+    const double p0 = c->n_pairs;
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return e;
+    int best_tpt = c->rpy_tpt, best_ctas = c->rpy_ctas;
+    float best = 1e30f;
+    for (int tpt = 1; tpt <= 2 && e == cudaSuccess; ++tpt) {
+        int occ;
+        if (c->prec == FIL_MIXED)
+            occ = tpt == 1 ? occupancy(rpy_pair32_kernel<1>) : occupancy(rpy_pair32_kernel<2>);
+        else
+            occ = tpt == 1 ? occupancy(rpy_pair64_kernel<1>) : occupancy(rpy_pair64_kernel<2>);
+        for (int ctas = 1; ctas <= std::min(occ, c->rpy_ctas_max) && e == cudaSuccess; ++ctas) {
+            c->rpy_tpt = tpt;
+            c->rpy_ctas = ctas;
+            set_grids(c);
+            build_tiles(c);
+            e = upload_tiles(c);
+            if (e == cudaSuccess) e = rpy_apply(c, Y, FT, VW);       // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = rpy_apply(c, Y, FT, VW);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                best_tpt = tpt;
+                best_ctas = ctas;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->rpy_tpt = best_tpt;
+    c->rpy_ctas = best_ctas;
+    set_grids(c);
+    build_tiles(c);
+    if (e == cudaSuccess) e = upload_tiles(c);
+    c->n_applies = a0;
+    c->n_launches = l0;
+    c->n_pairs = p0;
+    if (best_ms) *best_ms = best / std::max(1, reps);
+    return e;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free mobility apply (fil_rpy_apply_noalloc).
@@ -940,7 +1062,8 @@ cudaError_t noalloc_setup(int dev, unsigned char **ptr, int *grid) {
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         int occ = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rpy_pair32_kernel, kRpyThreads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rpy_pair32_kernel<kRpyTargetsPerThread>,
+                                                          kRpyThreads, 0);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
@@ -991,9 +1114,9 @@ extern "C" fil_status fil_rpy_apply_noalloc(int64_t n_seg, const double *Y, cons
     sm.n_tiles = tiles;
     sm.n_chunks = n_chunks;
     pack32_kernel<<<(unsigned)((Spad + pb - 1) / pb), pb, 0, st>>>(Y, FT, n_seg, Spad, sm, src);
-    rpy_pair32_kernel<<<G, kRpyThreads, 0, st>>>(src, sm, W, G, make_const<float, RpyConst32>(a),
-                                                 part);
+    rpy_pair32_kernel<kRpyTargetsPerThread><<<G, kRpyThreads, 0, st>>>(
+        src, sm, W, G, make_const<float, RpyConst32>(a), part);
     rpy_reduce32_kernel<<<(unsigned)((n_seg + pb - 1) / pb), pb, 0, st>>>(
-        part, n_seg, sm, W, G, 1.0 / (8.0 * kPi * eta), VW);
+        part, n_seg, sm, W, G, kRpyTile, 1.0 / (8.0 * kPi * eta), VW);
     return cudaGetLastError() == cudaSuccess ? FIL_OK : FIL_ECUDA;
 }

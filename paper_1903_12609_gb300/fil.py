@@ -33,7 +33,8 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_mlp_create", "fil_mlp_destroy", "fil_mlp_set_params", "fil_mlp_get_params",
             "fil_mlp_set_norm", "fil_mlp_forward", "fil_mlp_gradients", "fil_mlp_train_step",
             "fil_tc_gemm_bf16", "fil_warm_features", "fil_warm_targets", "fil_warm_attach",
-            "fil_warm_stats", "fil_create_ensemble", "fil_sys_stats", "fil_pair_count"]
+            "fil_warm_stats", "fil_create_ensemble", "fil_sys_stats", "fil_pair_count",
+            "fil_set_graph", "fil_autotune"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_SEG = 800, 256, 192, 32
 MLP_NPARAM = 256 * 800 + 256 + 2 * (256 * 256 + 256) + 192 * 256 + 192
 FIL_WARM_BEST_OF_TWO, FIL_WARM_PREDICTION_FIRST = 0, 1
@@ -104,6 +105,8 @@ def load_library(path=LIB_PATH):
                                 ctypes.POINTER(P)],
         "fil_sys_stats": [P, I32, D],
         "fil_pair_count": [P, D],
+        "fil_set_graph": [P, ctypes.c_int32],
+        "fil_autotune": [P, ctypes.c_int32, I32, I32, D],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -170,6 +173,17 @@ def fil_sys_stats(ctx, n_sys):
     _check(ctx, _lib.fil_sys_stats(ctx, it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                    fi.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return it, fi
+
+
+def fil_autotune(ctx, reps=3):
+    tile, ctas, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(ctx, _lib.fil_autotune(ctx, int(reps), ctypes.byref(tile), ctypes.byref(ctas),
+                                  ctypes.byref(ms)))
+    return tile.value, ctas.value, ms.value
+
+
+def fil_set_graph(ctx, enable):
+    _check(ctx, _lib.fil_set_graph(ctx, int(bool(enable))))
 
 
 def fil_pair_count(ctx):

@@ -36,8 +36,9 @@ def _positions(rng, segs, box):
     return np.concatenate(Y)
 
 
+@pytest.mark.parametrize("tune", [False, True])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_mobility_is_block_diagonal_over_systems(fil, prec):
+def test_mobility_is_block_diagonal_over_systems(fil, prec, tune):
     rng = np.random.default_rng(prec)
     Ys, FTs = [], []
     for segs in SYSTEMS:
@@ -47,6 +48,10 @@ def test_mobility_is_block_diagonal_over_systems(fil, prec):
     segs_all = [n for segs in SYSTEMS for n in segs]
     with fil.Filaments(segs_all, fil_per_sys=[len(s) for s in SYSTEMS], precision=prec,
                        max_iter=10) as m:
+        if tune:
+            m.set_state(Y, np.tile([1.0, 0.0, 0.0, 0.0], (len(Y), 1)))
+            tile, ctas, ms = m.autotune(2)
+            assert tile in (128, 256) and ctas >= 1 and ms > 0
         VW = np.zeros_like(FT)
         m.mobility_apply(Y, FT, VW)
     off = 0
@@ -70,8 +75,9 @@ def _system(segs, seed):
     return lay, base, t, mu, xi, rng
 
 
+@pytest.mark.parametrize("graph", [False, True])
 @pytest.mark.parametrize("j0", [(0, "drag"), (1, "rpy")])
-def test_ensemble_steps_match_each_system_alone(fil, j0):
+def test_ensemble_steps_match_each_system_alone(fil, j0, graph):
     systems = [[16], [20, 33, 7], [30] * 5, [1, 2, 3]]
     p = fo.Params(a=1.0, eta=1.0, dL=2.2, KB=2.0, KT=1.5, dt=0.2, tol=1e-10, max_iter=80)
     states, exts, lays = [], [], []
@@ -90,6 +96,7 @@ def test_ensemble_steps_match_each_system_alone(fil, j0):
         m.set_state(np.concatenate([s.Y for s in states]), np.concatenate([s.q for s in states]))
         m.set_external(np.concatenate([e.Fext for e in exts]), None,
                        np.concatenate([e.follower for e in exts]))
+        m.set_graph(graph)
         S = m.S
         Y = np.zeros((S, 3))
         for step in range(3):
@@ -104,3 +111,28 @@ def test_ensemble_steps_match_each_system_alone(fil, j0):
                 assert finf[k] <= p.tol * p.a
                 off += lay.S
             assert it_all == its.max()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_iterations_reproduce_launched_iterations(fil, prec):
+    """A single system stepped with and without the graph-captured Broyden
+    iteration: bit-identical trajectories and iteration counts."""
+    lay, base, t, mu, xi, rng = _system([20, 30, 12], 5)
+    # FP32 pair sums bound the attainable residual: a looser tolerance for them
+    p = fo.Params(a=1.0, eta=1.0, dL=2.2, KB=2.0, KT=1.5, dt=0.2,
+                  tol=1e-9 if prec == 0 else 1e-6, max_iter=60)
+    st = fo.initial_state(lay, p, base, t, mu, xi)
+    Fext = np.tile([0.0, 0.0, -2.2], (lay.S, 1))
+    out = {}
+    for graph in (False, True):
+        with fil.Filaments(lay.N, a=p.a, eta=p.eta, dL=p.dL, KB=p.KB, KT=p.KT, dt=p.dt,
+                           tol=p.tol, max_iter=p.max_iter, precision=prec, j0_model=1) as m:
+            m.set_state(st.Y, st.q)
+            m.set_external(Fext, None, None)
+            m.set_graph(graph)
+            its = [m.step() for _ in range(4)]
+            Y = np.zeros((lay.S, 3))
+            m.get_state(Y, None, None, None, None)
+            out[graph] = (its, Y)
+    assert out[True][0] == out[False][0]
+    np.testing.assert_array_equal(out[True][1], out[False][1])
