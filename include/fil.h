@@ -51,7 +51,10 @@ typedef enum {
     FIL_ENOCONV = 4,  /* Broyden reached max_iter without ||f||_inf <= tol*a  */
     FIL_ENAN = 5,     /* the residual became NaN or Inf                       */
     FIL_ESTALL = 6,   /* ||f(X_{k+1}) - f(X_k)||_2 = 0: no secant update      */
-    FIL_ESTATE = 7    /* call out of order (e.g. a Broyden step before begin) */
+    FIL_ESTATE = 7,   /* call out of order (e.g. a Broyden step before begin) */
+    FIL_EOVERFLOW = 8 /* a fixed-capacity table overflowed (steric cell grid:
+                         more segments in one cell or within range of one
+                         segment than it holds; the configuration has collapsed) */
 } fil_status;
 
 typedef enum {
@@ -133,6 +136,21 @@ fil_status fil_set_graph(fil_ctx *c, int32_t enable);
  * (sum over each apply of S_s^2 over the systems it evaluated; padding and
  * converged systems excluded). */
 fil_status fil_pair_count(const fil_ctx *c, double *pairs);
+
+/* Steric barrier between segments (Sec. 2.6): a repulsive force
+ *   F^B_nm = FS ((4a^2 chi^2 - r^2) / (4a^2 (chi^2 - 1)))^4 (Y_n - Y_m) / (2a)
+ * on segment n from every segment m of the same system with r = |Y_n - Y_m|
+ * < 2 chi a, except n itself and its neighbours n +- 1 in the same filament,
+ * added to the forces of every residual evaluation (fil_residual, the Broyden
+ * iterations, fil_step). FS = 0 (the default) switches it off; chi > 1. The
+ * first call with FS != 0 allocates a hashed cell grid (2^k >= 2S buckets of
+ * 16 segments, on the device); a residual evaluation whose grid overflows
+ * (more than 16 segments hashed to one bucket, or more than 48 within range
+ * of one segment) returns FIL_EOVERFLOW. Forces are summed per segment in
+ * increasing order of m, so results are reproducible run to run.
+ * FIL_EINVAL for a negative or non-finite FS or chi <= 1; FIL_ESTATE inside
+ * a step. */
+fil_status fil_set_steric(fil_ctx *c, double FS, double chi);
 
 /* Release the context and its device memory (synchronises its stream). */
 void fil_destroy(fil_ctx *c);

@@ -41,7 +41,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.linalg
 
-from . import rpy
+from . import rpy, steric
 
 PI = math.pi
 
@@ -166,6 +166,8 @@ class Params:
     dt: float = 0.01
     tol: float = 1e-8
     max_iter: int = 50
+    FS: float = 0.0       # steric barrier strength (Sec. 2.6); 0: no barrier
+    chi: float = 1.1      # steric range: the barrier acts for r < 2 chi a
 
 
 class Layout:
@@ -340,6 +342,8 @@ def residual(lay: Layout, p: Params, state: State, ext: External | None, X,
     al1, al0, be, ga = scheme(state)
     q, t, Y, u, lam = unpack(lay, p, X, state.q)
     F, T = forces_torques(lay, p, q, t, lam, ext)
+    if p.FS != 0.0:
+        F = F + steric.barrier_forces(lay.N, Y, p.a, p.FS, p.chi)
     V, W = (mob or mobility)(Y, F, T, p, nthreads)
     Yprev = state.Yprev if state.Yprev is not None else np.zeros_like(state.Y)
     uj = state.u if (state.u is not None and ga != 0.0) else np.zeros_like(u)

@@ -20,7 +20,8 @@ using namespace fil;
 
 namespace {
 
-// Device status: int flags[4] ([0] stall |df| = 0, [1] J0 singular), then
+// Device status: int flags[4] ([0] stall |df| = 0, [1] J0 singular, [2] steric
+// cell grid overflow), then
 // the bits of ||f||_inf of every system (atomic max). Read back as:
 struct StatusBlock {
     int flags[4];
@@ -178,6 +179,12 @@ fil_status read_status(fil_ctx *c, StatusBlock *hs, bool active_only = false) {
     CK(cudaStreamSynchronize(c->stream));
     const char *h = reinterpret_cast<const char *>(c->h_pinned);
     std::memcpy(hs->flags, h, 16);
+    if (hs->flags[2]) {
+        CK(cudaMemsetAsync(c->d_flags + 2, 0, sizeof(int), c->stream));
+        return set_err(c, FIL_EOVERFLOW,
+                       "steric barrier: cell grid overflow (too many segments in one bucket or "
+                       "within range of one segment)");
+    }
     c->finf_h.resize(c->n_sys);
     std::memcpy(c->finf_h.data(), h + 16, 8 * (size_t)c->n_sys);
     double m = 0.0;
@@ -195,13 +202,16 @@ fil_status read_status(fil_ctx *c, StatusBlock *hs, bool active_only = false) {
 double finf_of(const StatusBlock &s) { return s.fmax; }
 
 // f(X): unpack + forces (with_forces = 2 also keeps the internal torque for
-// J0), RPY mobility, residual rows, ||f||_inf into the status block.
+// J0), steric barrier, RPY mobility, residual rows, ||f||_inf into the status
+// block.
 // fprev non-null: inside a Broyden iteration of an ensemble, only the
 // systems still iterating are evaluated; the others keep fprev's rows.
 cudaError_t eval_residual(fil_ctx *c, const double *X, double *f, int with_forces,
                           const double *fprev = nullptr) {
     const bool act = fprev != nullptr;
     cudaError_t e = unpack_forces(c, X, with_forces, act);
+    if (e != cudaSuccess) return e;
+    e = steric_forces(c, act);
     if (e != cudaSuccess) return e;
     e = rpy_apply(c, c->Yc, c->FT, c->VW, act);
     if (e != cudaSuccess) return e;
@@ -313,6 +323,8 @@ fil_status fil_create_ensemble(const fil_params *p, int32_t n_sys, const int32_t
 
     auto bail = [&](fil_status s, const char *what, cudaError_t e) {
         if (c->arena) cudaFree(c->arena);
+    if (c->steric_count) cudaFree(c->steric_count);
+    if (c->steric_bucket) cudaFree(c->steric_bucket);
         if (c->h_pinned) cudaFreeHost(c->h_pinned);
         std::fprintf(stderr, "fil_create: %s: %s\n", what, cudaGetErrorString(e));
         delete c;
@@ -400,6 +412,8 @@ void fil_destroy(fil_ctx *c) {
     drop_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->arena) cudaFree(c->arena);
+    if (c->steric_count) cudaFree(c->steric_count);
+    if (c->steric_bucket) cudaFree(c->steric_bucket);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->prof_ev) {
         for (int i = 0; i < 2 * kProfMax; ++i) cudaEventDestroy(c->prof_ev[i]);
@@ -594,6 +608,7 @@ fil_status initial_iterate(fil_ctx *c, bool use_net, double *f0) {
         c->warm_pred += 1;
     } else {
         CK(unpack_forces(c, c->Xk, 2));      // back to the unpack of the extrapolation
+        CK(steric_forces(c));
         c->finf_h = f_ex;
         c->warm_extrap += 1;
     }
@@ -931,6 +946,32 @@ fil_status fil_set_graph(fil_ctx *c, int32_t enable) {
     if (enable && !c->cap_stream)
         CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     c->use_graph = enable ? 1 : 0;
+    return FIL_OK;
+}
+
+fil_status fil_set_steric(fil_ctx *c, double FS, double chi) {
+    if (!c) return FIL_EINVAL;
+    if (!(FS >= 0.0) || !std::isfinite(FS) || !(chi > 1.0) || !std::isfinite(chi))
+        return set_err(c, FIL_EINVAL, "fil_set_steric: need FS >= 0 finite and chi > 1");
+    if (c->in_step) return set_err(c, FIL_ESTATE, "fil_set_steric: a step is in progress");
+    CK(cudaSetDevice(c->device));
+    if (FS != 0.0 && !c->steric_count) {
+        int64_t nb = 1;
+        while (nb < 2 * c->lay.S) nb <<= 1;
+        int *cnt = nullptr, *bkt = nullptr;
+        if (cudaMalloc(&cnt, sizeof(int) * nb) != cudaSuccess ||
+            cudaMalloc(&bkt, sizeof(int) * nb * kStericCap) != cudaSuccess) {
+            cudaGetLastError();
+            if (cnt) cudaFree(cnt);
+            return set_err(c, FIL_ENOMEM, "fil_set_steric: cell grid allocation failed");
+        }
+        c->steric_count = cnt;
+        c->steric_bucket = bkt;
+        c->steric_buckets = nb;
+    }
+    drop_graphs(c);      // captured residual evaluations hold the old setting
+    c->steric_FS = FS;
+    c->steric_chi = chi;
     return FIL_OK;
 }
 

@@ -30,6 +30,8 @@ constexpr int kMaxSegPerFil = (int)(kSolveSmemMax / (6 * sizeof(double)));
 // FP32 inverse: (6N)^2 floats <= 200 KB, i.e. N <= 38; refinement steps per solve.
 constexpr int kMaxDenseSeg = 38;
 constexpr int kJ0Refine = 1;
+constexpr int kStericCap = 16;      // segments per bucket of the steric cell grid
+constexpr int kStericNbrMax = 48;   // segments within range of one segment
 
 struct Layout {
     int M = 0;           // filaments
@@ -159,6 +161,12 @@ struct fil_ctx {
     int warm_from_pred;    // the current step started from the prediction
     int64_t warm_pred, warm_extrap, warm_restart;   // starts from each candidate, restarts
 
+    // steric barrier (fil_set_steric)
+    double steric_FS = 0.0, steric_chi = 1.1;
+    int64_t steric_buckets = 0;    // power of two >= 2S
+    int *steric_count = nullptr;   // [steric_buckets] segments hashed to each bucket
+    int *steric_bucket = nullptr;  // [steric_buckets x kStericCap] their indices
+
     void *arena;           // the single device allocation
     size_t arena_bytes;
 
@@ -183,6 +191,9 @@ size_t rpy_partial_bytes(const fil_ctx *c);
 cudaError_t unpack_forces(fil_ctx *c, const double *X, int with_forces, bool active_only = false);
 // fprev non-null: systems that have converged copy their rows from fprev
 cudaError_t residual_rows(fil_ctx *c, const double *X, double *f, const double *fprev = nullptr);
+// adds the steric barrier forces of the positions Yc to FT (no-op when FS = 0);
+// active_only: segments of converged systems are skipped
+cudaError_t steric_forces(fil_ctx *c, bool active_only = false);
 cudaError_t init_straight(fil_ctx *c, const double *base, const double *t, const double *mu,
                           const double *xi);
 cudaError_t extrapolate_guess(fil_ctx *c, double *X0);

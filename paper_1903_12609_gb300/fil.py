@@ -19,11 +19,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # FIL_LIBRARY may point at another build of the same library (e.g. a tile-shape variant)
 LIB_PATH = os.environ.get("FIL_LIBRARY") or os.path.join(_HERE, "_lib", "libfil.so")
 
-FIL_OK, FIL_EINVAL, FIL_ENOMEM, FIL_ECUDA, FIL_ENOCONV, FIL_ENAN, FIL_ESTALL, FIL_ESTATE = range(8)
+(FIL_OK, FIL_EINVAL, FIL_ENOMEM, FIL_ECUDA, FIL_ENOCONV, FIL_ENAN, FIL_ESTALL, FIL_ESTATE,
+ FIL_EOVERFLOW) = range(9)
 FIL_FP64, FIL_MIXED = 0, 1
 FIL_J0_DRAG, FIL_J0_FILAMENT_RPY = 0, 1
 STATUS_NAMES = {0: "FIL_OK", 1: "FIL_EINVAL", 2: "FIL_ENOMEM", 3: "FIL_ECUDA", 4: "FIL_ENOCONV",
-                5: "FIL_ENAN", 6: "FIL_ESTALL", 7: "FIL_ESTATE"}
+                5: "FIL_ENAN", 6: "FIL_ESTALL", 7: "FIL_ESTATE", 8: "FIL_EOVERFLOW"}
 
 EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set_state",
             "fil_get_state", "fil_init_straight", "fil_set_external", "fil_mobility_apply",
@@ -34,7 +35,7 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_mlp_set_norm", "fil_mlp_forward", "fil_mlp_gradients", "fil_mlp_train_step",
             "fil_tc_gemm_bf16", "fil_warm_features", "fil_warm_targets", "fil_warm_attach",
             "fil_warm_stats", "fil_create_ensemble", "fil_sys_stats", "fil_pair_count",
-            "fil_set_graph", "fil_autotune"]
+            "fil_set_graph", "fil_autotune", "fil_set_steric"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_SEG = 800, 256, 192, 32
 MLP_NPARAM = 256 * 800 + 256 + 2 * (256 * 256 + 256) + 192 * 256 + 192
 FIL_WARM_BEST_OF_TWO, FIL_WARM_PREDICTION_FIRST = 0, 1
@@ -107,6 +108,7 @@ def load_library(path=LIB_PATH):
         "fil_pair_count": [P, D],
         "fil_set_graph": [P, ctypes.c_int32],
         "fil_autotune": [P, ctypes.c_int32, I32, I32, D],
+        "fil_set_steric": [P, ctypes.c_double, ctypes.c_double],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -184,6 +186,10 @@ def fil_autotune(ctx, reps=3):
 
 def fil_set_graph(ctx, enable):
     _check(ctx, _lib.fil_set_graph(ctx, int(bool(enable))))
+
+
+def fil_set_steric(ctx, FS, chi=1.1):
+    _check(ctx, _lib.fil_set_steric(ctx, float(FS), float(chi)))
 
 
 def fil_pair_count(ctx):
