@@ -32,6 +32,19 @@ Readings where the paper is silent (each also listed in the design notes):
 * External forces: a constant force per segment (gravity), a constant torque
   per segment and a follower force -f t_N on the last segment of a filament.
   External loads do not enter J0 (App. B keeps constraint and elastic terms).
+* Tethered filaments (Sec. 5.2.1; eqs. tethering_constraint, tethered_rotation_constraint,
+  tethering_constraint_force_and_torque): Y_1 and u_1 of a tethered filament
+  are prescribed for the step and the X slots that held them carry the two
+  multipliers instead (lambda_1, a force on segment 1, in the Y_1 slot;
+  lambda_2, giving the torque D^T lambda_2 on segment 1, in the u_1 slot); the
+  update equations f^1 and f^2_1 keep their form with the prescribed values
+  substituted. J0 of a tethered filament is the free filament's J0 at the
+  prescribed values with those two column blocks replaced by the derivatives
+  with respect to the multipliers, through the same mobility and the same
+  three-term dexpinv factor A_1 as the other rotation rows. A clamped end is a
+  tether with Y_1 fixed and u_1 = 0. The multipliers are not internal loads:
+  like external loads they stay out of J0's torque value. Their initial guess
+  is extrapolated from past steps like Lambda's.
 """
 from __future__ import annotations
 
@@ -227,6 +240,8 @@ class State:
     steps: int = 0
     u_prev: np.ndarray | None = None
     lam_prev: np.ndarray | None = None
+    tlam: np.ndarray | None = None        # (M, 6) tether multipliers of the last step
+    tlam_prev: np.ndarray | None = None   # (M, 6) of the step before
     extra: dict = field(default_factory=dict)
 
     def copy(self):
@@ -234,7 +249,19 @@ class State:
             return None if a is None else a.copy()
         return State(Y=self.Y.copy(), q=self.q.copy(), Yprev=cp(self.Yprev), u=cp(self.u),
                      lam=cp(self.lam), steps=self.steps, u_prev=cp(self.u_prev),
-                     lam_prev=cp(self.lam_prev))
+                     lam_prev=cp(self.lam_prev), tlam=cp(self.tlam),
+                     tlam_prev=cp(self.tlam_prev))
+
+
+@dataclass
+class Tether:
+    """Prescribed base motion of tethered filaments for one step (eqs.
+    tethering_constraint, tethered_rotation_constraint): where mask[i], Y_1 of
+    filament i is Y1[i] and the rotation of its first segment over the step is
+    u1[i] (q_1 = exp(u1[i]) q_1^j)."""
+    mask: np.ndarray      # (M,) bool
+    Y1: np.ndarray        # (M, 3)
+    u1: np.ndarray        # (M, 3)
 
 
 # --------------------------------------------------------------------------
@@ -266,6 +293,30 @@ def unpack(lay: Layout, p: Params, X, qj):
     t, _, _ = frames(q)
     Y = robot_arm_positions(lay, Y1, t, p.dL)
     return q, t, Y, u, lam
+
+
+def dexpinv_matrix(u):
+    """D with D v = dexpinv_u(v): columns dexpinv_u(e_c)."""
+    return np.stack([dexpinv(u, e) for e in np.eye(3)], axis=1)
+
+
+def tether_resolve(lay: Layout, X, tether: Tether | None):
+    """(Xr, lam1, lam2): X with the Y_1 and u_1 slots of tethered filaments
+    replaced by their prescribed values, and the multipliers read from those
+    slots ((M, 3) each, zero for free filaments)."""
+    Xr = np.array(X, dtype=np.float64)
+    lam1 = np.zeros((lay.M, 3))
+    lam2 = np.zeros((lay.M, 3))
+    if tether is None:
+        return Xr, lam1, lam2
+    for i in range(lay.M):
+        if tether.mask[i]:
+            b = lay.off_X[i]
+            lam1[i] = Xr[b:b + 3]
+            lam2[i] = Xr[b + 3:b + 6]
+            Xr[b:b + 3] = tether.Y1[i]
+            Xr[b + 3:b + 6] = tether.u1[i]
+    return Xr, lam1, lam2
 
 
 # --------------------------------------------------------------------------
@@ -335,13 +386,23 @@ def drag_mobility(Y, F, T, p: Params, nthreads=1):
 
 
 def residual(lay: Layout, p: Params, state: State, ext: External | None, X,
-             nthreads=1, return_parts=False, mob=None):
+             nthreads=1, return_parts=False, mob=None, tether: Tether | None = None):
     """f(X) of eqn (RA-3d-system) (per filament [f^1, f^2_1..N, f^3_2..N]).
 
-    mob replaces the RPY mobility (e.g. by drag_mobility for the f_0 of App. B)."""
+    mob replaces the RPY mobility (e.g. by drag_mobility for the f_0 of App. B).
+    With a tether, tethered filaments take their prescribed Y_1, u_1 and the
+    multiplier loads F_1 += lambda_1, T_1 += D^T lambda_2 (D v =
+    dexpinv_{u_1}(v)), eq. tethering_constraint_force_and_torque."""
     al1, al0, be, ga = scheme(state)
+    X, lam1, lam2 = tether_resolve(lay, X, tether)
     q, t, Y, u, lam = unpack(lay, p, X, state.q)
     F, T = forces_torques(lay, p, q, t, lam, ext)
+    if tether is not None:
+        for i in range(lay.M):
+            if tether.mask[i]:
+                s0 = lay.off_seg[i]
+                F[s0] += lam1[i]
+                T[s0] += dexpinv_matrix(tether.u1[i]).T @ lam2[i]
     if p.FS != 0.0:
         F = F + steric.barrier_forces(lay.N, Y, p.a, p.FS, p.chi)
     V, W = (mob or mobility)(Y, F, T, p, nthreads)
@@ -576,6 +637,48 @@ def jacobian0_general(lay: Layout, p: Params, state: State, X, model="rpy"):
     return blocks
 
 
+def tether_columns(lay: Layout, p: Params, state: State, Xr, tether: Tether, i, model):
+    """The 6N x 6 columns of a tethered filament's J0 for its multipliers
+    (lambda_1, lambda_2), at the resolved unknowns Xr: the loads G = d(F, T)/d
+    lambda (I on F_1, D^T on T_1) through the filament mobility M_f of `model`
+    ('drag': App. B.2's self mobility; 'rpy': the filament's RPY blocks),
+    position rows -b dt (M_f G)_V, rotation rows -b dt A_k (M_f G)_Omega with
+    A_k = I - [u_k x]/2 + [u_k x]^2/12, as the other columns of J0."""
+    _, _, be, _ = scheme(state)
+    bdt = be * p.dt
+    _, _, Y, u, _ = unpack(lay, p, Xr, state.q)
+    n, s0 = lay.N[i], lay.off_seg[i]
+    Mf = filament_mobility(p, Y[s0:s0 + n], model)
+    G = np.zeros((6 * n, 6))
+    G[0:3, 0:3] = np.eye(3)
+    G[3:6, 3:6] = dexpinv_matrix(tether.u1[i]).T
+    MG = Mf @ G
+    cols = np.zeros((6 * n, 6))
+    for k in range(n):
+        prow = 0 if k == 0 else 3 + 3 * n + 3 * (k - 1)
+        rrow = 3 + 3 * k
+        ux = _cross_left(u[s0 + k])
+        A = np.eye(3) - 0.5 * ux + ux @ ux / 12.0
+        cols[prow:prow + 3] = -bdt * MG[6 * k:6 * k + 3]
+        cols[rrow:rrow + 3] = -bdt * A @ MG[6 * k + 3:6 * k + 6]
+    return cols
+
+
+def jacobian0_tethered(lay: Layout, p: Params, state: State, X, tether: Tether | None,
+                       model="drag"):
+    """J0 blocks with tethered filaments: the free J0 (App. B.2 for 'drag', the
+    filament-RPY form otherwise) at the resolved unknowns, the first six
+    columns of each tethered filament's block replaced by tether_columns."""
+    Xr, _, _ = tether_resolve(lay, X, tether)
+    blocks = (jacobian0(lay, p, state, Xr) if model == "drag"
+              else jacobian0_general(lay, p, state, Xr, model))
+    if tether is not None:
+        for i in range(lay.M):
+            if tether.mask[i]:
+                blocks[i][:, 0:6] = tether_columns(lay, p, state, Xr, tether, i, model)
+    return blocks
+
+
 class J0Solver:
     """J0^{-1} v by a dense LU of each filament block (scipy/LAPACK)."""
 
@@ -644,9 +747,11 @@ class Broyden:
 # One BDF2 / Lie-group timestep
 # --------------------------------------------------------------------------
 
-def initial_guess(lay: Layout, state: State):
+def initial_guess(lay: Layout, state: State, tether: Tether | None = None):
     """X_0 of a step: each unknown extrapolated linearly from the two previous
-    steps where both exist (x_0 = 2 x^j - x^{j-1}), else the last value."""
+    steps where both exist (x_0 = 2 x^j - x^{j-1}), else the last value; the
+    multiplier slots of tethered filaments likewise from the multipliers of
+    past steps (zero before the first)."""
     Y1 = np.array([state.Y[lay.off_seg[i]] for i in range(lay.M)])
     if state.Yprev is not None:
         Y1 = 2.0 * Y1 - np.array([state.Yprev[lay.off_seg[i]] for i in range(lay.M)])
@@ -658,47 +763,59 @@ def initial_guess(lay: Layout, state: State):
         lam = 2.0 * state.lam - state.lam_prev if state.lam_prev is not None else state.lam.copy()
     else:
         lam = np.zeros((lay.n_lam, 3))
-    return lay.join_X(Y1, u, lam)
+    X0 = lay.join_X(Y1, u, lam)
+    if tether is not None:
+        if state.tlam is not None:
+            tl = 2.0 * state.tlam - state.tlam_prev if state.tlam_prev is not None else state.tlam
+        else:
+            tl = np.zeros((lay.M, 6))
+        for i in range(lay.M):
+            if tether.mask[i]:
+                X0[lay.off_X[i]:lay.off_X[i] + 6] = tl[i]
+    return X0
 
 
 def begin_step(lay: Layout, p: Params, state: State, ext: External | None, nthreads=1,
-               j0_model="drag"):
+               j0_model="drag", tether: Tether | None = None):
     """Initial guess, J0 at it (LU-factored) and f(X_0): the set-up of Algorithm 2.
 
     j0_model 'drag' is App. B.2 as printed; 'rpy' keeps each filament's own
     RPY blocks in f_0 (see jacobian0_general)."""
-    X0 = initial_guess(lay, state)
-    if j0_model == "drag":
-        blocks = jacobian0(lay, p, state, X0)
-    else:
-        blocks = jacobian0_general(lay, p, state, X0, model=j0_model)
+    X0 = initial_guess(lay, state, tether)
+    blocks = jacobian0_tethered(lay, p, state, X0, tether, j0_model)
     solver = J0Solver(lay, blocks)
 
     def fun(X):
-        return residual(lay, p, state, ext, X, nthreads)
+        return residual(lay, p, state, ext, X, nthreads, tether=tether)
 
     return Broyden(fun, solver.solve, X0, p.tol * p.a)
 
 
-def commit_step(lay: Layout, p: Params, state: State, X):
+def commit_step(lay: Layout, p: Params, state: State, X, tether: Tether | None = None):
     """q^{j+1} = exp(u*) q^j, Y^{j+1} from the robot arm, and the history shift.
-    u^{j-1}, Lambda^{j-1} are kept only when they came from a committed step."""
+    u^{j-1}, Lambda^{j-1} (and the tether multipliers of the step before) are
+    kept only when they came from a committed step."""
+    X, lam1, lam2 = tether_resolve(lay, X, tether)
     q, t, Y, u, lam = unpack(lay, p, X, state.q)
     stepped = state.steps >= 1
+    tlam = np.concatenate([lam1, lam2], axis=1) if tether is not None else None
     return State(Y=Y, q=q, Yprev=state.Y.copy(), u=u, lam=lam, steps=state.steps + 1,
                  u_prev=state.u.copy() if (stepped and state.u is not None) else None,
-                 lam_prev=state.lam.copy() if (stepped and state.lam is not None) else None)
+                 lam_prev=state.lam.copy() if (stepped and state.lam is not None) else None,
+                 tlam=tlam,
+                 tlam_prev=(state.tlam.copy() if (tether is not None and state.tlam is not None)
+                            else None))
 
 
 def step(lay: Layout, p: Params, state: State, ext: External | None, nthreads=1,
-         j0_model="drag"):
+         j0_model="drag", tether: Tether | None = None):
     """One timestep; returns (new_state, iterations)."""
-    br = begin_step(lay, p, state, ext, nthreads, j0_model)
+    br = begin_step(lay, p, state, ext, nthreads, j0_model, tether)
     while not br.converged():
         if br.k >= p.max_iter:
             raise RuntimeError("Broyden did not converge in %d iterations" % p.max_iter)
         br.iterate()
-    return commit_step(lay, p, state, br.X), br.k
+    return commit_step(lay, p, state, br.X, tether), br.k
 
 
 def initial_state(lay: Layout, p: Params, base, t_fil, mu_fil, xi=None, lam=None):
