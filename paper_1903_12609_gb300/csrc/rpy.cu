@@ -417,7 +417,7 @@ __device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
 // (hi, lo) accumulators.
 // ---------------------------------------------------------------------------
 template <int TPT>
-__global__ void __launch_bounds__(kRpyThreads, FIL_RPY_MINB)
+__global__ void __launch_bounds__(kRpyThreads, TPT == 2 ? FIL_RPY_MINB_TPT2 : FIL_RPY_MINB_TPT1)
 rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G, RpyConst32 k,
                   float *__restrict__ part) {
     constexpr int kRec = kRpyPairF4 * (kRpyChunk / 2);   // float4 per chunk

@@ -14,8 +14,14 @@ namespace fil {
 #ifndef FIL_RPY_UNROLL
 #define FIL_RPY_UNROLL 4
 #endif
-#ifndef FIL_RPY_MINB
-#define FIL_RPY_MINB 1
+// Resident CTAs per SM the FP32 pair kernel is compiled for, by targets per
+// thread: caps the registers (65536 / (128 threads x CTAs)) so that this many
+// CTAs fit.
+#ifndef FIL_RPY_MINB_TPT2
+#define FIL_RPY_MINB_TPT2 3
+#endif
+#ifndef FIL_RPY_MINB_TPT1
+#define FIL_RPY_MINB_TPT1 4
 #endif
 // 1: the FP32 pair kernel works on two sources at once with packed FP32x2
 // arithmetic (sm_100 family); 0: one source at a time.
