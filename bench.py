@@ -188,6 +188,8 @@ def run_mobility(args, fil, torch):
     FT = np.random.default_rng(1).standard_normal((S, 6))
     prec = fil.FIL_MIXED if args.precision == "mixed" else fil.FIL_FP64
     m = fil.Filaments(wl.seg_per_fil, precision=prec)
+    m.init_straight(base, t, mu, None)
+    tuned = m.autotune(5) if args.tune else None
     Yd = torch.from_numpy(Y).cuda()
     FTd = torch.from_numpy(FT).cuda()
     VW = torch.empty((S, 6), dtype=torch.float64, device="cuda")
@@ -203,7 +205,8 @@ def run_mobility(args, fil, torch):
     avg = ms / max(n, 1)
     print(json.dumps({"workload": "mobility apply, 32000 segments", "precision": args.precision,
                       "pair_kernel_ms": avg, "pairs_per_s": S * S / (avg * 1e-3),
-                      "tflops": FLOPS_PER_PAIR * S * S / (avg * 1e-3) / 1e12}), flush=True)
+                      "tflops": FLOPS_PER_PAIR * S * S / (avg * 1e-3) / 1e12,
+                      "autotuned": tuned}), flush=True)
 
 
 def run_ensemble(args, fil, torch):
@@ -306,13 +309,20 @@ def main():
                     help="learned warm start of each step (the committed network) and its mode")
     ap.add_argument("--n-sys", type=int, default=256, help="systems of the ensemble workload")
     ap.add_argument("--ens-max-iter", type=int, default=100)
-    ap.add_argument("--tune", type=int, default=1, help="autotune the pair kernel (ensemble)")
+    ap.add_argument("--tune", type=int, default=None,
+                    help="autotune the pair kernel's schedule after the warm-up steps "
+                         "(default: on for the ensemble, off for the single suspension, whose "
+                         "default schedule is the tuned one)")
+    ap.add_argument("--steric", type=float, default=0.0,
+                    help="steric barrier strength F^S (Sec. 2.6, chi = 1.1); 0 = off")
     ap.add_argument("--graph", type=int, default=1,
                     help="run each Broyden iteration as one CUDA graph launch (ensemble)")
     ap.add_argument("--workload", default="suspension",
                     choices=["suspension", "mobility", "ensemble"],
                     help="'mobility': only RPY applies on the 32k configuration (for profiling)")
     args = ap.parse_args()
+    if args.tune is None:
+        args.tune = 1 if args.workload == "ensemble" else 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -355,6 +365,8 @@ def main():
     m = fil.Filaments(wl.seg_per_fil, precision=prec, stream=stream.cuda_stream, **params)
     m.init_straight(base, t, mu, None)
     m.set_external(Fext, None, follower)
+    if args.steric > 0:
+        m.set_steric(args.steric, 1.1)
 
     # learned warm start (chosen form): the committed network, trained on other seeds
     net, warm_mode = None, None
@@ -369,6 +381,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         m.step()
+    tuned = m.autotune(5) if args.tune else None
     st0 = [np.zeros((S, 3)), np.zeros((S, 4)), np.zeros((S, 3)), np.zeros((S, 3)),
            np.zeros((S - n_fil, 3))]
     m.get_state(*st0)
@@ -461,6 +474,8 @@ def main():
                            **params)
         mp.set_state(Yh, qh, Yph, uh, lh)
         mp.set_external(Fext, None, follower)
+        if args.steric > 0:
+            mp.set_steric(args.steric, 1.1)
         barrier()
         pa0, _, _ = mp.counters()
         p0 = torch.cuda.Event(enable_timing=True)
@@ -497,6 +512,7 @@ def main():
             "segments": S, "precision": args.precision, "j0": args.j0,
             "initial_guess": ("learned warm start (%s)" % args.warm) if net is not None
                              else "extrapolation",
+            "steric_FS": args.steric if args.steric > 0 else None,
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "flushed between timed steps (256 MiB write)"},
         "timesteps_per_s": args.steps / (max_ms * 1e-3),
@@ -513,6 +529,8 @@ def main():
                      "avg_launch_ms": pair_avg_ms, "launches": int(n_pair_launch),
                      "share_of_step": pair_ms / dev_ms if dev_ms > 0 else None,
                      "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+        "autotuned": ({"tile": tuned[0], "ctas_per_sm": tuned[1], "ms_per_apply": tuned[2]}
+                      if tuned else None),
         "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
                 "steps": args.e2e_steps},

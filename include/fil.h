@@ -152,6 +152,34 @@ fil_status fil_pair_count(const fil_ctx *c, double *pairs);
  * a step. */
 fil_status fil_set_steric(fil_ctx *c, double FS, double chi);
 
+/* Tethered and clamped filaments (Sec. 5.2.1; eqs. tethering_constraint,
+ * tethered_rotation_constraint, tethering_constraint_force_and_torque).
+ * mask [M] (nonzero: tethered; a null mask unties every filament), Y1 [M x 3]
+ * the base position Y_1 each tethered filament must reach at the end of the
+ * next step, u1 [M x 3] the rotation of its first segment over that step
+ * (q_1 <- exp(u1) q_1^j); host or device arrays, rows of free filaments
+ * ignored. The values persist until the next call: call once for a clamp
+ * (Y1 fixed, u1 = 0), before every step for a moving base (a motor:
+ * Y1 = delta_0 (cos jw dt, sin jw dt, 0), u1 = (0, 0, w dt)).
+ * For a tethered filament the Y_1 slot of X (fil_residual, fil_get_iterate,
+ * fil_j0_solve) holds the multiplier lambda_1, a force on segment 1, and the
+ * u_1 slot lambda_2, which exerts the torque D^T lambda_2 on segment 1
+ * (D v = dexpinv_{u1}(v)); the first segment's update equations are those of
+ * a free filament with Y_1, u_1 substituted. The multipliers' initial guess
+ * is extrapolated from the last two steps; a change of the mask (or
+ * fil_set_state) restarts that history. J0 of a tethered filament is the free
+ * J0 with the six slot columns replaced by the multiplier derivatives (same
+ * mobility model), solved through the free J0 plus a rank-6 correction.
+ * The first call allocates (M x 66 + 13 nX doubles) on the device.
+ * FIL_ESTATE inside a step or with a warm-start network attached
+ * (fil_warm_attach refuses a network while filaments are tethered);
+ * FIL_EINVAL for null Y1 / u1 with a mask. */
+fil_status fil_set_tether(fil_ctx *c, const int32_t *mask, const double *Y1, const double *u1);
+
+/* Multipliers (lambda_1, lambda_2) of every filament from the last committed
+ * step, [M x 6] (zero for free filaments or before any tethered step). */
+fil_status fil_get_tether(fil_ctx *c, double *lam);
+
 /* Release the context and its device memory (synchronises its stream). */
 void fil_destroy(fil_ctx *c);
 

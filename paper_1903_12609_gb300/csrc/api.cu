@@ -206,20 +206,47 @@ double finf_of(const StatusBlock &s) { return s.fmax; }
 // block.
 // fprev non-null: inside a Broyden iteration of an ensemble, only the
 // systems still iterating are evaluated; the others keep fprev's rows.
+// Unpack of X and the loads of the mobility problem: with tethered filaments
+// the unpack runs on X with the prescribed values in the slots (c->txr, also
+// returned in *Xu) and the multipliers join the loads; then the steric barrier.
+cudaError_t unpack_all(fil_ctx *c, const double *X, int with_forces, bool act,
+                       const double **Xu) {
+    *Xu = X;
+    cudaError_t e;
+    if (c->tether_on) {
+        e = tether_resolve(c, X, c->txr);
+        if (e != cudaSuccess) return e;
+        *Xu = c->txr;
+    }
+    e = unpack_forces(c, *Xu, with_forces, act);
+    if (e != cudaSuccess) return e;
+    if (c->tether_on) {
+        e = tether_loads(c, X, act);
+        if (e != cudaSuccess) return e;
+    }
+    return steric_forces(c, act);
+}
+
 cudaError_t eval_residual(fil_ctx *c, const double *X, double *f, int with_forces,
                           const double *fprev = nullptr) {
     const bool act = fprev != nullptr;
-    cudaError_t e = unpack_forces(c, X, with_forces, act);
-    if (e != cudaSuccess) return e;
-    e = steric_forces(c, act);
+    const double *Xu = X;
+    cudaError_t e = unpack_all(c, X, with_forces, act, &Xu);
     if (e != cudaSuccess) return e;
     e = rpy_apply(c, c->Yc, c->FT, c->VW, act);
     if (e != cudaSuccess) return e;
-    return residual_rows(c, X, f, fprev);
+    return residual_rows(c, Xu, f, fprev);
 }
 
-cudaError_t j0_apply(fil_ctx *c, const double *b, double *x) {
+cudaError_t j0_apply_free(fil_ctx *c, const double *b, double *x) {
     return c->j0_model == FIL_J0_DRAG ? j0_solve(c, b, x) : j0_dense_solve(c, b, x);
+}
+
+// J0^{-1} b (tethered filaments: the free solve and the rank-6 correction)
+cudaError_t j0_apply(fil_ctx *c, const double *b, double *x) {
+    cudaError_t e = j0_apply_free(c, b, x);
+    if (e == cudaSuccess && c->tether_on) e = tether_j0_correct(c, x);
+    return e;
 }
 
 }  // namespace
@@ -323,6 +350,7 @@ fil_status fil_create_ensemble(const fil_params *p, int32_t n_sys, const int32_t
 
     auto bail = [&](fil_status s, const char *what, cudaError_t e) {
         if (c->arena) cudaFree(c->arena);
+    if (c->tether_mem) cudaFree(c->tether_mem);
     if (c->steric_count) cudaFree(c->steric_count);
     if (c->steric_bucket) cudaFree(c->steric_bucket);
         if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -412,6 +440,7 @@ void fil_destroy(fil_ctx *c) {
     drop_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->arena) cudaFree(c->arena);
+    if (c->tether_mem) cudaFree(c->tether_mem);
     if (c->steric_count) cudaFree(c->steric_count);
     if (c->steric_bucket) cudaFree(c->steric_bucket);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -459,6 +488,7 @@ fil_status fil_set_state(fil_ctx *c, const double *Y, const double *q, const dou
     CK(cudaStreamSynchronize(c->stream));
     c->have_prev = Yprev ? 1 : 0;
     c->hist = 0;
+    c->thist = 0;
     c->warm_corr_ok = 0;
     c->in_step = 0;
     return FIL_OK;
@@ -607,8 +637,8 @@ fil_status initial_iterate(fil_ctx *c, bool use_net, double *f0) {
         c->warm_from_pred = 1;
         c->warm_pred += 1;
     } else {
-        CK(unpack_forces(c, c->Xk, 2));      // back to the unpack of the extrapolation
-        CK(steric_forces(c));
+        const double *Xu;
+        CK(unpack_all(c, c->Xk, 2, false, &Xu));   // back to the unpack of the extrapolation
         c->finf_h = f_ex;
         c->warm_extrap += 1;
     }
@@ -706,10 +736,16 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net) {
     fil_status s = initial_iterate(c, use_net, &f0);
     if (s != FIL_OK) return s;
     const std::vector<double> f0_sys = c->finf_h;
+    const double *Xj = c->Xk;
+    if (c->tether_on) {
+        CK(tether_resolve(c, c->Xk, c->txr));
+        Xj = c->txr;
+    }
     if (c->j0_model == FIL_J0_DRAG)
-        CK(j0_build_factor(c, c->Xk));
+        CK(j0_build_factor(c, Xj));
     else
-        CK(j0_dense_build_factor(c, c->Xk));
+        CK(j0_dense_build_factor(c, Xj));
+    if (c->tether_on) CK(tether_j0_setup(c, j0_apply_free));
     StatusBlock sb;
     s = read_status(c, &sb);
     if (s != FIL_OK) return s;
@@ -844,7 +880,13 @@ fil_status fil_broyden_commit(fil_ctx *c) {
     if (!c) return FIL_EINVAL;
     if (!c->in_step) return set_err(c, FIL_ESTATE, "fil_broyden_commit: no step in progress");
     CK(cudaSetDevice(c->device));
-    CK(commit_state(c, c->Xk));
+    const double *Xc = c->Xk;
+    if (c->tether_on) {
+        CK(tether_record(c, c->Xk));
+        CK(tether_resolve(c, c->Xk, c->txr));
+        Xc = c->txr;
+    }
+    CK(commit_state(c, Xc));
     CK(warm_record_correction(c));
     c->warm_corr_ok = 1;
     c->have_prev = 1;
@@ -909,6 +951,8 @@ fil_status fil_warm_attach(fil_ctx *c, fil_mlp *net, int32_t mode) {
         return set_err(c, FIL_EINVAL, "fil_warm_attach: the network's max_batch is below n_fil");
     if (mode != FIL_WARM_BEST_OF_TWO && mode != FIL_WARM_PREDICTION_FIRST)
         return set_err(c, FIL_EINVAL, "fil_warm_attach: unknown mode");
+    if (net && c->tether_on)
+        return set_err(c, FIL_ESTATE, "fil_warm_attach: not with tethered filaments");
     c->warm_net = net;
     c->warm_mode = mode;
     return FIL_OK;
@@ -949,6 +993,86 @@ fil_status fil_set_graph(fil_ctx *c, int32_t enable) {
     return FIL_OK;
 }
 
+fil_status fil_set_tether(fil_ctx *c, const int32_t *mask, const double *Y1, const double *u1) {
+    if (!c) return FIL_EINVAL;
+    if (c->in_step) return set_err(c, FIL_ESTATE, "fil_set_tether: a step is in progress");
+    CK(cudaSetDevice(c->device));
+    const int M = c->lay.M;
+    if (!mask) {
+        if (c->tether_on) drop_graphs(c);
+        c->tether_on = 0;
+        c->thist = 0;
+        return FIL_OK;
+    }
+    if (!Y1 || !u1) return set_err(c, FIL_EINVAL, "fil_set_tether: Y1 and u1 are required");
+    if (c->warm_net)
+        return set_err(c, FIL_ESTATE, "fil_set_tether: detach the warm-start network first");
+    // the mask as host ints (the argument may be a device array)
+    std::vector<int32_t> hm(M);
+    CK(cudaMemcpy(hm.data(), mask, sizeof(int32_t) * M, cudaMemcpyDefault));
+    int any = 0;
+    for (int i = 0; i < M; ++i) {
+        hm[i] = hm[i] != 0;
+        any |= hm[i];
+    }
+    if (!c->tether_mem) {
+        const int64_t nX = c->lay.nX;
+        const size_t doubles = (size_t)M * (3 + 3 + 6 + 6 + 36 + 6) + (size_t)nX * (1 + 6 + 6);
+        void *mem = nullptr;
+        if (cudaMalloc(&mem, doubles * sizeof(double) + sizeof(int) * (size_t)M) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, FIL_ENOMEM, "fil_set_tether: allocation failed");
+        }
+        double *d = static_cast<double *>(mem);
+        c->tY1 = d; d += 3 * (size_t)M;
+        c->tu1 = d; d += 3 * (size_t)M;
+        c->tlam = d; d += 6 * (size_t)M;
+        c->tlam_prev = d; d += 6 * (size_t)M;
+        c->tCinv = d; d += 36 * (size_t)M;
+        c->tw = d; d += 6 * (size_t)M;
+        c->txr = d; d += nX;
+        c->tU = d; d += 6 * (size_t)nX;
+        c->tZ = d; d += 6 * (size_t)nX;
+        c->tmask = reinterpret_cast<int *>(d);
+        c->tether_mem = mem;
+        CK(cudaMemsetAsync(c->tmask, 0, sizeof(int) * M, c->stream));
+    }
+    // a changed mask starts the multipliers' history afresh
+    std::vector<int> old(M, 0);
+    if (c->tether_on) {
+        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaMemcpy(old.data(), c->tmask, sizeof(int) * M, cudaMemcpyDeviceToHost));
+    }
+    bool changed = !c->tether_on;
+    for (int i = 0; i < M; ++i) changed |= old[i] != hm[i];
+    CK(cudaMemcpyAsync(c->tmask, hm.data(), sizeof(int) * M, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->tY1, Y1, sizeof(double) * 3 * M, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(c->tu1, u1, sizeof(double) * 3 * M, cudaMemcpyDefault, c->stream));
+    if (changed) {
+        CK(cudaMemsetAsync(c->tlam, 0, sizeof(double) * 6 * M, c->stream));
+        CK(cudaMemsetAsync(c->tlam_prev, 0, sizeof(double) * 6 * M, c->stream));
+        c->thist = 0;
+        drop_graphs(c);
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    c->tether_on = any;
+    return FIL_OK;
+}
+
+fil_status fil_get_tether(fil_ctx *c, double *lam) {
+    if (!c || !lam) return FIL_EINVAL;
+    CK(cudaSetDevice(c->device));
+    const size_t bytes = sizeof(double) * 6 * c->lay.M;
+    if (!c->tether_mem) {
+        if (is_device_ptr(lam)) CK(cudaMemsetAsync(lam, 0, bytes, c->stream));
+        else std::memset(lam, 0, bytes);
+    } else {
+        CK(cudaMemcpyAsync(lam, c->tlam, bytes, cudaMemcpyDefault, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return FIL_OK;
+}
+
 fil_status fil_set_steric(fil_ctx *c, double FS, double chi) {
     if (!c) return FIL_EINVAL;
     if (!(FS >= 0.0) || !std::isfinite(FS) || !(chi > 1.0) || !std::isfinite(chi))
@@ -959,14 +1083,18 @@ fil_status fil_set_steric(fil_ctx *c, double FS, double chi) {
         int64_t nb = 1;
         while (nb < 2 * c->lay.S) nb <<= 1;
         int *cnt = nullptr, *bkt = nullptr;
+        const size_t table = sizeof(int) * (size_t)nb * kStericCap;   // a multiple of 16 bytes
+        const size_t per_seg = (sizeof(int4) + sizeof(float4)) * (size_t)c->lay.S;
         if (cudaMalloc(&cnt, sizeof(int) * nb) != cudaSuccess ||
-            cudaMalloc(&bkt, sizeof(int) * nb * kStericCap) != cudaSuccess) {
+            cudaMalloc(&bkt, table + per_seg) != cudaSuccess) {
             cudaGetLastError();
             if (cnt) cudaFree(cnt);
             return set_err(c, FIL_ENOMEM, "fil_set_steric: cell grid allocation failed");
         }
         c->steric_count = cnt;
         c->steric_bucket = bkt;
+        c->steric_cell = reinterpret_cast<int4 *>(reinterpret_cast<char *>(bkt) + table);
+        c->steric_frac = reinterpret_cast<float4 *>(c->steric_cell + c->lay.S);
         c->steric_buckets = nb;
     }
     drop_graphs(c);      // captured residual evaluations hold the old setting

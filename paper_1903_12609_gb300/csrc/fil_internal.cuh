@@ -166,6 +166,23 @@ struct fil_ctx {
     int64_t steric_buckets = 0;    // power of two >= 2S
     int *steric_count = nullptr;   // [steric_buckets] segments hashed to each bucket
     int *steric_bucket = nullptr;  // [steric_buckets x kStericCap] their indices
+    int4 *steric_cell = nullptr;   // [S] cell (ix, iy, iz) and system of each segment
+    float4 *steric_frac = nullptr; // [S] position within its cell, FP32
+
+    // tethered filaments (fil_set_tether)
+    int tether_on = 0;             // some filament is tethered
+    int *tmask = nullptr;          // [M] tethered
+    double *tY1 = nullptr;         // [M x 3] prescribed base position of the step
+    double *tu1 = nullptr;         // [M x 3] prescribed rotation of the first segment
+    double *tlam = nullptr;        // [M x 6] multipliers of the last committed step
+    double *tlam_prev = nullptr;   // [M x 6] of the step before
+    int thist = 0;                 // committed steps behind tlam / tlam_prev (0..2)
+    double *txr = nullptr;         // [nX] X with the prescribed values in the slots
+    double *tU = nullptr;          // [6 x nX] multiplier columns of J0
+    double *tZ = nullptr;          // [6 x nX] J0_free^{-1} of them
+    double *tCinv = nullptr;       // [M x 36] inverse capacitance matrices
+    double *tw = nullptr;          // [M x 6] weights of the current solve
+    void *tether_mem = nullptr;    // the allocation holding the arrays above
 
     void *arena;           // the single device allocation
     size_t arena_bytes;
@@ -194,6 +211,14 @@ cudaError_t residual_rows(fil_ctx *c, const double *X, double *f, const double *
 // adds the steric barrier forces of the positions Yc to FT (no-op when FS = 0);
 // active_only: segments of converged systems are skipped
 cudaError_t steric_forces(fil_ctx *c, bool active_only = false);
+// tethered filaments (tether.cu)
+cudaError_t tether_resolve(fil_ctx *c, const double *X, double *Xr);   // slots <- prescribed
+cudaError_t tether_loads(fil_ctx *c, const double *X, bool active_only);   // FT += multipliers
+cudaError_t tether_guess(fil_ctx *c, double *X0);                     // multiplier slots of X0
+cudaError_t tether_record(fil_ctx *c, const double *X);               // history shift
+cudaError_t tether_j0_setup(fil_ctx *c,
+                            cudaError_t (*free_solve)(fil_ctx *, const double *, double *));
+cudaError_t tether_j0_correct(fil_ctx *c, double *x);                 // Woodbury correction
 cudaError_t init_straight(fil_ctx *c, const double *base, const double *t, const double *mu,
                           const double *xi);
 cudaError_t extrapolate_guess(fil_ctx *c, double *X0);

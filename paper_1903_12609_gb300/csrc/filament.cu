@@ -332,7 +332,9 @@ cudaError_t extrapolate_guess(fil_ctx *c, double *X0) {
         c->lay, c->Y, c->Yprev, c->uprev, c->lam, c->uprev2, c->lamprev, c->have_prev,
         c->hist >= 2 ? 1 : 0, X0);
     c->n_launches += 1;
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && c->tether_on) e = tether_guess(c, X0);
+    return e;
 }
 
 cudaError_t commit_state(fil_ctx *c, const double *X) {

@@ -35,7 +35,8 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_mlp_set_norm", "fil_mlp_forward", "fil_mlp_gradients", "fil_mlp_train_step",
             "fil_tc_gemm_bf16", "fil_warm_features", "fil_warm_targets", "fil_warm_attach",
             "fil_warm_stats", "fil_create_ensemble", "fil_sys_stats", "fil_pair_count",
-            "fil_set_graph", "fil_autotune", "fil_set_steric"]
+            "fil_set_graph", "fil_autotune", "fil_set_steric", "fil_set_tether",
+            "fil_get_tether"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_SEG = 800, 256, 192, 32
 MLP_NPARAM = 256 * 800 + 256 + 2 * (256 * 256 + 256) + 192 * 256 + 192
 FIL_WARM_BEST_OF_TWO, FIL_WARM_PREDICTION_FIRST = 0, 1
@@ -109,6 +110,8 @@ def load_library(path=LIB_PATH):
         "fil_set_graph": [P, ctypes.c_int32],
         "fil_autotune": [P, ctypes.c_int32, I32, I32, D],
         "fil_set_steric": [P, ctypes.c_double, ctypes.c_double],
+        "fil_set_tether": [P, P, P, P],
+        "fil_get_tether": [P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -190,6 +193,19 @@ def fil_set_graph(ctx, enable):
 
 def fil_set_steric(ctx, FS, chi=1.1):
     _check(ctx, _lib.fil_set_steric(ctx, float(FS), float(chi)))
+
+
+def fil_set_tether(ctx, mask, Y1=None, u1=None):
+    """mask: sequence of M flags (None unties every filament); Y1, u1: (M, 3)."""
+    if mask is None:
+        _check(ctx, _lib.fil_set_tether(ctx, None, None, None))
+        return
+    m = np.ascontiguousarray(np.asarray(mask).astype(np.int32))
+    _check(ctx, _lib.fil_set_tether(ctx, _ptr(m, "int32"), _ptr(Y1), _ptr(u1)))
+
+
+def fil_get_tether(ctx, lam):
+    _check(ctx, _lib.fil_get_tether(ctx, _ptr(lam)))
 
 
 def fil_pair_count(ctx):
