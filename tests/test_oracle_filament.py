@@ -13,7 +13,9 @@
 * Algorithm 2's limited-memory iterates equal the textbook dense bad-Broyden
   update, and a linear problem with J0 = J converges in one iteration,
 * a converged timestep equals a finite-difference Newton solve,
-* quaternions stay unit across steps (multiplicative update, Sec. 2.9.3).
+* quaternions stay unit across steps (multiplicative update, Sec. 2.9.3),
+* BDF2 converges at second order in time on the settling-square problem of
+  Sec. 4.2 (scaled down), measured against a run with a 32 times smaller step.
 """
 import math
 
@@ -340,3 +342,33 @@ def test_filament_rpy_J0_cuts_broyden_iterations():
     s_rpy, it_rpy = fo.step(lay, p, st, ext, j0_model="rpy")
     assert it_rpy < it_drag
     np.testing.assert_allclose(s_rpy.Y, s_drag.Y, rtol=0, atol=1e-8)
+
+
+def _settling_square(N, n_steps, tf_over_T, tol=1e-12):
+    """Sec. 4.2's 3D test, scaled down: four straight vertical filaments at the
+    corners of a horizontal square of side 0.268 L (as in Sec. 5.4.3), B = 1000,
+    settling for tf under gravity; returns the final positions."""
+    from paper_1903_12609_gb300.inputs import workload_params
+    wl = workload_params(4, N, B=1000.0, dt_over_T=tf_over_T / n_steps, tol=tol)
+    D = 0.268 * wl.extra["L"]
+    base = np.array([[0, 0, 0], [D, 0, 0], [0, D, 0], [D, D, 0]], dtype=float)
+    lay = fo.Layout([N] * 4)
+    p = fo.Params(a=wl.a, eta=wl.eta, dL=wl.dL, KB=wl.KB, KT=wl.KT, dt=wl.dt, tol=wl.tol,
+                  max_iter=100)
+    st = fo.initial_state(lay, p, base, np.tile([0.0, 0.0, 1.0], (4, 1)),
+                          np.tile([1.0, 0.0, 0.0], (4, 1)))
+    ext = fo.External(Fext=np.tile([0.0, 0.0, -wl.W * wl.dL], (lay.S, 1)))
+    for _ in range(n_steps):
+        st, _ = fo.step(lay, p, st, ext)
+    return st.Y
+
+
+@pytest.mark.slow
+def test_bdf2_converges_at_second_order_in_time():
+    """Maximum position error at t = T/2 for dt = T/20, T/40, T/80 against
+    dt = T/640: halving dt divides it by ~4 (the backward-Euler first step
+    contributes one O(dt^2) local error only)."""
+    ref = _settling_square(8, 320, 0.5)
+    err = [np.linalg.norm(_settling_square(8, n, 0.5) - ref, axis=1).max() for n in (10, 20, 40)]
+    assert 3.6 < err[0] / err[1] < 4.4, err
+    assert 3.6 < err[1] / err[2] < 4.4, err
