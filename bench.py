@@ -315,8 +315,10 @@ def main():
                          "default schedule is the tuned one)")
     ap.add_argument("--steric", type=float, default=0.0,
                     help="steric barrier strength F^S (Sec. 2.6, chi = 1.1); 0 = off")
-    ap.add_argument("--graph", type=int, default=1,
-                    help="run each Broyden iteration as one CUDA graph launch (ensemble)")
+    ap.add_argument("--graph", type=int, default=0,
+                    help="run each Broyden iteration as one CUDA graph launch (ensemble; off by "
+                         "default: with kernels of 0.05-0.7 ms the launches are not the cost and "
+                         "the graph's speculative last iteration is)")
     ap.add_argument("--workload", default="suspension",
                     choices=["suspension", "mobility", "ensemble"],
                     help="'mobility': only RPY applies on the 32k configuration (for profiling)")

@@ -127,9 +127,10 @@ fil_status fil_autotune(fil_ctx *c, int32_t reps, int32_t *tile, int32_t *ctas_p
 /* Run each Broyden iteration of fil_broyden_step / fil_step as one CUDA graph
  * launch (enable = 1) instead of separate kernel launches: the graph holds the
  * update of X, the residual of the new iterate, the dot products, the J0 solve
- * and the history update, captured once per buffer parity (again whenever an
- * ensemble's set of iterating systems changes). Same results. Not with
- * fil_profile on. FIL_ESTATE inside a step. */
+ * and the history update, captured once per buffer parity at the start of a
+ * step (an ensemble's set of iterating systems and its list of RPY tiles are
+ * read from device memory, so the graphs stay valid as systems converge).
+ * Same results. Not with fil_profile on. FIL_ESTATE inside a step. */
 fil_status fil_set_graph(fil_ctx *c, int32_t enable);
 
 /* RPY pair interactions evaluated by this context's mobility applies so far

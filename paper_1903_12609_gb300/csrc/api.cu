@@ -104,6 +104,7 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->act_src_d = ar.take<int64_t>(c->rpy_tiles_max);
     c->act_tile_d = ar.take<int>(c->rpy_tiles_max);
     c->act_slot_d = ar.take<int>(c->Spad / kRpyThreads);
+    c->act_dyn_d = ar.take<int64_t>(2);
     c->pos_of_seg_d = ar.take<int64_t>(S);
     c->pad_map_d = ar.take<int>(c->Spad);
     c->Y = ar.take<double>(3 * S);
@@ -150,12 +151,14 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->d_finf = sb ? reinterpret_cast<unsigned long long *>(sb + 16) : nullptr;
     if (c->j0_model == FIL_J0_DRAG) {
         c->band = ar.take<double>((size_t)nband * kBandW);
+        c->band32 = c->prec == FIL_MIXED ? ar.take<float>((size_t)nband * kBandW) : nullptr;
         c->jinv = nullptr;
         c->jofs = nullptr;
         c->aux = nullptr;
         c->auxofs = nullptr;
     } else {
         c->band = nullptr;
+        c->band32 = nullptr;
         c->jinv = ar.take<float>((size_t)c->jdense_len);
         c->jofs = ar.take<int64_t>(M + 1);
         c->aux = ar.take<double>((size_t)c->aux_len);
@@ -242,9 +245,13 @@ cudaError_t j0_apply_free(fil_ctx *c, const double *b, double *x) {
     return c->j0_model == FIL_J0_DRAG ? j0_solve(c, b, x) : j0_dense_solve(c, b, x);
 }
 
-// J0^{-1} b (tethered filaments: the free solve and the rank-6 correction)
-cudaError_t j0_apply(fil_ctx *c, const double *b, double *x) {
-    cudaError_t e = j0_apply_free(c, b, x);
+// J0^{-1} b (tethered filaments: the free solve and the rank-6 correction).
+// active_only: inside the Broyden iterations of an ensemble, the rows of
+// converged systems are not computed (the caller masks or ignores them).
+cudaError_t j0_apply(fil_ctx *c, const double *b, double *x, bool active_only = false) {
+    const int *act = active_only && c->n_sys > 1 ? c->d_active : nullptr;
+    cudaError_t e = c->j0_model == FIL_J0_DRAG ? j0_solve(c, b, x, act)
+                                               : j0_dense_solve(c, b, x, act);
     if (e == cudaSuccess && c->tether_on) e = tether_j0_correct(c, x);
     return e;
 }
@@ -681,7 +688,7 @@ cudaError_t iteration_body(fil_ctx *c) {
     cudaError_t e = broyden_axpy_step(c);
     if (e == cudaSuccess) e = eval_residual(c, c->Xn, c->fn, 1, c->n_sys > 1 ? c->fk : nullptr);
     if (e == cudaSuccess) e = broyden_dots(c);
-    if (e == cudaSuccess) e = j0_apply(c, c->fn, c->g);
+    if (e == cudaSuccess) e = j0_apply(c, c->fn, c->g, true);
     if (e == cudaSuccess) e = broyden_update(c);
     return e;
 }
@@ -765,7 +772,7 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net) {
     if (!c->conv) {
         CK(upload_active(c));
         if (c->n_sys > 1) CK(rpy_set_active(c));
-        CK(j0_apply(c, c->fk, c->w));
+        CK(j0_apply(c, c->fk, c->w, true));
         CK(broyden_mask_inactive(c, c->w));
     }
     c->in_step = 1;
@@ -790,7 +797,8 @@ fil_status fil_broyden_step(fil_ctx *c, int32_t *converged, double *finf) {
         CK(cudaGraphLaunch(c->graph_exec[slot], c->stream));
         c->n_launches += c->graph_launches[slot];
         c->n_applies += c->graph_applies[slot];
-        c->n_pairs += c->graph_pairs[slot];
+        // the pairs of the systems active now (the captured count may be stale)
+        c->n_pairs += c->graph_applies[slot] * (c->n_sys > 1 ? c->pairs_act : c->pairs_all);
         StatusBlock sb;
         fil_status s = read_status(c, &sb);
         if (s != FIL_OK) return s;
@@ -808,10 +816,11 @@ fil_status fil_broyden_step(fil_ctx *c, int32_t *converged, double *finf) {
         }
         if (sb.flags[0]) return set_err(c, FIL_ESTALL, "Broyden: ||df|| = 0 (stalled)");
         if (c->n_sys > 1 && c->active_h != c->active_prev_h) {
+            // the graph reads the active set and the active-tile list from the
+            // device: rewriting them keeps it valid
             CK(upload_active(c));
             CK(broyden_mask_inactive(c, c->w));
             CK(rpy_set_active(c));
-            drop_graphs(c);
         }
         std::swap(c->Xk, c->Xn);
         std::swap(c->fk, c->fn);
@@ -842,7 +851,7 @@ fil_status fil_broyden_step(fil_ctx *c, int32_t *converged, double *finf) {
         CK(rpy_set_active(c));
     }
     CK(broyden_dots(c));
-    CK(j0_apply(c, c->fn, c->g));
+    CK(j0_apply(c, c->fn, c->g, true));
     CK(broyden_update(c));
     std::swap(c->Xk, c->Xn);
     std::swap(c->fk, c->fn);

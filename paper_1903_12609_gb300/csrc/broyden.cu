@@ -78,8 +78,10 @@ __device__ __forceinline__ void dots_group(const double *__restrict__ D, int64_t
 __global__ void dots_partial_kernel(int64_t n, const double *__restrict__ fn,
                                     const double *__restrict__ fk, const double *__restrict__ D,
                                     const int *__restrict__ dk, const int64_t *__restrict__ blk_beg,
-                                    double *__restrict__ part) {
+                                    const int *__restrict__ blk_sys,
+                                    const int *__restrict__ active, double *__restrict__ part) {
     __shared__ double sh[kDotGroup * 32];
+    if (active && !active[blk_sys[blockIdx.x]]) return;   // a converged system: not needed
     const int k = *dk;
     const int nb = gridDim.x;
     const int64_t i0 = blk_beg[blockIdx.x], i1 = blk_beg[blockIdx.x + 1];
@@ -122,7 +124,12 @@ __global__ void dots_final_kernel(int n_sys, int max_out, const int *__restrict_
     for (int b = sys_blk[sy] + lane; b < sys_blk[sy + 1]; b += 32) s += part[(int64_t)o * nblocks + b];
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
-    if (lane == 0) out[(int64_t)sy * sstride + o] = s;
+    if (lane == 0) {
+        out[(int64_t)sy * sstride + o] = s;
+        // |df|^2: also 1/|df| in slot k + 2 (free until the next iteration), so
+        // that the update multiplies instead of dividing in every entry
+        if (o == *dk) out[(int64_t)sy * sstride + o + 2] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    }
 }
 
 // g += sum_i c_i alpha_i; history pair k; w = g + c_k (df . fn)/|df|, with the
@@ -147,12 +154,12 @@ __global__ void update_kernel(int64_t n, const int *__restrict__ dk,
     if (!(ndf2 > 0.0)) flags[0] = 1;
     double gi = g[i];
     for (int l = 0; l < k; ++l) gi += C[(int64_t)l * n + i] * scal[l];
-    const double ndf = sqrt(ndf2);
-    const double c = -gi / ndf;
-    const double d = (fn[i] - fk[i]) / ndf;
+    const double indf = scal[k + 2];            // 1/|df|
+    const double c = -gi * indf;
+    const double d = (fn[i] - fk[i]) * indf;
     C[(int64_t)k * n + i] = c;
     D[(int64_t)k * n + i] = d;
-    w[i] = gi + c * (scal[k + 1] / ndf);
+    w[i] = gi + c * (scal[k + 1] * indf);
 }
 
 __global__ void k_advance_kernel(int *dk) { *dk += 1; }
@@ -183,8 +190,9 @@ cudaError_t broyden_axpy_step(fil_ctx *c) {
 
 cudaError_t broyden_dots(fil_ctx *c) {
     const int64_t n = c->lay.nX;
-    dots_partial_kernel<<<c->red_blocks, kRedThreads, 0, c->stream>>>(n, c->fn, c->fk, c->D, c->d_k,
-                                                                       c->blk_beg, c->red_part);
+    dots_partial_kernel<<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+        n, c->fn, c->fk, c->D, c->d_k, c->blk_beg, c->blk_sys,
+        c->n_sys > 1 ? c->d_active : nullptr, c->red_part);
     const int max_out = c->max_iter + 2;
     const int64_t jobs = (int64_t)c->n_sys * max_out;
     dots_final_kernel<<<(unsigned)((jobs + 7) / 8), 256, 0, c->stream>>>(

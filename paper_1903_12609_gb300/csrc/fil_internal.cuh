@@ -100,6 +100,7 @@ struct fil_ctx {
     double n_pairs;                // pairs evaluated by all applies so far
     int64_t *act_unit_off_d, *act_src_d;
     int *act_tile_d, *act_slot_d;
+    int64_t *act_dyn_d;    // {act_tiles, act_units} on the device
 
     // Broyden state
     double *Xk, *fk, *Xn, *fn, *w, *g, *C, *D;
@@ -136,6 +137,7 @@ struct fil_ctx {
     // (filament RPY mobility); piv holds 6S pivots (band rows use 6S - 3M)
     int j0_model;
     double *band;
+    float *band32;         // FP32 copy of the band, factored in place (mixed precision)
     int *piv;
     float *jinv;           // per filament: FP32 J0, then its inverse in place
     int64_t *jofs;         // [M+1] offsets of the (6N)^2 blocks
@@ -225,9 +227,12 @@ cudaError_t extrapolate_guess(fil_ctx *c, double *X0);
 cudaError_t commit_state(fil_ctx *c, const double *X);
 
 cudaError_t j0_build_factor(fil_ctx *c, const double *X);
-cudaError_t j0_solve(fil_ctx *c, const double *b, double *x);
+// active non-null: filaments of converged systems are skipped (their rows of x
+// are left as they were)
+cudaError_t j0_solve(fil_ctx *c, const double *b, double *x, const int *active = nullptr);
 cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X);
-cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x);
+cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x,
+                           const int *active = nullptr);
 
 cudaError_t broyden_axpy_step(fil_ctx *c);                 // Xn = Xk - w
 cudaError_t broyden_dots(fil_ctx *c);                      // alpha_i, ndf2, dff

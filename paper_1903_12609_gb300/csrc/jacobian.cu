@@ -105,8 +105,10 @@ __global__ void j0_build_kernel(Layout lay, const double *__restrict__ X,
     }
 }
 
-// In-place banded LU with partial pivoting (one warp per filament).
-__global__ void band_lu_kernel(Layout lay, double *__restrict__ band_all, int *__restrict__ piv_all,
+// In-place banded LU with partial pivoting (one warp per filament), in the
+// precision T of the stored factors.
+template <typename T>
+__global__ void band_lu_kernel(Layout lay, T *__restrict__ band_all, int *__restrict__ piv_all,
                                int *__restrict__ flags) {
     const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -115,13 +117,13 @@ __global__ void band_lu_kernel(Layout lay, double *__restrict__ band_all, int *_
     const int N = lay.off[warp + 1] - s0;
     const int n = 6 * N - 3;
     const int64_t row0 = 6 * (int64_t)s0 - 3 * (int64_t)warp;
-    double *A = band_all + row0 * kBandW;
+    T *A = band_all + row0 * kBandW;
     int *piv = piv_all + row0;
 #define BAND(i, c) A[(int64_t)(i) * kBandW + ((c) - (i) + kBandKL)]
     for (int j = 0; j < n; ++j) {
         const int last = min(n - 1, j + kBandKL);
         // pivot: first row of maximal |A(i, j)|, i in [j, last]
-        double v = -1.0;
+        T v = T(-1);
         int idx = j;
         if (j + lane <= last && lane <= kBandKL) {
             v = fabs(BAND(j + lane, j));
@@ -129,7 +131,7 @@ __global__ void band_lu_kernel(Layout lay, double *__restrict__ band_all, int *_
         }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, v, d);
+            const T ov = __shfl_down_sync(0xffffffffu, v, d);
             const int oi = __shfl_down_sync(0xffffffffu, idx, d);
             if (ov > v || (ov == v && oi < idx)) {
                 v = ov;
@@ -137,24 +139,24 @@ __global__ void band_lu_kernel(Layout lay, double *__restrict__ band_all, int *_
             }
         }
         const int p = __shfl_sync(0xffffffffu, idx, 0);
-        const double pv = __shfl_sync(0xffffffffu, v, 0);
+        const T pv = __shfl_sync(0xffffffffu, v, 0);
         if (lane == 0) piv[j] = p;
         const int cmax = min(n - 1, j + kBandKL + kBandKU);
         if (p != j) {
             const int c = j + lane;
             if (c <= cmax) {
-                const double t = BAND(j, c);
+                const T t = BAND(j, c);
                 BAND(j, c) = BAND(p, c);
                 BAND(p, c) = t;
             }
         }
         __syncwarp();
-        if (pv == 0.0) {
+        if (pv == T(0)) {
             if (lane == 0) atomicOr(flags + 1, 1);
             continue;
         }
-        const double inv = 1.0 / BAND(j, j);
-        double l = 0.0;
+        const T inv = T(1) / BAND(j, j);
+        T l = T(0);
         if (lane >= 1 && j + lane <= last) {
             l = BAND(j + lane, j) * inv;
             BAND(j + lane, j) = l;
@@ -169,29 +171,33 @@ __global__ void band_lu_kernel(Layout lay, double *__restrict__ band_all, int *_
         }
         __syncwarp();
     }
-    // the solves multiply by the reciprocal pivots (FP64 division is slow here)
+    // the solves multiply by the reciprocal pivots (division is slow)
     for (int j = lane; j < n; j += 32) {
-        const double d = BAND(j, j);
-        BAND(j, j) = d != 0.0 ? 1.0 / d : 0.0;
+        const T d = BAND(j, j);
+        BAND(j, j) = d != T(0) ? T(1) / d : T(0);
     }
 #undef BAND
 }
 
-// x = J0^{-1} b for every filament (b and x in the X / f layout; may alias).
-__global__ void band_solve_kernel(Layout lay, const double *__restrict__ band_all,
+// x = J0^{-1} b for every filament (b and x in the X / f layout; may alias),
+// with the factors and the working vector in precision T.
+template <typename T>
+__global__ void band_solve_kernel(Layout lay, const T *__restrict__ band_all,
                                   const int *__restrict__ piv_all, double ct,
-                                  const double *b, double *x, int zmax) {
-    extern __shared__ double zs[];
+                                  const double *b, double *x, int zmax,
+                                  const int *__restrict__ active) {
+    extern __shared__ __align__(16) unsigned char zraw[];
     const int wib = threadIdx.x >> 5;
     const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= lay.M) return;
-    double *z = zs + (int64_t)wib * zmax;
+    T *z = reinterpret_cast<T *>(zraw) + (int64_t)wib * zmax;
     const int s0 = lay.off[warp];
+    if (active && !active[lay.sys_of[s0]]) return;   // converged system: rows not needed
     const int N = lay.off[warp + 1] - s0;
     const int n = 6 * N - 3;
     const int64_t row0 = 6 * (int64_t)s0 - 3 * (int64_t)warp;
-    const double *A = band_all + row0 * kBandW;
+    const T *A = band_all + row0 * kBandW;
     const int *piv = piv_all + row0;
     const double *bf = b + 6 * (int64_t)s0;
     double *xf = x + 6 * (int64_t)s0;
@@ -199,11 +205,11 @@ __global__ void band_solve_kernel(Layout lay, const double *__restrict__ band_al
     // gather the right-hand side in band order
     for (int e = lane; e < 3 * N; e += 32) {
         const int s = e / 3, r = e % 3;
-        z[6 * s + r] = bf[3 + 3 * s + r];   // rotation rows of segment s
+        z[6 * s + r] = (T)bf[3 + 3 * s + r];   // rotation rows of segment s
         if (s <= N - 2) {
             const double b3n = bf[3 + 3 * N + 3 * s + r];                      // f3 of segment s+1
             const double b3p = (s == 0) ? bf[r] : bf[3 + 3 * N + 3 * (s - 1) + r];
-            z[6 * s + 3 + r] = b3n - b3p;
+            z[6 * s + 3 + r] = (T)(b3n - b3p);
         }
     }
     const double b1x = bf[0], b1y = bf[1], b1z = bf[2];
@@ -212,12 +218,12 @@ __global__ void band_solve_kernel(Layout lay, const double *__restrict__ band_al
     for (int j = 0; j < n; ++j) {
         const int p = piv[j];
         if (p != j && lane == 0) {
-            const double t = z[j];
+            const T t = z[j];
             z[j] = z[p];
             z[p] = t;
         }
         __syncwarp();
-        const double zj = z[j];
+        const T zj = z[j];
         const int i = j + 1 + lane;
         if (lane < kBandKL && i < n) z[i] -= BAND(i, j) * zj;
         __syncwarp();
@@ -225,7 +231,7 @@ __global__ void band_solve_kernel(Layout lay, const double *__restrict__ band_al
     // backward, column by column: z_j *= 1/U_jj (stored reciprocal), then the
     // kl + ku rows above take their U_ij z_j; two FP64 instructions per column
     for (int j = n - 1; j >= 0; --j) {
-        const double zj = z[j] * BAND(j, j);
+        const T zj = z[j] * BAND(j, j);
         __syncwarp();                       // every lane has read z_j
         const int i = j - 1 - lane;
         if (lane < kBandKL + kBandKU && i >= 0) z[i] -= BAND(i, j) * zj;
@@ -235,17 +241,22 @@ __global__ void band_solve_kernel(Layout lay, const double *__restrict__ band_al
     // scatter back: u_s, Lam_j, and Y_1 = b1 + c_t Lam_0
     for (int e = lane; e < 3 * N; e += 32) {
         const int s = e / 3, r = e % 3;
-        xf[3 + 3 * s + r] = z[6 * s + r];
-        if (s <= N - 2) xf[3 + 3 * N + 3 * s + r] = z[6 * s + 3 + r];
+        xf[3 + 3 * s + r] = (double)z[6 * s + r];
+        if (s <= N - 2) xf[3 + 3 * N + 3 * s + r] = (double)z[6 * s + 3 + r];
     }
     if (lane == 0) {
-        const double l0 = (N >= 2) ? z[3] : 0.0, l1 = (N >= 2) ? z[4] : 0.0,
-                     l2 = (N >= 2) ? z[5] : 0.0;
+        const double l0 = (N >= 2) ? (double)z[3] : 0.0, l1 = (N >= 2) ? (double)z[4] : 0.0,
+                     l2 = (N >= 2) ? (double)z[5] : 0.0;
         xf[0] = b1x + ct * l0;
         xf[1] = b1y + ct * l1;
         xf[2] = b1z + ct * l2;
     }
 #undef BAND
+}
+
+__global__ void to_float_kernel(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
 }
 
 constexpr int kJ0Threads = 128;
@@ -263,12 +274,25 @@ cudaError_t j0_build_factor(fil_ctx *c, const double *X) {
     const unsigned grid = (unsigned)(((int64_t)c->lay.M * 32 + kJ0Threads - 1) / kJ0Threads);
     const J0Params p = make_params(c);
     j0_build_kernel<<<grid, kJ0Threads, 0, c->stream>>>(c->lay, X, c->qc, c->Tint, p, c->band);
-    band_lu_kernel<<<grid, kJ0Threads, 0, c->stream>>>(c->lay, c->band, c->piv, c->d_flags);
-    c->n_launches += 2;
+    if (c->band32) {
+        // mixed precision: factors and solves in FP32 (J0 is an approximation of
+        // the Jacobian far coarser than FP32 rounding; FP64 issues at 1/64 of the
+        // FP32 rate on this GPU)
+        const int64_t ne = (6 * c->lay.S - 3 * (int64_t)c->lay.M) * kBandW;
+        to_float_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>(ne, c->band,
+                                                                            c->band32);
+        band_lu_kernel<float><<<grid, kJ0Threads, 0, c->stream>>>(c->lay, c->band32, c->piv,
+                                                                  c->d_flags);
+        c->n_launches += 3;
+    } else {
+        band_lu_kernel<double><<<grid, kJ0Threads, 0, c->stream>>>(c->lay, c->band, c->piv,
+                                                                   c->d_flags);
+        c->n_launches += 2;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t j0_solve(fil_ctx *c, const double *b, double *x) {
+cudaError_t j0_solve(fil_ctx *c, const double *b, double *x, const int *active) {
     // one warp per filament; up to 4 warps per CTA, fewer for long filaments so
     // that each warp's right-hand side fits in shared memory
     const int zmax = 6 * c->lay.maxN;
@@ -277,15 +301,22 @@ cudaError_t j0_solve(fil_ctx *c, const double *b, double *x) {
     if (warps < 1) return cudaErrorInvalidValue;
     const size_t smem = warps * per_warp;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(band_solve_kernel,
+        cudaError_t e = cudaFuncSetAttribute(band_solve_kernel<double>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(band_solve_kernel<float>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const int threads = 32 * warps;
     const unsigned grid = (unsigned)(((int64_t)c->lay.M * 32 + threads - 1) / threads);
-    band_solve_kernel<<<grid, threads, smem, c->stream>>>(c->lay, c->band, c->piv,
-                                                          make_params(c).ct, b, x, zmax);
+    if (c->band32)
+        band_solve_kernel<float><<<grid, threads, smem, c->stream>>>(
+            c->lay, c->band32, c->piv, make_params(c).ct, b, x, zmax, active);
+    else
+        band_solve_kernel<double><<<grid, threads, smem, c->stream>>>(
+            c->lay, c->band, c->piv, make_params(c).ct, b, x, zmax, active);
     c->n_launches += 1;
     return cudaGetLastError();
 }

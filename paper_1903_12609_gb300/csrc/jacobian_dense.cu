@@ -26,11 +26,13 @@
 //      written into the inverse buffer and inverted there in FP32 by
 //      Gauss-Jordan elimination (FP32 runs at 64x the FP64 rate on this part).
 // A solve (j0_solve_fused_kernel, one CTA per filament, the FP32 inverse
-// staged in shared memory once) applies the inverse and then kJ0Refine steps
-// of iterative refinement x += Inv (b - J0 x), with b - J0 x evaluated
-// matrix-free in FP64 from the aux block -- the same operator as the dense
-// definition -- so x reaches FP64 accuracy (each step multiplies the error by
-// ~cond(J0) * 2^-24).
+// staged in shared memory once) applies the inverse and then, in FP64 mode,
+// kJ0Refine steps of iterative refinement x += Inv (b - J0 x), with b - J0 x
+// evaluated matrix-free in FP64 from the aux block -- the same operator as the
+// dense definition -- so x reaches FP64 accuracy (each step multiplies the
+// error by ~cond(J0) * 2^-24). In mixed mode (FP32 pair sums, Broyden
+// tolerances of ~1e-4) the FP32 solve (relative error ~1e-7, far below the
+// error of J0 as an approximation of the Jacobian) is used as it is.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -427,9 +429,9 @@ __device__ __forceinline__ void inv_gemv_cta(const float *Inv, const float *r, d
     }
 }
 
-// Refined J0 solve, one CTA per filament with its FP32 inverse staged in
-// shared memory once:  x = Inv b;  kJ0Refine times { r = b - J0 x (FP64,
-// matrix-free); x += Inv r }.  b and x may alias.
+// J0 solve, one CTA per filament with its FP32 inverse staged in shared
+// memory once:  x = Inv b;  `refine` times { r = b - J0 x (FP64, matrix-free);
+// x += Inv r }.  b and x may alias.
 constexpr int kSolveThreads = 512;
 // shared memory of the largest solve: inverse, b, x, FT, VW, Y, r
 static_assert(36 * kMaxDenseSeg * kMaxDenseSeg * 4 + (12 * kMaxDenseSeg + 15 * kMaxDenseSeg) * 8 +
@@ -440,10 +442,12 @@ __global__ void __launch_bounds__(kSolveThreads)
 j0_solve_fused_kernel(Layout lay, const int64_t *__restrict__ jofs,
                       const int64_t *__restrict__ auxofs, DenseParams dp,
                       const double *__restrict__ aux_all, const float *__restrict__ inv_all,
-                      const double *b, double *x) {
+                      const double *b, double *x, const int *__restrict__ active,
+                      int refine) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int f = blockIdx.x;
     const int s0 = lay.off[f];
+    if (active && !active[lay.sys_of[s0]]) return;   // converged system: rows not needed
     const int N = lay.off[f + 1] - s0;
     const int n = 6 * N;
     float *Inv = reinterpret_cast<float *>(smraw);                  // n^2 (144 N^2 bytes)
@@ -465,7 +469,7 @@ j0_solve_fused_kernel(Layout lay, const int64_t *__restrict__ jofs,
     __syncthreads();
     inv_gemv_cta(Inv, rs, xs, n, false);
     __syncthreads();
-    for (int it = 0; it < kJ0Refine; ++it) {
+    for (int it = 0; it < refine; ++it) {
         residual_mf_cta(g, N, dp, xs, bs, rs, FT, VW, Ys);
         inv_gemv_cta(Inv, rs, xs, n, true);
         __syncthreads();
@@ -814,7 +818,7 @@ size_t j0_solve_smem(int maxN) {
     return n * n * sizeof(float) + (2 * n + 15 * (size_t)maxN) * sizeof(double) + n * sizeof(float);
 }
 
-cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x) {
+cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x, const int *active) {
     DenseParams dp;
     dp.jp = J0Params{c->dL, c->KB, c->KT, c->g0, c->kmu, c->knu, 0.0, 0.0};
     dp.bdt = c->j0_dp_bdt;
@@ -826,7 +830,8 @@ cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     j0_solve_fused_kernel<<<c->lay.M, kSolveThreads, smem, c->stream>>>(
-        c->lay, c->jofs, c->auxofs, dp, c->aux, c->jinv, b, x);
+        c->lay, c->jofs, c->auxofs, dp, c->aux, c->jinv, b, x, active,
+        c->prec == FIL_MIXED ? 0 : kJ0Refine);
     c->n_launches += 1;
     return cudaGetLastError();
 }

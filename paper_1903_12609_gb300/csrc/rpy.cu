@@ -106,7 +106,18 @@ struct SysMap {
     const int64_t *pos_of_seg;     // [S] padded position of each segment
     const int *pad_map;            // [Spad] segment at a padded position, or -1
     int64_t n_tiles, n_chunks;     // listed tiles; n_chunks: the one-system case
+    // non-null: {listed tiles, work units} read on the device, so that a captured
+    // launch stays valid when the list of active tiles is rewritten
+    const int64_t *dyn = nullptr;
 };
+
+// The listed tiles and the unit count of a launch (from the device when dynamic).
+__device__ __forceinline__ void resolve_dyn(SysMap &m, int64_t &W) {
+    if (m.dyn) {
+        m.n_tiles = m.dyn[0];
+        W = m.dyn[1];
+    }
+}
 
 __device__ __forceinline__ int64_t tile_unit_begin(const SysMap &m, int64_t tile) {
     return m.tile_unit_off ? m.tile_unit_off[tile] : tile * m.n_chunks;
@@ -426,6 +437,7 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
     __shared__ float4 sm[2][kRec];
     const int tid = threadIdx.x;
     const int64_t b = blockIdx.x;
+    resolve_dyn(smap, W);
     int64_t u = unit_start(b, W, G);
     const int64_t u_end = unit_start(b + 1, W, G);
 
@@ -605,6 +617,7 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
     __shared__ double sm[2][kRec];
     const int tid = threadIdx.x;
     const int64_t b = blockIdx.x;
+    resolve_dyn(smap, W);
     int64_t u = unit_start(b, W, G);
     const int64_t u_end = unit_start(b + 1, W, G);
 
@@ -681,7 +694,8 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
 __device__ __forceinline__ void cta_range_of_tile(const SysMap &sm, int64_t tile, int64_t W,
                                                   int64_t G, int64_t &b0, int64_t &b1) {
     // CTA b owns units [floor(bW/G), floor((b+1)W/G)); the CTA that holds unit
-    // u is ceil((u+1)G/W) - 1.
+    // u is ceil((u+1)G/W) - 1. With G > W (a fixed grid over a short active
+    // list) CTAs between two owners may own nothing: the reduce skips them.
     const int64_t u0 = tile_unit_begin(sm, tile);
     const int64_t u1 = tile_unit_begin(sm, tile + 1) - 1;
     b0 = ((u0 + 1) * G + W - 1) / W - 1;
@@ -691,6 +705,7 @@ __device__ __forceinline__ void cta_range_of_tile(const SysMap &sm, int64_t tile
 __global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, SysMap sm,
                                     int64_t W, int G, int T, double scale,
                                     double *__restrict__ VW) {
+    resolve_dyn(sm, W);
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= S) return;
     const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
@@ -704,6 +719,7 @@ __global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, S
     cta_range_of_tile(sm, tile, W, G, b0, b1);
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t b = b0; b <= b1; ++b) {
+        if (unit_start(b + 1, W, G) == unit_start(b, W, G)) continue;   // a CTA with no unit
         const float *p = part + (size_t)(b + tile) * 12 * T;
 #pragma unroll
         for (int c = 0; c < 6; ++c)
@@ -716,6 +732,7 @@ __global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, S
 __global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, SysMap sm,
                                     int64_t W, int G, int T, double scale,
                                     double *__restrict__ VW) {
+    resolve_dyn(sm, W);
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= S) return;
     const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
@@ -729,6 +746,7 @@ __global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, 
     cta_range_of_tile(sm, tile, W, G, b0, b1);
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t b = b0; b <= b1; ++b) {
+        if (unit_start(b + 1, W, G) == unit_start(b, W, G)) continue;   // a CTA with no unit
         const double *p = part + (size_t)(b + tile) * 6 * T;
 #pragma unroll
         for (int c = 0; c < 6; ++c) acc[c] += p[c * T + local];
@@ -748,6 +766,7 @@ SysMap sys_map(const fil_ctx *c, bool active_only) {
         m.tile_id = c->act_tile_d;
         m.slot_of = c->act_slot_d;
         m.n_tiles = c->act_tiles;
+        m.dyn = c->act_dyn_d;
     } else {
         m.tile_unit_off = c->tile_unit_off_d;
         m.tile_src = c->tile_src_d;
@@ -914,6 +933,9 @@ cudaError_t rpy_set_active(fil_ctx *c) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->act_slot_d, slot.data(), sizeof(int) * slot.size(),
                             cudaMemcpyHostToDevice, c->stream);
+    const int64_t dyn[2] = {c->act_tiles, c->act_units};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->act_dyn_d, dyn, sizeof(dyn), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // host vectors go out of scope
     return e;
 }
@@ -930,8 +952,10 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
     const int64_t W = active_only ? c->act_units : c->rpy_units;
     if (W == 0) return cudaSuccess;
     const int T = kRpyThreads * c->rpy_tpt;
+    // the active-tile list changes between applies: its launches keep a fixed grid
+    // (and read the unit count from the device), so captured graphs stay valid
     if (c->prec == FIL_MIXED) {
-        const int G = (int)std::min<int64_t>(c->rpy_grid32, W);
+        const int G = (int)(active_only ? c->rpy_grid32 : std::min<int64_t>(c->rpy_grid32, W));
         pack32_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, sm, c->src32);
         if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
         const RpyConst32 k = make_const<float, RpyConst32>(c->a);
@@ -945,7 +969,7 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
         rpy_reduce32_kernel<<<rgrid, pb, 0, c->stream>>>((const float *)c->partials, S, sm, W, G,
                                                          T, scale, VW);
     } else {
-        const int G = (int)std::min<int64_t>(c->rpy_grid64, W);
+        const int G = (int)(active_only ? c->rpy_grid64 : std::min<int64_t>(c->rpy_grid64, W));
         pack64_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, sm, c->src64);
         if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
         const RpyConst64 k = make_const<double, RpyConst64>(c->a);
