@@ -722,7 +722,6 @@ cudaError_t graph_for_current(fil_ctx *c, int *slot) {
     // the counters advanced during capture; each launch adds them instead
     c->graph_launches[i] = c->n_launches - l0;
     c->graph_applies[i] = c->n_applies - a0;
-    c->graph_pairs[i] = c->n_pairs - p0;
     c->n_launches = l0;
     c->n_applies = a0;
     c->n_pairs = p0;

@@ -128,7 +128,6 @@ struct fil_ctx {
     cudaGraphExec_t graph_exec[2];
     const double *graph_xk[2];
     int64_t graph_launches[2], graph_applies[2];
-    double graph_pairs[2];
     int in_step;           // a step was begun and not committed
     int iters_step;        // Broyden iterations of the current step
     int conv;              // current iterate satisfies ||f||_inf <= tol * a

@@ -429,6 +429,26 @@ __device__ __forceinline__ void inv_gemv_cta(const float *Inv, const float *r, d
     }
 }
 
+// x = Inv b without refinement (the mixed mode): the inverse is read once, so it
+// is streamed from global memory instead of being staged in shared memory, and
+// small CTAs keep many rows in flight per SM. Same summation order as the first
+// product of the fused solve. b and x may alias.
+constexpr int kApplyThreads = 256;
+__global__ void __launch_bounds__(kApplyThreads)
+j0_apply_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
+                        const float *__restrict__ inv_all, const double *b, double *x,
+                        const int *__restrict__ active) {
+    __shared__ float rs[6 * kMaxDenseSeg];
+    const int f = blockIdx.x;
+    const int s0 = lay.off[f];
+    if (active && !active[lay.sys_of[s0]]) return;   // converged system: rows not needed
+    const int n = 6 * (lay.off[f + 1] - s0);
+    const double *bg = b + 6 * (int64_t)s0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = (float)bg[i];
+    __syncthreads();
+    inv_gemv_cta(inv_all + jofs[f], rs, x + 6 * (int64_t)s0, n, false);
+}
+
 // J0 solve, one CTA per filament with its FP32 inverse staged in shared
 // memory once:  x = Inv b;  `refine` times { r = b - J0 x (FP64, matrix-free);
 // x += Inv r }.  b and x may alias.
@@ -819,6 +839,12 @@ size_t j0_solve_smem(int maxN) {
 }
 
 cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x, const int *active) {
+    if (c->prec == FIL_MIXED) {
+        j0_apply_inverse_kernel<<<c->lay.M, kApplyThreads, 0, c->stream>>>(c->lay, c->jofs,
+                                                                          c->jinv, b, x, active);
+        c->n_launches += 1;
+        return cudaGetLastError();
+    }
     DenseParams dp;
     dp.jp = J0Params{c->dL, c->KB, c->KT, c->g0, c->kmu, c->knu, 0.0, 0.0};
     dp.bdt = c->j0_dp_bdt;
@@ -831,7 +857,7 @@ cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x, const int *ac
     if (e != cudaSuccess) return e;
     j0_solve_fused_kernel<<<c->lay.M, kSolveThreads, smem, c->stream>>>(
         c->lay, c->jofs, c->auxofs, dp, c->aux, c->jinv, b, x, active,
-        c->prec == FIL_MIXED ? 0 : kJ0Refine);
+        kJ0Refine);
     c->n_launches += 1;
     return cudaGetLastError();
 }

@@ -12,13 +12,13 @@ namespace fil {
 #define FIL_RPY_TPT 2
 #endif
 #ifndef FIL_RPY_UNROLL
-#define FIL_RPY_UNROLL 4
+#define FIL_RPY_UNROLL 8
 #endif
 // Resident CTAs per SM the FP32 pair kernel is compiled for, by targets per
 // thread: caps the registers (65536 / (128 threads x CTAs)) so that this many
 // CTAs fit.
 #ifndef FIL_RPY_MINB_TPT2
-#define FIL_RPY_MINB_TPT2 3
+#define FIL_RPY_MINB_TPT2 4
 #endif
 #ifndef FIL_RPY_MINB_TPT1
 #define FIL_RPY_MINB_TPT1 4
