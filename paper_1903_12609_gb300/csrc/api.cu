@@ -137,9 +137,19 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->fn = ar.take<double>(nX);
     c->w = ar.take<double>(nX);
     c->g = ar.take<double>(nX);
-    c->C = ar.take<double>((size_t)c->max_iter * nX);
-    c->D = ar.take<double>((size_t)c->max_iter * nX);
+    if (c->prec == FIL_MIXED) {
+        // mixed mode: the Broyden history in FP32 (half the bytes; its sums then
+        // need no FP64 work per history vector)
+        c->C32 = ar.take<float>((size_t)c->max_iter * nX);
+        c->D32 = ar.take<float>((size_t)c->max_iter * nX);
+        c->C = c->D = nullptr;
+    } else {
+        c->C = ar.take<double>((size_t)c->max_iter * nX);
+        c->D = ar.take<double>((size_t)c->max_iter * nX);
+        c->C32 = c->D32 = nullptr;
+    }
     c->scal = ar.take<double>((size_t)c->n_sys * c->sstride);
+    c->scal32 = ar.take<float>((size_t)c->n_sys * c->sstride);
     c->red_part = ar.take<double>((size_t)(c->max_iter + 2) * red_blocks);
     c->blk_sys = ar.take<int>(red_blocks);
     c->blk_beg = ar.take<int64_t>(red_blocks + 1);

@@ -54,29 +54,36 @@ __device__ __forceinline__ void block_reduce_write(double (&acc)[G], double *sh,
 }
 
 // d_{o0+j} . fn for j < G over [i0, i1)
-template <int G>
-__device__ __forceinline__ void dots_group(const double *__restrict__ D, int64_t n, int o0,
+// (H = float: the mixed mode's FP32 history, products and the per-thread
+// partial sums in FP32, the block sums in FP64)
+template <int G, typename H>
+__device__ __forceinline__ void dots_group(const H *__restrict__ D, int64_t n, int o0,
                                            const double *__restrict__ fn, int64_t i0, int64_t i1,
                                            double *sh, int nb, double *part) {
-    double acc[G];
+    H acc[G];
 #pragma unroll
-    for (int j = 0; j < G; ++j) acc[j] = 0.0;
+    for (int j = 0; j < G; ++j) acc[j] = H(0);
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const double f = fn[i];
+        const H f = (H)fn[i];
 #pragma unroll
         for (int j = 0; j < G; ++j) acc[j] = fma(D[(int64_t)(o0 + j) * n + i], f, acc[j]);
     }
+    double accd[G];
     int o[G];
 #pragma unroll
-    for (int j = 0; j < G; ++j) o[j] = o0 + j;
-    block_reduce_write<G>(acc, sh, o, nb, part);
+    for (int j = 0; j < G; ++j) {
+        accd[j] = (double)acc[j];
+        o[j] = o0 + j;
+    }
+    block_reduce_write<G>(accd, sh, o, nb, part);
 }
 
 // Outputs o = 0..k-1: d_o . fn;  o = k: |fn - fk|^2;  o = k+1: (fn - fk) . fn,
 // over the X slice [blk_beg[b], blk_beg[b+1]) of block b. Outputs are taken
 // in compile-time groups so that every FP64 instruction is useful work.
+template <typename H>
 __global__ void dots_partial_kernel(int64_t n, const double *__restrict__ fn,
-                                    const double *__restrict__ fk, const double *__restrict__ D,
+                                    const double *__restrict__ fk, const H *__restrict__ D,
                                     const int *__restrict__ dk, const int64_t *__restrict__ blk_beg,
                                     const int *__restrict__ blk_sys,
                                     const int *__restrict__ active, double *__restrict__ part) {
@@ -98,22 +105,23 @@ __global__ void dots_partial_kernel(int64_t n, const double *__restrict__ fn,
     }
     int o0 = 0;
     for (; o0 + kDotGroup <= k; o0 += kDotGroup)
-        dots_group<kDotGroup>(D, n, o0, fn, i0, i1, sh, nb, part);
+        dots_group<kDotGroup, H>(D, n, o0, fn, i0, i1, sh, nb, part);
     switch (k - o0) {
-        case 1: dots_group<1>(D, n, o0, fn, i0, i1, sh, nb, part); break;
-        case 2: dots_group<2>(D, n, o0, fn, i0, i1, sh, nb, part); break;
-        case 3: dots_group<3>(D, n, o0, fn, i0, i1, sh, nb, part); break;
-        case 4: dots_group<4>(D, n, o0, fn, i0, i1, sh, nb, part); break;
-        case 5: dots_group<5>(D, n, o0, fn, i0, i1, sh, nb, part); break;
-        case 6: dots_group<6>(D, n, o0, fn, i0, i1, sh, nb, part); break;
-        case 7: dots_group<7>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 1: dots_group<1, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 2: dots_group<2, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 3: dots_group<3, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 4: dots_group<4, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 5: dots_group<5, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 6: dots_group<6, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
+        case 7: dots_group<7, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
         default: break;
     }
 }
 
 __global__ void dots_final_kernel(int n_sys, int max_out, const int *__restrict__ dk, int nblocks,
                                   const int *__restrict__ sys_blk, const double *__restrict__ part,
-                                  int sstride, double *__restrict__ out) {
+                                  int sstride, double *__restrict__ out,
+                                  float *__restrict__ out32) {
     // one warp per (system, output), lanes stride the system's partials, fixed-order tree
     const int64_t job = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -126,6 +134,7 @@ __global__ void dots_final_kernel(int n_sys, int max_out, const int *__restrict_
     for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
     if (lane == 0) {
         out[(int64_t)sy * sstride + o] = s;
+        if (out32) out32[(int64_t)sy * sstride + o] = (float)s;   // for the FP32 history sums
         // |df|^2: also 1/|df| in slot k + 2 (free until the next iteration), so
         // that the update multiplies instead of dividing in every entry
         if (o == *dk) out[(int64_t)sy * sstride + o + 2] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
@@ -134,12 +143,13 @@ __global__ void dots_final_kernel(int n_sys, int max_out, const int *__restrict_
 
 // g += sum_i c_i alpha_i; history pair k; w = g + c_k (df . fn)/|df|, with the
 // scalars of entry i's system; w = 0 in systems that have converged.
+template <typename H>
 __global__ void update_kernel(int64_t n, const int *__restrict__ dk,
-                              const double *__restrict__ scal_all, int sstride,
-                              const int *__restrict__ sys_of, const int *__restrict__ active,
-                              const double *__restrict__ fn, const double *__restrict__ fk,
-                              double *__restrict__ g, double *__restrict__ C,
-                              double *__restrict__ D, double *__restrict__ w,
+                              const double *__restrict__ scal_all, const float *__restrict__ scal32,
+                              int sstride, const int *__restrict__ sys_of,
+                              const int *__restrict__ active, const double *__restrict__ fn,
+                              const double *__restrict__ fk, double *__restrict__ g,
+                              H *__restrict__ C, H *__restrict__ D, double *__restrict__ w,
                               int *__restrict__ flags) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -153,12 +163,20 @@ __global__ void update_kernel(int64_t n, const int *__restrict__ dk,
     const double ndf2 = scal[k];
     if (!(ndf2 > 0.0)) flags[0] = 1;
     double gi = g[i];
-    for (int l = 0; l < k; ++l) gi += C[(int64_t)l * n + i] * scal[l];
+    if (sizeof(H) == sizeof(double)) {
+        for (int l = 0; l < k; ++l) gi += (double)C[(int64_t)l * n + i] * scal[l];
+    } else {
+        // the history sum in FP32 (mixed mode), added to g once
+        const float *sc32 = scal32 + (int64_t)sy * sstride;
+        float h = 0.f;
+        for (int l = 0; l < k; ++l) h = fmaf((float)C[(int64_t)l * n + i], sc32[l], h);
+        gi += (double)h;
+    }
     const double indf = scal[k + 2];            // 1/|df|
     const double c = -gi * indf;
     const double d = (fn[i] - fk[i]) * indf;
-    C[(int64_t)k * n + i] = c;
-    D[(int64_t)k * n + i] = d;
+    C[(int64_t)k * n + i] = (H)c;
+    D[(int64_t)k * n + i] = (H)d;
     w[i] = gi + c * (scal[k + 1] * indf);
 }
 
@@ -190,22 +208,34 @@ cudaError_t broyden_axpy_step(fil_ctx *c) {
 
 cudaError_t broyden_dots(fil_ctx *c) {
     const int64_t n = c->lay.nX;
-    dots_partial_kernel<<<c->red_blocks, kRedThreads, 0, c->stream>>>(
-        n, c->fn, c->fk, c->D, c->d_k, c->blk_beg, c->blk_sys,
-        c->n_sys > 1 ? c->d_active : nullptr, c->red_part);
+    if (c->C32)
+        dots_partial_kernel<float><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+            n, c->fn, c->fk, c->D32, c->d_k, c->blk_beg, c->blk_sys,
+            c->n_sys > 1 ? c->d_active : nullptr, c->red_part);
+    else
+        dots_partial_kernel<double><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+            n, c->fn, c->fk, c->D, c->d_k, c->blk_beg, c->blk_sys,
+            c->n_sys > 1 ? c->d_active : nullptr, c->red_part);
     const int max_out = c->max_iter + 2;
     const int64_t jobs = (int64_t)c->n_sys * max_out;
     dots_final_kernel<<<(unsigned)((jobs + 7) / 8), 256, 0, c->stream>>>(
-        c->n_sys, max_out, c->d_k, c->red_blocks, c->sys_blk_off, c->red_part, c->sstride, c->scal);
+        c->n_sys, max_out, c->d_k, c->red_blocks, c->sys_blk_off, c->red_part, c->sstride, c->scal,
+        c->C32 ? c->scal32 : nullptr);
     c->n_launches += 2;
     return cudaGetLastError();
 }
 
 cudaError_t broyden_update(fil_ctx *c) {
     const int64_t n = c->lay.nX;
-    update_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
-        n, c->d_k, c->scal, c->sstride, c->lay.sys_of, c->d_active, c->fn, c->fk, c->g, c->C, c->D,
-        c->w, c->d_flags);
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (c->C32)
+        update_kernel<float><<<grid, 256, 0, c->stream>>>(
+            n, c->d_k, c->scal, c->scal32, c->sstride, c->lay.sys_of, c->d_active, c->fn, c->fk,
+            c->g, c->C32, c->D32, c->w, c->d_flags);
+    else
+        update_kernel<double><<<grid, 256, 0, c->stream>>>(
+            n, c->d_k, c->scal, nullptr, c->sstride, c->lay.sys_of, c->d_active, c->fn, c->fk,
+            c->g, c->C, c->D, c->w, c->d_flags);
     k_advance_kernel<<<1, 1, 0, c->stream>>>(c->d_k);     // the next history slot
     c->n_launches += 2;
     return cudaGetLastError();

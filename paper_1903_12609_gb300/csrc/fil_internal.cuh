@@ -105,6 +105,8 @@ struct fil_ctx {
     // Broyden state
     double *Xk, *fk, *Xn, *fn, *w, *g, *C, *D;
     double *scal;          // per system (stride sstride): [alpha_0..alpha_{k-1}, ndf2, dff]
+    float *C32, *D32;      // the history in FP32 (mixed mode; C, D are then null)
+    float *scal32;         // FP32 copy of scal for the FP32 history sums
     int sstride;
     double *red_part;      // reduction partials, [(max_iter + 2) x red_blocks]
     int red_blocks;        // reduction blocks, each inside one system
