@@ -46,18 +46,24 @@ __device__ __forceinline__ Q4 qsqrt(Q4 p) {
     return {(p.w + 1.0) * r, p.x * r, p.y * r, p.z * r};
 }
 
-// exp(u) = (cos(|u|/2), sin(|u|/2) u/|u|), Sec. 2.9.3. For tiny |u| the
-// factor sin(x/2)/x uses its Taylor series 1/2 - x^2/48 + x^4/3840.
+// exp(u) = (cos(|u|/2), sin(|u|/2) u/|u|), Sec. 2.9.3. Rotation increments
+// are small (|u| < 1/4 in practice), where the Taylor series in x^2 of
+// cos(x/2) = sum_k (-1)^k x^2k / (4^k (2k)!) and of
+// sin(x/2)/x = sum_k (-1)^k x^2k / (2 4^k (2k+1)!), cut after the x^10 term,
+// are exact to ~1e-19 -- far cheaper in FP64 than a sine and a cosine; larger
+// angles use sincos.
 __device__ __forceinline__ Q4 qexp(V3 u) {
     const double t2 = dot(u, u);
-    const double ith = t2 > 0.0 ? rsqrt(t2) : 0.0;
-    const double th = t2 * ith;
-    double s, c;
-    sincos(0.5 * th, &s, &c);
-    double f;
-    if (th < 1e-4) {
-        f = 0.5 - t2 * (1.0 / 48.0) + t2 * t2 * (1.0 / 3840.0);
+    double c, f;
+    if (t2 < 0.0625) {
+        c = 1.0 + t2 * (-1.0 / 8.0 + t2 * (1.0 / 384.0 + t2 * (-1.0 / 46080.0 +
+            t2 * (1.0 / 10321920.0 + t2 * (-1.0 / 3715891200.0)))));
+        f = 0.5 + t2 * (-1.0 / 48.0 + t2 * (1.0 / 3840.0 + t2 * (-1.0 / 645120.0 +
+            t2 * (1.0 / 185794560.0 + t2 * (-1.0 / 81749606400.0)))));
     } else {
+        const double ith = rsqrt(t2);
+        double s;
+        sincos(0.5 * t2 * ith, &s, &c);
         f = s * ith;
     }
     return {c, f * u.x, f * u.y, f * u.z};
@@ -84,16 +90,19 @@ __device__ __forceinline__ V3 rotate(Q4 q, V3 v) {
 }
 
 // dexpinv_u(W) = W - (u x W)/2 - c(|u|) u x (u x W), eq. dexpinv_definition,
-// c(x) = (x cot(x/2) - 2)/(2x^2); below x = 1e-2 the Taylor series of x cot(x/2)
-// gives c = -1/12 - x^2/720 - x^4/30240.
+// c(x) = (x cot(x/2) - 2)/(2x^2). From (x/2) cot(x/2) = sum_k (-1)^k B_2k x^2k / (2k)!
+// (B_2k the Bernoulli numbers), c = sum_{k>=1} (-1)^k B_2k x^(2k-2) / (2k)!
+//   = -1/12 - x^2/720 - x^4/30240 - x^6/1209600 - x^8/47900160 - 691 x^10/1307674368000 - ...,
+// used below x = 1/4 (truncation < 1e-18 relative); tan above.
 __device__ __forceinline__ V3 dexpinv(V3 u, V3 W) {
-    double th = norm(u);
+    const double t2 = dot(u, u);
     double c;
-    if (th < 1e-2) {
-        double t2 = th * th;
-        c = -1.0 / 12.0 - t2 / 720.0 - t2 * t2 / 30240.0;
+    if (t2 < 0.0625) {
+        c = -1.0 / 12.0 + t2 * (-1.0 / 720.0 + t2 * (-1.0 / 30240.0 + t2 * (-1.0 / 1209600.0 +
+            t2 * (-1.0 / 47900160.0 + t2 * (-691.0 / 1307674368000.0)))));
     } else {
-        c = (th / tan(0.5 * th) - 2.0) / (2.0 * th * th);
+        const double th = sqrt(t2);
+        c = (th / tan(0.5 * th) - 2.0) / (2.0 * t2);
     }
     V3 uw = cross(u, W);
     V3 uuw = cross(u, uw);
