@@ -255,3 +255,21 @@ def test_bdf2_second_order_in_time_on_gpu(fil):
     err = [np.linalg.norm(run(n) - ref, axis=1).max() for n in (50, 100, 200)]
     assert 3.5 < err[0] / err[1] < 4.5, err
     assert 3.5 < err[1] / err[2] < 4.5, err
+
+
+@pytest.mark.parametrize("unorm", [1e-9, 0.01, 0.2499, 0.2501, 0.8])
+def test_residual_parity_across_small_angle_branches(fil, unorm):
+    """Rotation vectors on both sides of |u| = 1/4, where the quaternion exponential and the
+    dexpinv coefficient switch from their series to sincos / tan: the residual (which uses
+    both) matches the oracle to the FP64 tolerance."""
+    lay, p, st, ext, _ = _system([12, 7], 77, history=True)
+    rng = np.random.default_rng(3)
+    d = rng.standard_normal((lay.S, 3))
+    u = unorm * d / np.linalg.norm(d, axis=1, keepdims=True)
+    Y1 = np.array([st.Y[lay.off_seg[i]] for i in range(lay.M)])
+    X = lay.join_X(Y1, u, rng.standard_normal((lay.n_lam, 3)))
+    ref = fo.residual(lay, p, st, ext, X)
+    with _gpu(fil, lay, p, st, ext) as m:
+        f = np.zeros(6 * lay.S)
+        m.residual(X, f)
+    np.testing.assert_allclose(f, ref, rtol=0, atol=1e-12 * max(1.0, np.abs(st.Y).max()))
