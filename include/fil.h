@@ -60,7 +60,9 @@ typedef enum {
 typedef enum {
     FIL_FP64 = 0,     /* every step in FP64, including the RPY pair sums       */
     FIL_MIXED = 1     /* RPY pair sums in FP32 with per-target compensated
-                         accumulation; everything else FP64                    */
+                         accumulation; J0 factors / inverse and their solves
+                         and the Broyden history (c_i, d_i of Algorithm 2) in
+                         FP32; state, residual, iterates and norms in FP64     */
 } fil_precision;
 
 typedef enum {
@@ -255,7 +257,9 @@ fil_status fil_broyden_step(fil_ctx *c, int32_t *converged, double *finf);
 /* Copy the current iterate X_k and f(X_k) (each 6S, either may be NULL). */
 fil_status fil_get_iterate(fil_ctx *c, double *X, double *f);
 
-/* Apply the factored J0^{-1} of the current step to b (6S) -> x (6S). */
+/* Apply the factored J0^{-1} of the current step to b (6S) -> x (6S): exact to
+ * FP64 rounding in FP64 mode (dense model: FP32 inverse plus one FP64
+ * refinement step, ~1e-14 relative), to FP32 rounding (~1e-7) in mixed mode. */
 fil_status fil_j0_solve(fil_ctx *c, const double *b, double *x);
 
 /* Finish the timestep at the current iterate: q^{j+1} = exp(u) q^j,
