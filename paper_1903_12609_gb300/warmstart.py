@@ -10,7 +10,8 @@ from the prediction is restarted from the extrapolation), so every step
 converges to the same tolerance with or without it.
 
 Train and evaluate (one GPU):
-    python -m paper_1903_12609_gb300.warmstart --steps 10000 --out <file.npz>
+    python -m paper_1903_12609_gb300.warmstart --steps 4000 --out <file.npz>
+    python -m paper_1903_12609_gb300.warmstart --trajectories 40 --steps 100 --out <file.npz>
 """
 from __future__ import annotations
 
@@ -228,7 +229,12 @@ def main():
     import torch
     ap = argparse.ArgumentParser()
     ap.add_argument("--n-fil", type=int, default=1000)
-    ap.add_argument("--steps", type=int, default=4000, help="recorded solver steps")
+    ap.add_argument("--steps", type=int, default=4000,
+                    help="recorded solver steps (per trajectory)")
+    ap.add_argument("--trajectories", type=int, default=1,
+                    help="independent suspensions recorded (seeds seed, seed + 1000, ...): many "
+                         "short runs cover the early, nearly straight states a fresh suspension "
+                         "starts from; one long run covers later, deformed states")
     ap.add_argument("--epochs", type=int, default=12)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--lr", type=float, default=3e-4)
@@ -239,9 +245,14 @@ def main():
     args = ap.parse_args()
     log = lambda s: print(s, flush=True)   # noqa: E731
     t0 = time.time()
-    feat, targ, iters = record(torch, args.n_fil, args.steps, seed=args.seed)
-    log("recorded %d steps x %d filaments in %.1f s (plain: %.2f Broyden iterations/step)"
-        % (args.steps, args.n_fil, time.time() - t0, np.mean(iters)))
+    parts = [record(torch, args.n_fil, args.steps, seed=args.seed + 1000 * k)
+             for k in range(args.trajectories)]
+    feat = torch.cat([f for f, _, _ in parts]) if len(parts) > 1 else parts[0][0]
+    targ = torch.cat([t for _, t, _ in parts]) if len(parts) > 1 else parts[0][1]
+    iters = [i for _, _, its in parts for i in its]
+    del parts
+    log("recorded %d x %d steps x %d filaments in %.1f s (plain: %.2f Broyden iterations/step)"
+        % (args.trajectories, args.steps, args.n_fil, time.time() - t0, np.mean(iters)))
     wl = suspension(args.n_fil, SEG, seed=args.seed)[0]
     norm = fit_norm(torch, feat, targ, weights=residual_weights(wl), seed=args.seed)
     log("target RMS per block: %s" % json.dumps(block_stats(targ[:20000].cpu().numpy())))
@@ -250,8 +261,9 @@ def main():
                          lr=args.lr, seed=args.seed, log=log)
     log("trained in %.1f s" % (time.time() - t1))
     del feat, targ
-    meta = {"n_fil": args.n_fil, "steps": args.steps, "epochs": args.epochs, "batch": args.batch,
-            "lr": args.lr, "seed": args.seed, "history": hist}
+    meta = {"n_fil": args.n_fil, "steps": args.steps, "trajectories": args.trajectories,
+            "epochs": args.epochs, "batch": args.batch, "lr": args.lr, "seed": args.seed,
+            "history": hist}
     save(args.out, params, norm, meta)
     net = load(args.out, max_batch=max(1024, args.n_fil))
     ev = evaluate(torch, net, args.n_fil, args.eval_steps, seed=args.seed + 1)
