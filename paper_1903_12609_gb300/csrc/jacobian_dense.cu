@@ -88,16 +88,52 @@ __device__ __forceinline__ V3 mv(const M33 &m, V3 v) {
             m.m[6] * v.x + m.m[7] * v.y + m.m[8] * v.z};
 }
 
+// FP32 forms of pair_coef / apply_pair for the mixed mode's J0 (same branches).
+struct PairCoef32 {
+    float A, B, C, D, G;
+};
+
+__device__ __forceinline__ PairCoef32 pair_coef32(float dx, float dy, float dz, float a) {
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    PairCoef32 k;
+    if (r2 < 4.f * a * a) {
+        const float r = sqrtf(r2);
+        const float rinv = r > 0.f ? 1.f / r : 0.f;
+        const float ia3 = 1.f / (a * a * a);
+        k.A = (4.f / (3.f * a)) * (1.f - 9.f * r / (32.f * a));
+        k.B = rinv / (8.f * a * a);
+        k.C = ia3 * (1.f - 27.f * r / (32.f * a) + 5.f * r * r2 / (64.f * a * a * a));
+        k.D = ia3 * (9.f * rinv / (32.f * a) - 3.f * r / (64.f * a * a * a));
+        k.G = 0.5f * ia3 * (1.f - 3.f * r / (8.f * a));
+    } else {
+        const float rinv = rsqrtf(r2);
+        const float rinv2 = rinv * rinv, rinv3 = rinv * rinv2, rinv5 = rinv3 * rinv2;
+        k.A = rinv + (2.f * a * a / 3.f) * rinv3;
+        k.B = rinv3 - 2.f * a * a * rinv5;
+        k.C = -0.5f * rinv3;
+        k.D = 1.5f * rinv5;
+        k.G = rinv3;
+    }
+    return k;
+}
+
+// FP64 work per filament (one CTA per filament). fast (the mixed mode, whose
+// J0 is used only through its FP32 assembly): the two N^2 loops -- pair
+// coefficients and the angular velocity of the internal loads -- in FP32.
 __global__ void __launch_bounds__(kAsmThreads)
 j0_precompute_kernel(Layout lay, const int64_t *__restrict__ auxofs, const double *__restrict__ X,
                      const double *__restrict__ qc, const double *__restrict__ Yc,
-                     const double *__restrict__ Tint, DenseParams dp, double *__restrict__ aux_all) {
-    extern __shared__ double sm[];     // F_int 3N | Yrel 3N
+                     const double *__restrict__ Tint, DenseParams dp, double *__restrict__ aux_all,
+                     int fast) {
+    // F_int 3N | Yrel 3N (doubles), then for fast: Y 3N | F_int 3N | T_int 3N | pc 5N^2 (floats)
+    extern __shared__ double sm[];
     const int f = blockIdx.x;
     const int s0 = lay.off[f];
     const int N = lay.off[f + 1] - s0;
     AuxView g = aux_view(aux_all + auxofs[f], N);
     double *Fi = sm, *Yf = sm + 3 * N;
+    float *Y32 = reinterpret_cast<float *>(sm + 6 * N), *F32 = Y32 + 3 * N, *T32 = F32 + 3 * N,
+          *pc32 = T32 + 3 * N;
     const double *Xf = X + 6 * (int64_t)s0;
     const double *Lam = Xf + 3 + 3 * N;
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
@@ -121,6 +157,63 @@ j0_precompute_kernel(Layout lay, const int64_t *__restrict__ auxofs, const doubl
         }
     }
     __syncthreads();
+    if (fast) {
+        for (int e = threadIdx.x; e < 3 * N; e += blockDim.x) {
+            Y32[e] = (float)(Yf[e] - Yf[e % 3]);          // relative to segment 0
+            F32[e] = (float)Fi[e];
+            T32[e] = (float)Tint[3 * (int64_t)s0 + e];
+        }
+        __syncthreads();
+        const float a32 = (float)dp.a;
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+            const int n = e / N, m = e - (e / N) * N;
+            if (m < n) continue;
+            const PairCoef32 k = pair_coef32(Y32[3 * n] - Y32[3 * m], Y32[3 * n + 1] - Y32[3 * m + 1],
+                                             Y32[3 * n + 2] - Y32[3 * m + 2], a32);
+            const float v[5] = {k.A, k.B, k.C, k.D, k.G};
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                pc32[5 * e + c] = v[c];
+                g.pc[5 * (int64_t)e + c] = (double)v[c];
+            }
+            if (m != n) {
+                const int et = m * N + n;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    pc32[5 * et + c] = v[c];
+                    g.pc[5 * (int64_t)et + c] = (double)v[c];
+                }
+            }
+        }
+        __syncthreads();
+        for (int base = 0; base < N; base += (int)blockDim.x / 8) {
+            const int n = base + (int)threadIdx.x / 8;
+            const int sub = threadIdx.x & 7;
+            float Wx = 0.f, Wy = 0.f, Wz = 0.f;
+            if (n < N) {
+                for (int m = sub; m < N; m += 8) {
+                    const float *pc = pc32 + 5 * (n * N + m);
+                    const float dx = Y32[3 * n] - Y32[3 * m], dy = Y32[3 * n + 1] - Y32[3 * m + 1],
+                                dz = Y32[3 * n + 2] - Y32[3 * m + 2];
+                    const float vx = F32[3 * m], vy = F32[3 * m + 1], vz = F32[3 * m + 2];
+                    const float wx = T32[3 * m], wy = T32[3 * m + 1], wz = T32[3 * m + 2];
+                    // Omega += G (v x d) + C w + D (d.w) d
+                    const float dw = pc[3] * fmaf(dx, wx, fmaf(dy, wy, dz * wz));
+                    Wx += pc[4] * (vy * dz - vz * dy) + pc[2] * wx + dw * dx;
+                    Wy += pc[4] * (vz * dx - vx * dz) + pc[2] * wy + dw * dy;
+                    Wz += pc[4] * (vx * dy - vy * dx) + pc[2] * wz + dw * dz;
+                }
+            }
+#pragma unroll
+            for (int d = 4; d > 0; d >>= 1) {
+                Wx += __shfl_xor_sync(0xffffffffu, Wx, d);
+                Wy += __shfl_xor_sync(0xffffffffu, Wy, d);
+                Wz += __shfl_xor_sync(0xffffffffu, Wz, d);
+            }
+            if (n < N && sub == 0) st3(g.Om + 3 * n, dp.inv8pieta * v3(Wx, Wy, Wz));
+        }
+        __syncthreads();
+    } else {
     // the coefficients depend on r only: each unordered pair once, stored twice
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
         const int n = e / N, m = e - (e / N) * N;
@@ -159,6 +252,7 @@ j0_precompute_kernel(Layout lay, const int64_t *__restrict__ auxofs, const doubl
         if (n < N && sub == 0) st3(g.Om + 3 * n, dp.inv8pieta * W);
     }
     __syncthreads();
+    }
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
         // dT_n/du_n = (dL/2)[x Ls][x t] + Da(n) - Db(n-1)
         M33 dT = mscale(mmul(rskew(ld3(g.Ls + 3 * n)), rskew(ld3(g.t + 3 * n))), 0.5 * dp.jp.dL);
@@ -808,8 +902,17 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
     dp.a = c->a;
     c->j0_dp_bdt = dp.bdt;
     const int N = c->lay.maxN;
-    j0_precompute_kernel<<<c->lay.M, kAsmThreads, (size_t)6 * N * sizeof(double), c->stream>>>(
-        c->lay, c->auxofs, X, c->qc, c->Yc, c->Tint, dp, c->aux);
+    const int fast = c->prec == FIL_MIXED ? 1 : 0;
+    const size_t smem_pre = (size_t)6 * N * sizeof(double) +
+                            (fast ? (size_t)(9 * N + 5 * N * N) * sizeof(float) : 0);
+    if (smem_pre > 48 * 1024) {
+        cudaError_t ea = cudaFuncSetAttribute(j0_precompute_kernel,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem_pre);
+        if (ea != cudaSuccess) return ea;
+    }
+    j0_precompute_kernel<<<c->lay.M, kAsmThreads, smem_pre, c->stream>>>(
+        c->lay, c->auxofs, X, c->qc, c->Yc, c->Tint, dp, c->aux, fast);
     const size_t smem_asm = (size_t)(5 * N * N + 51 * N) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(j0_assemble32_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
