@@ -42,6 +42,10 @@
 #include "quat.cuh"
 #include "rpy_pair.cuh"
 
+#ifndef FIL_GJ_ROWS
+#define FIL_GJ_ROWS 0     // 1: the row-distributed register Gauss-Jordan (comparison)
+#endif
+
 namespace fil {
 namespace {
 
@@ -718,7 +722,11 @@ gauss_jordan_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
 // six 32-column chunks so that column indices into the register array are
 // static. The result is A^{-1} with rows and columns permuted:
 // A^{-1}[k][m] = S[p_k][q(m)], p_k the pivot row of column k and q its inverse.
-constexpr int kGjWarps = 16, kGjRows = 12, kGjPairs = 3, kGjMaxN = 64 * kGjPairs;  // 192
+constexpr int kGjWarps = 16, kGjMaxN = 192;
+
+#if FIL_GJ_ROWS
+constexpr int kGjRows = 12, kGjPairs = 3;
+static_assert(64 * kGjPairs == kGjMaxN && kGjWarps * kGjRows == kGjMaxN, "192 x 192");
 
 // Column values col[r] of this lane's rows -> colk (warp-major: entry
 // 12 w + r is row w + 16 r), and this warp's pivot candidate (largest |value|
@@ -865,6 +873,203 @@ gauss_jordan_inverse_reg_kernel(Layout lay, const int64_t *__restrict__ jofs, fl
     }
 }
 #undef FIL_GJ_PUBLISH
+#endif  // FIL_GJ_ROWS
+
+#if !FIL_GJ_ROWS
+// The same in-place Gauss-Jordan inverse with the matrix distributed by
+// columns: warp w holds columns w + 16 q (q < 12), lane l rows l + 32 j
+// (j < 6), as pairs of columns (w + 32 t, w + 32 t + 16) for the packed FP32
+// FMA. The pivot search of step k is one warp's reduction over its column: a
+// redux.sync over 32-bit keys, |a_ik| with its 8 low mantissa bits replaced by
+// 255 - i, so the first of the rows whose magnitudes agree to 15 significant
+// bits wins. The owner of column k publishes the negated column (each entry
+// twice, the packed multipliers of the update), the pivot row and 1/pivot;
+// after the single CTA barrier of the step every warp takes its part of the
+// pivot row from the lane that holds row p, through shared memory, and updates
+// its 72 entries. Column and pivot are double buffered.
+constexpr int kGcSlots = 6, kGcPairs = 6;    // row slots per lane, column pairs per warp
+constexpr int kGcThreads = 32 * kGjWarps;
+constexpr int kGcLoad = kGjMaxN * kGjMaxN / kGcThreads;   // elements per thread, load / store
+static_assert(32 * kGcSlots == kGjMaxN && kGjWarps * 2 * kGcPairs == kGjMaxN &&
+              kGcLoad * kGcThreads == kGjMaxN * kGjMaxN,
+              "column-layout Gauss-Jordan covers 192 x 192");
+
+// Row slot j (warp-uniform at run time) of the register array, as a static index.
+#define FIL_GC_SLOT_SWITCH(jp, BODY)           \
+    switch (jp) {                              \
+        case 0: { constexpr int J = 0; BODY } break; \
+        case 1: { constexpr int J = 1; BODY } break; \
+        case 2: { constexpr int J = 2; BODY } break; \
+        case 3: { constexpr int J = 3; BODY } break; \
+        case 4: { constexpr int J = 4; BODY } break; \
+        default: { constexpr int J = 5; BODY } break; \
+    }
+
+__global__ void __launch_bounds__(kGcThreads, 1)
+gauss_jordan_inverse_col_kernel(Layout lay, const int64_t *__restrict__ jofs, float *inv_all,
+                                int *__restrict__ flags) {
+    extern __shared__ float St[];                     // n x (n + 1): staging of the load / store
+    __shared__ float4 colk[2][32][kGcSlots / 2];      // -a_{l+32j,k} twice, j = 2 e, 2 e + 1
+    __shared__ float4 prow[kGjWarps][kGcPairs / 2];   // pivot row, this warp's column pairs
+    __shared__ float2 s_piv[2];                       // (p as bits, 1/pivot)
+    __shared__ int pivrow[kGjMaxN];
+    __shared__ int qinv[kGjMaxN];
+    const int f = blockIdx.x;
+    const int s0 = lay.off[f];
+    const int n = 6 * (lay.off[f + 1] - s0);
+    float *A = inv_all + jofs[f];   // J0 in FP32 on entry, its inverse on exit
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    {
+        // element e = tid + kGcThreads r of the row-major matrix is (row, col),
+        // stepped by (dq, dr) from r to r + 1
+        const int nn = n * n, ld = n + 1;
+        const int dq = kGcThreads / n, dr = kGcThreads - dq * n;
+        int row = tid / n, col = tid - (tid / n) * n;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            constexpr int kH = kGcLoad / 2;
+            float tmp[kH];            // a batch of loads in flight before its stores
+#pragma unroll
+            for (int r = 0; r < kH; ++r) {
+                const int e = tid + kGcThreads * (kH * h + r);
+                tmp[r] = e < nn ? A[e] : 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < kH; ++r) {
+                if (tid + kGcThreads * (kH * h + r) < nn) St[row * ld + col] = tmp[r];
+                row += dq;
+                col += dr;
+                if (col >= n) { col -= n; ++row; }
+            }
+        }
+    }
+    __syncthreads();
+    float2 a[kGcSlots][kGcPairs];     // a[j][t] = (column wid + 32 t, column wid + 32 t + 16)
+    unsigned used = 0;                // bit j: row lane + 32 j pivoted, or padding
+#pragma unroll
+    for (int j = 0; j < kGcSlots; ++j) {
+        const int i = lane + 32 * j, ld = n + 1;
+        if (i >= n) used |= 1u << j;
+#pragma unroll
+        for (int t = 0; t < kGcPairs; ++t) {
+            const int c0 = wid + 32 * t, c1 = c0 + 16;
+            a[j][t].x = (i < n && c0 < n) ? St[i * ld + c0] : 0.f;
+            a[j][t].y = (i < n && c1 < n) ? St[i * ld + c1] : 0.f;
+        }
+    }
+    // column k = wid + 16 q  <->  pair t = q / 2, half q & 1
+#pragma unroll
+    for (int q = 0; q < 2 * kGcPairs; ++q) {
+        for (int wk = 0; wk < kGjWarps; ++wk) {
+            const int k = wk + 16 * q;
+            if (k >= n) break;
+            const int buf = k & 1;
+            if (wid == wk) {
+                unsigned key = 0;
+#pragma unroll
+                for (int j = 0; j < kGcSlots; ++j) {
+                    const float v = (q & 1) ? a[j][q >> 1].y : a[j][q >> 1].x;
+                    const unsigned kj =
+                        (__float_as_uint(v) & 0x7fffff00u) | (255u - (unsigned)(lane + 32 * j));
+                    if (!((used >> j) & 1u)) key = max(key, kj);
+                }
+                key = __reduce_max_sync(0xffffffffu, key);
+                const int p = 255 - (int)(key & 255u);
+                // publish the negated column, then zero it
+#pragma unroll
+                for (int e = 0; e < kGcSlots / 2; ++e) {
+                    const float m0 = -((q & 1) ? a[2 * e][q >> 1].y : a[2 * e][q >> 1].x);
+                    const float m1 = -((q & 1) ? a[2 * e + 1][q >> 1].y : a[2 * e + 1][q >> 1].x);
+                    colk[buf][lane][e] = make_float4(m0, m0, m1, m1);
+                }
+#pragma unroll
+                for (int j = 0; j < kGcSlots; ++j) {
+                    if (q & 1) a[j][q >> 1].y = 0.f;
+                    else a[j][q >> 1].x = 0.f;
+                }
+                if (lane == (p & 31)) {
+                    float2 *cp = reinterpret_cast<float2 *>(&colk[buf][lane][0]) + (p >> 5);
+                    const float v = -cp->x;           // written by this lane just above
+                    if (!(fabsf(v) > 0.f)) atomicOr(flags + 1, 1);
+                    s_piv[buf] = make_float2(__int_as_float(p), fabsf(v) > 0.f ? __frcp_rn(v) : 0.f);
+                    *cp = make_float2(1.f, 1.f);      // multiplier +1: the pivot row becomes pr
+                    pivrow[k] = p;
+                }
+            }
+            __syncthreads();
+            const float2 piv = s_piv[buf];
+            const int p = __float_as_int(piv.x);
+            const float2 vinv2 = make_float2(piv.y, piv.y);
+            const int src = p & 31, jp = p >> 5;
+            if (lane == src) {
+                FIL_GC_SLOT_SWITCH(jp,
+                    _Pragma("unroll") for (int e = 0; e < kGcPairs / 2; ++e) {
+                        prow[wid][e] = make_float4(a[J][2 * e].x, a[J][2 * e].y,
+                                                   a[J][2 * e + 1].x, a[J][2 * e + 1].y);
+                        a[J][2 * e] = make_float2(0.f, 0.f);
+                        a[J][2 * e + 1] = make_float2(0.f, 0.f);
+                    })
+                used |= 1u << jp;
+            }
+            __syncwarp();
+            // this warp's part of the pivot row, scaled; entry k is 1/pivot
+            float2 pr[kGcPairs];
+#pragma unroll
+            for (int e = 0; e < kGcPairs / 2; ++e) {
+                const float4 r4 = prow[wid][e];
+                pr[2 * e] = __fmul2_rn(make_float2(r4.x, r4.y), vinv2);
+                pr[2 * e + 1] = __fmul2_rn(make_float2(r4.z, r4.w), vinv2);
+            }
+            if (wid == wk) {
+                if (q & 1) pr[q >> 1].y = piv.y;
+                else pr[q >> 1].x = piv.y;
+            }
+            // a_i <- a_i + m_i pr: m_i = -a_ik before the step, +1 for the pivot row
+#pragma unroll
+            for (int e = 0; e < kGcSlots / 2; ++e) {
+                const float4 m4 = colk[buf][lane][e];
+                const float2 m0 = make_float2(m4.x, m4.y), m1 = make_float2(m4.z, m4.w);
+#pragma unroll
+                for (int t = 0; t < kGcPairs; ++t) {
+                    a[2 * e][t] = __ffma2_rn(m0, pr[t], a[2 * e][t]);
+                    a[2 * e + 1][t] = __ffma2_rn(m1, pr[t], a[2 * e + 1][t]);
+                }
+            }
+        }
+    }
+    // A^{-1}[R][C] = S[pivrow[R]][qinv[C]], i.e. S[i][c] -> A^{-1}[qinv[i]][pivrow[c]]:
+    // scatter S into the staging buffer, then write rows coalesced
+    __syncthreads();
+    for (int k = tid; k < n; k += kGcThreads) qinv[pivrow[k]] = k;
+    __syncthreads();
+    const int nn = n * n, ld = n + 1;
+#pragma unroll
+    for (int j = 0; j < kGcSlots; ++j) {
+        const int i = lane + 32 * j;
+        if (i < n) {
+            const int R = qinv[i];
+#pragma unroll
+            for (int t = 0; t < kGcPairs; ++t) {
+                const int c0 = wid + 32 * t, c1 = c0 + 16;
+                if (c0 < n) St[R * ld + pivrow[c0]] = a[j][t].x;
+                if (c1 < n) St[R * ld + pivrow[c1]] = a[j][t].y;
+            }
+        }
+    }
+    __syncthreads();
+    const int dq = kGcThreads / n, dr = kGcThreads - dq * n;
+    int row = tid / n, col = tid - (tid / n) * n;
+#pragma unroll 8
+    for (int r = 0; r < kGcLoad; ++r) {
+        const int e = tid + kGcThreads * r;
+        if (e < nn) A[e] = St[row * ld + col];
+        row += dq;
+        col += dr;
+        if (col >= n) { col -= n; ++row; }
+    }
+}
+#undef FIL_GC_SLOT_SWITCH
+#endif  // !FIL_GJ_ROWS
 
 }  // namespace
 
@@ -922,8 +1127,17 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
         c->lay, c->jofs, c->auxofs, dp, c->aux, c->jinv);
 #ifndef FIL_GJ_SHARED_ONLY
     if (6 * N <= kGjMaxN) {
+#if FIL_GJ_ROWS
         gauss_jordan_inverse_reg_kernel<<<c->lay.M, 32 * kGjWarps, 0, c->stream>>>(
             c->lay, c->jofs, c->jinv, c->d_flags);
+#else
+        const size_t smem_gc = (size_t)6 * N * (6 * N + 1) * sizeof(float);
+        e = cudaFuncSetAttribute(gauss_jordan_inverse_col_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gc);
+        if (e != cudaSuccess) return e;
+        gauss_jordan_inverse_col_kernel<<<c->lay.M, kGcThreads, smem_gc, c->stream>>>(
+            c->lay, c->jofs, c->jinv, c->d_flags);
+#endif
         e = cudaGetLastError();
     } else
 #endif

@@ -136,3 +136,36 @@ def test_graph_iterations_reproduce_launched_iterations(fil, prec):
             out[graph] = (its, Y)
     assert out[True][0] == out[False][0]
     np.testing.assert_array_equal(out[True][1], out[False][1])
+
+
+@pytest.mark.parametrize("j0", [(0, "drag"), (1, "rpy")])
+def test_mixed_ensemble_converges_close_to_fp64(fil, j0):
+    """The mixed mode (FP32 pair sums, FP32 J0 solves, FP32 Broyden history) on an
+    ensemble: every system converges to the oracle's FP64 trajectory within the
+    accuracy its tolerance allows, and every system's ||f||_inf meets it."""
+    systems = [[16], [20, 33, 7], [30] * 5, [1, 2, 3]]
+    p = fo.Params(a=1.0, eta=1.0, dL=2.2, KB=2.0, KT=1.5, dt=0.2, tol=1e-6, max_iter=80)
+    states, exts, lays = [], [], []
+    for i, segs in enumerate(systems):
+        lay, base, t, mu, xi, rng = _system(segs, 30 + i)
+        states.append(fo.initial_state(lay, p, base, t, mu, xi))
+        exts.append(fo.External(Fext=np.tile([0.0, 0.0, -2.2], (lay.S, 1))))
+        lays.append(lay)
+    segs_all = [n for segs in systems for n in segs]
+    with fil.Filaments(segs_all, fil_per_sys=[len(s) for s in systems], a=p.a, eta=p.eta,
+                       dL=p.dL, KB=p.KB, KT=p.KT, dt=p.dt, tol=p.tol, max_iter=p.max_iter,
+                       precision=fil.FIL_MIXED, j0_model=j0[0]) as m:
+        m.set_state(np.concatenate([s.Y for s in states]), np.concatenate([s.q for s in states]))
+        m.set_external(np.concatenate([e.Fext for e in exts]), None, None)
+        Y = np.zeros((m.S, 3))
+        for _ in range(3):
+            m.step()
+            _, finf = m.sys_stats()
+            assert np.all(finf <= p.tol * p.a)
+            for k, lay in enumerate(lays):
+                states[k], _ = fo.step(lay, p, states[k], exts[k], j0_model=j0[1])
+        m.get_state(Y, None, None, None, None)
+    off = 0
+    for k, lay in enumerate(lays):
+        np.testing.assert_allclose(Y[off:off + lay.S], states[k].Y, rtol=0, atol=1e-4)
+        off += lay.S

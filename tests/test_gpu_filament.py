@@ -123,6 +123,30 @@ def test_j0_solve_matches_dense_oracle(fil, segs, history, model):
     np.testing.assert_allclose(x, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("segs", [[20], [32] * 6, [1, 7, 32, 13], [33, 3]])
+def test_mixed_j0_solve_within_fp32_rounding(fil, segs):
+    """Mixed mode applies an FP32 Gauss-Jordan inverse of each filament-RPY block
+    without refinement (a register kernel for 6N <= 192, a shared-memory one
+    above). Its error is bounded by that of an FP32 dense LU solve of the same
+    blocks, the rounding the arithmetic allows, times a small factor; an index or
+    pivoting mistake would be O(1)."""
+    lay, p, st, ext, _ = _system(segs, 31, history=True, twist=0.2)
+    with _gpu(fil, lay, p, st, ext, prec=fil.FIL_MIXED, j0=1) as m:
+        m.broyden_begin()
+        X0 = np.zeros(6 * lay.S)
+        m.get_iterate(X0, None)
+        b = np.random.default_rng(3).standard_normal(6 * lay.S)
+        x = np.zeros_like(b)
+        m.j0_solve(b, x)
+    blocks = fo.jacobian0_general(lay, p, st, X0, "rpy")
+    ref = fo.J0Solver(lay, blocks).solve(b)
+    x32 = np.concatenate([np.linalg.solve(B.astype(np.float32), b[o:o + B.shape[0]].astype(
+        np.float32)).astype(np.float64) for B, o in zip(blocks, lay.off_X)])
+    e32 = np.abs(x32 - ref).max()
+    assert e32 < 1e-3 * np.abs(ref).max()
+    assert np.abs(x - ref).max() <= 16 * e32 + 1e-12
+
+
 @pytest.mark.parametrize("segs", [[20], [32] * 4, [1, 7, 33]])
 @pytest.mark.parametrize("model", J0_MODELS)
 def test_broyden_iterates_match_oracle(fil, segs, model):
