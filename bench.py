@@ -179,6 +179,20 @@ def aggregate_ranks(units, ms, dist, device):
     return float(u[0]), float(t[0])
 
 
+def run_peaks(args, fil):
+    """Measured FMA rates against the derived peaks (SMs x lanes x 2 x clock)."""
+    out = {"metric": "measured FMA rate", "unit": "TFLOP/s", "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "FMA chains at full occupancy (fil_fma_peak)"}}
+    for name, fp64, lanes in (("fp32", False, FP32_LANES_PER_SM), ("fp64", True, 2)):
+        reps = [fil.fil_fma_peak(fp64) for _ in range(3)]
+        fl, mhz = max(reps)
+        out[name] = {"tflops": fl / 1e12, "sm_mhz": mhz,
+                     "derived_at_max_clock": N_SM * lanes * 2 * SM_MAX_MHZ * 1e6 / 1e12,
+                     "derived_at_measured_clock": N_SM * lanes * 2 * mhz * 1e6 / 1e12,
+                     "runs_tflops": [r[0] / 1e12 for r in reps]}
+    print(json.dumps(out), flush=True)
+
+
 def run_mobility(args, fil, torch):
     """RPY applies alone on the positions of the 32k suspension with N(0,1)
     loads: a lean launch sequence for kernel profiling (one JSON line)."""
@@ -320,8 +334,9 @@ def main():
                          "default: with kernels of 0.05-0.7 ms the launches are not the cost and "
                          "the graph's speculative last iteration is)")
     ap.add_argument("--workload", default="suspension",
-                    choices=["suspension", "mobility", "ensemble"],
-                    help="'mobility': only RPY applies on the 32k configuration (for profiling)")
+                    choices=["suspension", "mobility", "ensemble", "peaks"],
+                    help="'mobility': only RPY applies on the 32k configuration (for profiling); "
+                         "'peaks': the measured FP32 / FP64 FMA rates beside the derived ones")
     args = ap.parse_args()
     if args.tune is None:
         args.tune = 1 if args.workload == "ensemble" else 0
@@ -342,6 +357,9 @@ def main():
     torch.cuda.set_device(local)
     if args.workload == "mobility":
         run_mobility(args, fil, torch)
+        return
+    if args.workload == "peaks":
+        run_peaks(args, fil)
         return
     if args.workload == "ensemble":
         run_ensemble(args, fil, torch)
@@ -499,6 +517,9 @@ def main():
     if rank != 0:
         return
 
+    # measured FMA rates (after the timed region): context for the derived peak
+    p32, mhz32 = fil.fil_fma_peak(False)
+    p64, mhz64 = fil.fil_fma_peak(True)
     import __graft_entry__ as _g  # noqa: F401
     cpu = cpu_baseline(Yh, np.random.default_rng(2).standard_normal((S, 6)),
                        args.cpu_seconds) if world == 1 else None
@@ -530,7 +551,14 @@ def main():
                      "fma_pipe_active": prof.get("fma_pipe_active"),
                      "avg_launch_ms": pair_avg_ms, "launches": int(n_pair_launch),
                      "share_of_step": pair_ms / dev_ms if dev_ms > 0 else None,
-                     "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+                     "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+                     "peak_measured": {
+                         "fp32_tflops": p32 / 1e12, "fp32_sm_mhz": mhz32,
+                         "fp64_tflops": p64 / 1e12, "fp64_sm_mhz": mhz64,
+                         "frac_of_measured": (achieved / (p32 / 1e12)
+                                              if prec == fil.FIL_MIXED else None),
+                         "how": "fil_fma_peak: packed FP32x2 / FP64 FMA chains, full "
+                                "occupancy, 5 launches of ~20 ms"}},
         "autotuned": ({"tile": tuned[0], "ctas_per_sm": tuned[1], "ms_per_apply": tuned[2]}
                       if tuned else None),
         "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": UNIT,
@@ -541,6 +569,7 @@ def main():
         "wall_s": t_wall,
     }
     if plain is not None:
+        plain["frac_of_measured_fp64_peak"] = plain["pairs_per_s"] * FLOPS_PER_PAIR / p64
         line["plain_fp64"] = plain
         line["mixed_over_plain_timesteps"] = line["timesteps_per_s"] / plain["timesteps_per_s"]
     if cpu is not None:

@@ -288,6 +288,18 @@ fil_status fil_counters(const fil_ctx *c, int64_t *mobility_applies, int64_t *br
 fil_status fil_profile(fil_ctx *c, int32_t enable);
 fil_status fil_profile_read(fil_ctx *c, int64_t *launches, double *total_ms);
 
+/* Measured FMA rate of the current device. A measurement helper with no
+ * counterpart in the paper: the pair kernels' roofline fractions are reported
+ * against the derived peak SMs x lanes x 2 flops x clock, and this call
+ * measures what an FMA-only kernel actually reaches. It runs packed FP32x2
+ * FMAs (fp64 = 0) or FP64 FMAs (fp64 = 1) in independent dependency chains on
+ * every SM at full occupancy and returns the rate in flops/s (an FMA counts 2)
+ * and the SM clock during the run in MHz, read from clock64 against the GPU's
+ * nanosecond timer (either pointer may be NULL). Synchronous on the legacy
+ * default stream; about 0.1 s (FP32) or 0.2 s (FP64); allocates nothing.
+ * FIL_EINVAL for fp64 other than 0 or 1, FIL_ECUDA on a CUDA failure. */
+fil_status fil_fma_peak(int32_t fp64, double *flops_per_s, double *sm_mhz);
+
 /* Allocation-free mobility apply. The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory themselves --
  * code that runs where cudaMalloc is unavailable or not allowed, such as

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libfil.so")
 SOURCES = ["api.cu", "rpy.cu", "filament.cu", "jacobian.cu", "jacobian_dense.cu", "broyden.cu",
-           "mlp.cu", "warm.cu", "steric.cu", "tether.cu"]
+           "mlp.cu", "warm.cu", "steric.cu", "tether.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

@@ -36,7 +36,7 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_tc_gemm_bf16", "fil_warm_features", "fil_warm_targets", "fil_warm_attach",
             "fil_warm_stats", "fil_create_ensemble", "fil_sys_stats", "fil_pair_count",
             "fil_set_graph", "fil_autotune", "fil_set_steric", "fil_set_tether",
-            "fil_get_tether"]
+            "fil_get_tether", "fil_fma_peak"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_SEG = 800, 256, 192, 32
 MLP_NPARAM = 256 * 800 + 256 + 2 * (256 * 256 + 256) + 192 * 256 + 192
 FIL_WARM_BEST_OF_TWO, FIL_WARM_PREDICTION_FIRST = 0, 1
@@ -88,6 +88,7 @@ def load_library(path=LIB_PATH):
         "fil_profile": [P, ctypes.c_int32],
         "fil_profile_read": [P, I64, D],
         "fil_rpy_apply_noalloc": [ctypes.c_int64, P, P, P, ctypes.c_double, ctypes.c_double, P],
+        "fil_fma_peak": [ctypes.c_int32, D, D],
         "fil_mlp_create": [ctypes.c_int64, P, ctypes.POINTER(P)],
         "fil_mlp_destroy": [P],
         "fil_mlp_set_params": [P, P],
@@ -311,6 +312,16 @@ def fil_rpy_apply_noalloc(n_seg, Y, FT, VW, a=1.0, eta=1.0, stream=None):
                                     float(eta), ctypes.c_void_p(stream) if stream else None)
     if st != FIL_OK:
         raise FilError(st, "fil_rpy_apply_noalloc")
+
+
+def fil_fma_peak(fp64=False):
+    """Measured FMA rate of the current device: (flops/s, SM MHz during the
+    run), packed FP32x2 FMAs or FP64 FMAs at full occupancy."""
+    fl, mhz = ctypes.c_double(), ctypes.c_double()
+    st = _lib.fil_fma_peak(1 if fp64 else 0, ctypes.byref(fl), ctypes.byref(mhz))
+    if st != FIL_OK:
+        raise FilError(st, "fil_fma_peak")
+    return fl.value, mhz.value
 
 
 # ---- warm-start network (include/fil_mlp.h); FP32 arrays ---------------------

@@ -52,6 +52,12 @@ def test_invalid_layout_is_rejected(lib):
         assert e.value.status == lib.FIL_EINVAL
 
 
+def test_fma_peak_rejects_an_unknown_precision(lib):
+    import ctypes
+    fl, mhz = ctypes.c_double(), ctypes.c_double()
+    assert lib._lib.fil_fma_peak(2, ctypes.byref(fl), ctypes.byref(mhz)) == lib.FIL_EINVAL
+
+
 def test_oracle_library_builds():
     from oracle import build
     build.build()
