@@ -105,11 +105,38 @@ __global__ void j0_build_kernel(Layout lay, const double *__restrict__ X,
     }
 }
 
-// In-place banded LU with partial pivoting (one warp per filament), in the
-// precision T of the stored factors.
+constexpr int kJ0Threads = 128;
+constexpr int kLuRing = 16;    // band rows a warp keeps in shared memory
+constexpr int kLuAhead = 13;   // column j requests row j + kLuAhead
+
+// One element of a band row, global -> shared, asynchronously (cp.async).
 template <typename T>
-__global__ void band_lu_kernel(Layout lay, T *__restrict__ band_all, int *__restrict__ piv_all,
-                               int *__restrict__ flags) {
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int kPending>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(kPending) : "memory");
+}
+
+// In-place banded LU with partial pivoting (one warp per filament), in the
+// precision T of the stored factors. Column j reads and writes rows j .. j+8
+// only, and row j is final once column j is done, so each warp keeps a ring
+// of kLuRing band rows in shared memory: row j + kLuAhead is requested with
+// cp.async at column j (into the slot of row j - 3, already written back),
+// waited for five columns later, and row j is written back, with its pivot
+// replaced by the reciprocal the solves multiply by, when column j is done.
+template <typename T>
+__global__ void __launch_bounds__(kJ0Threads)
+band_lu_kernel(Layout lay, T *__restrict__ band_all, int *__restrict__ piv_all,
+               int *__restrict__ flags) {
+    static_assert(kLuAhead < kLuRing, "a requested row reuses the slot of a written-back row");
+    __shared__ T ring_all[kJ0Threads / 32][kLuRing * kBandW];
     const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= lay.M) return;
@@ -117,20 +144,35 @@ __global__ void band_lu_kernel(Layout lay, T *__restrict__ band_all, int *__rest
     const int N = lay.off[warp + 1] - s0;
     const int n = 6 * N - 3;
     const int64_t row0 = 6 * (int64_t)s0 - 3 * (int64_t)warp;
-    T *A = band_all + row0 * kBandW;
+    T *G = band_all + row0 * kBandW;
+    T *R = ring_all[threadIdx.x >> 5];
     int *piv = piv_all + row0;
-#define BAND(i, c) A[(int64_t)(i) * kBandW + ((c) - (i) + kBandKL)]
+#define RB(i, c) R[((i) & (kLuRing - 1)) * kBandW + ((c) - (i) + kBandKL)]
+    for (int r = 0; r < kLuAhead && r < n; ++r)
+        if (lane < kBandW) cp_async_elem(&R[r * kBandW + lane], G + (int64_t)r * kBandW + lane);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
     for (int j = 0; j < n; ++j) {
+        {
+            const int r = j + kLuAhead;
+            if (r < n && lane < kBandW)
+                cp_async_elem(&R[(r & (kLuRing - 1)) * kBandW + lane], G + (int64_t)r * kBandW + lane);
+            cp_async_commit();
+        }
+        // rows up to j + 8, requested at column j + 8 - kLuAhead or before, have landed
+        cp_async_wait<kLuAhead - kBandKL>();
+        __syncwarp();
         const int last = min(n - 1, j + kBandKL);
         // pivot: first row of maximal |A(i, j)|, i in [j, last]
         T v = T(-1);
         int idx = j;
         if (j + lane <= last && lane <= kBandKL) {
-            v = fabs(BAND(j + lane, j));
+            v = fabs(RB(j + lane, j));
             idx = j + lane;
         }
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
+        for (int d = 8; d > 0; d >>= 1) {
             const T ov = __shfl_down_sync(0xffffffffu, v, d);
             const int oi = __shfl_down_sync(0xffffffffu, idx, d);
             if (ov > v || (ov == v && oi < idx)) {
@@ -145,39 +187,41 @@ __global__ void band_lu_kernel(Layout lay, T *__restrict__ band_all, int *__rest
         if (p != j) {
             const int c = j + lane;
             if (c <= cmax) {
-                const T t = BAND(j, c);
-                BAND(j, c) = BAND(p, c);
-                BAND(p, c) = t;
+                const T t = RB(j, c);
+                RB(j, c) = RB(p, c);
+                RB(p, c) = t;
             }
         }
         __syncwarp();
         if (pv == T(0)) {
             if (lane == 0) atomicOr(flags + 1, 1);
-            continue;
-        }
-        const T inv = T(1) / BAND(j, j);
-        T l = T(0);
-        if (lane >= 1 && j + lane <= last) {
-            l = BAND(j + lane, j) * inv;
-            BAND(j + lane, j) = l;
+        } else {
+            const T inv = T(1) / RB(j, j);
+            if (lane >= 1 && j + lane <= last) RB(j + lane, j) = RB(j + lane, j) * inv;
+            __syncwarp();
+            // rank-1 update of rows j+1..last (lane / 16 + 2k), columns j+1..cmax (lane % 16)
+            const int c = j + 1 + (lane & 15);
+            if (c <= cmax) {
+                const T ujc = RB(j, c);
+#pragma unroll
+                for (int k = 0; k < kBandKL / 2; ++k) {
+                    const int i = j + 1 + (lane >> 4) + 2 * k;
+                    if (i <= last) RB(i, c) -= RB(i, j) * ujc;
+                }
+            }
         }
         __syncwarp();
-        // rank-1 update of rows j+1..last, columns j+1..cmax
-        const int nr = last - j, nc = cmax - j;
-        for (int e = lane; e < nr * nc; e += 32) {
-            const int i = j + 1 + e / nc;
-            const int c = j + 1 + e % nc;
-            BAND(i, c) -= BAND(i, j) * BAND(j, c);
+        // row j is final: write it back (the solves multiply by the reciprocal pivot)
+        if (lane < kBandW) {
+            T e = R[(j & (kLuRing - 1)) * kBandW + lane];
+            if (lane == kBandKL) e = e != T(0) ? T(1) / e : T(0);
+            G[(int64_t)j * kBandW + lane] = e;
         }
-        __syncwarp();
     }
-    // the solves multiply by the reciprocal pivots (division is slow)
-    for (int j = lane; j < n; j += 32) {
-        const T d = BAND(j, j);
-        BAND(j, j) = d != T(0) ? T(1) / d : T(0);
-    }
-#undef BAND
+#undef RB
 }
+
+constexpr int kSolvePf = 8;   // rows of factors loaded ahead by the band solve
 
 // x = J0^{-1} b for every filament (b and x in the X / f layout; may alias),
 // with the factors and the working vector in precision T.
@@ -214,30 +258,101 @@ __global__ void band_solve_kernel(Layout lay, const T *__restrict__ band_all,
     }
     const double b1x = bf[0], b1y = bf[1], b1z = bf[2];
     __syncwarp();
+    // The factors a row step needs do not depend on z, so each lane loads them
+    // kSolvePf rows ahead into a register queue: the loads of the next block are
+    // in flight while the current block's dependency chain runs through shared
+    // memory. Lane l's entries sit at a fixed offset of consecutive rows:
+    // forward L(j + 1 + l, j), backward U(j - 1 - l, j) and the reciprocal U_jj.
     // forward: L with row interchanges applied in elimination order
-    for (int j = 0; j < n; ++j) {
-        const int p = piv[j];
-        if (p != j && lane == 0) {
-            const T t = z[j];
-            z[j] = z[p];
-            z[p] = t;
+    T zprev = T(0);   // lane 0: the finished entry of the previous row / column
+    {
+        T lq[kSolvePf];
+        int pq[kSolvePf];
+#pragma unroll
+        for (int u = 0; u < kSolvePf; ++u) {
+            const int j = u;
+            lq[u] = (lane < kBandKL && j + 1 + lane < n) ? BAND(j + 1 + lane, j) : T(0);
+            pq[u] = j < n ? piv[j] : j;
         }
-        __syncwarp();
-        const T zj = z[j];
-        const int i = j + 1 + lane;
-        if (lane < kBandKL && i < n) z[i] -= BAND(i, j) * zj;
-        __syncwarp();
+        for (int jb = 0; jb < n; jb += kSolvePf) {
+            T ln[kSolvePf];
+            int pn[kSolvePf];
+#pragma unroll
+            for (int u = 0; u < kSolvePf; ++u) {
+                const int j = jb + kSolvePf + u;
+                ln[u] = (lane < kBandKL && j + 1 + lane < n) ? BAND(j + 1 + lane, j) : T(0);
+                pn[u] = j < n ? piv[j] : j;
+            }
+#pragma unroll
+            for (int u = 0; u < kSolvePf; ++u) {
+                const int j = jb + u;
+                if (j < n) {
+                    // row j after the interchange with row p (p in j .. j+8): every lane
+                    // reads both entries; the lane of row p takes the old z_j as its own
+                    // entry; z_j itself is stored one row later, when no lane reads it
+                    const int p = pq[u];
+                    const T zold = z[j], zp = z[p];
+                    const T zj = (p != j) ? zp : zold;
+                    const int i = j + 1 + lane;
+                    if (lane < kBandKL && i < n) z[i] = ((i == p) ? zold : z[i]) - lq[u] * zj;
+                    if (lane == 0) {
+                        if (j > 0) z[j - 1] = zprev;
+                        zprev = zj;
+                    }
+                    __syncwarp();
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kSolvePf; ++u) {
+                lq[u] = ln[u];
+                pq[u] = pn[u];
+            }
+        }
     }
+    if (lane == 0) z[n - 1] = zprev;
+    __syncwarp();
     // backward, column by column: z_j *= 1/U_jj (stored reciprocal), then the
-    // kl + ku rows above take their U_ij z_j; two FP64 instructions per column
-    for (int j = n - 1; j >= 0; --j) {
-        const T zj = z[j] * BAND(j, j);
-        __syncwarp();                       // every lane has read z_j
-        const int i = j - 1 - lane;
-        if (lane < kBandKL + kBandKU && i >= 0) z[i] -= BAND(i, j) * zj;
-        if (lane == 0) z[j] = zj;
-        __syncwarp();
+    // kl + ku rows above take their U_ij z_j
+    {
+        T uq[kSolvePf], dq[kSolvePf];
+#pragma unroll
+        for (int u = 0; u < kSolvePf; ++u) {
+            const int j = n - 1 - u;
+            uq[u] = (lane < kBandKL + kBandKU && j - 1 - lane >= 0) ? BAND(j - 1 - lane, j) : T(0);
+            dq[u] = j >= 0 ? BAND(j, j) : T(0);
+        }
+        for (int jb = n - 1; jb >= 0; jb -= kSolvePf) {
+            T un[kSolvePf], dn[kSolvePf];
+#pragma unroll
+            for (int u = 0; u < kSolvePf; ++u) {
+                const int j = jb - kSolvePf - u;
+                un[u] = (lane < kBandKL + kBandKU && j - 1 - lane >= 0) ? BAND(j - 1 - lane, j)
+                                                                         : T(0);
+                dn[u] = j >= 0 ? BAND(j, j) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < kSolvePf; ++u) {
+                const int j = jb - u;
+                if (j >= 0) {
+                    const T zj = z[j] * dq[u];
+                    const int i = j - 1 - lane;
+                    if (lane < kBandKL + kBandKU && i >= 0) z[i] -= uq[u] * zj;
+                    if (lane == 0) {
+                        if (j < n - 1) z[j + 1] = zprev;
+                        zprev = zj;
+                    }
+                    __syncwarp();
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kSolvePf; ++u) {
+                uq[u] = un[u];
+                dq[u] = dn[u];
+            }
+        }
     }
+    if (lane == 0) z[0] = zprev;
+    __syncwarp();
     // scatter back: u_s, Lam_j, and Y_1 = b1 + c_t Lam_0
     for (int e = lane; e < 3 * N; e += 32) {
         const int s = e / 3, r = e % 3;
@@ -258,8 +373,6 @@ __global__ void to_float_kernel(int64_t n, const double *__restrict__ a, float *
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
 }
-
-constexpr int kJ0Threads = 128;
 
 J0Params make_params(const fil_ctx *c) {
     const double beta = c->have_prev ? 2.0 / 3.0 : 1.0;
