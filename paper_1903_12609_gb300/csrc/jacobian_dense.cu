@@ -42,6 +42,9 @@
 #include "quat.cuh"
 #include "rpy_pair.cuh"
 
+#ifndef FIL_GEMV_ROWS
+#define FIL_GEMV_ROWS 4   // rows per warp in flight in the streamed inverse apply
+#endif
 #ifndef FIL_GJ_ROWS
 #define FIL_GJ_ROWS 0     // 1: the row-distributed register Gauss-Jordan (comparison)
 #endif
@@ -514,16 +517,31 @@ __device__ void residual_mf_cta(const AuxView &g, int N, const DenseParams &dp,
 
 // x (+)= Inv r for one filament, Inv (n x n, row-major) and r in shared
 // memory: warp per row, lanes stride the columns (conflict-free).
+// Each warp takes kGemvRows rows at a time, so that a lane has the loads of
+// several rows in flight; every row is summed in the same order as one row
+// at a time (lane-strided FMAs, then a butterfly over the lanes).
+template <int kGemvRows = 4>
 __device__ __forceinline__ void inv_gemv_cta(const float *Inv, const float *r, double *x, int n,
                                              bool accumulate) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = wid; i < n; i += nw) {
-        const float *row = Inv + (int64_t)i * n;
-        float t = 0.f;
-        for (int c = lane; c < n; c += 32) t = fmaf(row[c], r[c], t);
+    for (int i0 = wid * kGemvRows; i0 < n; i0 += nw * kGemvRows) {
+        float t[kGemvRows];
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
-        if (lane == 0) x[i] = accumulate ? x[i] + (double)t : (double)t;
+        for (int u = 0; u < kGemvRows; ++u) t[u] = 0.f;
+#pragma unroll 2
+        for (int c = lane; c < n; c += 32) {
+            const float rc = r[c];
+#pragma unroll
+            for (int u = 0; u < kGemvRows; ++u)
+                if (i0 + u < n) t[u] = fmaf(Inv[(int64_t)(i0 + u) * n + c], rc, t[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kGemvRows; ++u) {
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) t[u] += __shfl_xor_sync(0xffffffffu, t[u], d);
+            if (lane == 0 && i0 + u < n) x[i0 + u] = accumulate ? x[i0 + u] + (double)t[u]
+                                                               : (double)t[u];
+        }
     }
 }
 
@@ -544,7 +562,7 @@ j0_apply_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
     const double *bg = b + 6 * (int64_t)s0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = (float)bg[i];
     __syncthreads();
-    inv_gemv_cta(inv_all + jofs[f], rs, x + 6 * (int64_t)s0, n, false);
+    inv_gemv_cta<FIL_GEMV_ROWS>(inv_all + jofs[f], rs, x + 6 * (int64_t)s0, n, false);
 }
 
 // J0 solve, one CTA per filament with its FP32 inverse staged in shared
