@@ -160,7 +160,7 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->d_flags = sb ? reinterpret_cast<int *>(sb) : nullptr;
     c->d_finf = sb ? reinterpret_cast<unsigned long long *>(sb + 16) : nullptr;
     if (c->j0_model == FIL_J0_DRAG) {
-        c->band = ar.take<double>((size_t)nband * kBandW);
+        c->band = c->prec == FIL_MIXED ? nullptr : ar.take<double>((size_t)nband * kBandW);
         c->band32 = c->prec == FIL_MIXED ? ar.take<float>((size_t)nband * kBandW) : nullptr;
         c->jinv = nullptr;
         c->jofs = nullptr;

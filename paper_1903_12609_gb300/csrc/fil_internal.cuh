@@ -138,7 +138,7 @@ struct fil_ctx {
     // (filament RPY mobility); piv holds 6S pivots (band rows use 6S - 3M)
     int j0_model;
     double *band;
-    float *band32;         // FP32 copy of the band, factored in place (mixed precision)
+    float *band32;         // the band in FP32, factored in place (mixed precision; band unused)
     int *piv;
     float *jinv;           // per filament: FP32 J0, then its inverse in place
     int64_t *jofs;         // [M+1] offsets of the (6N)^2 blocks

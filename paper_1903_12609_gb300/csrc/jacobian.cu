@@ -30,7 +30,8 @@
 namespace fil {
 namespace {
 
-__device__ __forceinline__ void put_block(double *band, int64_t row_block, int64_t col_block,
+template <typename TO>
+__device__ __forceinline__ void put_block(TO *band, int64_t row_block, int64_t col_block,
                                           const M33 &B) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -38,23 +39,25 @@ __device__ __forceinline__ void put_block(double *band, int64_t row_block, int64
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
             const int64_t col = 3 * col_block + cc;
-            band[i * kBandW + (col - i + kBandKL)] = B.m[3 * r + cc];
+            band[i * kBandW + (col - i + kBandKL)] = (TO)B.m[3 * r + cc];
         }
     }
 }
 
-// Assemble the band of each filament (one warp per filament).
+// Assemble the band of each filament (one warp per filament), computed in
+// FP64 and stored in the precision TO of the factors.
+template <typename TO>
 __global__ void j0_build_kernel(Layout lay, const double *__restrict__ X,
                                 const double *__restrict__ qc, const double *__restrict__ Tint,
-                                J0Params p, double *__restrict__ band_all) {
+                                J0Params p, TO *__restrict__ band_all) {
     const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= lay.M) return;
     const int s0 = lay.off[warp];
     const int N = lay.off[warp + 1] - s0;
     const int64_t nrow = 6 * (int64_t)N - 3;
-    double *band = band_all + (6 * (int64_t)s0 - 3 * (int64_t)warp) * kBandW;
-    for (int64_t i = lane; i < nrow * kBandW; i += 32) band[i] = 0.0;
+    TO *band = band_all + (6 * (int64_t)s0 - 3 * (int64_t)warp) * kBandW;
+    for (int64_t i = lane; i < nrow * kBandW; i += 32) band[i] = TO(0);
     __syncwarp();
     const double *Xf = X + 6 * (int64_t)s0;
     const double *Lam = Xf + 3 + 3 * N;
@@ -369,10 +372,6 @@ __global__ void band_solve_kernel(Layout lay, const T *__restrict__ band_all,
 #undef BAND
 }
 
-__global__ void to_float_kernel(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (float)a[i];
-}
 
 J0Params make_params(const fil_ctx *c) {
     const double beta = c->have_prev ? 2.0 / 3.0 : 1.0;
@@ -386,22 +385,21 @@ J0Params make_params(const fil_ctx *c) {
 cudaError_t j0_build_factor(fil_ctx *c, const double *X) {
     const unsigned grid = (unsigned)(((int64_t)c->lay.M * 32 + kJ0Threads - 1) / kJ0Threads);
     const J0Params p = make_params(c);
-    j0_build_kernel<<<grid, kJ0Threads, 0, c->stream>>>(c->lay, X, c->qc, c->Tint, p, c->band);
     if (c->band32) {
-        // mixed precision: factors and solves in FP32 (J0 is an approximation of
-        // the Jacobian far coarser than FP32 rounding; FP64 issues at 1/64 of the
-        // FP32 rate on this GPU)
-        const int64_t ne = (6 * c->lay.S - 3 * (int64_t)c->lay.M) * kBandW;
-        to_float_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>(ne, c->band,
-                                                                            c->band32);
+        // mixed precision: the band is stored, factored and solved in FP32 (J0 is an
+        // approximation of the Jacobian far coarser than FP32 rounding; FP64 issues at
+        // 1/64 of the FP32 rate on this GPU); its entries are still computed in FP64
+        j0_build_kernel<float><<<grid, kJ0Threads, 0, c->stream>>>(c->lay, X, c->qc, c->Tint, p,
+                                                                   c->band32);
         band_lu_kernel<float><<<grid, kJ0Threads, 0, c->stream>>>(c->lay, c->band32, c->piv,
                                                                   c->d_flags);
-        c->n_launches += 3;
     } else {
+        j0_build_kernel<double><<<grid, kJ0Threads, 0, c->stream>>>(c->lay, X, c->qc, c->Tint, p,
+                                                                    c->band);
         band_lu_kernel<double><<<grid, kJ0Threads, 0, c->stream>>>(c->lay, c->band, c->piv,
                                                                    c->d_flags);
-        c->n_launches += 2;
     }
+    c->n_launches += 2;
     return cudaGetLastError();
 }
 
