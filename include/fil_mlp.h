@@ -3,7 +3,7 @@
  * step's unknowns X = (Y_1, u, Lambda) of a 32-segment filament (the initial
  * guess of the implicit step, which the paper extrapolates from past steps,
  * Sec. 3.3). The network and its training are not part of the paper; the
- * plain solve stays the judge: fil_step starts from whichever of the
+ * plain solve keeps the last word: fil_step starts from whichever of the
  * prediction and the extrapolation has the smaller residual and converges to
  * the same tolerance either way.
  *

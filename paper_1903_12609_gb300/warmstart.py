@@ -4,8 +4,8 @@ the library's tensor-core kernels, and loading a trained network into a
 solver context.
 
 The network corrects the extrapolated initial guess X_0 of each 32-segment
-filament (in the filament's own frame); inside fil_step the plain solve stays
-the judge (the start with the smaller residual is kept and a failed start
+filament (in the filament's own frame); inside fil_step the plain solve keeps
+the last word (the start with the smaller residual is kept and a failed start
 from the prediction is restarted from the extrapolation), so every step
 converges to the same tolerance with or without it.
 

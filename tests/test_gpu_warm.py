@@ -130,7 +130,7 @@ def test_zero_network_reproduces_the_plain_solve(fil, mode):
     np.testing.assert_array_equal(Y[True], Y[False])
 
 
-def test_prediction_is_assembled_and_judged(fil):
+def test_prediction_is_assembled_and_compared(fil):
     """A network whose output is a constant correction: X_pred = X_ex + R1 y,
     f(X_pred) as the oracle evaluates it, and the start with the smaller
     ||f||_inf is kept."""
