@@ -112,8 +112,16 @@ def cpu_baseline(Y, FT, seconds=10.0):
     t0 = time.perf_counter()
     rpy.apply_rows(Y, FT, rows, nthreads=cores)
     dt = time.perf_counter() - t0
+    # the same oracle on one thread, on a sample 1/cores the size (about as long)
+    n1 = max(16, n // cores)
+    rows1 = np.linspace(0, S - 1, n1).astype(np.int32)
+    t0 = time.perf_counter()
+    rpy.apply_rows(Y, FT, rows1, nthreads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": n * S / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d target rows x %d sources of one mobility apply (%.1f s)" % (n, S, dt)}
+            "sample": "%d target rows x %d sources of one mobility apply (%.1f s)" % (n, S, dt),
+            "single_thread": {"value": n1 * S / dt1, "cores": 1,
+                              "sample": "%d target rows x %d sources (%.1f s)" % (n1, S, dt1)}}
 
 
 def counters_from_profile():
