@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import filament as fo  # noqa: E402
 from paper_1903_12609_gb300.inputs import (random_frames, single_filament,  # noqa: E402
-                                           workload_params)
+                                           suspension, workload_params)
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +56,41 @@ def _gpu(fil, lay, p, st, ext, prec=0, j0=0):
 
 
 SEGS = [[20], [1, 5, 33], [32] * 6, [40, 65, 2, 1]]
+
+
+def test_full_size_residual_on_sampled_filaments(fil):
+    """The 32 000-segment suspension (1000 x 32, its physics and external loads),
+    FP64 path: the residual rows of sampled filaments against the oracle. The
+    oracle evaluates the mobility on those filaments' rows only (sources: all
+    32 000 segments); everything else it computes for the whole system."""
+    from oracle import rpy
+    wl, base, t, mu, Fext, follower = suspension(1000, 32, seed=0)
+    lay = fo.Layout([32] * 1000)
+    p = fo.Params(a=wl.a, eta=wl.eta, dL=wl.dL, KB=wl.KB, KT=wl.KT, dt=wl.dt, tol=wl.tol,
+                  max_iter=wl.max_iter)
+    st = fo.initial_state(lay, p, base, t, mu)
+    ext = fo.External(Fext=Fext, follower=follower)
+    rng = np.random.default_rng(7)
+    X = fo.initial_guess(lay, st)
+    X = X + 1e-3 * rng.standard_normal(X.shape)
+    fils = [0, 1, 499, 500, 998, 999] + list(rng.choice(np.arange(2, 998), 6, replace=False))
+    rows = np.concatenate([np.arange(32 * i, 32 * i + 32) for i in fils]).astype(np.int32)
+
+    def sampled_mobility(Y, F, T, p, nthreads=1):
+        V = np.zeros_like(Y)
+        W = np.zeros_like(Y)
+        VW = rpy.apply_rows(Y, np.concatenate([F, T], axis=1), rows, p.a, p.eta, nthreads=8)
+        V[rows], W[rows] = VW[:, :3], VW[:, 3:]
+        return V, W
+
+    ref = fo.residual(lay, p, st, ext, X, mob=sampled_mobility)
+    with _gpu(fil, lay, p, st, ext) as m:
+        f = np.zeros(6 * lay.S)
+        m.residual(X, f)
+    scale = max(1.0, np.abs(st.Y).max())
+    for i in fils:
+        b = lay.off_X[i]
+        np.testing.assert_allclose(f[b:b + 6 * 32], ref[b:b + 6 * 32], rtol=0, atol=1e-12 * scale)
 
 
 @pytest.mark.parametrize("segs", SEGS)
