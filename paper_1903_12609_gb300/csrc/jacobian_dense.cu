@@ -124,6 +124,13 @@ __device__ __forceinline__ PairCoef32 pair_coef32(float dx, float dy, float dz, 
     return k;
 }
 
+// Separation component of segments i, j from positions relative to segment 0
+// split into FP32 hi + lo parts: the hi difference is exact for nearby
+// segments, so d carries the rounding of d itself, not of |Y - Y_0|.
+__device__ __forceinline__ float dif_hl(const float *h, const float *l, int i, int j) {
+    return __fadd_rn(__fsub_rn(h[i], h[j]), __fsub_rn(l[i], l[j]));
+}
+
 // FP64 work per filament (one CTA per filament). fast (the mixed mode, whose
 // J0 is used only through its FP32 assembly): the two N^2 loops -- pair
 // coefficients and the angular velocity of the internal loads -- in FP32.
@@ -132,15 +139,16 @@ j0_precompute_kernel(Layout lay, const int64_t *__restrict__ auxofs, const doubl
                      const double *__restrict__ qc, const double *__restrict__ Yc,
                      const double *__restrict__ Tint, DenseParams dp, double *__restrict__ aux_all,
                      int fast) {
-    // F_int 3N | Yrel 3N (doubles), then for fast: Y 3N | F_int 3N | T_int 3N | pc 5N^2 (floats)
+    // F_int 3N | Yrel 3N (doubles), then for fast: Y hi 3N | Y lo 3N | F_int 3N | T_int 3N |
+    // pc 5N^2 (floats)
     extern __shared__ double sm[];
     const int f = blockIdx.x;
     const int s0 = lay.off[f];
     const int N = lay.off[f + 1] - s0;
     AuxView g = aux_view(aux_all + auxofs[f], N);
     double *Fi = sm, *Yf = sm + 3 * N;
-    float *Y32 = reinterpret_cast<float *>(sm + 6 * N), *F32 = Y32 + 3 * N, *T32 = F32 + 3 * N,
-          *pc32 = T32 + 3 * N;
+    float *Y32 = reinterpret_cast<float *>(sm + 6 * N), *Yl32 = Y32 + 3 * N, *F32 = Yl32 + 3 * N,
+          *T32 = F32 + 3 * N, *pc32 = T32 + 3 * N;
     const double *Xf = X + 6 * (int64_t)s0;
     const double *Lam = Xf + 3 + 3 * N;
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
@@ -166,7 +174,9 @@ j0_precompute_kernel(Layout lay, const int64_t *__restrict__ auxofs, const doubl
     __syncthreads();
     if (fast) {
         for (int e = threadIdx.x; e < 3 * N; e += blockDim.x) {
-            Y32[e] = (float)(Yf[e] - Yf[e % 3]);          // relative to segment 0
+            const double yr = Yf[e] - Yf[e % 3];         // relative to segment 0
+            Y32[e] = (float)yr;
+            Yl32[e] = (float)(yr - (double)Y32[e]);
             F32[e] = (float)Fi[e];
             T32[e] = (float)Tint[3 * (int64_t)s0 + e];
         }
@@ -175,8 +185,9 @@ j0_precompute_kernel(Layout lay, const int64_t *__restrict__ auxofs, const doubl
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
             const int n = e / N, m = e - (e / N) * N;
             if (m < n) continue;
-            const PairCoef32 k = pair_coef32(Y32[3 * n] - Y32[3 * m], Y32[3 * n + 1] - Y32[3 * m + 1],
-                                             Y32[3 * n + 2] - Y32[3 * m + 2], a32);
+            const PairCoef32 k = pair_coef32(dif_hl(Y32, Yl32, 3 * n, 3 * m),
+                                             dif_hl(Y32, Yl32, 3 * n + 1, 3 * m + 1),
+                                             dif_hl(Y32, Yl32, 3 * n + 2, 3 * m + 2), a32);
             const float v[5] = {k.A, k.B, k.C, k.D, k.G};
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
@@ -200,8 +211,9 @@ j0_precompute_kernel(Layout lay, const int64_t *__restrict__ auxofs, const doubl
             if (n < N) {
                 for (int m = sub; m < N; m += 8) {
                     const float *pc = pc32 + 5 * (n * N + m);
-                    const float dx = Y32[3 * n] - Y32[3 * m], dy = Y32[3 * n + 1] - Y32[3 * m + 1],
-                                dz = Y32[3 * n + 2] - Y32[3 * m + 2];
+                    const float dx = dif_hl(Y32, Yl32, 3 * n, 3 * m),
+                                dy = dif_hl(Y32, Yl32, 3 * n + 1, 3 * m + 1),
+                                dz = dif_hl(Y32, Yl32, 3 * n + 2, 3 * m + 2);
                     const float vx = F32[3 * m], vy = F32[3 * m + 1], vz = F32[3 * m + 2];
                     const float wx = T32[3 * m], wy = T32[3 * m + 1], wz = T32[3 * m + 2];
                     // Omega += G (v x d) + C w + D (d.w) d
@@ -301,13 +313,13 @@ __device__ __forceinline__ F3 mcol(const float *m9, int c) { return {m9[c], m9[3
 __global__ void __launch_bounds__(kAsmThreads)
 j0_assemble32_kernel(Layout lay, const int64_t *__restrict__ jofs,
                      const int64_t *__restrict__ auxofs, DenseParams dp, const double *__restrict__ aux_all, float *__restrict__ J_all) {
-    extern __shared__ float smf[];     // pc 5N^2 | Yrel 3N | t 3N | A, Du, dT, Da, Db 45N
+    extern __shared__ float smf[];     // pc 5N^2 | Yrel hi 3N | lo 3N | t 3N | A, Du, dT, Da, Db 45N
     const int f = blockIdx.x;
     const int s0 = lay.off[f];
     const int N = lay.off[f + 1] - s0;
     const int n6 = 6 * N;
     const AuxView g = aux_view(const_cast<double *>(aux_all) + auxofs[f], N);
-    float *pcs = smf, *Ys = smf + 5 * N * N, *ts = Ys + 3 * N, *m32 = ts + 3 * N;
+    float *pcs = smf, *Ys = smf + 5 * N * N, *Yl = Ys + 3 * N, *ts = Yl + 3 * N, *m32 = ts + 3 * N;
     float *A32 = m32, *Du32 = m32 + 9 * N, *dT32 = m32 + 18 * N, *Da32 = m32 + 27 * N,
           *Db32 = m32 + 36 * N;
     float *J = J_all + jofs[f];
@@ -315,7 +327,9 @@ j0_assemble32_kernel(Layout lay, const int64_t *__restrict__ jofs,
     for (int e = threadIdx.x; e < 5 * N * N; e += blockDim.x) pcs[e] = (float)g.pc[e];
     for (int e = threadIdx.x; e < 45 * N; e += blockDim.x) m32[e] = (float)g.A[e];   // A..Db
     for (int e = threadIdx.x; e < 3 * N; e += blockDim.x) {
-        Ys[e] = (float)(Y0[e] - Y0[e % 3]);     // positions relative to segment 0
+        const double yr = Y0[e] - Y0[e % 3];    // positions relative to segment 0, hi + lo
+        Ys[e] = (float)yr;
+        Yl[e] = (float)(yr - (double)Ys[e]);
         ts[e] = (float)g.t[e];
     }
     for (int64_t e = threadIdx.x; e < (int64_t)n6 * n6; e += blockDim.x) J[e] = 0.f;
@@ -326,7 +340,6 @@ j0_assemble32_kernel(Layout lay, const int64_t *__restrict__ jofs,
     for (int task = threadIdx.x; task < N * ncol; task += blockDim.x) {
         const int n = task / ncol;
         const int x = task - n * ncol;
-        const F3 Yn = f3v(Ys[3 * n], Ys[3 * n + 1], Ys[3 * n + 2]);
         F3 MV[3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         F3 MW[3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         int colX;
@@ -339,7 +352,8 @@ j0_assemble32_kernel(Layout lay, const int64_t *__restrict__ jofs,
                 // d T_m / d u_k: Db(k-1) for m = k-1, dT_k for m = k, -Da(k) for m = k+1
                 const float *Gt = (mm == -1) ? Db32 + 9 * (k - 1) : (mm == 0) ? dT32 + 9 * k : Da32 + 9 * k;
                 const float sg = (mm == 1) ? -1.f : 1.f;
-                const F3 d = f3v(Yn.x - Ys[3 * m], Yn.y - Ys[3 * m + 1], Yn.z - Ys[3 * m + 2]);
+                const F3 d = f3v(dif_hl(Ys, Yl, 3 * n, 3 * m), dif_hl(Ys, Yl, 3 * n + 1, 3 * m + 1),
+                                 dif_hl(Ys, Yl, 3 * n + 2, 3 * m + 2));
                 const float *c5 = pcs + 5 * (n * N + m);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -356,7 +370,8 @@ j0_assemble32_kernel(Layout lay, const int64_t *__restrict__ jofs,
                 const int m = j + mm;
                 const F3 tm = f3v(ts[3 * m], ts[3 * m + 1], ts[3 * m + 2]);
                 const float sF = mm == 0 ? 1.f : -1.f;
-                const F3 d = f3v(Yn.x - Ys[3 * m], Yn.y - Ys[3 * m + 1], Yn.z - Ys[3 * m + 2]);
+                const F3 d = f3v(dif_hl(Ys, Yl, 3 * n, 3 * m), dif_hl(Ys, Yl, 3 * n + 1, 3 * m + 1),
+                                 dif_hl(Ys, Yl, 3 * n + 2, 3 * m + 2));
                 const float *c5 = pcs + 5 * (n * N + m);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -1127,7 +1142,7 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
     const int N = c->lay.maxN;
     const int fast = c->prec == FIL_MIXED ? 1 : 0;
     const size_t smem_pre = (size_t)6 * N * sizeof(double) +
-                            (fast ? (size_t)(9 * N + 5 * N * N) * sizeof(float) : 0);
+                            (fast ? (size_t)(12 * N + 5 * N * N) * sizeof(float) : 0);
     if (smem_pre > 48 * 1024) {
         cudaError_t ea = cudaFuncSetAttribute(j0_precompute_kernel,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1136,7 +1151,7 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
     }
     j0_precompute_kernel<<<c->lay.M, kAsmThreads, smem_pre, c->stream>>>(
         c->lay, c->auxofs, X, c->qc, c->Yc, c->Tint, dp, c->aux, fast);
-    const size_t smem_asm = (size_t)(5 * N * N + 51 * N) * sizeof(float);
+    const size_t smem_asm = (size_t)(5 * N * N + 54 * N) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(j0_assemble32_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_asm);

@@ -93,6 +93,63 @@ def test_full_size_residual_on_sampled_filaments(fil):
         np.testing.assert_allclose(f[b:b + 6 * 32], ref[b:b + 6 * 32], rtol=0, atol=1e-12 * scale)
 
 
+def _subsystem(lay, st, X, fils):
+    """The filaments `fils` of a system as a system of their own (state and X
+    sliced; per-filament quantities such as J0 blocks do not depend on the rest)."""
+    sub = fo.Layout([lay.N[i] for i in fils])
+    seg = np.concatenate([np.arange(lay.off_seg[i], lay.off_seg[i] + lay.N[i]) for i in fils])
+    lam_rows = np.concatenate([np.arange(lay.off_seg[i] - i, lay.off_seg[i] - i + lay.N[i] - 1)
+                               for i in fils])
+    xs = np.concatenate([X[lay.off_X[i]:lay.off_X[i] + 6 * lay.N[i]] for i in fils])
+
+    def cut(a, rows):
+        return None if a is None else a[rows].copy()
+    st_sub = fo.State(Y=st.Y[seg].copy(), q=st.q[seg].copy(), Yprev=cut(st.Yprev, seg),
+                      u=cut(st.u, seg), lam=cut(st.lam, lam_rows), steps=st.steps)
+    return sub, st_sub, xs
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_j0_solve_on_sampled_filaments(fil, prec):
+    """The 32 000-segment suspension with the filament-RPY J0 (the bench's
+    configuration): J0^{-1} b on sampled filaments against the oracle's dense
+    LU of the same blocks, FP64 path to 1e-10. The mixed path assembles and
+    inverts J0 in FP32 with no refinement; its normwise backward error against
+    the oracle's blocks, |B x - b|_inf / (|B|_inf |x|_inf + |b|_inf) per block,
+    is bounded by 2 n u_32 (n = 6N = 192: an FP32 Gauss-Jordan inverse, and an
+    assembly whose entries sum at most n products), independent of cond(B)."""
+    wl, base, t, mu, Fext, follower = suspension(1000, 32, seed=0)
+    lay = fo.Layout([32] * 1000)
+    p = fo.Params(a=wl.a, eta=wl.eta, dL=wl.dL, KB=wl.KB, KT=wl.KT, dt=wl.dt, tol=wl.tol,
+                  max_iter=wl.max_iter)
+    st = fo.initial_state(lay, p, base, t, mu)
+    ext = fo.External(Fext=Fext, follower=follower)
+    rng = np.random.default_rng(8)
+    fils = [0, 999] + list(rng.choice(np.arange(1, 999), 6, replace=False))
+    b = rng.standard_normal(6 * lay.S)
+    with _gpu(fil, lay, p, st, ext, prec=prec, j0=1) as m:
+        m.broyden_begin()
+        X0 = np.zeros(6 * lay.S)
+        m.get_iterate(X0, None)
+        x = np.zeros_like(b)
+        m.j0_solve(b, x)
+    np.testing.assert_allclose(X0, fo.initial_guess(lay, st), rtol=0, atol=1e-12)
+    sub, st_sub, X0_sub = _subsystem(lay, st, X0, fils)
+    blocks = fo.jacobian0_general(sub, p, st_sub, X0_sub, "rpy")
+    b_sub = np.concatenate([b[lay.off_X[i]:lay.off_X[i] + 192] for i in fils])
+    ref = fo.J0Solver(sub, blocks).solve(b_sub)
+    got = np.concatenate([x[lay.off_X[i]:lay.off_X[i] + 192] for i in fils])
+    if prec == 0:
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+    else:
+        u32 = 2.0 ** -24
+        for B, o in zip(blocks, sub.off_X):
+            xi, bi = got[o:o + 192], b_sub[o:o + 192]
+            eta = np.abs(B @ xi - bi).max() / (np.abs(B).sum(axis=1).max() * np.abs(xi).max()
+                                                + np.abs(bi).max())
+            assert eta <= 2 * 192 * u32, eta
+
+
 @pytest.mark.parametrize("segs", SEGS)
 @pytest.mark.parametrize("history", [False, True])
 def test_residual_parity(fil, segs, history):
