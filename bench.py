@@ -321,7 +321,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="timed steps of the plain FP64 form for comparison (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--j0", default="filament_rpy", choices=["filament_rpy", "drag"],
                     help="approximate Jacobian: filament RPY blocks (default) or App. B.2 drag")
     ap.add_argument("--n-fil", type=int, default=1000,
@@ -461,10 +461,11 @@ def main():
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    e2e_iters = []
     e0.record(stream)
     for _ in range(args.e2e_steps):
         m.set_state(Yh, qh, Yph, uh, lh)
-        m.step()
+        e2e_iters.append(m.step())
         m.get_state(Yh, qh, Yph, uh, lh)
     e1.record(stream)
     barrier()
@@ -570,6 +571,8 @@ def main():
         "autotuned": ({"tile": tuned[0], "ctas_per_sm": tuned[1], "ms_per_apply": tuned[2]}
                       if tuned else None),
         "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": UNIT,
+                "timesteps_per_s": args.e2e_steps / (e2e_ms * 1e-3),
+                "broyden_iters_per_step": float(np.mean(e2e_iters)) if e2e_iters else None,
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
                 "steps": args.e2e_steps},
         "gpu_launches": int(k1 - k0),
