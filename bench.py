@@ -453,25 +453,48 @@ def main():
     traffic = prof.get("dram_bytes_per_launch")
 
     # ---- end to end through the C ABI with host buffers ----
-    Yh = np.zeros((S, 3)); qh = np.zeros((S, 4)); Yph = np.zeros((S, 3)); uh = np.zeros((S, 3))
-    lh = np.zeros((S - n_fil, 3))
-    m.get_state(Yh, qh, Yph, uh, lh)
-    e2e_pairs = 0.0
-    a2, _, _ = m.counters()
+    # (a) a time-stepping user: every step copies its external loads in from pinned host
+    #     memory (fil_set_external) and the positions and orientations out (fil_get_state);
+    #     the solver's state and history stay on the device
+    Fh = torch.from_numpy(np.ascontiguousarray(Fext)).pin_memory()
+    fh = torch.from_numpy(np.ascontiguousarray(follower, dtype=np.float64)).pin_memory()
+    Yo = torch.empty((S, 3), dtype=torch.float64).pin_memory()
+    qo = torch.empty((S, 4), dtype=torch.float64).pin_memory()
     barrier()
+    a2, _, _ = m.counters()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e2e_iters = []
     e0.record(stream)
     for _ in range(args.e2e_steps):
-        m.set_state(Yh, qh, Yph, uh, lh)
+        m.set_external(Fh, None, fh)
         e2e_iters.append(m.step())
-        m.get_state(Yh, qh, Yph, uh, lh)
+        m.get_state(Yo, qo, None, None, None)
     e1.record(stream)
     barrier()
     a3, _, _ = m.counters()
     e2e_ms = e0.elapsed_time(e1)
     e2e_pairs = (a3 - a2) * float(S) * S
+    in_bytes = 8 * (Fh.numel() + fh.numel())
+    out_bytes = 8 * (Yo.numel() + qo.numel())
+    # (b) restarting every step from host arrays (fil_set_state, fil_step, fil_get_state):
+    #     the whole state goes both ways and the step history is lost at each restart
+    Yh = np.zeros((S, 3)); qh = np.zeros((S, 4)); Yph = np.zeros((S, 3)); uh = np.zeros((S, 3))
+    lh = np.zeros((S - n_fil, 3))
+    m.get_state(Yh, qh, Yph, uh, lh)
+    barrier()
+    a4, _, _ = m.counters()
+    r_iters = []
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        m.set_state(Yh, qh, Yph, uh, lh)
+        r_iters.append(m.step())
+        m.get_state(Yh, qh, Yph, uh, lh)
+    e1.record(stream)
+    barrier()
+    a5, _, _ = m.counters()
+    r_ms = e0.elapsed_time(e1)
+    r_pairs = (a5 - a4) * float(S) * S
     state_bytes = 8 * (Yh.size + qh.size + Yph.size + uh.size + lh.size)
 
     # ---- learned warm start vs extrapolation, both from the state before the timed steps ----
@@ -571,10 +594,20 @@ def main():
         "autotuned": ({"tile": tuned[0], "ctas_per_sm": tuned[1], "ms_per_apply": tuned[2]}
                       if tuned else None),
         "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes,
                 "timesteps_per_s": args.e2e_steps / (e2e_ms * 1e-3),
                 "broyden_iters_per_step": float(np.mean(e2e_iters)) if e2e_iters else None,
-                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
-                "steps": args.e2e_steps},
+                "steps": args.e2e_steps,
+                "what": "fil_set_external (pinned host loads in), fil_step, fil_get_state "
+                        "(positions and quaternions out), every step",
+                "restarted": {"value": r_pairs / (r_ms * 1e-3), "unit": UNIT,
+                              "h2d_bytes_per_step": state_bytes,
+                              "d2h_bytes_per_step": state_bytes,
+                              "timesteps_per_s": args.e2e_steps / (r_ms * 1e-3),
+                              "broyden_iters_per_step": (float(np.mean(r_iters))
+                                                         if r_iters else None),
+                              "what": "fil_set_state, fil_step, fil_get_state of the whole "
+                                      "state from / to host arrays, every step"}},
         "gpu_launches": int(k1 - k0),
         "clocks": clocks,
         "wall_s": t_wall,
