@@ -48,3 +48,39 @@ def test_two_rank_aggregate():
 def test_single_rank_is_identity():
     import bench
     assert bench.aggregate_ranks(7.0, 3.0, None, "cpu") == (7.0, 3.0)
+
+
+def _run_bench(args, env_extra=None):
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **(env_extra or {}))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py")] + args, cwd=root,
+                       env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference: the oracle on the host cores, one JSON line with
+    the suspension metric, a cpu_baseline describing the run and an e2e record
+    with no host-device traffic."""
+    import bench
+    (line,) = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1"])
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["higher_is_better"] is True and line["value"] > 0
+    assert line["steps"] == 1 and line["warmup"] == 1
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert isinstance(cb["sample"], str) and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    assert _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1"],
+                      {"RANK": "1", "WORLD_SIZE": "2"}) == []
