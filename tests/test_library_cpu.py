@@ -63,3 +63,16 @@ def test_oracle_library_builds():
     build.build()
     assert os.path.exists(build.lib_path("liboracle_rpy.so"))
     ctypes.CDLL(build.lib_path("liboracle_rpy.so"))
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: importing the binding with no library at the configured
+    path raises ImportError."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, FIL_LIBRARY=str(tmp_path / "missing" / "libfil.so"))
+    r = subprocess.run([sys.executable, "-c", "import paper_1903_12609_gb300.fil"], cwd=root,
+                       env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "libfil.so" in r.stderr
