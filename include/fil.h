@@ -70,9 +70,11 @@ typedef enum {
                                  in f_0; banded O(N) factorisation per filament     */
     FIL_J0_FILAMENT_RPY = 1   /* f_0 keeps every RPY block between segments of the
                                  same filament (inter-filament coupling and dM/dY
-                                 dropped); dense LU per filament. Reduces to
-                                 FIL_J0_DRAG when those blocks are cut to the self
-                                 term; far fewer Broyden iterations in dense
+                                 dropped); a dense 6N x 6N block per filament,
+                                 inverted in FP32 by Gauss-Jordan elimination (plus
+                                 one FP64 refinement per solve in FP64 mode); N <= 38.
+                                 Reduces to FIL_J0_DRAG when those blocks are cut to
+                                 the self term; far fewer Broyden iterations in dense
                                  suspensions                                         */
 } fil_j0_model;
 
