@@ -59,10 +59,16 @@ typedef enum {
 
 typedef enum {
     FIL_FP64 = 0,     /* every step in FP64, including the RPY pair sums       */
-    FIL_MIXED = 1     /* RPY pair sums in FP32 with per-target compensated
+    FIL_MIXED = 1,    /* RPY pair sums in FP32 with per-target compensated
                          accumulation; J0 factors / inverse and their solves
                          and the Broyden history (c_i, d_i of Algorithm 2) in
                          FP32; state, residual, iterates and norms in FP64     */
+    FIL_PAIR32 = 2    /* RPY pair sums in FP32 with per-target compensated
+                         accumulation (as FIL_MIXED); everything else as
+                         FIL_FP64: the Broyden history, its dot products and
+                         rank-one updates, the J0 factors and solves (the
+                         filament-RPY inverse with its FP64 refinement), the
+                         quaternion exponential map, state and residual      */
 } fil_precision;
 
 typedef enum {
@@ -230,7 +236,7 @@ fil_status fil_set_external(fil_ctx *c, const double *Fext, const double *Text,
  * the far form for r >= 2a and the equal-radius overlapping form for r < 2a
  * (r = 0 between distinct segments takes the self values). Y is S x 3, FT and
  * VW are S x 6. Precision follows the context (FP64, or FP32 pair sums with
- * compensated per-target accumulation). */
+ * compensated per-target accumulation in FIL_MIXED and FIL_PAIR32). */
 fil_status fil_mobility_apply(fil_ctx *c, const double *Y, const double *FT, double *VW);
 
 /* Residual f(X) of eqn RA-3d-system at X (6S), using the context's state
@@ -261,7 +267,8 @@ fil_status fil_get_iterate(fil_ctx *c, double *X, double *f);
 
 /* Apply the factored J0^{-1} of the current step to b (6S) -> x (6S): exact to
  * FP64 rounding in FP64 mode (dense model: FP32 inverse plus one FP64
- * refinement step, ~1e-14 relative). In mixed mode J0 is assembled and
+ * refinement step, ~1e-14 relative); FIL_PAIR32 solves as FIL_FP64. In
+ * FIL_MIXED mode J0 is assembled and
  * factored or inverted in FP32 without refinement: the normwise backward
  * error per filament block is O(6N) FP32 roundings (~1e-6 measured on the
  * stiff blocks of a 32-segment suspension filament; the forward error scales
@@ -315,13 +322,20 @@ fil_status fil_fma_peak(int32_t fp64, double *flops_per_s, double *sm_mhz);
  * It computes the same product as fil_mobility_apply of a FIL_MIXED context
  * (FP32 pair sums with compensated accumulation, FP64 results) for S =
  * n_seg segments with radius a and viscosity eta: Y (S x 3), FT (S x 6) and
- * VW (S x 6) must be DEVICE pointers, owned by the caller. It allocates
- * nothing: its scratch is a fixed static device array of about 10.6 MB in
- * the library, which every GPU that loads the library keeps until the
- * process exits. Limits: 1 <= n_seg <= 32768; larger sizes, host pointers or
- * non-positive a, eta return FIL_EINVAL; CUDA failures return FIL_ECUDA.
+ * VW (S x 6) must be DEVICE pointers of the current device (or managed
+ * memory), owned by the caller. It allocates nothing: its scratch is a fixed
+ * static device array of about 10.6 MB in the library, which every GPU that
+ * loads the library keeps until the process exits. Limits: 1 <= n_seg <=
+ * 32768; larger sizes, host pointers, pointers to another GPU's memory or
+ * non-positive a, eta return FIL_EINVAL; a failed launch returns FIL_ECUDA.
+ * The scratch holds the stream-K partial sums of up to 4 x 152 CTAs (the
+ * context path's grid on a 152-SM GB300); on a part with more SMs the grid is
+ * capped there and the results differ from fil_mobility_apply's in rounding.
  * The first call on a device looks up the array's device address for that
- * device (cudaGetSymbolAddress) and should come before any stream capture.
+ * device (cudaGetSymbolAddress) and should come before any stream capture;
+ * the address is kept for the life of the process, so the device's primary
+ * context must stay the one in use (no cudaDeviceReset, no other driver
+ * context on that device, between calls).
  * Work is enqueued on `stream` (a cudaStream_t, NULL for the legacy stream)
  * without synchronising. All calls share the one array and leave their
  * contents in it; calls whose executions overlap on the GPU (different

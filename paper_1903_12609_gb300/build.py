@@ -33,11 +33,9 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, extra_flags=(), libdir=None):
-    """Compile (if stale) and link; returns the path of libfil.so. libdir and
-    extra_flags let tile-shape sweeps build variants beside the default."""
-    LIBDIR = libdir or globals()["LIBDIR"]
-    LIB = os.path.join(LIBDIR, "libfil.so")
+def build(force=False, verbose=False, ptxas_info=False):
+    """Compile (if stale) and link; returns the path of libfil.so. ptxas_info
+    prints ptxas's register and shared-memory report of every kernel."""
     os.makedirs(LIBDIR, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "fil.h"))
@@ -48,7 +46,7 @@ def build(force=False, verbose=False, extra_flags=(), libdir=None):
         obj = os.path.join(LIBDIR, src.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [sp] + headers):
-            cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(extra_flags) + ["-c", sp, "-o", obj]
+            cmd = [nvcc()] + ARCH + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", sp, "-o", obj]
             jobs.append(cmd)
 
     def run(cmd):
@@ -70,5 +68,4 @@ def build(force=False, verbose=False, extra_flags=(), libdir=None):
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True,
-          extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [])
+    build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv)

@@ -123,7 +123,7 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->Tint = ar.take<double>(3 * S);
     c->VW = ar.take<double>(6 * S);
     c->Mh = nullptr;
-    if (c->prec == FIL_MIXED) {
+    if (pair32_on(c)) {
         c->src32 = ar.take<float4>((size_t)kRpyPairF4 * (c->Spad / 2));
         c->src64 = nullptr;
     } else {
@@ -137,7 +137,7 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->fn = ar.take<double>(nX);
     c->w = ar.take<double>(nX);
     c->g = ar.take<double>(nX);
-    if (c->prec == FIL_MIXED) {
+    if (fast_mixed(c)) {
         // mixed mode: the Broyden history in FP32 (half the bytes; its sums then
         // need no FP64 work per history vector)
         c->C32 = ar.take<float>((size_t)c->max_iter * nX);
@@ -160,8 +160,8 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->d_flags = sb ? reinterpret_cast<int *>(sb) : nullptr;
     c->d_finf = sb ? reinterpret_cast<unsigned long long *>(sb + 16) : nullptr;
     if (c->j0_model == FIL_J0_DRAG) {
-        c->band = c->prec == FIL_MIXED ? nullptr : ar.take<double>((size_t)nband * kBandW);
-        c->band32 = c->prec == FIL_MIXED ? ar.take<float>((size_t)nband * kBandW) : nullptr;
+        c->band = fast_mixed(c) ? nullptr : ar.take<double>((size_t)nband * kBandW);
+        c->band32 = fast_mixed(c) ? ar.take<float>((size_t)nband * kBandW) : nullptr;
         c->jinv = nullptr;
         c->jofs = nullptr;
         c->aux = nullptr;
@@ -286,7 +286,7 @@ fil_status fil_create_ensemble(const fil_params *p, int32_t n_sys, const int32_t
     }
     if (!(p->a > 0) || !(p->eta > 0) || !(p->dL > 0) || !(p->dt > 0) || !(p->tol > 0) ||
         !(p->KB >= 0) || !(p->KT >= 0) || p->max_iter < 1 ||
-        (p->precision != FIL_FP64 && p->precision != FIL_MIXED) ||
+        (p->precision != FIL_FP64 && p->precision != FIL_MIXED && p->precision != FIL_PAIR32) ||
         (p->j0_model != FIL_J0_DRAG && p->j0_model != FIL_J0_FILAMENT_RPY) ||
         !std::isfinite(p->gamma0) || !std::isfinite(p->kappa_mu) || !std::isfinite(p->kappa_nu))
         return FIL_EINVAL;

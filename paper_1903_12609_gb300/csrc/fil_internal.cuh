@@ -47,6 +47,14 @@ struct Layout {
 
 }  // namespace fil
 
+struct fil_ctx;
+namespace fil {
+// RPY pair sums in FP32 (FIL_MIXED, FIL_PAIR32) rather than FP64.
+inline bool pair32_on(const fil_ctx *c);
+// J0 factors, solves and the Broyden history in FP32 (FIL_MIXED only).
+inline bool fast_mixed(const fil_ctx *c);
+}  // namespace fil
+
 struct fil_ctx {
     // parameters
     fil::Layout lay;
@@ -197,6 +205,9 @@ struct fil_ctx {
 };
 
 namespace fil {
+
+inline bool pair32_on(const fil_ctx *c) { return c->prec != FIL_FP64; }
+inline bool fast_mixed(const fil_ctx *c) { return c->prec == FIL_MIXED; }
 
 // Launchers (all enqueue on c->stream and return a cudaError_t).
 cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,

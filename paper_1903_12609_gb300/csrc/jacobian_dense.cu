@@ -42,17 +42,12 @@
 #include "quat.cuh"
 #include "rpy_pair.cuh"
 
-#ifndef FIL_GEMV_ROWS
-#define FIL_GEMV_ROWS 4   // rows per warp in flight in the streamed inverse apply
-#endif
-#ifndef FIL_GJ_ROWS
-#define FIL_GJ_ROWS 0     // 1: the row-distributed register Gauss-Jordan (comparison)
-#endif
 
 namespace fil {
 namespace {
 
 constexpr int kAsmThreads = 256;
+constexpr int kGemvRows = 4;   // rows per warp in flight in the streamed inverse apply
 constexpr int kInvThreads = 512;
 constexpr int kMaxInvN = 6 * kMaxDenseSeg;   // rows of the largest inverted block
 
@@ -535,23 +530,23 @@ __device__ void residual_mf_cta(const AuxView &g, int N, const DenseParams &dp,
 // Each warp takes kGemvRows rows at a time, so that a lane has the loads of
 // several rows in flight; every row is summed in the same order as one row
 // at a time (lane-strided FMAs, then a butterfly over the lanes).
-template <int kGemvRows = 4>
+template <int ROWS = kGemvRows>
 __device__ __forceinline__ void inv_gemv_cta(const float *Inv, const float *r, double *x, int n,
                                              bool accumulate) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i0 = wid * kGemvRows; i0 < n; i0 += nw * kGemvRows) {
-        float t[kGemvRows];
+    for (int i0 = wid * ROWS; i0 < n; i0 += nw * ROWS) {
+        float t[ROWS];
 #pragma unroll
-        for (int u = 0; u < kGemvRows; ++u) t[u] = 0.f;
+        for (int u = 0; u < ROWS; ++u) t[u] = 0.f;
 #pragma unroll 2
         for (int c = lane; c < n; c += 32) {
             const float rc = r[c];
 #pragma unroll
-            for (int u = 0; u < kGemvRows; ++u)
+            for (int u = 0; u < ROWS; ++u)
                 if (i0 + u < n) t[u] = fmaf(Inv[(int64_t)(i0 + u) * n + c], rc, t[u]);
         }
 #pragma unroll
-        for (int u = 0; u < kGemvRows; ++u) {
+        for (int u = 0; u < ROWS; ++u) {
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) t[u] += __shfl_xor_sync(0xffffffffu, t[u], d);
             if (lane == 0 && i0 + u < n) x[i0 + u] = accumulate ? x[i0 + u] + (double)t[u]
@@ -577,7 +572,7 @@ j0_apply_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
     const double *bg = b + 6 * (int64_t)s0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = (float)bg[i];
     __syncthreads();
-    inv_gemv_cta<FIL_GEMV_ROWS>(inv_all + jofs[f], rs, x + 6 * (int64_t)s0, n, false);
+    inv_gemv_cta<kGemvRows>(inv_all + jofs[f], rs, x + 6 * (int64_t)s0, n, false);
 }
 
 // J0 solve, one CTA per filament with its FP32 inverse staged in shared
@@ -739,177 +734,11 @@ gauss_jordan_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
         for (int c = lane; c < n; c += 32) out[(int64_t)i * n + pos[c]] = Asm[i * ld + c];
 }
 
-// Register-resident Gauss-Jordan inverse for blocks of n <= 192 (N <= 32),
-// with implicit pivoting. Thread (w, l) of 16 warps holds rows i = w + 16 r
-// (r < 12) and columns c = l + 32 j (j < 6) in registers, packed in float2
-// pairs (j = 2q, 2q+1). Step k pivots column k on the unused row p of largest
-// |a_pk| (first such; recorded, never swapped) and performs the in-place
-// Gauss-Jordan update
-//   column k <- 0;  row p <- 0;  a_i <- a_i + t_i pr  for every row,
-//   pr = row p / a_pk with entry k = 1/a_pk,  t_p = 1, t_i = -a_ik otherwise,
-// as one packed FMA per element: the owner lanes of column k publish it to
-// shared memory (with a_pk replaced by -1, so t_i = -colk_i for every row) and
-// zero it; the owner warp of row p stores it (entry k = 1) and zeroes it.
-// Column k+1 and each warp's pivot candidate for it are published right after
-// the update, so a step needs two barriers. The step loop is unrolled over the
-// six 32-column chunks so that column indices into the register array are
-// static. The result is A^{-1} with rows and columns permuted:
-// A^{-1}[k][m] = S[p_k][q(m)], p_k the pivot row of column k and q its inverse.
+// Register-resident Gauss-Jordan inverse for blocks of n <= 192 (N <= 32):
+// 16 warps per block.
 constexpr int kGjWarps = 16, kGjMaxN = 192;
 
-#if FIL_GJ_ROWS
-constexpr int kGjRows = 12, kGjPairs = 3;
-static_assert(64 * kGjPairs == kGjMaxN && kGjWarps * kGjRows == kGjMaxN, "192 x 192");
-
-// Column values col[r] of this lane's rows -> colk (warp-major: entry
-// 12 w + r is row w + 16 r), and this warp's pivot candidate (largest |value|
-// over its unused rows, smallest row on ties).
-__device__ __forceinline__ void gj_publish(const float (&col)[kGjRows], unsigned used, int wid,
-                                           float *colk, float *cand_v, int *cand_i) {
-    float4 *dst = reinterpret_cast<float4 *>(colk + kGjRows * wid);
-#pragma unroll
-    for (int r = 0; r < kGjRows; r += 4)
-        dst[r / 4] = make_float4(col[r], col[r + 1], col[r + 2], col[r + 3]);
-    float best = -1.f;
-    int bi = 0x7fffffff;
-#pragma unroll
-    for (int r = 0; r < kGjRows; ++r) {
-        const float x = ((used >> r) & 1u) ? -1.f : fabsf(col[r]);
-        if (x > best) { best = x; bi = wid + kGjWarps * r; }
-    }
-    cand_v[wid] = best;
-    cand_i[wid] = bi;
-}
-
-// Publish column kj*32 + (owner lane) and zero it in the registers.
-#define FIL_GJ_PUBLISH(kj, buf)                                                    \
-    {                                                                              \
-        float col[kGjRows];                                                        \
-        _Pragma("unroll") for (int r = 0; r < kGjRows; ++r) {                      \
-            if ((kj) & 1) { col[r] = a[r][(kj) >> 1].y; a[r][(kj) >> 1].y = 0.f; } \
-            else { col[r] = a[r][(kj) >> 1].x; a[r][(kj) >> 1].x = 0.f; }          \
-        }                                                                          \
-        gj_publish(col, used, wid, colk[buf], cand_v[buf], cand_i[buf]);           \
-    }
-
-__global__ void __launch_bounds__(32 * kGjWarps, 1)
-gauss_jordan_inverse_reg_kernel(Layout lay, const int64_t *__restrict__ jofs, float *inv_all,
-                                int *__restrict__ flags) {
-    __shared__ __align__(16) float colk[2][kGjMaxN];
-    __shared__ __align__(16) float2 prow2[32 * kGjPairs];   // [32 q + l] = row p at (l + 64q, +32)
-    __shared__ float cand_v[2][kGjWarps];
-    __shared__ int cand_i[2][kGjWarps];
-    __shared__ float pinv_s;
-    __shared__ int pivrow[kGjMaxN];
-    __shared__ int qinv[kGjMaxN];
-    const int f = blockIdx.x;
-    const int s0 = lay.off[f];
-    const int n = 6 * (lay.off[f + 1] - s0);
-    float *A = inv_all + jofs[f];   // J0 in FP32 on entry, its inverse on exit
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    float2 a[kGjRows][kGjPairs];
-    unsigned used = 0;
-#pragma unroll
-    for (int r = 0; r < kGjRows; ++r) {
-        const int i = wid + kGjWarps * r;
-        if (i >= n) used |= 1u << r;      // padding rows never pivot
-#pragma unroll
-        for (int q = 0; q < kGjPairs; ++q) {
-            const int c0 = lane + 64 * q, c1 = c0 + 32;
-            a[r][q].x = (i < n && c0 < n) ? A[(int64_t)i * n + c0] : 0.f;
-            a[r][q].y = (i < n && c1 < n) ? A[(int64_t)i * n + c1] : 0.f;
-        }
-    }
-    if (lane == 0) FIL_GJ_PUBLISH(0, 0)
-    __syncthreads();
-#pragma unroll
-    for (int kj = 0; kj < 2 * kGjPairs; ++kj) {
-        for (int kl = 0; kl < 32; ++kl) {
-            const int k = 32 * kj + kl;
-            if (k >= n) break;
-            const int buf = k & 1;
-            // (1) pivot: reduce the 16 warp candidates (every warp, same result)
-            float v = lane < kGjWarps ? cand_v[buf][lane] : -2.f;
-            int idx = lane < kGjWarps ? cand_i[buf][lane] : 0x7fffffff;
-#pragma unroll
-            for (int d = kGjWarps / 2; d > 0; d >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, v, d);
-                const int oi = __shfl_xor_sync(0xffffffffu, idx, d);
-                if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
-            }
-            const int p = __shfl_sync(0xffffffffu, idx, 0);
-            const int pw = p % kGjWarps, prr = p / kGjWarps;
-            if (tid == 0) {
-                pivrow[k] = p;
-                float *cp = &colk[buf][kGjRows * pw + prr];
-                if (!(fabsf(*cp) > 0.f)) atomicOr(flags + 1, 1);
-                pinv_s = __frcp_rn(*cp);
-                *cp = -1.f;                 // t_p = 1
-            }
-            if (wid == pw) {
-                used |= 1u << prr;
-                // (2) row p -> prow2 with entry k = 1, then zero it
-#pragma unroll
-                for (int r = 0; r < kGjRows; ++r)
-                    if (r == prr) {
-#pragma unroll
-                        for (int q = 0; q < kGjPairs; ++q) {
-                            const int c0 = lane + 64 * q;
-                            prow2[32 * q + lane] = make_float2(c0 == k ? 1.f : a[r][q].x,
-                                                               c0 + 32 == k ? 1.f : a[r][q].y);
-                            a[r][q] = make_float2(0.f, 0.f);
-                        }
-                    }
-            }
-            __syncthreads();
-            // (3) a_i <- a_i - colk_i pr
-            const float pinv = pinv_s;
-            float2 pr[kGjPairs];
-#pragma unroll
-            for (int q = 0; q < kGjPairs; ++q) pr[q] = __fmul2_rn(prow2[32 * q + lane], make_float2(pinv, pinv));
-            const float4 *cw = reinterpret_cast<const float4 *>(colk[buf] + kGjRows * wid);
-#pragma unroll
-            for (int r4 = 0; r4 < kGjRows / 4; ++r4) {
-                const float4 c4 = cw[r4];
-                const float cr[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float2 t2 = make_float2(-cr[u], -cr[u]);
-#pragma unroll
-                    for (int q = 0; q < kGjPairs; ++q)
-                        a[4 * r4 + u][q] = __ffma2_rn(t2, pr[q], a[4 * r4 + u][q]);
-                }
-            }
-            // (4) publish (and zero) column k + 1 with the pivot candidates for it
-            if (k + 1 < n) {
-                if (kl < 31) {
-                    if (lane == kl + 1) FIL_GJ_PUBLISH(kj, buf ^ 1)
-                } else if (kj + 1 < 2 * kGjPairs) {
-                    if (lane == 0) FIL_GJ_PUBLISH(kj + 1, buf ^ 1)
-                }
-            }
-            __syncthreads();
-        }
-    }
-    // A^{-1}[k][m] = S[p_k][q(m)]: element S[i][c] goes to A[q(i)][p_c]
-    for (int k = tid; k < n; k += blockDim.x) qinv[pivrow[k]] = k;
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kGjRows; ++r) {
-        const int i = wid + kGjWarps * r;
-#pragma unroll
-        for (int q = 0; q < kGjPairs; ++q) {
-            const int c0 = lane + 64 * q, c1 = c0 + 32;
-            if (i < n && c0 < n) A[(int64_t)qinv[i] * n + pivrow[c0]] = a[r][q].x;
-            if (i < n && c1 < n) A[(int64_t)qinv[i] * n + pivrow[c1]] = a[r][q].y;
-        }
-    }
-}
-#undef FIL_GJ_PUBLISH
-#endif  // FIL_GJ_ROWS
-
-#if !FIL_GJ_ROWS
-// The same in-place Gauss-Jordan inverse with the matrix distributed by
+// The in-place Gauss-Jordan inverse with the matrix distributed by
 // columns: warp w holds columns w + 16 q (q < 12), lane l rows l + 32 j
 // (j < 6), as pairs of columns (w + 32 t, w + 32 t + 16) for the packed FP32
 // FMA. The pivot search of step k is one warp's reduction over its column: a
@@ -1102,7 +931,6 @@ gauss_jordan_inverse_col_kernel(Layout lay, const int64_t *__restrict__ jofs, fl
     }
 }
 #undef FIL_GC_SLOT_SWITCH
-#endif  // !FIL_GJ_ROWS
 
 }  // namespace
 
@@ -1140,7 +968,7 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
     dp.a = c->a;
     c->j0_dp_bdt = dp.bdt;
     const int N = c->lay.maxN;
-    const int fast = c->prec == FIL_MIXED ? 1 : 0;
+    const int fast = fast_mixed(c) ? 1 : 0;
     const size_t smem_pre = (size_t)6 * N * sizeof(double) +
                             (fast ? (size_t)(12 * N + 5 * N * N) * sizeof(float) : 0);
     if (smem_pre > 48 * 1024) {
@@ -1158,23 +986,15 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
     if (e != cudaSuccess) return e;
     j0_assemble32_kernel<<<c->lay.M, kAsmThreads, smem_asm, c->stream>>>(
         c->lay, c->jofs, c->auxofs, dp, c->aux, c->jinv);
-#ifndef FIL_GJ_SHARED_ONLY
     if (6 * N <= kGjMaxN) {
-#if FIL_GJ_ROWS
-        gauss_jordan_inverse_reg_kernel<<<c->lay.M, 32 * kGjWarps, 0, c->stream>>>(
-            c->lay, c->jofs, c->jinv, c->d_flags);
-#else
         const size_t smem_gc = (size_t)6 * N * (6 * N + 1) * sizeof(float);
         e = cudaFuncSetAttribute(gauss_jordan_inverse_col_kernel,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gc);
         if (e != cudaSuccess) return e;
         gauss_jordan_inverse_col_kernel<<<c->lay.M, kGcThreads, smem_gc, c->stream>>>(
             c->lay, c->jofs, c->jinv, c->d_flags);
-#endif
         e = cudaGetLastError();
-    } else
-#endif
-    {
+    } else {
         const size_t smem_inv = (size_t)6 * N * (6 * N + 1) * sizeof(float);
         e = launch_gauss_jordan(c, (6 * N + 31) / 32, smem_inv);
     }
@@ -1189,7 +1009,7 @@ size_t j0_solve_smem(int maxN) {
 }
 
 cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x, const int *active) {
-    if (c->prec == FIL_MIXED) {
+    if (fast_mixed(c)) {
         j0_apply_inverse_kernel<<<c->lay.M, kApplyThreads, 0, c->stream>>>(c->lay, c->jofs,
                                                                           c->jinv, b, x, active);
         c->n_launches += 1;

@@ -24,7 +24,7 @@
 //    tile of kRpyTile targets and streams sources through double-buffered
 //    shared memory in chunks of kRpyChunk; all lanes read the same source
 //    (broadcast), so shared-memory traffic is 3 LDS.128 per source per thread.
-//  * Packed FP32x2 arithmetic (FIL_RPY_PACKED): a thread evaluates its target
+//  * Packed FP32x2 arithmetic: a thread evaluates its target
 //    against two sources at once, lane x of every float2 holding the even
 //    source and lane y the odd one; the records of a source pair are stored
 //    interleaved so that each loaded float2 is an operand. This halves the
@@ -45,6 +45,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <utility>
 
 #include "fil_internal.cuh"
 
@@ -155,7 +156,6 @@ __device__ __forceinline__ int64_t segment_at(const SysMap &m, int64_t P, int64_
 //   [2] = (T_x, T_y, T_z, F_z), with hi = fl32(Y), lo = fl32(Y - hi).
 // Padding records sit far away with zero load, so they add exactly zero.
 // ---------------------------------------------------------------------------
-#if FIL_RPY_PACKED
 // Packed layout: sources 2p and 2p+1 share the kRpyPairF4 float4 at
 // src + kRpyPairF4 p; each float2 holds one component of both (even, odd),
 // positions negated:
@@ -188,34 +188,6 @@ __global__ void pack32_kernel(const double *__restrict__ Y, const double *__rest
 #pragma unroll
     for (int c = 0; c < kV; ++c) o[2 * c] = v[c];
 }
-#else
-__global__ void pack32_kernel(const double *__restrict__ Y, const double *__restrict__ FT,
-                              int64_t S, int64_t Spad, SysMap sm, float4 *__restrict__ src) {
-    const int64_t P = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= Spad) return;
-    const int64_t i = segment_at(sm, P, S);
-    float4 r0, r1, r2;
-    if (i >= 0) {
-        double y0 = Y[3 * i], y1 = Y[3 * i + 1], y2 = Y[3 * i + 2];
-        float h0 = __double2float_rn(y0), h1 = __double2float_rn(y1), h2 = __double2float_rn(y2);
-        float l0 = __double2float_rn(y0 - (double)h0);
-        float l1 = __double2float_rn(y1 - (double)h1);
-        float l2 = __double2float_rn(y2 - (double)h2);
-        const double *f = FT + 6 * i;
-        r0 = make_float4(h0, h1, h2, __double2float_rn(f[0]));
-        r1 = make_float4(l0, l1, l2, __double2float_rn(f[1]));
-        r2 = make_float4(__double2float_rn(f[3]), __double2float_rn(f[4]),
-                         __double2float_rn(f[5]), __double2float_rn(f[2]));
-    } else {
-        r0 = make_float4(kFarPad, kFarPad, kFarPad, 0.f);
-        r1 = make_float4(0.f, 0.f, 0.f, 0.f);
-        r2 = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    src[3 * P] = r0;
-    src[3 * P + 1] = r1;
-    src[3 * P + 2] = r2;
-}
-#endif
 
 // FP64 records: 9 doubles per segment (Y, F, T); padding far away, no load.
 __global__ void pack64_kernel(const double *__restrict__ Y, const double *__restrict__ FT,
@@ -292,43 +264,6 @@ __device__ __forceinline__ void pair32(float thx, float thy, float thz, float tl
     acc[5] = fmaf(C, Tz, fmaf(dT, dz, fmaf(Fx, ey, fmaf(-Fy, ex, acc[5]))));
 }
 
-// The far-form pair term for every pair, branch-free, tracking the smallest
-// r^2 seen. A group of sources in which a warp saw r^2 < (2a)^2 is recomputed
-// from zero with pair32 (exact branches), so whatever this form produced for
-// overlapping or coincident pairs there (possibly Inf/NaN at r = 0) is
-// discarded; for every other group r^2 >= (2a)^2 and the terms are finite.
-__device__ __forceinline__ void pair32_far(float thx, float thy, float thz, float tlx, float tly,
-                                           float tlz, const float4 s0, const float4 s1,
-                                           const float4 s2, const RpyConst32 &k, float *acc,
-                                           float &rmin2) {
-    const float dx = __fsub_rn(thx, s0.x) + __fsub_rn(tlx, s1.x);
-    const float dy = __fsub_rn(thy, s0.y) + __fsub_rn(tly, s1.y);
-    const float dz = __fsub_rn(thz, s0.z) + __fsub_rn(tlz, s1.z);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    rmin2 = fminf(rmin2, r2);
-    const float rinv = rsqrt_approx(r2);
-    const float rinv2 = rinv * rinv;
-    const float rinv3 = rinv * rinv2;
-    const float rinv5 = rinv3 * rinv2;
-    const float A = fmaf(k.k23a2, rinv3, rinv);
-    const float B = fmaf(-k.k2a2, rinv5, rinv3);
-    const float C = -0.5f * rinv3;
-    const float D = 1.5f * rinv5;
-    const float G = rinv3;
-    const float Fx = s0.w, Fy = s1.w, Fz = s2.w;
-    const float Tx = s2.x, Ty = s2.y, Tz = s2.z;
-    const float bF = B * fmaf(dx, Fx, fmaf(dy, Fy, dz * Fz));
-    const float dT = D * fmaf(dx, Tx, fmaf(dy, Ty, dz * Tz));
-    const float ex = G * dx, ey = G * dy, ez = G * dz;
-    acc[0] = fmaf(A, Fx, fmaf(bF, dx, fmaf(Ty, ez, fmaf(-Tz, ey, acc[0]))));
-    acc[1] = fmaf(A, Fy, fmaf(bF, dy, fmaf(Tz, ex, fmaf(-Tx, ez, acc[1]))));
-    acc[2] = fmaf(A, Fz, fmaf(bF, dz, fmaf(Tx, ey, fmaf(-Ty, ex, acc[2]))));
-    acc[3] = fmaf(C, Tx, fmaf(dT, dx, fmaf(Fy, ez, fmaf(-Fz, ey, acc[3]))));
-    acc[4] = fmaf(C, Ty, fmaf(dT, dy, fmaf(Fz, ex, fmaf(-Fx, ez, acc[4]))));
-    acc[5] = fmaf(C, Tz, fmaf(dT, dz, fmaf(Fx, ey, fmaf(-Fy, ex, acc[5]))));
-}
-
-#if FIL_RPY_PACKED
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
 
@@ -376,7 +311,6 @@ __device__ __forceinline__ void unpack_source(const float4 *q, int h, float4 &s0
     s1 = make_float4(-f[8], -f[10], -f[12], f[14]);
     s2 = make_float4(f[16], f[18], f[20], f[22]);
 }
-#endif
 
 // One pair in FP64 (record layout: Y, F, T).
 __device__ __forceinline__ void pair64(double tx, double ty, double tz, const double *s,
@@ -428,7 +362,7 @@ __device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
 // (hi, lo) accumulators.
 // ---------------------------------------------------------------------------
 template <int TPT>
-__global__ void __launch_bounds__(kRpyThreads, TPT == 2 ? FIL_RPY_MINB_TPT2 : FIL_RPY_MINB_TPT1)
+__global__ void __launch_bounds__(kRpyThreads, TPT == 2 ? kRpyMinBlocksTpt2 : kRpyMinBlocksTpt1)
 rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G, RpyConst32 k,
                   float *__restrict__ part) {
     constexpr int kRec = kRpyPairF4 * (kRpyChunk / 2);   // float4 per chunk
@@ -453,16 +387,11 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
 #pragma unroll
         for (int t = 0; t < kT; ++t) {
             const int64_t n = ptile * kTile + t * kRpyThreads + tid;
-#if FIL_RPY_PACKED
             float4 a0, a1, a2;
             unpack_source(src + kRpyPairF4 * (n >> 1), (int)(n & 1), a0, a1, a2);
-#else
-            const float4 a0 = src[3 * n], a1 = src[3 * n + 1];
-#endif
             th[t][0] = a0.x; th[t][1] = a0.y; th[t][2] = a0.z;
             tl[t][0] = a1.x; tl[t][1] = a1.y; tl[t][2] = a1.z;
         }
-#if FIL_RPY_PACKED
         float2 thb[kT][3], tlb[kT][3];   // targets broadcast to both lanes
 #pragma unroll
         for (int t = 0; t < kT; ++t)
@@ -472,7 +401,6 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
                 tlb[t][c] = f2(tl[t][c], tl[t][c]);
             }
         const float2 k23 = f2(k.k23a2, k.k23a2), nk2 = f2(-k.k2a2, -k.k2a2);
-#endif
         float hi[kT][6], lo[kT][6];
 #pragma unroll
         for (int t = 0; t < kT; ++t)
@@ -499,7 +427,6 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
                     if (tid + r * kRpyThreads < kRec) pre[r] = g[tid + r * kRpyThreads];
             }
             const float4 *s = sm[buf];
-#if FIL_RPY_PACKED
 #pragma unroll 1
             for (int grp = 0; grp < kRpyChunk / kRpyComp; ++grp) {
                 float2 acc2[kT][6];
@@ -537,41 +464,6 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
                                    s1, s2, k, acc[t]);
                     }
                 }
-#else
-#pragma unroll 1
-            for (int grp = 0; grp < kRpyChunk / kRpyComp; ++grp) {
-                float acc[kT][6];
-#pragma unroll
-                for (int t = 0; t < kT; ++t)
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) acc[t][c] = 0.f;
-                float rmin2 = k.near2;
-#pragma unroll kRpyUnroll
-                for (int j = 0; j < kRpyComp; ++j) {
-                    const int rj = 3 * (grp * kRpyComp + j);
-                    const float4 s0 = s[rj], s1 = s[rj + 1], s2 = s[rj + 2];
-#pragma unroll
-                    for (int t = 0; t < kT; ++t)
-                        pair32_far(th[t][0], th[t][1], th[t][2], tl[t][0], tl[t][1], tl[t][2], s0,
-                                   s1, s2, k, acc[t], rmin2);
-                }
-                if (__any_sync(0xffffffffu, rmin2 < k.near2)) {
-                    // an overlapping (or self) pair: redo this group with the exact branches
-#pragma unroll
-                    for (int t = 0; t < kT; ++t)
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) acc[t][c] = 0.f;
-#pragma unroll 1
-                    for (int j = 0; j < kRpyComp; ++j) {
-                        const int rj = 3 * (grp * kRpyComp + j);
-                        const float4 s0 = s[rj], s1 = s[rj + 1], s2 = s[rj + 2];
-#pragma unroll
-                        for (int t = 0; t < kT; ++t)
-                            pair32(th[t][0], th[t][1], th[t][2], tl[t][0], tl[t][1], tl[t][2], s0,
-                                   s1, s2, k, acc[t]);
-                    }
-                }
-#endif
 #pragma unroll
                 for (int t = 0; t < kT; ++t)
 #pragma unroll
@@ -826,9 +718,8 @@ void set_grids(fil_ctx *c) {
 
 cudaError_t rpy_setup(fil_ctx *c) {
     c->rpy_tpt = kRpyTargetsPerThread;
-    int occ = c->prec == FIL_MIXED ? occupancy(rpy_pair32_kernel<kRpyTargetsPerThread>)
+    int occ = pair32_on(c) ? occupancy(rpy_pair32_kernel<kRpyTargetsPerThread>)
                                    : occupancy(rpy_pair64_kernel<kRpyTargetsPerThread>);
-    if (FIL_RPY_OCC > 0) occ = FIL_RPY_OCC;
     c->rpy_ctas = occ;
     c->rpy_ctas_max = std::max({occ, occupancy(rpy_pair32_kernel<1>), occupancy(rpy_pair32_kernel<2>),
                                 occupancy(rpy_pair64_kernel<1>), occupancy(rpy_pair64_kernel<2>)});
@@ -954,7 +845,7 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
     const int T = kRpyThreads * c->rpy_tpt;
     // the active-tile list changes between applies: its launches keep a fixed grid
     // (and read the unit count from the device), so captured graphs stay valid
-    if (c->prec == FIL_MIXED) {
+    if (pair32_on(c)) {
         const int G = (int)(active_only ? c->rpy_grid32 : std::min<int64_t>(c->rpy_grid32, W));
         pack32_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, sm, c->src32);
         if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
@@ -1006,7 +897,7 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
     float best = 1e30f;
     for (int tpt = 1; tpt <= 2 && e == cudaSuccess; ++tpt) {
         int occ;
-        if (c->prec == FIL_MIXED)
+        if (pair32_on(c))
             occ = tpt == 1 ? occupancy(rpy_pair32_kernel<1>) : occupancy(rpy_pair32_kernel<2>);
         else
             occ = tpt == 1 ? occupancy(rpy_pair64_kernel<1>) : occupancy(rpy_pair64_kernel<2>);
@@ -1059,7 +950,13 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
 namespace {
 
 constexpr int64_t kNoAllocMaxSeg = 32768;     // largest S accepted
-constexpr int kNoAllocMaxGrid = 4 * 152;      // stream-K CTAs at most
+// The context path runs the stream-K split over (resident CTAs per SM) x SMs
+// CTAs. The scratch holds the partial sums of at most kNoAllocMaxSMs SMs at
+// the pair kernel's compiled residency (GB300 has 152 SMs); on a larger part
+// the grid is capped here, and the results then differ from
+// fil_mobility_apply's in rounding only (another summation order).
+constexpr int kNoAllocMaxSMs = 152;
+constexpr int kNoAllocMaxGrid = kRpyMinBlocksTpt2 * kNoAllocMaxSMs;   // stream-K CTAs at most
 constexpr int64_t kNoAllocMaxTiles = (kNoAllocMaxSeg + kRpyTile - 1) / kRpyTile;
 constexpr int64_t kNoAllocMaxChunks = (kNoAllocMaxSeg + kRpyChunk - 1) / kRpyChunk;
 constexpr int64_t kNoAllocMaxSpad = (kNoAllocMaxTiles * kRpyTile > kNoAllocMaxChunks * kRpyChunk)
@@ -1099,13 +996,32 @@ cudaError_t noalloc_setup(int dev, unsigned char **ptr, int *grid) {
     return cudaSuccess;
 }
 
-bool on_device(const void *p) {
+// Memory the kernels may read on device `dev`: device memory of that device,
+// or managed memory. Host memory and memory of another GPU (which these
+// kernels could only reach through peer access) are rejected.
+bool on_device(const void *p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
+        cudaGetLastError();   // the error of this query only
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+// A launch whose own status is returned (cudaGetLastError would also report
+// an earlier, unrelated failure of the caller's).
+template <typename... KArgs, typename... Args>
+cudaError_t launch(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t st,
+                   Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 }  // namespace
@@ -1117,9 +1033,9 @@ extern "C" fil_status fil_rpy_apply_noalloc(int64_t n_seg, const double *Y, cons
     using namespace fil;
     if (n_seg < 1 || n_seg > kNoAllocMaxSeg) return FIL_EINVAL;
     if (!(a > 0) || !(eta > 0) || !Y || !FT || !VW) return FIL_EINVAL;
-    if (!on_device(Y) || !on_device(FT) || !on_device(VW)) return FIL_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return FIL_ECUDA;
+    if (!on_device(Y, dev) || !on_device(FT, dev) || !on_device(VW, dev)) return FIL_EINVAL;
     unsigned char *base = nullptr;
     int grid_max = 1;
     if (noalloc_setup(dev, &base, &grid_max) != cudaSuccess) return FIL_ECUDA;
@@ -1137,10 +1053,13 @@ extern "C" fil_status fil_rpy_apply_noalloc(int64_t n_seg, const double *Y, cons
     SysMap sm{};                       // one system, no tables
     sm.n_tiles = tiles;
     sm.n_chunks = n_chunks;
-    pack32_kernel<<<(unsigned)((Spad + pb - 1) / pb), pb, 0, st>>>(Y, FT, n_seg, Spad, sm, src);
-    rpy_pair32_kernel<kRpyTargetsPerThread><<<G, kRpyThreads, 0, st>>>(
-        src, sm, W, G, make_const<float, RpyConst32>(a), part);
-    rpy_reduce32_kernel<<<(unsigned)((n_seg + pb - 1) / pb), pb, 0, st>>>(
-        part, n_seg, sm, W, G, kRpyTile, 1.0 / (8.0 * kPi * eta), VW);
-    return cudaGetLastError() == cudaSuccess ? FIL_OK : FIL_ECUDA;
+    cudaError_t e = launch(pack32_kernel, (unsigned)((Spad + pb - 1) / pb), pb, st, Y, FT, n_seg,
+                           Spad, sm, src);
+    if (e == cudaSuccess)
+        e = launch(rpy_pair32_kernel<kRpyTargetsPerThread>, (unsigned)G, kRpyThreads, st,
+                   (const float4 *)src, sm, W, G, make_const<float, RpyConst32>(a), part);
+    if (e == cudaSuccess)
+        e = launch(rpy_reduce32_kernel, (unsigned)((n_seg + pb - 1) / pb), pb, st,
+                   (const float *)part, n_seg, sm, W, G, kRpyTile, 1.0 / (8.0 * kPi * eta), VW);
+    return e == cudaSuccess ? FIL_OK : FIL_ECUDA;
 }

@@ -16,12 +16,11 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-# FIL_LIBRARY may point at another build of the same library (e.g. a tile-shape variant)
-LIB_PATH = os.environ.get("FIL_LIBRARY") or os.path.join(_HERE, "_lib", "libfil.so")
+LIB_PATH = os.path.join(_HERE, "_lib", "libfil.so")
 
 (FIL_OK, FIL_EINVAL, FIL_ENOMEM, FIL_ECUDA, FIL_ENOCONV, FIL_ENAN, FIL_ESTALL, FIL_ESTATE,
  FIL_EOVERFLOW) = range(9)
-FIL_FP64, FIL_MIXED = 0, 1
+FIL_FP64, FIL_MIXED, FIL_PAIR32 = 0, 1, 2
 FIL_J0_DRAG, FIL_J0_FILAMENT_RPY = 0, 1
 STATUS_NAMES = {0: "FIL_OK", 1: "FIL_EINVAL", 2: "FIL_ENOMEM", 3: "FIL_ECUDA", 4: "FIL_ENOCONV",
                 5: "FIL_ENAN", 6: "FIL_ESTALL", 7: "FIL_ESTATE", 8: "FIL_EOVERFLOW"}

@@ -37,7 +37,7 @@ def _positions(rng, segs, box):
 
 
 @pytest.mark.parametrize("tune", [False, True])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_mobility_is_block_diagonal_over_systems(fil, prec, tune):
     rng = np.random.default_rng(prec)
     Ys, FTs = [], []
@@ -139,10 +139,12 @@ def test_graph_iterations_reproduce_launched_iterations(fil, prec):
 
 
 @pytest.mark.parametrize("j0", [(0, "drag"), (1, "rpy")])
-def test_mixed_ensemble_converges_close_to_fp64(fil, j0):
-    """The mixed mode (FP32 pair sums, FP32 J0 solves, FP32 Broyden history) on an
-    ensemble: every system converges to the oracle's FP64 trajectory within the
-    accuracy its tolerance allows, and every system's ||f||_inf meets it."""
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_ensemble_converges_close_to_fp64(fil, j0, prec):
+    """The mixed modes (FP32 pair sums; FIL_MIXED also FP32 J0 solves and FP32
+    Broyden history) on an ensemble: every system converges to the oracle's FP64
+    trajectory within the accuracy its tolerance allows, and every system's
+    ||f||_inf meets it."""
     systems = [[16], [20, 33, 7], [30] * 5, [1, 2, 3]]
     p = fo.Params(a=1.0, eta=1.0, dL=2.2, KB=2.0, KT=1.5, dt=0.2, tol=1e-6, max_iter=80)
     states, exts, lays = [], [], []
@@ -154,7 +156,7 @@ def test_mixed_ensemble_converges_close_to_fp64(fil, j0):
     segs_all = [n for segs in systems for n in segs]
     with fil.Filaments(segs_all, fil_per_sys=[len(s) for s in systems], a=p.a, eta=p.eta,
                        dL=p.dL, KB=p.KB, KT=p.KT, dt=p.dt, tol=p.tol, max_iter=p.max_iter,
-                       precision=fil.FIL_MIXED, j0_model=j0[0]) as m:
+                       precision=prec, j0_model=j0[0]) as m:
         m.set_state(np.concatenate([s.Y for s in states]), np.concatenate([s.q for s in states]))
         m.set_external(np.concatenate([e.Fext for e in exts]), None, None)
         Y = np.zeros((m.S, 3))

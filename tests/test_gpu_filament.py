@@ -109,11 +109,12 @@ def _subsystem(lay, st, X, fils):
     return sub, st_sub, xs
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_full_size_j0_solve_on_sampled_filaments(fil, prec):
     """The 32 000-segment suspension with the filament-RPY J0 (the bench's
     configuration): J0^{-1} b on sampled filaments against the oracle's dense
-    LU of the same blocks, FP64 path to 1e-10. The mixed path assembles and
+    LU of the same blocks, FP64 path (and FIL_PAIR32, whose J0 solves are the
+    FP64 path's) to 1e-10. The FIL_MIXED path assembles and
     inverts J0 in FP32 with no refinement; its normwise backward error against
     the oracle's blocks, |B x - b|_inf / (|B|_inf |x|_inf + |b|_inf) per block,
     is bounded by 2 n u_32 (n = 6N = 192: an FP32 Gauss-Jordan inverse, and an
@@ -139,7 +140,7 @@ def test_full_size_j0_solve_on_sampled_filaments(fil, prec):
     b_sub = np.concatenate([b[lay.off_X[i]:lay.off_X[i] + 192] for i in fils])
     ref = fo.J0Solver(sub, blocks).solve(b_sub)
     got = np.concatenate([x[lay.off_X[i]:lay.off_X[i] + 192] for i in fils])
-    if prec == 0:
+    if prec != fil.FIL_MIXED:
         np.testing.assert_allclose(got, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
     else:
         u32 = 2.0 ** -24
@@ -168,11 +169,12 @@ def test_residual_parity(fil, segs, history):
     assert abs(finf - np.abs(f).max()) == 0.0
 
 
-def test_residual_mixed_close_to_fp64(fil):
+@pytest.mark.parametrize("prec", [1, 2])
+def test_residual_mixed_close_to_fp64(fil, prec):
     lay, p, st, ext, _ = _system([32] * 6, 3, history=True)
     X = fo.initial_guess(lay, st)
     ref = fo.residual(lay, p, st, ext, X)
-    with _gpu(fil, lay, p, st, ext, prec=1) as m:
+    with _gpu(fil, lay, p, st, ext, prec=prec) as m:
         f = np.zeros(6 * lay.S)
         m.residual(X, f)
     # velocity errors of a few 1e-7 relative, times (2/3) dt
@@ -197,11 +199,14 @@ J0_MODELS = [(0, "drag"), (1, "rpy")]
 @pytest.mark.parametrize("segs", SEGS[:3] + [[38, 2, 1], [40, 65, 2, 1]])
 @pytest.mark.parametrize("history", [False, True])
 @pytest.mark.parametrize("model", J0_MODELS)
-def test_j0_solve_matches_dense_oracle(fil, segs, history, model):
+@pytest.mark.parametrize("prec", [0, 2])
+def test_j0_solve_matches_dense_oracle(fil, segs, history, model, prec):
+    """FP64 J0 solves (FIL_FP64, and FIL_PAIR32 whose J0 is the same) against the
+    oracle's dense LU of App. B.2's blocks or the filament-RPY blocks."""
     if model[0] == 1 and max(segs) > 38:
         pytest.skip("the filament-RPY J0 supports N <= 38 segments per filament")
     lay, p, st, ext, _ = _system(segs, 30, history=history, twist=0.2)
-    with _gpu(fil, lay, p, st, ext, j0=model[0]) as m:
+    with _gpu(fil, lay, p, st, ext, prec=prec, j0=model[0]) as m:
         m.broyden_begin()
         X0 = np.zeros(6 * lay.S)
         m.get_iterate(X0, None)
@@ -283,12 +288,13 @@ def test_c0_trajectory_parity(fil):
             np.testing.assert_allclose(np.linalg.norm(q, axis=1), 1.0, atol=1e-14)
 
 
-def test_mixed_step_converges_close_to_fp64(fil):
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_step_converges_close_to_fp64(fil, prec):
     lay, p, st, ext, _ = _system([32] * 8, 50, tol=1e-6, dt=0.2)
     ref = st
     for _ in range(3):
         ref, _ = fo.step(lay, p, ref, ext)
-    with _gpu(fil, lay, p, st, ext, prec=1) as m:
+    with _gpu(fil, lay, p, st, ext, prec=prec) as m:
         for _ in range(3):
             m.step()
         Y = np.zeros((lay.S, 3))

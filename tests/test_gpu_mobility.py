@@ -1,7 +1,8 @@
 """GPU parity of the RPY mobility apply (fil_mobility_apply) against the oracle.
 
 FP64 path: normwise relative error <= 1e-12 per call.
-Mixed path (FP32 pair sums): every component within
+Mixed paths (FP32 pair sums; FIL_MIXED and FIL_PAIR32 run the same apply):
+every component within
     |v_gpu - v_oracle| <= C_MIXED * 2^-24 * B
 where B is the oracle's sum over pairs of |parts of M_nm| (|F|, |T|) for that
 component. C_MIXED = 4 * 32 + 16: each group of 32 sources is accumulated by
@@ -53,7 +54,7 @@ def _check_mixed(got, ref, ref_abs):
     assert np.median(err / np.maximum(ref_abs, 1e-300)) < 8 * U32
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_c1_workload_parity(fil, prec):
     """100 random-walk filaments x 32 segments, 5% volume fraction, N(0,1) loads."""
     Y, FT = mobility_inputs(100, 32, seed=0)
@@ -67,7 +68,7 @@ def test_c1_workload_parity(fil, prec):
 
 @pytest.mark.parametrize("segs", [[1], [7], [255], [1, 256], [3, 254, 2], [100] * 5 + [13],
                                   [64] * 17 + [5]])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_ragged_sizes(fil, segs, prec):
     S = sum(segs)
     rng = np.random.default_rng(S)
@@ -81,7 +82,7 @@ def test_ragged_sizes(fil, segs, prec):
         _check_mixed(got, ref, ref_abs)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_overlaps_and_coincident_segments(fil, prec):
     """Dense cluster: most pairs overlap (r < 2a); two pairs coincide exactly."""
     rng = np.random.default_rng(11)
@@ -98,7 +99,7 @@ def test_overlaps_and_coincident_segments(fil, prec):
         _check_mixed(got, ref, ref_abs)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_full_size_sampled_rows(fil, prec):
     """32 000 segments (the full-suspension size): sampled targets vs the oracle."""
     Y, FT = mobility_inputs(1000, 32, volume_fraction=0.02, seed=3)
@@ -111,7 +112,7 @@ def test_full_size_sampled_rows(fil, prec):
         _check_mixed(got[rows], ref, ref_abs)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_deterministic_and_host_pointers(fil, prec):
     Y, FT = mobility_inputs(20, 32, seed=5)
     a = _gpu_apply(fil, [32] * 20, Y, FT, prec)

@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(a=0.0), dict(eta=-1.0), dict(dL=0.0), dict(dt=0.0),
-                                 dict(tol=0.0), dict(max_iter=0), dict(precision=7),
+                                 dict(tol=0.0), dict(max_iter=0), dict(precision=7), dict(precision=3),
                                  dict(KB=float("nan"))])
 def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
     with pytest.raises(lib.FilError) as e:
@@ -66,13 +66,16 @@ def test_oracle_library_builds():
 
 
 def test_binding_fails_loudly_without_the_library(tmp_path):
-    """No CPU fallback: importing the binding with no library at the configured
-    path raises ImportError."""
+    """No CPU fallback: importing the binding from a copy of the package that
+    has no built library raises ImportError."""
+    import shutil
     import subprocess
     import sys
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, FIL_LIBRARY=str(tmp_path / "missing" / "libfil.so"))
-    r = subprocess.run([sys.executable, "-c", "import paper_1903_12609_gb300.fil"], cwd=root,
-                       env=env, capture_output=True, text=True, timeout=300)
+    pkg = os.path.join(ROOT, "paper_1903_12609_gb300")
+    shutil.copytree(pkg, tmp_path / "paper_1903_12609_gb300",
+                    ignore=shutil.ignore_patterns("_lib", "weights", "__pycache__"))
+    env = dict(os.environ, PYTHONPATH=str(tmp_path))
+    r = subprocess.run([sys.executable, "-c", "import paper_1903_12609_gb300.fil"],
+                       cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode != 0
     assert "ImportError" in r.stderr and "libfil.so" in r.stderr
