@@ -263,15 +263,22 @@ def run_mobility(args, fil, torch):
 # roofline, clocks and the FP64-oracle comparison.
 # ---------------------------------------------------------------------------
 
-def run_c1_mobility(fil, torch, applies=1000, min_seconds=1.0):
+def run_c1_mobility(fil, torch, applies=1000, per_graph=100, min_seconds=1.0):
     """Mobility apply alone: 100 random-walk filaments x 32 segments (3200) at
-    5% volume fraction, N(0,1) loads, 1000 repeated applies (repeated in batches
-    until the timed region lasts >= min_seconds, for the clock record)."""
+    5% volume fraction, N(0,1) loads, 1000 repeated applies. At this size an
+    apply takes tens of microseconds, less than the host needs to issue it, so
+    the applies are captured in a CUDA graph (100 per graph; the apply
+    allocates nothing and does not synchronise with device arrays) and the
+    graph is replayed; the schedule is autotuned for the size first. The
+    1000-apply batch is repeated until the timed region lasts min_seconds
+    (for the clock record)."""
     from paper_1903_12609_gb300.inputs import mobility_inputs
     Y, FT = mobility_inputs(100, 32, seed=0)
     S = Y.shape[0]
     stream = torch.cuda.Stream()
     m = fil.Filaments([32] * 100, precision=fil.FIL_PAIR32, stream=stream.cuda_stream)
+    m.set_state(Y, np.tile([1.0, 0.0, 0.0, 0.0], (S, 1)))
+    tuned = m.autotune(50)
     Yd = torch.from_numpy(Y).cuda()
     FTd = torch.from_numpy(FT).cuda()
     VW = torch.empty((S, 6), dtype=torch.float64, device="cuda")
@@ -279,50 +286,59 @@ def run_c1_mobility(fil, torch, applies=1000, min_seconds=1.0):
         for _ in range(20):
             m.mobility_apply(Yd, FTd, VW)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     m.profile(True)
     m.profile_read()
     a0, _, k0 = m.counters()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+        for _ in range(per_graph):
+            m.mobility_apply(Yd, FTd, VW)
+    a1, _, k1 = m.counters()
+    launches_per_graph = k1 - k0
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     clk = clocks_start()
     t_wall = time.perf_counter()
-    batches = 0
+    replays = 0
     e0.record(stream)
     while True:
-        for _ in range(applies):
-            m.mobility_apply(Yd, FTd, VW)
-        batches += 1
+        for _ in range(applies // per_graph):
+            graph.replay()
+            replays += 1
         stream.synchronize()
-        if time.perf_counter() - t_wall >= min_seconds or batches >= 50:
+        if time.perf_counter() - t_wall >= min_seconds or replays >= 500:
             break
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clocks_stop(clk, torch.cuda.current_device())
+    # the events inside the graph hold the pair-kernel times of its last replay
     n_pair, pair_ms = m.profile_read()
     m.profile(False)
-    a1, _, k1 = m.counters()
     ms = e0.elapsed_time(e1)
     got = VW.cpu().numpy()
     m.close()
-    n_app = a1 - a0
+    n_app = replays * per_graph
     # FP64 oracle: the whole apply (all 3200 rows), timed on the host cores
     cores = os.cpu_count() or 1
     rows = np.arange(S, dtype=np.int32)
     ref, B, dt = _oracle_rows_timed(Y, FT, rows, cores)
     return {"metric": "RPY pair interactions/s", "value": n_app * float(S) * S / (ms * 1e-3),
-            "unit": UNIT, "applies": int(n_app), "batches_of_1000": batches,
-            "ms_per_apply": ms / n_app, "dtype": "f32+f64",
+            "unit": UNIT, "applies": int(n_app), "ms_per_apply": ms / n_app, "dtype": "f32+f64",
             "config": {"workload": "mobility apply alone: 100 random-walk filaments x 32 "
                                    "segments (3200), bond 2.2a, 5% volume fraction, F,T ~ N(0,1)",
                        "segments": S, "precision": "FP32 pair sums (compensated), FP64 results",
+                       "issue": "CUDA graph of %d applies (pack, pair, reduce kernels), replayed"
+                                % per_graph,
                        "l2": "inputs L2-resident (3200 segments); the metric is the apply "
                              "itself, repeated"},
             "roofline": pair_roofline(float(S) * S, pair_ms, n_pair),
+            "autotuned": {"tile": tuned[0], "ctas_per_sm": tuned[1], "ms_per_apply": tuned[2]},
             "velocity_error": velocity_error(got, ref, B),
             "cpu_baseline": {"value": S * float(S) / dt, "unit": UNIT, "cores": cores,
                              "kind": "oracle", "sample": "one whole apply, %d x %d pairs (%.2f s)"
                                                          % (S, S, dt)},
-            "gpu_launches": int(k1 - k0), "clocks": clocks}
+            "gpu_launches": int(launches_per_graph * replays), "clocks": clocks}
 
 
 def run_c0_single(fil, torch, steps=200):
@@ -495,6 +511,28 @@ def run_ensemble(args, fil, torch, nested=False):
     return rec
 
 
+def host_round_trip(torch, n=2000):
+    """What a device-side Broyden loop could save: the host's part of one
+    iteration of the library's loop is a status read (a small device-to-host
+    copy after the iteration's last kernel) and a stream synchronisation. This
+    times that round trip with a tiny kernel in front, n times."""
+    stream = torch.cuda.Stream()
+    x = torch.zeros(8, dtype=torch.int32, device="cuda")
+    h = torch.empty(8, dtype=torch.int32).pin_memory()
+    with torch.cuda.stream(stream):
+        for _ in range(50):
+            x.add_(1)
+            h.copy_(x, non_blocking=True)
+            stream.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            x.add_(1)
+            h.copy_(x, non_blocking=True)
+            stream.synchronize()
+        dt = time.perf_counter() - t0
+    return 1e6 * dt / n
+
+
 def run_tether(fil, torch, steps=20, warmup=3, frac=0.25):
     """The 32k suspension with every fourth filament clamped at its base (Sec.
     5.2.1: Y_1 fixed, u_1 = 0): FIL_PAIR32, extrapolated initial guess (the
@@ -564,6 +602,7 @@ def run_suspension(args, fil, torch, world, rank, local):
     m = fil.Filaments(wl.seg_per_fil, precision=prec, stream=stream.cuda_stream, **params)
     m.init_straight(base, t, mu, None)
     m.set_external(Fext, None, follower)
+    m.set_j0_reuse(args.j0_reuse)
     if args.steric > 0:
         m.set_steric(args.steric, 1.1)
 
@@ -601,6 +640,7 @@ def run_suspension(args, fil, torch, world, rank, local):
 
     # ---- timed region: K steps, L2 flushed between steps ----
     a0, i0, k0 = m.counters()
+    jb0, jr0 = m.j0_stats()
     m.profile(True)
     m.profile_read()
     barrier()
@@ -613,6 +653,7 @@ def run_suspension(args, fil, torch, world, rank, local):
     n_pair_launch, pair_ms = m.profile_read()
     m.profile(False)
     a1, i1, k1 = m.counters()
+    jb1, jr1 = m.j0_stats()
     applies = a1 - a0
     pairs = applies * float(S) * S
     Y_timed = np.zeros((S, 3))
@@ -760,6 +801,29 @@ def run_suspension(args, fil, torch, world, rank, local):
             "roofline": pair_roofline(float(S) * S, pms, npl),
             "from": "the same state as the timed steps, same initial-guess rule"}
 
+        # ---- the other J0 policy (built every step / kept up to 4 steps) from st0 ----
+        other = 1 if args.j0_reuse > 1 else 4
+        mr = fil.Filaments(wl.seg_per_fil, precision=prec, stream=stream.cuda_stream, **params)
+        mr.set_state(*st0)
+        mr.set_external(Fext, None, follower)
+        mr.set_j0_reuse(other)
+        netr = None
+        if warm_mode is not None:
+            from paper_1903_12609_gb300 import warmstart
+            netr = warmstart.load(max_batch=max(64, n_fil), stream=stream.cuda_stream)
+            fil.fil_warm_attach(mr.ctx, netr, warm_mode)
+        rb0, rr0 = mr.j0_stats()
+        ms_r, its_r = timed_steps(mr, args.steps)
+        rb1, rr1 = mr.j0_stats()
+        mr.close()
+        if netr is not None:
+            fil.fil_mlp_destroy(netr)
+        extra["j0_policy_variant"] = {
+            "j0_reuse_max_age": other, "timesteps_per_s": args.steps / (ms_r * 1e-3),
+            "broyden_iters_per_step": float(np.mean(its_r)), "steps": args.steps,
+            "j0_builds": int(rb1 - rb0), "j0_reuses": int(rr1 - rr0),
+            "from": "the same state as the timed steps, same precision and initial guess"}
+
         # ---- the plain FP64 form from st0 (extrapolated start) ----
         if args.plain_steps > 0:
             mp = fil.Filaments(wl.seg_per_fil, precision=fil.FIL_FP64,
@@ -793,11 +857,25 @@ def run_suspension(args, fil, torch, world, rank, local):
                 "what": "one step from the same state with the extrapolated start, this "
                         "precision vs FIL_FP64, both converged to ||f||_inf <= tol a"}
 
-        # ---- the other configurations ----
-        extra["c1_mobility_3200"] = run_c1_mobility(fil, torch)
-        extra["c0_single_filament"] = run_c0_single(fil, torch)
-        extra["c3_ensemble256"] = run_ensemble(args, fil, torch, nested=True)
-        extra["tethered_suspension"] = run_tether(fil, torch)
+        # ---- host work per Broyden iteration (the case for a device-side loop) ----
+        rt = host_round_trip(torch)
+        iters_mean = float(np.mean(iters))
+        extra["host_loop_overhead"] = {
+            "round_trip_us": rt, "iterations_per_step": iters_mean,
+            "share_of_step": rt * 1e-3 * (iters_mean + 1) / (max_ms / args.steps),
+            "what": "a tiny kernel, a 32-byte device-to-host copy and a stream synchronisation, "
+                    "timed 2000 times: the host's part of each Broyden iteration (and of the "
+                    "step set-up), which a loop kept on the device would remove"}
+
+        # ---- the other configurations (a failure is reported in its record) ----
+        for key, fn in (("c1_mobility_3200", lambda: run_c1_mobility(fil, torch)),
+                        ("c0_single_filament", lambda: run_c0_single(fil, torch)),
+                        ("c3_ensemble256", lambda: run_ensemble(args, fil, torch, nested=True)),
+                        ("tethered_suspension", lambda: run_tether(fil, torch))):
+            try:
+                extra[key] = fn()
+            except Exception as exc:   # keep the headline line when a nested record fails
+                extra[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     else:
         m.close()
         if net is not None:
@@ -830,12 +908,14 @@ def run_suspension(args, fil, torch, world, rank, local):
             "precision_note": PRECISION_NOTE[args.precision], "j0": args.j0,
             "initial_guess": ("learned warm start (%s)" % args.warm) if warm_mode is not None
                              else "extrapolation",
+            "j0_reuse_max_age": args.j0_reuse,
             "steric_FS": args.steric if args.steric > 0 else None,
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "flushed between timed steps (256 MiB write)"},
         "timesteps_per_s": args.steps / (max_ms * 1e-3),
         "broyden_iters_per_step": float(np.mean(iters)),
         "mobility_applies": int(applies),
+        "j0_builds": int(jb1 - jb0), "j0_reuses": int(jr1 - jr0),
         "roofline": roof,
         "autotuned": ({"tile": tuned[0], "ctas_per_sm": tuned[1], "ms_per_apply": tuned[2]}
                       if tuned else None),
@@ -937,6 +1017,8 @@ def main():
     ap.add_argument("--extra", type=int, default=1,
                     help="1: also the nested records (variants, other configurations, oracle "
                          "comparison); 0: the headline suspension only (for profiling)")
+    ap.add_argument("--j0-reuse", type=int, default=4,
+                    help="keep J0 for up to this many steps (fil_set_j0_reuse; 1 = every step)")
     ap.add_argument("--j0", default="filament_rpy", choices=["filament_rpy", "drag"],
                     help="approximate Jacobian: filament RPY blocks (default) or App. B.2 drag")
     ap.add_argument("--n-fil", type=int, default=1000,

@@ -289,6 +289,24 @@ fil_status fil_step(fil_ctx *c, int32_t *iters);
 /* Change the timestep (takes effect at the next fil_broyden_begin). */
 fil_status fil_set_dt(fil_ctx *c, double dt);
 
+/* J0 reuse across timesteps. The paper builds J0 at the initial guess of every
+ * step (Sec. 3.2.2: "evaluated each timestep"); J0 only shapes the Broyden
+ * iterates (H_0 of Algorithm 2), not the converged solution, so its factors
+ * may be kept for several steps. With max_age > 1, fil_broyden_begin / fil_step
+ * keep the factors of the step that built them for at most max_age steps in
+ * all, and build new ones earlier when the last committed step took more than
+ * one Broyden iteration more than the step that built them, when the scheme
+ * weight times dt changed (first step, fil_set_dt), after fil_set_state or
+ * fil_init_straight, and with tethered filaments (whose J0 columns follow the
+ * prescribed motion). fil_step restarts a step that fails on reused factors
+ * with factors built for it. max_age = 1 (the default) builds J0 every step.
+ * FIL_EINVAL for max_age < 1, FIL_ESTATE inside a step. */
+fil_status fil_set_j0_reuse(fil_ctx *c, int32_t max_age);
+
+/* Steps whose J0 was built and steps that reused an earlier J0, since the
+ * context was created (either pointer may be NULL). */
+fil_status fil_j0_stats(const fil_ctx *c, int64_t *builds, int64_t *reuses);
+
 /* Counters since creation: RPY applies, Broyden iterations and kernels this
  * library launched (any pointer may be NULL). */
 fil_status fil_counters(const fil_ctx *c, int64_t *mobility_applies, int64_t *broyden_iters,

@@ -91,3 +91,24 @@ def loss_and_grad(params, x, t, norm, bf16=True):
             dz = (dz_r @ _r(W, bf16)) * (acts[l] > 0)
     g = np.concatenate([np.concatenate([dW.ravel(), db]) for dW, db in grads])
     return loss, g
+
+
+def grad_magnitudes(params, x, t, norm, bf16=True):
+    """Magnitude sums of the gradient: the backward pass of loss_and_grad with
+    every factor replaced by its absolute value, so entry (i, j) of a weight
+    gradient is sum_b |dz_b,i| |h_b,j| and entry i of a bias gradient
+    sum_b |dz_b,i|, with |dz| propagated as (|dz| |W|) * relu-mask. A bound on
+    the rounding error of a gradient entry is a multiple of its magnitude sum
+    (each term can carry a BF16 rounding of either factor)."""
+    out_mean, out_std = np.asarray(norm[2], np.float64), np.asarray(norm[3], np.float64)
+    y, (acts, yhat, layers) = forward(params, x, norm, bf16)
+    B = x.shape[0]
+    dz = np.abs(yhat - (np.asarray(t, dtype=np.float64) - out_mean) / out_std) / B
+    mags = [None] * 4
+    for l in range(3, -1, -1):
+        W, _ = layers[l]
+        dz_r = _r(dz, bf16)
+        mags[l] = (dz_r.T @ np.abs(acts[l]), dz.sum(axis=0))
+        if l > 0:
+            dz = (dz_r @ np.abs(_r(W, bf16))) * (acts[l] > 0)
+    return np.concatenate([np.concatenate([mW.ravel(), mb]) for mW, mb in mags])

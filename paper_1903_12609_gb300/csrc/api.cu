@@ -508,6 +508,7 @@ fil_status fil_set_state(fil_ctx *c, const double *Y, const double *q, const dou
     c->thist = 0;
     c->warm_corr_ok = 0;
     c->in_step = 0;
+    c->j0_age = -1;
     return FIL_OK;
 }
 
@@ -553,6 +554,7 @@ fil_status fil_init_straight(fil_ctx *c, const double *base, const double *t, co
     c->hist = 0;
     c->warm_corr_ok = 0;
     c->in_step = 0;
+    c->j0_age = -1;
     return FIL_OK;
 }
 
@@ -744,7 +746,7 @@ cudaError_t graph_for_current(fil_ctx *c, int *slot) {
     return cudaSuccess;
 }
 
-fil_status begin_step(fil_ctx *c, double *finf, bool use_net) {
+fil_status begin_step(fil_ctx *c, double *finf, bool use_net, bool force_j0 = false) {
     if (!c) return FIL_EINVAL;
     CK(cudaSetDevice(c->device));
     CK(cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), c->stream));
@@ -757,10 +759,24 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net) {
         CK(tether_resolve(c, c->Xk, c->txr));
         Xj = c->txr;
     }
-    if (c->j0_model == FIL_J0_DRAG)
-        CK(j0_build_factor(c, Xj));
-    else
-        CK(j0_dense_build_factor(c, Xj));
+    // J0 of an earlier step is reused while it is young enough, the scheme
+    // weight is unchanged and the iteration count has not risen (J0 only
+    // shapes the iterates; the converged X solves f(X) = 0 either way)
+    const double weight = (c->have_prev ? 2.0 / 3.0 : 1.0) * c->dt;
+    c->j0_reused = !force_j0 && c->j0_reuse_max > 1 && !c->tether_on && c->j0_age >= 1 &&
+                   c->j0_age < c->j0_reuse_max && weight == c->j0_weight &&
+                   c->j0_last_iters <= c->j0_iters_ref + 1;
+    if (!c->j0_reused) {
+        if (c->j0_model == FIL_J0_DRAG)
+            CK(j0_build_factor(c, Xj));
+        else
+            CK(j0_dense_build_factor(c, Xj));
+        c->j0_age = 0;
+        c->j0_weight = weight;
+        c->j0_builds += 1;
+    } else {
+        c->j0_reuses += 1;
+    }
     if (c->tether_on) CK(tether_j0_setup(c, j0_apply_free));
     StatusBlock sb;
     s = read_status(c, &sb);
@@ -906,6 +922,9 @@ fil_status fil_broyden_commit(fil_ctx *c) {
     }
     CK(commit_state(c, Xc));
     CK(warm_record_correction(c));
+    if (c->j0_age == 0) c->j0_iters_ref = c->iters_step;
+    if (c->j0_age >= 0) c->j0_age += 1;
+    c->j0_last_iters = c->iters_step;
     c->warm_corr_ok = 1;
     c->have_prev = 1;
     c->hist += 1;
@@ -918,8 +937,9 @@ fil_status fil_step(fil_ctx *c, int32_t *iters) {
     if (!c) return FIL_EINVAL;
     int32_t total = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
-        // a start from the network's prediction that fails restarts from the extrapolation
-        fil_status s = begin_step(c, nullptr, attempt == 0);
+        // a start from the network's prediction, or on the J0 of an earlier step,
+        // that fails restarts from the extrapolation with a J0 built for this step
+        fil_status s = begin_step(c, nullptr, attempt == 0, attempt > 0);
         if (s != FIL_OK) return s;
         int32_t conv = c->conv;
         while (!conv && s == FIL_OK) s = fil_broyden_step(c, &conv, nullptr);
@@ -929,10 +949,25 @@ fil_status fil_step(fil_ctx *c, int32_t *iters) {
             return fil_broyden_commit(c);
         }
         c->in_step = 0;
-        if (!c->warm_from_pred) return s;
-        c->warm_restart += 1;
+        if (!c->warm_from_pred && !c->j0_reused) return s;
+        if (c->warm_from_pred) c->warm_restart += 1;
     }
-    return FIL_ECUDA;   // not reached: the second attempt never starts from the prediction
+    return FIL_ECUDA;   // not reached: the second attempt uses neither
+}
+
+fil_status fil_set_j0_reuse(fil_ctx *c, int32_t max_age) {
+    if (!c) return FIL_EINVAL;
+    if (max_age < 1) return set_err(c, FIL_EINVAL, "fil_set_j0_reuse: max_age >= 1");
+    if (c->in_step) return set_err(c, FIL_ESTATE, "fil_set_j0_reuse: a step is in progress");
+    c->j0_reuse_max = max_age;
+    return FIL_OK;
+}
+
+fil_status fil_j0_stats(const fil_ctx *c, int64_t *builds, int64_t *reuses) {
+    if (!c) return FIL_EINVAL;
+    if (builds) *builds = c->j0_builds;
+    if (reuses) *reuses = c->j0_reuses;
+    return FIL_OK;
 }
 
 fil_status fil_set_dt(fil_ctx *c, double dt) {

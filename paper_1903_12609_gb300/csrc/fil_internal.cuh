@@ -155,6 +155,16 @@ struct fil_ctx {
     int64_t *auxofs;       // [M+1]
     int64_t aux_len;
     double j0_dp_bdt;      // scheme weight * dt of the current J0
+    // J0 reuse across steps (fil_set_j0_reuse): the factors of a step are kept
+    // for up to j0_reuse_max steps while the Broyden iteration count stays
+    // within one of that of the step that built them
+    int j0_reuse_max = 1;
+    int j0_age = -1;          // steps committed with the current factors; -1: none
+    int j0_iters_ref = 0;     // iterations of the step that built them
+    int j0_last_iters = 0;    // iterations of the last committed step
+    double j0_weight = 0.0;   // scheme weight * dt the current factors were built with
+    int j0_reused = 0;        // the current step runs on factors of an earlier step
+    int64_t j0_builds = 0, j0_reuses = 0;
 
     // staging for host pointers (6S doubles each)
     double *stage_a, *stage_b, *stage_c;

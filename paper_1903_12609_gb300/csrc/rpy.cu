@@ -34,13 +34,19 @@
 //    over G = #SMs x resident-CTAs; a CTA writes one partial per tile it
 //    touches into slot (cta + tile) and a deterministic reduce kernel sums
 //    them in CTA order. No atomics: results are bitwise reproducible.
-//  * Mixed precision: positions enter as FP32 hi/lo pairs so that d keeps
-//    ~2 ulp relative accuracy for close pairs; each target sums kRpyComp pair
-//    terms in FP32 and folds them into a (hi, lo) compensated accumulator
-//    (TwoSum); the reduce adds the partials in FP64.
+//  * Mixed precision: positions are stored as FP32 hi/lo pairs (hi = fl32(Y),
+//    lo = fl32(Y - hi)). The inner loop forms d from the hi parts alone,
+//    which carries the rounding of the coordinates (~ulp(|Y|)) and is
+//    accurate for pairs that are far apart compared with that; a group of
+//    kRpyComp sources in which a warp met a pair closer than R_c = 4a is
+//    recomputed with d = (t_hi - s_hi) + (t_lo - s_lo), which keeps ~2 ulp of
+//    relative accuracy for close pairs. Each target sums kRpyComp pair terms
+//    in FP32 and folds them into a (hi, lo) compensated accumulator (TwoSum);
+//    the reduce adds the partials in FP64.
 //  * The inner loop is branch-free (far form only, tracking the smallest r^2);
-//    overlapping pairs are rare, so a group of kRpyComp sources in which a warp
-//    met one is recomputed with the exact far/overlap branches.
+//    close pairs are rare. A recomputed group in which a warp met an
+//    overlapping pair (r < 2a) is computed once more with the exact far /
+//    overlap branches.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +62,7 @@ constexpr float kFarPad = 1.0e5f;   // position of padding sources (they carry n
 
 struct RpyConst32 {
     float near2;       // (2a)^2
+    float close2;      // R_c^2 = (4a)^2: groups with a pair this close use hi/lo differences
     float k23a2;       // 2a^2/3
     float k2a2;        // 2a^2
     float ov_A0, ov_A1;          // A = ov_A0 - ov_A1 r
@@ -74,6 +81,7 @@ template <typename T, typename K>
 __host__ K make_const(double a) {
     K k;
     k.near2 = (T)(4.0 * a * a);
+    if constexpr (sizeof(T) == 4) k.close2 = (T)(16.0 * a * a);
     k.k23a2 = (T)(2.0 * a * a / 3.0);
     k.k2a2 = (T)(2.0 * a * a);
     k.ov_A0 = (T)(4.0 / (3.0 * a));
@@ -151,15 +159,18 @@ __device__ __forceinline__ int64_t segment_at(const SysMap &m, int64_t P, int64_
 }
 
 // ---------------------------------------------------------------------------
-// Pack: FP64 (Y, FT) -> padded FP32 source records, 3 float4 per segment:
-//   [0] = (hi_x, hi_y, hi_z, F_x), [1] = (lo_x, lo_y, lo_z, F_y),
-//   [2] = (T_x, T_y, T_z, F_z), with hi = fl32(Y), lo = fl32(Y - hi).
+// Pack: FP64 (Y, FT) -> padded FP32 source records of 12 values per segment.
+// Positions are taken relative to the first segment, y = Y - Y_0 (the apply is
+// translation invariant, and the FP32 rounding of y then depends on the extent
+// of the suspension, not on where it sits), hi = fl32(y), lo = fl32(y - hi),
+// negated:
+//   -hi_x -hi_y -hi_z  F_x F_y F_z  T_x T_y T_z  -lo_z -lo_x -lo_y
+// Sources 2p and 2p+1 share the kRpyPairF4 float4 at src + kRpyPairF4 p;
+// value c of source h sits at float 2c + h, so each float2 holds one
+// component of both (even, odd) and the far-form loop, which needs no lo
+// part, reads the first 4.5 float4 of a record.
 // Padding records sit far away with zero load, so they add exactly zero.
 // ---------------------------------------------------------------------------
-// Packed layout: sources 2p and 2p+1 share the kRpyPairF4 float4 at
-// src + kRpyPairF4 p; each float2 holds one component of both (even, odd),
-// positions negated:
-//   (-hi_x, -hi_y) (-hi_z, F_x) (-lo_x, -lo_y) (-lo_z, F_y) (T_x, T_y) (T_z, F_z).
 __global__ void pack32_kernel(const double *__restrict__ Y, const double *__restrict__ FT,
                               int64_t S, int64_t Spad, SysMap sm, float4 *__restrict__ src) {
     const int64_t P = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -168,17 +179,16 @@ __global__ void pack32_kernel(const double *__restrict__ Y, const double *__rest
     constexpr int kV = 2 * kRpyPairF4;
     float v[kV];
     if (i >= 0) {
-        const double y0 = Y[3 * i], y1 = Y[3 * i + 1], y2 = Y[3 * i + 2];
+        const double y0 = Y[3 * i] - Y[0], y1 = Y[3 * i + 1] - Y[1], y2 = Y[3 * i + 2] - Y[2];
         const float h0 = __double2float_rn(y0), h1 = __double2float_rn(y1),
                     h2 = __double2float_rn(y2);
         const double *f = FT + 6 * i;
-        v[0] = -h0; v[1] = -h1; v[2] = -h2; v[3] = __double2float_rn(f[0]);
-        v[4] = -__double2float_rn(y0 - (double)h0);
-        v[5] = -__double2float_rn(y1 - (double)h1);
-        v[6] = -__double2float_rn(y2 - (double)h2);
-        v[7] = __double2float_rn(f[1]);
-        v[8] = __double2float_rn(f[3]); v[9] = __double2float_rn(f[4]);
-        v[10] = __double2float_rn(f[5]); v[11] = __double2float_rn(f[2]);
+        v[0] = -h0; v[1] = -h1; v[2] = -h2;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[3 + c] = __double2float_rn(f[c]);
+        v[9] = -__double2float_rn(y2 - (double)h2);
+        v[10] = -__double2float_rn(y0 - (double)h0);
+        v[11] = -__double2float_rn(y1 - (double)h1);
     } else {
         v[0] = v[1] = v[2] = -kFarPad;
 #pragma unroll
@@ -223,72 +233,83 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return y;
 }
 
-// One pair in FP32: target (hi, lo) position vs. source record (s0, s1, s2).
-__device__ __forceinline__ void pair32(float thx, float thy, float thz, float tlx, float tly,
-                                       float tlz, const float4 s0, const float4 s1,
-                                       const float4 s2, const RpyConst32 &k, float *acc) {
-    const float dx = __fsub_rn(thx, s0.x) + __fsub_rn(tlx, s1.x);
-    const float dy = __fsub_rn(thy, s0.y) + __fsub_rn(tly, s1.y);
-    const float dz = __fsub_rn(thz, s0.z) + __fsub_rn(tlz, s1.z);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float A, B, C, D, G;
-    if (__builtin_expect(r2 < k.near2, 0)) {
-        const float r = sqrtf(r2);
-        const float rinv = r > 0.f ? 1.0f / r : 0.f;
-        A = fmaf(-k.ov_A1, r, k.ov_A0);
-        B = k.ov_B * rinv;
-        C = fmaf(k.ov_C3 * r2, r, fmaf(-k.ov_C1, r, k.ov_C0));
-        D = fmaf(k.ov_D0, rinv, -k.ov_D1 * r);
-        G = fmaf(-k.ov_G1, r, k.ov_G0);
-    } else {
-        const float rinv = rsqrt_approx(r2);
-        const float rinv2 = rinv * rinv;
-        const float rinv3 = rinv * rinv2;
-        const float rinv5 = rinv3 * rinv2;
-        A = fmaf(k.k23a2, rinv3, rinv);
-        B = fmaf(-k.k2a2, rinv5, rinv3);
-        C = -0.5f * rinv3;
-        D = 1.5f * rinv5;
-        G = rinv3;
-    }
-    const float Fx = s0.w, Fy = s1.w, Fz = s2.w;
-    const float Tx = s2.x, Ty = s2.y, Tz = s2.z;
-    const float bF = B * fmaf(dx, Fx, fmaf(dy, Fy, dz * Fz));
-    const float dT = D * fmaf(dx, Tx, fmaf(dy, Ty, dz * Tz));
-    const float ex = G * dx, ey = G * dy, ez = G * dz;
-    acc[0] = fmaf(A, Fx, fmaf(bF, dx, fmaf(Ty, ez, fmaf(-Tz, ey, acc[0]))));
-    acc[1] = fmaf(A, Fy, fmaf(bF, dy, fmaf(Tz, ex, fmaf(-Tx, ez, acc[1]))));
-    acc[2] = fmaf(A, Fz, fmaf(bF, dz, fmaf(Tx, ey, fmaf(-Ty, ex, acc[2]))));
-    acc[3] = fmaf(C, Tx, fmaf(dT, dx, fmaf(Fy, ez, fmaf(-Fz, ey, acc[3]))));
-    acc[4] = fmaf(C, Ty, fmaf(dT, dy, fmaf(Fz, ex, fmaf(-Fx, ez, acc[4]))));
-    acc[5] = fmaf(C, Tz, fmaf(dT, dz, fmaf(Fx, ey, fmaf(-Fy, ex, acc[5]))));
-}
-
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
 
-// pair32_far for one target and the two sources of a packed record (q0..q5),
-// lane x = even source, lane y = odd source; same operations, same rounding.
-__device__ __forceinline__ void pair32x2_far(const float2 *th, const float2 *tl, const float4 *q,
-                                             float2 k23, float2 nk2, float2 *acc,
-                                             float &rmin2) {
-    const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3], q4 = q[4], q5 = q[5];
-    const float2 dx = __fadd2_rn(__fadd2_rn(th[0], f2(q0.x, q0.y)), __fadd2_rn(tl[0], f2(q2.x, q2.y)));
-    const float2 dy = __fadd2_rn(__fadd2_rn(th[1], f2(q0.z, q0.w)), __fadd2_rn(tl[1], f2(q2.z, q2.w)));
-    const float2 dz = __fadd2_rn(__fadd2_rn(th[2], f2(q1.x, q1.y)), __fadd2_rn(tl[2], f2(q3.x, q3.y)));
+// sqrt(x) and 1/x: one MUFU operation each (PTX sqrt.approx.ftz.f32,
+// rcp.approx.ftz.f32; a few ulp at most, no slow path).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Exact coefficients of one pair (one lane): the far form for r^2 >= (2a)^2,
+// the overlapping-sphere form below it and the self values at r = 0, chosen
+// without a branch (both are evaluated; this runs in recomputed groups only).
+__device__ __forceinline__ void coef_exact(float r2, const RpyConst32 &k, float &A, float &B,
+                                           float &C, float &D, float &G) {
+    const bool ov = r2 < k.near2;
+    const float rinv = rsqrt_approx(fmaxf(r2, k.near2));   // the far form's, finite everywhere
+    const float rinv2 = rinv * rinv;
+    const float rinv3 = rinv * rinv2;
+    const float rinv5 = rinv3 * rinv2;
+    const float r = sqrt_approx(r2);
+    const float ri = r > 0.f ? rcp_approx(r) : 0.f;
+    A = ov ? fmaf(-k.ov_A1, r, k.ov_A0) : fmaf(k.k23a2, rinv3, rinv);
+    B = ov ? k.ov_B * ri : fmaf(-k.k2a2, rinv5, rinv3);
+    C = ov ? fmaf(k.ov_C3 * r2, r, fmaf(-k.ov_C1, r, k.ov_C0)) : -0.5f * rinv3;
+    D = ov ? fmaf(k.ov_D0, ri, -k.ov_D1 * r) : 1.5f * rinv5;
+    G = ov ? fmaf(-k.ov_G1, r, k.ov_G0) : rinv3;
+}
+
+// The pair terms of one target and the two sources of a packed record (q),
+// lane x = even source, lane y = odd source, tracking the smallest r^2 seen.
+// EXACT = false (the inner loop): d from the hi parts only and the far form
+// for every pair, branch-free; whatever it produces for close, overlapping or
+// coincident pairs (Inf or NaN at r = 0) is discarded by the caller, which
+// recomputes such groups. EXACT = true (recomputed groups): d = (t_hi - s_hi) +
+// (t_lo - s_lo) and the exact coefficients of every pair (coef_exact).
+template <bool EXACT>
+__device__ __forceinline__ void pair32x2(const float2 *th, const float2 *tl, const float4 *q,
+                                         const RpyConst32 &k, float2 k23, float2 nk2,
+                                         float2 *acc, float &rmin2) {
+    const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+    const float2 q4 = reinterpret_cast<const float2 *>(q + 4)[0];
+    float2 dx = __fadd2_rn(th[0], f2(q0.x, q0.y));
+    float2 dy = __fadd2_rn(th[1], f2(q0.z, q0.w));
+    float2 dz = __fadd2_rn(th[2], f2(q1.x, q1.y));
+    if (EXACT) {
+        const float4 q5 = q[5];
+        const float2 lz = reinterpret_cast<const float2 *>(q + 4)[1];
+        dx = __fadd2_rn(dx, __fadd2_rn(tl[0], f2(q5.x, q5.y)));
+        dy = __fadd2_rn(dy, __fadd2_rn(tl[1], f2(q5.z, q5.w)));
+        dz = __fadd2_rn(dz, __fadd2_rn(tl[2], lz));
+    }
     const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
     rmin2 = fminf(rmin2, fminf(r2.x, r2.y));
-    const float2 rinv = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-    const float2 rinv2 = __fmul2_rn(rinv, rinv);
-    const float2 rinv3 = __fmul2_rn(rinv, rinv2);
-    const float2 rinv5 = __fmul2_rn(rinv3, rinv2);
-    const float2 A = __ffma2_rn(k23, rinv3, rinv);
-    const float2 B = __ffma2_rn(nk2, rinv5, rinv3);
-    const float2 C = __fmul2_rn(f2(-0.5f, -0.5f), rinv3);
-    const float2 D = __fmul2_rn(f2(1.5f, 1.5f), rinv5);
-    const float2 G = rinv3;
-    const float2 Fx = f2(q1.z, q1.w), Fy = f2(q3.z, q3.w), Fz = f2(q5.z, q5.w);
-    const float2 Tx = f2(q4.x, q4.y), Ty = f2(q4.z, q4.w), Tz = f2(q5.x, q5.y);
+    float2 A, B, C, D, G;
+    if (!EXACT) {
+        const float2 rinv = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        const float2 rinv2 = __fmul2_rn(rinv, rinv);
+        const float2 rinv3 = __fmul2_rn(rinv, rinv2);
+        const float2 rinv5 = __fmul2_rn(rinv3, rinv2);
+        A = __ffma2_rn(k23, rinv3, rinv);
+        B = __ffma2_rn(nk2, rinv5, rinv3);
+        C = __fmul2_rn(f2(-0.5f, -0.5f), rinv3);
+        D = __fmul2_rn(f2(1.5f, 1.5f), rinv5);
+        G = rinv3;
+    } else {
+        coef_exact(r2.x, k, A.x, B.x, C.x, D.x, G.x);
+        coef_exact(r2.y, k, A.y, B.y, C.y, D.y, G.y);
+    }
+    const float2 Fx = f2(q1.z, q1.w), Fy = f2(q2.x, q2.y), Fz = f2(q2.z, q2.w);
+    const float2 Tx = f2(q3.x, q3.y), Ty = f2(q3.z, q3.w), Tz = q4;
     const float2 bF = __fmul2_rn(B, __ffma2_rn(dx, Fx, __ffma2_rn(dy, Fy, __fmul2_rn(dz, Fz))));
     const float2 dT = __fmul2_rn(D, __ffma2_rn(dx, Tx, __ffma2_rn(dy, Ty, __fmul2_rn(dz, Tz))));
     const float2 ex = __fmul2_rn(G, dx), ey = __fmul2_rn(G, dy), ez = __fmul2_rn(G, dz);
@@ -303,13 +324,14 @@ __device__ __forceinline__ void pair32x2_far(const float2 *th, const float2 *tl,
     acc[5] = __ffma2_rn(C, Tz, __ffma2_rn(dT, dz, __ffma2_rn(Fx, ey, __ffma2_rn(nFy, ex, acc[5]))));
 }
 
-// Scalar record (pair32's layout) of source h (0 even, 1 odd) of a packed record.
+// Scalar record ((hi, F_x), (lo, F_y), (T, F_z)) of source h (0 even, 1 odd) of
+// a packed record.
 __device__ __forceinline__ void unpack_source(const float4 *q, int h, float4 &s0, float4 &s1,
                                               float4 &s2) {
     const float *f = reinterpret_cast<const float *>(q) + h;
     s0 = make_float4(-f[0], -f[2], -f[4], f[6]);
-    s1 = make_float4(-f[8], -f[10], -f[12], f[14]);
-    s2 = make_float4(f[16], f[18], f[20], f[22]);
+    s1 = make_float4(-f[20], -f[22], -f[18], f[8]);
+    s2 = make_float4(f[12], f[14], f[16], f[10]);
 }
 
 // One pair in FP64 (record layout: Y, F, T).
@@ -349,6 +371,23 @@ __device__ __forceinline__ void pair64(double tx, double ty, double tz, const do
     acc[5] = fma(C, Tz, fma(dT, dz, fma(Fx, ey, fma(-Fy, ex, acc[5]))));
 }
 
+// Asynchronous copy of one chunk of source records (kRec float4) from global to
+// shared memory, 16 bytes per cp.async, spread over the CTA's threads; the
+// copies land when cp_async_wait_all returns (plus a barrier for the others').
+template <int kRec>
+__device__ __forceinline__ void stage_chunk(float4 *dst, const float4 *__restrict__ g, int tid) {
+#pragma unroll
+    for (int i = tid; i < kRec; i += kRpyThreads) {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + i);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(g + i) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // Unit range of CTA b in the stream-K split of W units over G CTAs.
 __device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
     return (b * W) / G;
@@ -383,23 +422,22 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
         const float4 *srcs = src + kRec * (src0 / kRpyChunk);   // this tile's system
         const int64_t ptile = smap.tile_id ? smap.tile_id[tile] : tile;   // padded tile
 
-        float th[kT][3], tl[kT][3];
+        // target positions (hi parts) broadcast to both lanes; the lo parts are
+        // read again only when a group is recomputed
+        // record of target t: trec + t * kTRecStep
+        constexpr int kTRecStep = kRpyPairF4 * (kRpyThreads / 2);
+        const float4 *trec = src + kRpyPairF4 * ((ptile * kTile + tid) >> 1);
+        float2 thb[kT][3];
 #pragma unroll
         for (int t = 0; t < kT; ++t) {
             const int64_t n = ptile * kTile + t * kRpyThreads + tid;
             float4 a0, a1, a2;
             unpack_source(src + kRpyPairF4 * (n >> 1), (int)(n & 1), a0, a1, a2);
-            th[t][0] = a0.x; th[t][1] = a0.y; th[t][2] = a0.z;
-            tl[t][0] = a1.x; tl[t][1] = a1.y; tl[t][2] = a1.z;
+            thb[t][0] = f2(a0.x, a0.x);
+            thb[t][1] = f2(a0.y, a0.y);
+            thb[t][2] = f2(a0.z, a0.z);
         }
-        float2 thb[kT][3], tlb[kT][3];   // targets broadcast to both lanes
-#pragma unroll
-        for (int t = 0; t < kT; ++t)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                thb[t][c] = f2(th[t][c], th[t][c]);
-                tlb[t][c] = f2(tl[t][c], tl[t][c]);
-            }
+        const int tpar = tid & 1;   // even / odd record slot of every target of this thread
         const float2 k23 = f2(k.k23a2, k.k23a2), nk2 = f2(-k.k2a2, -k.k2a2);
         float hi[kT][6], lo[kT][6];
 #pragma unroll
@@ -408,62 +446,54 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
             for (int c = 0; c < 6; ++c) hi[t][c] = lo[t][c] = 0.f;
 
         // first chunk -> buffer 0
-        {
-            const float4 *g = srcs + kRec * c_begin;
-            for (int i = tid; i < kRec; i += kRpyThreads) sm[0][i] = g[i];
-        }
+        stage_chunk<kRec>(sm[0], srcs + kRec * c_begin, tid);
+        cp_async_wait_all();
         __syncthreads();
 
         for (int64_t ch = c_begin; ch < c_end; ++ch) {
             const int buf = (int)((ch - c_begin) & 1);
-            // prefetch the next chunk into registers while computing this one
-            constexpr int kPre = (kRec + kRpyThreads - 1) / kRpyThreads;
-            float4 pre[kPre];
+            // the next chunk streams into the other buffer while this one is computed
+            // (that buffer was last read before the barrier that ended the previous chunk)
             const bool has_next = (ch + 1 < c_end);
-            if (has_next) {
-                const float4 *g = srcs + kRec * (ch + 1);
-#pragma unroll
-                for (int r = 0; r < kPre; ++r)
-                    if (tid + r * kRpyThreads < kRec) pre[r] = g[tid + r * kRpyThreads];
-            }
+            if (has_next) stage_chunk<kRec>(sm[buf ^ 1], srcs + kRec * (ch + 1), tid);
             const float4 *s = sm[buf];
 #pragma unroll 1
             for (int grp = 0; grp < kRpyChunk / kRpyComp; ++grp) {
+                const float4 *qg = s + kRpyPairF4 * (grp * (kRpyComp / 2));
                 float2 acc2[kT][6];
 #pragma unroll
                 for (int t = 0; t < kT; ++t)
 #pragma unroll
                     for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
-                float rmin2 = k.near2;
+                float rmin2 = k.close2;
 #pragma unroll (kRpyUnroll / 2)
                 for (int jp = 0; jp < kRpyComp / 2; ++jp) {
-                    const float4 *q = s + kRpyPairF4 * (grp * (kRpyComp / 2) + jp);
 #pragma unroll
                     for (int t = 0; t < kT; ++t)
-                        pair32x2_far(thb[t], tlb[t], q, k23, nk2, acc2[t], rmin2);
+                        pair32x2<false>(thb[t], thb[t], qg + kRpyPairF4 * jp, k, k23, nk2,
+                                        acc2[t], rmin2);
+                }
+                if (__any_sync(0xffffffffu, rmin2 < k.close2)) {
+                    // a pair closer than R_c (or overlapping): redo the group with hi/lo
+                    // differences and the exact coefficients
+#pragma unroll
+                    for (int t = 0; t < kT; ++t) {   // one target at a time (fewer live registers)
+                        float4 a0, a1, a2;
+                        unpack_source(trec + t * kTRecStep, tpar, a0, a1, a2);
+                        const float2 tlb[3] = {f2(a1.x, a1.x), f2(a1.y, a1.y), f2(a1.z, a1.z)};
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
+#pragma unroll 1
+                        for (int jp = 0; jp < kRpyComp / 2; ++jp)
+                            pair32x2<true>(thb[t], tlb, qg + kRpyPairF4 * jp, k, k23, nk2,
+                                           acc2[t], rmin2);
+                    }
                 }
                 float acc[kT][6];
 #pragma unroll
                 for (int t = 0; t < kT; ++t)
 #pragma unroll
                     for (int c = 0; c < 6; ++c) acc[t][c] = __fadd_rn(acc2[t][c].x, acc2[t][c].y);
-                if (__any_sync(0xffffffffu, rmin2 < k.near2)) {
-                    // an overlapping (or self) pair: redo this group with the exact branches
-#pragma unroll
-                    for (int t = 0; t < kT; ++t)
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) acc[t][c] = 0.f;
-#pragma unroll 1
-                    for (int j = 0; j < kRpyComp; ++j) {
-                        float4 s0, s1, s2;
-                        unpack_source(s + kRpyPairF4 * ((grp * kRpyComp + j) >> 1), j & 1, s0, s1,
-                                      s2);
-#pragma unroll
-                        for (int t = 0; t < kT; ++t)
-                            pair32(th[t][0], th[t][1], th[t][2], tl[t][0], tl[t][1], tl[t][2], s0,
-                                   s1, s2, k, acc[t]);
-                    }
-                }
 #pragma unroll
                 for (int t = 0; t < kT; ++t)
 #pragma unroll
@@ -474,11 +504,7 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
                         lo[t][c] = __fadd_rn(lo[t][c], e);
                     }
             }
-            if (has_next) {
-#pragma unroll
-                for (int r = 0; r < kPre; ++r)
-                    if (tid + r * kRpyThreads < kRec) sm[buf ^ 1][tid + r * kRpyThreads] = pre[r];
-            }
+            if (has_next) cp_async_wait_all();
             __syncthreads();
         }
 

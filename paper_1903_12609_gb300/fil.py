@@ -35,7 +35,7 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_tc_gemm_bf16", "fil_warm_features", "fil_warm_targets", "fil_warm_attach",
             "fil_warm_stats", "fil_create_ensemble", "fil_sys_stats", "fil_pair_count",
             "fil_set_graph", "fil_autotune", "fil_set_steric", "fil_set_tether",
-            "fil_get_tether", "fil_fma_peak"]
+            "fil_get_tether", "fil_fma_peak", "fil_set_j0_reuse", "fil_j0_stats"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_SEG = 800, 256, 192, 32
 MLP_NPARAM = 256 * 800 + 256 + 2 * (256 * 256 + 256) + 192 * 256 + 192
 FIL_WARM_BEST_OF_TWO, FIL_WARM_PREDICTION_FIRST = 0, 1
@@ -88,6 +88,8 @@ def load_library(path=LIB_PATH):
         "fil_profile_read": [P, I64, D],
         "fil_rpy_apply_noalloc": [ctypes.c_int64, P, P, P, ctypes.c_double, ctypes.c_double, P],
         "fil_fma_peak": [ctypes.c_int32, D, D],
+        "fil_set_j0_reuse": [P, ctypes.c_int32],
+        "fil_j0_stats": [P, I64, I64],
         "fil_mlp_create": [ctypes.c_int64, P, ctypes.POINTER(P)],
         "fil_mlp_destroy": [P],
         "fil_mlp_set_params": [P, P],
@@ -286,6 +288,16 @@ def fil_step(ctx):
 
 def fil_set_dt(ctx, dt):
     _check(ctx, _lib.fil_set_dt(ctx, float(dt)))
+
+
+def fil_set_j0_reuse(ctx, max_age):
+    _check(ctx, _lib.fil_set_j0_reuse(ctx, int(max_age)))
+
+
+def fil_j0_stats(ctx):
+    b, r = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, _lib.fil_j0_stats(ctx, ctypes.byref(b), ctypes.byref(r)))
+    return b.value, r.value
 
 
 def fil_counters(ctx):

@@ -395,3 +395,41 @@ def test_residual_parity_across_small_angle_branches(fil, unorm):
         f = np.zeros(6 * lay.S)
         m.residual(X, f)
     np.testing.assert_allclose(f, ref, rtol=0, atol=1e-12 * max(1.0, np.abs(st.Y).max()))
+
+
+@pytest.mark.parametrize("model", J0_MODELS)
+def test_j0_reuse_keeps_the_converged_trajectory(fil, model):
+    """J0 only shapes the iterates of Algorithm 2: with the factors of one step
+    reused for up to 4 steps (fil_set_j0_reuse) every step still converges to
+    ||f||_inf <= tol a, and the trajectory stays on the oracle's (which builds J0
+    every step) to within the tolerance the iterates are solved to."""
+    lay, p, st, ext, _ = _system([32] * 5, 71, tol=1e-10, dt=0.3)
+    with _gpu(fil, lay, p, st, ext, j0=model[0]) as m:
+        m.set_j0_reuse(4)
+        Y = np.zeros((lay.S, 3))
+        for _ in range(8):
+            st, _ = fo.step(lay, p, st, ext, j0_model=model[1])
+            m.step()
+            m.get_state(Y, None, None, None, None)
+            np.testing.assert_allclose(Y, st.Y, rtol=0, atol=1e-8)
+        builds, reuses = m.j0_stats()
+        assert builds + reuses == 8 and reuses >= 3, (builds, reuses)
+        # a new state invalidates the factors: the next step builds J0
+        m.set_state(st.Y, st.q)
+        m.step()
+        assert m.j0_stats()[0] == builds + 1
+
+
+def test_j0_reuse_off_and_argument_checks(fil):
+    lay, p, st, ext, _ = _system([16] * 3, 72, tol=1e-10, dt=0.3)
+    with _gpu(fil, lay, p, st, ext) as m:
+        for _ in range(3):
+            m.step()
+        assert m.j0_stats() == (3, 0)           # the default builds J0 every step
+        with pytest.raises(fil.FilError) as e:
+            m.set_j0_reuse(0)
+        assert e.value.status == fil.FIL_EINVAL
+        m.broyden_begin()
+        with pytest.raises(fil.FilError) as e:
+            m.set_j0_reuse(3)
+        assert e.value.status == fil.FIL_ESTATE

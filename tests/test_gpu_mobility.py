@@ -11,8 +11,12 @@ pair term carries <= ~12 roundings (hi/lo difference, rsqrt, products) and the
 inputs are rounded to FP32 once; the compensated fold of the group sums and
 the FP64 reduce add O(u^2).
 """
+import os
+
 import numpy as np
 import pytest
+
+from conftest import MIXED_MAX_C
 
 torch = pytest.importorskip("torch")
 
@@ -46,12 +50,16 @@ def _gpu_apply(fil, segs, Y, FT, prec, host=False, a=1.0, eta=1.0):
         return VW.cpu().numpy()
 
 
-def _check_mixed(got, ref, ref_abs):
+def _check_mixed(got, ref, ref_abs, name=None):
     bound = C_MIXED * U32 * ref_abs
     err = np.abs(got - ref)
-    assert np.all(err <= bound), float((err / np.maximum(ref_abs, 1e-300)).max() / U32)
+    c = err / np.maximum(ref_abs, 1e-300) / U32
+    if name is None:
+        name = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+    MIXED_MAX_C[name] = max(MIXED_MAX_C.get(name, 0.0), float(c.max()))
+    assert np.all(err <= bound), "max c = %.2f" % float(c.max())
     # typical error is a few ulps of B
-    assert np.median(err / np.maximum(ref_abs, 1e-300)) < 8 * U32
+    assert np.median(c) < 8, "median c = %.2f" % float(np.median(c))
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
@@ -97,6 +105,20 @@ def test_overlaps_and_coincident_segments(fil, prec):
         np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
     else:
         _check_mixed(got, ref, ref_abs)
+
+
+@pytest.mark.parametrize("shift", [(150.0, -90.0, 200.0), (-3000.0, 2500.0, 1000.0)])
+def test_far_from_origin(fil, shift):
+    """The C1 workload moved away from the origin. The far-form loop forms d
+    from the FP32 hi parts of the coordinates (their rounding kept for pairs
+    beyond R_c = 4a; closer pairs are recomputed with hi/lo differences); the
+    coordinates are taken relative to the first segment, so the error does not
+    grow with the distance from the origin. Same bound as everywhere."""
+    Y, FT = mobility_inputs(100, 32, seed=9)
+    Y = Y + np.asarray(shift)
+    ref, ref_abs = rpy.apply(Y, FT, with_abs=True, nthreads=8)
+    got = _gpu_apply(fil, [32] * 100, Y, FT, fil.FIL_PAIR32)
+    _check_mixed(got, ref, ref_abs)
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])

@@ -155,8 +155,11 @@ def _motor(N=20, w=0.05, Sp=30.0):
 
 @pytest.mark.parametrize("model", J0_MODELS)
 def test_motor_steps_match_oracle(fil, model):
+    """Motor steps against the oracle; J0 reuse is requested and must not apply
+    (the tethered J0 columns follow the prescribed motion of every step)."""
     lay, p, st, tether = _motor()
     with _gpu(fil, lay, p, st, None, tether(1), j0=model[0]) as m:
+        m.set_j0_reuse(5)
         Y = np.zeros((lay.S, 3))
         lam = np.zeros((1, 6))
         for j in range(1, 13):
@@ -170,6 +173,7 @@ def test_motor_steps_match_oracle(fil, model):
             np.testing.assert_allclose(Y, st.Y, rtol=0, atol=1e-8)
             np.testing.assert_allclose(Y[0], teth.Y1[0], rtol=0, atol=1e-12)
             np.testing.assert_allclose(lam, st.tlam, rtol=0, atol=1e-7 * np.abs(st.tlam).max())
+        assert m.j0_stats()[1] == 0
 
 
 @pytest.mark.parametrize("graph", [False, True])

@@ -161,16 +161,19 @@ WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 
 @pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="no trained warm-start network")
 def test_trained_network_starts_closer(fil):
-    """The committed network, on 200 filaments of the suspension workload (a
-    seed it was not trained on), continuing from the same state as the plain
-    solve: the start it gives (best of prediction and extrapolation) has a
-    smaller residual on average, the prediction is taken in most steps, and the
-    Broyden iterations do not grow; every step converges to the same tolerance."""
+    """What the trained network gains: the committed network on the full
+    suspension workload (1000 filaments x 32, a seed it was not trained on),
+    30 steps continuing from the same state as the plain solve. The start it
+    gives has a smaller residual on average (mean log10 ||f(X_0)||_inf at least
+    0.3 lower), the prediction is taken in most steps, and the Broyden
+    iterations per step fall by at least 5%; every step converges to the same
+    tolerance (the plain solve judges each step)."""
     from paper_1903_12609_gb300 import warmstart
-    net = warmstart.load(WEIGHTS, max_batch=256)
-    ev = warmstart.evaluate(torch, net, 200, 20, seed=11)
+    net = warmstart.load(WEIGHTS, max_batch=1024)
+    ev = warmstart.evaluate(torch, net, 1000, 30, seed=11)
     fil.fil_mlp_destroy(net)
-    plain, best = ev["plain"], ev["best_of_two"]
-    assert best["log10_f0"] < plain["log10_f0"], ev
+    plain, best, first = ev["plain"], ev["best_of_two"], ev["prediction_first"]
+    assert best["log10_f0"] < plain["log10_f0"] - 0.3, ev
     assert best["from_prediction"] > best["from_extrapolation"], ev
-    assert best["iters_per_step"] <= plain["iters_per_step"] + 0.25, ev
+    assert first["iters_per_step"] <= 0.95 * plain["iters_per_step"], ev
+    assert best["iters_per_step"] <= 0.95 * plain["iters_per_step"], ev

@@ -70,3 +70,24 @@ def test_bf16_rounding_ties_to_even():
     exp = np.array([one, one, one + 2.0 ** -6, one + 2.0 ** -7, -2.5, one + 2.0 ** -7])
     np.testing.assert_array_equal(mlp.bf16_round(vals), exp)
     assert mlp.bf16_bits(np.array([1.0]))[0] == 0x3F80
+
+
+def test_gradient_magnitudes_equal_the_gradient_when_nothing_cancels():
+    """With non-negative weights, biases, normalised inputs and output errors
+    (targets below the outputs), no term of the backward pass is negative, so
+    the magnitude sums are the gradient itself; in general they bound it."""
+    rng = np.random.default_rng(4)
+    p = np.abs(_net(rng))
+    norm = _norm(rng)
+    x = norm[0] + norm[1] * np.abs(rng.standard_normal((6, NIN)))
+    y, _ = mlp.forward(p, x, norm, bf16=False)
+    t = y - np.abs(rng.standard_normal(y.shape)) - 0.1
+    _, g = mlp.loss_and_grad(p, x, t, norm, bf16=False)
+    m = mlp.grad_magnitudes(p, x, t, norm, bf16=False)
+    np.testing.assert_allclose(m, g, rtol=1e-12, atol=1e-300)
+    # random signs: |g| <= magnitude sum, entry by entry
+    p2, t2 = _net(rng), rng.standard_normal((6, 192))
+    x2 = rng.standard_normal((6, NIN))
+    _, g2 = mlp.loss_and_grad(p2, x2, t2, norm, bf16=False)
+    m2 = mlp.grad_magnitudes(p2, x2, t2, norm, bf16=False)
+    assert np.all(np.abs(g2) <= m2 * (1 + 1e-12))
