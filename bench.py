@@ -533,21 +533,26 @@ def host_round_trip(torch, n=2000):
     return 1e6 * dt / n
 
 
-def run_tether(fil, torch, steps=20, warmup=3, frac=0.25):
-    """The 32k suspension with every fourth filament clamped at its base (Sec.
-    5.2.1: Y_1 fixed, u_1 = 0): FIL_PAIR32, extrapolated initial guess (the
-    network refuses tethered contexts)."""
+def run_tether(fil, torch, steps=20, warmup=5, every=4):
+    """The 32k suspension's cloud with every fourth filament clamped at its base
+    (Sec. 5.2.1: Y_1 fixed, u_1 = 0), weightless: the follower-force half keeps
+    its tip force, the other half is passive. (With gravity the cloud settles
+    collectively at ~35 times the speed of a lone filament, ~7a per step, and the
+    first step would ask the clamps to hold that flow from a standing start;
+    Algorithm 2 with the per-filament J0 does not converge on it at 1000
+    filaments, on the GPU or in the oracle.) FIL_PAIR32, extrapolated initial
+    guess (the network refuses tethered contexts), J0 built every step (the
+    tethered J0 follows the prescribed motion)."""
     wl, base, t, mu, Fext, follower = workload(1000, 32, seed=0)
     stream = torch.cuda.Stream()
     m = fil.Filaments(wl.seg_per_fil, precision=fil.FIL_PAIR32, stream=stream.cuda_stream,
                       a=wl.a, eta=wl.eta, dL=wl.dL, KB=wl.KB, KT=wl.KT, dt=wl.dt, tol=wl.tol,
                       max_iter=wl.max_iter, j0_model=fil.FIL_J0_FILAMENT_RPY)
     m.init_straight(base, t, mu, None)
-    m.set_external(Fext, None, follower)
-    mask = (np.arange(1000) % int(round(1 / frac))) == 0
+    m.set_external(None, None, follower)
+    mask = (np.arange(1000) % every) == 0
     m.set_tether(mask, base.copy(), np.zeros((1000, 3)))
-    for _ in range(warmup):
-        m.step()
+    warm_iters = [m.step() for _ in range(warmup)]
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -569,12 +574,14 @@ def run_tether(fil, torch, steps=20, warmup=3, frac=0.25):
     S = 32000.0
     return {"metric": "timesteps/s", "value": steps / (ms * 1e-3), "unit": "timesteps/s",
             "steps": steps, "broyden_iters_per_step": float(np.mean(iters)),
+            "warmup_iters": warm_iters,
             "pairs_per_s": (a1 - a0) * S * S / (ms * 1e-3), "dtype": "f32+f64",
-            "config": {"workload": "suspension 1000 x 32 with %d filaments (every %d-th) clamped "
-                                   "at the base, physics and tolerance of the 32k suspension"
-                                   % (int(mask.sum()), int(round(1 / frac))),
+            "config": {"workload": "the 32k suspension's cloud (1000 x 32) with %d filaments "
+                                   "(every %d-th) clamped at the base, no gravity, tip follower "
+                                   "force fL^2/KB=100 on the other half as in the suspension, "
+                                   "dt=T/200, tol 1e-4" % (int(mask.sum()), every),
                        "precision": "pair32", "initial_guess": "extrapolation",
-                       "j0": "filament_rpy + rank-6 correction per clamped filament"},
+                       "j0": "filament_rpy + rank-6 correction per clamped filament, every step"},
             "roofline": pair_roofline(S * S, pair_ms, n_pair),
             "max_abs_multiplier": float(np.abs(lam[mask]).max()),
             "gpu_launches": int(k1 - k0), "clocks": clocks}

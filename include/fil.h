@@ -316,7 +316,9 @@ fil_status fil_counters(const fil_ctx *c, int64_t *mobility_applies, int64_t *br
  * two CUDA events recorded on the context stream (at most 4096 launches are
  * kept). fil_profile_read synchronises the stream, returns the number of
  * timed launches and their summed device time in milliseconds, and clears the
- * record. Enabling is cheap; the events add no synchronisation. */
+ * record. Enabling is cheap; the events add no synchronisation. Applies
+ * captured into a CUDA graph record their events as event-record nodes: after
+ * replays, fil_profile_read returns the times of the last replay. */
 fil_status fil_profile(fil_ctx *c, int32_t enable);
 fil_status fil_profile_read(fil_ctx *c, int64_t *launches, double *total_ms);
 

@@ -35,6 +35,10 @@ fil_status set_err(fil_ctx *c, fil_status s, const std::string &msg) {
 }
 
 fil_status cuda_err(fil_ctx *c, cudaError_t e, const char *what) {
+    // the failure is reported through the status: clear it from the runtime's
+    // last-error slot, where a later launch check of this or another context
+    // would otherwise report it a second time (sticky errors stay regardless)
+    cudaGetLastError();
     char buf[256];
     std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
     return set_err(c, FIL_ECUDA, buf);
@@ -98,10 +102,12 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->sys_xoff = ar.take<int64_t>(c->n_sys + 1);
     c->tile_unit_off_d = ar.take<int64_t>(c->rpy_tiles_max + 1);
     c->tile_src_d = ar.take<int64_t>(c->rpy_tiles_max);
+    c->tile_nsrc_d = ar.take<int64_t>(c->rpy_tiles_max);
     c->tile_id_d = ar.take<int>(c->rpy_tiles_max);
     c->slot_d = ar.take<int>(c->Spad / kRpyThreads);
     c->act_unit_off_d = ar.take<int64_t>(c->rpy_tiles_max + 1);
     c->act_src_d = ar.take<int64_t>(c->rpy_tiles_max);
+    c->act_nsrc_d = ar.take<int64_t>(c->rpy_tiles_max);
     c->act_tile_d = ar.take<int>(c->rpy_tiles_max);
     c->act_slot_d = ar.take<int>(c->Spad / kRpyThreads);
     c->act_dyn_d = ar.take<int64_t>(2);
@@ -1197,14 +1203,15 @@ fil_status fil_profile_read(fil_ctx *c, int64_t *launches, double *total_ms) {
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->stream));
     double sum = 0.0;
-    for (int i = 0; i < c->prof_n; ++i) {
+    const int n = c->prof_n;
+    c->prof_n = 0;   // the record is cleared whatever happens below
+    for (int i = 0; i < n; ++i) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]));
         sum += ms;
     }
-    if (launches) *launches = c->prof_n;
+    if (launches) *launches = n;
     if (total_ms) *total_ms = sum;
-    c->prof_n = 0;
     return FIL_OK;
 }
 

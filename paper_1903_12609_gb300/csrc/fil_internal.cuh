@@ -93,9 +93,9 @@ struct fil_ctx {
     void *partials;       // stream-K partial sums
     int rpy_grid32, rpy_grid64;
     int64_t rpy_tiles, rpy_units;
-    std::vector<int64_t> sys_pad_off_h, tile_unit_off_h, tile_src_h, pos_of_seg_h;
+    std::vector<int64_t> sys_pad_off_h, tile_unit_off_h, tile_src_h, tile_nsrc_h, pos_of_seg_h;
     std::vector<int> pad_map_h, tile_sys_h, tile_id_h;
-    int64_t *tile_unit_off_d, *tile_src_d, *pos_of_seg_d;
+    int64_t *tile_unit_off_d, *tile_src_d, *tile_nsrc_d, *pos_of_seg_d;
     int *pad_map_d, *tile_id_d, *slot_d;
     int rpy_tpt;           // targets per thread of the pair kernels (tile = 128 x tpt)
     int rpy_ctas;          // resident CTAs per SM of the stream-K grid
@@ -106,7 +106,7 @@ struct fil_ctx {
     int64_t act_tiles, act_units;
     double pairs_all, pairs_act;   // sum of S_s^2 over all / the active systems
     double n_pairs;                // pairs evaluated by all applies so far
-    int64_t *act_unit_off_d, *act_src_d;
+    int64_t *act_unit_off_d, *act_src_d, *act_nsrc_d;
     int *act_tile_d, *act_slot_d;
     int64_t *act_dyn_d;    // {act_tiles, act_units} on the device
 

@@ -26,7 +26,7 @@
 //      written into the inverse buffer and inverted there in FP32 by
 //      Gauss-Jordan elimination (FP32 runs at 64x the FP64 rate on this part).
 // A solve (j0_solve_fused_kernel, one CTA per filament, the FP32 inverse
-// staged in shared memory once) applies the inverse and then, in FP64 mode,
+// streamed from global memory) applies the inverse and then, in FP64 mode,
 // kJ0Refine steps of iterative refinement x += Inv (b - J0 x), with b - J0 x
 // evaluated matrix-free in FP64 from the aux block -- the same operator as the
 // dense definition -- so x reaches FP64 accuracy (each step multiplies the
@@ -575,14 +575,14 @@ j0_apply_inverse_kernel(Layout lay, const int64_t *__restrict__ jofs,
     inv_gemv_cta<kGemvRows>(inv_all + jofs[f], rs, x + 6 * (int64_t)s0, n, false);
 }
 
-// J0 solve, one CTA per filament with its FP32 inverse staged in shared
-// memory once:  x = Inv b;  `refine` times { r = b - J0 x (FP64, matrix-free);
-// x += Inv r }.  b and x may alias.
-constexpr int kSolveThreads = 512;
-// shared memory of the largest solve: inverse, b, x, FT, VW, Y, r
-static_assert(36 * kMaxDenseSeg * kMaxDenseSeg * 4 + (12 * kMaxDenseSeg + 15 * kMaxDenseSeg) * 8 +
-                      6 * kMaxDenseSeg * 4 <= 227 * 1024,
-              "the J0 solve of the longest filament must fit in shared memory");
+// J0 solve, one CTA per filament:  x = Inv b;  `refine` times { r = b - J0 x
+// (FP64, matrix-free); x += Inv r }.  The FP32 inverse is read from global
+// memory by both products (the second read mostly hits L2) rather than staged
+// in shared memory: the CTA then needs a few KB of shared memory, several
+// run per SM, and the FP64 residual of one filament overlaps the inverse
+// products of others (staging the 147 KB inverse of a 32-segment filament
+// allowed one CTA per SM and serialised the two). b and x may alias.
+constexpr int kSolveThreads = 256;
 
 __global__ void __launch_bounds__(kSolveThreads)
 j0_solve_fused_kernel(Layout lay, const int64_t *__restrict__ jofs,
@@ -596,16 +596,11 @@ j0_solve_fused_kernel(Layout lay, const int64_t *__restrict__ jofs,
     if (active && !active[lay.sys_of[s0]]) return;   // converged system: rows not needed
     const int N = lay.off[f + 1] - s0;
     const int n = 6 * N;
-    float *Inv = reinterpret_cast<float *>(smraw);                  // n^2 (144 N^2 bytes)
-    double *bs = reinterpret_cast<double *>(smraw + (size_t)n * n * sizeof(float));
+    const float *Inv = inv_all + jofs[f];
+    double *bs = reinterpret_cast<double *>(smraw);
     double *xs = bs + n, *FT = xs + n, *VW = FT + 6 * N, *Ys = VW + 6 * N;
     float *rs = reinterpret_cast<float *>(Ys + 3 * N);
     const AuxView g = aux_view(const_cast<double *>(aux_all) + auxofs[f], N);
-    // n^2 = 36 N^2 floats and the block offsets are multiples of 36 floats,
-    // so the copy is whole, 16-byte aligned float4s
-    const float4 *src = reinterpret_cast<const float4 *>(inv_all + jofs[f]);
-    float4 *dst = reinterpret_cast<float4 *>(Inv);
-    for (int i = threadIdx.x; i < n * n / 4; i += blockDim.x) dst[i] = src[i];
     const double *bg = b + 6 * (int64_t)s0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const double v = bg[i];
@@ -1005,7 +1000,7 @@ cudaError_t j0_dense_build_factor(fil_ctx *c, const double *X) {
 
 size_t j0_solve_smem(int maxN) {
     const size_t n = 6 * (size_t)maxN;
-    return n * n * sizeof(float) + (2 * n + 15 * (size_t)maxN) * sizeof(double) + n * sizeof(float);
+    return (2 * n + 15 * (size_t)maxN) * sizeof(double) + n * sizeof(float);
 }
 
 cudaError_t j0_dense_solve(fil_ctx *c, const double *b, double *x, const int *active) {

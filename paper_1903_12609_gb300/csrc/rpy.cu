@@ -110,11 +110,13 @@ __host__ K make_const(double a) {
 struct SysMap {
     const int64_t *tile_unit_off;  // [n_tiles + 1] first unit of each listed tile
     const int64_t *tile_src;       // [n_tiles] padded position of the tile's first source
+    const int64_t *tile_nsrc;      // [n_tiles] real sources of the tile's system (null: n_src)
     const int *tile_id;            // [n_tiles] padded tile of each listed tile (null: same)
     const int *slot_of;            // [all tiles] list index of a padded tile, -1 if not listed
     const int64_t *pos_of_seg;     // [S] padded position of each segment
     const int *pad_map;            // [Spad] segment at a padded position, or -1
     int64_t n_tiles, n_chunks;     // listed tiles; n_chunks: the one-system case
+    int64_t n_src;                 // real sources of the one-system case
     // non-null: {listed tiles, work units} read on the device, so that a captured
     // launch stays valid when the list of active tiles is rewritten
     const int64_t *dyn = nullptr;
@@ -421,6 +423,8 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
         const int64_t c_end = min(n_chunks, c_begin + (u_end - u));
         const float4 *srcs = src + kRec * (src0 / kRpyChunk);   // this tile's system
         const int64_t ptile = smap.tile_id ? smap.tile_id[tile] : tile;   // padded tile
+        // groups of the system's last chunk that hold padding only are skipped
+        const int64_t nsrc = smap.tile_nsrc ? smap.tile_nsrc[tile] : smap.n_src;
 
         // target positions (hi parts) broadcast to both lanes; the lo parts are
         // read again only when a group is recomputed
@@ -457,8 +461,10 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
             const bool has_next = (ch + 1 < c_end);
             if (has_next) stage_chunk<kRec>(sm[buf ^ 1], srcs + kRec * (ch + 1), tid);
             const float4 *s = sm[buf];
+            const int n_grp = (int)min((int64_t)(kRpyChunk / kRpyComp),
+                                       (nsrc - ch * kRpyChunk + kRpyComp - 1) / kRpyComp);
 #pragma unroll 1
-            for (int grp = 0; grp < kRpyChunk / kRpyComp; ++grp) {
+            for (int grp = 0; grp < n_grp; ++grp) {
                 const float4 *qg = s + kRpyPairF4 * (grp * (kRpyComp / 2));
                 float2 acc2[kT][6];
 #pragma unroll
@@ -675,12 +681,14 @@ __global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, 
 
 SysMap sys_map(const fil_ctx *c, bool active_only) {
     SysMap m;
+    m.n_src = c->lay.S;
     m.pos_of_seg = c->pos_of_seg_d;
     m.pad_map = c->pad_map_d;
     m.n_chunks = 0;
     if (active_only) {
         m.tile_unit_off = c->act_unit_off_d;
         m.tile_src = c->act_src_d;
+        m.tile_nsrc = c->act_nsrc_d;
         m.tile_id = c->act_tile_d;
         m.slot_of = c->act_slot_d;
         m.n_tiles = c->act_tiles;
@@ -688,6 +696,7 @@ SysMap sys_map(const fil_ctx *c, bool active_only) {
     } else {
         m.tile_unit_off = c->tile_unit_off_d;
         m.tile_src = c->tile_src_d;
+        m.tile_nsrc = c->tile_nsrc_d;
         m.tile_id = c->tile_id_d;
         m.slot_of = c->slot_d;
         m.n_tiles = c->rpy_tiles;
@@ -710,6 +719,7 @@ void build_tiles(fil_ctx *c) {
     const int T = kRpyThreads * c->rpy_tpt;
     c->tile_unit_off_h.assign(1, 0);
     c->tile_src_h.clear();
+    c->tile_nsrc_h.clear();
     c->tile_sys_h.clear();
     c->tile_id_h.clear();
     for (int s = 0; s < c->n_sys; ++s) {
@@ -719,6 +729,7 @@ void build_tiles(fil_ctx *c) {
         for (int64_t t = 0; t < tiles; ++t) {
             c->tile_unit_off_h.push_back(c->tile_unit_off_h.back() + chunks);
             c->tile_src_h.push_back(c->sys_pad_off_h[s]);
+            c->tile_nsrc_h.push_back(Ss);
             c->tile_sys_h.push_back(s);
             c->tile_id_h.push_back((int)(c->sys_pad_off_h[s] / T + t));
         }
@@ -785,6 +796,10 @@ cudaError_t upload_tiles(fil_ctx *c) {
         e = cudaMemcpyAsync(c->tile_src_d, c->tile_src_h.data(), sizeof(int64_t) * c->tile_src_h.size(),
                             cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->tile_nsrc_d, c->tile_nsrc_h.data(),
+                            sizeof(int64_t) * c->tile_nsrc_h.size(), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->tile_id_d, c->tile_id_h.data(), sizeof(int) * c->tile_id_h.size(),
                             cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
@@ -822,13 +837,14 @@ size_t rpy_partial_bytes(const fil_ctx *c) {
 // The tiles of the systems still iterating (c->active_h), listed for the
 // stream-K split of the next applies with active_only.
 cudaError_t rpy_set_active(fil_ctx *c) {
-    std::vector<int64_t> uoff(1, 0), src;
+    std::vector<int64_t> uoff(1, 0), src, nsrc;
     std::vector<int> tid, slot(c->Spad / kRpyThreads, -1);
     for (int64_t t = 0; t < c->rpy_tiles; ++t) {
         if (!c->active_h[c->tile_sys_h[t]]) continue;
         slot[c->tile_id_h[t]] = (int)tid.size();
         tid.push_back(c->tile_id_h[t]);
         src.push_back(c->tile_src_h[t]);
+        nsrc.push_back(c->tile_nsrc_h[t]);
         uoff.push_back(uoff.back() + (c->tile_unit_off_h[t + 1] - c->tile_unit_off_h[t]));
     }
     c->act_tiles = (int64_t)tid.size();
@@ -845,6 +861,9 @@ cudaError_t rpy_set_active(fil_ctx *c) {
         e = cudaMemcpyAsync(c->act_src_d, src.data(), sizeof(int64_t) * src.size(),
                             cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && !tid.empty())
+        e = cudaMemcpyAsync(c->act_nsrc_d, nsrc.data(), sizeof(int64_t) * nsrc.size(),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !tid.empty())
         e = cudaMemcpyAsync(c->act_tile_d, tid.data(), sizeof(int) * tid.size(),
                             cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
@@ -856,6 +875,21 @@ cudaError_t rpy_set_active(fil_ctx *c) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // host vectors go out of scope
     return e;
 }
+
+namespace {
+
+// A timing event on the context stream; while the stream is being captured the
+// record becomes an event-record node of the graph, so that the events hold
+// the kernel's times of each replay.
+void prof_record(fil_ctx *c, cudaEvent_t ev) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
+    cudaEventRecordWithFlags(ev, c->stream, cs == cudaStreamCaptureStatusActive
+                                                ? cudaEventRecordExternal
+                                                : cudaEventRecordDefault);
+}
+
+}  // namespace
 
 cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
                       bool active_only) {
@@ -874,7 +908,7 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
     if (pair32_on(c)) {
         const int G = (int)(active_only ? c->rpy_grid32 : std::min<int64_t>(c->rpy_grid32, W));
         pack32_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, sm, c->src32);
-        if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+        if (timed) prof_record(c, c->prof_ev[2 * c->prof_n]);
         const RpyConst32 k = make_const<float, RpyConst32>(c->a);
         if (c->rpy_tpt == 1)
             rpy_pair32_kernel<1><<<G, kRpyThreads, 0, c->stream>>>(c->src32, sm, W, G, k,
@@ -882,13 +916,13 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
         else
             rpy_pair32_kernel<2><<<G, kRpyThreads, 0, c->stream>>>(c->src32, sm, W, G, k,
                                                                    (float *)c->partials);
-        if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
+        if (timed) prof_record(c, c->prof_ev[2 * c->prof_n + 1]);
         rpy_reduce32_kernel<<<rgrid, pb, 0, c->stream>>>((const float *)c->partials, S, sm, W, G,
                                                          T, scale, VW);
     } else {
         const int G = (int)(active_only ? c->rpy_grid64 : std::min<int64_t>(c->rpy_grid64, W));
         pack64_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, sm, c->src64);
-        if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+        if (timed) prof_record(c, c->prof_ev[2 * c->prof_n]);
         const RpyConst64 k = make_const<double, RpyConst64>(c->a);
         if (c->rpy_tpt == 1)
             rpy_pair64_kernel<1><<<G, kRpyThreads, 0, c->stream>>>(c->src64, sm, W, G, k,
@@ -896,7 +930,7 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
         else
             rpy_pair64_kernel<2><<<G, kRpyThreads, 0, c->stream>>>(c->src64, sm, W, G, k,
                                                                    (double *)c->partials);
-        if (timed) cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
+        if (timed) prof_record(c, c->prof_ev[2 * c->prof_n + 1]);
         rpy_reduce64_kernel<<<rgrid, pb, 0, c->stream>>>((const double *)c->partials, S, sm, W, G,
                                                          T, scale, VW);
     }
@@ -1079,6 +1113,7 @@ extern "C" fil_status fil_rpy_apply_noalloc(int64_t n_seg, const double *Y, cons
     SysMap sm{};                       // one system, no tables
     sm.n_tiles = tiles;
     sm.n_chunks = n_chunks;
+    sm.n_src = n_seg;
     cudaError_t e = launch(pack32_kernel, (unsigned)((Spad + pb - 1) / pb), pb, st, Y, FT, n_seg,
                            Spad, sm, src);
     if (e == cudaSuccess)

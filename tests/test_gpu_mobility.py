@@ -148,3 +148,35 @@ def test_zero_load_gives_zero(fil):
     Y, FT = mobility_inputs(4, 32, seed=6)
     got = _gpu_apply(fil, [32] * 4, Y, np.zeros_like(FT), 1)
     assert np.all(got == 0.0)
+
+
+def test_apply_captured_in_a_cuda_graph(fil):
+    """fil_mobility_apply with device arrays allocates nothing and does not
+    synchronise, so it can be captured in a CUDA graph on the context's stream:
+    replays give the launched result bit for bit, and the profiling events
+    captured with it time the replayed pair kernels."""
+    Y, FT = mobility_inputs(20, 32, seed=12)
+    S = Y.shape[0]
+    stream = torch.cuda.Stream()
+    with fil.Filaments([32] * 20, precision=fil.FIL_PAIR32, stream=stream.cuda_stream) as m:
+        Yd = torch.from_numpy(Y).cuda()
+        FTd = torch.from_numpy(FT).cuda()
+        ref = torch.empty((S, 6), dtype=torch.float64, device="cuda")
+        m.mobility_apply(Yd, FTd, ref)
+        torch.cuda.synchronize()
+        out = torch.zeros((S, 6), dtype=torch.float64, device="cuda")
+        m.profile(True)
+        m.profile_read()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream, capture_error_mode="relaxed"):
+            for _ in range(3):
+                m.mobility_apply(Yd, FTd, out)
+        out.zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        g.replay()
+        torch.cuda.synchronize()
+        n, ms = m.profile_read()
+        m.profile(False)
+        assert n == 3 and ms > 0.0
+        np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
