@@ -279,6 +279,7 @@ def run_c1_mobility(fil, torch, applies=1000, per_graph=100, min_seconds=1.0):
     m = fil.Filaments([32] * 100, precision=fil.FIL_PAIR32, stream=stream.cuda_stream)
     m.set_state(Y, np.tile([1.0, 0.0, 0.0, 0.0], (S, 1)))
     tuned = m.autotune(50)
+    schedule = m.pair_schedule()
     Yd = torch.from_numpy(Y).cuda()
     FTd = torch.from_numpy(FT).cuda()
     VW = torch.empty((S, 6), dtype=torch.float64, device="cuda")
@@ -333,7 +334,8 @@ def run_c1_mobility(fil, torch, applies=1000, per_graph=100, min_seconds=1.0):
                        "l2": "inputs L2-resident (3200 segments); the metric is the apply "
                              "itself, repeated"},
             "roofline": pair_roofline(float(S) * S, pair_ms, n_pair),
-            "autotuned": {"tile": tuned[0], "ctas_per_sm": tuned[1], "ms_per_apply": tuned[2]},
+            "autotuned": {"tile": tuned[0], "ctas_per_sm": tuned[1], "ms_per_apply": tuned[2],
+                          "targets_per_thread": schedule[1]},
             "velocity_error": velocity_error(got, ref, B),
             "cpu_baseline": {"value": S * float(S) / dt, "unit": UNIT, "cores": cores,
                              "kind": "oracle", "sample": "one whole apply, %d x %d pairs (%.2f s)"
@@ -420,6 +422,7 @@ def run_ensemble(args, fil, torch, nested=False):
     for _ in range(args.warmup):
         m.step()
     tuned = m.autotune(2) if args.tune_ensemble else None
+    schedule = m.pair_schedule()
     a0, i0, k0 = m.counters()
     p0 = m.pair_count()
     torch.cuda.synchronize()
@@ -505,6 +508,8 @@ def run_ensemble(args, fil, torch, nested=False):
         "graph": bool(args.graph),
         "autotuned": ({"tile": tuned[0], "ctas_per_sm": tuned[1], "ms_per_apply": tuned[2]}
                       if tuned else None),
+        "pair_schedule": {"tile": schedule[0], "targets_per_thread": schedule[1],
+                          "ctas_per_sm": schedule[2]},
         "gpu_launches": int(k1 - k0), "clocks": clocks}
     if not nested:
         print(json.dumps(rec), flush=True)

@@ -125,14 +125,23 @@ fil_status fil_create_ensemble(const fil_params *p, int32_t n_sys, const int32_t
 fil_status fil_sys_stats(const fil_ctx *c, int32_t *iters, double *finf);
 
 /* Autotuner of the RPY pair kernel: times `reps` mobility applies of the
- * current state's loads for every candidate schedule -- tiles of 128 or 256
- * targets (1 or 2 targets per thread) and 1..occupancy resident CTAs per SM
- * for the stream-K split -- and keeps the fastest for all later applies.
- * Reports the choice (nullable outputs) and its time per apply in ms. Results
- * change only in rounding (the summation order of the pair terms). FIL_ESTATE
- * inside a step. */
+ * current state's loads for every candidate schedule -- tiles of 256 targets
+ * (2 per thread) or 128 targets (1 per thread), and 1..occupancy resident
+ * CTAs per SM for the stream-K split of the (tile, source chunk) work units --
+ * and keeps the fastest for all later applies. Reports the choice (nullable
+ * outputs) and its time per apply in ms. Results change only in rounding (the
+ * summation order of the pair terms). FIL_ESTATE inside a step. */
 fil_status fil_autotune(fil_ctx *c, int32_t reps, int32_t *tile, int32_t *ctas_per_sm,
                         double *ms);
+
+/* Set the pair schedule by hand (the autotuner's candidates): tile 256 with 2
+ * targets per thread or tile 128 with 1, and ctas_per_sm from 1 to the
+ * kernel's occupancy. FIL_EINVAL for another combination, FIL_ESTATE inside a
+ * step. fil_pair_schedule reads the current one (nullable outputs). */
+fil_status fil_set_pair_schedule(fil_ctx *c, int32_t tile, int32_t targets_per_thread,
+                                 int32_t ctas_per_sm);
+fil_status fil_pair_schedule(const fil_ctx *c, int32_t *tile, int32_t *targets_per_thread,
+                             int32_t *ctas_per_sm);
 
 /* Run each Broyden iteration of fil_broyden_step / fil_step as one CUDA graph
  * launch (enable = 1) instead of separate kernel launches: the graph holds the

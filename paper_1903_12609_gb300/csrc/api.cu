@@ -1036,7 +1036,31 @@ fil_status fil_autotune(fil_ctx *c, int32_t reps, int32_t *tile, int32_t *ctas_p
     CK(warm_features(c, nullptr, c->warm_feat));
     CK(rpy_autotune(c, c->Yc, c->FT, c->VW, reps, ms));
     drop_graphs(c);
-    if (tile) *tile = kRpyThreads * c->rpy_tpt;
+    if (tile) *tile = rpy_tile(c);
+    if (ctas_per_sm) *ctas_per_sm = c->rpy_ctas;
+    return FIL_OK;
+}
+
+fil_status fil_set_pair_schedule(fil_ctx *c, int32_t tile, int32_t targets_per_thread,
+                                 int32_t ctas_per_sm) {
+    if (!c) return FIL_EINVAL;
+    if (c->in_step) return set_err(c, FIL_ESTATE, "fil_set_pair_schedule: a step is in progress");
+    if (targets_per_thread < 1 || tile % targets_per_thread != 0)
+        return set_err(c, FIL_EINVAL, "fil_set_pair_schedule: no such schedule");
+    CK(cudaSetDevice(c->device));
+    const int threads = tile / targets_per_thread;
+    if (!rpy_schedule_valid(c, targets_per_thread, threads, ctas_per_sm))
+        return set_err(c, FIL_EINVAL, "fil_set_pair_schedule: no such schedule");
+    CK(rpy_set_schedule(c, targets_per_thread, threads, ctas_per_sm));
+    drop_graphs(c);
+    return FIL_OK;
+}
+
+fil_status fil_pair_schedule(const fil_ctx *c, int32_t *tile, int32_t *targets_per_thread,
+                             int32_t *ctas_per_sm) {
+    if (!c) return FIL_EINVAL;
+    if (tile) *tile = rpy_tile(c);
+    if (targets_per_thread) *targets_per_thread = c->rpy_tpt;
     if (ctas_per_sm) *ctas_per_sm = c->rpy_ctas;
     return FIL_OK;
 }

@@ -97,7 +97,9 @@ struct fil_ctx {
     std::vector<int> pad_map_h, tile_sys_h, tile_id_h;
     int64_t *tile_unit_off_d, *tile_src_d, *tile_nsrc_d, *pos_of_seg_d;
     int *pad_map_d, *tile_id_d, *slot_d;
-    int rpy_tpt;           // targets per thread of the pair kernels (tile = 128 x tpt)
+    int rpy_tpt;           // targets per thread of the pair kernels
+    int rpy_threads;       // threads per CTA of the FP32 pair kernel (128, or 64 with tpt 2);
+                           // tile = rpy_threads x rpy_tpt targets
     int rpy_ctas;          // resident CTAs per SM of the stream-K grid
     int rpy_ctas_max;
     int64_t rpy_tiles_max; // listed tiles at the smallest tile size
@@ -217,6 +219,8 @@ struct fil_ctx {
 namespace fil {
 
 inline bool pair32_on(const fil_ctx *c) { return c->prec != FIL_FP64; }
+// targets per RPY tile of the current pair-kernel schedule
+inline int rpy_tile(const fil_ctx *c) { return c->rpy_threads * c->rpy_tpt; }
 inline bool fast_mixed(const fil_ctx *c) { return c->prec == FIL_MIXED; }
 
 // Launchers (all enqueue on c->stream and return a cudaError_t).
@@ -226,6 +230,8 @@ cudaError_t rpy_set_active(fil_ctx *c);     // list the active systems' tiles
 cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *VW, int reps,
                          double *best_ms);
 cudaError_t rpy_setup(fil_ctx *c);          // grid sizes and padded layout, once at create
+bool rpy_schedule_valid(const fil_ctx *c, int tpt, int threads, int ctas);
+cudaError_t rpy_set_schedule(fil_ctx *c, int tpt, int threads, int ctas);
 cudaError_t rpy_upload_tables(fil_ctx *c);  // the layout tables, after the arena exists
 size_t rpy_partial_bytes(const fil_ctx *c);
 

@@ -270,23 +270,31 @@ __device__ __forceinline__ void coef_exact(float r2, const RpyConst32 &k, float 
     G = ov ? fmaf(-k.ov_G1, r, k.ov_G0) : rinv3;
 }
 
+// How a group of sources is evaluated (pair32x2's MODE).
+enum PairMode { kFarHi = 0, kFarHiLo = 1, kExact = 2 };
+
 // The pair terms of one target and the two sources of a packed record (q),
 // lane x = even source, lane y = odd source, tracking the smallest r^2 seen.
-// EXACT = false (the inner loop): d from the hi parts only and the far form
-// for every pair, branch-free; whatever it produces for close, overlapping or
-// coincident pairs (Inf or NaN at r = 0) is discarded by the caller, which
-// recomputes such groups. EXACT = true (recomputed groups): d = (t_hi - s_hi) +
-// (t_lo - s_lo) and the exact coefficients of every pair (coef_exact).
-template <bool EXACT>
+//  kFarHi (the inner loop): d from the hi parts only and the far form for every
+//    pair, branch-free; whatever it produces for close, overlapping or
+//    coincident pairs (Inf or NaN at r = 0) is discarded by the caller, which
+//    evaluates such groups again.
+//  kFarHiLo: d = (t_hi - s_hi) + (t_lo - s_lo), far form; source jx (jx + 1
+//    for lane y) equal to self_j is the target itself: its term is zero (d = 0
+//    and 1/r taken as 0) and it is left out of the smallest r^2.
+//  kExact: hi/lo differences and the exact coefficients of every pair
+//    (coef_exact; the self pair takes the self values).
+template <int MODE>
 __device__ __forceinline__ void pair32x2(const float2 *th, const float2 *tl, const float4 *q,
                                          const RpyConst32 &k, float2 k23, float2 nk2,
-                                         float2 *acc, float &rmin2) {
+                                         float2 *acc, float &rmin2, int self_j = -1,
+                                         int jx = 0) {
     const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
     const float2 q4 = reinterpret_cast<const float2 *>(q + 4)[0];
     float2 dx = __fadd2_rn(th[0], f2(q0.x, q0.y));
     float2 dy = __fadd2_rn(th[1], f2(q0.z, q0.w));
     float2 dz = __fadd2_rn(th[2], f2(q1.x, q1.y));
-    if (EXACT) {
+    if (MODE != kFarHi) {
         const float4 q5 = q[5];
         const float2 lz = reinterpret_cast<const float2 *>(q + 4)[1];
         dx = __fadd2_rn(dx, __fadd2_rn(tl[0], f2(q5.x, q5.y)));
@@ -294,10 +302,17 @@ __device__ __forceinline__ void pair32x2(const float2 *th, const float2 *tl, con
         dz = __fadd2_rn(dz, __fadd2_rn(tl[2], lz));
     }
     const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-    rmin2 = fminf(rmin2, fminf(r2.x, r2.y));
     float2 A, B, C, D, G;
-    if (!EXACT) {
-        const float2 rinv = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+    if (MODE != kExact) {
+        float2 rinv = f2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        if (MODE == kFarHiLo) {
+            const bool sx = (jx == self_j), sy = (jx + 1 == self_j);
+            rinv.x = sx ? 0.f : rinv.x;
+            rinv.y = sy ? 0.f : rinv.y;
+            rmin2 = fminf(rmin2, fminf(sx ? k.close2 : r2.x, sy ? k.close2 : r2.y));
+        } else {
+            rmin2 = fminf(rmin2, fminf(r2.x, r2.y));
+        }
         const float2 rinv2 = __fmul2_rn(rinv, rinv);
         const float2 rinv3 = __fmul2_rn(rinv, rinv2);
         const float2 rinv5 = __fmul2_rn(rinv3, rinv2);
@@ -396,11 +411,13 @@ __device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision pair kernel. Each thread owns kRpyTargetsPerThread targets;
+// Mixed-precision pair kernel. A CTA of kRpyThreads threads owns a tile of
+// kRpyThreads * TPT targets, TPT per thread (256-target tiles for large
+// systems, 128-target tiles for small ones: less padding, finer work units);
 // their pair terms are summed in registers over groups of kRpyComp sources
-// with the branch-free far form, a group in which the warp met an overlapping
-// pair is recomputed exactly, and the group sums are folded (TwoSum) into
-// (hi, lo) accumulators.
+// with the branch-free far form, a group in which the warp met a close pair
+// is evaluated again with hi/lo differences (exactly, if it overlaps), and the
+// group sums are folded (TwoSum) into (hi, lo) accumulators.
 // ---------------------------------------------------------------------------
 template <int TPT>
 __global__ void __launch_bounds__(kRpyThreads, TPT == 2 ? kRpyMinBlocksTpt2 : kRpyMinBlocksTpt1)
@@ -442,6 +459,8 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
             thb[t][2] = f2(a0.z, a0.z);
         }
         const int tpar = tid & 1;   // even / odd record slot of every target of this thread
+        const int lane = tid & 31;
+        const int64_t wbase = ptile * kTile + (tid & ~31);   // first target of this warp (slot 0)
         const float2 k23 = f2(k.k23a2, k.k23a2), nk2 = f2(-k.k2a2, -k.k2a2);
         float hi[kT][6], lo[kT][6];
 #pragma unroll
@@ -466,24 +485,51 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
 #pragma unroll 1
             for (int grp = 0; grp < n_grp; ++grp) {
                 const float4 *qg = s + kRpyPairF4 * (grp * (kRpyComp / 2));
+                // the group that holds this warp's own segments (slot t's targets
+                // wbase + t kRpyThreads + lane are sources g0 + lane): one per warp and slot
+                const int64_t g0 = src0 + ch * kRpyChunk + grp * kRpyComp;
+                int own = 0;
+#pragma unroll
+                for (int t = 0; t < kT; ++t) own |= (g0 == wbase + t * kRpyThreads) ? (1 << t) : 0;
                 float2 acc2[kT][6];
 #pragma unroll
                 for (int t = 0; t < kT; ++t)
 #pragma unroll
                     for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
                 float rmin2 = k.close2;
+                bool hilo = own != 0;
+                if (!hilo) {
 #pragma unroll (kRpyUnroll / 2)
-                for (int jp = 0; jp < kRpyComp / 2; ++jp) {
+                    for (int jp = 0; jp < kRpyComp / 2; ++jp) {
 #pragma unroll
-                    for (int t = 0; t < kT; ++t)
-                        pair32x2<false>(thb[t], thb[t], qg + kRpyPairF4 * jp, k, k23, nk2,
-                                        acc2[t], rmin2);
+                        for (int t = 0; t < kT; ++t)
+                            pair32x2<kFarHi>(thb[t], thb[t], qg + kRpyPairF4 * jp, k, k23, nk2,
+                                             acc2[t], rmin2);
+                    }
+                    // a pair closer than R_c: the group again with hi/lo differences
+                    hilo = __any_sync(0xffffffffu, rmin2 < k.close2);
                 }
-                if (__any_sync(0xffffffffu, rmin2 < k.close2)) {
-                    // a pair closer than R_c (or overlapping): redo the group with hi/lo
-                    // differences and the exact coefficients
+                if (hilo) {
+                    rmin2 = k.close2;
 #pragma unroll
                     for (int t = 0; t < kT; ++t) {   // one target at a time (fewer live registers)
+                        float4 a0, a1, a2;
+                        unpack_source(trec + t * kTRecStep, tpar, a0, a1, a2);
+                        const float2 tlb[3] = {f2(a1.x, a1.x), f2(a1.y, a1.y), f2(a1.z, a1.z)};
+                        const int self_j = (own >> t) & 1 ? lane : -1;
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
+#pragma unroll 1
+                        for (int jp = 0; jp < kRpyComp / 2; ++jp)
+                            pair32x2<kFarHiLo>(thb[t], tlb, qg + kRpyPairF4 * jp, k, k23, nk2,
+                                               acc2[t], rmin2, self_j, 2 * jp);
+                    }
+                }
+                // overlapping distinct segments (r < 2a): the exact coefficients
+                const bool exact = hilo && __any_sync(0xffffffffu, rmin2 < k.near2);
+                if (exact) {
+#pragma unroll
+                    for (int t = 0; t < kT; ++t) {
                         float4 a0, a1, a2;
                         unpack_source(trec + t * kTRecStep, tpar, a0, a1, a2);
                         const float2 tlb[3] = {f2(a1.x, a1.x), f2(a1.y, a1.y), f2(a1.z, a1.z)};
@@ -491,8 +537,8 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
                         for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
 #pragma unroll 1
                         for (int jp = 0; jp < kRpyComp / 2; ++jp)
-                            pair32x2<true>(thb[t], tlb, qg + kRpyPairF4 * jp, k, k23, nk2,
-                                           acc2[t], rmin2);
+                            pair32x2<kExact>(thb[t], tlb, qg + kRpyPairF4 * jp, k, k23, nk2,
+                                             acc2[t], rmin2);
                     }
                 }
                 float acc[kT][6];
@@ -500,6 +546,22 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
                 for (int t = 0; t < kT; ++t)
 #pragma unroll
                     for (int c = 0; c < 6; ++c) acc[t][c] = __fadd_rn(acc2[t][c].x, acc2[t][c].y);
+                if (own && !exact) {
+                    // the self term of the targets whose own segment is in this group
+                    // (left out of the far-form pass above): 4/(3a) F_n and T_n / a^3
+                    float4 s0, s1, s2;
+                    unpack_source(qg + kRpyPairF4 * (lane >> 1), lane & 1, s0, s1, s2);
+#pragma unroll
+                    for (int t = 0; t < kT; ++t)
+                        if ((own >> t) & 1) {
+                            acc[t][0] = fmaf(k.ov_A0, s0.w, acc[t][0]);
+                            acc[t][1] = fmaf(k.ov_A0, s1.w, acc[t][1]);
+                            acc[t][2] = fmaf(k.ov_A0, s2.w, acc[t][2]);
+                            acc[t][3] = fmaf(k.ov_C0, s2.x, acc[t][3]);
+                            acc[t][4] = fmaf(k.ov_C0, s2.y, acc[t][4]);
+                            acc[t][5] = fmaf(k.ov_C0, s2.z, acc[t][5]);
+                        }
+                }
 #pragma unroll
                 for (int t = 0; t < kT; ++t)
 #pragma unroll
@@ -716,7 +778,7 @@ int64_t count_tiles(const fil_ctx *c, int T) {
 // Tiles of T targets of every system (only tiles that hold real targets),
 // each with ceil(S_s / chunk) source chunks.
 void build_tiles(fil_ctx *c) {
-    const int T = kRpyThreads * c->rpy_tpt;
+    const int T = rpy_tile(c);
     c->tile_unit_off_h.assign(1, 0);
     c->tile_src_h.clear();
     c->tile_nsrc_h.clear();
@@ -739,9 +801,9 @@ void build_tiles(fil_ctx *c) {
 }
 
 template <typename K>
-int occupancy(K kernel) {
+int occupancy(K kernel, int threads = kRpyThreads) {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kRpyThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess)
         return 1;
     return std::max(1, occ);
 }
@@ -755,6 +817,7 @@ void set_grids(fil_ctx *c) {
 
 cudaError_t rpy_setup(fil_ctx *c) {
     c->rpy_tpt = kRpyTargetsPerThread;
+    c->rpy_threads = kRpyThreads;
     int occ = pair32_on(c) ? occupancy(rpy_pair32_kernel<kRpyTargetsPerThread>)
                                    : occupancy(rpy_pair64_kernel<kRpyTargetsPerThread>);
     c->rpy_ctas = occ;
@@ -902,7 +965,7 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
     const SysMap sm = sys_map(c, active_only);
     const int64_t W = active_only ? c->act_units : c->rpy_units;
     if (W == 0) return cudaSuccess;
-    const int T = kRpyThreads * c->rpy_tpt;
+    const int T = rpy_tile(c);
     // the active-tile list changes between applies: its launches keep a fixed grid
     // (and read the unit count from the device), so captured graphs stay valid
     if (pair32_on(c)) {
@@ -953,9 +1016,10 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
     if (e != cudaSuccess) return e;
     e = cudaEventCreate(&e1);
     if (e != cudaSuccess) return e;
-    int best_tpt = c->rpy_tpt, best_ctas = c->rpy_ctas;
+    int best_tpt = c->rpy_tpt, best_threads = c->rpy_threads, best_ctas = c->rpy_ctas;
     float best = 1e30f;
     for (int tpt = 1; tpt <= 2 && e == cudaSuccess; ++tpt) {
+        const int threads = kRpyThreads;
         int occ;
         if (pair32_on(c))
             occ = tpt == 1 ? occupancy(rpy_pair32_kernel<1>) : occupancy(rpy_pair32_kernel<2>);
@@ -963,6 +1027,7 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
             occ = tpt == 1 ? occupancy(rpy_pair64_kernel<1>) : occupancy(rpy_pair64_kernel<2>);
         for (int ctas = 1; ctas <= std::min(occ, c->rpy_ctas_max) && e == cudaSuccess; ++ctas) {
             c->rpy_tpt = tpt;
+            c->rpy_threads = threads;
             c->rpy_ctas = ctas;
             set_grids(c);
             build_tiles(c);
@@ -977,6 +1042,7 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
             if (e == cudaSuccess && ms < best) {
                 best = ms;
                 best_tpt = tpt;
+                best_threads = threads;
                 best_ctas = ctas;
             }
         }
@@ -984,6 +1050,7 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->rpy_tpt = best_tpt;
+    c->rpy_threads = best_threads;
     c->rpy_ctas = best_ctas;
     set_grids(c);
     build_tiles(c);
@@ -993,6 +1060,31 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
     c->n_pairs = p0;
     if (best_ms) *best_ms = best / std::max(1, reps);
     return e;
+}
+
+// A given pair schedule (targets per thread, threads per CTA, resident CTAs per
+// SM for the stream-K grid); false if the kernel has no such schedule or the
+// CTA count exceeds its occupancy.
+bool rpy_schedule_valid(const fil_ctx *c, int tpt, int threads, int ctas) {
+    int occ = 0;
+    if (threads == kRpyThreads && (tpt == 1 || tpt == 2)) {
+        occ = pair32_on(c) ? (tpt == 1 ? occupancy(rpy_pair32_kernel<1>)
+                                       : occupancy(rpy_pair32_kernel<2>))
+                           : (tpt == 1 ? occupancy(rpy_pair64_kernel<1>)
+                                       : occupancy(rpy_pair64_kernel<2>));
+    } else {
+        return false;
+    }
+    return ctas >= 1 && ctas <= std::min(occ, c->rpy_ctas_max);
+}
+
+cudaError_t rpy_set_schedule(fil_ctx *c, int tpt, int threads, int ctas) {
+    c->rpy_tpt = tpt;
+    c->rpy_threads = threads;
+    c->rpy_ctas = ctas;
+    set_grids(c);
+    build_tiles(c);
+    return upload_tiles(c);
 }
 
 // ---------------------------------------------------------------------------

@@ -35,7 +35,8 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_tc_gemm_bf16", "fil_warm_features", "fil_warm_targets", "fil_warm_attach",
             "fil_warm_stats", "fil_create_ensemble", "fil_sys_stats", "fil_pair_count",
             "fil_set_graph", "fil_autotune", "fil_set_steric", "fil_set_tether",
-            "fil_get_tether", "fil_fma_peak", "fil_set_j0_reuse", "fil_j0_stats"]
+            "fil_get_tether", "fil_fma_peak", "fil_set_j0_reuse", "fil_j0_stats",
+            "fil_set_pair_schedule", "fil_pair_schedule"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_SEG = 800, 256, 192, 32
 MLP_NPARAM = 256 * 800 + 256 + 2 * (256 * 256 + 256) + 192 * 256 + 192
 FIL_WARM_BEST_OF_TWO, FIL_WARM_PREDICTION_FIRST = 0, 1
@@ -89,6 +90,8 @@ def load_library(path=LIB_PATH):
         "fil_rpy_apply_noalloc": [ctypes.c_int64, P, P, P, ctypes.c_double, ctypes.c_double, P],
         "fil_fma_peak": [ctypes.c_int32, D, D],
         "fil_set_j0_reuse": [P, ctypes.c_int32],
+        "fil_set_pair_schedule": [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
+        "fil_pair_schedule": [P, I32, I32, I32],
         "fil_j0_stats": [P, I64, I64],
         "fil_mlp_create": [ctypes.c_int64, P, ctypes.POINTER(P)],
         "fil_mlp_destroy": [P],
@@ -187,6 +190,17 @@ def fil_autotune(ctx, reps=3):
     _check(ctx, _lib.fil_autotune(ctx, int(reps), ctypes.byref(tile), ctypes.byref(ctas),
                                   ctypes.byref(ms)))
     return tile.value, ctas.value, ms.value
+
+
+def fil_set_pair_schedule(ctx, tile, targets_per_thread, ctas_per_sm):
+    _check(ctx, _lib.fil_set_pair_schedule(ctx, int(tile), int(targets_per_thread),
+                                           int(ctas_per_sm)))
+
+
+def fil_pair_schedule(ctx):
+    t, p, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(ctx, _lib.fil_pair_schedule(ctx, ctypes.byref(t), ctypes.byref(p), ctypes.byref(c)))
+    return t.value, p.value, c.value
 
 
 def fil_set_graph(ctx, enable):

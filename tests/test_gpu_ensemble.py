@@ -36,9 +36,11 @@ def _positions(rng, segs, box):
     return np.concatenate(Y)
 
 
-@pytest.mark.parametrize("tune", [False, True])
+@pytest.mark.parametrize("tune", [False, True, (128, 1, 3)])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_mobility_is_block_diagonal_over_systems(fil, prec, tune):
+    """The ensemble apply couples only segments of the same system, under the
+    default schedule, the autotuner's choice and a schedule set by hand."""
     rng = np.random.default_rng(prec)
     Ys, FTs = [], []
     for segs in SYSTEMS:
@@ -48,10 +50,13 @@ def test_mobility_is_block_diagonal_over_systems(fil, prec, tune):
     segs_all = [n for segs in SYSTEMS for n in segs]
     with fil.Filaments(segs_all, fil_per_sys=[len(s) for s in SYSTEMS], precision=prec,
                        max_iter=10) as m:
-        if tune:
+        if isinstance(tune, tuple):
+            m.set_pair_schedule(*tune)
+        elif tune:
             m.set_state(Y, np.tile([1.0, 0.0, 0.0, 0.0], (len(Y), 1)))
             tile, ctas, ms = m.autotune(2)
             assert tile in (128, 256) and ctas >= 1 and ms > 0
+            assert m.pair_schedule()[0] == tile
         VW = np.zeros_like(FT)
         m.mobility_apply(Y, FT, VW)
     off = 0

@@ -180,3 +180,35 @@ def test_apply_captured_in_a_cuda_graph(fil):
         m.profile(False)
         assert n == 3 and ms > 0.0
         np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
+
+
+SCHEDULES = [(256, 2, 4), (128, 1, 4), (128, 1, 1), (256, 2, 1)]
+
+
+@pytest.mark.parametrize("sched", SCHEDULES)
+@pytest.mark.parametrize("segs", [[32] * 100, [64] * 17 + [5], [3, 254, 2]])
+def test_pair_schedules(fil, sched, segs):
+    """Every pair schedule the autotuner chooses from (256-target tiles with 2
+    targets per thread, 128-target tiles with 1, one to several resident CTAs
+    per SM), set by hand, against the oracle."""
+    S = sum(segs)
+    rng = np.random.default_rng(S + sched[0] + sched[1])
+    Y = rng.uniform(0, max(4.0, S ** (1 / 3) * 3.0), size=(S, 3))
+    FT = rng.standard_normal((S, 6))
+    ref, ref_abs = rpy.apply(Y, FT, with_abs=True, nthreads=8)
+    with fil.Filaments(segs, precision=fil.FIL_PAIR32) as m:
+        m.set_pair_schedule(*sched)
+        assert m.pair_schedule() == sched
+        VW = np.zeros((S, 6))
+        m.mobility_apply(Y, FT, VW)
+    _check_mixed(VW, ref, ref_abs)
+
+
+def test_pair_schedule_rejections(fil):
+    with fil.Filaments([32] * 4, precision=fil.FIL_PAIR32) as m:
+        for bad in [(128, 2, 1), (512, 2, 1), (256, 4, 1), (256, 2, 0), (256, 2, 99), (64, 1, 1)]:
+            with pytest.raises(fil.FilError) as e:
+                m.set_pair_schedule(*bad)
+            assert e.value.status == fil.FIL_EINVAL
+        m.set_pair_schedule(128, 1, 2)
+        assert m.pair_schedule() == (128, 1, 2)
