@@ -421,7 +421,11 @@ def run_ensemble(args, fil, torch, nested=False):
     m.set_graph(args.graph)
     for _ in range(args.warmup):
         m.step()
-    tuned = m.autotune(2) if args.tune_ensemble else None
+    tuned = None
+    if args.ens_schedule:
+        m.set_pair_schedule(*[int(x) for x in args.ens_schedule.split(",")])
+    elif args.tune_ensemble:
+        tuned = m.autotune(2)
     schedule = m.pair_schedule()
     a0, i0, k0 = m.counters()
     p0 = m.pair_count()
@@ -1048,6 +1052,9 @@ def main():
                          "(its default schedule is the tuned one)")
     ap.add_argument("--tune-ensemble", type=int, default=1,
                     help="autotune the ensemble's pair-kernel schedule after its warm-up steps")
+    ap.add_argument("--ens-schedule", default=None,
+                    help="set the ensemble's pair schedule 'tile,targets_per_thread,ctas_per_sm' "
+                         "instead of autotuning it (e.g. for a profile of the tuned schedule)")
     ap.add_argument("--steric", type=float, default=0.0,
                     help="steric barrier strength F^S (Sec. 2.6, chi = 1.1); 0 = off")
     ap.add_argument("--graph", type=int, default=0,

@@ -412,12 +412,19 @@ __device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
 
 // ---------------------------------------------------------------------------
 // Mixed-precision pair kernel. A CTA of kRpyThreads threads owns a tile of
-// kRpyThreads * TPT targets, TPT per thread (256-target tiles for large
-// systems, 128-target tiles for small ones: less padding, finer work units);
-// their pair terms are summed in registers over groups of kRpyComp sources
-// with the branch-free far form, a group in which the warp met a close pair
-// is evaluated again with hi/lo differences (exactly, if it overlaps), and the
-// group sums are folded (TwoSum) into (hi, lo) accumulators.
+// kRpyThreads * TPT targets, TPT per thread; their pair terms are summed in
+// registers over groups of kRpyComp sources with the branch-free far form and
+// the group sums folded (TwoSum) into (hi, lo) accumulators.
+//  * TPT = 2, 256-target tiles (large systems): a group in which the warp met
+//    a pair closer than R_c is evaluated again with hi/lo differences and the
+//    exact coefficients.
+//  * TPT = 1, 128-target tiles (small systems: less padding, finer units; a
+//    warp's own segments then sit in one of every few dozen groups): the
+//    group holding the warp's own segments is recognised by index and
+//    evaluated once with hi/lo differences and the self pair masked, other
+//    close groups again with hi/lo differences in the far form, and exactly
+//    only when distinct segments overlap.
+// Measured on GB300, each structure is the faster one for its tile size.
 // ---------------------------------------------------------------------------
 template <int TPT>
 __global__ void __launch_bounds__(kRpyThreads, TPT == 2 ? kRpyMinBlocksTpt2 : kRpyMinBlocksTpt1)
@@ -459,8 +466,9 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
             thb[t][2] = f2(a0.z, a0.z);
         }
         const int tpar = tid & 1;   // even / odd record slot of every target of this thread
-        const int lane = tid & 31;
-        const int64_t wbase = ptile * kTile + (tid & ~31);   // first target of this warp (slot 0)
+        [[maybe_unused]] const int lane = tid & 31;
+        // first target of this warp (slot 0), for the own-group test of 128-target tiles
+        [[maybe_unused]] const int64_t wbase = ptile * kTile + (tid & ~31);
         const float2 k23 = f2(k.k23a2, k.k23a2), nk2 = f2(-k.k2a2, -k.k2a2);
         float hi[kT][6], lo[kT][6];
 #pragma unroll
@@ -485,20 +493,94 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
 #pragma unroll 1
             for (int grp = 0; grp < n_grp; ++grp) {
                 const float4 *qg = s + kRpyPairF4 * (grp * (kRpyComp / 2));
-                // the group that holds this warp's own segments (slot t's targets
-                // wbase + t kRpyThreads + lane are sources g0 + lane): one per warp and slot
-                const int64_t g0 = src0 + ch * kRpyChunk + grp * kRpyComp;
-                int own = 0;
+                float acc[kT][6];
+                if constexpr (TPT == 1) {
+                    // the group that holds this warp's own segments (slot t's targets
+                    // wbase + t kRpyThreads + lane are sources g0 + lane): one per warp and slot
+                    const int64_t g0 = src0 + ch * kRpyChunk + grp * kRpyComp;
+                    int own = 0;
 #pragma unroll
-                for (int t = 0; t < kT; ++t) own |= (g0 == wbase + t * kRpyThreads) ? (1 << t) : 0;
-                float2 acc2[kT][6];
+                    for (int t = 0; t < kT; ++t) own |= (g0 == wbase + t * kRpyThreads) ? (1 << t) : 0;
+                    float2 acc2[kT][6];
 #pragma unroll
-                for (int t = 0; t < kT; ++t)
+                    for (int t = 0; t < kT; ++t)
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
-                float rmin2 = k.close2;
-                bool hilo = own != 0;
-                if (!hilo) {
+                        for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
+                    float rmin2 = k.close2;
+                    bool hilo = own != 0;
+                    if (!hilo) {
+#pragma unroll (kRpyUnroll / 2)
+                        for (int jp = 0; jp < kRpyComp / 2; ++jp) {
+#pragma unroll
+                            for (int t = 0; t < kT; ++t)
+                                pair32x2<kFarHi>(thb[t], thb[t], qg + kRpyPairF4 * jp, k, k23, nk2,
+                                                 acc2[t], rmin2);
+                        }
+                        // a pair closer than R_c: the group again with hi/lo differences
+                        hilo = __any_sync(0xffffffffu, rmin2 < k.close2);
+                    }
+                    if (hilo) {
+                        rmin2 = k.close2;
+#pragma unroll
+                        for (int t = 0; t < kT; ++t) {   // one target at a time (fewer live registers)
+                            float4 a0, a1, a2;
+                            unpack_source(trec + t * kTRecStep, tpar, a0, a1, a2);
+                            const float2 tlb[3] = {f2(a1.x, a1.x), f2(a1.y, a1.y), f2(a1.z, a1.z)};
+                            const int self_j = (own >> t) & 1 ? lane : -1;
+#pragma unroll
+                            for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
+#pragma unroll 1
+                            for (int jp = 0; jp < kRpyComp / 2; ++jp)
+                                pair32x2<kFarHiLo>(thb[t], tlb, qg + kRpyPairF4 * jp, k, k23, nk2,
+                                                   acc2[t], rmin2, self_j, 2 * jp);
+                        }
+                    }
+                    // overlapping distinct segments (r < 2a): the exact coefficients
+                    const bool exact = hilo && __any_sync(0xffffffffu, rmin2 < k.near2);
+                    if (exact) {
+#pragma unroll
+                        for (int t = 0; t < kT; ++t) {
+                            float4 a0, a1, a2;
+                            unpack_source(trec + t * kTRecStep, tpar, a0, a1, a2);
+                            const float2 tlb[3] = {f2(a1.x, a1.x), f2(a1.y, a1.y), f2(a1.z, a1.z)};
+#pragma unroll
+                            for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
+#pragma unroll 1
+                            for (int jp = 0; jp < kRpyComp / 2; ++jp)
+                                pair32x2<kExact>(thb[t], tlb, qg + kRpyPairF4 * jp, k, k23, nk2,
+                                                 acc2[t], rmin2);
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < kT; ++t)
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) acc[t][c] = __fadd_rn(acc2[t][c].x, acc2[t][c].y);
+                    if (own && !exact) {
+                        // the self term of the targets whose own segment is in this group
+                        // (left out of the far-form pass above): 4/(3a) F_n and T_n / a^3
+                        float4 s0, s1, s2;
+                        unpack_source(qg + kRpyPairF4 * (lane >> 1), lane & 1, s0, s1, s2);
+#pragma unroll
+                        for (int t = 0; t < kT; ++t)
+                            if ((own >> t) & 1) {
+                                acc[t][0] = fmaf(k.ov_A0, s0.w, acc[t][0]);
+                                acc[t][1] = fmaf(k.ov_A0, s1.w, acc[t][1]);
+                                acc[t][2] = fmaf(k.ov_A0, s2.w, acc[t][2]);
+                                acc[t][3] = fmaf(k.ov_C0, s2.x, acc[t][3]);
+                                acc[t][4] = fmaf(k.ov_C0, s2.y, acc[t][4]);
+                                acc[t][5] = fmaf(k.ov_C0, s2.z, acc[t][5]);
+                            }
+                    }
+                } else {
+                    // 256-target tiles (large systems): a far pass with hi-only
+                    // differences; a group in which a warp met a pair closer than R_c
+                    // (own segments included) is evaluated again exactly
+                    float2 acc2[kT][6];
+#pragma unroll
+                    for (int t = 0; t < kT; ++t)
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
+                    float rmin2 = k.close2;
 #pragma unroll (kRpyUnroll / 2)
                     for (int jp = 0; jp < kRpyComp / 2; ++jp) {
 #pragma unroll
@@ -506,61 +588,25 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
                             pair32x2<kFarHi>(thb[t], thb[t], qg + kRpyPairF4 * jp, k, k23, nk2,
                                              acc2[t], rmin2);
                     }
-                    // a pair closer than R_c: the group again with hi/lo differences
-                    hilo = __any_sync(0xffffffffu, rmin2 < k.close2);
-                }
-                if (hilo) {
-                    rmin2 = k.close2;
+                    if (__any_sync(0xffffffffu, rmin2 < k.close2)) {
 #pragma unroll
-                    for (int t = 0; t < kT; ++t) {   // one target at a time (fewer live registers)
-                        float4 a0, a1, a2;
-                        unpack_source(trec + t * kTRecStep, tpar, a0, a1, a2);
-                        const float2 tlb[3] = {f2(a1.x, a1.x), f2(a1.y, a1.y), f2(a1.z, a1.z)};
-                        const int self_j = (own >> t) & 1 ? lane : -1;
+                        for (int t = 0; t < kT; ++t) {   // one target at a time (fewer live registers)
+                            float4 a0, a1, a2;
+                            unpack_source(trec + t * kTRecStep, tpar, a0, a1, a2);
+                            const float2 tlb[3] = {f2(a1.x, a1.x), f2(a1.y, a1.y), f2(a1.z, a1.z)};
 #pragma unroll
-                        for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
+                            for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
 #pragma unroll 1
-                        for (int jp = 0; jp < kRpyComp / 2; ++jp)
-                            pair32x2<kFarHiLo>(thb[t], tlb, qg + kRpyPairF4 * jp, k, k23, nk2,
-                                               acc2[t], rmin2, self_j, 2 * jp);
+                            for (int jp = 0; jp < kRpyComp / 2; ++jp)
+                                pair32x2<kExact>(thb[t], tlb, qg + kRpyPairF4 * jp, k, k23, nk2,
+                                                 acc2[t], rmin2);
+                        }
                     }
-                }
-                // overlapping distinct segments (r < 2a): the exact coefficients
-                const bool exact = hilo && __any_sync(0xffffffffu, rmin2 < k.near2);
-                if (exact) {
-#pragma unroll
-                    for (int t = 0; t < kT; ++t) {
-                        float4 a0, a1, a2;
-                        unpack_source(trec + t * kTRecStep, tpar, a0, a1, a2);
-                        const float2 tlb[3] = {f2(a1.x, a1.x), f2(a1.y, a1.y), f2(a1.z, a1.z)};
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) acc2[t][c] = f2(0.f, 0.f);
-#pragma unroll 1
-                        for (int jp = 0; jp < kRpyComp / 2; ++jp)
-                            pair32x2<kExact>(thb[t], tlb, qg + kRpyPairF4 * jp, k, k23, nk2,
-                                             acc2[t], rmin2);
-                    }
-                }
-                float acc[kT][6];
-#pragma unroll
-                for (int t = 0; t < kT; ++t)
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) acc[t][c] = __fadd_rn(acc2[t][c].x, acc2[t][c].y);
-                if (own && !exact) {
-                    // the self term of the targets whose own segment is in this group
-                    // (left out of the far-form pass above): 4/(3a) F_n and T_n / a^3
-                    float4 s0, s1, s2;
-                    unpack_source(qg + kRpyPairF4 * (lane >> 1), lane & 1, s0, s1, s2);
 #pragma unroll
                     for (int t = 0; t < kT; ++t)
-                        if ((own >> t) & 1) {
-                            acc[t][0] = fmaf(k.ov_A0, s0.w, acc[t][0]);
-                            acc[t][1] = fmaf(k.ov_A0, s1.w, acc[t][1]);
-                            acc[t][2] = fmaf(k.ov_A0, s2.w, acc[t][2]);
-                            acc[t][3] = fmaf(k.ov_C0, s2.x, acc[t][3]);
-                            acc[t][4] = fmaf(k.ov_C0, s2.y, acc[t][4]);
-                            acc[t][5] = fmaf(k.ov_C0, s2.z, acc[t][5]);
-                        }
+#pragma unroll
+                        for (int c = 0; c < 6; ++c)
+                            acc[t][c] = __fadd_rn(acc2[t][c].x, acc2[t][c].y);
                 }
 #pragma unroll
                 for (int t = 0; t < kT; ++t)
