@@ -419,6 +419,7 @@ def run_ensemble(args, fil, torch, nested=False):
     m.init_straight(base, t, mu, None)
     m.set_external(Fext, None, follower)
     m.set_graph(args.graph)
+    m.set_j0_reuse(args.j0_reuse)
     for _ in range(args.warmup):
         m.step()
     tuned = None
@@ -496,6 +497,7 @@ def run_ensemble(args, fil, torch, nested=False):
                    "j0": "filament_rpy" if j0 == fil.FIL_J0_FILAMENT_RPY else "drag",
                    "precision": args.ens_precision, "precision_note":
                        PRECISION_NOTE[args.ens_precision],
+                   "j0_reuse_max_age": args.j0_reuse,
                    "pairs_per_apply": pairs_per_apply, "parallelism": "single"},
         "pairs_per_s": pairs / (ms * 1e-3),
         "ensemble_timesteps_per_s": steps / (ms * 1e-3),

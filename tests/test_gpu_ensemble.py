@@ -176,3 +176,38 @@ def test_mixed_ensemble_converges_close_to_fp64(fil, j0, prec):
     for k, lay in enumerate(lays):
         np.testing.assert_allclose(Y[off:off + lay.S], states[k].Y, rtol=0, atol=1e-4)
         off += lay.S
+
+
+@pytest.mark.parametrize("j0", [(0, "drag"), (1, "rpy")])
+def test_ensemble_with_j0_reuse_stays_on_each_systems_trajectory(fil, j0):
+    """An ensemble stepped with J0 kept for up to 3 steps (fil_set_j0_reuse):
+    every system meets the tolerance at every step and stays on the oracle's
+    trajectory of that system alone (built with J0 every step) to the
+    accuracy the tolerance gives."""
+    systems = [[16], [20, 33, 7], [30] * 5, [1, 2, 3]]
+    p = fo.Params(a=1.0, eta=1.0, dL=2.2, KB=2.0, KT=1.5, dt=0.2, tol=1e-10, max_iter=80)
+    states, exts, lays = [], [], []
+    for i, segs in enumerate(systems):
+        lay, base, t, mu, xi, rng = _system(segs, 40 + i)
+        states.append(fo.initial_state(lay, p, base, t, mu, xi))
+        exts.append(fo.External(Fext=np.tile([0.0, 0.0, -2.2], (lay.S, 1))))
+        lays.append(lay)
+    segs_all = [n for segs in systems for n in segs]
+    with fil.Filaments(segs_all, fil_per_sys=[len(s) for s in systems], a=p.a, eta=p.eta,
+                       dL=p.dL, KB=p.KB, KT=p.KT, dt=p.dt, tol=p.tol, max_iter=p.max_iter,
+                       j0_model=j0[0]) as m:
+        m.set_state(np.concatenate([s.Y for s in states]), np.concatenate([s.q for s in states]))
+        m.set_external(np.concatenate([e.Fext for e in exts]), None, None)
+        m.set_j0_reuse(3)
+        Y = np.zeros((m.S, 3))
+        for step in range(7):
+            m.step()
+            _, finf = m.sys_stats()
+            assert np.all(finf <= p.tol * p.a)
+            m.get_state(Y, None, None, None, None)
+            off = 0
+            for k, lay in enumerate(lays):
+                states[k], _ = fo.step(lay, p, states[k], exts[k], j0_model=j0[1])
+                np.testing.assert_allclose(Y[off:off + lay.S], states[k].Y, rtol=0, atol=1e-8)
+                off += lay.S
+        assert m.j0_stats()[1] >= 2
