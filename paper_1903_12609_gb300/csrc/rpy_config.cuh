@@ -7,7 +7,7 @@ namespace fil {
 // RPY pair-kernel geometry (tuned on GB300 at 32 000 segments).
 // ----------------------------------------------------------------------------
 constexpr int kRpyThreads = 128;               // threads per CTA
-constexpr int kRpyUnroll = 8;                  // unroll of the per-source loop
+constexpr int kRpyUnroll = 16;                 // unroll of the per-source loop
 constexpr int kRpyTargetsPerThread = 2;        // register-blocked targets
 constexpr int kRpyTile = kRpyThreads * kRpyTargetsPerThread;   // targets per tile
 constexpr int kRpyChunk = 128;                 // sources per shared-memory chunk
