@@ -469,6 +469,10 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
         [[maybe_unused]] const int lane = tid & 31;
         // first target of this warp (slot 0), for the own-group test of 128-target tiles
         [[maybe_unused]] const int64_t wbase = ptile * kTile + (tid & ~31);
+        // 128-target tiles (small systems): a warp whose targets are all padding (in a
+        // system's last tile) computes nothing; the reduce never reads those rows
+        bool idle = false;
+        if constexpr (TPT == 1) idle = wbase - src0 >= nsrc;
         const float2 k23 = f2(k.k23a2, k.k23a2), nk2 = f2(-k.k2a2, -k.k2a2);
         float hi[kT][6], lo[kT][6];
 #pragma unroll
@@ -491,7 +495,7 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
             const int n_grp = (int)min((int64_t)(kRpyChunk / kRpyComp),
                                        (nsrc - ch * kRpyChunk + kRpyComp - 1) / kRpyComp);
 #pragma unroll 1
-            for (int grp = 0; grp < n_grp; ++grp) {
+            for (int grp = 0; grp < (idle ? 0 : n_grp); ++grp) {
                 const float4 *qg = s + kRpyPairF4 * (grp * (kRpyComp / 2));
                 float acc[kT][6];
                 if constexpr (TPT == 1) {
