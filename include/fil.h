@@ -124,12 +124,13 @@ fil_status fil_create_ensemble(const fil_params *p, int32_t n_sys, const int32_t
  * current / last step and the last ||f||_inf that was read. */
 fil_status fil_sys_stats(const fil_ctx *c, int32_t *iters, double *finf);
 
-/* Autotuner of the RPY pair kernel: times `reps` mobility applies of the
- * current state's loads for every candidate schedule -- tiles of 256 targets
+/* Autotuner of the RPY pair kernel: times the pair and reduce kernels of `reps`
+ * mobility applies of the current state's loads (CUDA events around them, so
+ * host launch gaps do not count) for every candidate schedule -- tiles of 256 targets
  * (2 per thread) or 128 targets (1 per thread), and 1..occupancy resident
  * CTAs per SM for the stream-K split of the (tile, source chunk) work units --
  * and keeps the fastest for all later applies. Reports the choice (nullable
- * outputs) and its time per apply in ms. Results change only in rounding (the
+ * outputs) and its pair + reduce time per apply in ms. Results change only in rounding (the
  * summation order of the pair terms). FIL_ESTATE inside a step. */
 fil_status fil_autotune(fil_ctx *c, int32_t reps, int32_t *tile, int32_t *ctas_per_sm,
                         double *ms);

@@ -214,6 +214,7 @@ struct fil_ctx {
     int prof_on;           // time RPY pair-kernel launches with CUDA events
     int prof_n;
     cudaEvent_t *prof_ev;  // 2 * kProfMax events, created on first use
+    cudaEvent_t *tune_ev = nullptr;   // the autotuner's pair of events for the next apply
 };
 
 namespace fil {

@@ -50,6 +50,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 #include <mutex>
 #include <utility>
 
@@ -1021,6 +1022,7 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
     if (pair32_on(c)) {
         const int G = (int)(active_only ? c->rpy_grid32 : std::min<int64_t>(c->rpy_grid32, W));
         pack32_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, sm, c->src32);
+        if (c->tune_ev) cudaEventRecord(c->tune_ev[0], c->stream);
         if (timed) prof_record(c, c->prof_ev[2 * c->prof_n]);
         const RpyConst32 k = make_const<float, RpyConst32>(c->a);
         if (c->rpy_tpt == 1)
@@ -1032,9 +1034,11 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
         if (timed) prof_record(c, c->prof_ev[2 * c->prof_n + 1]);
         rpy_reduce32_kernel<<<rgrid, pb, 0, c->stream>>>((const float *)c->partials, S, sm, W, G,
                                                          T, scale, VW);
+        if (c->tune_ev) cudaEventRecord(c->tune_ev[1], c->stream);
     } else {
         const int G = (int)(active_only ? c->rpy_grid64 : std::min<int64_t>(c->rpy_grid64, W));
         pack64_kernel<<<pgrid, pb, 0, c->stream>>>(Y, FT, S, c->Spad, sm, c->src64);
+        if (c->tune_ev) cudaEventRecord(c->tune_ev[0], c->stream);
         if (timed) prof_record(c, c->prof_ev[2 * c->prof_n]);
         const RpyConst64 k = make_const<double, RpyConst64>(c->a);
         if (c->rpy_tpt == 1)
@@ -1046,6 +1050,7 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
         if (timed) prof_record(c, c->prof_ev[2 * c->prof_n + 1]);
         rpy_reduce64_kernel<<<rgrid, pb, 0, c->stream>>>((const double *)c->partials, S, sm, W, G,
                                                          T, scale, VW);
+        if (c->tune_ev) cudaEventRecord(c->tune_ev[1], c->stream);
     }
     if (timed) c->prof_n += 1;
     c->n_applies += 1;
@@ -1061,11 +1066,12 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
                          double *best_ms) {
     const int64_t a0 = c->n_applies, l0 = c->n_launches;
     const double p0 = c->n_pairs;
-    cudaEvent_t e0, e1;
-    cudaError_t e = cudaEventCreate(&e0);
-    if (e != cudaSuccess) return e;
-    e = cudaEventCreate(&e1);
-    if (e != cudaSuccess) return e;
+    // each rep's pair and reduce kernels are timed by their own pair of events, so
+    // that host launch gaps between applies (which dominate tiny problems) do not
+    // enter the comparison
+    std::vector<cudaEvent_t> ev(2 * (size_t)std::max(1, reps), nullptr);
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
     int best_tpt = c->rpy_tpt, best_threads = c->rpy_threads, best_ctas = c->rpy_ctas;
     float best = 1e30f;
     for (int tpt = 1; tpt <= 2 && e == cudaSuccess; ++tpt) {
@@ -1083,12 +1089,18 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
             build_tiles(c);
             e = upload_tiles(c);
             if (e == cudaSuccess) e = rpy_apply(c, Y, FT, VW);       // warm-up
-            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = rpy_apply(c, Y, FT, VW);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+                c->tune_ev = &ev[2 * r];
+                e = rpy_apply(c, Y, FT, VW);
+                c->tune_ev = nullptr;
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+                float one = 0.f;
+                e = cudaEventElapsedTime(&one, ev[2 * r], ev[2 * r + 1]);
+                ms += one;
+            }
             if (e == cudaSuccess && ms < best) {
                 best = ms;
                 best_tpt = tpt;
@@ -1097,8 +1109,9 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    c->tune_ev = nullptr;
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
     c->rpy_tpt = best_tpt;
     c->rpy_threads = best_threads;
     c->rpy_ctas = best_ctas;

@@ -14,9 +14,10 @@ constexpr int kRpyChunk = 128;                 // sources per shared-memory chun
 constexpr int kRpyComp = 32;                   // sources per compensated partial (FP32)
 // Resident CTAs per SM the FP32 pair kernel is compiled for, by targets per
 // thread: caps the registers (65536 / (128 threads x CTAs)) so that this many
-// CTAs fit.
+// CTAs fit (2 targets: 128 registers, 4 CTAs; 1 target: 80 registers, 6 CTAs,
+// which measured faster on small systems than 4 or 5).
 constexpr int kRpyMinBlocksTpt2 = 4;
-constexpr int kRpyMinBlocksTpt1 = 4;
+constexpr int kRpyMinBlocksTpt1 = 6;
 // float4 per two FP32 source records (the packed FP32x2 layout)
 constexpr int kRpyPairF4 = 6;
 
