@@ -33,7 +33,8 @@
 //  * Stream-K persistent grid: the (tile, chunk) work units are split evenly
 //    over G = #SMs x resident-CTAs; a CTA writes one partial per tile it
 //    touches into slot (cta + tile) and a deterministic reduce kernel sums
-//    them in CTA order. No atomics: results are bitwise reproducible.
+//    them (eight lanes per target, each over a fixed stride of CTAs, then a
+//    fixed shuffle tree). No atomics: results are bitwise reproducible.
 //  * Mixed precision: positions are stored as FP32 hi/lo pairs (hi = fl32(Y),
 //    lo = fl32(Y - hi)). The inner loop forms d from the hi parts alone,
 //    which carries the rounding of the coordinates (~ulp(|Y|)) and is
@@ -725,8 +726,8 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
 }
 
 // ---------------------------------------------------------------------------
-// Reduce the stream-K partials of each target (in CTA order) and scale by
-// 1/(8 pi eta). One thread per target.
+// Reduce the stream-K partials of each target and scale by 1/(8 pi eta)
+// (kRedLanes threads per target, see reduce_target).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cta_range_of_tile(const SysMap &sm, int64_t tile, int64_t W,
                                                   int64_t G, int64_t &b0, int64_t &b1) {
@@ -739,57 +740,66 @@ __device__ __forceinline__ void cta_range_of_tile(const SysMap &sm, int64_t tile
     b1 = ((u1 + 1) * G + W - 1) / W - 1;
 }
 
-__global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, SysMap sm,
-                                    int64_t W, int G, int T, double scale,
-                                    double *__restrict__ VW) {
-    resolve_dyn(sm, W);
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= S) return;
+// kRedLanes lanes per target: lane l sums the partials of the CTAs b0 + l,
+// b0 + l + kRedLanes, ... (in CTA order) and the lane sums are combined by a
+// fixed shuffle tree, so the result does not depend on timing; spreading a
+// target's partials over lanes keeps the latency low when a tile's chunks are
+// split over many CTAs (small problems, many CTAs per SM).
+constexpr int kRedLanes = 8;
+
+template <typename PT, int NPART>
+__device__ __forceinline__ void reduce_target(const PT *__restrict__ part, int64_t S, SysMap &sm,
+                                              int64_t W, int G, int T, double scale,
+                                              double *__restrict__ VW) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = gt / kRedLanes;
+    const int l = (int)(gt % kRedLanes);
+    // the lanes of one target are an aligned group within a warp
+    const unsigned gmask = ((1u << kRedLanes) - 1u) << (threadIdx.x & 31 & ~(kRedLanes - 1));
+    if (n >= S) return;                      // whole groups leave together
     const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
     int64_t tile = P / T;
     const int local = (int)(P - tile * T);
     if (sm.slot_of) {
         tile = sm.slot_of[tile];
-        if (tile < 0) return;         // a system left out of this apply
+        if (tile < 0) return;                 // a system left out of this apply
     }
     int64_t b0, b1;
     cta_range_of_tile(sm, tile, W, G, b0, b1);
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t b = b0; b <= b1; ++b) {
+    for (int64_t b = b0 + l; b <= b1; b += kRedLanes) {
         if (unit_start(b + 1, W, G) == unit_start(b, W, G)) continue;   // a CTA with no unit
-        const float *p = part + (size_t)(b + tile) * 12 * T;
+        const PT *p = part + (size_t)(b + tile) * (6 * NPART) * T;
 #pragma unroll
-        for (int c = 0; c < 6; ++c)
-            acc[c] += (double)p[c * T + local] + (double)p[(6 + c) * T + local];
+        for (int c = 0; c < 6; ++c) {
+            double v = (double)p[c * T + local];
+            if (NPART == 2) v += (double)p[(6 + c) * T + local];
+            acc[c] += v;
+        }
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) VW[6 * n + c] = acc[c] * scale;
+    for (int d = kRedLanes / 2; d > 0; d >>= 1)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] += __shfl_xor_sync(gmask, acc[c], d);
+    if (l == 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) VW[6 * n + c] = acc[c] * scale;
+    }
+}
+
+// FP32 partials: (hi, lo) of each component, 12 floats per target and CTA.
+__global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, SysMap sm,
+                                    int64_t W, int G, int T, double scale,
+                                    double *__restrict__ VW) {
+    resolve_dyn(sm, W);
+    reduce_target<float, 2>(part, S, sm, W, G, T, scale, VW);
 }
 
 __global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, SysMap sm,
                                     int64_t W, int G, int T, double scale,
                                     double *__restrict__ VW) {
     resolve_dyn(sm, W);
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= S) return;
-    const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
-    int64_t tile = P / T;
-    const int local = (int)(P - tile * T);
-    if (sm.slot_of) {
-        tile = sm.slot_of[tile];
-        if (tile < 0) return;         // a system left out of this apply
-    }
-    int64_t b0, b1;
-    cta_range_of_tile(sm, tile, W, G, b0, b1);
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t b = b0; b <= b1; ++b) {
-        if (unit_start(b + 1, W, G) == unit_start(b, W, G)) continue;   // a CTA with no unit
-        const double *p = part + (size_t)(b + tile) * 6 * T;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) acc[c] += p[c * T + local];
-    }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) VW[6 * n + c] = acc[c] * scale;
+    reduce_target<double, 1>(part, S, sm, W, G, T, scale, VW);
 }
 
 SysMap sys_map(const fil_ctx *c, bool active_only) {
@@ -1011,7 +1021,7 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
     const double scale = 1.0 / (8.0 * kPi * c->eta);
     const int pb = 256;
     const unsigned pgrid = (unsigned)((c->Spad + pb - 1) / pb);
-    const unsigned rgrid = (unsigned)((S + pb - 1) / pb);
+    const unsigned rgrid = (unsigned)((S * kRedLanes + pb - 1) / pb);
     const bool timed = c->prof_on && c->prof_n < kProfMax;
     const SysMap sm = sys_map(c, active_only);
     const int64_t W = active_only ? c->act_units : c->rpy_units;
@@ -1275,7 +1285,7 @@ extern "C" fil_status fil_rpy_apply_noalloc(int64_t n_seg, const double *Y, cons
         e = launch(rpy_pair32_kernel<kRpyTargetsPerThread>, (unsigned)G, kRpyThreads, st,
                    (const float4 *)src, sm, W, G, make_const<float, RpyConst32>(a), part);
     if (e == cudaSuccess)
-        e = launch(rpy_reduce32_kernel, (unsigned)((n_seg + pb - 1) / pb), pb, st,
+        e = launch(rpy_reduce32_kernel, (unsigned)((n_seg * kRedLanes + pb - 1) / pb), pb, st,
                    (const float *)part, n_seg, sm, W, G, kRpyTile, 1.0 / (8.0 * kPi * eta), VW);
     return e == cudaSuccess ? FIL_OK : FIL_ECUDA;
 }
