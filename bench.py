@@ -45,6 +45,8 @@ if ROOT not in sys.path:
 METRIC = ("RPY pair interactions/s (% FMA peak); timesteps/s at 32k segments, "
           "plain vs chosen form")
 UNIT = "pair interactions/s"
+EXTRAP_NAME = {1: "linear extrapolation", 2: "quadratic extrapolation",
+               3: "adaptive extrapolation (linear or quadratic per filament and block)"}
 # algorithmic flops of one far-field pair (FMA = 2): the fixed count of the structured
 # far-field formula used as the roofline unit (the kernel itself issues ~51 FP32
 # operations per pair)
@@ -343,9 +345,10 @@ def run_c1_mobility(fil, torch, applies=1000, per_graph=100, min_seconds=1.0):
             "gpu_launches": int(launches_per_graph * replays), "clocks": clocks}
 
 
-def run_c0_single(fil, torch, steps=200):
+def run_c0_single(fil, torch, steps=200, order=1):
     """Single filament (N = 20) sedimenting from a 45-degree tilt, B = 1000,
-    dt = T/100, Broyden tolerance 1e-8, 200 steps, all FP64 (App. B.2 J0)."""
+    dt = T/100, Broyden tolerance 1e-8, 200 steps, all FP64 (App. B.2 J0),
+    initial guess extrapolated at the given order."""
     from paper_1903_12609_gb300.inputs import single_filament, workload_params
     wl = workload_params(1, 20, B=1000.0, dt_over_T=0.01, tol=1e-8)
     base, t, mu, xi = single_filament(20, seed=0)
@@ -353,6 +356,7 @@ def run_c0_single(fil, torch, steps=200):
     m = fil.Filaments([20], a=wl.a, eta=wl.eta, dL=wl.dL, KB=wl.KB, KT=wl.KT, dt=wl.dt,
                       tol=wl.tol, max_iter=50, precision=fil.FIL_FP64,
                       j0_model=fil.FIL_J0_DRAG, stream=stream.cuda_stream)
+    m.set_extrapolation(order)
     m.init_straight(base, t, mu, xi)
     m.set_external(np.tile([0.0, 0.0, -wl.W * wl.dL], (20, 1)), None, None)
     torch.cuda.synchronize()
@@ -388,7 +392,8 @@ def run_c0_single(fil, torch, steps=200):
             "pairs_per_s": (a1 - a0) * 400.0 / (ms * 1e-3), "dtype": "f64",
             "config": {"workload": "single filament N=20, B=1000, 45-degree tilt with 1e-3 "
                                    "perturbation, sedimenting; BDF2 dt=T/100, tol 1e-8",
-                       "precision": "fp64", "j0": "drag (App. B.2)"},
+                       "precision": "fp64", "j0": "drag (App. B.2)",
+                       "initial_guess": EXTRAP_NAME[order]},
             "roofline": {"bound": "latency", "note": "400 pairs per apply: each Broyden "
                                                      "iteration is a chain of small kernels and "
                                                      "one status read"},
@@ -420,6 +425,7 @@ def run_ensemble(args, fil, torch, nested=False):
     m.set_external(Fext, None, follower)
     m.set_graph(args.graph)
     m.set_j0_reuse(args.j0_reuse)
+    m.set_extrapolation(args.extrapolation)
     for _ in range(args.warmup):
         m.step()
     tuned = None
@@ -498,6 +504,7 @@ def run_ensemble(args, fil, torch, nested=False):
                    "precision": args.ens_precision, "precision_note":
                        PRECISION_NOTE[args.ens_precision],
                    "j0_reuse_max_age": args.j0_reuse,
+                   "initial_guess": EXTRAP_NAME[args.extrapolation],
                    "pairs_per_apply": pairs_per_apply, "parallelism": "single"},
         "pairs_per_s": pairs / (ms * 1e-3),
         "ensemble_timesteps_per_s": steps / (ms * 1e-3),
@@ -544,7 +551,7 @@ def host_round_trip(torch, n=2000):
     return 1e6 * dt / n
 
 
-def run_tether(fil, torch, steps=20, warmup=5, every=4):
+def run_tether(fil, torch, steps=20, warmup=5, every=4, order=1):
     """The 32k suspension's cloud with every fourth filament clamped at its base
     (Sec. 5.2.1: Y_1 fixed, u_1 = 0), weightless: the follower-force half keeps
     its tip force, the other half is passive. (With gravity the cloud settles
@@ -552,13 +559,15 @@ def run_tether(fil, torch, steps=20, warmup=5, every=4):
     first step would ask the clamps to hold that flow from a standing start;
     Algorithm 2 with the per-filament J0 does not converge on it at 1000
     filaments, on the GPU or in the oracle.) FIL_PAIR32, extrapolated initial
-    guess (the network refuses tethered contexts), J0 built every step (the
-    tethered J0 follows the prescribed motion)."""
+    guess of the given order (tether multipliers linear; the network refuses
+    tethered contexts), J0 built every step (the tethered J0 follows the
+    prescribed motion)."""
     wl, base, t, mu, Fext, follower = workload(1000, 32, seed=0)
     stream = torch.cuda.Stream()
     m = fil.Filaments(wl.seg_per_fil, precision=fil.FIL_PAIR32, stream=stream.cuda_stream,
                       a=wl.a, eta=wl.eta, dL=wl.dL, KB=wl.KB, KT=wl.KT, dt=wl.dt, tol=wl.tol,
                       max_iter=wl.max_iter, j0_model=fil.FIL_J0_FILAMENT_RPY)
+    m.set_extrapolation(order)
     m.init_straight(base, t, mu, None)
     m.set_external(None, None, follower)
     mask = (np.arange(1000) % every) == 0
@@ -591,7 +600,8 @@ def run_tether(fil, torch, steps=20, warmup=5, every=4):
                                    "(every %d-th) clamped at the base, no gravity, tip follower "
                                    "force fL^2/KB=100 on the other half as in the suspension, "
                                    "dt=T/200, tol 1e-4" % (int(mask.sum()), every),
-                       "precision": "pair32", "initial_guess": "extrapolation",
+                       "precision": "pair32",
+                       "initial_guess": EXTRAP_NAME[order],
                        "j0": "filament_rpy + rank-6 correction per clamped filament, every step"},
             "roofline": pair_roofline(S * S, pair_ms, n_pair),
             "max_abs_multiplier": float(np.abs(lam[mask]).max()),
@@ -621,18 +631,26 @@ def run_suspension(args, fil, torch, world, rank, local):
     m.init_straight(base, t, mu, None)
     m.set_external(Fext, None, follower)
     m.set_j0_reuse(args.j0_reuse)
+    m.set_extrapolation(args.extrapolation)
     if args.steric > 0:
         m.set_steric(args.steric, 1.1)
 
-    # learned warm start (chosen form): the committed network, trained on other seeds
-    net, warm_mode = None, None
+    # learned warm start (chosen form): the committed network, trained on other seeds for
+    # the extrapolation order it corrects
+    net, warm_mode, net_order, net_note = None, None, None, None
     if args.warm != "off" and prec != fil.FIL_FP64:
         from paper_1903_12609_gb300 import warmstart
         if os.path.exists(warmstart.DEFAULT_WEIGHTS):
-            net = warmstart.load(max_batch=max(64, n_fil), stream=stream.cuda_stream)
+            net_order = warmstart.trained_order()
             warm_mode = (fil.FIL_WARM_PREDICTION_FIRST if args.warm == "prediction_first"
                          else fil.FIL_WARM_BEST_OF_TWO)
-            fil.fil_warm_attach(m.ctx, net, warm_mode)
+            net = warmstart.load(max_batch=max(64, n_fil), stream=stream.cuda_stream)
+            if net_order == args.extrapolation:
+                fil.fil_warm_attach(m.ctx, net, warm_mode)
+            else:
+                net_note = ("the committed network corrects the %s; not attached to the "
+                            "timed steps (%s)" % (EXTRAP_NAME[net_order],
+                                                  EXTRAP_NAME[args.extrapolation]))
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -747,34 +765,45 @@ def run_suspension(args, fil, torch, world, rank, local):
         Y1c, q1c = np.zeros((S, 3)), np.zeros((S, 4))
         m.get_state(Y1c, q1c, None, None, None)
 
-        # ---- learned warm start vs extrapolation: the timed window's first 20 steps
-        #      from st0, and 20 steps from step 200 of the same trajectory ----
+        # ---- initial guesses of a step: linear and quadratic extrapolation and the learned
+        #      warm start (at the order it was trained for), on the timed window's first 20
+        #      steps from st0 and 20 steps from step 200 of the same trajectory ----
+        ig = {"weights": (os.path.relpath(warmstart.DEFAULT_WEIGHTS, ROOT)
+                          if net is not None else None),
+              "network_trained_for_order": net_order, "mode": args.warm}
+        K = 20
+        m.set_state(*st0)
+        m.set_extrapolation(args.extrapolation)
+        fil.fil_warm_attach(m.ctx, net if net_note is None else None, warm_mode or 0)
+        for _ in range(200 - args.warmup):
+            m.step()
+        st200 = [np.zeros_like(a) for a in st0]
+        m.get_state(*st200)
+        arms = [("extrapolation_linear", 1, None), ("extrapolation_quadratic", 2, None),
+                ("extrapolation_adaptive", 3, None)]
         if net is not None:
-            warm = {"mode": args.warm, "weights": os.path.relpath(warmstart.DEFAULT_WEIGHTS,
-                                                                  ROOT)}
-            K = 20
-            m.set_state(*st0)
-            fil.fil_warm_attach(m.ctx, net, warm_mode)
-            for _ in range(200 - args.warmup):
-                m.step()
-            st200 = [np.zeros_like(a) for a in st0]
-            m.get_state(*st200)
-            for wname, state, what in (
-                    ("early", st0, "20 steps from the state after the warm-up steps of a "
-                                   "fresh cloud (the timed window's first 20 steps)"),
-                    ("later", st200, "20 steps from step 200 of the same trajectory")):
-                rec = {"window": what}
-                for name, use in (("extrapolation", False), ("learned", True)):
-                    m.set_state(*state)
-                    fil.fil_warm_attach(m.ctx, net if use else None, warm_mode)
-                    ms_w, its = timed_steps(m, K, with_flush=False)
-                    rec[name] = {"timesteps_per_s": K / (ms_w * 1e-3),
-                                 "broyden_iters_per_step": float(np.mean(its)), "steps": K}
-                rec["iteration_ratio"] = (rec["learned"]["broyden_iters_per_step"]
-                                          / rec["extrapolation"]["broyden_iters_per_step"])
-                warm[wname] = rec
-            fil.fil_warm_attach(m.ctx, None)
-            extra["warm_start"] = warm
+            arms.append(("learned", net_order, net))
+        for wname, state, what in (
+                ("early", st0, "20 steps from the state after the warm-up steps of a "
+                               "fresh cloud (the timed window's first 20 steps)"),
+                ("later", st200, "20 steps from step 200 of the same trajectory")):
+            rec = {"window": what}
+            for name, order, use in arms:
+                m.set_state(*state)
+                m.set_extrapolation(order)
+                fil.fil_warm_attach(m.ctx, use, warm_mode or 0)
+                ms_w, its = timed_steps(m, K, with_flush=False)
+                rec[name] = {"timesteps_per_s": K / (ms_w * 1e-3), "order": order,
+                             "broyden_iters_per_step": float(np.mean(its)), "steps": K}
+            if net is not None:
+                base = {1: "extrapolation_linear", 2: "extrapolation_quadratic",
+                        3: "extrapolation_adaptive"}[net_order]
+                rec["learned_over_its_extrapolation_iterations"] = (
+                    rec["learned"]["broyden_iters_per_step"]
+                    / rec[base]["broyden_iters_per_step"])
+            ig[wname] = rec
+        fil.fil_warm_attach(m.ctx, None)
+        extra["initial_guess"] = ig
 
         # ---- velocity error vs the FP64 oracle on the positions after the timed steps
         #      (N(0,1) loads; sampled target rows = the CPU baseline's sample) ----
@@ -796,12 +825,11 @@ def run_suspension(args, fil, torch, world, rank, local):
                            **params)
         mm.set_state(*st0)
         mm.set_external(Fext, None, follower)
+        mm.set_extrapolation(args.extrapolation)
         netm = None
-        if args.warm != "off":
-            from paper_1903_12609_gb300 import warmstart
-            if os.path.exists(warmstart.DEFAULT_WEIGHTS):
-                netm = warmstart.load(max_batch=max(64, n_fil), stream=stream.cuda_stream)
-                fil.fil_warm_attach(mm.ctx, netm, warm_mode)
+        if warm_mode is not None and net_note is None:
+            netm = warmstart.load(max_batch=max(64, n_fil), stream=stream.cuda_stream)
+            fil.fil_warm_attach(mm.ctx, netm, warm_mode)
         mm.profile(True)
         mm.profile_read()
         ma0, _, _ = mm.counters()
@@ -825,9 +853,9 @@ def run_suspension(args, fil, torch, world, rank, local):
         mr.set_state(*st0)
         mr.set_external(Fext, None, follower)
         mr.set_j0_reuse(other)
+        mr.set_extrapolation(args.extrapolation)
         netr = None
-        if warm_mode is not None:
-            from paper_1903_12609_gb300 import warmstart
+        if warm_mode is not None and net_note is None:
             netr = warmstart.load(max_batch=max(64, n_fil), stream=stream.cuda_stream)
             fil.fil_warm_attach(mr.ctx, netr, warm_mode)
         rb0, rr0 = mr.j0_stats()
@@ -862,7 +890,7 @@ def run_suspension(args, fil, torch, world, rank, local):
                      "pairs_per_s": (pa1 - pa0) * float(S) * S / (pms_ * 1e-3),
                      "broyden_iters_per_step": float(np.mean(pits)),
                      "steps": args.plain_steps, "precision": "fp64",
-                     "initial_guess": "extrapolation",
+                     "initial_guess": "order-1 extrapolation", "j0_reuse_max_age": 1,
                      "from": "steps 2.. from the same state as the timed steps"}
             plain["frac_of_measured_fp64_peak"] = plain["pairs_per_s"] * FLOPS_PER_PAIR / p64
             extra["plain_fp64"] = plain
@@ -887,9 +915,11 @@ def run_suspension(args, fil, torch, world, rank, local):
 
         # ---- the other configurations (a failure is reported in its record) ----
         for key, fn in (("c1_mobility_3200", lambda: run_c1_mobility(fil, torch)),
-                        ("c0_single_filament", lambda: run_c0_single(fil, torch)),
+                        ("c0_single_filament",
+                         lambda: run_c0_single(fil, torch, order=args.extrapolation)),
                         ("c3_ensemble256", lambda: run_ensemble(args, fil, torch, nested=True)),
-                        ("tethered_suspension", lambda: run_tether(fil, torch))):
+                        ("tethered_suspension",
+                         lambda: run_tether(fil, torch, order=args.extrapolation))):
             try:
                 extra[key] = fn()
             except Exception as exc:   # keep the headline line when a nested record fails
@@ -924,8 +954,11 @@ def run_suspension(args, fil, torch, world, rank, local):
                         "dt=T/200, Broyden tol 1e-4" % (n_fil, S),
             "segments": S, "precision": args.precision,
             "precision_note": PRECISION_NOTE[args.precision], "j0": args.j0,
-            "initial_guess": ("learned warm start (%s)" % args.warm) if warm_mode is not None
-                             else "extrapolation",
+            "initial_guess": (("learned warm start (%s) on the %s"
+                               % (args.warm, EXTRAP_NAME[args.extrapolation]))
+                              if warm_mode is not None and net_note is None
+                              else EXTRAP_NAME[args.extrapolation]),
+            "initial_guess_note": net_note,
             "j0_reuse_max_age": args.j0_reuse,
             "steric_FS": args.steric if args.steric > 0 else None,
             "parallelism": "replicas" if world > 1 else "single",
@@ -993,32 +1026,6 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def aggregate_ranks(units, ms, dist, device):
-    """(sum of units over ranks, max of device time over ranks); one rank: as is."""
-    if dist is None:
-        return units, ms
-    import torch
-    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
-    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
-    dist.all_reduce(u, op=dist.ReduceOp.SUM)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(u[0]), float(t[0])
-
-
-def run_peaks(args, fil):
-    """Measured FMA rates against the derived peaks (SMs x lanes x 2 x clock)."""
-    out = {"metric": "measured FMA rate", "unit": "TFLOP/s", "n_gpus": 1, "data": "synthetic",
-           "config": {"workload": "FMA chains at full occupancy (fil_fma_peak)"}}
-    for name, fp64, lanes in (("fp32", False, FP32_LANES_PER_SM), ("fp64", True, 2)):
-        reps = [fil.fil_fma_peak(fp64) for _ in range(3)]
-        fl, mhz = max(reps)
-        out[name] = {"tflops": fl / 1e12, "sm_mhz": mhz,
-                     "derived_at_max_clock": N_SM * lanes * 2 * SM_MAX_MHZ * 1e6 / 1e12,
-                     "derived_at_measured_clock": N_SM * lanes * 2 * mhz * 1e6 / 1e12,
-                     "runs_tflops": [r[0] / 1e12 for r in reps]}
-    print(json.dumps(out), flush=True)
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1041,6 +1048,10 @@ def main():
                     help="approximate Jacobian: filament RPY blocks (default) or App. B.2 drag")
     ap.add_argument("--n-fil", type=int, default=1000,
                     help="filaments of 32 segments (1000 = the 32k suspension; smaller for profiling)")
+    ap.add_argument("--extrapolation", type=int, default=3, choices=[1, 2, 3],
+                    help="extrapolated initial guess (fil_set_extrapolation): 1 linear, "
+                         "2 quadratic, 3 adaptive per filament and block; the learned warm "
+                         "start is attached only when trained for this choice")
     ap.add_argument("--warm", default="prediction_first",
                     choices=["prediction_first", "best_of_two", "off"],
                     help="learned warm start of each step (the committed network) and its mode")

@@ -84,6 +84,14 @@ typedef enum {
                                  suspensions                                         */
 } fil_j0_model;
 
+typedef enum {
+    FIL_EXTRAP_LINEAR = 1,     /* x_0 = 2 x^j - x^{j-1}                              */
+    FIL_EXTRAP_QUADRATIC = 2,  /* x_0 = 3 x^j - 3 x^{j-1} + x^{j-2}                  */
+    FIL_EXTRAP_ADAPTIVE = 3    /* per filament and per block of unknowns (Y_1, u,
+                                  Lambda): the one of the two that predicted the
+                                  last committed step better                         */
+} fil_extrapolation_order;
+
 typedef struct {
     int32_t n_fil;                /* number of filaments M >= 1                    */
     const int32_t *seg_per_fil;   /* HOST array of M segment counts N_i >= 1; copied */
@@ -300,7 +308,7 @@ fil_status fil_step(fil_ctx *c, int32_t *iters);
 fil_status fil_set_dt(fil_ctx *c, double dt);
 
 /* J0 reuse across timesteps. The paper builds J0 at the initial guess of every
- * step (Sec. 3.2.2: "evaluated each timestep"); J0 only shapes the Broyden
+ * step (Sec. 3.2.2 evaluates it once per timestep); J0 only shapes the Broyden
  * iterates (H_0 of Algorithm 2), not the converged solution, so its factors
  * may be kept for several steps. With max_age > 1, fil_broyden_begin / fil_step
  * keep the factors of the step that built them for at most max_age steps in
@@ -316,6 +324,33 @@ fil_status fil_set_j0_reuse(fil_ctx *c, int32_t max_age);
 /* Steps whose J0 was built and steps that reused an earlier J0, since the
  * context was created (either pointer may be NULL). */
 fil_status fil_j0_stats(const fil_ctx *c, int64_t *builds, int64_t *reuses);
+
+/* Extrapolation that gives a step's initial guess X_0 (fil_extrapolation_order).
+ * The paper starts Algorithm 2 from guesses extrapolated from the solutions of
+ * past timesteps (Sec. 3.3) without stating the form. Each unknown takes the
+ * value at the next step of the polynomial through its last committed values:
+ * FIL_EXTRAP_LINEAR (the default) through two, FIL_EXTRAP_QUADRATIC through
+ * three. FIL_EXTRAP_ADAPTIVE chooses between the two for each filament and
+ * each of its blocks of unknowns (Y_1; u_1..u_N; Lambda): when a step is
+ * committed, each block's solution is compared with what the linear and the
+ * quadratic extrapolation gave for it (sums of squared differences) and the
+ * next step uses the order that came closer (linear until both could be
+ * compared). The quadratic form has the smaller truncation error but weighs
+ * the past solutions by 3, -3, 1 instead of 2, -1, so it carries more of
+ * their own error (each is converged only to the tolerance): it wins when the
+ * motion over a step is large compared with that, and loses when it is not.
+ * With fewer committed values an order drops to what they allow: Y_1 uses
+ * Y^j, Y^{j-1} (held from the first committed step on, or given to
+ * fil_set_state) and Y^{j-2}; u and Lambda use the values of committed steps
+ * only, u = 0 and Lambda = Lambda^j before the first. Tether multipliers stay
+ * linear. The converged solution does not depend on X_0 beyond the tolerance;
+ * the iteration count does. A warm-start network (fil_warm_attach) predicts a
+ * correction to this extrapolation, so use it with the order it was trained
+ * with. FIL_EINVAL for another value, FIL_ESTATE inside a step. */
+fil_status fil_set_extrapolation(fil_ctx *c, int32_t order);
+
+/* The extrapolation in use (a fil_extrapolation_order value). */
+fil_status fil_extrapolation(const fil_ctx *c, int32_t *order);
 
 /* Counters since creation: RPY applies, Broyden iterations and kernels this
  * library launched (any pointer may be NULL). */

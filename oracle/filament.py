@@ -22,6 +22,11 @@ Readings where the paper is silent (each also listed in the design notes):
   previous steps, x_0 = 2 x^j - x^{j-1}, when both exist (Y_1 from the BDF2
   history; u and Lambda from the last two committed steps); with one previous
   step u = u^j and Lambda = Lambda^j; on the first step Y_1^j, u = 0, Lambda^j.
+  Optionally (order 2) the quadratic through the last three values,
+  x_0 = 3 x^j - 3 x^{j-1} + x^{j-2}, for each unknown that has three; or
+  (order 3, adaptive) per filament and block of unknowns (Y_1, u, Lambda) the
+  one of the two that came closer (sum of squared differences) to the block's
+  solution at the last commit, linear until both could be compared.
 * Convergence: ||f||_inf <= tol * a (Sec. 3.3 states the tolerance for the
   infinity norm relative to a). Norms in Algorithm 2 are the 2-norm over the
   whole system.
@@ -231,7 +236,8 @@ class External:
 @dataclass
 class State:
     """BDF2 history: Y^j, Y^{j-1} (None before the first step), q^j, u^j, Lambda^j,
-    and for the initial guess u^{j-1}, Lambda^{j-1} (None until two steps exist)."""
+    and for the initial guess u^{j-1}, Lambda^{j-1} (None until two steps exist)
+    and Y^{j-2}, u^{j-2}, Lambda^{j-2} (None until they exist)."""
     Y: np.ndarray
     q: np.ndarray
     Yprev: np.ndarray | None = None
@@ -242,6 +248,10 @@ class State:
     lam_prev: np.ndarray | None = None
     tlam: np.ndarray | None = None        # (M, 6) tether multipliers of the last step
     tlam_prev: np.ndarray | None = None   # (M, 6) of the step before
+    Yprev2: np.ndarray | None = None
+    u_prev2: np.ndarray | None = None
+    lam_prev2: np.ndarray | None = None
+    xord: np.ndarray | None = None        # (M, 3) adaptive orders of Y_1, u, Lambda
     extra: dict = field(default_factory=dict)
 
     def copy(self):
@@ -250,7 +260,9 @@ class State:
         return State(Y=self.Y.copy(), q=self.q.copy(), Yprev=cp(self.Yprev), u=cp(self.u),
                      lam=cp(self.lam), steps=self.steps, u_prev=cp(self.u_prev),
                      lam_prev=cp(self.lam_prev), tlam=cp(self.tlam),
-                     tlam_prev=cp(self.tlam_prev))
+                     tlam_prev=cp(self.tlam_prev), Yprev2=cp(self.Yprev2),
+                     u_prev2=cp(self.u_prev2), lam_prev2=cp(self.lam_prev2),
+                     xord=cp(self.xord))
 
 
 @dataclass
@@ -747,22 +759,74 @@ class Broyden:
 # One BDF2 / Lie-group timestep
 # --------------------------------------------------------------------------
 
-def initial_guess(lay: Layout, state: State, tether: Tether | None = None):
-    """X_0 of a step: each unknown extrapolated linearly from the two previous
-    steps where both exist (x_0 = 2 x^j - x^{j-1}), else the last value; the
-    multiplier slots of tethered filaments likewise from the multipliers of
-    past steps (zero before the first)."""
-    Y1 = np.array([state.Y[lay.off_seg[i]] for i in range(lay.M)])
-    if state.Yprev is not None:
-        Y1 = 2.0 * Y1 - np.array([state.Yprev[lay.off_seg[i]] for i in range(lay.M)])
-    if state.u is not None and state.Yprev is not None:
-        u = 2.0 * state.u - state.u_prev if state.u_prev is not None else state.u.copy()
+def extrapolate(values, order):
+    """The next value of the polynomial through the last min(order + 1,
+    len(values)) of values = [x^j, x^{j-1}, x^{j-2}, ...] (None entries end the
+    list): Newton's backward-difference form, x_0 = sum_k nabla^k x^j, with
+    nabla x^j = x^j - x^{j-1} (the polynomial's value one step ahead; order 1
+    gives 2 x^j - x^{j-1}, order 2 gives 3 x^j - 3 x^{j-1} + x^{j-2})."""
+    vals = []
+    for v in values:
+        if v is None:
+            break
+        vals.append(np.asarray(v, dtype=np.float64))
+    vals = vals[:order + 1]
+    out = np.zeros_like(vals[0])
+    diff = list(vals)
+    for _ in range(len(vals)):
+        out = out + diff[0]
+        diff = [diff[k] - diff[k + 1] for k in range(len(diff) - 1)]
+    return out
+
+
+ADAPTIVE = 3
+
+
+def _blocks(lay: Layout, i: int):
+    """Row slices of filament i: its Y_1 row (in per-filament arrays), its u
+    rows (per segment) and its Lambda rows."""
+    return (slice(i, i + 1), slice(lay.off_seg[i], lay.off_seg[i + 1]),
+            slice(lay.off_lam[i], lay.off_lam[i + 1]))
+
+
+def _histories(lay: Layout, state: State):
+    """[x^j, x^{j-1}, x^{j-2}] of the Y_1, u and Lambda blocks (None where a
+    level does not exist); u only once Y^{j-1} exists (else u = 0)."""
+    first = [lay.off_seg[i] for i in range(lay.M)]
+
+    def y1(a):
+        return None if a is None else np.array([a[k] for k in first])
+
+    hy = [y1(state.Y), y1(state.Yprev), y1(state.Yprev2)]
+    hu = ([state.u, state.u_prev, state.u_prev2]
+          if state.u is not None and state.Yprev is not None else None)
+    hl = [state.lam, state.lam_prev, state.lam_prev2] if state.lam is not None else None
+    return hy, hu, hl
+
+
+def initial_guess(lay: Layout, state: State, tether: Tether | None = None, order: int = 1):
+    """X_0 of a step: each unknown extrapolated from the previous steps with
+    the polynomial of degree order (1: x_0 = 2 x^j - x^{j-1}) through as many
+    of its last values as exist, else the last value (order ADAPTIVE: degree
+    state.xord[i, block] per filament and block, at most 2); the multiplier
+    slots of tethered filaments linearly from the multipliers of past steps
+    (zero before the first)."""
+    hy, hu, hl = _histories(lay, state)
+    if order != ADAPTIVE:
+        Y1 = extrapolate(hy, order)
+        u = extrapolate(hu, order) if hu is not None else np.zeros((lay.S, 3))
+        lam = extrapolate(hl, order) if hl is not None else np.zeros((lay.n_lam, 3))
     else:
+        xord = state.xord if state.xord is not None else np.ones((lay.M, 3), dtype=int)
+        Y1 = np.zeros((lay.M, 3))
         u = np.zeros((lay.S, 3))
-    if state.lam is not None:
-        lam = 2.0 * state.lam - state.lam_prev if state.lam_prev is not None else state.lam.copy()
-    else:
         lam = np.zeros((lay.n_lam, 3))
+        for i in range(lay.M):
+            for b, (out, hist, rows) in enumerate(zip((Y1, u, lam), (hy, hu, hl),
+                                                      _blocks(lay, i))):
+                if hist is not None:
+                    out[rows] = extrapolate([None if h is None else h[rows] for h in hist],
+                                            int(xord[i, b]))
     X0 = lay.join_X(Y1, u, lam)
     if tether is not None:
         if state.tlam is not None:
@@ -776,12 +840,12 @@ def initial_guess(lay: Layout, state: State, tether: Tether | None = None):
 
 
 def begin_step(lay: Layout, p: Params, state: State, ext: External | None, nthreads=1,
-               j0_model="drag", tether: Tether | None = None):
+               j0_model="drag", tether: Tether | None = None, order: int = 1):
     """Initial guess, J0 at it (LU-factored) and f(X_0): the set-up of Algorithm 2.
 
     j0_model 'drag' is App. B.2 as printed; 'rpy' keeps each filament's own
     RPY blocks in f_0 (see jacobian0_general)."""
-    X0 = initial_guess(lay, state, tether)
+    X0 = initial_guess(lay, state, tether, order)
     blocks = jacobian0_tethered(lay, p, state, X0, tether, j0_model)
     solver = J0Solver(lay, blocks)
 
@@ -791,11 +855,33 @@ def begin_step(lay: Layout, p: Params, state: State, ext: External | None, nthre
     return Broyden(fun, solver.solve, X0, p.tol * p.a)
 
 
-def commit_step(lay: Layout, p: Params, state: State, X, tether: Tether | None = None):
+def adaptive_orders(lay: Layout, state: State, X):
+    """The adaptive choice at a commit (before the history shift): for each
+    filament and block (Y_1, u, Lambda) whose last three values exist, 2 if
+    the quadratic extrapolation came strictly closer to the block's solution
+    in X than the linear one (sums of squared differences), else 1."""
+    xs = lay.split_X(X)
+    out = np.ones((lay.M, 3), dtype=int)
+    for b, hist in enumerate(_histories(lay, state)):
+        if hist is None or any(h is None for h in hist):
+            continue
+        for i in range(lay.M):
+            rows = _blocks(lay, i)[b]
+            h = [x[rows] for x in hist]
+            e1 = float(np.sum((xs[b][rows] - extrapolate(h, 1)) ** 2))
+            e2 = float(np.sum((xs[b][rows] - extrapolate(h, 2)) ** 2))
+            out[i, b] = 2 if e2 < e1 else 1
+    return out
+
+
+def commit_step(lay: Layout, p: Params, state: State, X, tether: Tether | None = None,
+                order: int = 1):
     """q^{j+1} = exp(u*) q^j, Y^{j+1} from the robot arm, and the history shift.
     u^{j-1}, Lambda^{j-1} (and the tether multipliers of the step before) are
-    kept only when they came from a committed step."""
+    kept only when they came from a committed step; with order ADAPTIVE the
+    orders of the next guess (adaptive_orders)."""
     X, lam1, lam2 = tether_resolve(lay, X, tether)
+    xord = adaptive_orders(lay, state, X) if order == ADAPTIVE else state.xord
     q, t, Y, u, lam = unpack(lay, p, X, state.q)
     stepped = state.steps >= 1
     tlam = np.concatenate([lam1, lam2], axis=1) if tether is not None else None
@@ -804,18 +890,22 @@ def commit_step(lay: Layout, p: Params, state: State, X, tether: Tether | None =
                  lam_prev=state.lam.copy() if (stepped and state.lam is not None) else None,
                  tlam=tlam,
                  tlam_prev=(state.tlam.copy() if (tether is not None and state.tlam is not None)
-                            else None))
+                            else None),
+                 Yprev2=state.Yprev.copy() if state.Yprev is not None else None,
+                 u_prev2=state.u_prev.copy() if state.u_prev is not None else None,
+                 lam_prev2=state.lam_prev.copy() if state.lam_prev is not None else None,
+                 xord=xord)
 
 
 def step(lay: Layout, p: Params, state: State, ext: External | None, nthreads=1,
-         j0_model="drag", tether: Tether | None = None):
+         j0_model="drag", tether: Tether | None = None, order: int = 1):
     """One timestep; returns (new_state, iterations)."""
-    br = begin_step(lay, p, state, ext, nthreads, j0_model, tether)
+    br = begin_step(lay, p, state, ext, nthreads, j0_model, tether, order)
     while not br.converged():
         if br.k >= p.max_iter:
             raise RuntimeError("Broyden did not converge in %d iterations" % p.max_iter)
         br.iterate()
-    return commit_step(lay, p, state, br.X, tether), br.k
+    return commit_step(lay, p, state, br.X, tether, order), br.k
 
 
 def initial_state(lay: Layout, p: Params, base, t_fil, mu_fil, xi=None, lam=None):

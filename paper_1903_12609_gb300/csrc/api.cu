@@ -120,6 +120,10 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->lam = ar.take<double>(3 * (nlam > 0 ? nlam : 1));
     c->uprev2 = ar.take<double>(3 * S);
     c->lamprev = ar.take<double>(3 * (nlam > 0 ? nlam : 1));
+    c->Yprev2 = ar.take<double>(3 * S);
+    c->uprev3 = ar.take<double>(3 * S);
+    c->lamprev2 = ar.take<double>(3 * (nlam > 0 ? nlam : 1));
+    c->xord = ar.take<int8_t>(3 * M);
     c->Fext = ar.take<double>(3 * S);
     c->Text = ar.take<double>(3 * S);
     c->follower = ar.take<double>(M);
@@ -364,7 +368,7 @@ fil_status fil_create_ensemble(const fil_params *p, int32_t n_sys, const int32_t
     c->jdense_len = jofs[p->n_fil];
     c->aux_len = auxofs[p->n_fil];
     c->stream = (cudaStream_t)p->stream;
-    c->have_prev = 0; c->hist = 0; c->steps = 0; c->k = 0; c->in_step = 0;
+    c->have_prev = 0; c->ylev = 0; c->hist = 0; c->steps = 0; c->k = 0; c->in_step = 0;
     c->has_Fext = c->has_Text = c->has_follower = 0;
     c->n_applies = c->n_iters = 0;
     c->iters_step = 0; c->conv = 0;
@@ -509,7 +513,10 @@ fil_status fil_set_state(fil_ctx *c, const double *Y, const double *q, const dou
             CK(cudaMemsetAsync(c->lam, 0, sizeof(double) * 3 * c->lay.nlam, c->stream));
     }
     CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemsetAsync(c->xord, 1, 3 * c->lay.M, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     c->have_prev = Yprev ? 1 : 0;
+    c->ylev = Yprev ? 1 : 0;
     c->hist = 0;
     c->thist = 0;
     c->warm_corr_ok = 0;
@@ -555,8 +562,10 @@ fil_status fil_init_straight(fil_ctx *c, const double *base, const double *t, co
     CK(cudaMemsetAsync(c->Yprev, 0, sizeof(double) * 3 * S, c->stream));
     CK(cudaMemsetAsync(c->uprev, 0, sizeof(double) * 3 * S, c->stream));
     if (c->lay.nlam > 0) CK(cudaMemsetAsync(c->lam, 0, sizeof(double) * 3 * c->lay.nlam, c->stream));
+    CK(cudaMemsetAsync(c->xord, 1, 3 * M, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->have_prev = 0;
+    c->ylev = 0;
     c->hist = 0;
     c->warm_corr_ok = 0;
     c->in_step = 0;
@@ -933,6 +942,7 @@ fil_status fil_broyden_commit(fil_ctx *c) {
     c->j0_last_iters = c->iters_step;
     c->warm_corr_ok = 1;
     c->have_prev = 1;
+    c->ylev = c->ylev < 2 ? c->ylev + 1 : 2;
     c->hist += 1;
     c->steps += 1;
     c->in_step = 0;
@@ -973,6 +983,21 @@ fil_status fil_j0_stats(const fil_ctx *c, int64_t *builds, int64_t *reuses) {
     if (!c) return FIL_EINVAL;
     if (builds) *builds = c->j0_builds;
     if (reuses) *reuses = c->j0_reuses;
+    return FIL_OK;
+}
+
+fil_status fil_set_extrapolation(fil_ctx *c, int32_t order) {
+    if (!c) return FIL_EINVAL;
+    if (order != FIL_EXTRAP_LINEAR && order != FIL_EXTRAP_QUADRATIC && order != FIL_EXTRAP_ADAPTIVE)
+        return set_err(c, FIL_EINVAL, "fil_set_extrapolation: order must be 1, 2 or 3");
+    if (c->in_step) return set_err(c, FIL_ESTATE, "fil_set_extrapolation: a step is in progress");
+    c->extrap_order = order;
+    return FIL_OK;
+}
+
+fil_status fil_extrapolation(const fil_ctx *c, int32_t *order) {
+    if (!c || !order) return FIL_EINVAL;
+    *order = c->extrap_order;
     return FIL_OK;
 }
 

@@ -66,10 +66,15 @@ struct fil_ctx {
     std::string err;
 
     // time-integration state (uprev2, lamprev: u and Lambda one step further
-    // back, used by the initial guess once hist >= 2)
+    // back, used by the initial guess once hist >= 2; Yprev2, uprev3, lamprev2
+    // one step further still, used by the quadratic initial guess)
     double *Y, *Yprev, *q, *uprev, *lam, *uprev2, *lamprev;
+    double *Yprev2, *uprev3, *lamprev2;
     int have_prev;
     int hist;              // steps committed since the last set_state / init
+    int ylev;              // past Y levels held (Yprev, Yprev2): 0..2
+    int extrap_order = 1;  // FIL_EXTRAP_LINEAR / _QUADRATIC / _ADAPTIVE
+    int8_t *xord;          // adaptive order per filament and block (Y_1, u, Lambda): 3M
     int64_t steps;
 
     // external loads

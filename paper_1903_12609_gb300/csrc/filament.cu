@@ -225,40 +225,113 @@ __global__ void init_straight_kernel(Layout lay, const double *__restrict__ base
     }
 }
 
-// X_0 of a step: each unknown extrapolated linearly from the two previous
-// steps (x_0 = 2 x^j - x^{j-1}) where both exist -- Y_1 from the BDF2 history,
-// u and Lambda once two steps were committed (lin) -- else the last value
-// (u = 0 and Y_1 = Y_1^j on the first step). One thread per segment.
+// Value at the next step of the polynomial through the last ord + 1 committed
+// values x^j (x0), x^{j-1} (x1), x^{j-2} (x2): ord 0 keeps x^j, ord 1 gives
+// 2 x^j - x^{j-1}, ord 2 gives 3 x^j - 3 x^{j-1} + x^{j-2}.
+__device__ __forceinline__ V3 extrapolated(V3 x0, const double *x1, const double *x2, int ord) {
+    if (ord == 1) return 2.0 * x0 - ld3(x1);
+    if (ord == 2) return 3.0 * (x0 - ld3(x1)) + ld3(x2);
+    return x0;
+}
+
+// X_0 of a step: each unknown extrapolated from the committed steps, Y_1 with
+// order y_ord from its BDF2 history (Y^j, Y^{j-1}, Y^{j-2}), u and Lambda with
+// order u_ord from (u^j, u^{j-1}, u^{j-2}) and (Lambda^j, ...); u_ord < 0
+// before the first step: u = 0, Lambda = Lambda^j. With xord (the adaptive
+// choice) each filament's blocks Y_1, u, Lambda use at most xord[3i + 0..2].
+// One thread per segment.
 __global__ void extrapolate_kernel(Layout lay, const double *__restrict__ Y,
                                    const double *__restrict__ Yprev,
+                                   const double *__restrict__ Yprev2,
                                    const double *__restrict__ uprev,
-                                   const double *__restrict__ lam,
                                    const double *__restrict__ uprev2,
-                                   const double *__restrict__ lamprev, int have_prev, int lin,
-                                   double *__restrict__ X0) {
+                                   const double *__restrict__ uprev3,
+                                   const double *__restrict__ lam,
+                                   const double *__restrict__ lamprev,
+                                   const double *__restrict__ lamprev2, int y_ord, int u_ord,
+                                   const int8_t *__restrict__ xord, double *__restrict__ X0) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= lay.S) return;
     const int i = lay.fil_of[g];
     const int s0 = lay.off[i];
     const int N = lay.off[i + 1] - s0;
     const int n = (int)(g - s0);
+    int l_ord = u_ord > 0 ? u_ord : 0;
+    if (xord) {
+        y_ord = min(y_ord, (int)xord[3 * i]);
+        if (u_ord > 0) u_ord = min(u_ord, (int)xord[3 * i + 1]);
+        l_ord = min(l_ord, (int)xord[3 * i + 2]);
+    }
     double *Xf = X0 + 6 * (int64_t)s0;
-    if (n == 0) {
-        V3 y1 = ld3(Y + 3 * g);
-        if (have_prev) y1 = 2.0 * y1 - ld3(Yprev + 3 * g);
-        st3(Xf, y1);
-    }
+    if (n == 0) st3(Xf, extrapolated(ld3(Y + 3 * g), Yprev + 3 * g, Yprev2 + 3 * g, y_ord));
     V3 u0 = v3(0, 0, 0);
-    if (have_prev) {
-        u0 = ld3(uprev + 3 * g);
-        if (lin) u0 = 2.0 * u0 - ld3(uprev2 + 3 * g);
-    }
+    if (u_ord >= 0) u0 = extrapolated(ld3(uprev + 3 * g), uprev2 + 3 * g, uprev3 + 3 * g, u_ord);
     st3(Xf + 3 + 3 * n, u0);
     if (n <= N - 2) {
         const int64_t li = 3 * (int64_t)(s0 - i + n);
-        V3 l0 = ld3(lam + li);
-        if (lin) l0 = 2.0 * l0 - ld3(lamprev + li);
-        st3(Xf + 3 + 3 * N + 3 * n, l0);
+        st3(Xf + 3 + 3 * N + 3 * n, extrapolated(ld3(lam + li), lamprev + li, lamprev2 + li, l_ord));
+    }
+}
+
+// Squared differences between a solution x* and the linear and quadratic
+// extrapolations from x^j, x^{j-1}, x^{j-2}, accumulated into e[0], e[1].
+__device__ __forceinline__ void extrap_errors(const double *xs, const double *x0, const double *x1,
+                                              const double *x2, double e[2]) {
+    const V3 s = ld3(xs), a = ld3(x0);
+    const V3 dl = s - extrapolated(a, x1, x2, 1);
+    const V3 dq = s - extrapolated(a, x1, x2, 2);
+    e[0] += dot(dl, dl);
+    e[1] += dot(dq, dq);
+}
+
+// Adaptive order (before the history shift of a commit): for each filament
+// and block (Y_1, u, Lambda) whose last three values exist (y_ok, u_ok), the
+// order whose extrapolation came closer to the committed solution X (sums of
+// squared differences; the quadratic one only if strictly closer); blocks
+// that cannot be compared get the linear order. One warp per filament, lane
+// sums combined by a fixed shuffle tree.
+__global__ void extrap_select_kernel(Layout lay, const double *__restrict__ X,
+                                     const double *__restrict__ Y,
+                                     const double *__restrict__ Yprev,
+                                     const double *__restrict__ Yprev2,
+                                     const double *__restrict__ uprev,
+                                     const double *__restrict__ uprev2,
+                                     const double *__restrict__ uprev3,
+                                     const double *__restrict__ lam,
+                                     const double *__restrict__ lamprev,
+                                     const double *__restrict__ lamprev2, int y_ok, int u_ok,
+                                     int8_t *__restrict__ xord) {
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= lay.M) return;
+    const int s0 = lay.off[i];
+    const int N = lay.off[i + 1] - s0;
+    const double *Xf = X + 6 * (int64_t)s0;
+    double eu[2] = {0, 0}, el[2] = {0, 0};
+    if (u_ok) {
+        for (int n = lane; n < N; n += 32) {
+            const int64_t g = s0 + n;
+            extrap_errors(Xf + 3 + 3 * n, uprev + 3 * g, uprev2 + 3 * g, uprev3 + 3 * g, eu);
+            if (n <= N - 2) {
+                const int64_t li = 3 * (int64_t)(s0 - i + n);
+                extrap_errors(Xf + 3 + 3 * N + 3 * n, lam + li, lamprev + li, lamprev2 + li, el);
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            eu[0] += __shfl_xor_sync(0xffffffffu, eu[0], d);
+            eu[1] += __shfl_xor_sync(0xffffffffu, eu[1], d);
+            el[0] += __shfl_xor_sync(0xffffffffu, el[0], d);
+            el[1] += __shfl_xor_sync(0xffffffffu, el[1], d);
+        }
+    }
+    if (lane == 0) {
+        double ey[2] = {0, 0};
+        if (y_ok) extrap_errors(Xf, Y + 3 * (int64_t)s0, Yprev + 3 * (int64_t)s0,
+                                Yprev2 + 3 * (int64_t)s0, ey);
+        xord[3 * i] = (y_ok && ey[1] < ey[0]) ? 2 : 1;
+        xord[3 * i + 1] = (u_ok && eu[1] < eu[0]) ? 2 : 1;
+        xord[3 * i + 2] = (u_ok && el[1] < el[0]) ? 2 : 1;
     }
 }
 
@@ -266,9 +339,10 @@ __global__ void extrapolate_kernel(Layout lay, const double *__restrict__ Y,
 __global__ void commit_kernel(Layout lay, const double *__restrict__ X,
                               const double *__restrict__ qc, const double *__restrict__ Yc,
                               double *__restrict__ Y, double *__restrict__ Yprev,
-                              double *__restrict__ q, double *__restrict__ uprev,
-                              double *__restrict__ lam, double *__restrict__ uprev2,
-                              double *__restrict__ lamprev) {
+                              double *__restrict__ Yprev2, double *__restrict__ q,
+                              double *__restrict__ uprev, double *__restrict__ uprev2,
+                              double *__restrict__ uprev3, double *__restrict__ lam,
+                              double *__restrict__ lamprev, double *__restrict__ lamprev2) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= lay.S) return;
     const int i = lay.fil_of[g];
@@ -276,13 +350,16 @@ __global__ void commit_kernel(Layout lay, const double *__restrict__ X,
     const int N = lay.off[i + 1] - s0;
     const int n = (int)(g - s0);
     const double *Xf = X + 6 * (int64_t)s0;
+    st3(Yprev2 + 3 * g, ld3(Yprev + 3 * g));
     st3(Yprev + 3 * g, ld3(Y + 3 * g));
     st3(Y + 3 * g, ld3(Yc + 3 * g));
     st4(q + 4 * g, ld4(qc + 4 * g));
+    st3(uprev3 + 3 * g, ld3(uprev2 + 3 * g));
     st3(uprev2 + 3 * g, ld3(uprev + 3 * g));
     st3(uprev + 3 * g, ld3(Xf + 3 + 3 * n));
     if (n <= N - 2) {
         const int64_t li = 3 * (int64_t)(s0 - i + n);
+        st3(lamprev2 + li, ld3(lamprev + li));
         st3(lamprev + li, ld3(lam + li));
         st3(lam + li, ld3(Xf + 3 + 3 * N + 3 * n));
     }
@@ -328,9 +405,18 @@ cudaError_t init_straight(fil_ctx *c, const double *base, const double *t, const
 }
 
 cudaError_t extrapolate_guess(fil_ctx *c, double *X0) {
+    // order of each unknown's polynomial: as high as the committed history and
+    // the chosen order allow (Y_1 has one level more than u and Lambda: the
+    // BDF2 history holds Y^{j-1} from the first step on); the adaptive choice
+    // lowers it per filament and block
+    const bool adaptive = c->extrap_order == FIL_EXTRAP_ADAPTIVE;
+    const int cap = adaptive ? 2 : c->extrap_order;
+    const int y_ord = c->ylev < cap ? c->ylev : cap;
+    const int u_lev = c->have_prev ? (c->hist >= 3 ? 2 : c->hist >= 2 ? 1 : 0) : -1;
+    const int u_ord = u_lev < cap ? u_lev : cap;
     extrapolate_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(
-        c->lay, c->Y, c->Yprev, c->uprev, c->lam, c->uprev2, c->lamprev, c->have_prev,
-        c->hist >= 2 ? 1 : 0, X0);
+        c->lay, c->Y, c->Yprev, c->Yprev2, c->uprev, c->uprev2, c->uprev3, c->lam, c->lamprev,
+        c->lamprev2, y_ord, u_ord, adaptive ? c->xord : nullptr, X0);
     c->n_launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && c->tether_on) e = tether_guess(c, X0);
@@ -340,8 +426,17 @@ cudaError_t extrapolate_guess(fil_ctx *c, double *X0) {
 cudaError_t commit_state(fil_ctx *c, const double *X) {
     cudaError_t e = unpack_forces(c, X, 0);
     if (e != cudaSuccess) return e;
+    if (c->extrap_order == FIL_EXTRAP_ADAPTIVE) {
+        // the comparison needs the three values before this commit: Y_1 once
+        // two past levels are held, u and Lambda once three steps were committed
+        extrap_select_kernel<<<warp_grid(c->lay.M, 128), 128, 0, c->stream>>>(
+            c->lay, X, c->Y, c->Yprev, c->Yprev2, c->uprev, c->uprev2, c->uprev3, c->lam,
+            c->lamprev, c->lamprev2, c->ylev >= 2 ? 1 : 0, c->hist >= 3 ? 1 : 0, c->xord);
+        c->n_launches += 1;
+    }
     commit_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(
-        c->lay, X, c->qc, c->Yc, c->Y, c->Yprev, c->q, c->uprev, c->lam, c->uprev2, c->lamprev);
+        c->lay, X, c->qc, c->Yc, c->Y, c->Yprev, c->Yprev2, c->q, c->uprev, c->uprev2, c->uprev3,
+        c->lam, c->lamprev, c->lamprev2);
     c->n_launches += 1;
     return cudaGetLastError();
 }

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfil.so")
  FIL_EOVERFLOW) = range(9)
 FIL_FP64, FIL_MIXED, FIL_PAIR32 = 0, 1, 2
 FIL_J0_DRAG, FIL_J0_FILAMENT_RPY = 0, 1
+FIL_EXTRAP_LINEAR, FIL_EXTRAP_QUADRATIC, FIL_EXTRAP_ADAPTIVE = 1, 2, 3
 STATUS_NAMES = {0: "FIL_OK", 1: "FIL_EINVAL", 2: "FIL_ENOMEM", 3: "FIL_ECUDA", 4: "FIL_ENOCONV",
                 5: "FIL_ENAN", 6: "FIL_ESTALL", 7: "FIL_ESTATE", 8: "FIL_EOVERFLOW"}
 
@@ -36,7 +37,8 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_warm_stats", "fil_create_ensemble", "fil_sys_stats", "fil_pair_count",
             "fil_set_graph", "fil_autotune", "fil_set_steric", "fil_set_tether",
             "fil_get_tether", "fil_fma_peak", "fil_set_j0_reuse", "fil_j0_stats",
-            "fil_set_pair_schedule", "fil_pair_schedule"]
+            "fil_set_pair_schedule", "fil_pair_schedule", "fil_set_extrapolation",
+            "fil_extrapolation"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_SEG = 800, 256, 192, 32
 MLP_NPARAM = 256 * 800 + 256 + 2 * (256 * 256 + 256) + 192 * 256 + 192
 FIL_WARM_BEST_OF_TWO, FIL_WARM_PREDICTION_FIRST = 0, 1
@@ -93,6 +95,8 @@ def load_library(path=LIB_PATH):
         "fil_set_pair_schedule": [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
         "fil_pair_schedule": [P, I32, I32, I32],
         "fil_j0_stats": [P, I64, I64],
+        "fil_set_extrapolation": [P, ctypes.c_int32],
+        "fil_extrapolation": [P, I32],
         "fil_mlp_create": [ctypes.c_int64, P, ctypes.POINTER(P)],
         "fil_mlp_destroy": [P],
         "fil_mlp_set_params": [P, P],
@@ -312,6 +316,16 @@ def fil_j0_stats(ctx):
     b, r = ctypes.c_int64(), ctypes.c_int64()
     _check(ctx, _lib.fil_j0_stats(ctx, ctypes.byref(b), ctypes.byref(r)))
     return b.value, r.value
+
+
+def fil_set_extrapolation(ctx, order):
+    _check(ctx, _lib.fil_set_extrapolation(ctx, int(order)))
+
+
+def fil_extrapolation(ctx):
+    o = ctypes.c_int32()
+    _check(ctx, _lib.fil_extrapolation(ctx, ctypes.byref(o)))
+    return o.value
 
 
 def fil_counters(ctx):

@@ -4,7 +4,9 @@ the library's tensor-core kernels, and loading a trained network into a
 solver context.
 
 The network corrects the extrapolated initial guess X_0 of each 32-segment
-filament (in the filament's own frame); inside fil_step the plain solve keeps
+filament (in the filament's own frame), for the extrapolation order it was
+trained with (fil_set_extrapolation; stored with the weights, see
+trained_order); inside fil_step the plain solve keeps
 the last word (the start with the smaller residual is kept and a failed start
 from the prediction is restarted from the extrapolation), so every step
 converges to the same tolerance with or without it.
@@ -30,25 +32,34 @@ DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "warmstart_n32.npz")
 SEG, NIN, NOUT = fil.MLP_SEG, fil.MLP_IN, fil.MLP_OUT
 
 
-def make_context(n_fil, seed=0, stream=None, **over):
+def make_context(n_fil, seed=0, stream=None, order=1, **over):
     """A solver context on the suspension workload (mixed precision,
-    filament-RPY J0), initialised with straight filaments."""
+    filament-RPY J0, extrapolation of the given order), initialised with
+    straight filaments."""
     wl, base, t, mu, Fext, follower = suspension(n_fil, SEG, seed=seed)
     params = dict(a=wl.a, eta=wl.eta, dL=wl.dL, KB=wl.KB, KT=wl.KT, dt=wl.dt, tol=wl.tol,
                   max_iter=wl.max_iter, precision=fil.FIL_MIXED,
                   j0_model=fil.FIL_J0_FILAMENT_RPY)
     params.update(over)
     m = fil.Filaments(wl.seg_per_fil, stream=stream, **params)
+    m.set_extrapolation(order)
     m.init_straight(base, t, mu, None)
     m.set_external(Fext, None, follower)
     return m, wl
 
 
-def record(torch, n_fil, n_steps, seed=0, skip=10):
+def trained_order(path=DEFAULT_WEIGHTS):
+    """The extrapolation order whose guess the stored network corrects (1 for
+    weights saved before the order was recorded)."""
+    z = np.load(path)
+    return int(json.loads(str(z["meta"])).get("extrapolation_order", 1))
+
+
+def record(torch, n_fil, n_steps, seed=0, skip=10, order=1):
     """Run the plain solver and keep, for every step after the first `skip`,
     the network inputs before the step and the targets after it (device
     tensors [n_steps * n_fil, 416] and [n_steps * n_fil, 192])."""
-    m, _ = make_context(n_fil, seed)
+    m, _ = make_context(n_fil, seed, order=order)
     feat = torch.empty((n_steps, n_fil, NIN), dtype=torch.float32, device="cuda")
     targ = torch.empty((n_steps, n_fil, NOUT), dtype=torch.float32, device="cuda")
     iters = []
@@ -182,12 +193,12 @@ def load(path=DEFAULT_WEIGHTS, max_batch=1024, stream=None):
     return net
 
 
-def evaluate(torch, net, n_fil, n_steps, seed=1, warmup=5):
+def evaluate(torch, net, n_fil, n_steps, seed=1, warmup=5, order=1):
     """Per arm (the plain solve, and the network attached in each mode), all
     continuing from the same state after `warmup` plain steps: Broyden
     iterations per step, the mean of log10 ||f(X_0)||_inf (how close the start
     is), timesteps/s, and how often each candidate was taken."""
-    m, wl = make_context(n_fil, seed)
+    m, wl = make_context(n_fil, seed, order=order)
     tol = wl.tol * wl.a
     for _ in range(warmup):
         m.step()
@@ -241,12 +252,14 @@ def main():
     ap.add_argument("--seed", type=int, default=100,
                     help="workload seed of the training trajectory (the bench uses seed 0)")
     ap.add_argument("--eval-steps", type=int, default=50)
+    ap.add_argument("--extrapolation", type=int, default=1, choices=[1, 2],
+                    help="order of the extrapolated guess the network learns to correct")
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     args = ap.parse_args()
     log = lambda s: print(s, flush=True)   # noqa: E731
     t0 = time.time()
-    parts = [record(torch, args.n_fil, args.steps, seed=args.seed + 1000 * k)
-             for k in range(args.trajectories)]
+    parts = [record(torch, args.n_fil, args.steps, seed=args.seed + 1000 * k,
+                    order=args.extrapolation) for k in range(args.trajectories)]
     feat = torch.cat([f for f, _, _ in parts]) if len(parts) > 1 else parts[0][0]
     targ = torch.cat([t for _, t, _ in parts]) if len(parts) > 1 else parts[0][1]
     iters = [i for _, _, its in parts for i in its]
@@ -263,10 +276,11 @@ def main():
     del feat, targ
     meta = {"n_fil": args.n_fil, "steps": args.steps, "trajectories": args.trajectories,
             "epochs": args.epochs, "batch": args.batch, "lr": args.lr, "seed": args.seed,
-            "history": hist}
+            "extrapolation_order": args.extrapolation, "history": hist}
     save(args.out, params, norm, meta)
     net = load(args.out, max_batch=max(1024, args.n_fil))
-    ev = evaluate(torch, net, args.n_fil, args.eval_steps, seed=args.seed + 1)
+    ev = evaluate(torch, net, args.n_fil, args.eval_steps, seed=args.seed + 1,
+                  order=args.extrapolation)
     fil.fil_mlp_destroy(net)
     meta["evaluation"] = ev
     save(args.out, params, norm, meta)

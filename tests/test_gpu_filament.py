@@ -433,3 +433,95 @@ def test_j0_reuse_off_and_argument_checks(fil):
         with pytest.raises(fil.FilError) as e:
             m.set_j0_reuse(3)
         assert e.value.status == fil.FIL_ESTATE
+
+
+@pytest.mark.parametrize("history", [False, True])
+@pytest.mark.parametrize("model", J0_MODELS)
+def test_quadratic_extrapolation_matches_oracle(fil, history, model):
+    """fil_set_extrapolation(2): X_0 of each of 7 steps equals the oracle's
+    order-2 guess (the oracle stepping alongside at the same tolerance; X_0
+    inherits the two trajectories' difference, within a few tolerances, times
+    the extrapolation weights 3 + 3 + 1), and it is not the linear guess once
+    three committed values exist. With Y^{j-1} given to fil_set_state, Y_1 is
+    quadratic from the second step on; u and Lambda from the fourth."""
+    lay, p, st, ext, _ = _system([20, 7, 33], 73, history=history, tol=1e-12, dt=0.2)
+    with _gpu(fil, lay, p, st, ext, j0=model[0]) as m:
+        assert m.extrapolation() == 1
+        m.set_extrapolation(2)
+        assert m.extrapolation() == 2
+        X0 = np.zeros(6 * lay.S)
+        for k in range(7):
+            br = fo.begin_step(lay, p, st, ext, j0_model=model[1], order=2)
+            m.broyden_begin()
+            m.get_iterate(X0, None)
+            sc = max(1.0, np.abs(br.X).max())
+            np.testing.assert_allclose(X0, br.X, rtol=0, atol=1e-9 * sc)
+            if k >= 3:
+                lin = fo.initial_guess(lay, st, order=1)
+                assert np.abs(lin - br.X).max() > 1e3 * 1e-9 * sc
+            while True:
+                conv, _ = m.broyden_step()
+                if conv:
+                    break
+            m.broyden_commit()
+            while not br.converged():
+                br.iterate()
+            st = fo.commit_step(lay, p, st, br.X)
+
+
+def test_extrapolation_argument_checks(fil):
+    lay, p, st, ext, _ = _system([16] * 2, 74, tol=1e-10)
+    with _gpu(fil, lay, p, st, ext) as m:
+        for bad in (0, 4, -1):
+            with pytest.raises(fil.FilError) as e:
+                m.set_extrapolation(bad)
+            assert e.value.status == fil.FIL_EINVAL
+        m.broyden_begin()
+        with pytest.raises(fil.FilError) as e:
+            m.set_extrapolation(2)
+        assert e.value.status == fil.FIL_ESTATE
+        assert m.extrapolation() == 1
+
+
+@pytest.mark.parametrize("model", J0_MODELS)
+def test_adaptive_extrapolation_matches_oracle(fil, model):
+    """FIL_EXTRAP_ADAPTIVE: X_0 of each of 9 steps equals the oracle's (FP64,
+    the oracle stepping alongside). The tolerance is loose (1e-6) so that the
+    converged history carries noise and the linear guess wins some blocks (a
+    filament sedimenting fast, one slowly, two unforced): both orders occur.
+    With the same iterations on both sides the FP64 trajectories agree to
+    rounding, far inside the gap between the two orders' guesses, so a wrong
+    choice of order shows."""
+    segs = [12, 7, 16, 9]
+    rng = np.random.default_rng(75)
+    lay = fo.Layout(segs)
+    p = fo.Params(a=1.0, eta=1.0, dL=2.2, KB=2.0, KT=1.5, dt=0.2, tol=1e-6, max_iter=60)
+    base = np.array([[0, 0, 0], [40.0, 0, 0], [0, 40.0, 0], [40, 40, 0]])
+    t, mu = random_frames(rng, len(segs))
+    st = fo.initial_state(lay, p, base, t, mu, 0.05 * rng.standard_normal((lay.S, 3)))
+    F = np.zeros((lay.S, 3))
+    F[lay.off_seg[0]:lay.off_seg[1], 2] = -2.0
+    F[lay.off_seg[2]:lay.off_seg[3], 2] = -0.5
+    ext = fo.External(Fext=F, Text=np.zeros((lay.S, 3)), follower=np.array([0.0, 0.0, 0.0, 0.3]))
+    seen = set()
+    with _gpu(fil, lay, p, st, ext, j0=model[0]) as m:
+        m.set_extrapolation(fil.FIL_EXTRAP_ADAPTIVE)
+        assert m.extrapolation() == fil.FIL_EXTRAP_ADAPTIVE
+        X0 = np.zeros(6 * lay.S)
+        for k in range(9):
+            br = fo.begin_step(lay, p, st, ext, j0_model=model[1], order=fo.ADAPTIVE)
+            conv = m.broyden_begin() <= p.tol * p.a
+            m.get_iterate(X0, None)
+            sc = max(1.0, np.abs(br.X).max())
+            np.testing.assert_allclose(X0, br.X, rtol=0, atol=1e-9 * sc)
+            n = 0
+            while not conv:
+                conv, _ = m.broyden_step()
+                n += 1
+            m.broyden_commit()
+            while not br.converged():
+                br.iterate()
+            assert n == br.k, (k, n, br.k)
+            st = fo.commit_step(lay, p, st, br.X, order=fo.ADAPTIVE)
+            seen.update(np.unique(st.xord).tolist())
+    assert seen == {1, 2}, seen

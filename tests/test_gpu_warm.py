@@ -165,12 +165,13 @@ def test_trained_network_starts_closer(fil):
     suspension workload (1000 filaments x 32, a seed it was not trained on),
     30 steps continuing from the same state as the plain solve. The start it
     gives has a smaller residual on average (mean log10 ||f(X_0)||_inf at least
-    0.3 lower), the prediction is taken in most steps, and the Broyden
+    0.3 lower) than the extrapolation it was trained to correct (the order stored
+    with the weights), the prediction is taken in most steps, and the Broyden
     iterations per step fall by at least 5%; every step converges to the same
     tolerance (the plain solve judges each step)."""
     from paper_1903_12609_gb300 import warmstart
     net = warmstart.load(WEIGHTS, max_batch=1024)
-    ev = warmstart.evaluate(torch, net, 1000, 30, seed=11)
+    ev = warmstart.evaluate(torch, net, 1000, 30, seed=11, order=warmstart.trained_order(WEIGHTS))
     fil.fil_mlp_destroy(net)
     plain, best, first = ev["plain"], ev["best_of_two"], ev["prediction_first"]
     assert best["log10_f0"] < plain["log10_f0"] - 0.3, ev

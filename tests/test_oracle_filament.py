@@ -372,3 +372,230 @@ def test_bdf2_converges_at_second_order_in_time():
     err = [np.linalg.norm(_settling_square(8, n, 0.5) - ref, axis=1).max() for n in (10, 20, 40)]
     assert 3.6 < err[0] / err[1] < 4.4, err
     assert 3.6 < err[1] / err[2] < 4.4, err
+
+
+# --------------------------------------------------------------------------
+# Initial guess (Sec. 3.3: guesses extrapolated from past steps; the order is
+# a reading, linear by default, quadratic as an option)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+def test_extrapolation_is_exact_on_polynomials_of_its_degree(order):
+    """Samples p(0), p(-1), p(-2), p(-3) of a polynomial of degree order are
+    continued exactly to p(1); one degree higher, the error is the leading
+    finite difference: for p = c t^(order+1), p(1) - x_0 = (order+1)! c (the
+    (order+1)-th backward difference of t^(order+1) at unit spacing)."""
+    rng = np.random.default_rng(30)
+    coef = rng.standard_normal((order + 2, 4))           # a vector of 4 unknowns
+
+    def p(t, deg):
+        return sum(coef[k] * t ** k for k in range(deg + 1))
+
+    hist = [p(-float(j), order) for j in range(4)]
+    np.testing.assert_allclose(fo.extrapolate(hist, order), p(1.0, order), rtol=0, atol=1e-13)
+    hist = [coef[order + 1] * (-float(j)) ** (order + 1) for j in range(4)]
+    err = coef[order + 1] * 1.0 - fo.extrapolate(hist, order)
+    np.testing.assert_allclose(err, math.factorial(order + 1) * coef[order + 1], rtol=1e-13)
+
+
+def test_extrapolation_error_falls_at_the_order_plus_one():
+    """On a smooth signal the extrapolation error falls as h^(order+1)."""
+    for order in (1, 2):
+        errs = []
+        for h in (0.02, 0.01):
+            hist = [np.array([math.sin(1.0 - j * h)]) for j in range(3)]
+            errs.append(abs(fo.extrapolate(hist, order)[0] - math.sin(1.0 + h)))
+        assert abs(math.log2(errs[0] / errs[1]) - (order + 1)) < 0.1, (order, errs)
+
+
+def test_extrapolation_drops_to_the_values_that_exist():
+    x = [np.array([3.0]), np.array([1.0]), None, np.array([100.0])]
+    np.testing.assert_allclose(fo.extrapolate(x, 2), [5.0])           # linear: 2*3 - 1
+    np.testing.assert_allclose(fo.extrapolate(x[:1], 2), [3.0])
+    np.testing.assert_allclose(fo.extrapolate(x, 0), [3.0])
+
+
+def test_quadratic_initial_guess_wires_each_history_level():
+    """A state whose Y, u and Lambda histories are quadratic in the step index:
+    the order-2 guess is their value at the next step in every slot; with u^{j-2}
+    and Lambda^{j-2} missing those fall back to the linear guess while Y_1 stays
+    quadratic; order 1 is the linear guess."""
+    rng = np.random.default_rng(31)
+    lay = fo.Layout([5, 3])
+    c = [rng.standard_normal((lay.S, 3)) for _ in range(3)]
+    d = [rng.standard_normal((lay.S, 3)) for _ in range(3)]
+    e = [rng.standard_normal((lay.n_lam, 3)) for _ in range(3)]
+
+    def quad(k, t):
+        return k[0] + k[1] * t + k[2] * t * t
+
+    st = fo.State(Y=quad(c, 0.0), q=np.tile([1.0, 0, 0, 0], (lay.S, 1)), Yprev=quad(c, -1.0),
+                  Yprev2=quad(c, -2.0), u=quad(d, 0.0), u_prev=quad(d, -1.0),
+                  u_prev2=quad(d, -2.0), lam=quad(e, 0.0), lam_prev=quad(e, -1.0),
+                  lam_prev2=quad(e, -2.0), steps=3)
+    first = [lay.off_seg[i] for i in range(lay.M)]
+    want = lay.join_X(quad(c, 1.0)[first], quad(d, 1.0), quad(e, 1.0))
+    np.testing.assert_allclose(fo.initial_guess(lay, st, order=2), want, rtol=0, atol=1e-13)
+    lin = lay.join_X(2 * quad(c, 0.0)[first] - quad(c, -1.0)[first],
+                     2 * quad(d, 0.0) - quad(d, -1.0), 2 * quad(e, 0.0) - quad(e, -1.0))
+    np.testing.assert_allclose(fo.initial_guess(lay, st, order=1), lin, rtol=0, atol=1e-13)
+    st.u_prev2 = st.lam_prev2 = None
+    mixed = lay.join_X(quad(c, 1.0)[first], 2 * quad(d, 0.0) - quad(d, -1.0),
+                       2 * quad(e, 0.0) - quad(e, -1.0))
+    np.testing.assert_allclose(fo.initial_guess(lay, st, order=2), mixed, rtol=0, atol=1e-13)
+
+
+def test_commit_fills_the_history_levels_in_turn():
+    """After k committed steps from a fresh state: Y^{j-2} from the second
+    commit on, u^{j-1}, Lambda^{j-1} from the second, u^{j-2}, Lambda^{j-2}
+    from the third, each equal to the value committed that many steps back."""
+    rng = np.random.default_rng(32)
+    lay = fo.Layout([6])
+    p = _params(KB=2.0, KT=2.0, dt=0.1, tol=1e-10)
+    st = _random_filament_state(rng, lay, p, twist=0.1)
+    ext = fo.External(Fext=np.tile([0, 0, -1.0], (lay.S, 1)))
+    seen = [st]
+    for k in range(1, 5):
+        st, _ = fo.step(lay, p, st, ext, order=2)
+        seen.append(st)
+        assert (st.Yprev2 is not None) == (k >= 2)
+        assert (st.u_prev is not None) == (k >= 2)
+        assert (st.u_prev2 is not None) == (k >= 3)
+        if k >= 2:
+            np.testing.assert_array_equal(st.Yprev2, seen[k - 2].Y)
+            np.testing.assert_array_equal(st.u_prev, seen[k - 1].u)
+            np.testing.assert_array_equal(st.lam_prev, seen[k - 1].lam)
+        if k >= 3:
+            np.testing.assert_array_equal(st.u_prev2, seen[k - 2].u)
+            np.testing.assert_array_equal(st.lam_prev2, seen[k - 2].lam)
+
+
+def test_quadratic_guess_keeps_the_solution_and_saves_iterations():
+    """The converged step does not depend on X_0 beyond the tolerance: 12 steps
+    of a settling, bending pair of filaments with order 1 and order 2 end at
+    the same positions to within a few tolerances, and from the fourth step on
+    the quadratic guess starts closer (smaller ||f(X_0)||) on every step."""
+    rng = np.random.default_rng(33)
+    lay = fo.Layout([8, 8])
+    p = _params(KB=2.0, KT=2.0, dt=0.1, tol=1e-11)
+    st0 = _random_filament_state(rng, lay, p, twist=0.05)
+    st0.Y = st0.Y + np.repeat(np.array([[0.0, 0, 0], [12.0, 0, 0]]), 8, axis=0)
+    ext = fo.External(Fext=np.tile([0, 0, -1.0], (lay.S, 1)), follower=np.array([0.2, 0.0]))
+    sts = {1: st0, 2: st0}
+    for k in range(12):
+        f0 = {}
+        for order in (1, 2):
+            br = fo.begin_step(lay, p, sts[order], ext, order=order)
+            f0[order] = np.abs(br.f).max()
+            while not br.converged():
+                br.iterate()
+            sts[order] = fo.commit_step(lay, p, sts[order], br.X)
+        if k >= 3:
+            assert f0[2] < f0[1], (k, f0)
+    np.testing.assert_allclose(sts[2].Y, sts[1].Y, rtol=0, atol=1e-8)
+
+
+def _two_filament_history():
+    """Two filaments (5 and 3 segments) whose Y_1, u and Lambda histories are
+    built block by block: quadratic in the step index (x* its continuation),
+    linear with alternating noise on the past values (x* the clean
+    continuation), or exactly linear (x* its continuation)."""
+    rng = np.random.default_rng(34)
+    lay = fo.Layout([5, 3])
+    first = [lay.off_seg[i] for i in range(lay.M)]
+
+    def series(shape, kind):
+        # small integer coefficients and binary-fraction noise: every
+        # extrapolation below is exact in floating point, so ties are ties
+        c = rng.integers(-4, 5, size=(3,) + shape).astype(np.float64)
+        vals = [c[0] + c[1] * t + (c[2] * t * t if kind == "quad" else 0.0)
+                for t in (1.0, 0.0, -1.0, -2.0)]          # x*, x^j, x^{j-1}, x^{j-2}
+        if kind == "noisy":
+            noise = 0.5 * np.abs(c[2]) + 0.25
+            vals[1] = vals[1] + noise
+            vals[2] = vals[2] - noise
+            vals[3] = vals[3] + noise
+        return vals
+
+    return lay, first, series
+
+
+def test_adaptive_orders_pick_the_closer_extrapolation():
+    """adaptive_orders: 2 where the block's past is quadratic (the quadratic
+    guess is exact), 1 where noise on the past values makes the quadratic
+    weights (3, -3, 1) miss by more than the linear ones (2, -1), 1 on a tie
+    (an exactly linear past, where both are exact), 1 where three past values
+    do not exist; per filament and per block."""
+    lay, first, series = _two_filament_history()
+    kinds = [("quad", "noisy", "lin"), ("noisy", "quad", "quad")]
+    Y = np.zeros((4, lay.S, 3))
+    U = np.zeros((4, lay.S, 3))
+    L = np.zeros((4, lay.n_lam, 3))
+    for i, (ky, ku, kl) in enumerate(kinds):
+        s, e = lay.off_seg[i], lay.off_seg[i + 1]
+        vy = series((3,), ky)
+        for k in range(4):
+            Y[k, s:e] = vy[k]                       # only Y_1 matters; rows of one filament
+        vu = series((e - s, 3), ku)
+        vl = series((e - s - 1, 3), kl)
+        for k in range(4):
+            U[k, s:e] = vu[k]
+            L[k, lay.off_lam[i]:lay.off_lam[i + 1]] = vl[k]
+    st = fo.State(Y=Y[1], q=np.tile([1.0, 0, 0, 0], (lay.S, 1)), Yprev=Y[2], Yprev2=Y[3],
+                  u=U[1], u_prev=U[2], u_prev2=U[3], lam=L[1], lam_prev=L[2],
+                  lam_prev2=L[3], steps=3)
+    X = lay.join_X(Y[0][first], U[0], L[0])
+    np.testing.assert_array_equal(fo.adaptive_orders(lay, st, X), [[2, 1, 1], [1, 2, 2]])
+    st.u_prev2 = st.lam_prev2 = None
+    np.testing.assert_array_equal(fo.adaptive_orders(lay, st, X), [[2, 1, 1], [1, 1, 1]])
+    st.Yprev2 = None
+    np.testing.assert_array_equal(fo.adaptive_orders(lay, st, X), np.ones((2, 3)))
+
+
+def test_adaptive_guess_uses_each_blocks_order():
+    """initial_guess(order=ADAPTIVE) extrapolates each filament's blocks with
+    the orders in state.xord (quadratic histories: order 2 is their
+    continuation, order 1 the linear guess), and with no xord linearly."""
+    lay, first, series = _two_filament_history()
+    vy = series((lay.S, 3), "quad")
+    vu = series((lay.S, 3), "quad")
+    vl = series((lay.n_lam, 3), "quad")
+    st = fo.State(Y=vy[1], q=np.tile([1.0, 0, 0, 0], (lay.S, 1)), Yprev=vy[2], Yprev2=vy[3],
+                  u=vu[1], u_prev=vu[2], u_prev2=vu[3], lam=vl[1], lam_prev=vl[2],
+                  lam_prev2=vl[3], steps=3, xord=np.array([[2, 1, 2], [1, 2, 1]]))
+    X0 = fo.initial_guess(lay, st, order=fo.ADAPTIVE)
+    Y1, u, lam = lay.split_X(X0)
+    lin = [2 * v[1] - v[2] for v in (vy, vu, vl)]
+    for i in range(lay.M):
+        want = [vy[0][first[i]] if st.xord[i, 0] == 2 else lin[0][first[i]]]
+        np.testing.assert_allclose(Y1[i], want[0], rtol=0, atol=1e-13)
+        rows = slice(lay.off_seg[i], lay.off_seg[i + 1])
+        ref = vu[0] if st.xord[i, 1] == 2 else lin[1]
+        np.testing.assert_allclose(u[rows], ref[rows], rtol=0, atol=1e-13)
+        rows = slice(lay.off_lam[i], lay.off_lam[i + 1])
+        ref = vl[0] if st.xord[i, 2] == 2 else lin[2]
+        np.testing.assert_allclose(lam[rows], ref[rows], rtol=0, atol=1e-13)
+    st.xord = None
+    np.testing.assert_allclose(fo.initial_guess(lay, st, order=fo.ADAPTIVE),
+                               fo.initial_guess(lay, st, order=1), rtol=0, atol=0)
+
+
+def test_adaptive_guess_keeps_the_solution():
+    """Adaptive and linear runs of the same 12 steps end at the same
+    positions to within a few tolerances, and the adaptive run takes no more
+    Broyden iterations in all."""
+    rng = np.random.default_rng(35)
+    lay = fo.Layout([8, 8])
+    p = _params(KB=2.0, KT=2.0, dt=0.1, tol=1e-9)
+    st0 = _random_filament_state(rng, lay, p, twist=0.05)
+    st0.Y = st0.Y + np.repeat(np.array([[0.0, 0, 0], [12.0, 0, 0]]), 8, axis=0)
+    ext = fo.External(Fext=np.tile([0, 0, -1.0], (lay.S, 1)), follower=np.array([0.2, 0.0]))
+    end, its = {}, {}
+    for order in (1, fo.ADAPTIVE):
+        st, n = st0, 0
+        for _ in range(12):
+            st, k = fo.step(lay, p, st, ext, order=order)
+            n += k
+        end[order], its[order] = st.Y, n
+    np.testing.assert_allclose(end[fo.ADAPTIVE], end[1], rtol=0, atol=1e-7)
+    assert its[fo.ADAPTIVE] <= its[1], its
