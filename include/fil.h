@@ -88,8 +88,8 @@ typedef enum {
     FIL_EXTRAP_LINEAR = 1,     /* x_0 = 2 x^j - x^{j-1}                              */
     FIL_EXTRAP_QUADRATIC = 2,  /* x_0 = 3 x^j - 3 x^{j-1} + x^{j-2}                  */
     FIL_EXTRAP_ADAPTIVE = 3    /* per filament and per block of unknowns (Y_1, u,
-                                  Lambda): the one of the two that predicted the
-                                  last committed step better                         */
+                                  Lambda): the linear guess plus a fitted fraction
+                                  (0..1) of the quadratic correction             */
 } fil_extrapolation_order;
 
 typedef struct {
@@ -329,23 +329,26 @@ fil_status fil_j0_stats(const fil_ctx *c, int64_t *builds, int64_t *reuses);
  * The paper starts Algorithm 2 from guesses extrapolated from the solutions of
  * past timesteps (Sec. 3.3) without stating the form. Each unknown takes the
  * value at the next step of the polynomial through its last committed values:
- * FIL_EXTRAP_LINEAR (the default) through two, FIL_EXTRAP_QUADRATIC through
- * three. FIL_EXTRAP_ADAPTIVE chooses between the two for each filament and
- * each of its blocks of unknowns (Y_1; u_1..u_N; Lambda): when a step is
- * committed, each block's solution is compared with what the linear and the
- * quadratic extrapolation gave for it (sums of squared differences) and the
- * next step uses the order that came closer (linear until both could be
- * compared). The quadratic form has the smaller truncation error but weighs
- * the past solutions by 3, -3, 1 instead of 2, -1, so it carries more of
- * their own error (each is converged only to the tolerance): it wins when the
- * motion over a step is large compared with that, and loses when it is not.
- * With fewer committed values an order drops to what they allow: Y_1 uses
+ * FIL_EXTRAP_LINEAR (the default) through two, x_0 = 2 x^j - x^{j-1};
+ * FIL_EXTRAP_QUADRATIC through three, x_0 = 3 x^j - 3 x^{j-1} + x^{j-2}, which
+ * is the linear guess plus the second difference d = x^j - 2 x^{j-1} + x^{j-2}.
+ * The quadratic form has the smaller truncation error but weighs the past
+ * solutions by 3, -3, 1 instead of 2, -1, so it carries more of their own
+ * error (each is converged only to the tolerance): it wins when the motion
+ * over a step is large compared with that, and loses when it is not.
+ * FIL_EXTRAP_ADAPTIVE uses x_0 = 2 x^j - x^{j-1} + theta d, with theta fitted
+ * for each filament and each of its blocks of unknowns (Y_1; u_1..u_N; Lambda)
+ * by least squares over the past commits: at each commit, with x* the block's
+ * solution and l, d the linear guess and second difference it was predicted
+ * from, P <- 0.7 P + <x* - l, d> and Q <- 0.7 Q + <d, d>; theta = P / Q clipped
+ * to [0, 1] (0, i.e. linear, until a block has been fitted).
+ * With fewer committed values the order drops to what they allow: Y_1 uses
  * Y^j, Y^{j-1} (held from the first committed step on, or given to
  * fil_set_state) and Y^{j-2}; u and Lambda use the values of committed steps
  * only, u = 0 and Lambda = Lambda^j before the first. Tether multipliers stay
  * linear. The converged solution does not depend on X_0 beyond the tolerance;
  * the iteration count does. A warm-start network (fil_warm_attach) predicts a
- * correction to this extrapolation, so use it with the order it was trained
+ * correction to this extrapolation, so use it with the choice it was trained
  * with. FIL_EINVAL for another value, FIL_ESTATE inside a step. */
 fil_status fil_set_extrapolation(fil_ctx *c, int32_t order);
 

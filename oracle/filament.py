@@ -25,8 +25,9 @@ Readings where the paper is silent (each also listed in the design notes):
   Optionally (order 2) the quadratic through the last three values,
   x_0 = 3 x^j - 3 x^{j-1} + x^{j-2}, for each unknown that has three; or
   (order 3, adaptive) per filament and block of unknowns (Y_1, u, Lambda) the
-  one of the two that came closer (sum of squared differences) to the block's
-  solution at the last commit, linear until both could be compared.
+  linear guess plus theta times the second difference d = x^j - 2 x^{j-1} +
+  x^{j-2}, theta the least-squares coefficient of d in the past solutions'
+  departures from their linear guesses, weighted 0.7^age, clipped to [0, 1].
 * Convergence: ||f||_inf <= tol * a (Sec. 3.3 states the tolerance for the
   infinity norm relative to a). Norms in Algorithm 2 are the 2-norm over the
   whole system.
@@ -251,7 +252,7 @@ class State:
     Yprev2: np.ndarray | None = None
     u_prev2: np.ndarray | None = None
     lam_prev2: np.ndarray | None = None
-    xord: np.ndarray | None = None        # (M, 3) adaptive orders of Y_1, u, Lambda
+    xfit: np.ndarray | None = None        # (M, 3, 2) adaptive fit (P, Q) of Y_1, u, Lambda
     extra: dict = field(default_factory=dict)
 
     def copy(self):
@@ -262,7 +263,7 @@ class State:
                      lam_prev=cp(self.lam_prev), tlam=cp(self.tlam),
                      tlam_prev=cp(self.tlam_prev), Yprev2=cp(self.Yprev2),
                      u_prev2=cp(self.u_prev2), lam_prev2=cp(self.lam_prev2),
-                     xord=cp(self.xord))
+                     xfit=cp(self.xfit))
 
 
 @dataclass
@@ -804,29 +805,43 @@ def _histories(lay: Layout, state: State):
     return hy, hu, hl
 
 
+FIT_DECAY = 0.7
+
+
+def fit_theta(PQ):
+    """theta of a block from its fit (P, Q): P / Q clipped to [0, 1], 0 if Q = 0."""
+    P, Q = PQ
+    return 0.0 if not Q > 0 else min(max(P / Q, 0.0), 1.0)
+
+
 def initial_guess(lay: Layout, state: State, tether: Tether | None = None, order: int = 1):
     """X_0 of a step: each unknown extrapolated from the previous steps with
     the polynomial of degree order (1: x_0 = 2 x^j - x^{j-1}) through as many
-    of its last values as exist, else the last value (order ADAPTIVE: degree
-    state.xord[i, block] per filament and block, at most 2); the multiplier
-    slots of tethered filaments linearly from the multipliers of past steps
-    (zero before the first)."""
+    of its last values as exist, else the last value (order ADAPTIVE: a block
+    with three values takes x_0 = 2 x^j - x^{j-1} + theta d, theta from the
+    block's fit in state.xfit); the multiplier slots of tethered filaments
+    linearly from the multipliers of past steps (zero before the first)."""
     hy, hu, hl = _histories(lay, state)
     if order != ADAPTIVE:
         Y1 = extrapolate(hy, order)
         u = extrapolate(hu, order) if hu is not None else np.zeros((lay.S, 3))
         lam = extrapolate(hl, order) if hl is not None else np.zeros((lay.n_lam, 3))
     else:
-        xord = state.xord if state.xord is not None else np.ones((lay.M, 3), dtype=int)
+        fit = state.xfit if state.xfit is not None else np.zeros((lay.M, 3, 2))
         Y1 = np.zeros((lay.M, 3))
         u = np.zeros((lay.S, 3))
         lam = np.zeros((lay.n_lam, 3))
         for i in range(lay.M):
             for b, (out, hist, rows) in enumerate(zip((Y1, u, lam), (hy, hu, hl),
                                                       _blocks(lay, i))):
-                if hist is not None:
-                    out[rows] = extrapolate([None if h is None else h[rows] for h in hist],
-                                            int(xord[i, b]))
+                if hist is None:
+                    continue
+                h = [None if x is None else x[rows] for x in hist]
+                if any(x is None for x in h):
+                    out[rows] = extrapolate(h, 2)          # fewer than three values
+                else:
+                    d = h[0] - 2.0 * h[1] + h[2]
+                    out[rows] = 2.0 * h[0] - h[1] + fit_theta(fit[i, b]) * d
     X0 = lay.join_X(Y1, u, lam)
     if tether is not None:
         if state.tlam is not None:
@@ -855,22 +870,25 @@ def begin_step(lay: Layout, p: Params, state: State, ext: External | None, nthre
     return Broyden(fun, solver.solve, X0, p.tol * p.a)
 
 
-def adaptive_orders(lay: Layout, state: State, X):
-    """The adaptive choice at a commit (before the history shift): for each
-    filament and block (Y_1, u, Lambda) whose last three values exist, 2 if
-    the quadratic extrapolation came strictly closer to the block's solution
-    in X than the linear one (sums of squared differences), else 1."""
+def adaptive_fit(lay: Layout, state: State, X):
+    """The adaptive fit at a commit (before the history shift): for each
+    filament and block (Y_1, u, Lambda) whose last three values exist, with
+    x* the block's solution in X, l = 2 x^j - x^{j-1} and d = x^j - 2 x^{j-1}
+    + x^{j-2}: P <- FIT_DECAY P + <x* - l, d>, Q <- FIT_DECAY Q + <d, d>. The
+    theta = P / Q these give is the least-squares coefficient c minimising
+    sum_k FIT_DECAY^age_k |x*_k - l_k - c d_k|^2 over the commits so far."""
     xs = lay.split_X(X)
-    out = np.ones((lay.M, 3), dtype=int)
+    out = (state.xfit.copy() if state.xfit is not None else np.zeros((lay.M, 3, 2)))
     for b, hist in enumerate(_histories(lay, state)):
         if hist is None or any(h is None for h in hist):
             continue
         for i in range(lay.M):
             rows = _blocks(lay, i)[b]
-            h = [x[rows] for x in hist]
-            e1 = float(np.sum((xs[b][rows] - extrapolate(h, 1)) ** 2))
-            e2 = float(np.sum((xs[b][rows] - extrapolate(h, 2)) ** 2))
-            out[i, b] = 2 if e2 < e1 else 1
+            x0, x1, x2 = (h[rows] for h in hist)
+            d = x0 - 2.0 * x1 + x2
+            r = xs[b][rows] - (2.0 * x0 - x1)
+            out[i, b, 0] = FIT_DECAY * out[i, b, 0] + float(np.sum(r * d))
+            out[i, b, 1] = FIT_DECAY * out[i, b, 1] + float(np.sum(d * d))
     return out
 
 
@@ -879,9 +897,9 @@ def commit_step(lay: Layout, p: Params, state: State, X, tether: Tether | None =
     """q^{j+1} = exp(u*) q^j, Y^{j+1} from the robot arm, and the history shift.
     u^{j-1}, Lambda^{j-1} (and the tether multipliers of the step before) are
     kept only when they came from a committed step; with order ADAPTIVE the
-    orders of the next guess (adaptive_orders)."""
+    fit of the next guess is updated (adaptive_fit)."""
     X, lam1, lam2 = tether_resolve(lay, X, tether)
-    xord = adaptive_orders(lay, state, X) if order == ADAPTIVE else state.xord
+    xfit = adaptive_fit(lay, state, X) if order == ADAPTIVE else state.xfit
     q, t, Y, u, lam = unpack(lay, p, X, state.q)
     stepped = state.steps >= 1
     tlam = np.concatenate([lam1, lam2], axis=1) if tether is not None else None
@@ -894,7 +912,7 @@ def commit_step(lay: Layout, p: Params, state: State, X, tether: Tether | None =
                  Yprev2=state.Yprev.copy() if state.Yprev is not None else None,
                  u_prev2=state.u_prev.copy() if state.u_prev is not None else None,
                  lam_prev2=state.lam_prev.copy() if state.lam_prev is not None else None,
-                 xord=xord)
+                 xfit=xfit)
 
 
 def step(lay: Layout, p: Params, state: State, ext: External | None, nthreads=1,

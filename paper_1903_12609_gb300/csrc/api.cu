@@ -123,7 +123,7 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->Yprev2 = ar.take<double>(3 * S);
     c->uprev3 = ar.take<double>(3 * S);
     c->lamprev2 = ar.take<double>(3 * (nlam > 0 ? nlam : 1));
-    c->xord = ar.take<int8_t>(3 * M);
+    c->xfit = ar.take<double>(6 * M);
     c->Fext = ar.take<double>(3 * S);
     c->Text = ar.take<double>(3 * S);
     c->follower = ar.take<double>(M);
@@ -513,7 +513,7 @@ fil_status fil_set_state(fil_ctx *c, const double *Y, const double *q, const dou
             CK(cudaMemsetAsync(c->lam, 0, sizeof(double) * 3 * c->lay.nlam, c->stream));
     }
     CK(cudaStreamSynchronize(c->stream));
-    CK(cudaMemsetAsync(c->xord, 1, 3 * c->lay.M, c->stream));
+    CK(cudaMemsetAsync(c->xfit, 0, sizeof(double) * 6 * c->lay.M, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->have_prev = Yprev ? 1 : 0;
     c->ylev = Yprev ? 1 : 0;
@@ -562,7 +562,7 @@ fil_status fil_init_straight(fil_ctx *c, const double *base, const double *t, co
     CK(cudaMemsetAsync(c->Yprev, 0, sizeof(double) * 3 * S, c->stream));
     CK(cudaMemsetAsync(c->uprev, 0, sizeof(double) * 3 * S, c->stream));
     if (c->lay.nlam > 0) CK(cudaMemsetAsync(c->lam, 0, sizeof(double) * 3 * c->lay.nlam, c->stream));
-    CK(cudaMemsetAsync(c->xord, 1, 3 * M, c->stream));
+    CK(cudaMemsetAsync(c->xfit, 0, sizeof(double) * 6 * M, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->have_prev = 0;
     c->ylev = 0;

@@ -74,7 +74,7 @@ struct fil_ctx {
     int hist;              // steps committed since the last set_state / init
     int ylev;              // past Y levels held (Yprev, Yprev2): 0..2
     int extrap_order = 1;  // FIL_EXTRAP_LINEAR / _QUADRATIC / _ADAPTIVE
-    int8_t *xord;          // adaptive order per filament and block (Y_1, u, Lambda): 3M
+    double *xfit;          // adaptive fit (P, Q) per filament and block (Y_1, u, Lambda): 6M
     int64_t steps;
 
     // external loads

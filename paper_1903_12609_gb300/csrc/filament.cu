@@ -234,12 +234,30 @@ __device__ __forceinline__ V3 extrapolated(V3 x0, const double *x1, const double
     return x0;
 }
 
+// Fraction theta of the second difference in the adaptive guess of one block:
+// P / Q from its fit statistics (P, Q), clipped to [0, 1]; 0 before a fit.
+__device__ __forceinline__ double fit_theta(const double *pq) {
+    const double P = pq[0], Q = pq[1];
+    if (!(Q > 0.0)) return 0.0;
+    return fmin(fmax(P / Q, 0.0), 1.0);
+}
+
+// Guess of one 3-vector: extrapolated at order ord (<= 1), or with three
+// values either quadratic (theta < 0) or the linear guess plus theta times
+// the second difference (the adaptive form).
+__device__ __forceinline__ V3 guess(V3 x0, const double *x1, const double *x2, int ord,
+                                    double theta) {
+    if (ord < 2 || theta < 0.0) return extrapolated(x0, x1, x2, ord);
+    const V3 a = ld3(x1);
+    return (2.0 * x0 - a) + theta * ((x0 - 2.0 * a) + ld3(x2));
+}
+
 // X_0 of a step: each unknown extrapolated from the committed steps, Y_1 with
 // order y_ord from its BDF2 history (Y^j, Y^{j-1}, Y^{j-2}), u and Lambda with
 // order u_ord from (u^j, u^{j-1}, u^{j-2}) and (Lambda^j, ...); u_ord < 0
-// before the first step: u = 0, Lambda = Lambda^j. With xord (the adaptive
-// choice) each filament's blocks Y_1, u, Lambda use at most xord[3i + 0..2].
-// One thread per segment.
+// before the first step: u = 0, Lambda = Lambda^j. With xfit (the adaptive
+// form) an order-2 block takes its fitted theta (xfit[6i + 2b], b = 0: Y_1,
+// 1: u, 2: Lambda). One thread per segment.
 __global__ void extrapolate_kernel(Layout lay, const double *__restrict__ Y,
                                    const double *__restrict__ Yprev,
                                    const double *__restrict__ Yprev2,
@@ -249,89 +267,97 @@ __global__ void extrapolate_kernel(Layout lay, const double *__restrict__ Y,
                                    const double *__restrict__ lam,
                                    const double *__restrict__ lamprev,
                                    const double *__restrict__ lamprev2, int y_ord, int u_ord,
-                                   const int8_t *__restrict__ xord, double *__restrict__ X0) {
+                                   const double *__restrict__ xfit, double *__restrict__ X0) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= lay.S) return;
     const int i = lay.fil_of[g];
     const int s0 = lay.off[i];
     const int N = lay.off[i + 1] - s0;
     const int n = (int)(g - s0);
-    int l_ord = u_ord > 0 ? u_ord : 0;
-    if (xord) {
-        y_ord = min(y_ord, (int)xord[3 * i]);
-        if (u_ord > 0) u_ord = min(u_ord, (int)xord[3 * i + 1]);
-        l_ord = min(l_ord, (int)xord[3 * i + 2]);
-    }
+    const double *fit = xfit ? xfit + 6 * (int64_t)i : nullptr;
     double *Xf = X0 + 6 * (int64_t)s0;
-    if (n == 0) st3(Xf, extrapolated(ld3(Y + 3 * g), Yprev + 3 * g, Yprev2 + 3 * g, y_ord));
+    if (n == 0)
+        st3(Xf, guess(ld3(Y + 3 * g), Yprev + 3 * g, Yprev2 + 3 * g, y_ord,
+                      fit ? fit_theta(fit) : -1.0));
     V3 u0 = v3(0, 0, 0);
-    if (u_ord >= 0) u0 = extrapolated(ld3(uprev + 3 * g), uprev2 + 3 * g, uprev3 + 3 * g, u_ord);
+    if (u_ord >= 0)
+        u0 = guess(ld3(uprev + 3 * g), uprev2 + 3 * g, uprev3 + 3 * g, u_ord,
+                   fit ? fit_theta(fit + 2) : -1.0);
     st3(Xf + 3 + 3 * n, u0);
     if (n <= N - 2) {
         const int64_t li = 3 * (int64_t)(s0 - i + n);
-        st3(Xf + 3 + 3 * N + 3 * n, extrapolated(ld3(lam + li), lamprev + li, lamprev2 + li, l_ord));
+        st3(Xf + 3 + 3 * N + 3 * n, guess(ld3(lam + li), lamprev + li, lamprev2 + li,
+                                          u_ord > 0 ? u_ord : 0, fit ? fit_theta(fit + 4) : -1.0));
     }
 }
 
-// Squared differences between a solution x* and the linear and quadratic
-// extrapolations from x^j, x^{j-1}, x^{j-2}, accumulated into e[0], e[1].
-__device__ __forceinline__ void extrap_errors(const double *xs, const double *x0, const double *x1,
-                                              const double *x2, double e[2]) {
-    const V3 s = ld3(xs), a = ld3(x0);
-    const V3 dl = s - extrapolated(a, x1, x2, 1);
-    const V3 dq = s - extrapolated(a, x1, x2, 2);
-    e[0] += dot(dl, dl);
-    e[1] += dot(dq, dq);
+// Terms of the adaptive fit of one 3-vector: with l = 2 x^j - x^{j-1} and
+// d = x^j - 2 x^{j-1} + x^{j-2}, pq[0] += <x* - l, d> and pq[1] += <d, d>.
+__device__ __forceinline__ void fit_terms(const double *xs, const double *x0, const double *x1,
+                                          const double *x2, double pq[2]) {
+    const V3 a = ld3(x0), b = ld3(x1);
+    const V3 d = (a - 2.0 * b) + ld3(x2);
+    const V3 r = ld3(xs) - (2.0 * a - b);
+    pq[0] += dot(r, d);
+    pq[1] += dot(d, d);
 }
 
-// Adaptive order (before the history shift of a commit): for each filament
-// and block (Y_1, u, Lambda) whose last three values exist (y_ok, u_ok), the
-// order whose extrapolation came closer to the committed solution X (sums of
-// squared differences; the quadratic one only if strictly closer); blocks
-// that cannot be compared get the linear order. One warp per filament, lane
-// sums combined by a fixed shuffle tree.
-__global__ void extrap_select_kernel(Layout lay, const double *__restrict__ X,
-                                     const double *__restrict__ Y,
-                                     const double *__restrict__ Yprev,
-                                     const double *__restrict__ Yprev2,
-                                     const double *__restrict__ uprev,
-                                     const double *__restrict__ uprev2,
-                                     const double *__restrict__ uprev3,
-                                     const double *__restrict__ lam,
-                                     const double *__restrict__ lamprev,
-                                     const double *__restrict__ lamprev2, int y_ok, int u_ok,
-                                     int8_t *__restrict__ xord) {
+// Adaptive fit at a commit (before the history shift): for each filament and
+// block (Y_1, u, Lambda) whose last three values exist (y_ok, u_ok),
+// P <- kFitDecay P + <x* - l, d>, Q <- kFitDecay Q + <d, d> over the block's
+// 3-vectors, x* the committed solution X. One warp per filament, lane sums
+// combined by a fixed shuffle tree.
+constexpr double kFitDecay = 0.7;
+
+__global__ void extrap_fit_kernel(Layout lay, const double *__restrict__ X,
+                                  const double *__restrict__ Y, const double *__restrict__ Yprev,
+                                  const double *__restrict__ Yprev2,
+                                  const double *__restrict__ uprev,
+                                  const double *__restrict__ uprev2,
+                                  const double *__restrict__ uprev3,
+                                  const double *__restrict__ lam,
+                                  const double *__restrict__ lamprev,
+                                  const double *__restrict__ lamprev2, int y_ok, int u_ok,
+                                  double *__restrict__ xfit) {
     const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= lay.M) return;
     const int s0 = lay.off[i];
     const int N = lay.off[i + 1] - s0;
     const double *Xf = X + 6 * (int64_t)s0;
-    double eu[2] = {0, 0}, el[2] = {0, 0};
+    double fu[2] = {0, 0}, fl[2] = {0, 0};
     if (u_ok) {
         for (int n = lane; n < N; n += 32) {
             const int64_t g = s0 + n;
-            extrap_errors(Xf + 3 + 3 * n, uprev + 3 * g, uprev2 + 3 * g, uprev3 + 3 * g, eu);
+            fit_terms(Xf + 3 + 3 * n, uprev + 3 * g, uprev2 + 3 * g, uprev3 + 3 * g, fu);
             if (n <= N - 2) {
                 const int64_t li = 3 * (int64_t)(s0 - i + n);
-                extrap_errors(Xf + 3 + 3 * N + 3 * n, lam + li, lamprev + li, lamprev2 + li, el);
+                fit_terms(Xf + 3 + 3 * N + 3 * n, lam + li, lamprev + li, lamprev2 + li, fl);
             }
         }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
-            eu[0] += __shfl_xor_sync(0xffffffffu, eu[0], d);
-            eu[1] += __shfl_xor_sync(0xffffffffu, eu[1], d);
-            el[0] += __shfl_xor_sync(0xffffffffu, el[0], d);
-            el[1] += __shfl_xor_sync(0xffffffffu, el[1], d);
+            fu[0] += __shfl_xor_sync(0xffffffffu, fu[0], d);
+            fu[1] += __shfl_xor_sync(0xffffffffu, fu[1], d);
+            fl[0] += __shfl_xor_sync(0xffffffffu, fl[0], d);
+            fl[1] += __shfl_xor_sync(0xffffffffu, fl[1], d);
         }
     }
     if (lane == 0) {
-        double ey[2] = {0, 0};
-        if (y_ok) extrap_errors(Xf, Y + 3 * (int64_t)s0, Yprev + 3 * (int64_t)s0,
-                                Yprev2 + 3 * (int64_t)s0, ey);
-        xord[3 * i] = (y_ok && ey[1] < ey[0]) ? 2 : 1;
-        xord[3 * i + 1] = (u_ok && eu[1] < eu[0]) ? 2 : 1;
-        xord[3 * i + 2] = (u_ok && el[1] < el[0]) ? 2 : 1;
+        double *f = xfit + 6 * (int64_t)i;
+        if (y_ok) {
+            double fy[2] = {0, 0};
+            const int64_t g = s0;
+            fit_terms(Xf, Y + 3 * g, Yprev + 3 * g, Yprev2 + 3 * g, fy);
+            f[0] = kFitDecay * f[0] + fy[0];
+            f[1] = kFitDecay * f[1] + fy[1];
+        }
+        if (u_ok) {
+            f[2] = kFitDecay * f[2] + fu[0];
+            f[3] = kFitDecay * f[3] + fu[1];
+            f[4] = kFitDecay * f[4] + fl[0];
+            f[5] = kFitDecay * f[5] + fl[1];
+        }
     }
 }
 
@@ -407,8 +433,8 @@ cudaError_t init_straight(fil_ctx *c, const double *base, const double *t, const
 cudaError_t extrapolate_guess(fil_ctx *c, double *X0) {
     // order of each unknown's polynomial: as high as the committed history and
     // the chosen order allow (Y_1 has one level more than u and Lambda: the
-    // BDF2 history holds Y^{j-1} from the first step on); the adaptive choice
-    // lowers it per filament and block
+    // BDF2 history holds Y^{j-1} from the first step on); the adaptive form
+    // replaces the quadratic one by its fitted blend per filament and block
     const bool adaptive = c->extrap_order == FIL_EXTRAP_ADAPTIVE;
     const int cap = adaptive ? 2 : c->extrap_order;
     const int y_ord = c->ylev < cap ? c->ylev : cap;
@@ -416,7 +442,7 @@ cudaError_t extrapolate_guess(fil_ctx *c, double *X0) {
     const int u_ord = u_lev < cap ? u_lev : cap;
     extrapolate_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(
         c->lay, c->Y, c->Yprev, c->Yprev2, c->uprev, c->uprev2, c->uprev3, c->lam, c->lamprev,
-        c->lamprev2, y_ord, u_ord, adaptive ? c->xord : nullptr, X0);
+        c->lamprev2, y_ord, u_ord, adaptive ? c->xfit : nullptr, X0);
     c->n_launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && c->tether_on) e = tether_guess(c, X0);
@@ -427,11 +453,11 @@ cudaError_t commit_state(fil_ctx *c, const double *X) {
     cudaError_t e = unpack_forces(c, X, 0);
     if (e != cudaSuccess) return e;
     if (c->extrap_order == FIL_EXTRAP_ADAPTIVE) {
-        // the comparison needs the three values before this commit: Y_1 once
-        // two past levels are held, u and Lambda once three steps were committed
-        extrap_select_kernel<<<warp_grid(c->lay.M, 128), 128, 0, c->stream>>>(
+        // the fit needs the three values before this commit: Y_1 once two past
+        // levels are held, u and Lambda once three steps were committed
+        extrap_fit_kernel<<<warp_grid(c->lay.M, 128), 128, 0, c->stream>>>(
             c->lay, X, c->Y, c->Yprev, c->Yprev2, c->uprev, c->uprev2, c->uprev3, c->lam,
-            c->lamprev, c->lamprev2, c->ylev >= 2 ? 1 : 0, c->hist >= 3 ? 1 : 0, c->xord);
+            c->lamprev, c->lamprev2, c->ylev >= 2 ? 1 : 0, c->hist >= 3 ? 1 : 0, c->xfit);
         c->n_launches += 1;
     }
     commit_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(

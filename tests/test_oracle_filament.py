@@ -520,62 +520,106 @@ def _two_filament_history():
     return lay, first, series
 
 
-def test_adaptive_orders_pick_the_closer_extrapolation():
-    """adaptive_orders: 2 where the block's past is quadratic (the quadratic
-    guess is exact), 1 where noise on the past values makes the quadratic
-    weights (3, -3, 1) miss by more than the linear ones (2, -1), 1 on a tie
-    (an exactly linear past, where both are exact), 1 where three past values
-    do not exist; per filament and per block."""
-    lay, first, series = _two_filament_history()
-    kinds = [("quad", "noisy", "lin"), ("noisy", "quad", "quad")]
+def _history_state(lay, first, series, kinds):
+    """State (steps=3) and solution X from per-filament (Y_1, u, Lambda) kinds."""
     Y = np.zeros((4, lay.S, 3))
     U = np.zeros((4, lay.S, 3))
     L = np.zeros((4, lay.n_lam, 3))
     for i, (ky, ku, kl) in enumerate(kinds):
         s, e = lay.off_seg[i], lay.off_seg[i + 1]
         vy = series((3,), ky)
-        for k in range(4):
-            Y[k, s:e] = vy[k]                       # only Y_1 matters; rows of one filament
         vu = series((e - s, 3), ku)
         vl = series((e - s - 1, 3), kl)
         for k in range(4):
+            Y[k, s:e] = vy[k]
             U[k, s:e] = vu[k]
             L[k, lay.off_lam[i]:lay.off_lam[i + 1]] = vl[k]
     st = fo.State(Y=Y[1], q=np.tile([1.0, 0, 0, 0], (lay.S, 1)), Yprev=Y[2], Yprev2=Y[3],
                   u=U[1], u_prev=U[2], u_prev2=U[3], lam=L[1], lam_prev=L[2],
                   lam_prev2=L[3], steps=3)
-    X = lay.join_X(Y[0][first], U[0], L[0])
-    np.testing.assert_array_equal(fo.adaptive_orders(lay, st, X), [[2, 1, 1], [1, 2, 2]])
+    return st, lay.join_X(Y[0][first], U[0], L[0])
+
+
+def test_adaptive_fit_of_one_commit():
+    """One commit's fit: theta = 1 where the block's past is quadratic (the
+    solution departs from the linear guess by exactly the second difference),
+    0 where noise on the past values (+n, -n, +n) makes the second difference
+    4n point against the departure -3n (the clip at 0: linear), 0 where the
+    past is exactly linear (no second difference: Q = 0); per filament and
+    block; no fit where three past values do not exist."""
+    lay, first, series = _two_filament_history()
+    st, X = _history_state(lay, first, series, [("quad", "noisy", "lin"),
+                                                ("noisy", "quad", "quad")])
+    fit = fo.adaptive_fit(lay, st, X)
+    theta = np.array([[fo.fit_theta(fit[i, b]) for b in range(3)] for i in range(2)])
+    np.testing.assert_array_equal(theta, [[1.0, 0.0, 0.0], [0.0, 1.0, 1.0]])
+    assert fit[0, 2, 1] == 0.0                          # exactly linear: Q = 0
+    assert fit[1, 0, 0] < 0                             # noise: P < 0, clipped
     st.u_prev2 = st.lam_prev2 = None
-    np.testing.assert_array_equal(fo.adaptive_orders(lay, st, X), [[2, 1, 1], [1, 1, 1]])
+    fit = fo.adaptive_fit(lay, st, X)
+    assert np.all(fit[:, 1:] == 0) and np.all(fit[:, 0, 1] > 0)
     st.Yprev2 = None
-    np.testing.assert_array_equal(fo.adaptive_orders(lay, st, X), np.ones((2, 3)))
+    assert np.all(fo.adaptive_fit(lay, st, X) == 0)
 
 
-def test_adaptive_guess_uses_each_blocks_order():
-    """initial_guess(order=ADAPTIVE) extrapolates each filament's blocks with
-    the orders in state.xord (quadratic histories: order 2 is their
-    continuation, order 1 the linear guess), and with no xord linearly."""
+def test_adaptive_fit_is_the_weighted_least_squares_coefficient():
+    """Over several commits the fit's theta minimises
+    sum_k 0.7^age_k |x*_k - l_k - theta d_k|^2 (checked by a bounded scalar
+    minimisation of that objective), for a block whose departures are a noisy
+    fraction of its second differences."""
+    from scipy.optimize import minimize_scalar
+    rng = np.random.default_rng(36)
+    lay = fo.Layout([4])
+    st = fo.State(Y=np.zeros((4, 3)), q=np.tile([1.0, 0, 0, 0], (4, 1)), steps=3)
+    terms = []
+    for k in range(6):
+        hist = [rng.standard_normal((4, 3)) for _ in range(3)]
+        st.u, st.u_prev, st.u_prev2 = hist
+        st.Yprev, st.Yprev2 = np.zeros((4, 3)), None     # u needs Y^{j-1}; no Y_1 fit
+        st.lam = st.lam_prev = st.lam_prev2 = np.zeros((3, 3))
+        lin = 2 * hist[0] - hist[1]
+        d = hist[0] - 2 * hist[1] + hist[2]
+        xs = lin + 0.4 * d + 0.3 * rng.standard_normal((4, 3))
+        X = lay.join_X(np.zeros((1, 3)), xs, np.zeros((3, 3)))
+        st.xfit = fo.adaptive_fit(lay, st, X)
+        terms.append((xs - lin, d))
+    ages = np.arange(len(terms))[::-1]
+
+    def objective(c):
+        return sum(0.7 ** a * np.sum((r - c * d) ** 2) for a, (r, d) in zip(ages, terms))
+
+    best = minimize_scalar(objective, bounds=(-2, 3), method="bounded",
+                           options={"xatol": 1e-10}).x
+    theta = fo.fit_theta(st.xfit[0, 1])
+    assert 0 < theta < 1
+    assert abs(theta - best) < 1e-7, (theta, best)
+
+
+def test_adaptive_guess_uses_each_blocks_theta():
+    """initial_guess(order=ADAPTIVE) gives each block the linear guess plus its
+    theta times the second difference (quadratic histories: theta = 1 is their
+    continuation, 0 the linear guess), and with no fit the linear guess."""
     lay, first, series = _two_filament_history()
     vy = series((lay.S, 3), "quad")
     vu = series((lay.S, 3), "quad")
     vl = series((lay.n_lam, 3), "quad")
+    thetas = np.array([[1.0, 0.25, 0.0], [0.5, 1.0, 0.75]])
+    fit = np.stack([thetas * 2.0, np.full((2, 3), 2.0)], axis=-1)     # P = 2 theta, Q = 2
     st = fo.State(Y=vy[1], q=np.tile([1.0, 0, 0, 0], (lay.S, 1)), Yprev=vy[2], Yprev2=vy[3],
                   u=vu[1], u_prev=vu[2], u_prev2=vu[3], lam=vl[1], lam_prev=vl[2],
-                  lam_prev2=vl[3], steps=3, xord=np.array([[2, 1, 2], [1, 2, 1]]))
+                  lam_prev2=vl[3], steps=3, xfit=fit)
     X0 = fo.initial_guess(lay, st, order=fo.ADAPTIVE)
     Y1, u, lam = lay.split_X(X0)
-    lin = [2 * v[1] - v[2] for v in (vy, vu, vl)]
-    for i in range(lay.M):
-        want = [vy[0][first[i]] if st.xord[i, 0] == 2 else lin[0][first[i]]]
-        np.testing.assert_allclose(Y1[i], want[0], rtol=0, atol=1e-13)
-        rows = slice(lay.off_seg[i], lay.off_seg[i + 1])
-        ref = vu[0] if st.xord[i, 1] == 2 else lin[1]
-        np.testing.assert_allclose(u[rows], ref[rows], rtol=0, atol=1e-13)
-        rows = slice(lay.off_lam[i], lay.off_lam[i + 1])
-        ref = vl[0] if st.xord[i, 2] == 2 else lin[2]
-        np.testing.assert_allclose(lam[rows], ref[rows], rtol=0, atol=1e-13)
-    st.xord = None
+    blocks = ((Y1, [x[first] for x in vy], lambda i: slice(i, i + 1)),
+              (u, vu, lambda i: slice(lay.off_seg[i], lay.off_seg[i + 1])),
+              (lam, vl, lambda i: slice(lay.off_lam[i], lay.off_lam[i + 1])))
+    for b, (got, v, rows_of) in enumerate(blocks):
+        for i in range(lay.M):
+            r = rows_of(i)
+            lin = 2 * v[1][r] - v[2][r]
+            want = lin + thetas[i, b] * (v[0][r] - lin)       # v[0] - lin = d for these
+            np.testing.assert_allclose(got[r], want, rtol=0, atol=1e-12)
+    st.xfit = None
     np.testing.assert_allclose(fo.initial_guess(lay, st, order=fo.ADAPTIVE),
                                fo.initial_guess(lay, st, order=1), rtol=0, atol=0)
 
