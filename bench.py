@@ -2,8 +2,10 @@
 32 000-segment filament suspension on one GB300 (per GPU; weak scaling over
 independent replicas when launched on several GPUs).
 
-One step = one whole timestep of the method: initial guess (the learned warm
-start, with the extrapolation as fallback), J0 assembly and inversion, the
+One step = one whole timestep of the method: initial guess (extrapolated from
+past steps, by default the adaptive blend of the linear and quadratic guesses;
+the learned warm start is attached when its weights were trained on the chosen
+extrapolation, e.g. --extrapolation 1), J0 assembly and inversion, the
 Broyden loop (each iteration: unpack, forces, RPY mobility over all S^2 pairs,
 residual, J0 solve, rank-one update) and the commit. The value is the number
 of RPY pair interactions evaluated in the timed steps divided by their device
@@ -20,8 +22,9 @@ accumulation; the Broyden history and updates, the J0 solves, the quaternion
 steps, the state and the residual in FP64.
 
 The default run also reports, as nested records with their own config,
-roofline, clocks and FP64-oracle comparison: the all-FP32-solve variant
-("mixed"), the plain FP64 solve, the mobility apply alone at 3200 segments
+roofline, clocks and FP64-oracle comparison: the initial-guess rules side by
+side, the all-FP32-solve variant ("mixed"), the plain FP64 solve (the paper's
+form: linear guess, J0 every step), the mobility apply alone at 3200 segments
 (1000 applies), the single sedimenting filament (200 FP64 steps), the
 256-system ensemble and the suspension with clamped filaments.
 

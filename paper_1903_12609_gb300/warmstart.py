@@ -252,7 +252,7 @@ def main():
     ap.add_argument("--seed", type=int, default=100,
                     help="workload seed of the training trajectory (the bench uses seed 0)")
     ap.add_argument("--eval-steps", type=int, default=50)
-    ap.add_argument("--extrapolation", type=int, default=1, choices=[1, 2],
+    ap.add_argument("--extrapolation", type=int, default=1, choices=[1, 2, 3],
                     help="order of the extrapolated guess the network learns to correct")
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     args = ap.parse_args()
