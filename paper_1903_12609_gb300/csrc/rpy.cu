@@ -33,8 +33,8 @@
 //  * Stream-K persistent grid: the (tile, chunk) work units are split evenly
 //    over G = #SMs x resident-CTAs; a CTA writes one partial per tile it
 //    touches into slot (cta + tile) and a deterministic reduce kernel sums
-//    them (eight lanes per target, each over a fixed stride of CTAs, then a
-//    fixed shuffle tree). No atomics: results are bitwise reproducible.
+//    them (eight warps per 32 targets, each over a fixed stride of CTAs,
+//    combined in warp order). No atomics: results are bitwise reproducible.
 //  * Mixed precision: positions are stored as FP32 hi/lo pairs (hi = fl32(Y),
 //    lo = fl32(Y - hi)). The inner loop forms d from the hi parts alone,
 //    which carries the rounding of the coordinates (~ulp(|Y|)) and is
@@ -727,7 +727,7 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
 
 // ---------------------------------------------------------------------------
 // Reduce the stream-K partials of each target and scale by 1/(8 pi eta)
-// (kRedLanes threads per target, see reduce_target).
+// (kRedWarps threads per target, see reduce_targets).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cta_range_of_tile(const SysMap &sm, int64_t tile, int64_t W,
                                                   int64_t G, int64_t &b0, int64_t &b1) {
@@ -740,35 +740,58 @@ __device__ __forceinline__ void cta_range_of_tile(const SysMap &sm, int64_t tile
     b1 = ((u1 + 1) * G + W - 1) / W - 1;
 }
 
-// kRedLanes lanes per target: lane l sums the partials of the CTAs b0 + l,
-// b0 + l + kRedLanes, ... (in CTA order) and the lane sums are combined by a
-// fixed shuffle tree, so the result does not depend on timing; spreading a
-// target's partials over lanes keeps the latency low when a tile's chunks are
-// split over many CTAs (small problems, many CTAs per SM).
-constexpr int kRedLanes = 8;
+// A block of rw = blockDim.x / 32 warps reduces 32 consecutive targets: lane t
+// of warp l sums, for target t, the partials of the CTAs b0 + l, b0 + l + rw,
+// ... (in CTA order; a warp's loads are 32 consecutive targets of one slot),
+// and warp 0 adds the rw sums in warp order, so the result does not depend on
+// timing. Spreading a target's partials over warps keeps the latency low when
+// a tile's chunks are split over many CTAs (small problems, many CTAs per SM);
+// red_warps picks rw from the grid and the tile count alone, so every path
+// that launches the same apply (graph or not) sums in the same order.
+constexpr int kRedWarps = 8;
+constexpr int kRedThreads = 32 * kRedWarps;
+
+int red_warps(int64_t G, int64_t tiles) {
+    const int64_t per_tile = (G + tiles - 1) / (tiles > 0 ? tiles : 1);   // CTAs per tile
+    const int64_t rw = (per_tile + 3) / 4;
+    return (int)(rw < 1 ? 1 : rw > kRedWarps ? kRedWarps : rw);
+}
 
 template <typename PT, int NPART>
-__device__ __forceinline__ void reduce_target(const PT *__restrict__ part, int64_t S, SysMap &sm,
-                                              int64_t W, int G, int T, double scale,
-                                              double *__restrict__ VW) {
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t n = gt / kRedLanes;
-    const int l = (int)(gt % kRedLanes);
-    // the lanes of one target are an aligned group within a warp
-    const unsigned gmask = ((1u << kRedLanes) - 1u) << (threadIdx.x & 31 & ~(kRedLanes - 1));
-    if (n >= S) return;                      // whole groups leave together
-    const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
-    int64_t tile = P / T;
-    const int local = (int)(P - tile * T);
-    if (sm.slot_of) {
-        tile = sm.slot_of[tile];
-        if (tile < 0) return;                 // a system left out of this apply
+__device__ __forceinline__ void reduce_targets(const PT *__restrict__ part, int64_t S,
+                                               SysMap &sm, int64_t W, int G, int T, double scale,
+                                               double *__restrict__ VW) {
+    __shared__ double red[kRedWarps][6][32];
+    __shared__ int64_t s_tile[32], s_b0[32], s_b1[32];
+    __shared__ int s_local[32], s_live[32];
+    const int t = threadIdx.x & 31, l = threadIdx.x >> 5, rw = (int)(blockDim.x >> 5);
+    const int64_t n = (int64_t)blockIdx.x * 32 + t;
+    // the target's slot and CTA range, once per target (warp 0); a target past
+    // S or of a system left out of this apply is not live (nothing written)
+    if (l == 0) {
+        int64_t tile = 0, b0 = 1, b1 = 0;
+        int local = 0, live = 0;
+        if (n < S) {
+            const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
+            tile = P / T;
+            local = (int)(P - tile * T);
+            if (sm.slot_of) tile = sm.slot_of[tile];
+            live = tile >= 0;
+            if (live) cta_range_of_tile(sm, tile, W, G, b0, b1);
+        }
+        s_tile[t] = tile;
+        s_b0[t] = b0;
+        s_b1[t] = b1;
+        s_local[t] = local;
+        s_live[t] = live;
     }
-    int64_t b0, b1;
-    cta_range_of_tile(sm, tile, W, G, b0, b1);
+    __syncthreads();
+    const int64_t tile = s_tile[t], b1 = s_b1[t];
+    const int local = s_local[t];
+    const bool sparse = (int64_t)G > W;   // then some CTAs own no unit
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t b = b0 + l; b <= b1; b += kRedLanes) {
-        if (unit_start(b + 1, W, G) == unit_start(b, W, G)) continue;   // a CTA with no unit
+    for (int64_t b = s_b0[t] + l; b <= b1; b += rw) {
+        if (sparse && unit_start(b + 1, W, G) == unit_start(b, W, G)) continue;
         const PT *p = part + (size_t)(b + tile) * (6 * NPART) * T;
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -778,28 +801,33 @@ __device__ __forceinline__ void reduce_target(const PT *__restrict__ part, int64
         }
     }
 #pragma unroll
-    for (int d = kRedLanes / 2; d > 0; d >>= 1)
+    for (int c = 0; c < 6; ++c) red[l][c][t] = acc[c];
+    __syncthreads();
+    if (l == 0 && s_live[t]) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) acc[c] += __shfl_xor_sync(gmask, acc[c], d);
-    if (l == 0) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) VW[6 * n + c] = acc[c] * scale;
+        for (int c = 0; c < 6; ++c) {
+            double v = red[0][c][t];
+            for (int w = 1; w < rw; ++w) v += red[w][c][t];
+            VW[6 * n + c] = v * scale;
+        }
     }
 }
 
 // FP32 partials: (hi, lo) of each component, 12 floats per target and CTA.
-__global__ void rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, SysMap sm,
+__global__ void __launch_bounds__(kRedThreads)
+rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, SysMap sm,
                                     int64_t W, int G, int T, double scale,
                                     double *__restrict__ VW) {
     resolve_dyn(sm, W);
-    reduce_target<float, 2>(part, S, sm, W, G, T, scale, VW);
+    reduce_targets<float, 2>(part, S, sm, W, G, T, scale, VW);
 }
 
-__global__ void rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, SysMap sm,
+__global__ void __launch_bounds__(kRedThreads)
+rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, SysMap sm,
                                     int64_t W, int G, int T, double scale,
                                     double *__restrict__ VW) {
     resolve_dyn(sm, W);
-    reduce_target<double, 1>(part, S, sm, W, G, T, scale, VW);
+    reduce_targets<double, 1>(part, S, sm, W, G, T, scale, VW);
 }
 
 SysMap sys_map(const fil_ctx *c, bool active_only) {
@@ -1021,7 +1049,7 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
     const double scale = 1.0 / (8.0 * kPi * c->eta);
     const int pb = 256;
     const unsigned pgrid = (unsigned)((c->Spad + pb - 1) / pb);
-    const unsigned rgrid = (unsigned)((S * kRedLanes + pb - 1) / pb);
+    const unsigned rgrid = (unsigned)((S + 31) / 32);
     const bool timed = c->prof_on && c->prof_n < kProfMax;
     const SysMap sm = sys_map(c, active_only);
     const int64_t W = active_only ? c->act_units : c->rpy_units;
@@ -1042,7 +1070,8 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
             rpy_pair32_kernel<2><<<G, kRpyThreads, 0, c->stream>>>(c->src32, sm, W, G, k,
                                                                    (float *)c->partials);
         if (timed) prof_record(c, c->prof_ev[2 * c->prof_n + 1]);
-        rpy_reduce32_kernel<<<rgrid, pb, 0, c->stream>>>((const float *)c->partials, S, sm, W, G,
+        rpy_reduce32_kernel<<<rgrid, 32 * red_warps(G, c->rpy_tiles), 0, c->stream>>>(
+            (const float *)c->partials, S, sm, W, G,
                                                          T, scale, VW);
         if (c->tune_ev) cudaEventRecord(c->tune_ev[1], c->stream);
     } else {
@@ -1058,7 +1087,8 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
             rpy_pair64_kernel<2><<<G, kRpyThreads, 0, c->stream>>>(c->src64, sm, W, G, k,
                                                                    (double *)c->partials);
         if (timed) prof_record(c, c->prof_ev[2 * c->prof_n + 1]);
-        rpy_reduce64_kernel<<<rgrid, pb, 0, c->stream>>>((const double *)c->partials, S, sm, W, G,
+        rpy_reduce64_kernel<<<rgrid, 32 * red_warps(G, c->rpy_tiles), 0, c->stream>>>(
+            (const double *)c->partials, S, sm, W, G,
                                                          T, scale, VW);
         if (c->tune_ev) cudaEventRecord(c->tune_ev[1], c->stream);
     }
@@ -1285,7 +1315,7 @@ extern "C" fil_status fil_rpy_apply_noalloc(int64_t n_seg, const double *Y, cons
         e = launch(rpy_pair32_kernel<kRpyTargetsPerThread>, (unsigned)G, kRpyThreads, st,
                    (const float4 *)src, sm, W, G, make_const<float, RpyConst32>(a), part);
     if (e == cudaSuccess)
-        e = launch(rpy_reduce32_kernel, (unsigned)((n_seg * kRedLanes + pb - 1) / pb), pb, st,
+        e = launch(rpy_reduce32_kernel, (unsigned)((n_seg + 31) / 32), 32 * red_warps(G, tiles), st,
                    (const float *)part, n_seg, sm, W, G, kRpyTile, 1.0 / (8.0 * kPi * eta), VW);
     return e == cudaSuccess ? FIL_OK : FIL_ECUDA;
 }
