@@ -38,10 +38,19 @@ __device__ __forceinline__ PairCoef pair_coef(V3 d, double a) {
     return k;
 }
 
-// (V, Omega) += M_nm (v, w) in units of 1/(8 pi eta)
+// (V, Omega) += M_nm (v, w) in units of 1/(8 pi eta), as fused multiply-adds
+// (35 FP64 operations: the two dot products, e = G d, and four terms per
+// component; GB300 runs FP64 at 1/64 of the FP32 rate, so the count matters)
 __device__ __forceinline__ void apply_pair(const PairCoef &k, V3 d, V3 v, V3 w, V3 &V, V3 &W) {
-    V = V + k.A * v + (k.B * dot(d, v)) * d + k.G * cross(w, d);
-    W = W + k.G * cross(v, d) + k.C * w + (k.D * dot(d, w)) * d;
+    const double bdv = k.B * fma(d.x, v.x, fma(d.y, v.y, d.z * v.z));
+    const double ddw = k.D * fma(d.x, w.x, fma(d.y, w.y, d.z * w.z));
+    const double ex = k.G * d.x, ey = k.G * d.y, ez = k.G * d.z;
+    V.x = fma(k.A, v.x, fma(bdv, d.x, fma(w.y, ez, fma(-w.z, ey, V.x))));
+    V.y = fma(k.A, v.y, fma(bdv, d.y, fma(w.z, ex, fma(-w.x, ez, V.y))));
+    V.z = fma(k.A, v.z, fma(bdv, d.z, fma(w.x, ey, fma(-w.y, ex, V.z))));
+    W.x = fma(k.C, w.x, fma(ddw, d.x, fma(v.y, ez, fma(-v.z, ey, W.x))));
+    W.y = fma(k.C, w.y, fma(ddw, d.y, fma(v.z, ex, fma(-v.x, ez, W.y))));
+    W.z = fma(k.C, w.z, fma(ddw, d.z, fma(v.x, ey, fma(-v.y, ex, W.z))));
 }
 
 }  // namespace fil
