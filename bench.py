@@ -850,8 +850,8 @@ def run_suspension(args, fil, torch, world, rank, local):
             "roofline": pair_roofline(float(S) * S, pms, npl),
             "from": "the same state as the timed steps, same initial-guess rule"}
 
-        # ---- the other J0 policy (built every step / kept up to 4 steps) from st0 ----
-        other = 1 if args.j0_reuse > 1 else 4
+        # ---- the other J0 policy (built every step / kept up to 8 steps) from st0 ----
+        other = 1 if args.j0_reuse > 1 else 8
         mr = fil.Filaments(wl.seg_per_fil, precision=prec, stream=stream.cuda_stream, **params)
         mr.set_state(*st0)
         mr.set_external(Fext, None, follower)
@@ -1045,7 +1045,7 @@ def main():
     ap.add_argument("--extra", type=int, default=1,
                     help="1: also the nested records (variants, other configurations, oracle "
                          "comparison); 0: the headline suspension only (for profiling)")
-    ap.add_argument("--j0-reuse", type=int, default=4,
+    ap.add_argument("--j0-reuse", type=int, default=8,
                     help="keep J0 for up to this many steps (fil_set_j0_reuse; 1 = every step)")
     ap.add_argument("--j0", default="filament_rpy", choices=["filament_rpy", "drag"],
                     help="approximate Jacobian: filament RPY blocks (default) or App. B.2 drag")
