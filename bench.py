@@ -634,6 +634,7 @@ def run_suspension(args, fil, torch, world, rank, local):
     m.init_straight(base, t, mu, None)
     m.set_external(Fext, None, follower)
     m.set_j0_reuse(args.j0_reuse)
+    m.set_broyden_memory(args.broyden_memory)
     m.set_extrapolation(args.extrapolation)
     if args.steric > 0:
         m.set_steric(args.steric, 1.1)
@@ -829,6 +830,8 @@ def run_suspension(args, fil, torch, world, rank, local):
         mm.set_state(*st0)
         mm.set_external(Fext, None, follower)
         mm.set_extrapolation(args.extrapolation)
+        mm.set_j0_reuse(args.j0_reuse)
+        mm.set_broyden_memory(args.broyden_memory)
         netm = None
         if warm_mode is not None and net_note is None:
             netm = warmstart.load(max_batch=max(64, n_fil), stream=stream.cuda_stream)
@@ -848,7 +851,7 @@ def run_suspension(args, fil, torch, world, rank, local):
             "broyden_iters_per_step": float(np.mean(its_m)), "steps": args.steps,
             "precision": "mixed", "precision_note": PRECISION_NOTE["mixed"],
             "roofline": pair_roofline(float(S) * S, pms, npl),
-            "from": "the same state as the timed steps, same initial-guess rule"}
+            "from": "the same state as the timed steps, same initial-guess rule, J0 policy and Broyden memory"}
 
         # ---- the other J0 policy (built every step / kept up to 8 steps) from st0 ----
         other = 1 if args.j0_reuse > 1 else 8
@@ -856,6 +859,7 @@ def run_suspension(args, fil, torch, world, rank, local):
         mr.set_state(*st0)
         mr.set_external(Fext, None, follower)
         mr.set_j0_reuse(other)
+        mr.set_broyden_memory(args.broyden_memory)
         mr.set_extrapolation(args.extrapolation)
         netr = None
         if warm_mode is not None and net_note is None:
@@ -963,6 +967,7 @@ def run_suspension(args, fil, torch, world, rank, local):
                               else EXTRAP_NAME[args.extrapolation]),
             "initial_guess_note": net_note,
             "j0_reuse_max_age": args.j0_reuse,
+            "broyden_memory": args.broyden_memory,
             "steric_FS": args.steric if args.steric > 0 else None,
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "flushed between timed steps (256 MiB write)"},
@@ -1045,6 +1050,9 @@ def main():
     ap.add_argument("--extra", type=int, default=1,
                     help="1: also the nested records (variants, other configurations, oracle "
                          "comparison); 0: the headline suspension only (for profiling)")
+    ap.add_argument("--broyden-memory", type=int, default=0,
+                    help="Broyden pairs carried into the next step while J0 is kept "
+                         "(fil_set_broyden_memory; 0 = reset every step, the paper's choice)")
     ap.add_argument("--j0-reuse", type=int, default=8,
                     help="keep J0 for up to this many steps (fil_set_j0_reuse; 1 = every step)")
     ap.add_argument("--j0", default="filament_rpy", choices=["filament_rpy", "drag"],

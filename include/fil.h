@@ -352,6 +352,24 @@ fil_status fil_j0_stats(const fil_ctx *c, int64_t *builds, int64_t *reuses);
  * with. FIL_EINVAL for another value, FIL_ESTATE inside a step. */
 fil_status fil_set_extrapolation(fil_ctx *c, int32_t order);
 
+/* Broyden memory across timesteps. Algorithm 2 starts every step from
+ * H_0 = J0^{-1}; its rank-one corrections, which learn the coupling between
+ * filaments that the block-diagonal J0 leaves out, are discarded at the end of
+ * the step. With keep > 0, a step whose J0 is the previous step's (see
+ * fil_set_j0_reuse) starts instead from H_0 = J0^{-1} + sum_i c_i d_i^T over the
+ * last min(keep, k) pairs (c_i, d_i) of the previous step's H_k, so that its
+ * first iterate already uses them; the new step's updates are appended. The
+ * pairs are dropped whenever J0 is rebuilt, after fil_set_state,
+ * fil_init_straight or a failed step, and with tethered filaments. Like J0,
+ * H_0 only shapes the iterates: every step still converges to ||f||_inf <= tol a.
+ * keep = 0 (the default) is the paper's reset at every step. The call
+ * allocates device memory for max_iter + keep history pairs the first time it
+ * needs more than max_iter (its only allocation after fil_create besides
+ * fil_set_steric's cell grid). Contexts of one system only (FIL_EINVAL for an
+ * ensemble); FIL_EINVAL for keep < 0 or keep > max_iter, FIL_ESTATE inside a
+ * step, FIL_ENOMEM if the allocation fails. */
+fil_status fil_set_broyden_memory(fil_ctx *c, int32_t keep);
+
 /* The extrapolation in use (a fil_extrapolation_order value). */
 fil_status fil_extrapolation(const fil_ctx *c, int32_t *order);
 

@@ -855,19 +855,28 @@ def initial_guess(lay: Layout, state: State, tether: Tether | None = None, order
 
 
 def begin_step(lay: Layout, p: Params, state: State, ext: External | None, nthreads=1,
-               j0_model="drag", tether: Tether | None = None, order: int = 1):
+               j0_model="drag", tether: Tether | None = None, order: int = 1,
+               j0: "J0Solver | None" = None, memory=()):
     """Initial guess, J0 at it (LU-factored) and f(X_0): the set-up of Algorithm 2.
 
     j0_model 'drag' is App. B.2 as printed; 'rpy' keeps each filament's own
-    RPY blocks in f_0 (see jacobian0_general)."""
+    RPY blocks in f_0 (see jacobian0_general). j0: a J0Solver of an earlier
+    step to use instead (J0 kept across steps); memory: (c_i, d_i) pairs of an
+    earlier step's H_k carried into H_0 = J0^{-1} + sum c_i d_i^T (the carried
+    Broyden memory; the returned object's .solver is the J0 used)."""
     X0 = initial_guess(lay, state, tether, order)
-    blocks = jacobian0_tethered(lay, p, state, X0, tether, j0_model)
-    solver = J0Solver(lay, blocks)
+    if j0 is None:
+        blocks = jacobian0_tethered(lay, p, state, X0, tether, j0_model)
+        j0 = J0Solver(lay, blocks)
 
     def fun(X):
         return residual(lay, p, state, ext, X, nthreads, tether=tether)
 
-    return Broyden(fun, solver.solve, X0, p.tol * p.a)
+    br = Broyden(fun, j0.solve, X0, p.tol * p.a)
+    br.c = [np.array(c, dtype=np.float64) for c, _ in memory]
+    br.d = [np.array(d, dtype=np.float64) for _, d in memory]
+    br.solver = j0
+    return br
 
 
 def adaptive_fit(lay: Layout, state: State, X):

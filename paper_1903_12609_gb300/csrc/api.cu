@@ -340,7 +340,8 @@ fil_status fil_create_ensemble(const fil_params *p, int32_t n_sys, const int32_t
             f = f1;
         }
     }
-    c->sstride = c->max_iter + 8;
+    c->hist_cap = c->max_iter;
+    c->sstride = c->hist_cap + 8;
     c->active_h.assign(n_sys, 0);
     c->sys_iters_h.assign(n_sys, 0);
     c->finf_h.assign(n_sys, 0.0);
@@ -470,6 +471,7 @@ void fil_destroy(fil_ctx *c) {
     if (c->tether_mem) cudaFree(c->tether_mem);
     if (c->steric_count) cudaFree(c->steric_count);
     if (c->steric_bucket) cudaFree(c->steric_bucket);
+    if (c->bmem_mem) cudaFree(c->bmem_mem);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->prof_ev) {
         for (int i = 0; i < 2 * kProfMax; ++i) cudaEventDestroy(c->prof_ev[i]);
@@ -517,6 +519,7 @@ fil_status fil_set_state(fil_ctx *c, const double *Y, const double *q, const dou
     CK(cudaStreamSynchronize(c->stream));
     c->have_prev = Yprev ? 1 : 0;
     c->ylev = Yprev ? 1 : 0;
+    c->bmem_ok = 0;
     c->hist = 0;
     c->thist = 0;
     c->warm_corr_ok = 0;
@@ -566,6 +569,7 @@ fil_status fil_init_straight(fil_ctx *c, const double *base, const double *t, co
     CK(cudaStreamSynchronize(c->stream));
     c->have_prev = 0;
     c->ylev = 0;
+    c->bmem_ok = 0;
     c->hist = 0;
     c->warm_corr_ok = 0;
     c->in_step = 0;
@@ -798,8 +802,15 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net, bool force_j0 = fa
     if (s != FIL_OK) return s;
     c->finf_h = f0_sys;
     if (finf) *finf = f0;
-    c->k = 0;
-    CK(cudaMemsetAsync(c->d_k, 0, sizeof(int), c->stream));
+    // the previous step's history pairs are kept when this step keeps its J0
+    // (they extend that J0's inverse); the last commit's pairs are used once
+    const bool carry = c->bmem_keep > 0 && c->bmem_ok && c->j0_reused && c->n_sys == 1 &&
+                       !c->tether_on && c->k_last > 0;
+    const int m = carry ? std::min(c->bmem_keep, c->k_last) : 0;
+    c->bmem_ok = 0;
+    c->k = m;
+    c->k_carry = m;
+    if (m == 0) CK(cudaMemsetAsync(c->d_k, 0, sizeof(int), c->stream));
     drop_graphs(c);      // scheme weights, J0 and the active set may have changed
     c->iters_step = 0;
     c->in_step = 0;
@@ -813,7 +824,12 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net, bool force_j0 = fa
         CK(upload_active(c));
         if (c->n_sys > 1) CK(rpy_set_active(c));
         CK(j0_apply(c, c->fk, c->w, true));
+        if (m > 0) CK(broyden_carry(c, c->k_last - m, m, c->fk, c->w));
         CK(broyden_mask_inactive(c, c->w));
+    } else if (m > 0) {
+        c->k = 0;
+        c->k_carry = 0;
+        CK(cudaMemsetAsync(c->d_k, 0, sizeof(int), c->stream));
     }
     c->in_step = 1;
     return FIL_OK;
@@ -943,6 +959,8 @@ fil_status fil_broyden_commit(fil_ctx *c) {
     c->warm_corr_ok = 1;
     c->have_prev = 1;
     c->ylev = c->ylev < 2 ? c->ylev + 1 : 2;
+    c->k_last = c->k;
+    c->bmem_ok = 1;
     c->hist += 1;
     c->steps += 1;
     c->in_step = 0;
@@ -983,6 +1001,52 @@ fil_status fil_j0_stats(const fil_ctx *c, int64_t *builds, int64_t *reuses) {
     if (!c) return FIL_EINVAL;
     if (builds) *builds = c->j0_builds;
     if (reuses) *reuses = c->j0_reuses;
+    return FIL_OK;
+}
+
+fil_status fil_set_broyden_memory(fil_ctx *c, int32_t keep) {
+    if (!c) return FIL_EINVAL;
+    if (keep < 0 || keep > c->max_iter)
+        return set_err(c, FIL_EINVAL, "fil_set_broyden_memory: keep must be in [0, max_iter]");
+    if (c->n_sys > 1)
+        return set_err(c, FIL_EINVAL, "fil_set_broyden_memory: contexts of one system only");
+    if (c->in_step) return set_err(c, FIL_ESTATE, "fil_set_broyden_memory: a step is in progress");
+    CK(cudaSetDevice(c->device));
+    const int cap = c->max_iter + keep;
+    if (cap > c->hist_cap) {
+        // a larger history (C, D), its scalars and the dot-product partials
+        CK(cudaStreamSynchronize(c->stream));
+        const int64_t nX = c->lay.nX;
+        const size_t hb = c->C32 ? sizeof(float) : sizeof(double);
+        const int sstride = cap + 8;
+        auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+        const size_t bC = up((size_t)cap * nX * hb);
+        const size_t bS = up((size_t)c->n_sys * sstride * sizeof(double));
+        const size_t bS32 = up((size_t)c->n_sys * sstride * sizeof(float));
+        const size_t bR = up((size_t)(cap + 2) * c->red_blocks * sizeof(double));
+        char *mem = nullptr;
+        if (cudaMalloc(&mem, 2 * bC + bS + bS32 + bR) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, FIL_ENOMEM, "fil_set_broyden_memory: device allocation failed");
+        }
+        drop_graphs(c);     // captured launches hold the old buffers
+        if (c->C32) {
+            c->C32 = (float *)mem;
+            c->D32 = (float *)(mem + bC);
+        } else {
+            c->C = (double *)mem;
+            c->D = (double *)(mem + bC);
+        }
+        c->scal = (double *)(mem + 2 * bC);
+        c->scal32 = (float *)(mem + 2 * bC + bS);
+        c->red_part = (double *)(mem + 2 * bC + bS + bS32);
+        if (c->bmem_mem) cudaFree(c->bmem_mem);
+        c->bmem_mem = mem;
+        c->hist_cap = cap;
+        c->sstride = sstride;
+        c->bmem_ok = 0;       // the pairs of the last step stayed in the old buffers
+    }
+    c->bmem_keep = keep;
     return FIL_OK;
 }
 

@@ -181,6 +181,21 @@ __global__ void update_kernel(int64_t n, const int *__restrict__ dk,
 }
 
 __global__ void k_advance_kernel(int *dk) { *dk += 1; }
+__global__ void k_set_kernel(int *dk, int k) { *dk = k; }
+
+// w += sum_{l<k} c_l alpha_l (alpha_l = d_l . f in scal, system 0): the carried
+// part of H_0 f at the start of a step.
+template <typename H>
+__global__ void history_apply_kernel(int64_t n, const int *__restrict__ dk,
+                                     const double *__restrict__ scal,
+                                     const H *__restrict__ C, double *__restrict__ w) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = *dk;
+    double s = w[i];
+    for (int l = 0; l < k; ++l) s += (double)C[(int64_t)l * n + i] * scal[l];
+    w[i] = s;
+}
 
 __global__ void mask_inactive_kernel(int64_t n, const int *__restrict__ sys_of,
                                      const int *__restrict__ active, double *__restrict__ v) {
@@ -216,7 +231,7 @@ cudaError_t broyden_dots(fil_ctx *c) {
         dots_partial_kernel<double><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
             n, c->fn, c->fk, c->D, c->d_k, c->blk_beg, c->blk_sys,
             c->n_sys > 1 ? c->d_active : nullptr, c->red_part);
-    const int max_out = c->max_iter + 2;
+    const int max_out = c->hist_cap + 2;
     const int64_t jobs = (int64_t)c->n_sys * max_out;
     dots_final_kernel<<<(unsigned)((jobs + 7) / 8), 256, 0, c->stream>>>(
         c->n_sys, max_out, c->d_k, c->red_blocks, c->sys_blk_off, c->red_part, c->sstride, c->scal,
@@ -238,6 +253,42 @@ cudaError_t broyden_update(fil_ctx *c) {
             c->g, c->C, c->D, c->w, c->d_flags);
     k_advance_kernel<<<1, 1, 0, c->stream>>>(c->d_k);     // the next history slot
     c->n_launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t broyden_carry(fil_ctx *c, int from, int m, const double *f, double *w) {
+    const int64_t n = c->lay.nX;
+    const size_t vb = (size_t)n * (c->C32 ? sizeof(float) : sizeof(double));
+    char *C = c->C32 ? (char *)c->C32 : (char *)c->C;
+    char *D = c->D32 ? (char *)c->D32 : (char *)c->D;
+    // pair from + i -> i in increasing i: each copy reads a slot above the one
+    // it writes, never one already written
+    for (int i = 0; from > 0 && i < m; ++i) {
+        cudaError_t e = cudaMemcpyAsync(C + i * vb, C + (size_t)(from + i) * vb, vb,
+                                        cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(D + i * vb, D + (size_t)(from + i) * vb, vb,
+                                cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    k_set_kernel<<<1, 1, 0, c->stream>>>(c->d_k, m);
+    // alpha_i = d_i . f (outputs k and k + 1 come out zero with fn = fk = f)
+    if (c->C32)
+        dots_partial_kernel<float><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+            n, f, f, c->D32, c->d_k, c->blk_beg, c->blk_sys, nullptr, c->red_part);
+    else
+        dots_partial_kernel<double><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+            n, f, f, c->D, c->d_k, c->blk_beg, c->blk_sys, nullptr, c->red_part);
+    const int max_out = c->hist_cap + 2;
+    dots_final_kernel<<<(unsigned)((max_out + 7) / 8), 256, 0, c->stream>>>(
+        1, max_out, c->d_k, c->red_blocks, c->sys_blk_off, c->red_part, c->sstride, c->scal,
+        c->C32 ? c->scal32 : nullptr);
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (c->C32)
+        history_apply_kernel<float><<<grid, 256, 0, c->stream>>>(n, c->d_k, c->scal, c->C32, w);
+    else
+        history_apply_kernel<double><<<grid, 256, 0, c->stream>>>(n, c->d_k, c->scal, c->C, w);
+    c->n_launches += 4;
     return cudaGetLastError();
 }
 

@@ -123,6 +123,14 @@ struct fil_ctx {
     float *C32, *D32;      // the history in FP32 (mixed mode; C, D are then null)
     float *scal32;         // FP32 copy of scal for the FP32 history sums
     int sstride;
+    // Broyden history capacity (pairs; max_iter, or max_iter + keep after
+    // fil_set_broyden_memory) and the memory carried across steps
+    int hist_cap = 0;
+    int bmem_keep = 0;     // pairs kept for the next step (0: reset every step)
+    int bmem_ok = 0;       // the last commit left pairs 0..k_last-1 to carry
+    int k_last = 0;
+    int k_carry = 0;       // pairs this step started with
+    void *bmem_mem = nullptr;   // the allocation of the larger history, if made
     double *red_part;      // reduction partials, [(max_iter + 2) x red_blocks]
     int red_blocks;        // reduction blocks, each inside one system
     int *blk_sys;          // [red_blocks] system of a block
@@ -272,6 +280,9 @@ cudaError_t broyden_axpy_step(fil_ctx *c);                 // Xn = Xk - w
 cudaError_t broyden_dots(fil_ctx *c);                      // alpha_i, ndf2, dff
 cudaError_t broyden_update(fil_ctx *c);
 cudaError_t broyden_mask_inactive(fil_ctx *c, double *v);   // v = 0 in converged systems
+// carried memory at the start of a step: history pairs [from, from + m) moved
+// to [0, m), the device k set to m, and w += sum_{i<m} c_i (d_i . f)
+cudaError_t broyden_carry(fil_ctx *c, int from, int m, const double *f, double *w);
 cudaError_t warm_features(fil_ctx *c, const double *Xex, float *feat);
 cudaError_t warm_targets(fil_ctx *c, float *targ);
 cudaError_t warm_record_correction(fil_ctx *c);

@@ -38,7 +38,7 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_set_graph", "fil_autotune", "fil_set_steric", "fil_set_tether",
             "fil_get_tether", "fil_fma_peak", "fil_set_j0_reuse", "fil_j0_stats",
             "fil_set_pair_schedule", "fil_pair_schedule", "fil_set_extrapolation",
-            "fil_extrapolation"]
+            "fil_extrapolation", "fil_set_broyden_memory"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_SEG = 800, 256, 192, 32
 MLP_NPARAM = 256 * 800 + 256 + 2 * (256 * 256 + 256) + 192 * 256 + 192
 FIL_WARM_BEST_OF_TWO, FIL_WARM_PREDICTION_FIRST = 0, 1
@@ -96,6 +96,7 @@ def load_library(path=LIB_PATH):
         "fil_pair_schedule": [P, I32, I32, I32],
         "fil_j0_stats": [P, I64, I64],
         "fil_set_extrapolation": [P, ctypes.c_int32],
+        "fil_set_broyden_memory": [P, ctypes.c_int32],
         "fil_extrapolation": [P, I32],
         "fil_mlp_create": [ctypes.c_int64, P, ctypes.POINTER(P)],
         "fil_mlp_destroy": [P],
@@ -320,6 +321,10 @@ def fil_j0_stats(ctx):
 
 def fil_set_extrapolation(ctx, order):
     _check(ctx, _lib.fil_set_extrapolation(ctx, int(order)))
+
+
+def fil_set_broyden_memory(ctx, keep):
+    _check(ctx, _lib.fil_set_broyden_memory(ctx, int(keep)))
 
 
 def fil_extrapolation(ctx):

@@ -199,6 +199,9 @@ def test_ensemble_with_j0_reuse_stays_on_each_systems_trajectory(fil, j0):
         m.set_state(np.concatenate([s.Y for s in states]), np.concatenate([s.q for s in states]))
         m.set_external(np.concatenate([e.Fext for e in exts]), None, None)
         m.set_j0_reuse(3)
+        with pytest.raises(fil.FilError) as e:           # carried memory: one system only
+            m.set_broyden_memory(4)
+        assert e.value.status == fil.FIL_EINVAL
         Y = np.zeros((m.S, 3))
         for step in range(7):
             m.step()

@@ -526,3 +526,63 @@ def test_adaptive_extrapolation_matches_oracle(fil, model):
             thetas += [fo.fit_theta(pq) for pq in st.xfit.reshape(-1, 2) if pq[1] > 0]
     th = np.array(thetas)
     assert (th < 0.4).any() and (th > 0.9).any() and ((th > 0.05) & (th < 0.95)).any(), th
+
+
+@pytest.mark.parametrize("model", J0_MODELS)
+def test_carried_broyden_memory_matches_oracle(fil, model):
+    """fil_set_broyden_memory(6) with J0 kept across steps: every Broyden iterate
+    of 6 steps equals the oracle's (FP64), the oracle starting each step from
+    the J0 the library used (rebuilt where fil_j0_stats says it was) and from
+    the last 6 of the previous step's pairs; the library skips the update of
+    the iteration that converges, so that pair is not carried. The same
+    iteration counts, iterates within 1e-8 relative at tol 1e-6: a carried
+    pair d = df / |df| from the end of a converged step has |df| ~ tol, so the
+    two sides' ~1e-13 residual rounding differs in it by ~1e-13 / tol, and the
+    carried steps' iterates inherit that (measured: <= 7e-10 at tol 1e-6,
+    7e-7 at 1e-8, 3e-5 at 1e-11; without carried pairs 5e-13 at every tol)."""
+    keep = 6
+    lay, p, st, ext, _ = _system([20, 32, 11], 76, history=True, tol=1e-6, dt=0.15)
+    with _gpu(fil, lay, p, st, ext, j0=model[0]) as m:
+        m.set_j0_reuse(50)
+        m.set_broyden_memory(keep)
+        solver, mem = None, []
+        X = np.zeros(6 * lay.S)
+        f = np.zeros(6 * lay.S)
+        carried = 0
+        for j in range(6):
+            builds = m.j0_stats()[0]
+            f0 = m.broyden_begin()
+            rebuilt = m.j0_stats()[0] > builds
+            if rebuilt:
+                solver, mem = None, []
+            br = fo.begin_step(lay, p, st, ext, j0_model=model[1], j0=solver,
+                               memory=mem[-keep:])
+            carried += 0 if rebuilt else len(mem[-keep:])
+            assert abs(f0 - np.abs(br.f).max()) <= 1e-12 * max(1, np.abs(st.Y).max())
+            conv = f0 <= p.tol * p.a
+            while not conv:
+                conv, _ = m.broyden_step()
+                br.iterate()
+                m.get_iterate(X, f)
+                sc = np.abs(br.X).max()
+                np.testing.assert_allclose(X, br.X, rtol=0, atol=1e-8 * sc)
+                assert conv == br.converged(), (j, br.k)
+            m.broyden_commit()
+            solver = br.solver
+            mem = list(zip(br.c, br.d))[:-1] if br.k > 0 else []
+            st = fo.commit_step(lay, p, st, br.X)
+        assert carried > 0, "no step started from carried pairs"
+
+
+def test_broyden_memory_argument_checks(fil):
+    lay, p, st, ext, _ = _system([16] * 2, 77, tol=1e-10)
+    with _gpu(fil, lay, p, st, ext) as m:
+        for bad in (-1, p.max_iter + 1):
+            with pytest.raises(fil.FilError) as e:
+                m.set_broyden_memory(bad)
+            assert e.value.status == fil.FIL_EINVAL
+        m.set_broyden_memory(3)
+        m.broyden_begin()
+        with pytest.raises(fil.FilError) as e:
+            m.set_broyden_memory(2)
+        assert e.value.status == fil.FIL_ESTATE

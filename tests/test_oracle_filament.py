@@ -643,3 +643,63 @@ def test_adaptive_guess_keeps_the_solution():
         end[order], its[order] = st.Y, n
     np.testing.assert_allclose(end[fo.ADAPTIVE], end[1], rtol=0, atol=1e-7)
     assert its[fo.ADAPTIVE] <= its[1], its
+
+
+# --------------------------------------------------------------------------
+# Broyden memory carried across steps (an option; the paper resets H_0 = J0^{-1})
+# --------------------------------------------------------------------------
+
+def _carry_system(seed):
+    rng = np.random.default_rng(seed)
+    lay = fo.Layout([8, 8, 8])
+    p = _params(KB=2.0, KT=2.0, dt=0.2, tol=1e-11)
+    st = _random_filament_state(rng, lay, p, twist=0.05)
+    st.Y = st.Y + np.repeat(np.array([[0.0, 0, 0], [9.0, 0, 0], [0, 9.0, 0]]), 8, axis=0)
+    ext = fo.External(Fext=np.tile([0, 0, -1.5], (lay.S, 1)), follower=np.array([0.3, 0.0, 0.1]))
+    return lay, p, st, ext
+
+
+def test_carried_memory_starts_from_the_previous_inverse():
+    """With every pair of a converged step carried and its J0 kept, the next
+    step's H_0 is the previous step's final H: it satisfies that step's last
+    secant equation H dF = dX (bad Broyden's H_{k+1} does) to rounding, more
+    than a thousand times closer than J0^{-1} alone."""
+    lay, p, st, ext = _carry_system(40)
+    st, _ = fo.step(lay, p, st, ext, j0_model="rpy")            # a BDF2 history
+    br = fo.begin_step(lay, p, st, ext, j0_model="rpy")
+    Xs, fs = [br.X.copy()], [br.f.copy()]
+    while not br.converged():
+        br.iterate()
+        Xs.append(br.X.copy())
+        fs.append(br.f.copy())
+    assert br.k >= 3
+    dX, dF = Xs[-1] - Xs[-2], fs[-1] - fs[-2]
+    st2 = fo.commit_step(lay, p, st, br.X)
+    nxt = fo.begin_step(lay, p, st2, ext, j0=br.solver, memory=list(zip(br.c, br.d)))
+    err_h = np.abs(nxt.H(dF) - dX).max()
+    err_j0 = np.abs(br.solver.solve(dF) - dX).max()
+    assert err_h <= 1e-14 * np.abs(br.X).max() and err_h < 1e-3 * err_j0, (err_h, err_j0)
+
+
+def test_carried_memory_keeps_the_solution():
+    """Eight steps with J0 kept and the previous step's pairs carried (at most
+    12, the most recent) against the same steps with H_0 = J0^{-1}: the same
+    positions to within a few tolerances. (Whether it saves iterations depends
+    on how much coupling between filaments J0 leaves out: here, three distant
+    filaments, it does not; on large clouds it does.)"""
+    lay, p, st0, ext = _carry_system(41)
+    st0, _ = fo.step(lay, p, st0, ext, j0_model="rpy")
+    ends, its = {}, {}
+    for keep in (0, 12):
+        st, solver, mem, n = st0, None, [], 0
+        for j in range(8):
+            br = fo.begin_step(lay, p, st, ext, j0_model="rpy", j0=solver,
+                               memory=mem[-keep:] if keep else ())
+            while not br.converged():
+                br.iterate()
+                n += 1
+            solver, mem = br.solver, list(zip(br.c, br.d))
+            st = fo.commit_step(lay, p, st, br.X)
+        ends[keep], its[keep] = st.Y, n
+    np.testing.assert_allclose(ends[12], ends[0], rtol=0, atol=1e-8)
+    assert its[12] > 8 and its[0] > 8, its
