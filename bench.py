@@ -597,7 +597,7 @@ def run_tether(fil, torch, steps=20, warmup=5, every=4, order=1):
     S = 32000.0
     return {"metric": "timesteps/s", "value": steps / (ms * 1e-3), "unit": "timesteps/s",
             "steps": steps, "broyden_iters_per_step": float(np.mean(iters)),
-            "warmup_iters": warm_iters,
+            "iters": [int(i) for i in iters], "warmup_iters": warm_iters,
             "pairs_per_s": (a1 - a0) * S * S / (ms * 1e-3), "dtype": "f32+f64",
             "config": {"workload": "the 32k suspension's cloud (1000 x 32) with %d filaments "
                                    "(every %d-th) clamped at the base, no gravity, tip follower "
@@ -1050,7 +1050,7 @@ def main():
     ap.add_argument("--extra", type=int, default=1,
                     help="1: also the nested records (variants, other configurations, oracle "
                          "comparison); 0: the headline suspension only (for profiling)")
-    ap.add_argument("--broyden-memory", type=int, default=0,
+    ap.add_argument("--broyden-memory", type=int, default=48,
                     help="Broyden pairs carried into the next step while J0 is kept "
                          "(fil_set_broyden_memory; 0 = reset every step, the paper's choice)")
     ap.add_argument("--j0-reuse", type=int, default=8,
@@ -1112,9 +1112,11 @@ def main():
         run_peaks(args, fil)
     elif args.workload == "ensemble":
         run_ensemble(args, fil, torch)
-    elif args.workload in ("c0", "c1", "tether"):
-        fn = {"c0": run_c0_single, "c1": run_c1_mobility, "tether": run_tether}[args.workload]
-        print(json.dumps(fn(fil, torch)), flush=True)
+    elif args.workload == "c1":
+        print(json.dumps(run_c1_mobility(fil, torch)), flush=True)
+    elif args.workload in ("c0", "tether"):
+        fn = {"c0": run_c0_single, "tether": run_tether}[args.workload]
+        print(json.dumps(fn(fil, torch, order=args.extrapolation)), flush=True)
     else:
         run_suspension(args, fil, torch, world, rank, local)
 
