@@ -428,6 +428,7 @@ def run_ensemble(args, fil, torch, nested=False):
     m.set_external(Fext, None, follower)
     m.set_graph(args.graph)
     m.set_j0_reuse(args.j0_reuse)
+    m.set_broyden_memory(args.ens_broyden_memory)
     m.set_extrapolation(args.extrapolation)
     for _ in range(args.warmup):
         m.step()
@@ -508,6 +509,7 @@ def run_ensemble(args, fil, torch, nested=False):
                        PRECISION_NOTE[args.ens_precision],
                    "j0_reuse_max_age": args.j0_reuse,
                    "initial_guess": EXTRAP_NAME[args.extrapolation],
+                   "broyden_memory": args.ens_broyden_memory,
                    "pairs_per_apply": pairs_per_apply, "parallelism": "single"},
         "pairs_per_s": pairs / (ms * 1e-3),
         "ensemble_timesteps_per_s": steps / (ms * 1e-3),
@@ -1071,6 +1073,9 @@ def main():
     ap.add_argument("--ens-steps", type=int, default=10,
                     help="timed steps of the ensemble record of the default run")
     ap.add_argument("--ens-precision", default="mixed", choices=["pair32", "mixed", "fp64"])
+    ap.add_argument("--ens-broyden-memory", type=int, default=0,
+                    help="Broyden pairs carried across steps in the ensemble (measured slower "
+                         "there: the slowest system's iterations rise)")
     ap.add_argument("--tune", type=int, default=0,
                     help="autotune the suspension's pair-kernel schedule after the warm-up steps "
                          "(its default schedule is the tuned one)")

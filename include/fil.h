@@ -365,8 +365,9 @@ fil_status fil_set_extrapolation(fil_ctx *c, int32_t order);
  * keep = 0 (the default) is the paper's reset at every step. The call
  * allocates device memory for max_iter + keep history pairs the first time it
  * needs more than max_iter (its only allocation after fil_create besides
- * fil_set_steric's cell grid). Contexts of one system only (FIL_EINVAL for an
- * ensemble); FIL_EINVAL for keep < 0 or keep > max_iter, FIL_ESTATE inside a
+ * fil_set_steric's cell grid). In an ensemble each system keeps its own pairs
+ * (a system that converged before the others has zero rows in the later
+ * pairs). FIL_EINVAL for keep < 0 or keep > max_iter, FIL_ESTATE inside a
  * step, FIL_ENOMEM if the allocation fails. */
 fil_status fil_set_broyden_memory(fil_ctx *c, int32_t keep);
 

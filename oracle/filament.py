@@ -902,13 +902,15 @@ def adaptive_fit(lay: Layout, state: State, X):
 
 
 def commit_step(lay: Layout, p: Params, state: State, X, tether: Tether | None = None,
-                order: int = 1):
+                order: int = 1, iterated: bool = True):
     """q^{j+1} = exp(u*) q^j, Y^{j+1} from the robot arm, and the history shift.
     u^{j-1}, Lambda^{j-1} (and the tether multipliers of the step before) are
     kept only when they came from a committed step; with order ADAPTIVE the
-    fit of the next guess is updated (adaptive_fit)."""
+    fit of the next guess is updated (adaptive_fit) unless the step took no
+    Broyden iteration (iterated False: X is the guess itself, which says
+    nothing about the guess's error)."""
     X, lam1, lam2 = tether_resolve(lay, X, tether)
-    xfit = adaptive_fit(lay, state, X) if order == ADAPTIVE else state.xfit
+    xfit = adaptive_fit(lay, state, X) if order == ADAPTIVE and iterated else state.xfit
     q, t, Y, u, lam = unpack(lay, p, X, state.q)
     stepped = state.steps >= 1
     tlam = np.concatenate([lam1, lam2], axis=1) if tether is not None else None
@@ -932,7 +934,7 @@ def step(lay: Layout, p: Params, state: State, ext: External | None, nthreads=1,
         if br.k >= p.max_iter:
             raise RuntimeError("Broyden did not converge in %d iterations" % p.max_iter)
         br.iterate()
-    return commit_step(lay, p, state, br.X, tether, order), br.k
+    return commit_step(lay, p, state, br.X, tether, order, iterated=br.k > 0), br.k
 
 
 def initial_state(lay: Layout, p: Params, base, t_fil, mu_fil, xi=None, lam=None):

@@ -124,6 +124,7 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
     c->uprev3 = ar.take<double>(3 * S);
     c->lamprev2 = ar.take<double>(3 * (nlam > 0 ? nlam : 1));
     c->xfit = ar.take<double>(6 * M);
+    c->d_iterated = ar.take<int>(c->n_sys);
     c->Fext = ar.take<double>(3 * S);
     c->Text = ar.take<double>(3 * S);
     c->follower = ar.take<double>(M);
@@ -804,8 +805,8 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net, bool force_j0 = fa
     if (finf) *finf = f0;
     // the previous step's history pairs are kept when this step keeps its J0
     // (they extend that J0's inverse); the last commit's pairs are used once
-    const bool carry = c->bmem_keep > 0 && c->bmem_ok && c->j0_reused && c->n_sys == 1 &&
-                       !c->tether_on && c->k_last > 0;
+    const bool carry = c->bmem_keep > 0 && c->bmem_ok && c->j0_reused && !c->tether_on &&
+                       c->k_last > 0;
     const int m = carry ? std::min(c->bmem_keep, c->k_last) : 0;
     c->bmem_ok = 0;
     c->k = m;
@@ -1008,8 +1009,6 @@ fil_status fil_set_broyden_memory(fil_ctx *c, int32_t keep) {
     if (!c) return FIL_EINVAL;
     if (keep < 0 || keep > c->max_iter)
         return set_err(c, FIL_EINVAL, "fil_set_broyden_memory: keep must be in [0, max_iter]");
-    if (c->n_sys > 1)
-        return set_err(c, FIL_EINVAL, "fil_set_broyden_memory: contexts of one system only");
     if (c->in_step) return set_err(c, FIL_ESTATE, "fil_set_broyden_memory: a step is in progress");
     CK(cudaSetDevice(c->device));
     const int cap = c->max_iter + keep;

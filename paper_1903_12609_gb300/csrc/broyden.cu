@@ -154,11 +154,15 @@ __global__ void update_kernel(int64_t n, const int *__restrict__ dk,
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int sy = sys_of[i / 6];
+    const int k = *dk;
     if (!active[sy]) {
+        // a converged system takes no step and no history pair (zero rows, so
+        // that carried pairs hold nothing stale for it)
         w[i] = 0.0;
+        C[(int64_t)k * n + i] = (H)0;
+        D[(int64_t)k * n + i] = (H)0;
         return;
     }
-    const int k = *dk;
     const double *scal = scal_all + (int64_t)sy * sstride;
     const double ndf2 = scal[k];
     if (!(ndf2 > 0.0)) flags[0] = 1;
@@ -183,15 +187,17 @@ __global__ void update_kernel(int64_t n, const int *__restrict__ dk,
 __global__ void k_advance_kernel(int *dk) { *dk += 1; }
 __global__ void k_set_kernel(int *dk, int k) { *dk = k; }
 
-// w += sum_{l<k} c_l alpha_l (alpha_l = d_l . f in scal, system 0): the carried
-// part of H_0 f at the start of a step.
+// w += sum_{l<k} c_l alpha_l (alpha_l = d_l . f in the scalars of entry i's
+// system): the carried part of H_0 f at the start of a step.
 template <typename H>
 __global__ void history_apply_kernel(int64_t n, const int *__restrict__ dk,
-                                     const double *__restrict__ scal,
-                                     const H *__restrict__ C, double *__restrict__ w) {
+                                     const double *__restrict__ scal_all, int sstride,
+                                     const int *__restrict__ sys_of, const H *__restrict__ C,
+                                     double *__restrict__ w) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int k = *dk;
+    const double *scal = scal_all + (int64_t)sys_of[i / 6] * sstride;
     double s = w[i];
     for (int l = 0; l < k; ++l) s += (double)C[(int64_t)l * n + i] * scal[l];
     w[i] = s;
@@ -280,14 +286,17 @@ cudaError_t broyden_carry(fil_ctx *c, int from, int m, const double *f, double *
         dots_partial_kernel<double><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
             n, f, f, c->D, c->d_k, c->blk_beg, c->blk_sys, nullptr, c->red_part);
     const int max_out = c->hist_cap + 2;
-    dots_final_kernel<<<(unsigned)((max_out + 7) / 8), 256, 0, c->stream>>>(
-        1, max_out, c->d_k, c->red_blocks, c->sys_blk_off, c->red_part, c->sstride, c->scal,
-        c->C32 ? c->scal32 : nullptr);
+    const int64_t jobs = (int64_t)c->n_sys * max_out;
+    dots_final_kernel<<<(unsigned)((jobs + 7) / 8), 256, 0, c->stream>>>(
+        c->n_sys, max_out, c->d_k, c->red_blocks, c->sys_blk_off, c->red_part, c->sstride,
+        c->scal, c->C32 ? c->scal32 : nullptr);
     const unsigned grid = (unsigned)((n + 255) / 256);
     if (c->C32)
-        history_apply_kernel<float><<<grid, 256, 0, c->stream>>>(n, c->d_k, c->scal, c->C32, w);
+        history_apply_kernel<float><<<grid, 256, 0, c->stream>>>(n, c->d_k, c->scal, c->sstride,
+                                                                  c->lay.sys_of, c->C32, w);
     else
-        history_apply_kernel<double><<<grid, 256, 0, c->stream>>>(n, c->d_k, c->scal, c->C, w);
+        history_apply_kernel<double><<<grid, 256, 0, c->stream>>>(n, c->d_k, c->scal, c->sstride,
+                                                                   c->lay.sys_of, c->C, w);
     c->n_launches += 4;
     return cudaGetLastError();
 }

@@ -75,6 +75,7 @@ struct fil_ctx {
     int ylev;              // past Y levels held (Yprev, Yprev2): 0..2
     int extrap_order = 1;  // FIL_EXTRAP_LINEAR / _QUADRATIC / _ADAPTIVE
     double *xfit;          // adaptive fit (P, Q) per filament and block (Y_1, u, Lambda): 6M
+    int *d_iterated;       // [n_sys] whether a system took a Broyden iteration this step
     int64_t steps;
 
     // external loads

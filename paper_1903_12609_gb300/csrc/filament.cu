@@ -11,6 +11,8 @@
 // segment for the element-wise residual rows.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "fil_internal.cuh"
 #include "quat.cuh"
 
@@ -305,8 +307,10 @@ __device__ __forceinline__ void fit_terms(const double *xs, const double *x0, co
 // Adaptive fit at a commit (before the history shift): for each filament and
 // block (Y_1, u, Lambda) whose last three values exist (y_ok, u_ok),
 // P <- kFitDecay P + <x* - l, d>, Q <- kFitDecay Q + <d, d> over the block's
-// 3-vectors, x* the committed solution X. One warp per filament, lane sums
-// combined by a fixed shuffle tree.
+// 3-vectors, x* the committed solution X; filaments of a system that took no
+// Broyden iteration this step (iterated[system] = 0: x* is the guess itself and
+// says nothing about its error) keep their fit. One warp per filament, lane
+// sums combined by a fixed shuffle tree.
 constexpr double kFitDecay = 0.7;
 
 __global__ void extrap_fit_kernel(Layout lay, const double *__restrict__ X,
@@ -318,11 +322,12 @@ __global__ void extrap_fit_kernel(Layout lay, const double *__restrict__ X,
                                   const double *__restrict__ lam,
                                   const double *__restrict__ lamprev,
                                   const double *__restrict__ lamprev2, int y_ok, int u_ok,
-                                  double *__restrict__ xfit) {
+                                  const int *__restrict__ iterated, double *__restrict__ xfit) {
     const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= lay.M) return;
     const int s0 = lay.off[i];
+    if (!iterated[lay.sys_of[s0]]) return;     // the whole warp leaves together
     const int N = lay.off[i + 1] - s0;
     const double *Xf = X + 6 * (int64_t)s0;
     double fu[2] = {0, 0}, fl[2] = {0, 0};
@@ -454,10 +459,17 @@ cudaError_t commit_state(fil_ctx *c, const double *X) {
     if (e != cudaSuccess) return e;
     if (c->extrap_order == FIL_EXTRAP_ADAPTIVE) {
         // the fit needs the three values before this commit: Y_1 once two past
-        // levels are held, u and Lambda once three steps were committed
+        // levels are held, u and Lambda once three steps were committed; and
+        // which systems iterated this step
+        std::vector<int> iterated(c->n_sys);
+        for (int s = 0; s < c->n_sys; ++s) iterated[s] = c->sys_iters_h[s] > 0 ? 1 : 0;
+        e = cudaMemcpyAsync(c->d_iterated, iterated.data(), sizeof(int) * c->n_sys,
+                            cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return e;
         extrap_fit_kernel<<<warp_grid(c->lay.M, 128), 128, 0, c->stream>>>(
             c->lay, X, c->Y, c->Yprev, c->Yprev2, c->uprev, c->uprev2, c->uprev3, c->lam,
-            c->lamprev, c->lamprev2, c->ylev >= 2 ? 1 : 0, c->hist >= 3 ? 1 : 0, c->xfit);
+            c->lamprev, c->lamprev2, c->ylev >= 2 ? 1 : 0, c->hist >= 3 ? 1 : 0, c->d_iterated,
+            c->xfit);
         c->n_launches += 1;
     }
     commit_kernel<<<seg_grid(c->lay.S, 256), 256, 0, c->stream>>>(

@@ -522,7 +522,7 @@ def test_adaptive_extrapolation_matches_oracle(fil, model):
             while not br.converged():
                 br.iterate()
             assert n == br.k, (k, n, br.k)
-            st = fo.commit_step(lay, p, st, br.X, order=fo.ADAPTIVE)
+            st = fo.commit_step(lay, p, st, br.X, order=fo.ADAPTIVE, iterated=br.k > 0)
             thetas += [fo.fit_theta(pq) for pq in st.xfit.reshape(-1, 2) if pq[1] > 0]
     th = np.array(thetas)
     assert (th < 0.4).any() and (th > 0.9).any() and ((th > 0.05) & (th < 0.95)).any(), th

@@ -703,3 +703,18 @@ def test_carried_memory_keeps_the_solution():
         ends[keep], its[keep] = st.Y, n
     np.testing.assert_allclose(ends[12], ends[0], rtol=0, atol=1e-8)
     assert its[12] > 8 and its[0] > 8, its
+
+
+def test_adaptive_fit_skips_a_step_without_iterations():
+    """A commit whose solution is the guess itself (no Broyden iteration)
+    leaves the fit as it was; the same commit counted as iterated moves it."""
+    lay, first, series = _two_filament_history()
+    st, X = _history_state(lay, first, series, [("quad", "noisy", "quad"),
+                                                ("noisy", "quad", "noisy")])
+    st.xfit = np.full((lay.M, 3, 2), 0.5)
+    st.q = fo.qmul(fo.qexp(np.zeros((lay.S, 3))), st.q)
+    p = _params()
+    kept = fo.commit_step(lay, p, st, X, order=fo.ADAPTIVE, iterated=False)
+    np.testing.assert_array_equal(kept.xfit, st.xfit)
+    moved = fo.commit_step(lay, p, st, X, order=fo.ADAPTIVE, iterated=True)
+    assert np.abs(moved.xfit - st.xfit).max() > 0.1
