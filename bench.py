@@ -556,7 +556,7 @@ def host_round_trip(torch, n=2000):
     return 1e6 * dt / n
 
 
-def run_tether(fil, torch, steps=20, warmup=5, every=4, order=1):
+def run_tether(fil, torch, steps=40, warmup=5, every=4, order=1):
     """The 32k suspension's cloud with every fourth filament clamped at its base
     (Sec. 5.2.1: Y_1 fixed, u_1 = 0), weightless: the follower-force half keeps
     its tip force, the other half is passive. (With gravity the cloud settles
