@@ -810,7 +810,6 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net, bool force_j0 = fa
     const int m = carry ? std::min(c->bmem_keep, c->k_last) : 0;
     c->bmem_ok = 0;
     c->k = m;
-    c->k_carry = m;
     if (m == 0) CK(cudaMemsetAsync(c->d_k, 0, sizeof(int), c->stream));
     drop_graphs(c);      // scheme weights, J0 and the active set may have changed
     c->iters_step = 0;
@@ -829,7 +828,6 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net, bool force_j0 = fa
         CK(broyden_mask_inactive(c, c->w));
     } else if (m > 0) {
         c->k = 0;
-        c->k_carry = 0;
         CK(cudaMemsetAsync(c->d_k, 0, sizeof(int), c->stream));
     }
     c->in_step = 1;

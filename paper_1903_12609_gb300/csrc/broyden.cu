@@ -79,7 +79,10 @@ __device__ __forceinline__ void dots_group(const H *__restrict__ D, int64_t n, i
 }
 
 // Outputs o = 0..k-1: d_o . fn;  o = k: |fn - fk|^2;  o = k+1: (fn - fk) . fn,
-// over the X slice [blk_beg[b], blk_beg[b+1]) of block b. Outputs are taken
+// over the X slice [blk_beg[b], blk_beg[b+1]) of block column b. Row y = 0 of
+// the grid takes the last two, row y >= 1 the outputs 8(y-1) .. 8(y-1)+7 (rows
+// past k leave at once), so a long history is read by many blocks at a time;
+// each output's sum is the same whichever row computes it. Outputs are taken
 // in compile-time groups so that every FP64 instruction is useful work.
 template <typename H>
 __global__ void dots_partial_kernel(int64_t n, const double *__restrict__ fn,
@@ -92,7 +95,7 @@ __global__ void dots_partial_kernel(int64_t n, const double *__restrict__ fn,
     const int k = *dk;
     const int nb = gridDim.x;
     const int64_t i0 = blk_beg[blockIdx.x], i1 = blk_beg[blockIdx.x + 1];
-    {
+    if (blockIdx.y == 0) {
         double acc[2] = {0.0, 0.0};
         for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             const double f = fn[i];
@@ -102,11 +105,11 @@ __global__ void dots_partial_kernel(int64_t n, const double *__restrict__ fn,
         }
         const int o[2] = {k, k + 1};
         block_reduce_write<2>(acc, sh, o, nb, part);
+        return;
     }
-    int o0 = 0;
-    for (; o0 + kDotGroup <= k; o0 += kDotGroup)
-        dots_group<kDotGroup, H>(D, n, o0, fn, i0, i1, sh, nb, part);
-    switch (k - o0) {
+    const int o0 = (int)(blockIdx.y - 1) * kDotGroup;
+    if (o0 >= k) return;
+    switch (k - o0 < kDotGroup ? k - o0 : kDotGroup) {
         case 1: dots_group<1, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
         case 2: dots_group<2, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
         case 3: dots_group<3, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
@@ -114,7 +117,7 @@ __global__ void dots_partial_kernel(int64_t n, const double *__restrict__ fn,
         case 5: dots_group<5, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
         case 6: dots_group<6, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
         case 7: dots_group<7, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
-        default: break;
+        default: dots_group<kDotGroup, H>(D, n, o0, fn, i0, i1, sh, nb, part); break;
     }
 }
 
@@ -209,6 +212,13 @@ __global__ void mask_inactive_kernel(int64_t n, const int *__restrict__ sys_of,
     if (i < n && !active[sys_of[i / 6]]) v[i] = 0.0;
 }
 
+// Grid of dots_partial_kernel: a column per X slice, a row for the two
+// step outputs and one per group of kDotGroup history outputs (the history
+// holds at most hist_cap pairs; rows past the current k leave at once).
+dim3 dots_grid(const fil_ctx *c) {
+    return dim3((unsigned)c->red_blocks, (unsigned)(1 + (c->hist_cap + kDotGroup - 1) / kDotGroup));
+}
+
 }  // namespace
 
 cudaError_t broyden_mask_inactive(fil_ctx *c, double *v) {
@@ -230,11 +240,11 @@ cudaError_t broyden_axpy_step(fil_ctx *c) {
 cudaError_t broyden_dots(fil_ctx *c) {
     const int64_t n = c->lay.nX;
     if (c->C32)
-        dots_partial_kernel<float><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+        dots_partial_kernel<float><<<dots_grid(c), kRedThreads, 0, c->stream>>>(
             n, c->fn, c->fk, c->D32, c->d_k, c->blk_beg, c->blk_sys,
             c->n_sys > 1 ? c->d_active : nullptr, c->red_part);
     else
-        dots_partial_kernel<double><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+        dots_partial_kernel<double><<<dots_grid(c), kRedThreads, 0, c->stream>>>(
             n, c->fn, c->fk, c->D, c->d_k, c->blk_beg, c->blk_sys,
             c->n_sys > 1 ? c->d_active : nullptr, c->red_part);
     const int max_out = c->hist_cap + 2;
@@ -280,10 +290,10 @@ cudaError_t broyden_carry(fil_ctx *c, int from, int m, const double *f, double *
     k_set_kernel<<<1, 1, 0, c->stream>>>(c->d_k, m);
     // alpha_i = d_i . f (outputs k and k + 1 come out zero with fn = fk = f)
     if (c->C32)
-        dots_partial_kernel<float><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+        dots_partial_kernel<float><<<dots_grid(c), kRedThreads, 0, c->stream>>>(
             n, f, f, c->D32, c->d_k, c->blk_beg, c->blk_sys, nullptr, c->red_part);
     else
-        dots_partial_kernel<double><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+        dots_partial_kernel<double><<<dots_grid(c), kRedThreads, 0, c->stream>>>(
             n, f, f, c->D, c->d_k, c->blk_beg, c->blk_sys, nullptr, c->red_part);
     const int max_out = c->hist_cap + 2;
     const int64_t jobs = (int64_t)c->n_sys * max_out;

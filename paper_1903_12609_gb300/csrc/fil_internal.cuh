@@ -130,7 +130,6 @@ struct fil_ctx {
     int bmem_keep = 0;     // pairs kept for the next step (0: reset every step)
     int bmem_ok = 0;       // the last commit left pairs 0..k_last-1 to carry
     int k_last = 0;
-    int k_carry = 0;       // pairs this step started with
     void *bmem_mem = nullptr;   // the allocation of the larger history, if made
     double *red_part;      // reduction partials, [(max_iter + 2) x red_blocks]
     int red_blocks;        // reduction blocks, each inside one system
