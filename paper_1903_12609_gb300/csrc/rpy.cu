@@ -666,14 +666,23 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
         const int64_t c_end = min(n_chunks, c_begin + (u_end - u));
         const double *srcs = src + 9 * src0;
         const int64_t ptile = smap.tile_id ? smap.tile_id[tile] : tile;
+        // real sources of the tile's system (its padding follows them): padded
+        // sources carry no load and padded targets are never read, so both are
+        // left out (a small system would otherwise cost a whole padded tile x
+        // chunk at the FP64 rate)
+        const int64_t nsrc = smap.tile_nsrc ? smap.tile_nsrc[tile] : smap.n_src;
 
         double ty[TPT][3];
+        bool live[TPT];
+        bool any = false;
 #pragma unroll
         for (int t = 0; t < TPT; ++t) {
             const int64_t n = ptile * kTile + t * kRpyThreads + tid;
             ty[t][0] = src[9 * n];
             ty[t][1] = src[9 * n + 1];
             ty[t][2] = src[9 * n + 2];
+            live[t] = n - src0 < nsrc;
+            any = any || live[t];
         }
         double acc[TPT][6];
 #pragma unroll
@@ -699,11 +708,12 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
                 }
             }
             const double *s = sm[buf];
+            const int jmax = any ? (int)min((int64_t)kRpyChunk, nsrc - ch * kRpyChunk) : 0;
 #pragma unroll 2
-            for (int j = 0; j < kRpyChunk; ++j) {
+            for (int j = 0; j < jmax; ++j) {
 #pragma unroll
                 for (int t = 0; t < TPT; ++t)
-                    pair64(ty[t][0], ty[t][1], ty[t][2], s + 9 * j, k, acc[t]);
+                    if (live[t]) pair64(ty[t][0], ty[t][1], ty[t][2], s + 9 * j, k, acc[t]);
             }
             if (has_next) {
 #pragma unroll
