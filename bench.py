@@ -638,6 +638,7 @@ def run_suspension(args, fil, torch, world, rank, local):
     m.set_j0_reuse(args.j0_reuse)
     m.set_broyden_memory(args.broyden_memory)
     m.set_extrapolation(args.extrapolation)
+    m.set_graph(args.graph)
     if args.steric > 0:
         m.set_steric(args.steric, 1.1)
 
