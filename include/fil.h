@@ -341,7 +341,9 @@ fil_status fil_j0_stats(const fil_ctx *c, int64_t *builds, int64_t *reuses);
  * by least squares over the past commits: at each commit, with x* the block's
  * solution and l, d the linear guess and second difference it was predicted
  * from, P <- 0.7 P + <x* - l, d> and Q <- 0.7 Q + <d, d>; theta = P / Q clipped
- * to [0, 1] (0, i.e. linear, until a block has been fitted).
+ * to [0, 1] (0, i.e. linear, until a block has been fitted); a step that took
+ * no Broyden iteration (its solution is the guess itself) leaves the fit as it
+ * was.
  * With fewer committed values the order drops to what they allow: Y_1 uses
  * Y^j, Y^{j-1} (held from the first committed step on, or given to
  * fil_set_state) and Y^{j-2}; u and Lambda use the values of committed steps
@@ -363,9 +365,10 @@ fil_status fil_set_extrapolation(fil_ctx *c, int32_t order);
  * fil_init_straight or a failed step, and with tethered filaments. Like J0,
  * H_0 only shapes the iterates: every step still converges to ||f||_inf <= tol a.
  * keep = 0 (the default) is the paper's reset at every step. The call
- * allocates device memory for max_iter + keep history pairs the first time it
- * needs more than max_iter (its only allocation after fil_create besides
- * fil_set_steric's cell grid). In an ensemble each system keeps its own pairs
+ * allocates device memory for max_iter + keep history pairs when that is more
+ * than the context holds (the pairs of the last step are then not carried);
+ * besides fil_set_steric's cell grid it is the only allocation after
+ * fil_create. In an ensemble each system keeps its own pairs
  * (a system that converged before the others has zero rows in the later
  * pairs). FIL_EINVAL for keep < 0 or keep > max_iter, FIL_ESTATE inside a
  * step, FIL_ENOMEM if the allocation fails. */
