@@ -856,8 +856,8 @@ def run_suspension(args, fil, torch, world, rank, local):
             "roofline": pair_roofline(float(S) * S, pms, npl),
             "from": "the same state as the timed steps, same initial-guess rule, J0 policy and Broyden memory"}
 
-        # ---- the other J0 policy (built every step / kept up to 8 steps) from st0 ----
-        other = 1 if args.j0_reuse > 1 else 8
+        # ---- the other J0 policy (built every step / kept up to 10 steps) from st0 ----
+        other = 1 if args.j0_reuse > 1 else 10
         mr = fil.Filaments(wl.seg_per_fil, precision=prec, stream=stream.cuda_stream, **params)
         mr.set_state(*st0)
         mr.set_external(Fext, None, follower)
@@ -1056,7 +1056,7 @@ def main():
     ap.add_argument("--broyden-memory", type=int, default=48,
                     help="Broyden pairs carried into the next step while J0 is kept "
                          "(fil_set_broyden_memory; 0 = reset every step, the paper's choice)")
-    ap.add_argument("--j0-reuse", type=int, default=8,
+    ap.add_argument("--j0-reuse", type=int, default=10,
                     help="keep J0 for up to this many steps (fil_set_j0_reuse; 1 = every step)")
     ap.add_argument("--j0", default="filament_rpy", choices=["filament_rpy", "drag"],
                     help="approximate Jacobian: filament RPY blocks (default) or App. B.2 drag")
