@@ -556,7 +556,7 @@ def host_round_trip(torch, n=2000):
     return 1e6 * dt / n
 
 
-def run_tether(fil, torch, steps=40, warmup=5, every=4, order=1):
+def run_tether(fil, torch, steps=40, warmup=5, every=4, order=1, j0_reuse=1, memory=0):
     """The 32k suspension's cloud with every fourth filament clamped at its base
     (Sec. 5.2.1: Y_1 fixed, u_1 = 0), weightless: the follower-force half keeps
     its tip force, the other half is passive. (With gravity the cloud settles
@@ -565,14 +565,16 @@ def run_tether(fil, torch, steps=40, warmup=5, every=4, order=1):
     Algorithm 2 with the per-filament J0 does not converge on it at 1000
     filaments, on the GPU or in the oracle.) FIL_PAIR32, extrapolated initial
     guess of the given order (tether multipliers linear; the network refuses
-    tethered contexts), J0 built every step (the tethered J0 follows the
-    prescribed motion)."""
+    tethered contexts); the clamps are set once, so J0 may be kept for up to
+    j0_reuse steps and `memory` Broyden pairs carried while it is."""
     wl, base, t, mu, Fext, follower = workload(1000, 32, seed=0)
     stream = torch.cuda.Stream()
     m = fil.Filaments(wl.seg_per_fil, precision=fil.FIL_PAIR32, stream=stream.cuda_stream,
                       a=wl.a, eta=wl.eta, dL=wl.dL, KB=wl.KB, KT=wl.KT, dt=wl.dt, tol=wl.tol,
                       max_iter=wl.max_iter, j0_model=fil.FIL_J0_FILAMENT_RPY)
     m.set_extrapolation(order)
+    m.set_j0_reuse(j0_reuse)
+    m.set_broyden_memory(memory)
     m.init_straight(base, t, mu, None)
     m.set_external(None, None, follower)
     mask = (np.arange(1000) % every) == 0
@@ -607,7 +609,8 @@ def run_tether(fil, torch, steps=40, warmup=5, every=4, order=1):
                                    "dt=T/200, tol 1e-4" % (int(mask.sum()), every),
                        "precision": "pair32",
                        "initial_guess": EXTRAP_NAME[order],
-                       "j0": "filament_rpy + rank-6 correction per clamped filament, every step"},
+                       "j0": "filament_rpy + rank-6 correction per clamped filament",
+                       "j0_reuse_max_age": j0_reuse, "broyden_memory": memory},
             "roofline": pair_roofline(S * S, pair_ms, n_pair),
             "max_abs_multiplier": float(np.abs(lam[mask]).max()),
             "gpu_launches": int(k1 - k0), "clocks": clocks}
@@ -929,7 +932,9 @@ def run_suspension(args, fil, torch, world, rank, local):
                          lambda: run_c0_single(fil, torch, order=args.extrapolation)),
                         ("c3_ensemble256", lambda: run_ensemble(args, fil, torch, nested=True)),
                         ("tethered_suspension",
-                         lambda: run_tether(fil, torch, order=args.extrapolation))):
+                         lambda: run_tether(fil, torch, order=args.extrapolation,
+                                            j0_reuse=args.j0_reuse,
+                                            memory=args.broyden_memory))):
             try:
                 extra[key] = fn()
             except Exception as exc:   # keep the headline line when a nested record fails
@@ -1121,8 +1126,12 @@ def main():
     elif args.workload == "c1":
         print(json.dumps(run_c1_mobility(fil, torch)), flush=True)
     elif args.workload in ("c0", "tether"):
-        fn = {"c0": run_c0_single, "tether": run_tether}[args.workload]
-        print(json.dumps(fn(fil, torch, order=args.extrapolation)), flush=True)
+        if args.workload == "c0":
+            rec = run_c0_single(fil, torch, order=args.extrapolation)
+        else:
+            rec = run_tether(fil, torch, order=args.extrapolation, j0_reuse=args.j0_reuse,
+                             memory=args.broyden_memory)
+        print(json.dumps(rec), flush=True)
     else:
         run_suspension(args, fil, torch, world, rank, local)
 

@@ -315,8 +315,9 @@ fil_status fil_set_dt(fil_ctx *c, double dt);
  * all, and build new ones earlier when the last committed step took more than
  * one Broyden iteration more than the step that built them, when the scheme
  * weight times dt changed (first step, fil_set_dt), after fil_set_state or
- * fil_init_straight, and with tethered filaments (whose J0 columns follow the
- * prescribed motion). fil_step restarts a step that fails on reused factors
+ * fil_init_straight, and after every fil_set_tether (tethered J0 columns follow
+ * the prescribed motion; a prescription set once, such as a clamp, lets J0 be
+ * kept). fil_step restarts a step that fails on reused factors
  * with factors built for it. max_age = 1 (the default) builds J0 every step.
  * FIL_EINVAL for max_age < 1, FIL_ESTATE inside a step. */
 fil_status fil_set_j0_reuse(fil_ctx *c, int32_t max_age);
@@ -361,8 +362,8 @@ fil_status fil_set_extrapolation(fil_ctx *c, int32_t order);
  * fil_set_j0_reuse) starts instead from H_0 = J0^{-1} + sum_i c_i d_i^T over the
  * last min(keep, k) pairs (c_i, d_i) of the previous step's H_k, so that its
  * first iterate already uses them; the new step's updates are appended. The
- * pairs are dropped whenever J0 is rebuilt, after fil_set_state,
- * fil_init_straight or a failed step, and with tethered filaments. Like J0,
+ * pairs are dropped whenever J0 is rebuilt (so also after every
+ * fil_set_tether), after fil_set_state, fil_init_straight or a failed step. Like J0,
  * H_0 only shapes the iterates: every step still converges to ||f||_inf <= tol a.
  * keep = 0 (the default) is the paper's reset at every step. The call
  * allocates device memory for max_iter + keep history pairs when that is more

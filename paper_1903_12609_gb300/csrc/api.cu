@@ -783,7 +783,9 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net, bool force_j0 = fa
     // weight is unchanged and the iteration count has not risen (J0 only
     // shapes the iterates; the converged X solves f(X) = 0 either way)
     const double weight = (c->have_prev ? 2.0 / 3.0 : 1.0) * c->dt;
-    c->j0_reused = !force_j0 && c->j0_reuse_max > 1 && !c->tether_on && c->j0_age >= 1 &&
+    // (with tethers: while their prescription is the one J0 was built with)
+    c->j0_reused = !force_j0 && c->j0_reuse_max > 1 && !(c->tether_on && c->tether_fresh) &&
+                   c->j0_age >= 1 &&
                    c->j0_age < c->j0_reuse_max && weight == c->j0_weight &&
                    c->j0_last_iters <= c->j0_iters_ref + 1;
     if (!c->j0_reused) {
@@ -794,6 +796,7 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net, bool force_j0 = fa
         c->j0_age = 0;
         c->j0_weight = weight;
         c->j0_builds += 1;
+        c->tether_fresh = 0;
     } else {
         c->j0_reuses += 1;
     }
@@ -805,8 +808,7 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net, bool force_j0 = fa
     if (finf) *finf = f0;
     // the previous step's history pairs are kept when this step keeps its J0
     // (they extend that J0's inverse); the last commit's pairs are used once
-    const bool carry = c->bmem_keep > 0 && c->bmem_ok && c->j0_reused && !c->tether_on &&
-                       c->k_last > 0;
+    const bool carry = c->bmem_keep > 0 && c->bmem_ok && c->j0_reused && c->k_last > 0;
     const int m = carry ? std::min(c->bmem_keep, c->k_last) : 0;
     c->bmem_ok = 0;
     c->k = m;
@@ -1225,6 +1227,7 @@ fil_status fil_set_tether(fil_ctx *c, const int32_t *mask, const double *Y1, con
     }
     CK(cudaStreamSynchronize(c->stream));
     c->tether_on = any;
+    c->tether_fresh = 1;      // the next step builds J0 for this prescription
     return FIL_OK;
 }
 

@@ -128,6 +128,7 @@ struct fil_ctx {
     // fil_set_broyden_memory) and the memory carried across steps
     int hist_cap = 0;
     int bmem_keep = 0;     // pairs kept for the next step (0: reset every step)
+    int tether_fresh = 0;  // fil_set_tether was called since J0 was last built
     int bmem_ok = 0;       // the last commit left pairs 0..k_last-1 to carry
     int k_last = 0;
     void *bmem_mem = nullptr;   // the allocation of the larger history, if made

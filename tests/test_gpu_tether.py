@@ -154,9 +154,34 @@ def _motor(N=20, w=0.05, Sp=30.0):
 
 
 @pytest.mark.parametrize("model", J0_MODELS)
+def test_tether_set_once_keeps_j0_and_the_trajectory(fil, model):
+    """A tether prescription set once (the same Y_1 and u_1 for every step)
+    lets J0 be kept (fil_set_j0_reuse) and the Broyden pairs be carried
+    (fil_set_broyden_memory): every step stays on the oracle's trajectory (J0
+    built and memory reset every step) to the accuracy the tolerance gives,
+    and setting the tether again makes the next step build J0."""
+    lay, p, st, ext, teth, _ = _system([16, 9, 20], 41, tol=1e-10, dt=0.1)
+    with _gpu(fil, lay, p, st, ext, teth, j0=model[0]) as m:
+        m.set_j0_reuse(5)
+        m.set_broyden_memory(8)
+        Y = np.zeros((lay.S, 3))
+        for _ in range(8):
+            st, _ = fo.step(lay, p, st, ext, j0_model=model[1], tether=teth)
+            m.step()
+            m.get_state(Y, None, None, None, None)
+            np.testing.assert_allclose(Y, st.Y, rtol=0, atol=1e-8)
+        builds, reuses = m.j0_stats()
+        assert reuses >= 3, (builds, reuses)
+        m.set_tether(teth.mask, teth.Y1, teth.u1)
+        m.step()
+        assert m.j0_stats()[0] == builds + 1
+
+
+@pytest.mark.parametrize("model", J0_MODELS)
 def test_motor_steps_match_oracle(fil, model):
     """Motor steps against the oracle; J0 reuse is requested and must not apply
-    (the tethered J0 columns follow the prescribed motion of every step)."""
+    (the prescription is set anew for every step, and the tethered J0 columns
+    follow it)."""
     lay, p, st, tether = _motor()
     with _gpu(fil, lay, p, st, None, tether(1), j0=model[0]) as m:
         m.set_j0_reuse(5)
