@@ -155,12 +155,16 @@ def _motor(N=20, w=0.05, Sp=30.0):
 
 @pytest.mark.parametrize("model", J0_MODELS)
 def test_tether_set_once_keeps_j0_and_the_trajectory(fil, model):
-    """A tether prescription set once (the same Y_1 and u_1 for every step)
-    lets J0 be kept (fil_set_j0_reuse) and the Broyden pairs be carried
-    (fil_set_broyden_memory): every step stays on the oracle's trajectory (J0
-    built and memory reset every step) to the accuracy the tolerance gives,
-    and setting the tether again makes the next step build J0."""
+    """A tether prescription set once (two filaments clamped where their first
+    segments are: Y_1 held, u_1 = 0) lets J0 be kept (fil_set_j0_reuse) and
+    the Broyden pairs be carried (fil_set_broyden_memory): every step stays on
+    the oracle's trajectory (J0 built and memory reset every step) to the
+    accuracy the tolerance gives, and setting the tether again makes the next
+    step build J0."""
     lay, p, st, ext, teth, _ = _system([16, 9, 20], 41, tol=1e-10, dt=0.1)
+    first = [lay.off_seg[i] for i in range(lay.M)]
+    teth = fo.Tether(mask=teth.mask, Y1=np.array([st.Y[k] for k in first]),
+                     u1=np.zeros((lay.M, 3)))
     with _gpu(fil, lay, p, st, ext, teth, j0=model[0]) as m:
         m.set_j0_reuse(5)
         m.set_broyden_memory(8)
