@@ -1076,7 +1076,7 @@ def main():
                     help="learned warm start of each step (the committed network) and its mode")
     ap.add_argument("--n-sys", type=int, default=256, help="systems of the ensemble workload")
     ap.add_argument("--ens-max-iter", type=int, default=100)
-    ap.add_argument("--ens-steps", type=int, default=10,
+    ap.add_argument("--ens-steps", type=int, default=40,
                     help="timed steps of the ensemble record of the default run")
     ap.add_argument("--ens-precision", default="mixed", choices=["pair32", "mixed", "fp64"])
     ap.add_argument("--ens-broyden-memory", type=int, default=0,
