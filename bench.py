@@ -268,7 +268,7 @@ def run_mobility(args, fil, torch):
 # roofline, clocks and the FP64-oracle comparison.
 # ---------------------------------------------------------------------------
 
-def run_c1_mobility(fil, torch, applies=1000, per_graph=100, min_seconds=1.0):
+def run_c1_mobility(fil, torch, applies=1000, per_graph=100, min_seconds=1.0, schedule=None):
     """Mobility apply alone: 100 random-walk filaments x 32 segments (3200) at
     5% volume fraction, N(0,1) loads, 1000 repeated applies. At this size an
     apply takes tens of microseconds, less than the host needs to issue it, so
@@ -276,14 +276,19 @@ def run_c1_mobility(fil, torch, applies=1000, per_graph=100, min_seconds=1.0):
     allocates nothing and does not synchronise with device arrays) and the
     graph is replayed; the schedule is autotuned for the size first. The
     1000-apply batch is repeated until the timed region lasts min_seconds
-    (for the clock record)."""
+    (for the clock record). `schedule` ('tile,targets_per_thread,ctas_per_sm')
+    sets the pair schedule by hand instead."""
     from paper_1903_12609_gb300.inputs import mobility_inputs
     Y, FT = mobility_inputs(100, 32, seed=0)
     S = Y.shape[0]
     stream = torch.cuda.Stream()
     m = fil.Filaments([32] * 100, precision=fil.FIL_PAIR32, stream=stream.cuda_stream)
     m.set_state(Y, np.tile([1.0, 0.0, 0.0, 0.0], (S, 1)))
-    tuned = m.autotune(50)
+    if schedule:
+        m.set_pair_schedule(*[int(x) for x in schedule.split(",")])
+        tuned = (m.pair_schedule()[0], m.pair_schedule()[2], None)
+    else:
+        tuned = m.autotune(50)
     schedule = m.pair_schedule()
     Yd = torch.from_numpy(Y).cuda()
     FTd = torch.from_numpy(FT).cuda()
@@ -334,7 +339,7 @@ def run_c1_mobility(fil, torch, applies=1000, per_graph=100, min_seconds=1.0):
             "config": {"workload": "mobility apply alone: 100 random-walk filaments x 32 "
                                    "segments (3200), bond 2.2a, 5% volume fraction, F,T ~ N(0,1)",
                        "segments": S, "precision": "FP32 pair sums (compensated), FP64 results",
-                       "issue": "CUDA graph of %d applies (pack, pair, reduce kernels), replayed"
+                       "issue": "CUDA graph of %d applies (pack and pair kernels), replayed"
                                 % per_graph,
                        "l2": "inputs L2-resident (3200 segments); the metric is the apply "
                              "itself, repeated"},
@@ -1090,6 +1095,9 @@ def main():
     ap.add_argument("--ens-schedule", default=None,
                     help="set the ensemble's pair schedule 'tile,targets_per_thread,ctas_per_sm' "
                          "instead of autotuning it (e.g. for a profile of the tuned schedule)")
+    ap.add_argument("--c1-schedule", default=None,
+                    help="set the 3200-segment apply's pair schedule "
+                         "'tile,targets_per_thread,ctas_per_sm' instead of autotuning it")
     ap.add_argument("--steric", type=float, default=0.0,
                     help="steric barrier strength F^S (Sec. 2.6, chi = 1.1); 0 = off")
     ap.add_argument("--graph", type=int, default=0,
@@ -1124,7 +1132,7 @@ def main():
     elif args.workload == "ensemble":
         run_ensemble(args, fil, torch)
     elif args.workload == "c1":
-        print(json.dumps(run_c1_mobility(fil, torch)), flush=True)
+        print(json.dumps(run_c1_mobility(fil, torch, schedule=args.c1_schedule)), flush=True)
     elif args.workload in ("c0", "tether"):
         if args.workload == "c0":
             rec = run_c0_single(fil, torch, order=args.extrapolation)

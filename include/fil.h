@@ -132,13 +132,16 @@ fil_status fil_create_ensemble(const fil_params *p, int32_t n_sys, const int32_t
  * current / last step and the last ||f||_inf that was read. */
 fil_status fil_sys_stats(const fil_ctx *c, int32_t *iters, double *finf);
 
-/* Autotuner of the RPY pair kernel: times the pair and reduce kernels of `reps`
- * mobility applies of the current state's loads (CUDA events around them, so
- * host launch gaps do not count) for every candidate schedule -- tiles of 256 targets
- * (2 per thread) or 128 targets (1 per thread), and 1..occupancy resident
- * CTAs per SM for the stream-K split of the (tile, source chunk) work units --
- * and keeps the fastest for all later applies. Reports the choice (nullable
- * outputs) and its pair + reduce time per apply in ms. Results change only in rounding (the
+/* Autotuner of the RPY pair kernel: times the pair kernel (which also sums
+ * each tile's partials) of `reps` mobility applies of the current state's
+ * loads (CUDA events around it, so host launch gaps do not count) for every
+ * candidate schedule -- tiles of 256 targets (2 per thread) or 128 targets
+ * (1 per thread), and 1..occupancy resident CTAs per SM for the stream-K split
+ * of the (tile, source chunk) work units -- and keeps the fastest for all
+ * later applies. The applies first run for 50 ms of wall time (an idle GPU's
+ * clock is still rising then) and the candidates are swept twice, each
+ * keeping its faster time. Reports the choice (nullable outputs) and its
+ * pair-kernel time per apply in ms. Results change only in rounding (the
  * summation order of the pair terms). FIL_ESTATE inside a step. */
 fil_status fil_autotune(fil_ctx *c, int32_t reps, int32_t *tile, int32_t *ctas_per_sm,
                         double *ms);
@@ -361,8 +364,9 @@ fil_status fil_set_extrapolation(fil_ctx *c, int32_t order);
  * the step. With keep > 0, a step whose J0 is the previous step's (see
  * fil_set_j0_reuse) starts instead from H_0 = J0^{-1} + sum_i c_i d_i^T over the
  * last min(keep, k) pairs (c_i, d_i) of the previous step's H_k, so that its
- * first iterate already uses them; the new step's updates are appended. The
- * pairs are dropped whenever J0 is rebuilt (so also after every
+ * first iterate already uses them; the new step's updates are appended. A
+ * step that converges on entry ends with H_k = H_0, so the pairs it carried
+ * are the ones it passes on. The pairs are dropped whenever J0 is rebuilt (so also after every
  * fil_set_tether), after fil_set_state, fil_init_straight or a failed step. Like J0,
  * H_0 only shapes the iterates: every step still converges to ||f||_inf <= tol a.
  * keep = 0 (the default) is the paper's reset at every step. The call

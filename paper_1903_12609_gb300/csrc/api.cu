@@ -142,6 +142,7 @@ void carve(fil_ctx *c, Arena &ar, int red_blocks, size_t partial_bytes) {
         c->src32 = nullptr;
     }
     c->partials = ar.take<char>(partial_bytes);
+    c->tile_cnt = ar.take<int>(c->rpy_tiles_max);
     c->Xk = ar.take<double>(nX);
     c->fk = ar.take<double>(nX);
     c->Xn = ar.take<double>(nX);
@@ -811,6 +812,7 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net, bool force_j0 = fa
     const bool carry = c->bmem_keep > 0 && c->bmem_ok && c->j0_reused && c->k_last > 0;
     const int m = carry ? std::min(c->bmem_keep, c->k_last) : 0;
     c->bmem_ok = 0;
+    c->k_hold = 0;
     c->k = m;
     if (m == 0) CK(cudaMemsetAsync(c->d_k, 0, sizeof(int), c->stream));
     drop_graphs(c);      // scheme weights, J0 and the active set may have changed
@@ -829,7 +831,11 @@ fil_status begin_step(fil_ctx *c, double *finf, bool use_net, bool force_j0 = fa
         if (m > 0) CK(broyden_carry(c, c->k_last - m, m, c->fk, c->w));
         CK(broyden_mask_inactive(c, c->w));
     } else if (m > 0) {
+        // converged on entry: this step's H_k is its H_0, whose pairs are the
+        // ones it would have carried; nothing moved them, so the commit leaves
+        // them for the next step (which carries them if it keeps J0 too)
         c->k = 0;
+        c->k_hold = c->k_last;
         CK(cudaMemsetAsync(c->d_k, 0, sizeof(int), c->stream));
     }
     c->in_step = 1;
@@ -960,7 +966,8 @@ fil_status fil_broyden_commit(fil_ctx *c) {
     c->warm_corr_ok = 1;
     c->have_prev = 1;
     c->ylev = c->ylev < 2 ? c->ylev + 1 : 2;
-    c->k_last = c->k;
+    c->k_last = c->k_hold > 0 ? c->k_hold : c->k;
+    c->k_hold = 0;
     c->bmem_ok = 1;
     c->hist += 1;
     c->steps += 1;

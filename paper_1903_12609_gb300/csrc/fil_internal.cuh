@@ -97,6 +97,7 @@ struct fil_ctx {
     double *src64;        // 12 doubles per (padded) segment, FP64 path
     int64_t Spad;
     void *partials;       // stream-K partial sums
+    int *tile_cnt;        // per listed tile: work units whose partial is written (zero between launches)
     int rpy_grid32, rpy_grid64;
     int64_t rpy_tiles, rpy_units;
     std::vector<int64_t> sys_pad_off_h, tile_unit_off_h, tile_src_h, tile_nsrc_h, pos_of_seg_h;
@@ -131,6 +132,7 @@ struct fil_ctx {
     int tether_fresh = 0;  // fil_set_tether was called since J0 was last built
     int bmem_ok = 0;       // the last commit left pairs 0..k_last-1 to carry
     int k_last = 0;
+    int k_hold = 0;        // a step that converged on entry keeps k_last (its pairs) for the next
     void *bmem_mem = nullptr;   // the allocation of the larger history, if made
     double *red_part;      // reduction partials, [(max_iter + 2) x red_blocks]
     int red_blocks;        // reduction blocks, each inside one system

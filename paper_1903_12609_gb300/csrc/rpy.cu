@@ -32,9 +32,10 @@
 //    one-source form).
 //  * Stream-K persistent grid: the (tile, chunk) work units are split evenly
 //    over G = #SMs x resident-CTAs; a CTA writes one partial per tile it
-//    touches into slot (cta + tile) and a deterministic reduce kernel sums
-//    them (eight warps per 32 targets, each over a fixed stride of CTAs,
-//    combined in warp order). No atomics: results are bitwise reproducible.
+//    touches into slot (cta + tile), and the CTA that completes a tile (a
+//    counter per tile) sums its partials in CTA order and writes the tile's
+//    rows, in the same launch. The order of the sums never depends on timing:
+//    results are bitwise reproducible.
 //  * Mixed precision: positions are stored as FP32 hi/lo pairs (hi = fl32(Y),
 //    lo = fl32(Y - hi)). The inner loop forms d from the hi parts alone,
 //    which carries the rounding of the coordinates (~ulp(|Y|)) and is
@@ -43,7 +44,7 @@
 //    recomputed with d = (t_hi - s_hi) + (t_lo - s_lo), which keeps ~2 ulp of
 //    relative accuracy for close pairs. Each target sums kRpyComp pair terms
 //    in FP32 and folds them into a (hi, lo) compensated accumulator (TwoSum);
-//    the reduce adds the partials in FP64.
+//    the tile's sum adds the partials in FP64.
 //  * The inner loop is branch-free (far form only, tracking the smallest r^2);
 //    close pairs are rare. A recomputed group in which a warp met an
 //    overlapping pair (r < 2a) is computed once more with the exact far /
@@ -51,8 +52,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <vector>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 
 #include "fil_internal.cuh"
@@ -413,6 +416,105 @@ __device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
 }
 
 // ---------------------------------------------------------------------------
+// Completion of a tile: the stream-K partials of its targets are summed and
+// scaled by 1/(8 pi eta) inside the pair kernel, by the CTA that finishes the
+// tile's last work unit, so that no separate reduce launch follows the pair
+// kernel and the sums of early tiles overlap the pair work of late ones.
+// Every CTA that wrote a partial of the tile adds the units it covered to the
+// tile's counter (one acquire-release atomic after a barrier, which orders
+// the whole CTA's stores before it); the CTA whose addition completes
+// the tile's unit count reads the partials of all the tile's CTAs (from L2),
+// adds them in CTA order -- the same order whichever CTA came last, so results
+// do not depend on timing -- writes the targets' rows of VW and sets the
+// counter back to zero for the next launch.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cta_range_of_tile(const SysMap &sm, int64_t tile, int64_t W,
+                                                  int64_t G, int64_t &u0, int64_t &u1,
+                                                  int64_t &b0, int64_t &b1) {
+    // CTA b owns units [floor(bW/G), floor((b+1)W/G)); the CTA that holds unit
+    // u is ceil((u+1)G/W) - 1.
+    u0 = tile_unit_begin(sm, tile);
+    u1 = tile_unit_begin(sm, tile + 1) - 1;
+    b0 = ((u0 + 1) * G + W - 1) / W - 1;
+    b1 = ((u1 + 1) * G + W - 1) / W - 1;
+}
+
+// fetch-and-add with acquire-release semantics at GPU scope: its release
+// covers the writes the CTA's threads made before the preceding barrier, its
+// acquire the reads they make after the following one
+__device__ __forceinline__ int fetch_add_acq_rel(int *p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;"
+                 : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+template <typename PT, int NPART, int TPT>
+__device__ __forceinline__ void finish_tile(const PT *part, const SysMap &smap, int64_t tile,
+                                            int64_t ptile, int64_t units, int64_t n_chunks,
+                                            int64_t W, int64_t G, int *__restrict__ cnt,
+                                            double scale, double *__restrict__ VW) {
+    constexpr int kTile = kRpyThreads * TPT;
+    __shared__ int s_last;
+    const int tid = threadIdx.x;
+    __syncthreads();   // the CTA's partial is written before it is counted
+    if (tid == 0)
+        s_last = fetch_add_acq_rel(cnt + tile, (int)units) + (int)units == (int)n_chunks;
+    __syncthreads();
+    if (!s_last) return;
+    int64_t u0, u1, b0, b1;
+    cta_range_of_tile(smap, tile, W, G, u0, u1, b0, b1);
+    // With G > W (a fixed grid over a short active list) a CTA owns at most one
+    // unit and some own none: the tile's CTAs are then the owners of its units.
+    const bool by_unit = G > W;
+    const int64_t n_parts = by_unit ? u1 - u0 + 1 : b1 - b0 + 1;
+    // FP32 partials (hi, lo) are added in float-float arithmetic (TwoSum of the
+    // hi parts, the lo parts added to its error, renormalised by a second
+    // TwoSum: ~2^-44 relative, far below the 2^-24 of the pair terms) and
+    // converted to FP64 once per target: the whole tile's sum runs on one SM,
+    // and on GB300 the FP64 pipe has 1/64 of the FP32 rate.
+    // FP64 partials are added in FP64.
+    using Acc = typename std::conditional<NPART == 2, float, double>::type;
+    Acc ah[TPT][6], al[TPT][6];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) ah[t][c] = al[t][c] = (Acc)0;
+#pragma unroll 4
+    for (int64_t i = 0; i < n_parts; ++i) {
+        const int64_t cb = by_unit ? ((u0 + i + 1) * G + W - 1) / W - 1 : b0 + i;
+        const PT *p = part + (size_t)(cb + tile) * (6 * NPART) * kTile;
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            const int local = t * kRpyThreads + tid;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                if constexpr (NPART == 2) {
+                    const float h = __ldcg(p + c * kTile + local);
+                    const float l = __ldcg(p + (6 + c) * kTile + local);
+                    float sh, e;
+                    two_sum(ah[t][c], h, sh, e);
+                    e = __fadd_rn(e, __fadd_rn(al[t][c], l));
+                    two_sum(sh, e, ah[t][c], al[t][c]);
+                } else {
+                    ah[t][c] += (double)__ldcg(p + c * kTile + local);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int64_t n = segment_at(smap, ptile * kTile + t * kRpyThreads + tid, smap.n_src);
+        if (n >= 0) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+                VW[6 * n + c] = ((double)ah[t][c] + (double)al[t][c]) * scale;
+        }
+    }
+    if (tid == 0) cnt[tile] = 0;
+}
+
+// ---------------------------------------------------------------------------
 // Mixed-precision pair kernel. A CTA of kRpyThreads threads owns a tile of
 // kRpyThreads * TPT targets, TPT per thread; their pair terms are summed in
 // registers over groups of kRpyComp sources with the branch-free far form and
@@ -431,7 +533,8 @@ __device__ __forceinline__ int64_t unit_start(int64_t b, int64_t W, int64_t G) {
 template <int TPT>
 __global__ void __launch_bounds__(kRpyThreads, TPT == 2 ? kRpyMinBlocksTpt2 : kRpyMinBlocksTpt1)
 rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G, RpyConst32 k,
-                  float *__restrict__ part) {
+                  float *__restrict__ part, int *__restrict__ cnt, double scale,
+                  double *__restrict__ VW) {
     constexpr int kRec = kRpyPairF4 * (kRpyChunk / 2);   // float4 per chunk
     constexpr int kT = TPT;                               // targets per thread
     constexpr int kTile = kRpyThreads * TPT;              // targets per tile
@@ -639,6 +742,8 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
                 p[(6 + c) * kTile + local] = lo[t][c];
             }
         }
+        finish_tile<float, 2, TPT>(part, smap, tile, ptile, c_end - c_begin, n_chunks, W, G, cnt,
+                                   scale, VW);
         u = ubeg + c_end;
     }
 }
@@ -649,7 +754,8 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
 template <int TPT>
 __global__ void __launch_bounds__(kRpyThreads)
 rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G, RpyConst64 k,
-                  double *__restrict__ part) {
+                  double *__restrict__ part, int *__restrict__ cnt, double scale,
+                  double *__restrict__ VW) {
     constexpr int kRec = 9 * kRpyChunk;
     constexpr int kTile = kRpyThreads * TPT;
     __shared__ double sm[2][kRec];
@@ -731,113 +837,10 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
 #pragma unroll
             for (int c = 0; c < 6; ++c) p[c * kTile + local] = acc[t][c];
         }
+        finish_tile<double, 1, TPT>(part, smap, tile, ptile, c_end - c_begin, n_chunks, W, G, cnt,
+                                    scale, VW);
         u = ubeg + c_end;
     }
-}
-
-// ---------------------------------------------------------------------------
-// Reduce the stream-K partials of each target and scale by 1/(8 pi eta)
-// (kRedWarps threads per target, see reduce_targets).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void cta_range_of_tile(const SysMap &sm, int64_t tile, int64_t W,
-                                                  int64_t G, int64_t &b0, int64_t &b1) {
-    // CTA b owns units [floor(bW/G), floor((b+1)W/G)); the CTA that holds unit
-    // u is ceil((u+1)G/W) - 1. With G > W (a fixed grid over a short active
-    // list) CTAs between two owners may own nothing: the reduce skips them.
-    const int64_t u0 = tile_unit_begin(sm, tile);
-    const int64_t u1 = tile_unit_begin(sm, tile + 1) - 1;
-    b0 = ((u0 + 1) * G + W - 1) / W - 1;
-    b1 = ((u1 + 1) * G + W - 1) / W - 1;
-}
-
-// A block of rw = blockDim.x / 32 warps reduces 32 consecutive targets: lane t
-// of warp l sums, for target t, the partials of the CTAs b0 + l, b0 + l + rw,
-// ... (in CTA order; a warp's loads are 32 consecutive targets of one slot),
-// and warp 0 adds the rw sums in warp order, so the result does not depend on
-// timing. Spreading a target's partials over warps keeps the latency low when
-// a tile's chunks are split over many CTAs (small problems, many CTAs per SM);
-// red_warps picks rw from the grid and the tile count alone, so every path
-// that launches the same apply (graph or not) sums in the same order.
-constexpr int kRedWarps = 8;
-constexpr int kRedThreads = 32 * kRedWarps;
-
-int red_warps(int64_t G, int64_t tiles) {
-    const int64_t per_tile = (G + tiles - 1) / (tiles > 0 ? tiles : 1);   // CTAs per tile
-    const int64_t rw = (per_tile + 3) / 4;
-    return (int)(rw < 1 ? 1 : rw > kRedWarps ? kRedWarps : rw);
-}
-
-template <typename PT, int NPART>
-__device__ __forceinline__ void reduce_targets(const PT *__restrict__ part, int64_t S,
-                                               SysMap &sm, int64_t W, int G, int T, double scale,
-                                               double *__restrict__ VW) {
-    __shared__ double red[kRedWarps][6][32];
-    __shared__ int64_t s_tile[32], s_b0[32], s_b1[32];
-    __shared__ int s_local[32], s_live[32];
-    const int t = threadIdx.x & 31, l = threadIdx.x >> 5, rw = (int)(blockDim.x >> 5);
-    const int64_t n = (int64_t)blockIdx.x * 32 + t;
-    // the target's slot and CTA range, once per target (warp 0); a target past
-    // S or of a system left out of this apply is not live (nothing written)
-    if (l == 0) {
-        int64_t tile = 0, b0 = 1, b1 = 0;
-        int local = 0, live = 0;
-        if (n < S) {
-            const int64_t P = sm.pos_of_seg ? sm.pos_of_seg[n] : n;
-            tile = P / T;
-            local = (int)(P - tile * T);
-            if (sm.slot_of) tile = sm.slot_of[tile];
-            live = tile >= 0;
-            if (live) cta_range_of_tile(sm, tile, W, G, b0, b1);
-        }
-        s_tile[t] = tile;
-        s_b0[t] = b0;
-        s_b1[t] = b1;
-        s_local[t] = local;
-        s_live[t] = live;
-    }
-    __syncthreads();
-    const int64_t tile = s_tile[t], b1 = s_b1[t];
-    const int local = s_local[t];
-    const bool sparse = (int64_t)G > W;   // then some CTAs own no unit
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t b = s_b0[t] + l; b <= b1; b += rw) {
-        if (sparse && unit_start(b + 1, W, G) == unit_start(b, W, G)) continue;
-        const PT *p = part + (size_t)(b + tile) * (6 * NPART) * T;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            double v = (double)p[c * T + local];
-            if (NPART == 2) v += (double)p[(6 + c) * T + local];
-            acc[c] += v;
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) red[l][c][t] = acc[c];
-    __syncthreads();
-    if (l == 0 && s_live[t]) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            double v = red[0][c][t];
-            for (int w = 1; w < rw; ++w) v += red[w][c][t];
-            VW[6 * n + c] = v * scale;
-        }
-    }
-}
-
-// FP32 partials: (hi, lo) of each component, 12 floats per target and CTA.
-__global__ void __launch_bounds__(kRedThreads)
-rpy_reduce32_kernel(const float *__restrict__ part, int64_t S, SysMap sm,
-                                    int64_t W, int G, int T, double scale,
-                                    double *__restrict__ VW) {
-    resolve_dyn(sm, W);
-    reduce_targets<float, 2>(part, S, sm, W, G, T, scale, VW);
-}
-
-__global__ void __launch_bounds__(kRedThreads)
-rpy_reduce64_kernel(const double *__restrict__ part, int64_t S, SysMap sm,
-                                    int64_t W, int G, int T, double scale,
-                                    double *__restrict__ VW) {
-    resolve_dyn(sm, W);
-    reduce_targets<double, 1>(part, S, sm, W, G, T, scale, VW);
 }
 
 SysMap sys_map(const fil_ctx *c, bool active_only) {
@@ -1059,12 +1062,10 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
     const double scale = 1.0 / (8.0 * kPi * c->eta);
     const int pb = 256;
     const unsigned pgrid = (unsigned)((c->Spad + pb - 1) / pb);
-    const unsigned rgrid = (unsigned)((S + 31) / 32);
     const bool timed = c->prof_on && c->prof_n < kProfMax;
     const SysMap sm = sys_map(c, active_only);
     const int64_t W = active_only ? c->act_units : c->rpy_units;
     if (W == 0) return cudaSuccess;
-    const int T = rpy_tile(c);
     // the active-tile list changes between applies: its launches keep a fixed grid
     // (and read the unit count from the device), so captured graphs stay valid
     if (pair32_on(c)) {
@@ -1074,15 +1075,12 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
         if (timed) prof_record(c, c->prof_ev[2 * c->prof_n]);
         const RpyConst32 k = make_const<float, RpyConst32>(c->a);
         if (c->rpy_tpt == 1)
-            rpy_pair32_kernel<1><<<G, kRpyThreads, 0, c->stream>>>(c->src32, sm, W, G, k,
-                                                                   (float *)c->partials);
+            rpy_pair32_kernel<1><<<G, kRpyThreads, 0, c->stream>>>(
+                c->src32, sm, W, G, k, (float *)c->partials, c->tile_cnt, scale, VW);
         else
-            rpy_pair32_kernel<2><<<G, kRpyThreads, 0, c->stream>>>(c->src32, sm, W, G, k,
-                                                                   (float *)c->partials);
+            rpy_pair32_kernel<2><<<G, kRpyThreads, 0, c->stream>>>(
+                c->src32, sm, W, G, k, (float *)c->partials, c->tile_cnt, scale, VW);
         if (timed) prof_record(c, c->prof_ev[2 * c->prof_n + 1]);
-        rpy_reduce32_kernel<<<rgrid, 32 * red_warps(G, c->rpy_tiles), 0, c->stream>>>(
-            (const float *)c->partials, S, sm, W, G,
-                                                         T, scale, VW);
         if (c->tune_ev) cudaEventRecord(c->tune_ev[1], c->stream);
     } else {
         const int G = (int)(active_only ? c->rpy_grid64 : std::min<int64_t>(c->rpy_grid64, W));
@@ -1091,50 +1089,64 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
         if (timed) prof_record(c, c->prof_ev[2 * c->prof_n]);
         const RpyConst64 k = make_const<double, RpyConst64>(c->a);
         if (c->rpy_tpt == 1)
-            rpy_pair64_kernel<1><<<G, kRpyThreads, 0, c->stream>>>(c->src64, sm, W, G, k,
-                                                                   (double *)c->partials);
+            rpy_pair64_kernel<1><<<G, kRpyThreads, 0, c->stream>>>(
+                c->src64, sm, W, G, k, (double *)c->partials, c->tile_cnt, scale, VW);
         else
-            rpy_pair64_kernel<2><<<G, kRpyThreads, 0, c->stream>>>(c->src64, sm, W, G, k,
-                                                                   (double *)c->partials);
+            rpy_pair64_kernel<2><<<G, kRpyThreads, 0, c->stream>>>(
+                c->src64, sm, W, G, k, (double *)c->partials, c->tile_cnt, scale, VW);
         if (timed) prof_record(c, c->prof_ev[2 * c->prof_n + 1]);
-        rpy_reduce64_kernel<<<rgrid, 32 * red_warps(G, c->rpy_tiles), 0, c->stream>>>(
-            (const double *)c->partials, S, sm, W, G,
-                                                         T, scale, VW);
         if (c->tune_ev) cudaEventRecord(c->tune_ev[1], c->stream);
     }
     if (timed) c->prof_n += 1;
     c->n_applies += 1;
     c->n_pairs += active_only ? c->pairs_act : c->pairs_all;
-    c->n_launches += 3;
+    c->n_launches += 2;
     return cudaGetLastError();
 }
 
 
 // Autotuner of the pair kernel: times every (targets per thread, resident CTAs
-// per SM) candidate on `reps` applies of (Y, FT) and keeps the fastest.
+// per SM) candidate on `reps` applies of (Y, FT) and keeps the fastest. An idle
+// GPU runs at a low clock for some tens of milliseconds after work arrives, so
+// the applies first run for kSpinUpMs of wall time, and the candidates are then
+// swept twice, each keeping the faster of its two times: a candidate measured
+// while the clock still climbs is not chosen against or for that reason.
 cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *VW, int reps,
                          double *best_ms) {
+    constexpr double kSpinUpMs = 50.0;
+    constexpr int kSweeps = 2;
     const int64_t a0 = c->n_applies, l0 = c->n_launches;
     const double p0 = c->n_pairs;
-    // each rep's pair and reduce kernels are timed by their own pair of events, so
+    // each rep's pair kernel is timed by its own pair of events, so
     // that host launch gaps between applies (which dominate tiny problems) do not
     // enter the comparison
     std::vector<cudaEvent_t> ev(2 * (size_t)std::max(1, reps), nullptr);
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
-    int best_tpt = c->rpy_tpt, best_threads = c->rpy_threads, best_ctas = c->rpy_ctas;
-    float best = 1e30f;
-    for (int tpt = 1; tpt <= 2 && e == cudaSuccess; ++tpt) {
-        const int threads = kRpyThreads;
+    struct cand { int tpt, ctas; float ms; };
+    std::vector<cand> cands;
+    for (int tpt = 1; tpt <= 2; ++tpt) {
         int occ;
         if (pair32_on(c))
             occ = tpt == 1 ? occupancy(rpy_pair32_kernel<1>) : occupancy(rpy_pair32_kernel<2>);
         else
             occ = tpt == 1 ? occupancy(rpy_pair64_kernel<1>) : occupancy(rpy_pair64_kernel<2>);
-        for (int ctas = 1; ctas <= std::min(occ, c->rpy_ctas_max) && e == cudaSuccess; ++ctas) {
-            c->rpy_tpt = tpt;
-            c->rpy_threads = threads;
-            c->rpy_ctas = ctas;
+        for (int ctas = 1; ctas <= std::min(occ, c->rpy_ctas_max); ++ctas)
+            cands.push_back({tpt, ctas, 1e30f});
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    while (e == cudaSuccess) {
+        for (int r = 0; r < 4 && e == cudaSuccess; ++r) e = rpy_apply(c, Y, FT, VW);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        const std::chrono::duration<double, std::milli> dt = std::chrono::steady_clock::now() - t0;
+        if (dt.count() >= kSpinUpMs) break;
+    }
+    for (int sweep = 0; sweep < kSweeps && e == cudaSuccess; ++sweep) {
+        for (cand &k : cands) {
+            if (e != cudaSuccess) break;
+            c->rpy_tpt = k.tpt;
+            c->rpy_threads = kRpyThreads;
+            c->rpy_ctas = k.ctas;
             set_grids(c);
             build_tiles(c);
             e = upload_tiles(c);
@@ -1151,19 +1163,22 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
                 e = cudaEventElapsedTime(&one, ev[2 * r], ev[2 * r + 1]);
                 ms += one;
             }
-            if (e == cudaSuccess && ms < best) {
-                best = ms;
-                best_tpt = tpt;
-                best_threads = threads;
-                best_ctas = ctas;
-            }
+            if (e == cudaSuccess) k.ms = std::min(k.ms, ms);
         }
     }
     c->tune_ev = nullptr;
     for (cudaEvent_t x : ev)
         if (x) cudaEventDestroy(x);
+    float best = 1e30f;
+    int best_tpt = c->rpy_tpt, best_ctas = c->rpy_ctas;
+    for (const cand &k : cands)
+        if (k.ms < best) {
+            best = k.ms;
+            best_tpt = k.tpt;
+            best_ctas = k.ctas;
+        }
     c->rpy_tpt = best_tpt;
-    c->rpy_threads = best_threads;
+    c->rpy_threads = kRpyThreads;
     c->rpy_ctas = best_ctas;
     set_grids(c);
     build_tiles(c);
@@ -1207,9 +1222,9 @@ cudaError_t rpy_set_schedule(fil_ctx *c, int tpt, int threads, int ctas) {
 // where cudaMalloc is unavailable or forbidden, e.g. inside another
 // framework's memory pool or a process whose allocations are owned by
 // someone else -- this variant of the mixed-precision apply uses no context
-// and allocates nothing: its scratch (packed FP32 sources and the stream-K
-// partial sums) is the file-scope array below, which every GPU that loads the
-// library holds until the process exits. The caller passes the inputs and
+// and allocates nothing: its scratch (packed FP32 sources, the stream-K
+// partial sums and the tiles' completion counters) is the file-scope arrays
+// below, which every GPU that loads the library holds until the process exits. The caller passes the inputs and
 // the output in device memory.
 // ---------------------------------------------------------------------------
 namespace {
@@ -1233,20 +1248,27 @@ constexpr size_t kNoAllocPartBytes =
 constexpr size_t kNoAllocBytes = kNoAllocSrcBytes + kNoAllocPartBytes;   // ~10.6 MB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+// per-tile completion counters of the pair kernel: zero at load, and every
+// launch leaves them zero
+static __device__ int g_noalloc_cnt[kNoAllocMaxTiles] = {0};
 
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 unsigned char *g_noalloc_ptr[kNoAllocMaxDevices];   // device address of the array, per device
+int *g_noalloc_cnt_ptr[kNoAllocMaxDevices];         // and of the counters
 int g_noalloc_grid[kNoAllocMaxDevices];
 
-// Once per device, with that device current: the device address of the array
-// (the name itself is only a host-side stand-in) and the stream-K grid size.
-cudaError_t noalloc_setup(int dev, unsigned char **ptr, int *grid) {
+// Once per device, with that device current: the device addresses of the
+// arrays (their names are only host-side stand-ins) and the stream-K grid size.
+cudaError_t noalloc_setup(int dev, unsigned char **ptr, int **cnt, int *grid) {
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
+        void *p = nullptr, *q = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
+        e = cudaGetSymbolAddress(&q, g_noalloc_cnt);
+        if (e != cudaSuccess) return e;
+        g_noalloc_cnt_ptr[dev] = static_cast<int *>(q);
         int occ = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rpy_pair32_kernel<kRpyTargetsPerThread>,
                                                           kRpyThreads, 0);
@@ -1257,6 +1279,7 @@ cudaError_t noalloc_setup(int dev, unsigned char **ptr, int *grid) {
         g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
     }
     *ptr = g_noalloc_ptr[dev];
+    *cnt = g_noalloc_cnt_ptr[dev];
     *grid = g_noalloc_grid[dev];
     return cudaSuccess;
 }
@@ -1302,8 +1325,9 @@ extern "C" fil_status fil_rpy_apply_noalloc(int64_t n_seg, const double *Y, cons
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return FIL_ECUDA;
     if (!on_device(Y, dev) || !on_device(FT, dev) || !on_device(VW, dev)) return FIL_EINVAL;
     unsigned char *base = nullptr;
+    int *cnt = nullptr;
     int grid_max = 1;
-    if (noalloc_setup(dev, &base, &grid_max) != cudaSuccess) return FIL_ECUDA;
+    if (noalloc_setup(dev, &base, &cnt, &grid_max) != cudaSuccess) return FIL_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t tiles = (n_seg + kRpyTile - 1) / kRpyTile;
     const int64_t n_chunks = (n_seg + kRpyChunk - 1) / kRpyChunk;
@@ -1312,8 +1336,8 @@ extern "C" fil_status fil_rpy_apply_noalloc(int64_t n_seg, const double *Y, cons
     const int G = (int)std::min<int64_t>(grid_max, W);
     float4 *src = reinterpret_cast<float4 *>(base);
     float *part = reinterpret_cast<float *>(base + kNoAllocSrcBytes);
-    // every source record up to Spad and every partial slot the reduce reads
-    // is written below, so nothing has to start at zero
+    // every source record up to Spad and every partial slot a tile's sum reads
+    // is written below; the tile counters are zero between launches
     const int pb = 256;
     SysMap sm{};                       // one system, no tables
     sm.n_tiles = tiles;
@@ -1323,9 +1347,7 @@ extern "C" fil_status fil_rpy_apply_noalloc(int64_t n_seg, const double *Y, cons
                            Spad, sm, src);
     if (e == cudaSuccess)
         e = launch(rpy_pair32_kernel<kRpyTargetsPerThread>, (unsigned)G, kRpyThreads, st,
-                   (const float4 *)src, sm, W, G, make_const<float, RpyConst32>(a), part);
-    if (e == cudaSuccess)
-        e = launch(rpy_reduce32_kernel, (unsigned)((n_seg + 31) / 32), 32 * red_warps(G, tiles), st,
-                   (const float *)part, n_seg, sm, W, G, kRpyTile, 1.0 / (8.0 * kPi * eta), VW);
+                   (const float4 *)src, sm, W, G, make_const<float, RpyConst32>(a), part, cnt,
+                   1.0 / (8.0 * kPi * eta), VW);
     return e == cudaSuccess ? FIL_OK : FIL_ECUDA;
 }

@@ -529,19 +529,23 @@ def test_adaptive_extrapolation_matches_oracle(fil, model):
 
 
 @pytest.mark.parametrize("model", J0_MODELS)
-def test_carried_broyden_memory_matches_oracle(fil, model):
+@pytest.mark.parametrize("tol,n_steps", [(1e-6, 6), (3e-3, 10)])
+def test_carried_broyden_memory_matches_oracle(fil, model, tol, n_steps):
     """fil_set_broyden_memory(6) with J0 kept across steps: every Broyden iterate
-    of 6 steps equals the oracle's (FP64), the oracle starting each step from
-    the J0 the library used (rebuilt where fil_j0_stats says it was) and from
-    the last 6 of the previous step's pairs; the library skips the update of
-    the iteration that converges, so that pair is not carried. The same
-    iteration counts, iterates within 1e-8 relative at tol 1e-6: a carried
-    pair d = df / |df| from the end of a converged step has |df| ~ tol, so the
-    two sides' ~1e-13 residual rounding differs in it by ~1e-13 / tol, and the
+    of n_steps steps equals the oracle's (FP64), the oracle starting each step
+    from the J0 the library used (rebuilt where fil_j0_stats says it was) and
+    from the last 6 of the previous step's pairs; the library skips the update
+    of the iteration that converges, so that pair is not carried, and a step
+    that converges on entry (H_k = H_0) passes on the pairs it carried. The
+    same iteration counts, iterates within 1e-8 relative: a carried pair
+    d = df / |df| from the end of a converged step has |df| ~ tol, so the two
+    sides' ~1e-13 residual rounding differs in it by ~1e-13 / tol, and the
     carried steps' iterates inherit that (measured: <= 7e-10 at tol 1e-6,
-    7e-7 at 1e-8, 3e-5 at 1e-11; without carried pairs 5e-13 at every tol)."""
+    7e-7 at 1e-8, 3e-5 at 1e-11; without carried pairs 5e-13 at every tol).
+    At tol 3e-3 the oracle's run has steps 5-8 converge on entry and step 9
+    iterate from the 3 pairs they passed on."""
     keep = 6
-    lay, p, st, ext, _ = _system([20, 32, 11], 76, history=True, tol=1e-6, dt=0.15)
+    lay, p, st, ext, _ = _system([20, 32, 11], 76, history=True, tol=tol, dt=0.15)
     with _gpu(fil, lay, p, st, ext, j0=model[0]) as m:
         m.set_j0_reuse(50)
         m.set_broyden_memory(keep)
@@ -549,7 +553,8 @@ def test_carried_broyden_memory_matches_oracle(fil, model):
         X = np.zeros(6 * lay.S)
         f = np.zeros(6 * lay.S)
         carried = 0
-        for j in range(6):
+        held = through_hold = False   # pairs passed on by a step converged on entry
+        for j in range(n_steps):
             builds = m.j0_stats()[0]
             f0 = m.broyden_begin()
             rebuilt = m.j0_stats()[0] > builds
@@ -558,6 +563,8 @@ def test_carried_broyden_memory_matches_oracle(fil, model):
             br = fo.begin_step(lay, p, st, ext, j0_model=model[1], j0=solver,
                                memory=mem[-keep:])
             carried += 0 if rebuilt else len(mem[-keep:])
+            if rebuilt:
+                held = False
             assert abs(f0 - np.abs(br.f).max()) <= 1e-12 * max(1, np.abs(st.Y).max())
             conv = f0 <= p.tol * p.a
             while not conv:
@@ -569,9 +576,16 @@ def test_carried_broyden_memory_matches_oracle(fil, model):
                 assert conv == br.converged(), (j, br.k)
             m.broyden_commit()
             solver = br.solver
-            mem = list(zip(br.c, br.d))[:-1] if br.k > 0 else []
+            if br.k > 0:
+                through_hold = through_hold or (held and len(mem[-keep:]) > 0)
+                mem = list(zip(br.c, br.d))[:-1]
+                held = False
+            elif mem:
+                held = True
             st = fo.commit_step(lay, p, st, br.X)
         assert carried > 0, "no step started from carried pairs"
+        if tol > 1e-4:
+            assert through_hold, "no step iterated from pairs passed on by a converged step"
 
 
 def test_broyden_memory_argument_checks(fil):
