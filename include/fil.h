@@ -419,8 +419,9 @@ fil_status fil_fma_peak(int32_t fp64, double *flops_per_s, double *sm_mhz);
  * n_seg segments with radius a and viscosity eta: Y (S x 3), FT (S x 6) and
  * VW (S x 6) must be DEVICE pointers of the current device (or managed
  * memory), owned by the caller. It allocates nothing: its scratch is a fixed
- * static device array of about 10.6 MB in the library, which every GPU that
- * loads the library keeps until the process exits. Limits: 1 <= n_seg <=
+ * static device array of about 10.6 MB in the library (plus 128 per-tile
+ * completion counters, zero between calls), which every GPU that loads the
+ * library keeps until the process exits. Limits: 1 <= n_seg <=
  * 32768; larger sizes, host pointers, pointers to another GPU's memory or
  * non-positive a, eta return FIL_EINVAL; a failed launch returns FIL_ECUDA.
  * The scratch holds the stream-K partial sums of up to 4 x 152 CTAs (the
