@@ -268,6 +268,14 @@ def run_mobility(args, fil, torch):
 # roofline, clocks and the FP64-oracle comparison.
 # ---------------------------------------------------------------------------
 
+def set_schedule(m, text):
+    """A pair schedule 'tile,targets_per_thread,ctas_per_sm[,source_split]' set by hand."""
+    v = [int(x) for x in text.split(",")]
+    m.set_pair_schedule(*v[:3])
+    if len(v) > 3:
+        m.set_source_split(v[3])
+
+
 def run_c1_mobility(fil, torch, applies=1000, per_graph=100, min_seconds=1.0, schedule=None):
     """Mobility apply alone: 100 random-walk filaments x 32 segments (3200) at
     5% volume fraction, N(0,1) loads, 1000 repeated applies. At this size an
@@ -285,11 +293,12 @@ def run_c1_mobility(fil, torch, applies=1000, per_graph=100, min_seconds=1.0, sc
     m = fil.Filaments([32] * 100, precision=fil.FIL_PAIR32, stream=stream.cuda_stream)
     m.set_state(Y, np.tile([1.0, 0.0, 0.0, 0.0], (S, 1)))
     if schedule:
-        m.set_pair_schedule(*[int(x) for x in schedule.split(",")])
+        set_schedule(m, schedule)
         tuned = (m.pair_schedule()[0], m.pair_schedule()[2], None)
     else:
         tuned = m.autotune(50)
     schedule = m.pair_schedule()
+    split = m.source_split()
     Yd = torch.from_numpy(Y).cuda()
     FTd = torch.from_numpy(FT).cuda()
     VW = torch.empty((S, 6), dtype=torch.float64, device="cuda")
@@ -345,7 +354,7 @@ def run_c1_mobility(fil, torch, applies=1000, per_graph=100, min_seconds=1.0, sc
                              "itself, repeated"},
             "roofline": pair_roofline(float(S) * S, pair_ms, n_pair),
             "autotuned": {"tile": tuned[0], "ctas_per_sm": tuned[1], "ms_per_apply": tuned[2],
-                          "targets_per_thread": schedule[1]},
+                          "targets_per_thread": schedule[1], "source_split": split},
             "velocity_error": velocity_error(got, ref, B),
             "cpu_baseline": {"value": S * float(S) / dt, "unit": UNIT, "cores": cores,
                              "kind": "oracle", "sample": "one whole apply, %d x %d pairs (%.2f s)"
@@ -439,10 +448,11 @@ def run_ensemble(args, fil, torch, nested=False):
         m.step()
     tuned = None
     if args.ens_schedule:
-        m.set_pair_schedule(*[int(x) for x in args.ens_schedule.split(",")])
+        set_schedule(m, args.ens_schedule)
     elif args.tune_ensemble:
         tuned = m.autotune(2)
     schedule = m.pair_schedule()
+    split = m.source_split()
     a0, i0, k0 = m.counters()
     p0 = m.pair_count()
     torch.cuda.synchronize()
@@ -532,7 +542,7 @@ def run_ensemble(args, fil, torch, nested=False):
         "autotuned": ({"tile": tuned[0], "ctas_per_sm": tuned[1], "ms_per_apply": tuned[2]}
                       if tuned else None),
         "pair_schedule": {"tile": schedule[0], "targets_per_thread": schedule[1],
-                          "ctas_per_sm": schedule[2]},
+                          "ctas_per_sm": schedule[2], "source_split": split},
         "gpu_launches": int(k1 - k0), "clocks": clocks}
     if not nested:
         print(json.dumps(rec), flush=True)
@@ -1093,11 +1103,13 @@ def main():
     ap.add_argument("--tune-ensemble", type=int, default=1,
                     help="autotune the ensemble's pair-kernel schedule after its warm-up steps")
     ap.add_argument("--ens-schedule", default=None,
-                    help="set the ensemble's pair schedule 'tile,targets_per_thread,ctas_per_sm' "
-                         "instead of autotuning it (e.g. for a profile of the tuned schedule)")
+                    help="set the ensemble's pair schedule 'tile,targets_per_thread,ctas_per_sm"
+                         "[,source_split]' instead of autotuning it (e.g. for a profile of the "
+                         "tuned schedule)")
     ap.add_argument("--c1-schedule", default=None,
                     help="set the 3200-segment apply's pair schedule "
-                         "'tile,targets_per_thread,ctas_per_sm' instead of autotuning it")
+                         "'tile,targets_per_thread,ctas_per_sm[,source_split]' instead of "
+                         "autotuning it")
     ap.add_argument("--steric", type=float, default=0.0,
                     help="steric barrier strength F^S (Sec. 2.6, chi = 1.1); 0 = off")
     ap.add_argument("--graph", type=int, default=0,

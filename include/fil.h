@@ -136,8 +136,9 @@ fil_status fil_sys_stats(const fil_ctx *c, int32_t *iters, double *finf);
  * each tile's partials) of `reps` mobility applies of the current state's
  * loads (CUDA events around it, so host launch gaps do not count) for every
  * candidate schedule -- tiles of 256 targets (2 per thread) or 128 targets
- * (1 per thread), and 1..occupancy resident CTAs per SM for the stream-K split
- * of the (tile, source chunk) work units -- and keeps the fastest for all
+ * (1 per thread, with source split 1 or 2 on the FP32 path: see
+ * fil_set_source_split), and 1..occupancy resident CTAs per SM for the
+ * stream-K split of the (tile, source chunk) work units -- and keeps the fastest for all
  * later applies. The applies first run for 50 ms of wall time (an idle GPU's
  * clock is still rising then) and the candidates are swept twice, each
  * keeping its faster time. Reports the choice (nullable outputs) and its
@@ -148,12 +149,25 @@ fil_status fil_autotune(fil_ctx *c, int32_t reps, int32_t *tile, int32_t *ctas_p
 
 /* Set the pair schedule by hand (the autotuner's candidates): tile 256 with 2
  * targets per thread or tile 128 with 1, and ctas_per_sm from 1 to the
- * kernel's occupancy. FIL_EINVAL for another combination, FIL_ESTATE inside a
- * step. fil_pair_schedule reads the current one (nullable outputs). */
+ * kernel's occupancy; the source split goes back to 1. FIL_EINVAL for another
+ * combination, FIL_ESTATE inside a step. fil_pair_schedule reads the current
+ * one (nullable outputs). */
 fil_status fil_set_pair_schedule(fil_ctx *c, int32_t tile, int32_t targets_per_thread,
                                  int32_t ctas_per_sm);
 fil_status fil_pair_schedule(const fil_ctx *c, int32_t *tile, int32_t *targets_per_thread,
                              int32_t *ctas_per_sm);
+
+/* Source split of the FP32 pair kernel with one target per thread (128-target
+ * tiles): split = 2 runs each CTA with twice the warps on the same targets, the
+ * two halves taking alternate 32-source groups of every chunk (their sums are
+ * added in float-float arithmetic, first half first), for problems whose few
+ * work units leave the SMs short of warps. Applies to the current schedule;
+ * fil_set_pair_schedule sets it back to 1, fil_autotune chooses it with the
+ * rest. FIL_EINVAL for a split other than 1 or 2, for 2 with 256-target tiles
+ * or the FP64 path, or when ctas_per_sm exceeds the split kernel's occupancy
+ * (2 on GB300); FIL_ESTATE inside a step. Results change only in rounding. */
+fil_status fil_set_source_split(fil_ctx *c, int32_t split);
+fil_status fil_source_split(const fil_ctx *c, int32_t *split);
 
 /* Run each Broyden iteration of fil_broyden_step / fil_step as one CUDA graph
  * launch (enable = 1) instead of separate kernel launches: the graph holds the

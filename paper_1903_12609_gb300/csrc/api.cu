@@ -1144,10 +1144,27 @@ fil_status fil_set_pair_schedule(fil_ctx *c, int32_t tile, int32_t targets_per_t
         return set_err(c, FIL_EINVAL, "fil_set_pair_schedule: no such schedule");
     CK(cudaSetDevice(c->device));
     const int threads = tile / targets_per_thread;
-    if (!rpy_schedule_valid(c, targets_per_thread, threads, ctas_per_sm))
+    if (!rpy_schedule_valid(c, targets_per_thread, threads, ctas_per_sm, 1))
         return set_err(c, FIL_EINVAL, "fil_set_pair_schedule: no such schedule");
-    CK(rpy_set_schedule(c, targets_per_thread, threads, ctas_per_sm));
+    CK(rpy_set_schedule(c, targets_per_thread, threads, ctas_per_sm, 1));
     drop_graphs(c);
+    return FIL_OK;
+}
+
+fil_status fil_set_source_split(fil_ctx *c, int32_t split) {
+    if (!c) return FIL_EINVAL;
+    if (c->in_step) return set_err(c, FIL_ESTATE, "fil_set_source_split: a step is in progress");
+    CK(cudaSetDevice(c->device));
+    if (!rpy_schedule_valid(c, c->rpy_tpt, c->rpy_threads, c->rpy_ctas, split))
+        return set_err(c, FIL_EINVAL, "fil_set_source_split: not with the current schedule");
+    CK(rpy_set_schedule(c, c->rpy_tpt, c->rpy_threads, c->rpy_ctas, split));
+    drop_graphs(c);
+    return FIL_OK;
+}
+
+fil_status fil_source_split(const fil_ctx *c, int32_t *split) {
+    if (!c || !split) return FIL_EINVAL;
+    *split = c->rpy_split;
     return FIL_OK;
 }
 

@@ -105,6 +105,7 @@ struct fil_ctx {
     int64_t *tile_unit_off_d, *tile_src_d, *tile_nsrc_d, *pos_of_seg_d;
     int *pad_map_d, *tile_id_d, *slot_d;
     int rpy_tpt;           // targets per thread of the pair kernels
+    int rpy_split = 1;     // source split of the FP32 one-target kernel (1 or 2 halves per CTA)
     int rpy_threads;       // threads per CTA of the FP32 pair kernel (128, or 64 with tpt 2);
                            // tile = rpy_threads x rpy_tpt targets
     int rpy_ctas;          // resident CTAs per SM of the stream-K grid
@@ -247,8 +248,8 @@ cudaError_t rpy_set_active(fil_ctx *c);     // list the active systems' tiles
 cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *VW, int reps,
                          double *best_ms);
 cudaError_t rpy_setup(fil_ctx *c);          // grid sizes and padded layout, once at create
-bool rpy_schedule_valid(const fil_ctx *c, int tpt, int threads, int ctas);
-cudaError_t rpy_set_schedule(fil_ctx *c, int tpt, int threads, int ctas);
+bool rpy_schedule_valid(const fil_ctx *c, int tpt, int threads, int ctas, int split);
+cudaError_t rpy_set_schedule(fil_ctx *c, int tpt, int threads, int ctas, int split);
 cudaError_t rpy_upload_tables(fil_ctx *c);  // the layout tables, after the arena exists
 size_t rpy_partial_bytes(const fil_ctx *c);
 

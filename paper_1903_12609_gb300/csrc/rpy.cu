@@ -396,10 +396,10 @@ __device__ __forceinline__ void pair64(double tx, double ty, double tz, const do
 // Asynchronous copy of one chunk of source records (kRec float4) from global to
 // shared memory, 16 bytes per cp.async, spread over the CTA's threads; the
 // copies land when cp_async_wait_all returns (plus a barrier for the others').
-template <int kRec>
+template <int kRec, int kThreads>
 __device__ __forceinline__ void stage_chunk(float4 *dst, const float4 *__restrict__ g, int tid) {
 #pragma unroll
-    for (int i = tid; i < kRec; i += kRpyThreads) {
+    for (int i = tid; i < kRec; i += kThreads) {
         const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + i);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(g + i) : "memory");
     }
@@ -453,7 +453,8 @@ template <typename PT, int NPART, int TPT>
 __device__ __forceinline__ void finish_tile(const PT *part, const SysMap &smap, int64_t tile,
                                             int64_t ptile, int64_t units, int64_t n_chunks,
                                             int64_t W, int64_t G, int *__restrict__ cnt,
-                                            double scale, double *__restrict__ VW) {
+                                            double scale, double *__restrict__ VW,
+                                            bool worker = true) {
     constexpr int kTile = kRpyThreads * TPT;
     __shared__ int s_last;
     const int tid = threadIdx.x;
@@ -461,7 +462,8 @@ __device__ __forceinline__ void finish_tile(const PT *part, const SysMap &smap, 
     if (tid == 0)
         s_last = fetch_add_acq_rel(cnt + tile, (int)units) + (int)units == (int)n_chunks;
     __syncthreads();
-    if (!s_last) return;
+    // (`worker`: false for the second half of a source-split CTA, which holds no targets)
+    if (!s_last || !worker) return;
     int64_t u0, u1, b0, b1;
     cta_range_of_tile(smap, tile, W, G, u0, u1, b0, b1);
     // With G > W (a fixed grid over a short active list) a CTA owns at most one
@@ -529,17 +531,28 @@ __device__ __forceinline__ void finish_tile(const PT *part, const SysMap &smap, 
 //    close groups again with hi/lo differences in the far form, and exactly
 //    only when distinct segments overlap.
 // Measured on GB300, each structure is the faster one for its tile size.
+// SPLIT = 2 (128-target tiles only) gives a CTA twice the warps on the same
+// targets: the two halves take alternate 32-source groups of every chunk and
+// their sums are added (float-float, in half order) before the partial is
+// written, so a work unit is done by eight warps instead of four -- more
+// warps at work on small problems, whose few units leave SMs short of them.
 // ---------------------------------------------------------------------------
-template <int TPT>
-__global__ void __launch_bounds__(kRpyThreads, TPT == 2 ? kRpyMinBlocksTpt2 : kRpyMinBlocksTpt1)
+template <int TPT, int SPLIT = 1>
+__global__ void __launch_bounds__(kRpyThreads * SPLIT,
+                                  TPT == 2 ? kRpyMinBlocksTpt2
+                                           : (SPLIT == 1 ? kRpyMinBlocksTpt1 : kRpyMinBlocksSplit2))
 rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G, RpyConst32 k,
                   float *__restrict__ part, int *__restrict__ cnt, double scale,
                   double *__restrict__ VW) {
     constexpr int kRec = kRpyPairF4 * (kRpyChunk / 2);   // float4 per chunk
     constexpr int kT = TPT;                               // targets per thread
     constexpr int kTile = kRpyThreads * TPT;              // targets per tile
+    static_assert(SPLIT == 1 || (SPLIT == 2 && TPT == 1), "source split: 128-target tiles only");
     __shared__ float4 sm[2][kRec];
-    const int tid = threadIdx.x;
+    // target slot, and which of the SPLIT sets of source groups the thread takes
+    // (both compile-time for SPLIT = 1, so the unsplit kernels are unchanged)
+    const int tid = SPLIT == 1 ? (int)threadIdx.x : (int)(threadIdx.x % kRpyThreads);
+    const int half = SPLIT == 1 ? 0 : (int)(threadIdx.x / kRpyThreads);
     const int64_t b = blockIdx.x;
     resolve_dyn(smap, W);
     int64_t u = unit_start(b, W, G);
@@ -586,7 +599,7 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
             for (int c = 0; c < 6; ++c) hi[t][c] = lo[t][c] = 0.f;
 
         // first chunk -> buffer 0
-        stage_chunk<kRec>(sm[0], srcs + kRec * c_begin, tid);
+        stage_chunk<kRec, kRpyThreads * SPLIT>(sm[0], srcs + kRec * c_begin, threadIdx.x);
         cp_async_wait_all();
         __syncthreads();
 
@@ -595,12 +608,14 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
             // the next chunk streams into the other buffer while this one is computed
             // (that buffer was last read before the barrier that ended the previous chunk)
             const bool has_next = (ch + 1 < c_end);
-            if (has_next) stage_chunk<kRec>(sm[buf ^ 1], srcs + kRec * (ch + 1), tid);
+            if (has_next)
+                stage_chunk<kRec, kRpyThreads * SPLIT>(sm[buf ^ 1], srcs + kRec * (ch + 1),
+                                                       threadIdx.x);
             const float4 *s = sm[buf];
             const int n_grp = (int)min((int64_t)(kRpyChunk / kRpyComp),
                                        (nsrc - ch * kRpyChunk + kRpyComp - 1) / kRpyComp);
 #pragma unroll 1
-            for (int grp = 0; grp < (idle ? 0 : n_grp); ++grp) {
+            for (int grp = half; grp < (idle ? 0 : n_grp); grp += SPLIT) {
                 const float4 *qg = s + kRpyPairF4 * (grp * (kRpyComp / 2));
                 float acc[kT][6];
                 if constexpr (TPT == 1) {
@@ -731,19 +746,44 @@ rpy_pair32_kernel(const float4 *__restrict__ src, SysMap smap, int64_t W, int G,
             __syncthreads();
         }
 
+        if constexpr (SPLIT > 1) {
+            // the second half's sums join the first's (TwoSum of the hi parts, the lo
+            // parts into its error, renormalised); the buffer is next written after
+            // the next segment's first chunk barrier
+            __shared__ float xs[12][kRpyThreads];
+            if (half == 1) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    xs[c][tid] = hi[0][c];
+                    xs[6 + c][tid] = lo[0][c];
+                }
+            }
+            __syncthreads();
+            if (half == 0) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    float sh, e;
+                    two_sum(hi[0][c], xs[c][tid], sh, e);
+                    e = __fadd_rn(e, __fadd_rn(lo[0][c], xs[6 + c][tid]));
+                    two_sum(sh, e, hi[0][c], lo[0][c]);
+                }
+            }
+        }
         // partial of this CTA for this tile -> slot (b + tile)
-        float *p = part + (size_t)(b + tile) * 12 * kTile;
+        if (half == 0) {
+            float *p = part + (size_t)(b + tile) * 12 * kTile;
 #pragma unroll
-        for (int t = 0; t < kT; ++t) {
-            const int local = t * kRpyThreads + tid;
+            for (int t = 0; t < kT; ++t) {
+                const int local = t * kRpyThreads + tid;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                p[c * kTile + local] = hi[t][c];
-                p[(6 + c) * kTile + local] = lo[t][c];
+                for (int c = 0; c < 6; ++c) {
+                    p[c * kTile + local] = hi[t][c];
+                    p[(6 + c) * kTile + local] = lo[t][c];
+                }
             }
         }
         finish_tile<float, 2, TPT>(part, smap, tile, ptile, c_end - c_begin, n_chunks, W, G, cnt,
-                                   scale, VW);
+                                   scale, VW, SPLIT == 1 || half == 0);
         u = ubeg + c_end;
     }
 }
@@ -915,6 +955,16 @@ void set_grids(fil_ctx *c) {
     c->rpy_grid64 = c->rpy_ctas * c->num_sms;
 }
 
+// Resident CTAs per SM of the pair kernel of a schedule (targets per thread,
+// source split; the split exists for the FP32 kernel with one target per thread).
+int pair_occupancy(const fil_ctx *c, int tpt, int split) {
+    if (!pair32_on(c))
+        return tpt == 1 ? occupancy(rpy_pair64_kernel<1>) : occupancy(rpy_pair64_kernel<2>);
+    if (tpt == 2) return occupancy(rpy_pair32_kernel<2>);
+    return split == 2 ? occupancy(rpy_pair32_kernel<1, 2>, 2 * kRpyThreads)
+                      : occupancy(rpy_pair32_kernel<1>);
+}
+
 }  // namespace
 
 cudaError_t rpy_setup(fil_ctx *c) {
@@ -923,7 +973,9 @@ cudaError_t rpy_setup(fil_ctx *c) {
     int occ = pair32_on(c) ? occupancy(rpy_pair32_kernel<kRpyTargetsPerThread>)
                                    : occupancy(rpy_pair64_kernel<kRpyTargetsPerThread>);
     c->rpy_ctas = occ;
+    c->rpy_split = 1;
     c->rpy_ctas_max = std::max({occ, occupancy(rpy_pair32_kernel<1>), occupancy(rpy_pair32_kernel<2>),
+                                occupancy(rpy_pair32_kernel<1, 2>, 2 * kRpyThreads),
                                 occupancy(rpy_pair64_kernel<1>), occupancy(rpy_pair64_kernel<2>)});
     set_grids(c);
     // padded layout: system s occupies [pad_off[s], pad_off[s+1]), a multiple of kRpyPad
@@ -1074,7 +1126,10 @@ cudaError_t rpy_apply(fil_ctx *c, const double *Y, const double *FT, double *VW,
         if (c->tune_ev) cudaEventRecord(c->tune_ev[0], c->stream);
         if (timed) prof_record(c, c->prof_ev[2 * c->prof_n]);
         const RpyConst32 k = make_const<float, RpyConst32>(c->a);
-        if (c->rpy_tpt == 1)
+        if (c->rpy_tpt == 1 && c->rpy_split == 2)
+            rpy_pair32_kernel<1, 2><<<G, 2 * kRpyThreads, 0, c->stream>>>(
+                c->src32, sm, W, G, k, (float *)c->partials, c->tile_cnt, scale, VW);
+        else if (c->rpy_tpt == 1)
             rpy_pair32_kernel<1><<<G, kRpyThreads, 0, c->stream>>>(
                 c->src32, sm, W, G, k, (float *)c->partials, c->tile_cnt, scale, VW);
         else
@@ -1123,16 +1178,14 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
     std::vector<cudaEvent_t> ev(2 * (size_t)std::max(1, reps), nullptr);
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
-    struct cand { int tpt, ctas; float ms; };
+    struct cand { int tpt, split, ctas; float ms; };
     std::vector<cand> cands;
     for (int tpt = 1; tpt <= 2; ++tpt) {
-        int occ;
-        if (pair32_on(c))
-            occ = tpt == 1 ? occupancy(rpy_pair32_kernel<1>) : occupancy(rpy_pair32_kernel<2>);
-        else
-            occ = tpt == 1 ? occupancy(rpy_pair64_kernel<1>) : occupancy(rpy_pair64_kernel<2>);
-        for (int ctas = 1; ctas <= std::min(occ, c->rpy_ctas_max); ++ctas)
-            cands.push_back({tpt, ctas, 1e30f});
+        for (int split = 1; split <= (tpt == 1 && pair32_on(c) ? 2 : 1); ++split) {
+            const int occ = pair_occupancy(c, tpt, split);
+            for (int ctas = 1; ctas <= std::min(occ, c->rpy_ctas_max); ++ctas)
+                cands.push_back({tpt, split, ctas, 1e30f});
+        }
     }
     const auto t0 = std::chrono::steady_clock::now();
     while (e == cudaSuccess) {
@@ -1145,6 +1198,7 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
         for (cand &k : cands) {
             if (e != cudaSuccess) break;
             c->rpy_tpt = k.tpt;
+            c->rpy_split = k.split;
             c->rpy_threads = kRpyThreads;
             c->rpy_ctas = k.ctas;
             set_grids(c);
@@ -1170,14 +1224,16 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
     for (cudaEvent_t x : ev)
         if (x) cudaEventDestroy(x);
     float best = 1e30f;
-    int best_tpt = c->rpy_tpt, best_ctas = c->rpy_ctas;
+    int best_tpt = c->rpy_tpt, best_split = c->rpy_split, best_ctas = c->rpy_ctas;
     for (const cand &k : cands)
         if (k.ms < best) {
             best = k.ms;
             best_tpt = k.tpt;
+            best_split = k.split;
             best_ctas = k.ctas;
         }
     c->rpy_tpt = best_tpt;
+    c->rpy_split = best_split;
     c->rpy_threads = kRpyThreads;
     c->rpy_ctas = best_ctas;
     set_grids(c);
@@ -1193,21 +1249,16 @@ cudaError_t rpy_autotune(fil_ctx *c, const double *Y, const double *FT, double *
 // A given pair schedule (targets per thread, threads per CTA, resident CTAs per
 // SM for the stream-K grid); false if the kernel has no such schedule or the
 // CTA count exceeds its occupancy.
-bool rpy_schedule_valid(const fil_ctx *c, int tpt, int threads, int ctas) {
-    int occ = 0;
-    if (threads == kRpyThreads && (tpt == 1 || tpt == 2)) {
-        occ = pair32_on(c) ? (tpt == 1 ? occupancy(rpy_pair32_kernel<1>)
-                                       : occupancy(rpy_pair32_kernel<2>))
-                           : (tpt == 1 ? occupancy(rpy_pair64_kernel<1>)
-                                       : occupancy(rpy_pair64_kernel<2>));
-    } else {
-        return false;
-    }
+bool rpy_schedule_valid(const fil_ctx *c, int tpt, int threads, int ctas, int split) {
+    if (threads != kRpyThreads || (tpt != 1 && tpt != 2)) return false;
+    if (split != 1 && !(split == 2 && tpt == 1 && pair32_on(c))) return false;
+    const int occ = pair_occupancy(c, tpt, split);
     return ctas >= 1 && ctas <= std::min(occ, c->rpy_ctas_max);
 }
 
-cudaError_t rpy_set_schedule(fil_ctx *c, int tpt, int threads, int ctas) {
+cudaError_t rpy_set_schedule(fil_ctx *c, int tpt, int threads, int ctas, int split) {
     c->rpy_tpt = tpt;
+    c->rpy_split = split;
     c->rpy_threads = threads;
     c->rpy_ctas = ctas;
     set_grids(c);

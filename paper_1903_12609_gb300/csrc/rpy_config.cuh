@@ -18,6 +18,9 @@ constexpr int kRpyComp = 32;                   // sources per compensated partia
 // which measured faster on small systems than 4 or 5).
 constexpr int kRpyMinBlocksTpt2 = 4;
 constexpr int kRpyMinBlocksTpt1 = 6;
+// The one-target kernel with its sources split over two halves of a 256-thread
+// CTA: 2 resident CTAs (124 registers; at 3 CTAs, 80 registers, it spills).
+constexpr int kRpyMinBlocksSplit2 = 2;
 // float4 per two FP32 source records (the packed FP32x2 layout)
 constexpr int kRpyPairF4 = 6;
 

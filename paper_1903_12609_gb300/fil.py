@@ -38,7 +38,8 @@ EXPORTED = ["fil_create", "fil_destroy", "fil_last_error", "fil_sizes", "fil_set
             "fil_set_graph", "fil_autotune", "fil_set_steric", "fil_set_tether",
             "fil_get_tether", "fil_fma_peak", "fil_set_j0_reuse", "fil_j0_stats",
             "fil_set_pair_schedule", "fil_pair_schedule", "fil_set_extrapolation",
-            "fil_extrapolation", "fil_set_broyden_memory"]
+            "fil_extrapolation", "fil_set_broyden_memory", "fil_set_source_split",
+            "fil_source_split"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_SEG = 800, 256, 192, 32
 MLP_NPARAM = 256 * 800 + 256 + 2 * (256 * 256 + 256) + 192 * 256 + 192
 FIL_WARM_BEST_OF_TWO, FIL_WARM_PREDICTION_FIRST = 0, 1
@@ -94,6 +95,8 @@ def load_library(path=LIB_PATH):
         "fil_set_j0_reuse": [P, ctypes.c_int32],
         "fil_set_pair_schedule": [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
         "fil_pair_schedule": [P, I32, I32, I32],
+        "fil_set_source_split": [P, ctypes.c_int32],
+        "fil_source_split": [P, I32],
         "fil_j0_stats": [P, I64, I64],
         "fil_set_extrapolation": [P, ctypes.c_int32],
         "fil_set_broyden_memory": [P, ctypes.c_int32],
@@ -206,6 +209,16 @@ def fil_pair_schedule(ctx):
     t, p, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(ctx, _lib.fil_pair_schedule(ctx, ctypes.byref(t), ctypes.byref(p), ctypes.byref(c)))
     return t.value, p.value, c.value
+
+
+def fil_set_source_split(ctx, split):
+    _check(ctx, _lib.fil_set_source_split(ctx, int(split)))
+
+
+def fil_source_split(ctx):
+    v = ctypes.c_int32()
+    _check(ctx, _lib.fil_source_split(ctx, ctypes.byref(v)))
+    return v.value
 
 
 def fil_set_graph(ctx, enable):

@@ -9,7 +9,7 @@ component. C_MIXED = 4 * 32 + 16: each group of 32 sources is accumulated by
 4 FP32 FMAs per component and pair (<= 128 roundings of the running sum), each
 pair term carries <= ~12 roundings (hi/lo difference, rsqrt, products) and the
 inputs are rounded to FP32 once; the compensated fold of the group sums and
-the FP64 reduce add O(u^2).
+the float-float sums of the partials add O(u^2).
 """
 import os
 
@@ -182,26 +182,51 @@ def test_apply_captured_in_a_cuda_graph(fil):
         np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
 
 
-SCHEDULES = [(256, 2, 4), (128, 1, 4), (128, 1, 1), (256, 2, 1)]
+SCHEDULES = [(256, 2, 4, 1), (128, 1, 4, 1), (128, 1, 1, 1), (256, 2, 1, 1), (128, 1, 2, 2),
+             (128, 1, 1, 2)]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
 @pytest.mark.parametrize("segs", [[32] * 100, [64] * 17 + [5], [3, 254, 2]])
 def test_pair_schedules(fil, sched, segs):
     """Every pair schedule the autotuner chooses from (256-target tiles with 2
-    targets per thread, 128-target tiles with 1, one to several resident CTAs
-    per SM), set by hand, against the oracle."""
+    targets per thread, 128-target tiles with 1 and the sources of a chunk
+    split over one or two halves of the CTA, one to several resident CTAs per
+    SM), set by hand, against the oracle."""
     S = sum(segs)
     rng = np.random.default_rng(S + sched[0] + sched[1])
     Y = rng.uniform(0, max(4.0, S ** (1 / 3) * 3.0), size=(S, 3))
     FT = rng.standard_normal((S, 6))
     ref, ref_abs = rpy.apply(Y, FT, with_abs=True, nthreads=8)
     with fil.Filaments(segs, precision=fil.FIL_PAIR32) as m:
-        m.set_pair_schedule(*sched)
-        assert m.pair_schedule() == sched
+        m.set_pair_schedule(*sched[:3])
+        m.set_source_split(sched[3])
+        assert m.pair_schedule() == sched[:3] and m.source_split() == sched[3]
         VW = np.zeros((S, 6))
         m.mobility_apply(Y, FT, VW)
     _check_mixed(VW, ref, ref_abs)
+
+
+def test_source_split_on_the_c1_workload(fil):
+    """The split kernel on the 3200-segment random-walk suspension (5% volume
+    fraction: many close groups, own groups on every diagonal chunk) against the
+    oracle, and against the unsplit kernel (the same pair terms, summed in
+    another order: within the mixed bound of each other)."""
+    Y, FT = mobility_inputs(100, 32, seed=0)
+    ref, ref_abs = rpy.apply(Y, FT, with_abs=True, nthreads=8)
+    out = {}
+    for split in (1, 2):
+        with fil.Filaments([32] * 100, precision=fil.FIL_PAIR32) as m:
+            m.set_pair_schedule(128, 1, 2)
+            m.set_source_split(split)
+            VW = np.zeros_like(ref)
+            m.mobility_apply(Y, FT, VW)
+            VW2 = np.zeros_like(ref)
+            m.mobility_apply(Y, FT, VW2)
+            np.testing.assert_array_equal(VW, VW2)   # deterministic
+        _check_mixed(VW, ref, ref_abs)
+        out[split] = VW
+    assert np.all(np.abs(out[1] - out[2]) <= 2 * C_MIXED * U32 * ref_abs)
 
 
 def test_pair_schedule_rejections(fil):
@@ -212,3 +237,20 @@ def test_pair_schedule_rejections(fil):
             assert e.value.status == fil.FIL_EINVAL
         m.set_pair_schedule(128, 1, 2)
         assert m.pair_schedule() == (128, 1, 2)
+        # the source split: 1 or 2, and 2 only with one target per thread
+        for bad in (0, 3):
+            with pytest.raises(fil.FilError) as e:
+                m.set_source_split(bad)
+            assert e.value.status == fil.FIL_EINVAL
+        m.set_source_split(2)
+        assert m.source_split() == 2
+        m.set_pair_schedule(256, 2, 1)
+        assert m.source_split() == 1          # a new schedule starts unsplit
+        with pytest.raises(fil.FilError) as e:
+            m.set_source_split(2)
+        assert e.value.status == fil.FIL_EINVAL
+    with fil.Filaments([32] * 4, precision=fil.FIL_FP64) as m:
+        m.set_pair_schedule(128, 1, 1)
+        with pytest.raises(fil.FilError) as e:
+            m.set_source_split(2)             # the FP64 kernel has no split
+        assert e.value.status == fil.FIL_EINVAL
