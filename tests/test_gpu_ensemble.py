@@ -36,11 +36,14 @@ def _positions(rng, segs, box):
     return np.concatenate(Y)
 
 
-@pytest.mark.parametrize("tune", [False, True, (128, 1, 3)])
+@pytest.mark.parametrize("tune", [False, True, (128, 1, 3), (128, 1, 2, 2)])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_mobility_is_block_diagonal_over_systems(fil, prec, tune):
     """The ensemble apply couples only segments of the same system, under the
-    default schedule, the autotuner's choice and a schedule set by hand."""
+    default schedule, the autotuner's choice and schedules set by hand (the
+    last with the source split, which the FP64 path does not have)."""
+    if isinstance(tune, tuple) and len(tune) > 3 and prec == 0:
+        pytest.skip("no source split on the FP64 path")
     rng = np.random.default_rng(prec)
     Ys, FTs = [], []
     for segs in SYSTEMS:
@@ -51,7 +54,9 @@ def test_mobility_is_block_diagonal_over_systems(fil, prec, tune):
     with fil.Filaments(segs_all, fil_per_sys=[len(s) for s in SYSTEMS], precision=prec,
                        max_iter=10) as m:
         if isinstance(tune, tuple):
-            m.set_pair_schedule(*tune)
+            m.set_pair_schedule(*tune[:3])
+            if len(tune) > 3:
+                m.set_source_split(tune[3])
         elif tune:
             m.set_state(Y, np.tile([1.0, 0.0, 0.0, 0.0], (len(Y), 1)))
             tile, ctas, ms = m.autotune(2)
@@ -143,13 +148,16 @@ def test_graph_iterations_reproduce_launched_iterations(fil, prec):
     np.testing.assert_array_equal(out[True][1], out[False][1])
 
 
+@pytest.mark.parametrize("split", [1, 2])
 @pytest.mark.parametrize("j0", [(0, "drag"), (1, "rpy")])
 @pytest.mark.parametrize("prec", [1, 2])
-def test_mixed_ensemble_converges_close_to_fp64(fil, j0, prec):
+def test_mixed_ensemble_converges_close_to_fp64(fil, j0, prec, split):
     """The mixed modes (FP32 pair sums; FIL_MIXED also FP32 J0 solves and FP32
     Broyden history) on an ensemble: every system converges to the oracle's FP64
     trajectory within the accuracy its tolerance allows, and every system's
-    ||f||_inf meets it."""
+    ||f||_inf meets it; with the one-target pair kernel, unsplit and with its
+    sources split over two halves of each CTA (late iterations then run the
+    split kernel over the short list of tiles still active)."""
     systems = [[16], [20, 33, 7], [30] * 5, [1, 2, 3]]
     p = fo.Params(a=1.0, eta=1.0, dL=2.2, KB=2.0, KT=1.5, dt=0.2, tol=1e-6, max_iter=80)
     states, exts, lays = [], [], []
@@ -164,6 +172,8 @@ def test_mixed_ensemble_converges_close_to_fp64(fil, j0, prec):
                        precision=prec, j0_model=j0[0]) as m:
         m.set_state(np.concatenate([s.Y for s in states]), np.concatenate([s.q for s in states]))
         m.set_external(np.concatenate([e.Fext for e in exts]), None, None)
+        m.set_pair_schedule(128, 1, 2)
+        m.set_source_split(split)
         Y = np.zeros((m.S, 3))
         for _ in range(3):
             m.step()
