@@ -817,17 +817,24 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
         // left out (a small system would otherwise cost a whole padded tile x
         // chunk at the FP64 rate)
         const int64_t nsrc = smap.tile_nsrc ? smap.tile_nsrc[tile] : smap.n_src;
+        // A tile whose real targets fit in one warp (a system of <= 32 segments)
+        // would leave three of the four warps idle, and one warp issues FP64
+        // only through its own sub-partition's share of the SM's small FP64
+        // rate: then every warp takes the first warp's targets and every fourth
+        // source, and the four sums are added in warp order before the partial.
+        const bool narrow = nsrc - (ptile * kTile - src0) <= 32;
+        const int wid = tid >> 5;
 
         double ty[TPT][3];
         bool live[TPT];
         bool any = false;
 #pragma unroll
         for (int t = 0; t < TPT; ++t) {
-            const int64_t n = ptile * kTile + t * kRpyThreads + tid;
+            const int64_t n = ptile * kTile + t * kRpyThreads + (narrow ? (tid & 31) : tid);
             ty[t][0] = src[9 * n];
             ty[t][1] = src[9 * n + 1];
             ty[t][2] = src[9 * n + 2];
-            live[t] = n - src0 < nsrc;
+            live[t] = (!narrow || t == 0) && n - src0 < nsrc;
             any = any || live[t];
         }
         double acc[TPT][6];
@@ -855,8 +862,9 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
             }
             const double *s = sm[buf];
             const int jmax = any ? (int)min((int64_t)kRpyChunk, nsrc - ch * kRpyChunk) : 0;
+            const int jstep = narrow ? kRpyThreads / 32 : 1;
 #pragma unroll 2
-            for (int j = 0; j < jmax; ++j) {
+            for (int j = narrow ? wid : 0; j < jmax; j += jstep) {
 #pragma unroll
                 for (int t = 0; t < TPT; ++t)
                     if (live[t]) pair64(ty[t][0], ty[t][1], ty[t][2], s + 9 * j, k, acc[t]);
@@ -869,6 +877,25 @@ rpy_pair64_kernel(const double *__restrict__ src, SysMap smap, int64_t W, int G,
                 }
             }
             __syncthreads();
+        }
+        if (narrow) {
+            // the other warps' sums join the first warp's; their own slots (and
+            // the second slot of every thread) are padding and stay zero. The
+            // buffer is next written after the next segment's first barrier.
+            __shared__ double red64[kRpyThreads / 32 - 1][6][32];
+            if (wid > 0) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    red64[wid - 1][c][tid & 31] = acc[0][c];
+                    acc[0][c] = 0.0;
+                }
+            }
+            __syncthreads();
+            if (wid == 0) {
+                for (int w = 0; w < kRpyThreads / 32 - 1; ++w)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) acc[0][c] += red64[w][c][tid];
+            }
         }
         double *p = part + (size_t)(b + tile) * 6 * kTile;
 #pragma unroll
